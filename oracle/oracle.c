@@ -1,0 +1,964 @@
+/*
+ * oracle.c -- plain, slow FP64 reference of the raycasting method.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the oracle against which the CUDA
+ * library is checked. Only the test suite, the package smoke check and the
+ * bench's CPU-baseline leg may load it. It shares no code, header, table or
+ * helper with the CUDA library, and it never reads anything the library wrote.
+ *
+ * What it computes (Adeshina et al., "Hardware-Accelerated Raycasting: Towards
+ * an Effective Brain MRI Visualization", Sec. 4.1-4.2):
+ *   - one viewing ray per pixel, from the eye through the pixel centre into the
+ *     volume (Sec. 4.1, step 1: the path of the ray);
+ *   - evenly spaced samples S_k along the ray inside the volume, each the
+ *     trilinear resample of the voxel grid (Sec. 4.1 step 2; Sec. 3.2 names
+ *     trilinear filtering as the resampling filter);
+ *   - classification of each sample by the transfer function into colour and
+ *     opacity (Sec. 2.6, Sec. 4.2);
+ *   - the compositing ray function (Sec. 4.1 step 3, Sec. 4.2): the intensity
+ *     reaching the eye is the sum of the sample emissions I(S_k), each
+ *     attenuated by e^{-tau(S_k, S_eye)} (Eq. 3-4), the discrete form of the
+ *     integral of Eq. 5. Over one sample segment e^{-tau} is that segment's
+ *     transparency (1 - alpha'), so the attenuation from S_k to the eye is the
+ *     product of the transparencies of the samples in front of S_k;
+ *   - the other ray functions the paper lists (Sec. 2.4 item ii, Sec. 4.1):
+ *     maximum intensity projection, average intensity projection, x-ray sum,
+ *     isosurface (first crossing) and thresholding (first sample above).
+ *
+ * Readings where the paper is silent (each one is a written specification that
+ * the CUDA library implements on its own):
+ *   - index space has voxel centres at integers; world x = i * spacing;
+ *   - the camera basis is computed in FP64 from (eye, target, up) and rounded
+ *     to FP32; ray directions and sample positions use the FP32 operations
+ *     written out in ray_setup_f32, sample_t and position_at_t, each correctly
+ *     rounded;
+ *     every step after the sample position is FP64;
+ *   - opacity is given per reference step (the finest voxel spacing) and is
+ *     corrected to the step used: alpha' = 1 - (1 - alpha)^(ds / ds_ref), which
+ *     is Eq. 3's e^{-tau} for a segment of length ds;
+ *   - early termination after the first sample whose accumulated opacity is
+ *     >= term; the first decision inside +-tie_band of term is reported and the
+ *     result of the other branch is returned beside the primary one;
+ *   - headlight Blinn-Phong shading with central-difference gradients (the
+ *     paper's "simulated light effect", Sec. 2.4).
+ *
+ * Build: gcc -O2 -std=gnu11 -ffp-contract=off -fPIC -shared -pthread
+ * (no contraction: each FP32 operation of the ray specification rounds once).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#if defined(__FLT_EVAL_METHOD__) && __FLT_EVAL_METHOD__ != 0
+#error "the FP32 ray specification needs FLT_EVAL_METHOD == 0"
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* public records (mirrored by oracle/__init__.py)                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const uint16_t *data;   /* x fastest, then y, then z */
+    int32_t nx, ny, nz;
+    float sx, sy, sz;       /* voxel spacing, mm */
+    int32_t vmax;           /* largest valid code; larger codes clamp to it */
+    int32_t value_mode;     /* 0: raw codes; 1: FP16 of code/vmax (normalised) */
+} orc_volume;
+
+typedef struct {
+    const float *rgba;      /* K x 4, straight colour + opacity per reference step */
+    int32_t K;
+    int32_t fp16;           /* 1: use the FP16 rounding of each entry */
+} orc_tf;
+
+typedef struct {
+    float eye[3], target[3], up[3];
+    float fovy_deg;
+    int32_t width, height;
+} orc_camera;
+
+enum { ORC_COMPOSITE = 0, ORC_MIP = 1, ORC_AVERAGE = 2, ORC_XRAY = 3, ORC_ISO = 4, ORC_THRESHOLD = 5 };
+
+typedef struct {
+    float step_vox;     /* sample spacing in units of the finest voxel spacing */
+    float term;         /* early termination at accumulated opacity >= term */
+    int32_t shade;      /* 1: headlight Blinn-Phong */
+    float ka, kd, ks;   /* ambient, diffuse, specular weights; exponent 16 */
+    int32_t func;       /* ray function, ORC_* */
+    float iso;          /* iso-value / threshold in volume value units */
+    int32_t fp64_rays;  /* 1: ray setup in FP64 (information only) */
+    float tie_band;     /* half width of the termination tie band */
+} orc_params;
+
+/* ------------------------------------------------------------------------ */
+/* internal state                                                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const uint16_t *v;
+    int n[3];
+    float s[3];
+    double vrange;          /* value of full scale: vmax (raw) or 1 (normalised) */
+    double *lut;            /* value of each code, after the vmax clamp */
+    double *tf;             /* K x 4 */
+    int K;
+    float f[3], r[3], u[3], tx, ty, o[3];   /* FP32 camera record */
+    double fd[3], rd[3], ud[3], txd, tyd, od[3];
+    int W, H;
+    orc_params P;
+    float smin;             /* reference step ds_ref = finest spacing */
+} scene;
+
+typedef struct {
+    int hit;
+    float o[3], d[3], dir[3], tn, tf, ds;
+    double od[3], dd[3], dird[3], tnd, tfd, dsd;
+    int fp64;
+    int nsamp;
+} ray;
+
+static double half_round(float x) { return (double)(_Float16)x; }
+
+static void normalize3(double v[3]) {
+    double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n; v[1] /= n; v[2] /= n;
+}
+
+static void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static int scene_init(scene *S, const orc_volume *vol, const orc_tf *tf,
+                      const orc_camera *cam, const orc_params *prm) {
+    memset(S, 0, sizeof *S);
+    if (vol->nx < 2 || vol->ny < 2 || vol->nz < 2 || vol->vmax < 1) return 1;
+    if (!(vol->sx > 0 && vol->sy > 0 && vol->sz > 0)) return 1;
+    if (tf->K < 2 || cam->width < 1 || cam->height < 1) return 1;
+    S->v = vol->data;
+    S->n[0] = vol->nx; S->n[1] = vol->ny; S->n[2] = vol->nz;
+    S->s[0] = vol->sx; S->s[1] = vol->sy; S->s[2] = vol->sz;
+    S->lut = (double *)malloc(65536 * sizeof(double));
+    S->tf = (double *)malloc((size_t)tf->K * 4 * sizeof(double));
+    if (!S->lut || !S->tf) return 2;
+    for (int code = 0; code < 65536; code++) {
+        int c = code > vol->vmax ? vol->vmax : code;
+        S->lut[code] = vol->value_mode ? half_round((float)c / (float)vol->vmax) : (double)c;
+    }
+    S->vrange = vol->value_mode ? 1.0 : (double)vol->vmax;
+    S->K = tf->K;
+    for (int i = 0; i < 4 * tf->K; i++)
+        S->tf[i] = tf->fp16 ? half_round(tf->rgba[i]) : (double)tf->rgba[i];
+    S->P = *prm;
+    S->W = cam->width; S->H = cam->height;
+    S->smin = fminf(fminf(vol->sx, vol->sy), vol->sz);
+
+    /* camera basis in FP64 (look-at), rounded once to FP32 */
+    double f[3], up[3], r[3], u[3];
+    for (int c = 0; c < 3; c++) {
+        f[c] = (double)cam->target[c] - (double)cam->eye[c];
+        up[c] = (double)cam->up[c];
+    }
+    normalize3(f);
+    cross3(f, up, r);
+    normalize3(r);
+    cross3(r, f, u);
+    double th = tan((double)cam->fovy_deg * 3.14159265358979323846 / 360.0);
+    double tx = th * (double)cam->width / (double)cam->height;
+    for (int c = 0; c < 3; c++) {
+        S->fd[c] = f[c]; S->rd[c] = r[c]; S->ud[c] = u[c];
+        S->f[c] = (float)f[c]; S->r[c] = (float)r[c]; S->u[c] = (float)u[c];
+        S->od[c] = (double)cam->eye[c] / (double)S->s[c];
+        S->o[c] = (float)S->od[c];
+    }
+    S->txd = tx; S->tyd = th;
+    S->tx = (float)tx; S->ty = (float)th;
+    return 0;
+}
+
+static void scene_free(scene *S) {
+    free(S->lut);
+    free(S->tf);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.1 step 1: the path of the ray                                       */
+/* ------------------------------------------------------------------------ */
+/* FP32 ray specification; each operation rounds once (no contraction). */
+static void ray_setup_f32(const scene *S, float step_vox, int x, int y, ray *R) {
+    float a = ((float)x + 0.5f) / (float)S->W;
+    float ndcx = (a * 2.0f - 1.0f) * S->tx;
+    float b = ((float)y + 0.5f) / (float)S->H;
+    float ndcy = (1.0f - b * 2.0f) * S->ty;
+    float v[3];
+    for (int c = 0; c < 3; c++) v[c] = (S->f[c] + ndcx * S->r[c]) + ndcy * S->u[c];
+    float len = sqrtf((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+    for (int c = 0; c < 3; c++) {
+        R->dir[c] = v[c] / len;
+        R->d[c] = R->dir[c] / S->s[c];
+        R->o[c] = S->o[c];
+    }
+    R->fp64 = 0;
+    R->hit = 0;
+    R->nsamp = 0;
+    /* slab test against the box [0, N-1] in index space; t is world distance */
+    float tn = 0.0f, tf = INFINITY;
+    for (int c = 0; c < 3; c++) {
+        float hi = (float)(S->n[c] - 1);
+        if (R->d[c] == 0.0f) {
+            if (R->o[c] < 0.0f || R->o[c] > hi) return;
+            continue;
+        }
+        float t0 = (0.0f - R->o[c]) / R->d[c];
+        float t1 = (hi - R->o[c]) / R->d[c];
+        tn = fmaxf(tn, fminf(t0, t1));
+        tf = fminf(tf, fmaxf(t0, t1));
+    }
+    if (!(tf >= tn)) return;
+    R->tn = tn;
+    R->tf = tf;
+    R->ds = step_vox * S->smin;
+    R->nsamp = (int)floorf((tf - tn) / R->ds) + 1;
+    R->hit = 1;
+}
+
+/* The same construction in FP64 (information only: not the parity target). */
+static void ray_setup_f64(const scene *S, float step_vox, int x, int y, ray *R) {
+    double a = ((double)x + 0.5) / (double)S->W;
+    double ndcx = (a * 2.0 - 1.0) * S->txd;
+    double b = ((double)y + 0.5) / (double)S->H;
+    double ndcy = (1.0 - b * 2.0) * S->tyd;
+    double v[3];
+    for (int c = 0; c < 3; c++) v[c] = (S->fd[c] + ndcx * S->rd[c]) + ndcy * S->ud[c];
+    double len = sqrt((v[0] * v[0] + v[1] * v[1]) + v[2] * v[2]);
+    for (int c = 0; c < 3; c++) {
+        R->dird[c] = v[c] / len;
+        R->dd[c] = R->dird[c] / (double)S->s[c];
+        R->od[c] = S->od[c];
+    }
+    R->fp64 = 1;
+    R->hit = 0;
+    R->nsamp = 0;
+    double tn = 0.0, tf = INFINITY;
+    for (int c = 0; c < 3; c++) {
+        double hi = (double)(S->n[c] - 1);
+        if (R->dd[c] == 0.0) {
+            if (R->od[c] < 0.0 || R->od[c] > hi) return;
+            continue;
+        }
+        double t0 = (0.0 - R->od[c]) / R->dd[c];
+        double t1 = (hi - R->od[c]) / R->dd[c];
+        tn = fmax(tn, fmin(t0, t1));
+        tf = fmin(tf, fmax(t0, t1));
+    }
+    if (!(tf >= tn)) return;
+    R->tnd = tn;
+    R->tfd = tf;
+    R->dsd = (double)step_vox * (double)S->smin;
+    R->nsamp = (int)floor((tf - tn) / R->dsd) + 1;
+    R->hit = 1;
+}
+
+static void ray_setup(const scene *S, int x, int y, ray *R) {
+    if (S->P.fp64_rays) ray_setup_f64(S, S->P.step_vox, x, y, R);
+    else ray_setup_f32(S, S->P.step_vox, x, y, R);
+}
+
+/* world distance and index-space position of evenly spaced sample k */
+static double sample_t(const ray *R, int k) {
+    if (R->fp64) return R->tnd + (double)k * R->dsd;
+    return (double)fmaf((float)k, R->ds, R->tn);
+}
+
+static void position_at_t(const ray *R, double t, double p[3]) {
+    for (int c = 0; c < 3; c++) {
+        if (R->fp64) p[c] = R->od[c] + t * R->dd[c];
+        else p[c] = (double)fmaf((float)t, R->d[c], R->o[c]);
+    }
+}
+
+static double step_len(const ray *R) { return R->fp64 ? R->dsd : (double)R->ds; }
+
+static void world_dir(const ray *R, double dir[3]) {
+    for (int c = 0; c < 3; c++) dir[c] = R->fp64 ? R->dird[c] : (double)R->dir[c];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.1 step 2: the values along the ray (trilinear resampling)           */
+/* ------------------------------------------------------------------------ */
+static double voxel(const scene *S, int x, int y, int z) {
+    return S->lut[S->v[((size_t)z * S->n[1] + y) * S->n[0] + x]];
+}
+
+/* cell base index and weight along one axis; p is clamped to [0, n-1] */
+static void cell(double p, int n, int *i, double *w) {
+    double q = p < 0.0 ? 0.0 : (p > (double)(n - 1) ? (double)(n - 1) : p);
+    int b = (int)floor(q);
+    if (b > n - 2) b = n - 2;
+    *i = b;
+    *w = q - (double)b;
+}
+
+static double trilinear(const scene *S, const double p[3]) {
+    int i, j, k;
+    double wx, wy, wz;
+    cell(p[0], S->n[0], &i, &wx);
+    cell(p[1], S->n[1], &j, &wy);
+    cell(p[2], S->n[2], &k, &wz);
+    double c00 = voxel(S, i, j, k) * (1 - wx) + voxel(S, i + 1, j, k) * wx;
+    double c10 = voxel(S, i, j + 1, k) * (1 - wx) + voxel(S, i + 1, j + 1, k) * wx;
+    double c01 = voxel(S, i, j, k + 1) * (1 - wx) + voxel(S, i + 1, j, k + 1) * wx;
+    double c11 = voxel(S, i, j + 1, k + 1) * (1 - wx) + voxel(S, i + 1, j + 1, k + 1) * wx;
+    double c0 = c00 * (1 - wy) + c10 * wy;
+    double c1 = c01 * (1 - wy) + c11 * wy;
+    return c0 * (1 - wz) + c1 * wz;
+}
+
+/* central differences of the trilinear field, one index unit per axis,
+ * divided by the spacing: a world-space gradient (value units per mm) */
+static void gradient(const scene *S, const double p[3], double g[3]) {
+    for (int a = 0; a < 3; a++) {
+        double q[3] = {p[0], p[1], p[2]};
+        q[a] = p[a] + 1.0;
+        double fp = trilinear(S, q);
+        q[a] = p[a] - 1.0;
+        double fm = trilinear(S, q);
+        g[a] = (fp - fm) / 2.0 / (double)S->s[a];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* classification (Sec. 2.6) and shading                                      */
+/* ------------------------------------------------------------------------ */
+/* table coordinate of a value: u = v (K-1) / full scale */
+static double tf_coord(const scene *S, double v) { return v * (double)(S->K - 1) / S->vrange; }
+
+static void classify(const scene *S, double u, double rgba[4], int *i0, double *w0) {
+    double q = u < 0.0 ? 0.0 : (u > (double)(S->K - 1) ? (double)(S->K - 1) : u);
+    int i = (int)floor(q);
+    if (i > S->K - 2) i = S->K - 2;
+    double w = q - (double)i;
+    for (int c = 0; c < 4; c++) rgba[c] = S->tf[4 * i + c] * (1 - w) + S->tf[4 * (i + 1) + c] * w;
+    if (i0) *i0 = i;
+    if (w0) *w0 = w;
+}
+
+/* headlight Blinn-Phong: light and view both along -dir, so the half vector is
+ * the light vector; two-sided |n.L|. dcol[c] = d colour / d rgb[c]. */
+static void shade(const scene *S, const double rgb[3], const double g[3], const double dir[3],
+                  double col[3], double dcol[3]) {
+    const orc_params *P = &S->P;
+    double gl = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double sf, spec;
+    if (gl < 1e-6 * S->vrange) {
+        sf = (double)P->ka + (double)P->kd;
+        spec = 0.0;
+    } else {
+        double ndl = fabs(g[0] * dir[0] + g[1] * dir[1] + g[2] * dir[2]) / gl;
+        double n2 = ndl * ndl, n4 = n2 * n2, n8 = n4 * n4, n16 = n8 * n8;
+        sf = (double)P->ka + (double)P->kd * ndl;
+        spec = (double)P->ks * n16;
+    }
+    for (int c = 0; c < 3; c++) {
+        double x = rgb[c] * sf + spec;
+        col[c] = x < 1.0 ? x : 1.0;
+        dcol[c] = x < 1.0 ? sf : 0.0;
+    }
+}
+
+/* opacity per reference step -> opacity of a segment of length ds (Eq. 3) */
+static double correct_alpha(double a, double ratio) { return 1.0 - pow(1.0 - a, ratio); }
+
+/* all quantities of one sample */
+typedef struct {
+    double t, p[3], v, u, rgba[4], a, col[3], dcol[3], w;
+    int i;
+} sample;
+
+static void eval_sample(const scene *S, const ray *R, double t, double ratio, sample *s) {
+    s->t = t;
+    position_at_t(R, t, s->p);
+    s->v = trilinear(S, s->p);
+    s->u = tf_coord(S, s->v);
+    classify(S, s->u, s->rgba, &s->i, &s->w);
+    s->a = correct_alpha(s->rgba[3], ratio);
+    if (S->P.shade) {
+        double g[3], dir[3];
+        gradient(S, s->p, g);
+        world_dir(R, dir);
+        shade(S, s->rgba, g, dir, s->col, s->dcol);
+    } else {
+        for (int c = 0; c < 3; c++) { s->col[c] = s->rgba[c]; s->dcol[c] = 1.0; }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.1 step 3: the ray functions                                          */
+/* ------------------------------------------------------------------------ */
+/* Compositing (Sec. 4.2, Eq. 4): I = sum_k T_k alpha'_k c_k with
+ * T_k = prod_{j<k} (1 - alpha'_j), evaluated from the eye backwards into the
+ * volume, stopped after the first sample whose opacity 1 - T reaches term.
+ * flip_k >= 0 inverts the stop decision at that sample (tie alternative). */
+static void composite(const scene *S, const ray *R, int flip_k, double out[4], int *nsamp,
+                      int *tie_k) {
+    double C[3] = {0, 0, 0}, T = 1.0;
+    double ratio = step_len(R) / (double)S->smin;
+    int k = 0;
+    if (tie_k) *tie_k = -1;
+    for (; k < R->nsamp; k++) {
+        sample s;
+        eval_sample(S, R, sample_t(R, k), ratio, &s);
+        for (int c = 0; c < 3; c++) C[c] += T * s.a * s.col[c];
+        T *= (1.0 - s.a);
+        double opacity = 1.0 - T;
+        int stop = opacity >= (double)S->P.term;
+        if (tie_k && *tie_k < 0 && fabs(opacity - (double)S->P.term) < (double)S->P.tie_band)
+            *tie_k = k;
+        if (k == flip_k) stop = !stop;
+        if (stop) { k++; break; }
+    }
+    out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
+    *nsamp = k;
+}
+
+/* MIP, average, x-ray, isosurface and threshold (Sec. 2.4 ii, Sec. 4.1).
+ * Output channels: MIP/average: (m, m, m, 1) with m the max / mean value over
+ * full scale; x-ray: (x, x, x, 1) with x = sum_k v_k ds / full scale (mm);
+ * isosurface: (t*, shaded intensity at the crossing sample, k*, 1) with t* the
+ * linearly interpolated crossing distance between the two bracketing samples;
+ * threshold: (TF colour of the first sample >= iso, 1). 0 when nothing is
+ * found or the ray misses. */
+static void other_function(const scene *S, const ray *R, double out[4], int *nsamp) {
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    int func = S->P.func;
+    double acc = 0.0, prev_v = 0.0, prev_t = 0.0;
+    *nsamp = R->nsamp;
+    if (R->nsamp <= 0) return;
+    for (int k = 0; k < R->nsamp; k++) {
+        double p[3], t = sample_t(R, k);
+        position_at_t(R, t, p);
+        double v = trilinear(S, p);
+        if (func == ORC_MIP) {
+            if (k == 0 || v > acc) acc = v;
+        } else if (func == ORC_AVERAGE || func == ORC_XRAY) {
+            acc += v;
+        } else if (v >= (double)S->P.iso) {
+            *nsamp = k + 1;
+            if (func == ORC_THRESHOLD) {
+                double rgba[4];
+                classify(S, tf_coord(S, v), rgba, NULL, NULL);
+                out[0] = rgba[0]; out[1] = rgba[1]; out[2] = rgba[2]; out[3] = 1.0;
+            } else {
+                double ts = t;
+                if (k > 0) ts = prev_t + (t - prev_t) * ((double)S->P.iso - prev_v) / (v - prev_v);
+                double g[3], dir[3], white[3] = {1, 1, 1}, col[3], dcol[3];
+                gradient(S, p, g);
+                world_dir(R, dir);
+                shade(S, white, g, dir, col, dcol);
+                out[0] = ts; out[1] = col[0]; out[2] = (double)k; out[3] = 1.0;
+            }
+            return;
+        }
+        prev_v = v;
+        prev_t = t;
+    }
+    if (func == ORC_MIP) acc = acc / S->vrange;
+    else if (func == ORC_AVERAGE) acc = acc / (double)R->nsamp / S->vrange;
+    else if (func == ORC_XRAY) acc = acc * step_len(R) / S->vrange;
+    else return;
+    out[0] = out[1] = out[2] = acc;
+    out[3] = 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* threading over pixels                                                      */
+/* ------------------------------------------------------------------------ */
+typedef struct job job;
+typedef void (*pixel_fn)(job *J, int64_t idx, int tid);
+struct job {
+    const scene *S;
+    const int32_t *pix;
+    int64_t npix;
+    int64_t next;
+    pixel_fn fn;
+    int nthreads;
+    /* outputs / extra inputs */
+    double *rgba, *rgba_alt, *aux, *aux2;
+    uint8_t *tie;
+    int32_t *nsamp;
+    const double *dimg;
+    double *dtf_thread;     /* nthreads x K x 4 */
+    const float *pdf;
+    float lambda;
+    int nimp;
+    sample **scratch;       /* per thread */
+    int *cap;               /* per thread: samples the scratch holds */
+};
+
+typedef struct { job *J; int tid; } worker_arg;
+
+#define CHUNK 32
+
+static void *worker(void *arg) {
+    worker_arg *A = (worker_arg *)arg;
+    job *J = A->J;
+    for (;;) {
+        int64_t start = __atomic_fetch_add(&J->next, CHUNK, __ATOMIC_RELAXED);
+        if (start >= J->npix) break;
+        int64_t end = start + CHUNK < J->npix ? start + CHUNK : J->npix;
+        for (int64_t i = start; i < end; i++) J->fn(J, i, A->tid);
+    }
+    return NULL;
+}
+
+/* static round-robin chunks: results independent of thread timing */
+static void *worker_static(void *arg) {
+    worker_arg *A = (worker_arg *)arg;
+    job *J = A->J;
+    for (int64_t start = (int64_t)A->tid * CHUNK; start < J->npix;
+         start += (int64_t)J->nthreads * CHUNK) {
+        int64_t end = start + CHUNK < J->npix ? start + CHUNK : J->npix;
+        for (int64_t i = start; i < end; i++) J->fn(J, i, A->tid);
+    }
+    return NULL;
+}
+
+static void run_job(job *J, int nthreads, int deterministic) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    J->nthreads = nthreads;
+    J->next = 0;
+    pthread_t th[256];
+    worker_arg args[256];
+    for (int t = 0; t < nthreads; t++) {
+        args[t].J = J;
+        args[t].tid = t;
+    }
+    void *(*fn)(void *) = deterministic ? worker_static : worker;
+    int started = 0;
+    for (int t = 1; t < nthreads; t++) {
+        if (pthread_create(&th[t], NULL, fn, &args[t]) != 0) break;
+        started = t;
+    }
+    fn(&args[0]);
+    for (int t = 1; t <= started; t++) pthread_join(th[t], NULL);
+    /* threads that failed to start leave their static chunks: run them here */
+    if (deterministic)
+        for (int t = started + 1; t < nthreads; t++) fn(&args[t]);
+}
+
+static void pixel_xy(const job *J, int64_t idx, int *x, int *y) {
+    int64_t lin = J->pix ? (int64_t)J->pix[idx] : idx;
+    *x = (int)(lin % J->S->W);
+    *y = (int)(lin / J->S->W);
+}
+
+/* ------------------------------------------------------------------------ */
+/* rendering                                                                  */
+/* ------------------------------------------------------------------------ */
+static void render_pixel(job *J, int64_t idx, int tid) {
+    (void)tid;
+    const scene *S = J->S;
+    int x, y;
+    pixel_xy(J, idx, &x, &y);
+    ray R;
+    ray_setup(S, x, y, &R);
+    double out[4] = {0, 0, 0, 0}, alt[4] = {0, 0, 0, 0};
+    int ns = 0, tie_k = -1;
+    if (R.hit) {
+        if (S->P.func == ORC_COMPOSITE) {
+            composite(S, &R, -1, out, &ns, &tie_k);
+            if (tie_k >= 0) {
+                int ns2;
+                composite(S, &R, tie_k, alt, &ns2, NULL);
+            } else {
+                memcpy(alt, out, sizeof out);
+            }
+        } else {
+            other_function(S, &R, out, &ns);
+            memcpy(alt, out, sizeof out);
+        }
+    }
+    for (int c = 0; c < 4; c++) {
+        J->rgba[4 * idx + c] = out[c];
+        if (J->rgba_alt) J->rgba_alt[4 * idx + c] = alt[c];
+    }
+    if (J->tie) J->tie[idx] = (uint8_t)(tie_k >= 0);
+    if (J->nsamp) J->nsamp[idx] = ns;
+}
+
+int orc_render(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
+               const orc_params *prm, const int32_t *pix, int64_t npix, double *rgba,
+               double *rgba_alt, uint8_t *tie, int32_t *nsamp, int nthreads) {
+    scene S;
+    int rc = scene_init(&S, vol, tf, cam, prm);
+    if (rc) { scene_free(&S); return rc; }
+    job J;
+    memset(&J, 0, sizeof J);
+    J.S = &S;
+    J.pix = pix;
+    J.npix = pix ? npix : (int64_t)cam->width * cam->height;
+    J.fn = render_pixel;
+    J.rgba = rgba;
+    J.rgba_alt = rgba_alt;
+    J.tie = tie;
+    J.nsamp = nsamp;
+    run_job(&J, nthreads, 0);
+    scene_free(&S);
+    return 0;
+}
+
+/* every sample of one ray, no termination; record of 14 doubles per sample:
+ * t, px, py, pz, v, u, r, g, b, a, a', col r, col g, col b */
+int orc_ray_samples(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
+                    const orc_params *prm, int x, int y, int max_samples, double *out,
+                    int32_t *nsamp_total) {
+    scene S;
+    int rc = scene_init(&S, vol, tf, cam, prm);
+    if (rc) { scene_free(&S); return rc; }
+    ray R;
+    ray_setup(&S, x, y, &R);
+    *nsamp_total = R.hit ? R.nsamp : 0;
+    double ratio = R.hit ? step_len(&R) / (double)S.smin : 1.0;
+    for (int k = 0; R.hit && k < R.nsamp && k < max_samples; k++) {
+        sample s;
+        eval_sample(&S, &R, sample_t(&R, k), ratio, &s);
+        double *o = out + 14 * (size_t)k;
+        o[0] = s.t; o[1] = s.p[0]; o[2] = s.p[1]; o[3] = s.p[2]; o[4] = s.v; o[5] = s.u;
+        for (int c = 0; c < 4; c++) o[6 + c] = s.rgba[c];
+        o[10] = s.a;
+        for (int c = 0; c < 3; c++) o[11 + c] = s.col[c];
+    }
+    scene_free(&S);
+    return 0;
+}
+
+/* ray geometry for tests: (hit, tn, tf, ds, nsamp, o[3], d[3], dir[3]) */
+int orc_ray_geometry(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
+                     const orc_params *prm, int x, int y, double *out) {
+    scene S;
+    int rc = scene_init(&S, vol, tf, cam, prm);
+    if (rc) { scene_free(&S); return rc; }
+    ray R;
+    ray_setup(&S, x, y, &R);
+    out[0] = R.hit;
+    out[1] = R.fp64 ? R.tnd : R.tn;
+    out[2] = R.fp64 ? R.tfd : R.tf;
+    out[3] = step_len(&R);
+    out[4] = R.nsamp;
+    for (int c = 0; c < 3; c++) {
+        out[5 + c] = R.fp64 ? R.od[c] : R.o[c];
+        out[8 + c] = R.fp64 ? R.dd[c] : R.d[c];
+        out[11 + c] = R.fp64 ? R.dird[c] : R.dir[c];
+    }
+    scene_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* transfer-function gradient of the compositing function                     */
+/* ------------------------------------------------------------------------ */
+/* For one ray with samples k = 0..n-1 (n up to termination) the image is
+ * I_c = sum_k T_k a'_k col_kc (c = r, g, b) and I_a = 1 - T_n, with
+ * T_{k+1} = T_k (1 - a'_k). Plain reverse-mode differentiation over the stored
+ * samples: with G_{k} = dL/dT_k, G_n = -dL/dI_a and
+ *   dL/da'_k  = T_k (g . col_k) - G_{k+1} T_k
+ *   dL/dcol_kc = g_c T_k a'_k
+ *   G_k       = a'_k (g . col_k) + G_{k+1} (1 - a'_k).
+ * Then da'/da = r (1 - min(a, 1 - 1e-6))^(r - 1) and the table entries i, i+1
+ * receive the lerp weights (1 - w, w). */
+static void grad_pixel(job *J, int64_t idx, int tid) {
+    const scene *S = J->S;
+    int x, y;
+    pixel_xy(J, idx, &x, &y);
+    ray R;
+    ray_setup(S, x, y, &R);
+    double out[4] = {0, 0, 0, 0};
+    double *dtf = J->dtf_thread + (size_t)tid * S->K * 4;
+    if (!R.hit) {
+        if (J->rgba) for (int c = 0; c < 4; c++) J->rgba[4 * idx + c] = 0.0;
+        return;
+    }
+    if (J->cap[tid] < R.nsamp) {
+        free(J->scratch[tid]);
+        J->scratch[tid] = (sample *)malloc((size_t)R.nsamp * sizeof(sample) +
+                                           ((size_t)R.nsamp + 1) * sizeof(double));
+        J->cap[tid] = J->scratch[tid] ? R.nsamp : 0;
+        if (!J->scratch[tid]) abort();
+    }
+    sample *sm = J->scratch[tid];
+    double *T = (double *)(sm + R.nsamp);
+    double ratio = step_len(&R) / (double)S->smin;
+    int n = 0;
+    T[0] = 1.0;
+    double C[3] = {0, 0, 0};
+    for (int k = 0; k < R.nsamp; k++) {
+        eval_sample(S, &R, sample_t(&R, k), ratio, &sm[k]);
+        for (int c = 0; c < 3; c++) C[c] += T[k] * sm[k].a * sm[k].col[c];
+        T[k + 1] = T[k] * (1.0 - sm[k].a);
+        n = k + 1;
+        if (1.0 - T[k + 1] >= (double)S->P.term) break;
+    }
+    out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T[n];
+    if (J->rgba) for (int c = 0; c < 4; c++) J->rgba[4 * idx + c] = out[c];
+    const double *g = J->dimg + 4 * idx;
+    double G = -g[3];
+    for (int k = n - 1; k >= 0; k--) {
+        const sample *s = &sm[k];
+        double gc = g[0] * s->col[0] + g[1] * s->col[1] + g[2] * s->col[2];
+        double dA = T[k] * gc - G * T[k];
+        G = s->a * gc + G * (1.0 - s->a);
+        double ac = s->rgba[3] < 1.0 - 1e-6 ? s->rgba[3] : 1.0 - 1e-6;
+        double dalpha = dA * ratio * pow(1.0 - ac, ratio - 1.0);
+        for (int c = 0; c < 3; c++) {
+            double dcol = g[c] * T[k] * s->a * s->dcol[c];
+            dtf[4 * s->i + c] += (1.0 - s->w) * dcol;
+            dtf[4 * (s->i + 1) + c] += s->w * dcol;
+        }
+        dtf[4 * s->i + 3] += (1.0 - s->w) * dalpha;
+        dtf[4 * (s->i + 1) + 3] += s->w * dalpha;
+    }
+}
+
+int orc_render_grad(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
+                    const orc_params *prm, const int32_t *pix, int64_t npix,
+                    const double *dimg, double *dtf, double *rgba, int nthreads) {
+    scene S;
+    int rc = scene_init(&S, vol, tf, cam, prm);
+    if (rc) { scene_free(&S); return rc; }
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    job J;
+    memset(&J, 0, sizeof J);
+    J.S = &S;
+    J.pix = pix;
+    J.npix = pix ? npix : (int64_t)cam->width * cam->height;
+    J.fn = grad_pixel;
+    J.dimg = dimg;
+    J.rgba = rgba;
+    J.dtf_thread = (double *)calloc((size_t)nthreads * S.K * 4, sizeof(double));
+    J.scratch = (sample **)calloc((size_t)nthreads, sizeof(sample *));
+    J.cap = (int *)calloc((size_t)nthreads, sizeof(int));
+    int ok = J.dtf_thread && J.scratch && J.cap;
+    if (ok) {
+        run_job(&J, nthreads, 1);
+        memset(dtf, 0, (size_t)S.K * 4 * sizeof(double));
+        for (int t = 0; t < nthreads; t++)
+            for (int i = 0; i < S.K * 4; i++) dtf[i] += J.dtf_thread[(size_t)t * S.K * 4 + i];
+    }
+    for (int t = 0; J.scratch && t < nthreads; t++) free(J.scratch[t]);
+    free(J.scratch);
+    free(J.cap);
+    free(J.dtf_thread);
+    scene_free(&S);
+    return ok ? 0 : 2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* opacity profiles along the ray (training targets of the learned proposal)  */
+/* ------------------------------------------------------------------------ */
+/* 512 samples at the centres of 512 equal segments of [t_near, t_far]
+ * (t_k = fmaf(k + 0.5, L / 512, t_near) in FP32), composited without early
+ * termination; the weights T_k a'_k are summed 16 at a time into 32 bins.
+ * aux = 32 bins per pixel, aux2 = final transmittance. */
+#define PROF_SAMPLES 512
+#define PROF_BINS 32
+
+static void profile_pixel(job *J, int64_t idx, int tid) {
+    (void)tid;
+    const scene *S = J->S;
+    int x, y;
+    pixel_xy(J, idx, &x, &y);
+    ray R;
+    ray_setup_f32(S, S->P.step_vox, x, y, &R);
+    double *bins = J->aux + (size_t)PROF_BINS * idx;
+    for (int b = 0; b < PROF_BINS; b++) bins[b] = 0.0;
+    double T = 1.0;
+    if (R.hit) {
+        float delta = (R.tf - R.tn) / (float)PROF_SAMPLES;
+        double ratio = (double)delta / (double)S->smin;
+        for (int k = 0; k < PROF_SAMPLES; k++) {
+            float t = fmaf((float)k + 0.5f, delta, R.tn);
+            sample s;
+            eval_sample(S, &R, (double)t, ratio, &s);
+            bins[k / (PROF_SAMPLES / PROF_BINS)] += T * s.a;
+            T *= (1.0 - s.a);
+        }
+    }
+    J->aux2[idx] = T;
+}
+
+int orc_profiles(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
+                 const orc_params *prm, const int32_t *pix, int64_t npix, double *bins,
+                 double *tfinal, int nthreads) {
+    scene S;
+    int rc = scene_init(&S, vol, tf, cam, prm);
+    if (rc) { scene_free(&S); return rc; }
+    job J;
+    memset(&J, 0, sizeof J);
+    J.S = &S;
+    J.pix = pix;
+    J.npix = pix ? npix : (int64_t)cam->width * cam->height;
+    J.fn = profile_pixel;
+    J.aux = bins;
+    J.aux2 = tfinal;
+    run_job(&J, nthreads, 0);
+    scene_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* importance-sampled compositing from a per-ray opacity PDF                  */
+/* ------------------------------------------------------------------------ */
+/* The 32-bin PDF over [t_near, t_far] is mixed with the uniform density,
+ * q_b = (1 - lambda) pdf_b + lambda / 32, and nimp stratified quantiles
+ * (j + 0.5) / nimp of its piecewise-linear CDF give the sample distances t_j.
+ * Sample j stands for the segment between the midpoints to its neighbours
+ * (the first and last segments reach t_near and t_far), and its opacity is
+ * corrected to that segment's length. Positions follow this FP32
+ * specification (each operation rounds once):
+ *   L = t_far - t_near; bw = L / 32; om = 1 - lambda; lu = lambda / 32;
+ *   q_b = fmaf(om, pdf_b, lu); F_0 = 0, F_{b+1} = F_b + q_b;
+ *   target_j = ((j + 0.5) / nimp) * F_32;
+ *   b_j = last b in [0, 31] with F_b <= target_j;
+ *   f_j = min(max((target_j - F_b) / q_b, 0), 1); t_j = fmaf(b_j + f_j, bw, t_near);
+ *   m_j = (t_j + t_{j+1}) * 0.5 (m_{-1} = t_near, m_{nimp-1} = t_far);
+ *   seg_j = m_j - m_{j-1}.
+ * Compositing and early termination as in composite(). aux2 = T at the end. */
+static void importance_pixel(job *J, int64_t idx, int tid) {
+    (void)tid;
+    const scene *S = J->S;
+    int x, y;
+    pixel_xy(J, idx, &x, &y);
+    ray R;
+    ray_setup_f32(S, S->P.step_vox, x, y, &R);
+    double out[4] = {0, 0, 0, 0};
+    double T = 1.0;
+    int ns = 0;
+    if (R.hit && J->nimp > 0) {
+        const float *pdf = J->pdf + (size_t)PROF_BINS * idx;
+        float L = R.tf - R.tn;
+        float bw = L / (float)PROF_BINS;
+        float om = 1.0f - J->lambda;
+        float lu = J->lambda / (float)PROF_BINS;
+        float q[PROF_BINS], F[PROF_BINS + 1];
+        F[0] = 0.0f;
+        for (int b = 0; b < PROF_BINS; b++) {
+            q[b] = fmaf(om, pdf[b], lu);
+            F[b + 1] = F[b] + q[b];
+        }
+        float *ts = (float *)malloc(sizeof(float) * (size_t)J->nimp);
+        for (int j = 0; j < J->nimp; j++) {
+            float target = (((float)j + 0.5f) / (float)J->nimp) * F[PROF_BINS];
+            int b = 0;
+            for (int c = 1; c < PROF_BINS; c++)
+                if (F[c] <= target) b = c;
+            float fr = (target - F[b]) / q[b];
+            fr = fminf(fmaxf(fr, 0.0f), 1.0f);
+            ts[j] = fmaf((float)b + fr, bw, R.tn);
+        }
+        double C[3] = {0, 0, 0};
+        float mprev = R.tn;
+        for (int j = 0; j < J->nimp; j++) {
+            float mnext = j + 1 < J->nimp ? (ts[j] + ts[j + 1]) * 0.5f : R.tf;
+            float seg = mnext - mprev;
+            mprev = mnext;
+            sample s;
+            eval_sample(S, &R, (double)ts[j], (double)seg / (double)S->smin, &s);
+            for (int c = 0; c < 3; c++) C[c] += T * s.a * s.col[c];
+            T *= (1.0 - s.a);
+            ns = j + 1;
+            if (1.0 - T >= (double)S->P.term) break;
+        }
+        free(ts);
+        out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
+    }
+    for (int c = 0; c < 4; c++) J->rgba[4 * idx + c] = out[c];
+    J->aux2[idx] = T;
+    if (J->nsamp) J->nsamp[idx] = ns;
+}
+
+int orc_importance(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
+                   const orc_params *prm, const int32_t *pix, int64_t npix, const float *pdf,
+                   float lambda, int nimp, double *rgba, double *tfinal, int32_t *nsamp,
+                   int nthreads) {
+    scene S;
+    int rc = scene_init(&S, vol, tf, cam, prm);
+    if (rc) { scene_free(&S); return rc; }
+    job J;
+    memset(&J, 0, sizeof J);
+    J.S = &S;
+    J.pix = pix;
+    J.npix = pix ? npix : (int64_t)cam->width * cam->height;
+    J.fn = importance_pixel;
+    J.pdf = pdf;
+    J.lambda = lambda;
+    J.nimp = nimp;
+    J.rgba = rgba;
+    J.aux2 = tfinal;
+    J.nsamp = nsamp;
+    run_job(&J, nthreads, 0);
+    scene_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* empty-space structures                                                     */
+/* ------------------------------------------------------------------------ */
+/* Cell-brick b along an axis holds the trilinear cells whose base index lies in
+ * 16b..16b+15; its footprint is the voxels 16b..min(16b+16, n-1). There are
+ * ceil((n-1)/16) cell-bricks per axis, x fastest. Values clamp to vmax. */
+void orc_brick_minmax(const orc_volume *vol, uint16_t *mn, uint16_t *mx) {
+    int n[3] = {vol->nx, vol->ny, vol->nz};
+    int nb[3];
+    for (int a = 0; a < 3; a++) nb[a] = (n[a] - 1 + 15) / 16;
+    for (int bz = 0; bz < nb[2]; bz++)
+        for (int by = 0; by < nb[1]; by++)
+            for (int bx = 0; bx < nb[0]; bx++) {
+                int lo = 65535, hi = 0;
+                int z1 = 16 * bz + 16 < n[2] - 1 ? 16 * bz + 16 : n[2] - 1;
+                int y1 = 16 * by + 16 < n[1] - 1 ? 16 * by + 16 : n[1] - 1;
+                int x1 = 16 * bx + 16 < n[0] - 1 ? 16 * bx + 16 : n[0] - 1;
+                for (int z = 16 * bz; z <= z1; z++)
+                    for (int y = 16 * by; y <= y1; y++)
+                        for (int x = 16 * bx; x <= x1; x++) {
+                            int v = vol->data[((size_t)z * n[1] + y) * n[0] + x];
+                            if (v > vol->vmax) v = vol->vmax;
+                            if (v < lo) lo = v;
+                            if (v > hi) hi = v;
+                        }
+                size_t b = ((size_t)bz * nb[1] + by) * nb[0] + bx;
+                mn[b] = (uint16_t)lo;
+                mx[b] = (uint16_t)hi;
+            }
+}
+
+/* A brick is occupied unless every table entry a sample inside it can touch
+ * has zero opacity. For values in [mn, mx] the lerp touches entries
+ * lo = floor(u(mn)) .. hi = min(floor(u(mx)) + 1, K - 1). Raw values:
+ * u(v) = v (K-1) / vmax, floored exactly in integers. FP16-normalised values:
+ * u(v) = h(v) (K-1) with h(v) the FP16 rounding of the FP32 quotient v / vmax. */
+void orc_occupancy(const orc_volume *vol, const orc_tf *tf, const uint16_t *mn,
+                   const uint16_t *mx, uint8_t *occ) {
+    int nb = ((vol->nx - 1 + 15) / 16) * ((vol->ny - 1 + 15) / 16) * ((vol->nz - 1 + 15) / 16);
+    int K = tf->K;
+    for (int b = 0; b < nb; b++) {
+        long lo, hi;
+        if (vol->value_mode) {
+            lo = (long)floor(half_round((float)mn[b] / (float)vol->vmax) * (double)(K - 1));
+            hi = (long)floor(half_round((float)mx[b] / (float)vol->vmax) * (double)(K - 1)) + 1;
+        } else {
+            lo = ((long)mn[b] * (K - 1)) / vol->vmax;
+            hi = ((long)mx[b] * (K - 1)) / vol->vmax + 1;
+        }
+        if (hi > K - 1) hi = K - 1;
+        if (lo > K - 1) lo = K - 1;
+        int any = 0;
+        for (long i = lo; i <= hi; i++) {
+            double a = tf->fp16 ? half_round(tf->rgba[4 * i + 3]) : (double)tf->rgba[4 * i + 3];
+            if (a != 0.0) any = 1;
+        }
+        occ[b] = (uint8_t)any;
+    }
+}
