@@ -1,0 +1,356 @@
+"""Throughput of the shaded raycast of a 256x256x180 uint16 head phantom at
+1024 x 1024 over a 36-view orbit (FP32 storage, step 0.5 voxel, Blinn-Phong,
+16^3 min/max brick grid for empty-space skipping, early termination at 0.99).
+
+One step = one pass of the whole hot path over the resident phantom: re-layout
+and min/max grid from the device copy of the codes, occupancy mask for the
+transfer function, then the 36 views rendered. Metric: dense-equivalent
+Gsamples/s (samples of the plain march up to termination, skipped ones
+included) and ms/frame.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank renders its own orbit on its own GPU (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "shaded_256x256x180"
+METRIC = "Gsamples/s (dense-equivalent), 1024^2 of 256x256x180 u16, shaded, 36-view orbit"
+BYTES_PER_SAMPLE = 128          # 32 distinct FP32 voxels per shaded sample
+L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_sources_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1211_5595_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the march from the committed ncu summary, if
+    it was captured on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "march_shaded_256x256x180.md")
+    try:
+        kv = {}
+        for line in open(path):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("sources_sha256_16") != kernel_sources_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[2 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def setup_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def params(w, skip=True):
+    import paper_1211_5595_gb300 as rc
+    return rc.RenderParams(step_vox=w["step"], term=w["term"], shade=w["shade"], skip=skip)
+
+
+def cameras(ph, w):
+    return [synth.orbit_camera(ph.dims, ph.spacing, az, width=w["width"], height=w["height"])
+            for az in w["azimuths"]]
+
+
+def cpu_oracle_sample(ph, tf, w, cams, budget_s, pixels_per_view=None):
+    """Times the FP64 oracle on host cores over whole views (or seeded pixel
+    subsets) until budget_s of work is done. Returns (Gsamples/s, cores, desc)."""
+    import oracle
+    oracle.build()
+    cores = oracle.default_threads()
+    samples = 0
+    views = 0
+    t0 = time.perf_counter()
+    for i, cam in enumerate(cams):
+        sc = oracle.Scene(ph.vol, ph.spacing, tf, cam, step=w["step"], term=w["term"], shade=w["shade"])
+        pix = None
+        if pixels_per_view:
+            pix = synth.sample_pixels(w["width"], w["height"], pixels_per_view, seed=9000 + i)
+        r = oracle.render(sc, pixels=pix, nthreads=cores)
+        samples += int(r["nsamp"].sum())
+        views += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    what = f"{pixels_per_view} seeded pixels of each of" if pixels_per_view else "full 1024^2 frames of"
+    return samples / dt / 1e9, cores, f"{what} {views} view(s), {samples} samples, {dt:.1f} s"
+
+
+def run_reference(args, w, world, rank):
+    """The oracle as the reference arm (host cores, bounded sample per step)."""
+    if rank != 0:
+        return 0
+    ph = synth.workload_phantom(WORKLOAD)
+    tf = synth.tf_table(w["K"])
+    cams = cameras(ph, w)
+    import oracle
+    oracle.build()
+    cores = oracle.default_threads()
+    per_view = 256
+    times, samples = [], 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        s = 0
+        for i, cam in enumerate(cams):
+            sc = oracle.Scene(ph.vol, ph.spacing, tf, cam, step=w["step"], term=w["term"], shade=w["shade"])
+            pix = synth.sample_pixels(w["width"], w["height"], per_view, seed=9000 + i)
+            s += int(oracle.render(sc, pixels=pix, nthreads=cores)["nsamp"].sum())
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            samples += s
+    tot = sum(times)
+    val = samples / tot / 1e9
+    sample = f"{per_view} seeded pixels of each of the 36 views per step (FP64 oracle, all cores)"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded head phantom)",
+            "config": {"workload": WORKLOAD, "image": "1024x1024", "views": 36, "sample": sample},
+            "cpu_baseline": {"value": val, "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = synth.WORKLOADS[WORKLOAD]
+    world, rank, local = setup_dist()
+    if args.impl == "reference":
+        return run_reference(args, w, world, rank)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1211_5595_gb300 import build as _b
+    _b.build()
+    import paper_1211_5595_gb300 as rc
+
+    ph = synth.workload_phantom(WORKLOAD)
+    tf = synth.tf_table(w["K"])
+    cams = cameras(ph, w)
+    nviews = len(cams)
+    H, W = w["height"], w["width"]
+    stream = torch.cuda.current_stream()
+    ctx = rc.rc_context_create(local, stream.cuda_stream)
+    vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, rc.RC_STORE_F32)
+    codes_host = torch.from_numpy(ph.vol.view(np.int16).reshape(-1)).pin_memory()
+    codes_dev = codes_host.to("cuda", non_blocking=True)
+    tf_host = torch.from_numpy(tf).pin_memory()
+    tf_dev = tf_host.to("cuda")
+    rc.rc_volume_upload(ctx, vol, codes_dev)
+    rc.rc_tf_set_device(ctx, tf_dev)
+    P = params(w)
+    outs = torch.empty((nviews, H, W, 4), device="cuda", dtype=torch.float32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda", dtype=torch.float32)
+
+    # dense-equivalent and evaluated samples of one orbit (deterministic)
+    dense = evald = 0
+    for v, cam in enumerate(cams):
+        rc.rc_camera_set(ctx, cam)
+        st = rc.rc_render(ctx, vol, P, outs[v], stats=True)
+        dense += st["dense_samples"]
+        evald += st["evaluated_samples"]
+
+    def step(events=None):
+        rc.rc_volume_upload(ctx, vol, codes_dev)          # a1 re-layout + a2 min/max grid
+        rc.rc_tf_set_device(ctx, tf_dev)                   # a3 occupancy for the table
+        for v, cam in enumerate(cams):
+            rc.rc_camera_set(ctx, cam)
+            if events is not None:
+                events[v][0].record(stream)
+            rc.rc_render(ctx, vol, P, outs[v])
+            if events is not None:
+                events[v][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nviews)]
+               for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        for s in range(args.steps):
+            step_ev[s][0].record(stream)
+            step(kern_ev[s])
+            step_ev[s][1].record(stream)
+            flush.zero_()                                   # L2 flush between steps, outside the events
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    frame_ms = [a.elapsed_time(b) for row in kern_ev for a, b in row]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * dense * args.steps / (total_ms / 1e3) / 1e9
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the C-ABI with host buffers: pinned codes and table
+    # in, every view's image out, copies inside the timed region
+    img_host = torch.empty((nviews, H, W, 4), dtype=torch.float32).pin_memory()
+    codes_np = codes_host.numpy().view(np.uint16)
+
+    def e2e_step():
+        rc.rc_volume_upload(ctx, vol, codes_np)
+        rc.rc_tf_set(ctx, tf)
+        for v, cam in enumerate(cams):
+            rc.rc_camera_set(ctx, cam)
+            rc.rc_render(ctx, vol, P, outs[v])
+        img_host.copy_(outs, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    h2d = codes_host.numel() * 2 + tf.nbytes
+    d2h = img_host.numel() * 4
+
+    hbm_peak, peak_kind = peaks()
+    frame_avg_s = statistics.mean(frame_ms) / 1e3
+    achieved = evald / nviews * BYTES_PER_SAMPLE / frame_avg_s / 1e9
+    traffic = profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded head phantom, Rician noise)",
+        "config": {"workload": WORKLOAD, "volume": "256x256x180 u16 -> FP32 16^3 bricks", "image": "1024x1024",
+                   "views": nviews, "step_vox": w["step"], "shading": "Blinn-Phong headlight",
+                   "skip": "16^3 min/max brick grid", "term": w["term"],
+                   "l2": "flushed between steps (256 MB write, outside the step events)",
+                   "ms_per_frame_median": statistics.median(frame_ms),
+                   "dense_samples_per_step": dense, "evaluated_samples_per_step": evald},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "kernel": "composite_kernel<F32, shaded>",
+                     "model": f"{BYTES_PER_SAMPLE} B per evaluated sample (32 distinct FP32 voxels) / mean launch time",
+                     "peak_kind": f"{peak_kind} copy bandwidth"},
+        "e2e": {"value": world * dense * args.steps / e2e_s / 1e9, "unit": "Gsamples/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * (2 + 1 + 1 + nviews),
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, cores, desc = cpu_oracle_sample(ph, tf, w, cams, args.cpu_budget)
+        line["cpu_baseline"] = {"value": val, "unit": "Gsamples/s", "cores": cores, "kind": "oracle", "sample": desc}
+    rc.rc_volume_destroy(ctx, vol)
+    rc.rc_context_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * rc.h -- C ABI of the GB300 direct-volume-rendering raycaster.
+ *
+ * The calls follow the paper's statement of the problem (Adeshina et al.,
+ * "Hardware-Accelerated Raycasting: Towards an Effective Brain MRI
+ * Visualization"): a scalar volume on a Cartesian voxel grid (Sec. 2.1) whose
+ * slices have a thickness and gaps (Sec. 1, anisotropic spacing), colour and
+ * opacity transfer functions (Sec. 2.6, Sec. 6), camera settings (Sec. 6) and a
+ * raycast function that computes the compositing integral for every pixel
+ * (Sec. 4.1-4.2, Eq. 1-5; Sec. 6).
+ *
+ * Conventions shared by every call:
+ *  - Status codes only; no exception or longjmp crosses this boundary.
+ *    rc_last_error() gives the text of the last failure of a context.
+ *  - Arguments are validated before anything is launched or changed; a call
+ *    that fails leaves the earlier state of its objects as it was.
+ *  - Library objects (context, volume) are opaque, owned by the library and
+ *    released by their *_destroy call. Inputs are copied. Output buffers are
+ *    caller-owned DEVICE memory unless stated otherwise.
+ *  - Every device operation is asynchronous on the context's CUDA stream
+ *    (set at creation or by rc_context_set_stream). A call that returns
+ *    statistics to host memory synchronises that stream.
+ *  - One context per host thread; contexts are independent.
+ *  - Index space: voxel (i, j, k) has its centre at integer coordinates,
+ *    world position (i*sx, j*sy, k*sz) mm; the volume box is [0, N-1] per axis.
+ *    Voxel arrays are x fastest, then y, then z.
+ *  - Images are row-major H x W x 4 floats, y = 0 at the top, premultiplied
+ *    RGBA on a black background.
+ */
+#ifndef RC_H
+#define RC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RC_OK = 0,
+    RC_ERR_INVALID_ARG = 1,   /* null pointer, bad size, out-of-range value */
+    RC_ERR_OOM = 2,           /* device or host allocation failed */
+    RC_ERR_CUDA = 3,          /* a CUDA runtime call or a kernel failed */
+    RC_ERR_STATE = 4,         /* call out of order (e.g. render before upload) */
+    RC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+    RC_ERR_UNSUPPORTED = 6,   /* valid but not supported combination */
+    RC_ERR_FORMAT = 7         /* malformed serialized blob */
+} rc_status;
+
+/* How the volume is held on the device (Sec. 2.1 scalar data):
+ * F32: FP32 codes (exact copies of the uint16 codes);
+ * F16: FP16 of code / vmax (normalised to [0, 1]);
+ * U16: the raw uint16 codes. */
+typedef enum { RC_STORE_F32 = 0, RC_STORE_F16 = 1, RC_STORE_U16 = 2 } rc_storage;
+
+/* Ray functions listed in Sec. 4.1 (and Sec. 2.4 ii). The default and the
+ * subject of the paper is compositing (Sec. 4.2). Output channels of the
+ * others: MIP / AVERAGE: (m, m, m, 1), m = max / mean sample value over full
+ * scale; XRAY: (x, x, x, 1), x = sum of sample values times the step in mm over
+ * full scale; ISO: (t*, headlight-shaded intensity at the first sample at or
+ * above iso, index of that sample, 1), t* = the crossing distance in mm,
+ * linearly interpolated between the two samples around it; THRESHOLD:
+ * (transfer-function colour of the first sample at or above iso, 1). A ray
+ * that misses the box, or finds no crossing, gives 0 in all four channels. */
+typedef enum {
+    RC_FUNC_COMPOSITE = 0, RC_FUNC_MIP = 1, RC_FUNC_AVERAGE = 2,
+    RC_FUNC_XRAY = 3, RC_FUNC_ISO = 4, RC_FUNC_THRESHOLD = 5
+} rc_ray_function;
+
+typedef struct rc_context rc_context;
+typedef struct rc_volume rc_volume;
+
+/* Perspective pinhole camera (Sec. 6, camera settings). The camera basis is
+ * f = normalize(target - eye), r = normalize(f x up), u = r x f, computed in
+ * FP64 and rounded to FP32. Pixel (x, y) looks along
+ * normalize(f + ndc_x r + ndc_y u) with ndc_x = ((x + 0.5)/W * 2 - 1) tan(fovy/2) W/H
+ * and ndc_y = (1 - (y + 0.5)/H * 2) tan(fovy/2), each operation an FP32
+ * operation rounded once. */
+typedef struct {
+    float eye[3], target[3], up[3];   /* world, mm */
+    float fovy_deg;                   /* vertical field of view, (0, 180) */
+    int32_t width, height;            /* pixels, >= 1 */
+} rc_camera;
+
+typedef struct {
+    float step_vox;     /* sample spacing ds in units of the finest spacing (>= 1e-3).
+                           Opacity is per reference step ds_ref = min(spacing) and
+                           is corrected to 1 - (1 - a)^(ds/ds_ref) (Eq. 3). */
+    float term;         /* early ray termination once 1 - T >= term; (0, 1] */
+    int32_t shade;      /* 1: central-difference gradients, headlight Blinn-Phong */
+    float ka, kd, ks;   /* shading weights; specular exponent 16 */
+    int32_t func;       /* rc_ray_function */
+    float iso;          /* iso-value / threshold, in the volume's code units */
+    int32_t skip;       /* 1: skip bricks the occupancy mask marks empty (exact) */
+    int32_t reserved;   /* must be 0 */
+} rc_render_params;
+
+typedef struct {
+    uint64_t dense_samples;      /* samples up to termination, skipped ones included */
+    uint64_t evaluated_samples;  /* samples resampled and classified */
+    uint64_t rays_hit;           /* rays that intersect the volume box */
+    uint64_t rays_total;
+} rc_stats;
+
+/* Text of a status code (static storage). */
+const char *rc_status_string(rc_status s);
+
+/* Text of the last failure on ctx (valid until the next call on ctx); for a
+ * NULL ctx, the last failure of a call that had no context (thread-local). */
+const char *rc_last_error(const rc_context *ctx);
+
+/* Creates a context on CUDA device `device`, launching on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). */
+rc_status rc_context_create(int device, void *cuda_stream, rc_context **out);
+rc_status rc_context_set_stream(rc_context *ctx, void *cuda_stream);
+/* Synchronises the context's stream and frees everything the context owns.
+ * Volumes must be destroyed first (RC_ERR_STATE otherwise). */
+rc_status rc_context_destroy(rc_context *ctx);
+
+/* Volume of nx x ny x nz voxels (each >= 2) with spacing sx, sy, sz mm (> 0) and
+ * valid codes 0..vmax (>= 1; larger codes clamp to vmax) (Sec. 2.1, Sec. 1).
+ * The device holds it in 16^3 bricks in the chosen storage, with a min/max
+ * grid over cell-bricks (the trilinear cells whose base index lies in
+ * 16b..16b+15 per axis, footprint voxels 16b..min(16b+16, N-1)). */
+rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz,
+                           float sx, float sy, float sz, uint16_t vmax,
+                           rc_storage storage, rc_volume **out);
+/* Copies n_voxels (== nx*ny*nz) uint16 codes, x fastest, from host memory
+ * (src_is_device = 0; pinned memory makes the copy asynchronous) or device
+ * memory (1), re-lays them out in bricks and rebuilds the min/max grid. */
+rc_status rc_volume_upload(rc_volume *vol, const uint16_t *src, size_t n_voxels,
+                           int src_is_device);
+rc_status rc_volume_destroy(rc_volume *vol);
+
+/* Number of cell-bricks per axis, ceil((N-1)/16). */
+rc_status rc_volume_brick_dims(const rc_volume *vol, int dims[3]);
+
+/* Transfer function (Sec. 2.6, Sec. 6): n_entries (2..4096) straight RGBA
+ * entries in [0, 1], host memory, entry i at code i*vmax/(n_entries-1); a value
+ * between entries is the linear interpolation of its two neighbours. fp16 = 1
+ * stores the table as FP16 (the precision form). */
+rc_status rc_tf_set(rc_context *ctx, const float *rgba, int n_entries, int fp16);
+/* Same from device memory (asynchronous device-to-device copy). Values are not
+ * range-checked on this path. */
+rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries, int fp16);
+
+rc_status rc_camera_set(rc_context *ctx, const rc_camera *cam);
+
+/* Renders the current camera view of vol with the current transfer function
+ * (Sec. 4.1-4.2): per pixel one ray, evenly spaced trilinear samples,
+ * classification, optional shading, front-to-back compositing with early
+ * termination. out_rgba: device, width*height*4 floats, caller-owned,
+ * overwritten. stats: optional host pointer; when given the call synchronises
+ * the stream and fills it. */
+rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                    float *out_rgba, rc_stats *stats);
+
+/* Gradient of a loss with respect to the transfer function entries, given the
+ * gradient of the loss with respect to the composited image (Eq. 4-5 are
+ * differentiable in the table). dL_dimage: device, width*height*4 floats;
+ * dL_dtf: device, n_entries*4 floats, overwritten. Compositing function only;
+ * empty-space skipping is not used (an empty brick still has a gradient). The
+ * forward march is recomputed per ray; nothing is stored per sample. The
+ * result does not depend on thread scheduling (fixed-point accumulation). */
+rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol,
+                             const rc_render_params *params, const float *dL_dimage,
+                             float *dL_dtf);
+
+/* Copies the cell-brick min/max grid (uint16, brick_dims order x fastest) into
+ * caller device buffers mn, mx. */
+rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *vol, uint16_t *mn, uint16_t *mx);
+
+/* Writes the occupancy mask of vol under the current transfer function into
+ * caller device memory (one byte per cell-brick, 1 = may hold non-zero
+ * opacity). A brick is empty when every table entry a sample inside it can
+ * touch, floor(u(min)) .. min(floor(u(max)) + 1, K - 1), has opacity 0, with
+ * u(v) = v (K-1) / vmax (raw codes) or fp16(v / vmax) (K-1) (F16 storage). */
+rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RC_H */

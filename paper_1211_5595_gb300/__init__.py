@@ -1,0 +1,239 @@
+"""Python binding of librc.so, the GB300 direct-volume-rendering raycaster.
+
+Argument marshalling only: every call goes straight to the same-named C entry
+point of include/rc.h, and every step of the rendering runs in the library's
+CUDA kernels. PyTorch supplies device memory (tensors) and streams. There is
+no CPU fallback: when librc.so is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librc.so")
+
+RC_OK, RC_ERR_INVALID_ARG, RC_ERR_OOM, RC_ERR_CUDA, RC_ERR_STATE, RC_ERR_TIMEOUT, \
+    RC_ERR_UNSUPPORTED, RC_ERR_FORMAT = range(8)
+RC_STORE_F32, RC_STORE_F16, RC_STORE_U16 = range(3)
+RC_FUNC_COMPOSITE, RC_FUNC_MIP, RC_FUNC_AVERAGE, RC_FUNC_XRAY, RC_FUNC_ISO, RC_FUNC_THRESHOLD = range(6)
+
+
+class RCError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+class rc_camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("target", C.c_float * 3), ("up", C.c_float * 3),
+                ("fovy_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class rc_render_params(C.Structure):
+    _fields_ = [("step_vox", C.c_float), ("term", C.c_float), ("shade", C.c_int32),
+                ("ka", C.c_float), ("kd", C.c_float), ("ks", C.c_float), ("func", C.c_int32),
+                ("iso", C.c_float), ("skip", C.c_int32), ("reserved", C.c_int32)]
+
+
+class rc_stats(C.Structure):
+    _fields_ = [("dense_samples", C.c_uint64), ("evaluated_samples", C.c_uint64),
+                ("rays_hit", C.c_uint64), ("rays_total", C.c_uint64)]
+
+
+# Every symbol include/rc.h declares, with its ctypes signature.
+_P = C.c_void_p
+_I = C.c_int
+SIGNATURES = {
+    "rc_status_string": (C.c_char_p, [_I]),
+    "rc_last_error": (C.c_char_p, [_P]),
+    "rc_context_create": (_I, [_I, _P, C.POINTER(_P)]),
+    "rc_context_set_stream": (_I, [_P, _P]),
+    "rc_context_destroy": (_I, [_P]),
+    "rc_volume_create": (_I, [_P, _I, _I, _I, C.c_float, C.c_float, C.c_float, C.c_uint16, _I,
+                              C.POINTER(_P)]),
+    "rc_volume_upload": (_I, [_P, _P, C.c_size_t, _I]),
+    "rc_volume_destroy": (_I, [_P]),
+    "rc_volume_brick_dims": (_I, [_P, C.POINTER(C.c_int * 3)]),
+    "rc_tf_set": (_I, [_P, _P, _I, _I]),
+    "rc_tf_set_device": (_I, [_P, _P, _I, _I]),
+    "rc_camera_set": (_I, [_P, C.POINTER(rc_camera)]),
+    "rc_render": (_I, [_P, _P, C.POINTER(rc_render_params), _P, C.POINTER(rc_stats)]),
+    "rc_render_backward": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
+    "rc_brick_grid_get": (_I, [_P, _P, _P, _P]),
+    "rc_skip_mask_get": (_I, [_P, _P, _P]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded librc.so; raises when the extension has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA extension missing: {LIB_PATH} (run paper_1211_5595_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None, what=""):
+    if status != RC_OK:
+        msg = lib().rc_last_error(ctx)
+        raise RCError(status, f"{what}: {msg.decode() if msg else lib().rc_status_string(status).decode()}")
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor or numpy array (or an int)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _default_stream(device):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# same-named wrappers of the C entry points
+# ---------------------------------------------------------------------------
+def rc_status_string(status: int) -> str:
+    return lib().rc_status_string(status).decode()
+
+
+def rc_last_error(ctx=None) -> str:
+    m = lib().rc_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def rc_context_create(device: int = 0, stream=None):
+    out = _P()
+    s = _default_stream(device) if stream is None else stream
+    _check(lib().rc_context_create(device, s, C.byref(out)), None, "rc_context_create")
+    return out.value
+
+
+def rc_context_set_stream(ctx, stream):
+    _check(lib().rc_context_set_stream(ctx, stream), ctx, "rc_context_set_stream")
+
+
+def rc_context_destroy(ctx):
+    _check(lib().rc_context_destroy(ctx), ctx, "rc_context_destroy")
+
+
+def rc_volume_create(ctx, dims, spacing, vmax=4095, storage=RC_STORE_F32):
+    out = _P()
+    nx, ny, nz = (int(d) for d in dims)
+    sx, sy, sz = (float(s) for s in spacing)
+    _check(lib().rc_volume_create(ctx, nx, ny, nz, sx, sy, sz, int(vmax), int(storage), C.byref(out)),
+           ctx, "rc_volume_create")
+    return out.value
+
+
+def rc_volume_upload(ctx, vol, src):
+    """src: numpy uint16 array (host) or a CUDA tensor of 2-byte codes."""
+    dev = hasattr(src, "is_cuda") and src.is_cuda
+    if not dev:
+        src = np.ascontiguousarray(src, dtype=np.uint16)
+    n = src.numel() if dev else src.size
+    _check(lib().rc_volume_upload(vol, _ptr(src), n, 1 if dev else 0), ctx, "rc_volume_upload")
+
+
+def rc_volume_destroy(ctx, vol):
+    _check(lib().rc_volume_destroy(vol), ctx, "rc_volume_destroy")
+
+
+def rc_volume_brick_dims(vol):
+    d = (C.c_int * 3)()
+    _check(lib().rc_volume_brick_dims(vol, C.byref(d)), None, "rc_volume_brick_dims")
+    return tuple(d)
+
+
+def rc_tf_set(ctx, rgba, fp16=False):
+    t = np.ascontiguousarray(rgba, dtype=np.float32)
+    _check(lib().rc_tf_set(ctx, t.ctypes.data, t.shape[0], int(bool(fp16))), ctx, "rc_tf_set")
+
+
+def rc_tf_set_device(ctx, rgba, fp16=False):
+    _check(lib().rc_tf_set_device(ctx, _ptr(rgba), rgba.shape[0], int(bool(fp16))), ctx, "rc_tf_set_device")
+
+
+def make_camera(cam) -> rc_camera:
+    return rc_camera((C.c_float * 3)(*cam["eye"]), (C.c_float * 3)(*cam["target"]),
+                     (C.c_float * 3)(*cam["up"]), float(cam["fovy_deg"]), int(cam["width"]),
+                     int(cam["height"]))
+
+
+def rc_camera_set(ctx, cam):
+    c = cam if isinstance(cam, rc_camera) else make_camera(cam)
+    _check(lib().rc_camera_set(ctx, C.byref(c)), ctx, "rc_camera_set")
+
+
+@dataclass
+class RenderParams:
+    step_vox: float = 0.5
+    term: float = 0.99
+    shade: bool = False
+    ka: float = 0.1
+    kd: float = 0.7
+    ks: float = 0.2
+    func: int = RC_FUNC_COMPOSITE
+    iso: float = 0.0
+    skip: bool = True
+
+    def c(self) -> rc_render_params:
+        return rc_render_params(self.step_vox, self.term, int(bool(self.shade)), self.ka, self.kd,
+                                self.ks, int(self.func), self.iso, int(bool(self.skip)), 0)
+
+
+def _params(p):
+    if isinstance(p, rc_render_params):
+        return p
+    if isinstance(p, RenderParams):
+        return p.c()
+    return RenderParams(**p).c()
+
+
+def rc_render(ctx, vol, params, out, stats=False):
+    """Renders into out (CUDA float32 tensor H x W x 4). With stats=True the
+    call synchronises and returns the sample counters."""
+    p = _params(params)
+    st = rc_stats() if stats else None
+    _check(lib().rc_render(ctx, vol, C.byref(p), _ptr(out), C.byref(st) if st is not None else None),
+           ctx, "rc_render")
+    if st is None:
+        return None
+    return dict(dense_samples=st.dense_samples, evaluated_samples=st.evaluated_samples,
+                rays_hit=st.rays_hit, rays_total=st.rays_total)
+
+
+def rc_render_backward(ctx, vol, params, dimage, dtf):
+    p = _params(params)
+    _check(lib().rc_render_backward(ctx, vol, C.byref(p), _ptr(dimage), _ptr(dtf)), ctx,
+           "rc_render_backward")
+
+
+def rc_brick_grid_get(ctx, vol, mn, mx):
+    _check(lib().rc_brick_grid_get(ctx, vol, _ptr(mn), _ptr(mx)), ctx, "rc_brick_grid_get")
+
+
+def rc_skip_mask_get(ctx, vol, occ):
+    _check(lib().rc_skip_mask_get(ctx, vol, _ptr(occ)), ctx, "rc_skip_mask_get")

@@ -1,0 +1,195 @@
+// Adjoint of the compositing ray function with respect to the transfer-function
+// table (Eq. 4-5 are differentiable in the table entries).
+//
+// Per ray, pass 1 recomputes the forward march (no empty-space skipping) to get
+// C_final, T_final and the number n of samples up to termination. Pass 2
+// marches again front to back, rebuilding T_k and the prefix C_{<=k}, so that
+// the suffix S_k = C_final - C_{<=k} is known without storing samples or
+// dividing transmittance backwards:
+//   dI_c/da'_k = T_k col_kc - S_kc / (1 - a'_k),  dI_a/da'_k = T_k - (T_{k+1} - T_n) / (1 - a'_k)
+//   dI_c/dcol_kc = T_k a'_k,  da'/da = r (1 - min(a, 1 - 1e-6))^(r - 1)
+// and the two table entries of the sample's lerp receive weights (1 - w, w).
+// Contributions are summed as 64-bit fixed point (scale 2^32 / max|dL/dI|) in
+// shared memory, then in global memory: integer sums do not depend on the order
+// of the atomics, so the result is deterministic.
+#include "rc_device.cuh"
+
+namespace rc {
+
+__global__ void absmax_kernel(const float *__restrict__ x, long long n, unsigned *out) {
+    float m = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    unsigned u = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, u);
+}
+
+cudaError_t launch_absmax(const float *x, long long n, float *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    absmax_kernel<<<1216, 256, 0, s>>>(x, n, (unsigned *)out);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ float fixed_scale(const float *absmax) {
+    return 4294967296.0f / fmaxf(*absmax, 1e-30f);
+}
+
+__device__ __forceinline__ void acc_add(unsigned long long *acc, int idx, float v, float scale) {
+    long long q = __float2ll_rn(v * scale);
+    if (q != 0) atomicAdd(acc + idx, (unsigned long long)q);
+}
+
+template <int ST, bool SHADE>
+__global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const float *absmax) {
+    const MarchArgs &a = A.m;
+    const int K = a.tf.K;
+    extern __shared__ float4 smem[];
+    float4 *s_tf = smem;
+    unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(smem + K);
+    load_tf(a.tf, s_tf);
+    for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) s_acc[e] = 0ull;
+    __syncthreads();
+    const float scale = fixed_scale(absmax);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    const bool inimg = x < a.cam.W && y < a.cam.H;
+    Ray R;
+    bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
+    float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (hit) g = A.dimg[(size_t)y * a.cam.W + x];
+    if (hit && (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f)) {
+        const float km1 = (float)(K - 1);
+        // pass 1: forward
+        float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
+        int n = 0;
+        for (int k = 0; k < R.nsamp; k++) {
+            float p[3], gr[3], val;
+            position_at(R, sample_t(R, k), p);
+            Cell c;
+            cell_of(a.vol, p, c);
+            if (SHADE) val = value_grad<ST>(a.vol, c, gr);
+            else val = trilinear<ST>(a.vol, c);
+            float4 e = classify(s_tf, K, tf_coord(a.vol, val, km1));
+            float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
+            float r = e.x, gg = e.y, b = e.z;
+            if (SHADE) {
+                float sf, spec;
+                shade_factor(a.p, a.vol, gr, R.dir, sf, spec);
+                r = fminf(1.0f, __fmaf_rn(r, sf, spec));
+                gg = fminf(1.0f, __fmaf_rn(gg, sf, spec));
+                b = fminf(1.0f, __fmaf_rn(b, sf, spec));
+            }
+            float ta = T * ap;
+            C0 = __fmaf_rn(ta, r, C0);
+            C1 = __fmaf_rn(ta, gg, C1);
+            C2 = __fmaf_rn(ta, b, C2);
+            T = T * (1.0f - ap);
+            n = k + 1;
+            if ((1.0f - T) >= a.p.term) break;
+        }
+        const float Cf0 = C0, Cf1 = C1, Cf2 = C2, Tf = T;
+        // pass 2: prefix sums again, gradient per sample
+        C0 = C1 = C2 = 0.0f;
+        T = 1.0f;
+        for (int k = 0; k < n; k++) {
+            float p[3], gr[3], val;
+            position_at(R, sample_t(R, k), p);
+            Cell c;
+            cell_of(a.vol, p, c);
+            if (SHADE) val = value_grad<ST>(a.vol, c, gr);
+            else val = trilinear<ST>(a.vol, c);
+            int i;
+            float w;
+            float4 e = classify(s_tf, K, tf_coord(a.vol, val, km1), &i, &w);
+            float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
+            float r = e.x, gg = e.y, b = e.z;
+            float d0 = 1.0f, d1 = 1.0f, d2 = 1.0f;
+            if (SHADE) {
+                float sf, spec;
+                shade_factor(a.p, a.vol, gr, R.dir, sf, spec);
+                float u0 = __fmaf_rn(r, sf, spec), u1 = __fmaf_rn(gg, sf, spec), u2 = __fmaf_rn(b, sf, spec);
+                d0 = u0 < 1.0f ? sf : 0.0f;
+                d1 = u1 < 1.0f ? sf : 0.0f;
+                d2 = u2 < 1.0f ? sf : 0.0f;
+                r = fminf(1.0f, u0);
+                gg = fminf(1.0f, u1);
+                b = fminf(1.0f, u2);
+            }
+            const float Tk = T;
+            float ta = T * ap;
+            C0 = __fmaf_rn(ta, r, C0);
+            C1 = __fmaf_rn(ta, gg, C1);
+            C2 = __fmaf_rn(ta, b, C2);
+            T = T * (1.0f - ap);
+            const float om = 1.0f - ap;
+            const float inv = om > 0.0f ? 1.0f / om : 0.0f;
+            float dap = g.x * (Tk * r - (Cf0 - C0) * inv) + g.y * (Tk * gg - (Cf1 - C1) * inv) +
+                        g.z * (Tk * b - (Cf2 - C2) * inv) + g.w * (Tk - (T - Tf) * inv);
+            float ac = fminf(e.w, 1.0f - 1e-6f);
+            float dal;
+            if (a.p.rmode == 0) dal = dap;
+            else dal = dap * a.p.ratio * powf(1.0f - ac, a.p.ratio - 1.0f);
+            float dr = g.x * ta * d0, dg = g.y * ta * d1, db = g.z * ta * d2;
+            const float w0 = 1.0f - w;
+            acc_add(s_acc, 4 * i + 0, w0 * dr, scale);
+            acc_add(s_acc, 4 * i + 1, w0 * dg, scale);
+            acc_add(s_acc, 4 * i + 2, w0 * db, scale);
+            acc_add(s_acc, 4 * i + 3, w0 * dal, scale);
+            acc_add(s_acc, 4 * i + 4, w * dr, scale);
+            acc_add(s_acc, 4 * i + 5, w * dg, scale);
+            acc_add(s_acc, 4 * i + 6, w * db, scale);
+            acc_add(s_acc, 4 * i + 7, w * dal, scale);
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) {
+        unsigned long long v = s_acc[e];
+        if (v != 0ull) atomicAdd(reinterpret_cast<unsigned long long *>(A.acc) + e, v);
+    }
+}
+
+__global__ void finalize_kernel(const long long *acc, int n, const float *absmax, float *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double scale = (double)fixed_scale(absmax);
+    out[i] = (float)((double)acc[i] / scale);
+}
+
+template <typename Kern>
+static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, const float *absmax, cudaStream_t s) {
+    size_t smem = (size_t)a.m.tf.K * (sizeof(float4) + 4 * sizeof(long long));
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((a.m.cam.W + 15) / 16, (a.m.cam.H + 7) / 8);
+    kern<<<grid, 128, smem, s>>>(a, absmax);
+    return cudaGetLastError();
+}
+
+// acc must hold 4K long longs followed by one float (the |dL/dI| maximum).
+cudaError_t launch_adjoint(const AdjointArgs &a, float *dL_dtf, cudaStream_t s) {
+    const int K = a.m.tf.K;
+    float *absmax = reinterpret_cast<float *>(a.acc + 4 * K);
+    cudaError_t e = launch_absmax(reinterpret_cast<const float *>(a.dimg), (long long)a.m.cam.W * a.m.cam.H * 4,
+                                  absmax, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * K, s);
+    if (e != cudaSuccess) return e;
+    switch (a.m.vol.storage * 2 + (a.m.p.shade ? 1 : 0)) {
+        case RC_STORE_F32 * 2: e = launch_adj(adjoint_kernel<RC_STORE_F32, false>, a, absmax, s); break;
+        case RC_STORE_F32 * 2 + 1: e = launch_adj(adjoint_kernel<RC_STORE_F32, true>, a, absmax, s); break;
+        case RC_STORE_F16 * 2: e = launch_adj(adjoint_kernel<RC_STORE_F16, false>, a, absmax, s); break;
+        case RC_STORE_F16 * 2 + 1: e = launch_adj(adjoint_kernel<RC_STORE_F16, true>, a, absmax, s); break;
+        case RC_STORE_U16 * 2: e = launch_adj(adjoint_kernel<RC_STORE_U16, false>, a, absmax, s); break;
+        default: e = launch_adj(adjoint_kernel<RC_STORE_U16, true>, a, absmax, s);
+    }
+    if (e != cudaSuccess) return e;
+    finalize_kernel<<<(4 * K + 255) / 256, 256, 0, s>>>(a.acc, 4 * K, absmax, dL_dtf);
+    return cudaGetLastError();
+}
+
+}  // namespace rc

@@ -1,0 +1,529 @@
+// Host side of the C ABI declared in include/rc.h: validation, object
+// lifetimes, camera records, lazy occupancy rebuilds and kernel dispatch.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "rc_internal.h"
+
+using namespace rc;
+
+struct rc_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    char err[512] = {0};
+    // transfer function
+    float4 *d_tf32 = nullptr;
+    uint2 *d_tf16 = nullptr;
+    int tf_cap = 0;
+    int K = 0;
+    int tf_fp16 = 0;
+    uint64_t tf_version = 0;
+    // camera
+    bool cam_set = false;
+    rc_camera cam{};
+    // statistics counters
+    unsigned long long *d_stats = nullptr;
+    unsigned long long *h_stats = nullptr;   // pinned
+    // scratch of the adjoint: 4K fixed-point accumulators + |dL/dI| maximum
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int nvolumes = 0;
+};
+
+struct rc_volume {
+    rc_context *ctx = nullptr;
+    int n[3] = {0, 0, 0};
+    float s[3] = {0, 0, 0};
+    int vmax = 0;
+    rc_storage storage = RC_STORE_F32;
+    int nbv[3] = {0, 0, 0};      // storage bricks per axis
+    int cb[3] = {0, 0, 0};       // cell-bricks per axis
+    int nbricks = 0;             // cell-bricks
+    void *d_data = nullptr;
+    uint16_t *d_stage = nullptr;
+    uint16_t *d_mn = nullptr, *d_mx = nullptr;
+    uint8_t *d_occ = nullptr;
+    bool uploaded = false;
+    uint64_t data_version = 0;
+    uint64_t occ_tf_version = ~0ull;
+    uint64_t occ_data_version = ~0ull;
+};
+
+static thread_local char g_err[512];
+
+static rc_status fail(rc_context *ctx, rc_status s, const char *fmt, ...) {
+    char *buf = ctx ? ctx->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define RC_CUDA(ctx, call)                                                                      \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? RC_ERR_OOM : RC_ERR_CUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                         \
+    } while (0)
+
+// Makes ctx's device current for the scope of one call.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+extern "C" {
+
+const char *rc_status_string(rc_status s) {
+    switch (s) {
+        case RC_OK: return "ok";
+        case RC_ERR_INVALID_ARG: return "invalid argument";
+        case RC_ERR_OOM: return "out of memory";
+        case RC_ERR_CUDA: return "CUDA error";
+        case RC_ERR_STATE: return "invalid state";
+        case RC_ERR_TIMEOUT: return "device wait timed out";
+        case RC_ERR_UNSUPPORTED: return "unsupported";
+        case RC_ERR_FORMAT: return "malformed data";
+    }
+    return "unknown status";
+}
+
+const char *rc_last_error(const rc_context *ctx) { return ctx ? ctx->err : g_err; }
+
+rc_status rc_context_create(int device, void *cuda_stream, rc_context **out) {
+    if (!out) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_context_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, RC_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= ndev)
+        return fail(nullptr, RC_ERR_INVALID_ARG, "rc_context_create: device %d of %d", device, ndev);
+    DeviceScope ds(device);
+    if (!ds.ok) return fail(nullptr, RC_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+    rc_context *ctx = new (std::nothrow) rc_context();
+    if (!ctx) return fail(nullptr, RC_ERR_OOM, "rc_context_create: host allocation");
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (cudaMalloc(&ctx->d_stats, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_stats, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(ctx->d_stats);
+        delete ctx;
+        return fail(nullptr, RC_ERR_OOM, "rc_context_create: statistics buffers");
+    }
+    *out = ctx;
+    return RC_OK;
+}
+
+rc_status rc_context_set_stream(rc_context *ctx, void *cuda_stream) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_context_set_stream: ctx is NULL");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return RC_OK;
+}
+
+rc_status rc_context_destroy(rc_context *ctx) {
+    if (!ctx) return RC_OK;
+    if (ctx->nvolumes > 0) return fail(ctx, RC_ERR_STATE, "rc_context_destroy: %d volumes still alive", ctx->nvolumes);
+    DeviceScope ds(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_tf32);
+    cudaFree(ctx->d_tf16);
+    cudaFree(ctx->d_stats);
+    cudaFreeHost(ctx->h_stats);
+    cudaFree(ctx->d_scratch);
+    delete ctx;
+    return RC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// volumes
+// ---------------------------------------------------------------------------
+static void volume_free(rc_volume *v) {
+    cudaFree(v->d_data);
+    cudaFree(v->d_stage);
+    cudaFree(v->d_mn);
+    cudaFree(v->d_mx);
+    cudaFree(v->d_occ);
+}
+
+rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, float sy, float sz, uint16_t vmax,
+                           rc_storage storage, rc_volume **out) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_volume_create: ctx is NULL");
+    if (!out) return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_create: out is NULL");
+    *out = nullptr;
+    if (nx < 2 || ny < 2 || nz < 2)
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_create: dims %d x %d x %d (each must be >= 2)", nx, ny, nz);
+    if (!(sx > 0.0f && sy > 0.0f && sz > 0.0f) || !isfinite(sx) || !isfinite(sy) || !isfinite(sz))
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_create: spacing must be finite and > 0");
+    if (vmax < 1) return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_create: vmax must be >= 1");
+    if (storage != RC_STORE_F32 && storage != RC_STORE_F16 && storage != RC_STORE_U16)
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_create: storage %d", (int)storage);
+    int nbv[3] = {(nx + 15) / 16, (ny + 15) / 16, (nz + 15) / 16};
+    long long padded = (long long)nbv[0] * nbv[1] * nbv[2] * kBrickVox;
+    if (padded >= (1ll << 31))
+        return fail(ctx, RC_ERR_UNSUPPORTED, "rc_volume_create: %lld padded voxels (limit 2^31)", padded);
+    DeviceScope ds(ctx->device);
+    rc_volume *v = new (std::nothrow) rc_volume();
+    if (!v) return fail(ctx, RC_ERR_OOM, "rc_volume_create: host allocation");
+    v->ctx = ctx;
+    v->n[0] = nx; v->n[1] = ny; v->n[2] = nz;
+    v->s[0] = sx; v->s[1] = sy; v->s[2] = sz;
+    v->vmax = vmax;
+    v->storage = storage;
+    for (int a = 0; a < 3; a++) {
+        v->nbv[a] = nbv[a];
+        v->cb[a] = (v->n[a] - 1 + 15) / 16;
+    }
+    v->nbricks = v->cb[0] * v->cb[1] * v->cb[2];
+    size_t esz = storage == RC_STORE_F32 ? 4 : 2;
+    size_t nvox = (size_t)nx * ny * nz;
+    if (cudaMalloc(&v->d_data, (size_t)padded * esz) != cudaSuccess ||
+        cudaMalloc(&v->d_stage, nvox * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&v->d_mn, v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&v->d_mx, v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&v->d_occ, v->nbricks) != cudaSuccess) {
+        cudaGetLastError();
+        volume_free(v);
+        delete v;
+        return fail(ctx, RC_ERR_OOM, "rc_volume_create: device allocation (%lld voxels)", padded);
+    }
+    ctx->nvolumes++;
+    *out = v;
+    return RC_OK;
+}
+
+static VolDev vol_dev(const rc_volume *v) {
+    VolDev d;
+    d.data = v->d_data;
+    d.storage = (int)v->storage;
+    float smin = fminf(fminf(v->s[0], v->s[1]), v->s[2]);
+    for (int a = 0; a < 3; a++) {
+        d.n[a] = v->n[a];
+        d.cb[a] = v->cb[a];
+        d.s[a] = v->s[a];
+        d.inv2s[a] = 0.5f / v->s[a];
+    }
+    d.sy = (unsigned)v->nbv[0] * kBrickVox;
+    d.sz = (unsigned)v->nbv[0] * v->nbv[1] * kBrickVox;
+    d.smin = smin;
+    d.vmax = v->vmax;
+    d.vscale = v->storage == RC_STORE_F16 ? 1.0f : (float)v->vmax;
+    d.gmin = 1e-6f * d.vscale;
+    return d;
+}
+
+rc_status rc_volume_upload(rc_volume *v, const uint16_t *src, size_t n_voxels, int src_is_device) {
+    if (!v) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_volume_upload: vol is NULL");
+    rc_context *ctx = v->ctx;
+    if (!src) return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_upload: src is NULL");
+    size_t nvox = (size_t)v->n[0] * v->n[1] * v->n[2];
+    if (n_voxels != nvox)
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_upload: %zu voxels given, volume has %zu", n_voxels, nvox);
+    DeviceScope ds(ctx->device);
+    RC_CUDA(ctx, cudaMemcpyAsync(v->d_stage, src, nvox * sizeof(uint16_t),
+                                 src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    VolDev d = vol_dev(v);
+    RC_CUDA(ctx, launch_relayout(v->d_stage, d, v->d_data, v->nbv[0], v->nbv[1], v->nbv[2], ctx->stream));
+    RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, v->d_mn, v->d_mx, ctx->stream));
+    v->uploaded = true;
+    v->data_version++;
+    return RC_OK;
+}
+
+rc_status rc_volume_destroy(rc_volume *v) {
+    if (!v) return RC_OK;
+    rc_context *ctx = v->ctx;
+    DeviceScope ds(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    volume_free(v);
+    ctx->nvolumes--;
+    delete v;
+    return RC_OK;
+}
+
+rc_status rc_volume_brick_dims(const rc_volume *v, int dims[3]) {
+    if (!v || !dims) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_volume_brick_dims: NULL argument");
+    for (int a = 0; a < 3; a++) dims[a] = v->cb[a];
+    return RC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// transfer function and camera
+// ---------------------------------------------------------------------------
+static rc_status tf_reserve(rc_context *ctx, int K) {
+    if (K <= ctx->tf_cap) return RC_OK;
+    float4 *a = nullptr;
+    uint2 *b = nullptr;
+    if (cudaMalloc(&a, (size_t)K * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&b, (size_t)K * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(a);
+        return fail(ctx, RC_ERR_OOM, "rc_tf_set: device allocation");
+    }
+    // the old tables may still be read by queued kernels
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_tf32);
+    cudaFree(ctx->d_tf16);
+    ctx->d_tf32 = a;
+    ctx->d_tf16 = b;
+    ctx->tf_cap = K;
+    return RC_OK;
+}
+
+__global__ void tf_to_half_kernel(const float4 *src, uint2 *dst, int K) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    float4 v = src[i];
+    __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
+    uint2 o;
+    o.x = *reinterpret_cast<unsigned *>(&lo);
+    o.y = *reinterpret_cast<unsigned *>(&hi);
+    dst[i] = o;
+}
+
+static rc_status tf_common(rc_context *ctx, const float *rgba, int K, int fp16, bool dev) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_tf_set: ctx is NULL");
+    if (!rgba) return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf_set: rgba is NULL");
+    if (K < 2 || K > 4096) return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf_set: %d entries (2..4096)", K);
+    if (!dev) {
+        for (int i = 0; i < 4 * K; i++)
+            if (!(rgba[i] >= 0.0f && rgba[i] <= 1.0f))
+                return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf_set: entry %d channel %d = %g outside [0, 1]", i / 4,
+                            i % 4, (double)rgba[i]);
+    }
+    DeviceScope ds(ctx->device);
+    rc_status st = tf_reserve(ctx, K);
+    if (st != RC_OK) return st;
+    RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_tf32, rgba, (size_t)K * sizeof(float4),
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    tf_to_half_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_tf32, ctx->d_tf16, K);
+    RC_CUDA(ctx, cudaGetLastError());
+    if (!dev) RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host source may be reused at once
+    ctx->K = K;
+    ctx->tf_fp16 = fp16 ? 1 : 0;
+    ctx->tf_version++;
+    return RC_OK;
+}
+
+rc_status rc_tf_set(rc_context *ctx, const float *rgba, int n_entries, int fp16) {
+    return tf_common(ctx, rgba, n_entries, fp16, false);
+}
+
+rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries, int fp16) {
+    return tf_common(ctx, rgba_dev, n_entries, fp16, true);
+}
+
+rc_status rc_camera_set(rc_context *ctx, const rc_camera *cam) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_camera_set: ctx is NULL");
+    if (!cam) return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: cam is NULL");
+    if (cam->width < 1 || cam->height < 1 || (long long)cam->width * cam->height > (1ll << 28))
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: image %d x %d", cam->width, cam->height);
+    if (!(cam->fovy_deg > 0.0f && cam->fovy_deg < 180.0f))
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: fovy %g", (double)cam->fovy_deg);
+    double f[3], up[3], c[3];
+    for (int a = 0; a < 3; a++) {
+        if (!isfinite(cam->eye[a]) || !isfinite(cam->target[a]) || !isfinite(cam->up[a]))
+            return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: non-finite vector");
+        f[a] = (double)cam->target[a] - (double)cam->eye[a];
+        up[a] = cam->up[a];
+    }
+    c[0] = f[1] * up[2] - f[2] * up[1];
+    c[1] = f[2] * up[0] - f[0] * up[2];
+    c[2] = f[0] * up[1] - f[1] * up[0];
+    if (f[0] * f[0] + f[1] * f[1] + f[2] * f[2] == 0.0 || c[0] * c[0] + c[1] * c[1] + c[2] * c[2] == 0.0)
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: eye == target or up parallel to the view");
+    ctx->cam = *cam;
+    ctx->cam_set = true;
+    return RC_OK;
+}
+
+// Camera record: look-at basis in FP64 (f = normalize(target - eye),
+// r = normalize(f x up), u = r x f), rounded once to FP32; eye in index space.
+static CamRec camera_record(const rc_camera &cam, const float s[3]) {
+    double f[3], up[3], r[3], u[3];
+    for (int a = 0; a < 3; a++) {
+        f[a] = (double)cam.target[a] - (double)cam.eye[a];
+        up[a] = (double)cam.up[a];
+    }
+    double n = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int a = 0; a < 3; a++) f[a] /= n;
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    n = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int a = 0; a < 3; a++) r[a] /= n;
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    double th = tan((double)cam.fovy_deg * 3.14159265358979323846 / 360.0);
+    double tx = th * (double)cam.width / (double)cam.height;
+    CamRec c;
+    for (int a = 0; a < 3; a++) {
+        c.f[a] = (float)f[a];
+        c.r[a] = (float)r[a];
+        c.u[a] = (float)u[a];
+        c.o[a] = (float)((double)cam.eye[a] / (double)s[a]);
+    }
+    c.tx = (float)tx;
+    c.ty = (float)th;
+    c.W = cam.width;
+    c.H = cam.height;
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// rendering
+// ---------------------------------------------------------------------------
+static rc_status check_render(rc_context *ctx, const rc_volume *v, const rc_render_params *p, const void *out,
+                              const char *who) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
+    if (!v || !p || !out) return fail(ctx, RC_ERR_INVALID_ARG, "%s: NULL argument", who);
+    if (v->ctx != ctx) return fail(ctx, RC_ERR_INVALID_ARG, "%s: volume belongs to another context", who);
+    if (!(p->step_vox >= 1e-3f) || !isfinite(p->step_vox))
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: step_vox %g", who, (double)p->step_vox);
+    if (!(p->term > 0.0f && p->term <= 1.0f)) return fail(ctx, RC_ERR_INVALID_ARG, "%s: term %g", who, (double)p->term);
+    if (p->shade != 0 && p->shade != 1) return fail(ctx, RC_ERR_INVALID_ARG, "%s: shade %d", who, p->shade);
+    if (p->skip != 0 && p->skip != 1) return fail(ctx, RC_ERR_INVALID_ARG, "%s: skip %d", who, p->skip);
+    if (p->func < RC_FUNC_COMPOSITE || p->func > RC_FUNC_THRESHOLD)
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: func %d", who, p->func);
+    if (p->reserved != 0) return fail(ctx, RC_ERR_INVALID_ARG, "%s: reserved must be 0", who);
+    if (!isfinite(p->ka) || !isfinite(p->kd) || !isfinite(p->ks) || p->ka < 0 || p->kd < 0 || p->ks < 0 ||
+        !isfinite(p->iso))
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: shading weights / iso", who);
+    if (!v->uploaded) return fail(ctx, RC_ERR_STATE, "%s: volume has no data (call rc_volume_upload)", who);
+    if (ctx->K < 2) return fail(ctx, RC_ERR_STATE, "%s: no transfer function (call rc_tf_set)", who);
+    if (!ctx->cam_set) return fail(ctx, RC_ERR_STATE, "%s: no camera (call rc_camera_set)", who);
+    if (v->storage != RC_STORE_F16 && (long long)(ctx->K - 1) * v->vmax >= (1ll << 24))
+        return fail(ctx, RC_ERR_UNSUPPORTED, "%s: (entries - 1) * vmax must stay below 2^24", who);
+    return RC_OK;
+}
+
+static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v) {
+    if (v->occ_tf_version == ctx->tf_version && v->occ_data_version == v->data_version) return RC_OK;
+    TFDev tf{ctx->d_tf32, ctx->d_tf16, ctx->K, ctx->tf_fp16};
+    RC_CUDA(ctx, launch_occupancy(v->d_mn, v->d_mx, v->nbricks, v->vmax, v->storage == RC_STORE_F16, tf,
+                                  v->d_occ, ctx->stream));
+    v->occ_tf_version = ctx->tf_version;
+    v->occ_data_version = v->data_version;
+    return RC_OK;
+}
+
+static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render_params *p, float *out) {
+    MarchArgs a;
+    a.vol = vol_dev(v);
+    a.cam = camera_record(ctx->cam, v->s);
+    a.tf = TFDev{ctx->d_tf32, ctx->d_tf16, ctx->K, ctx->tf_fp16};
+    a.p.step_vox = p->step_vox;
+    a.p.term = p->term;
+    a.p.shade = p->shade;
+    a.p.ka = p->ka;
+    a.p.kd = p->kd;
+    a.p.ks = p->ks;
+    a.p.func = p->func;
+    a.p.iso = p->func == RC_FUNC_ISO || p->func == RC_FUNC_THRESHOLD
+                  ? (v->storage == RC_STORE_F16 ? p->iso / (float)v->vmax : p->iso)
+                  : p->iso;
+    a.p.skip = p->skip;
+    // ds / ds_ref, with ds = step * smin rounded in FP32 as on the device
+    float ds = p->step_vox * a.vol.smin;
+    a.p.ratio = ds / a.vol.smin;
+    a.p.rmode = a.p.ratio == 1.0f ? 0 : a.p.ratio == 0.5f ? 1 : a.p.ratio == 0.25f ? 2 : 3;
+    a.occ = v->d_occ;
+    a.out = reinterpret_cast<float4 *>(out);
+    a.stats = nullptr;
+    return a;
+}
+
+rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, float *out_rgba,
+                    rc_stats *stats) {
+    rc_status st = check_render(ctx, vol, p, out_rgba, "rc_render");
+    if (st != RC_OK) return st;
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    if (p->skip && p->func == RC_FUNC_COMPOSITE) {
+        st = ensure_occupancy(ctx, v);
+        if (st != RC_OK) return st;
+    }
+    MarchArgs a = march_args(ctx, v, p, out_rgba);
+    if (stats) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        a.stats = ctx->d_stats;
+    }
+    RC_CUDA(ctx, launch_march(a, ctx->stream));
+    if (stats) {
+        RC_CUDA(ctx, cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, 4 * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        stats->dense_samples = ctx->h_stats[0];
+        stats->evaluated_samples = ctx->h_stats[1];
+        stats->rays_hit = ctx->h_stats[2];
+        stats->rays_total = ctx->h_stats[3];
+    }
+    return RC_OK;
+}
+
+rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                             const float *dL_dimage, float *dL_dtf) {
+    rc_status st = check_render(ctx, vol, p, dL_dtf, "rc_render_backward");
+    if (st != RC_OK) return st;
+    if (!dL_dimage) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_backward: dL_dimage is NULL");
+    if (p->func != RC_FUNC_COMPOSITE)
+        return fail(ctx, RC_ERR_UNSUPPORTED, "rc_render_backward: compositing function only");
+    DeviceScope ds(ctx->device);
+    size_t need = (size_t)4 * ctx->K * sizeof(long long) + 16;
+    if (ctx->scratch_bytes < need) {
+        void *buf = nullptr;
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        RC_CUDA(ctx, cudaMalloc(&buf, need));
+        cudaFree(ctx->d_scratch);
+        ctx->d_scratch = buf;
+        ctx->scratch_bytes = need;
+    }
+    AdjointArgs a;
+    a.m = march_args(ctx, vol, p, nullptr);
+    a.m.p.skip = 0;
+    a.dimg = reinterpret_cast<const float4 *>(dL_dimage);
+    a.acc = reinterpret_cast<long long *>(ctx->d_scratch);
+    a.acc_scale = 0.0f;
+    RC_CUDA(ctx, launch_adjoint(a, dL_dtf, ctx->stream));
+    return RC_OK;
+}
+
+rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *v, uint16_t *mn, uint16_t *mx) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_brick_grid_get: ctx is NULL");
+    if (!v || !mn || !mx) return fail(ctx, RC_ERR_INVALID_ARG, "rc_brick_grid_get: NULL argument");
+    if (!v->uploaded) return fail(ctx, RC_ERR_STATE, "rc_brick_grid_get: volume has no data");
+    DeviceScope ds(ctx->device);
+    RC_CUDA(ctx, cudaMemcpyAsync(mn, v->d_mn, v->nbricks * sizeof(uint16_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    RC_CUDA(ctx, cudaMemcpyAsync(mx, v->d_mx, v->nbricks * sizeof(uint16_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    return RC_OK;
+}
+
+rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_skip_mask_get: ctx is NULL");
+    if (!vol || !occ) return fail(ctx, RC_ERR_INVALID_ARG, "rc_skip_mask_get: NULL argument");
+    if (!vol->uploaded) return fail(ctx, RC_ERR_STATE, "rc_skip_mask_get: volume has no data");
+    if (ctx->K < 2) return fail(ctx, RC_ERR_STATE, "rc_skip_mask_get: no transfer function");
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    rc_status st = ensure_occupancy(ctx, v);
+    if (st != RC_OK) return st;
+    RC_CUDA(ctx, cudaMemcpyAsync(occ, v->d_occ, v->nbricks, cudaMemcpyDeviceToDevice, ctx->stream));
+    return RC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+// Device building blocks of the march: the FP32 ray specification, bricked
+// voxel addressing, trilinear resampling with central-difference gradients,
+// transfer-function classification, opacity correction and shading.
+#pragma once
+
+#include "rc_internal.h"
+
+namespace rc {
+
+struct Ray {
+    float o[3], d[3], dir[3];
+    float tn, tf, ds;
+    int nsamp;
+};
+
+// Sec. 4.1 step 1, the path of the ray. Every operation is an explicitly
+// rounded FP32 intrinsic (never contracted), so sample positions are the
+// exact values of the written specification:
+//   a = (x + 0.5) / W;  ndc_x = (a*2 - 1) * tx;  b = (y + 0.5) / H;
+//   ndc_y = (1 - b*2) * ty;  v = (f + ndc_x r) + ndc_y u;
+//   len = sqrt((v0^2 + v1^2) + v2^2);  dir = v / len;  d = dir / s;
+//   slab against [0, N-1] per axis (axes with d == 0 test o against the box);
+//   t_near = max(0, max_a min(t0, t1)), t_far = min_a max(t0, t1);
+//   ds = step * smin;  nsamp = floor((t_far - t_near) / ds) + 1.
+__device__ __forceinline__ bool setup_ray(const CamRec &c, const VolDev &v, float step_vox,
+                                          int x, int y, Ray &R) {
+    float a = __fdiv_rn(__fadd_rn((float)x, 0.5f), (float)c.W);
+    float ndcx = __fmul_rn(__fsub_rn(__fmul_rn(a, 2.0f), 1.0f), c.tx);
+    float b = __fdiv_rn(__fadd_rn((float)y, 0.5f), (float)c.H);
+    float ndcy = __fmul_rn(__fsub_rn(1.0f, __fmul_rn(b, 2.0f)), c.ty);
+    float vv[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+        vv[i] = __fadd_rn(__fadd_rn(c.f[i], __fmul_rn(ndcx, c.r[i])), __fmul_rn(ndcy, c.u[i]));
+    float len = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(vv[0], vv[0]), __fmul_rn(vv[1], vv[1])),
+                                     __fmul_rn(vv[2], vv[2])));
+    float tn = 0.0f, tf = __int_as_float(0x7f800000);
+    bool hit = true;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        R.dir[i] = __fdiv_rn(vv[i], len);
+        R.d[i] = __fdiv_rn(R.dir[i], v.s[i]);
+        R.o[i] = c.o[i];
+        float hi = (float)(v.n[i] - 1);
+        if (R.d[i] == 0.0f) {
+            if (R.o[i] < 0.0f || R.o[i] > hi) hit = false;
+        } else {
+            float t0 = __fdiv_rn(__fsub_rn(0.0f, R.o[i]), R.d[i]);
+            float t1 = __fdiv_rn(__fsub_rn(hi, R.o[i]), R.d[i]);
+            tn = fmaxf(tn, fminf(t0, t1));
+            tf = fminf(tf, fmaxf(t0, t1));
+        }
+    }
+    if (!hit || !(tf >= tn)) {
+        R.nsamp = 0;
+        return false;
+    }
+    R.tn = tn;
+    R.tf = tf;
+    R.ds = __fmul_rn(step_vox, v.smin);
+    // at most 2^24 samples per ray (the API bounds step_vox, so this only
+    // guards the int conversion)
+    R.nsamp = (int)fminf(floorf(__fdiv_rn(__fsub_rn(tf, tn), R.ds)), 16777215.0f) + 1;
+    return true;
+}
+
+// Evenly spaced sample k (Sec. 4.1): t_k = fma(k, ds, t_near), p = fma(t_k, d, o).
+__device__ __forceinline__ float sample_t(const Ray &R, int k) {
+    return __fmaf_rn((float)k, R.ds, R.tn);
+}
+
+__device__ __forceinline__ void position_at(const Ray &R, float t, float p[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) p[i] = __fmaf_rn(t, R.d[i], R.o[i]);
+}
+
+// Trilinear cell of a position: p clamped to [0, N-1], base = min(floor, N-2),
+// weight = p - base (exact in FP32).
+struct Cell {
+    int i[3];
+    float w[3];
+};
+
+__device__ __forceinline__ void cell_of(const VolDev &v, const float p[3], Cell &c) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float q = fminf(fmaxf(p[a], 0.0f), (float)(v.n[a] - 1));
+        int b = min((int)q, v.n[a] - 2);   // q >= 0: truncation is floor
+        c.i[a] = b;
+        c.w[a] = __fsub_rn(q, (float)b);
+    }
+}
+
+__device__ __forceinline__ int brick_of(const VolDev &v, const Cell &c) {
+    return ((c.i[2] >> 4) * v.cb[1] + (c.i[1] >> 4)) * v.cb[0] + (c.i[0] >> 4);
+}
+
+// Bricked addressing is separable: offset(x, y, z) = ox(x) + oy(y) + oz(z).
+__device__ __forceinline__ unsigned offx(int x) { return ((unsigned)(x >> 4) << 12) | (unsigned)(x & 15); }
+__device__ __forceinline__ unsigned offy(const VolDev &v, int y) {
+    return (unsigned)(y >> 4) * v.sy + ((unsigned)(y & 15) << 4);
+}
+__device__ __forceinline__ unsigned offz(const VolDev &v, int z) {
+    return (unsigned)(z >> 4) * v.sz + ((unsigned)(z & 15) << 8);
+}
+
+template <int ST>
+__device__ __forceinline__ float fetch(const VolDev &v, unsigned off) {
+    if (ST == RC_STORE_F32) return __ldg((const float *)v.data + off);
+    if (ST == RC_STORE_F16) return __half2float(__ldg((const __half *)v.data + off));
+    return (float)__ldg((const unsigned short *)v.data + off);
+}
+
+// a + w (b - a): one rounding, stays inside [min(a,b), max(a,b)] when b - a is
+// exact (true for integer codes and for FP16 values in [0, 1]).
+__device__ __forceinline__ float lerp(float a, float b, float w) { return __fmaf_rn(w, b - a, a); }
+
+template <int ST>
+__device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
+    unsigned x0 = offx(c.i[0]), x1 = offx(c.i[0] + 1);
+    unsigned y0 = offy(v, c.i[1]), y1 = offy(v, c.i[1] + 1);
+    unsigned z0 = offz(v, c.i[2]), z1 = offz(v, c.i[2] + 1);
+    float wx = c.w[0], wy = c.w[1], wz = c.w[2];
+    float c00 = lerp(fetch<ST>(v, x0 + y0 + z0), fetch<ST>(v, x1 + y0 + z0), wx);
+    float c10 = lerp(fetch<ST>(v, x0 + y1 + z0), fetch<ST>(v, x1 + y1 + z0), wx);
+    float c01 = lerp(fetch<ST>(v, x0 + y0 + z1), fetch<ST>(v, x1 + y0 + z1), wx);
+    float c11 = lerp(fetch<ST>(v, x0 + y1 + z1), fetch<ST>(v, x1 + y1 + z1), wx);
+    return lerp(lerp(c00, c10, wy), lerp(c01, c11, wy), wz);
+}
+
+// Value and world-space central-difference gradient of the trilinear field,
+// one index unit per axis, from the 32 distinct voxels around the cell.
+// The samples at p -/+ e_a use the cells with base coordinates
+// {max(i-1, 0), i} and {i+1, min(i+2, N-1)} and the same weight, which equals
+// resampling the clamped positions p -/+ 1.
+template <int ST>
+__device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, float g[3]) {
+    const int i = c.i[0], j = c.i[1], k = c.i[2];
+    const unsigned X0 = offx(max(i - 1, 0)), X1 = offx(i), X2 = offx(i + 1), X3 = offx(min(i + 2, v.n[0] - 1));
+    const unsigned Y0 = offy(v, max(j - 1, 0)), Y1 = offy(v, j), Y2 = offy(v, j + 1),
+                   Y3 = offy(v, min(j + 2, v.n[1] - 1));
+    const unsigned Z0 = offz(v, max(k - 1, 0)), Z1 = offz(v, k), Z2 = offz(v, k + 1),
+                   Z3 = offz(v, min(k + 2, v.n[2] - 1));
+    const float wx = c.w[0], wy = c.w[1], wz = c.w[2];
+#define RC_F(X, Y, Z) fetch<ST>(v, (X) + (Y) + (Z))
+#define RC_LX(XA, XB, Y, Z) lerp(RC_F(XA, Y, Z), RC_F(XB, Y, Z), wx)
+    // rows along x (y, z) through the centre cell
+    float L11 = RC_LX(X1, X2, Y1, Z1), L21 = RC_LX(X1, X2, Y2, Z1);
+    float L12 = RC_LX(X1, X2, Y1, Z2), L22 = RC_LX(X1, X2, Y2, Z2);
+    // -x and +x cells
+    float M11 = RC_LX(X0, X1, Y1, Z1), M21 = RC_LX(X0, X1, Y2, Z1);
+    float M12 = RC_LX(X0, X1, Y1, Z2), M22 = RC_LX(X0, X1, Y2, Z2);
+    float P11 = RC_LX(X2, X3, Y1, Z1), P21 = RC_LX(X2, X3, Y2, Z1);
+    float P12 = RC_LX(X2, X3, Y1, Z2), P22 = RC_LX(X2, X3, Y2, Z2);
+    // rows of the -y/+y and -z/+z cells
+    float L01 = RC_LX(X1, X2, Y0, Z1), L02 = RC_LX(X1, X2, Y0, Z2);
+    float L31 = RC_LX(X1, X2, Y3, Z1), L32 = RC_LX(X1, X2, Y3, Z2);
+    float L10 = RC_LX(X1, X2, Y1, Z0), L20 = RC_LX(X1, X2, Y2, Z0);
+    float L13 = RC_LX(X1, X2, Y1, Z3), L23 = RC_LX(X1, X2, Y2, Z3);
+#undef RC_LX
+#undef RC_F
+    float a1 = lerp(L11, L21, wy), a2 = lerp(L12, L22, wy);
+    float val = lerp(a1, a2, wz);
+    float xm = lerp(lerp(M11, M21, wy), lerp(M12, M22, wy), wz);
+    float xp = lerp(lerp(P11, P21, wy), lerp(P12, P22, wy), wz);
+    float ym = lerp(lerp(L01, L11, wy), lerp(L02, L12, wy), wz);
+    float yp = lerp(lerp(L21, L31, wy), lerp(L22, L32, wy), wz);
+    float a0 = lerp(L10, L20, wy), a3 = lerp(L13, L23, wy);
+    float zm = lerp(a0, a1, wz);
+    float zp = lerp(a2, a3, wz);
+    g[0] = (xp - xm) * v.inv2s[0];
+    g[1] = (yp - ym) * v.inv2s[1];
+    g[2] = (zp - zm) * v.inv2s[2];
+    return val;
+}
+
+// Table coordinate u = v (K-1) / vscale with the FP32 operations rounded once;
+// for integer codes floor(u) is the exact integer floor, and u is monotone in
+// v, which makes the brick occupancy test exact.
+__device__ __forceinline__ float tf_coord(const VolDev &v, float val, float km1) {
+    return v.storage == RC_STORE_F16 ? __fmul_rn(val, km1) : __fdiv_rn(__fmul_rn(val, km1), v.vscale);
+}
+
+// Sec. 2.6: linear interpolation of the two neighbouring table entries.
+__device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, int *i0 = nullptr,
+                                           float *w0 = nullptr) {
+    float q = fminf(fmaxf(u, 0.0f), (float)(K - 1));
+    int i = min((int)q, K - 2);
+    float w = q - (float)i;
+    float4 a = tab[i], b = tab[i + 1];
+    if (i0) *i0 = i;
+    if (w0) *w0 = w;
+    return make_float4(lerp(a.x, b.x, w), lerp(a.y, b.y, w), lerp(a.z, b.z, w), lerp(a.w, b.w, w));
+}
+
+// Eq. 3 for a segment of length ds: alpha' = 1 - (1 - alpha)^(ds/ds_ref).
+__device__ __forceinline__ float correct_alpha(float a, int rmode, float ratio) {
+    float t = 1.0f - a;
+    if (rmode == 0) return a;
+    if (rmode == 1) return 1.0f - sqrtf(t);
+    if (rmode == 2) return 1.0f - sqrtf(sqrtf(t));
+    return 1.0f - powf(t, ratio);
+}
+
+// Headlight Blinn-Phong with a two-sided diffuse term: light and view along
+// -dir, half vector = light vector; colour = min(1, rgb (ka + kd n.l) + ks (n.l)^16).
+// Below gmin the normal is undefined and the colour is min(1, rgb (ka + kd)).
+__device__ __forceinline__ void shade_factor(const MarchParams &P, const VolDev &v, const float g[3],
+                                             const float dir[3], float &sf, float &spec) {
+    float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    if (g2 < v.gmin * v.gmin) {
+        sf = P.ka + P.kd;
+        spec = 0.0f;
+        return;
+    }
+    float ndl = fabsf(g[0] * dir[0] + g[1] * dir[1] + g[2] * dir[2]) * rsqrtf(g2);
+    ndl = fminf(ndl, 1.0f);
+    float n2 = ndl * ndl, n4 = n2 * n2, n8 = n4 * n4;
+    sf = P.ka + P.kd * ndl;
+    spec = P.ks * (n8 * n8);
+}
+
+__device__ __forceinline__ float4 half4_to_float4(uint2 h) {
+    __half2 lo = *reinterpret_cast<__half2 *>(&h.x);
+    __half2 hi = *reinterpret_cast<__half2 *>(&h.y);
+    float2 a = __half22float2(lo), b = __half22float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Copies the table into shared memory as FP32 (FP16 entries converted exactly).
+__device__ __forceinline__ void load_tf(const TFDev &tf, float4 *s_tf) {
+    for (int e = threadIdx.x; e < tf.K; e += blockDim.x)
+        s_tf[e] = tf.fp16 ? half4_to_float4(tf.f16[e]) : tf.f32[e];
+}
+
+// Jump over a brick the occupancy mask marks empty. Returns the index of the
+// first sample that may lie outside brick(c): the sample m just before the
+// computed exit distance is verified to be in the same brick; since each
+// coordinate of the computed positions is monotone in k, every sample between
+// k and m is then inside too. Falls back to k + 1 when the check fails.
+__device__ __forceinline__ int jump_empty(const Ray &R, const VolDev &v, const Cell &c, int k) {
+    const float INF = __int_as_float(0x7f800000);
+    float texit = INF;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        int b = c.i[a] >> 4;
+        if (R.d[a] > 0.0f && b < v.cb[a] - 1)
+            texit = fminf(texit, __fdiv_rn((float)(16 * b + 16) - R.o[a], R.d[a]));
+        else if (R.d[a] < 0.0f && b > 0)
+            texit = fminf(texit, __fdiv_rn((float)(16 * b) - R.o[a], R.d[a]));
+    }
+    if (texit == INF) return R.nsamp;
+    float fm = floorf(__fdiv_rn(texit - R.tn, R.ds));
+    int m = fm >= (float)R.nsamp ? R.nsamp - 1 : (int)fm;
+    if (m <= k) return k + 1;
+    const int b0 = brick_of(v, c);
+#pragma unroll 1
+    for (int tries = 0; tries < 2 && m > k; tries++, m--) {
+        float p[3];
+        position_at(R, sample_t(R, m), p);
+        Cell cm;
+        cell_of(v, p, cm);
+        if (brick_of(v, cm) == b0) return m + 1;
+    }
+    return k + 1;
+}
+
+}  // namespace rc

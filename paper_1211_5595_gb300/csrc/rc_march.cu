@@ -1,0 +1,175 @@
+// Forward march (Sec. 4.1-4.2): one thread per ray, warps on 8 x 4 pixel tiles,
+// bricked volume gathers through the read-only path, transfer function in
+// shared memory, exact empty-space skipping over the cell-brick occupancy mask
+// and warp-vote early ray termination.
+#include "rc_device.cuh"
+
+namespace rc {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void pixel_of_thread(int &x, int &y) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+}
+
+__device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned dense, unsigned evald,
+                                          unsigned hit, unsigned inimg) {
+    dense = __reduce_add_sync(kFull, dense);
+    evald = __reduce_add_sync(kFull, evald);
+    hit = __reduce_add_sync(kFull, hit);
+    inimg = __reduce_add_sync(kFull, inimg);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(stats + 0, (unsigned long long)dense);
+        atomicAdd(stats + 1, (unsigned long long)evald);
+        atomicAdd(stats + 2, (unsigned long long)hit);
+        atomicAdd(stats + 3, (unsigned long long)inimg);
+    }
+}
+
+// Compositing ray function (Sec. 4.2, Eq. 4): C += T a' c, T *= (1 - a'),
+// front to back from the eye; stop after the sample where 1 - T >= term.
+template <int ST, bool SHADE>
+__global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
+    extern __shared__ float4 s_tf[];
+    load_tf(a.tf, s_tf);
+    __syncthreads();
+    int x, y;
+    pixel_of_thread(x, y);
+    const bool inimg = x < a.cam.W && y < a.cam.H;
+    Ray R;
+    const bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
+    const int nsamp = hit ? R.nsamp : 0;
+    const float km1 = (float)(a.tf.K - 1);
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
+    int k = 0;
+    unsigned evald = 0;
+    bool active = nsamp > 0;
+    while (__any_sync(kFull, active)) {
+        if (!active) continue;
+        float p[3];
+        position_at(R, sample_t(R, k), p);
+        Cell c;
+        cell_of(a.vol, p, c);
+        if (a.p.skip && !__ldg(a.occ + brick_of(a.vol, c))) {
+            k = jump_empty(R, a.vol, c, k);
+            active = k < nsamp;
+            continue;
+        }
+        float val, g[3];
+        if (SHADE) val = value_grad<ST>(a.vol, c, g);
+        else val = trilinear<ST>(a.vol, c);
+        float4 e = classify(s_tf, a.tf.K, tf_coord(a.vol, val, km1));
+        float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
+        float r = e.x, gg = e.y, b = e.z;
+        if (SHADE) {
+            float sf, spec;
+            shade_factor(a.p, a.vol, g, R.dir, sf, spec);
+            r = fminf(1.0f, __fmaf_rn(r, sf, spec));
+            gg = fminf(1.0f, __fmaf_rn(gg, sf, spec));
+            b = fminf(1.0f, __fmaf_rn(b, sf, spec));
+        }
+        float ta = T * ap;
+        C0 = __fmaf_rn(ta, r, C0);
+        C1 = __fmaf_rn(ta, gg, C1);
+        C2 = __fmaf_rn(ta, b, C2);
+        T = T * (1.0f - ap);
+        evald++;
+        k++;
+        active = k < nsamp && (1.0f - T) < a.p.term;
+    }
+    if (inimg) a.out[(size_t)y * a.cam.W + x] = make_float4(C0, C1, C2, 1.0f - T);
+    if (a.stats) add_stats(a.stats, (unsigned)min(k, nsamp), evald, hit ? 1u : 0u, inimg ? 1u : 0u);
+}
+
+// The other ray functions of Sec. 4.1 (MIP, average, x-ray, isosurface,
+// threshold); output channels as documented in rc.h.
+template <int ST>
+__global__ void __launch_bounds__(128) function_kernel(const MarchArgs a) {
+    extern __shared__ float4 s_tf[];
+    load_tf(a.tf, s_tf);
+    __syncthreads();
+    int x, y;
+    pixel_of_thread(x, y);
+    const bool inimg = x < a.cam.W && y < a.cam.H;
+    Ray R;
+    const bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
+    const int nsamp = hit ? R.nsamp : 0;
+    const int func = a.p.func;
+    float4 out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float acc = 0.0f, prev_v = 0.0f, prev_t = 0.0f;
+    int k = 0;
+    bool found = false;
+    for (; k < nsamp; k++) {
+        float t = sample_t(R, k), p[3];
+        position_at(R, t, p);
+        Cell c;
+        cell_of(a.vol, p, c);
+        float v = trilinear<ST>(a.vol, c);
+        if (func == RC_FUNC_MIP) {
+            acc = k == 0 ? v : fmaxf(acc, v);
+        } else if (func == RC_FUNC_AVERAGE || func == RC_FUNC_XRAY) {
+            acc += v;
+        } else if (v >= a.p.iso) {
+            found = true;
+            if (func == RC_FUNC_THRESHOLD) {
+                float4 e = classify(s_tf, a.tf.K, tf_coord(a.vol, v, (float)(a.tf.K - 1)));
+                out = make_float4(e.x, e.y, e.z, 1.0f);
+            } else {
+                float ts = k > 0 ? prev_t + (t - prev_t) * ((a.p.iso - prev_v) / (v - prev_v)) : t;
+                float g[3], sf, spec;
+                value_grad<ST>(a.vol, c, g);
+                shade_factor(a.p, a.vol, g, R.dir, sf, spec);
+                out = make_float4(ts, fminf(1.0f, sf + spec), (float)k, 1.0f);
+            }
+            k++;
+            break;
+        }
+        prev_v = v;
+        prev_t = t;
+    }
+    if (!found && nsamp > 0) {
+        float m = 0.0f;
+        bool have = true;
+        if (func == RC_FUNC_MIP) m = acc / a.vol.vscale;
+        else if (func == RC_FUNC_AVERAGE) m = acc / (float)nsamp / a.vol.vscale;
+        else if (func == RC_FUNC_XRAY) m = acc * R.ds / a.vol.vscale;
+        else have = false;
+        if (have) out = make_float4(m, m, m, 1.0f);
+    }
+    if (inimg) a.out[(size_t)y * a.cam.W + x] = out;
+    if (a.stats) add_stats(a.stats, (unsigned)k, (unsigned)k, hit ? 1u : 0u, inimg ? 1u : 0u);
+}
+
+template <typename K>
+static cudaError_t launch_kernel(K kern, const MarchArgs &a, cudaStream_t s) {
+    size_t smem = (size_t)a.tf.K * sizeof(float4);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((a.cam.W + 15) / 16, (a.cam.H + 7) / 8);
+    kern<<<grid, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_march(const MarchArgs &a, cudaStream_t s) {
+    if (a.p.func != RC_FUNC_COMPOSITE) {
+        switch (a.vol.storage) {
+            case RC_STORE_F32: return launch_kernel(function_kernel<RC_STORE_F32>, a, s);
+            case RC_STORE_F16: return launch_kernel(function_kernel<RC_STORE_F16>, a, s);
+            default: return launch_kernel(function_kernel<RC_STORE_U16>, a, s);
+        }
+    }
+    switch (a.vol.storage * 2 + (a.p.shade ? 1 : 0)) {
+        case RC_STORE_F32 * 2: return launch_kernel(composite_kernel<RC_STORE_F32, false>, a, s);
+        case RC_STORE_F32 * 2 + 1: return launch_kernel(composite_kernel<RC_STORE_F32, true>, a, s);
+        case RC_STORE_F16 * 2: return launch_kernel(composite_kernel<RC_STORE_F16, false>, a, s);
+        case RC_STORE_F16 * 2 + 1: return launch_kernel(composite_kernel<RC_STORE_F16, true>, a, s);
+        case RC_STORE_U16 * 2: return launch_kernel(composite_kernel<RC_STORE_U16, false>, a, s);
+        default: return launch_kernel(composite_kernel<RC_STORE_U16, true>, a, s);
+    }
+}
+
+}  // namespace rc
