@@ -90,7 +90,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -203,11 +203,14 @@ def run_reference(args, w, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--views", type=int, default=0, help="render only the first N orbit views (profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / uint16 storage forms")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -228,6 +231,8 @@ def main():
     ph = synth.workload_phantom(WORKLOAD)
     tf = synth.tf_table(w["K"])
     cams = cameras(ph, w)
+    if args.views:
+        cams = cams[:args.views]
     nviews = len(cams)
     H, W = w["height"], w["width"]
     stream = torch.cuda.current_stream()
@@ -294,27 +299,58 @@ def main():
 
     # end to end through the C-ABI with host buffers: pinned codes and table
     # in, every view's image out, copies inside the timed region
-    img_host = torch.empty((nviews, H, W, 4), dtype=torch.float32).pin_memory()
-    codes_np = codes_host.numpy().view(np.uint16)
+    e2e = None
+    if not args.no_e2e:
+        img_host = torch.empty((nviews, H, W, 4), dtype=torch.float32).pin_memory()
+        codes_np = codes_host.numpy().view(np.uint16)
 
-    def e2e_step():
-        rc.rc_volume_upload(ctx, vol, codes_np)
-        rc.rc_tf_set(ctx, tf)
-        for v, cam in enumerate(cams):
-            rc.rc_camera_set(ctx, cam)
-            rc.rc_render(ctx, vol, P, outs[v])
-        img_host.copy_(outs, non_blocking=True)
-        stream.synchronize()
+        def e2e_step():
+            rc.rc_volume_upload(ctx, vol, codes_np)
+            rc.rc_tf_set(ctx, tf)
+            for v, cam in enumerate(cams):
+                rc.rc_camera_set(ctx, cam)
+                rc.rc_render(ctx, vol, P, outs[v])
+            img_host.copy_(outs, non_blocking=True)
+            stream.synchronize()
 
-    for _ in range(args.warmup):
-        e2e_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    e2e_s = time.perf_counter() - t0
-    h2d = codes_host.numel() * 2 + tf.nbytes
-    d2h = img_host.numel() * 4
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * dense * args.steps / e2e_s / 1e9, "unit": "Gsamples/s",
+               "h2d_bytes_per_step": codes_host.numel() * 2 + tf.nbytes,
+               "d2h_bytes_per_step": img_host.numel() * 4}
+
+    # reduced-precision storage forms on the same workload: FP16 (normalised)
+    # and raw uint16 volumes with the FP16 table, against the FP32 images
+    forms = {}
+    if not args.no_forms:
+        ref_imgs = outs.clone()
+        fp32_frame_ms = statistics.median(frame_ms)
+        for name, storage in (("f16", rc.RC_STORE_F16), ("u16", rc.RC_STORE_U16)):
+            v2 = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, storage)
+            rc.rc_volume_upload(ctx, v2, codes_dev)
+            rc.rc_tf_set_device(ctx, tf_dev, fp16=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cams]
+            for rep in range(2):
+                for v, cam in enumerate(cams):
+                    rc.rc_camera_set(ctx, cam)
+                    ev[v][0].record(stream)
+                    rc.rc_render(ctx, v2, P, outs[v])
+                    ev[v][1].record(stream)
+                flush.zero_()
+            torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+            mse = ((outs - ref_imgs) ** 2).mean(dim=(1, 2, 3))
+            psnr = float((10 * torch.log10(1.0 / mse.clamp_min(1e-30))).min())
+            forms[name] = {"ms_per_frame_median": ms, "gsamples_s": dense / nviews / (ms / 1e3) / 1e9,
+                           "speedup_vs_f32": fp32_frame_ms / ms, "psnr_db_min_vs_f32": psnr,
+                           "max_abs_vs_f32": float((outs - ref_imgs).abs().max())}
+            rc.rc_volume_destroy(ctx, v2)
+        rc.rc_tf_set_device(ctx, tf_dev)
 
     hbm_peak, peak_kind = peaks()
     frame_avg_s = statistics.mean(frame_ms) / 1e3
@@ -335,8 +371,8 @@ def main():
                      "kernel": "composite_kernel<F32, shaded>",
                      "model": f"{BYTES_PER_SAMPLE} B per evaluated sample (32 distinct FP32 voxels) / mean launch time",
                      "peak_kind": f"{peak_kind} copy bandwidth"},
-        "e2e": {"value": world * dense * args.steps / e2e_s / 1e9, "unit": "Gsamples/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": e2e,
+        "forms": forms,
         "gpu_launches": args.steps * (2 + 1 + 1 + nviews),
         "clocks": clocks.summary(),
     }

