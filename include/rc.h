@@ -167,6 +167,24 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol,
                              const rc_render_params *params, const float *dL_dimage,
                              float *dL_dtf);
 
+/* The gradient of rc_render_backward for callers that cannot allocate device
+ * memory once they are running: for example a host application whose device
+ * memory is all handed out up front by its own allocator, or a frame loop in
+ * which a cudaMalloc (which can synchronise the whole device) is not allowed.
+ * The paper has no counterpart; this is a service of the library.
+ * Same arguments and result as rc_render_backward. It allocates nothing: the
+ * fixed-point accumulators live in one file-scope device array sized for
+ * tables of at most 1024 entries (32 KB + 256 B, held on every GPU that loads
+ * the library until the process exits); a larger table returns
+ * RC_ERR_UNSUPPORTED. The first call on a device looks up that array's device
+ * address (and may load the library's device code), so make the first call
+ * before any stream capture. Every call shares the one array and clears it on
+ * the stream before use; calls whose work overlaps on the GPU (other streams or
+ * contexts on the same device) race on it and must be serialised by the caller. */
+rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol,
+                                     const rc_render_params *params, const float *dL_dimage,
+                                     float *dL_dtf);
+
 /* Copies the cell-brick min/max grid (uint16, brick_dims order x fastest) into
  * caller device buffers mn, mx. */
 rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *vol, uint16_t *mn, uint16_t *mx);

@@ -63,6 +63,7 @@ SIGNATURES = {
     "rc_camera_set": (_I, [_P, C.POINTER(rc_camera)]),
     "rc_render": (_I, [_P, _P, C.POINTER(rc_render_params), _P, C.POINTER(rc_stats)]),
     "rc_render_backward": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
+    "rc_render_backward_noalloc": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
     "rc_brick_grid_get": (_I, [_P, _P, _P, _P]),
     "rc_skip_mask_get": (_I, [_P, _P, _P]),
 }
@@ -229,6 +230,14 @@ def rc_render_backward(ctx, vol, params, dimage, dtf):
     p = _params(params)
     _check(lib().rc_render_backward(ctx, vol, C.byref(p), _ptr(dimage), _ptr(dtf)), ctx,
            "rc_render_backward")
+
+
+def rc_render_backward_noalloc(ctx, vol, params, dimage, dtf):
+    """rc_render_backward without any device allocation (static scratch,
+    tables of at most 1024 entries); see include/rc.h."""
+    p = _params(params)
+    _check(lib().rc_render_backward_noalloc(ctx, vol, C.byref(p), _ptr(dimage), _ptr(dtf)), ctx,
+           "rc_render_backward_noalloc")
 
 
 def rc_brick_grid_get(ctx, vol, mn, mx):

@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "rc_internal.h"
@@ -498,6 +499,68 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_ren
     a.m.p.skip = 0;
     a.dimg = reinterpret_cast<const float4 *>(dL_dimage);
     a.acc = reinterpret_cast<long long *>(ctx->d_scratch);
+    a.acc_scale = 0.0f;
+    RC_CUDA(ctx, launch_adjoint(a, dL_dtf, ctx->stream));
+    return RC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// transfer-function gradient without device allocation
+// ---------------------------------------------------------------------------
+// Scratch of rc_render_backward_noalloc: the 4K fixed-point accumulators and
+// the |dL/dI| maximum for tables of at most kNoAllocMaxEntries entries. It is a
+// file-scope device array, so every GPU that loads this library holds it
+// (32 KB + 256 B) until the process exits. Host code must not use the symbol
+// itself as an address: it is a host-side stand-in. The device address is
+// looked up once per device with that device current.
+constexpr int kNoAllocMaxEntries = 1024;
+static __device__ __align__(256) long long g_tf_grad_scratch[4 * kNoAllocMaxEntries + 32];
+
+constexpr int kNoAllocMaxDevices = 64;
+static void *g_tf_grad_scratch_addr[kNoAllocMaxDevices];
+static std::mutex g_tf_grad_scratch_mu;
+
+static rc_status noalloc_scratch(rc_context *ctx, long long **out) {
+    if (ctx->device >= kNoAllocMaxDevices)
+        return fail(ctx, RC_ERR_UNSUPPORTED, "rc_render_backward_noalloc: device index %d >= %d", ctx->device,
+                    kNoAllocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_tf_grad_scratch_mu);
+    if (!g_tf_grad_scratch_addr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_tf_grad_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ctx, RC_ERR_CUDA, "rc_render_backward_noalloc: cudaGetSymbolAddress: %s",
+                        cudaGetErrorString(e));
+        g_tf_grad_scratch_addr[ctx->device] = p;
+    }
+    *out = reinterpret_cast<long long *>(g_tf_grad_scratch_addr[ctx->device]);
+    return RC_OK;
+}
+
+extern "C" {
+
+rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                     const float *dL_dimage, float *dL_dtf) {
+    rc_status st = check_render(ctx, vol, p, dL_dtf, "rc_render_backward_noalloc");
+    if (st != RC_OK) return st;
+    if (!dL_dimage) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_backward_noalloc: dL_dimage is NULL");
+    if (p->func != RC_FUNC_COMPOSITE)
+        return fail(ctx, RC_ERR_UNSUPPORTED, "rc_render_backward_noalloc: compositing function only");
+    if (ctx->K > kNoAllocMaxEntries)
+        return fail(ctx, RC_ERR_UNSUPPORTED,
+                    "rc_render_backward_noalloc: table of %d entries exceeds the static scratch (at most %d)",
+                    ctx->K, kNoAllocMaxEntries);
+    DeviceScope ds(ctx->device);
+    long long *scratch = nullptr;
+    st = noalloc_scratch(ctx, &scratch);
+    if (st != RC_OK) return st;
+    AdjointArgs a;
+    a.m = march_args(ctx, vol, p, nullptr);
+    a.m.p.skip = 0;
+    a.dimg = reinterpret_cast<const float4 *>(dL_dimage);
+    a.acc = scratch;            // cleared on the stream before the kernel runs
     a.acc_scale = 0.0f;
     RC_CUDA(ctx, launch_adjoint(a, dL_dtf, ctx->stream));
     return RC_OK;
