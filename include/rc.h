@@ -97,10 +97,12 @@ typedef struct {
 } rc_render_params;
 
 typedef struct {
-    uint64_t dense_samples;      /* samples up to termination, skipped ones included */
+    uint64_t dense_samples;      /* samples up to termination, skipped ones included
+                                    (0 for the importance-sampled renders) */
     uint64_t evaluated_samples;  /* samples resampled and classified */
     uint64_t rays_hit;           /* rays that intersect the volume box */
     uint64_t rays_total;
+    uint64_t fallback_rays;      /* importance-sampled renders: rays re-marched */
 } rc_stats;
 
 /* Text of a status code (static storage). */
@@ -195,6 +197,85 @@ rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *vol, uint16_t *mn,
  * touch, floor(u(min)) .. min(floor(u(max)) + 1, K - 1), has opacity 0, with
  * u(v) = v (K-1) / vmax (raw codes) or fp16(v / vmax) (K-1) (F16 storage). */
 rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ);
+
+/* ---- learned sampling proposal -------------------------------------------
+ * The paper marches evenly spaced samples (Sec. 4.1). This extension lets a
+ * small network predict, per ray, a 32-bin opacity PDF over the ray's chord
+ * [t_near, t_far] and the ray's final transmittance T^. The PDF marks where
+ * the ray's contribution ends: b_end is one bin past the first bin >= b_start
+ * where the running sum of the PDF reaches 1 - 1/64 (a margin for early
+ * predictions; at most 31, and 31 if never); b_start is the first
+ * bin whose start, centre or end lies in an occupied cell-brick (the whole
+ * chord when none does). nimp samples at the centres of nimp equal segments of
+ * [t_a, t_b] (start of bin b_start to end of bin b_end) replace the evenly
+ * spaced march of Sec. 4.1 and are composited as in Sec. 4.2, each opacity
+ * corrected to its segment (Eq. 3). Rays whose composited transmittance differs
+ * from T^ by more than eps are re-marched by the plain march. The paper has no
+ * learned part.
+ *
+ * Features of a ray (112 floats): e = fma(t_near, d, o) / (N - 1) per axis (the
+ * entry point in [0, 1]^3) and the world direction, x = (e, dir); for each x_c
+ * and j = 0..5: sin(2^j pi x_c), cos(2^j pi x_c) (72 values, c outer, j inner);
+ * for b = 0..31 the occupancy (0/1) of the cell-brick holding the point at
+ * t = fma(b + 0.5, (t_far - t_near)/32, t_near); then 2 zeros. A ray that misses
+ * the box has all-zero features.
+ *
+ * Network: h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2), h3 = relu(h2 W3 + b3),
+ * z = h3 W4 + b4 with W1 112x64, W2 and W3 64x64, W4 64x40; weights and layer
+ * inputs rounded to BF16, FP32 accumulation, FP32 biases; PDF = softmax(z[0:32]),
+ * T^ = sigmoid(z[32]); z[33:40] is padding. Parameters (FP32, RC_PROPOSAL_PARAMS
+ * floats) in the order W1 (input-major: W1[k*64 + n]), b1, W2, b2, W3, b3, W4
+ * (W4[k*40 + n]), b4. */
+#define RC_PROPOSAL_BINS 32
+#define RC_PROPOSAL_FEATURES 112
+#define RC_PROPOSAL_OUTPUTS 33
+#define RC_PROPOSAL_PARAMS 18152
+
+/* Loads the network from a little-endian blob: "RCPROP01", uint32 version (1),
+ * n_features (112), n_hidden (64), n_hidden_layers (3), n_out (40),
+ * n_out_used (33), n_params (18152), has_adam (0/1), uint64 adam_step, then
+ * n_params FP32 parameters and, with has_adam, the Adam first and second
+ * moments (n_params FP32 each). Malformed blobs return RC_ERR_FORMAT and leave
+ * the previous network in place. */
+rc_status rc_proposal_load(rc_context *ctx, const void *blob, size_t bytes);
+/* Writes the blob (with Adam state) into host memory. With blob == NULL only
+ * *bytes_out is set. Synchronises the stream. */
+rc_status rc_proposal_save(rc_context *ctx, void *blob, size_t capacity, size_t *bytes_out);
+
+/* Training targets for the current camera: per pixel 33 floats (device,
+ * H*W*33): the weights T_k a'_k of 512 samples at the centres of 512 equal
+ * segments of the chord (no early termination) summed 16 per bin, then the
+ * final transmittance (1 and zero weights for rays that miss). */
+rc_status rc_profiles_generate(rc_context *ctx, const rc_volume *vol,
+                               const rc_render_params *params, float *out);
+/* Features of every pixel's ray for the current camera (device, H*W*112). */
+rc_status rc_proposal_features(rc_context *ctx, const rc_volume *vol,
+                               const rc_render_params *params, float *out);
+/* Network on n feature rows (device n*112) -> n rows of (PDF[32], T^) (device). */
+rc_status rc_proposal_forward(rc_context *ctx, const float *features, int64_t n, float *out);
+/* Gradient of the mean loss over n rays with respect to the FP32 parameters
+ * (device RC_PROPOSAL_PARAMS floats) and the loss (device float, may be NULL).
+ * targets: n rows of 33 (profile bins, final transmittance). Loss per ray:
+ * w KL(q || p) + (T^ - T)^2 with q = bins / sum(bins), w = sum(bins); BF16
+ * rounding treated as identity in the backward. Deterministic. */
+rc_status rc_proposal_grad(rc_context *ctx, const float *features, const float *targets, int64_t n,
+                           float *grad, float *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on that
+ * gradient; loss as above (device, may be NULL). */
+rc_status rc_proposal_train_step(rc_context *ctx, const float *features, const float *targets, int64_t n,
+                                 float lr, float *loss);
+/* Importance-sampled render from given per-pixel PDFs (device H*W*32) and
+ * transmittances T^ (device H*W): nimp (1..4096) samples per ray over the range
+ * described above; rays with |T - T^| > eps fall back to the plain march
+ * (eps > 1: never). fallback: per-pixel flags (device) or NULL. stats counts
+ * fallback rays in fallback_rays. */
+rc_status rc_render_importance(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                               const float *pdf, const float *that, int nimp, float eps,
+                               float *out_rgba, uint8_t *fallback, rc_stats *stats);
+/* The same with the loaded network evaluated in the kernel (features, network,
+ * importance march and fallback fused in one launch). */
+rc_status rc_render_proposal(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                             int nimp, float eps, float *out_rgba, uint8_t *fallback, rc_stats *stats);
 
 #ifdef __cplusplus
 }

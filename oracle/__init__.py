@@ -72,8 +72,9 @@ def lib():
         L.orc_ray_geometry.argtypes = [P, P, P, P, C.c_int, C.c_int, P]
         L.orc_render_grad.argtypes = [P, P, P, P, P, C.c_int64, P, P, P, C.c_int]
         L.orc_profiles.argtypes = [P, P, P, P, P, C.c_int64, P, P, C.c_int]
-        L.orc_importance.argtypes = [P, P, P, P, P, C.c_int64, P, C.c_float, C.c_int, P, P, P,
-                                     C.c_int]
+        L.orc_importance.argtypes = [P, P, P, P, P, C.c_int64, P, P, C.c_int, P, P, P, C.c_int]
+        L.orc_proposal_features.argtypes = [P, P, P, P, P, C.c_int64, P, P]
+        L.orc_proposal_features.restype = C.c_int
         L.orc_brick_minmax.argtypes = [P, P, P]
         L.orc_occupancy.argtypes = [P, P, P, P, P]
         for f in ("orc_render", "orc_ray_samples", "orc_ray_geometry", "orc_render_grad",
@@ -197,13 +198,20 @@ def profiles(scene: Scene, pixels=None, nthreads=None):
     return bins, tfin
 
 
-def importance(scene: Scene, pdf, lam=0.05, nimp=64, pixels=None, nthreads=None):
-    """Composite of nimp stratified samples drawn from per-ray 32-bin PDFs."""
+def importance(scene: Scene, pdf, nimp=64, pixels=None, nthreads=None, occ=None):
+    """Composite of nimp samples per ray evenly spaced over the range from the
+    first occupied bin to the bin where the ray's 32-bin PDF saturates.
+    occ: cell-brick occupancy (computed from the scene when not given)."""
     n = scene.npix(pixels)
     p = np.ascontiguousarray(np.asarray(pdf, dtype=np.float32).reshape(n, 32))
+    if occ is None:
+        mn, mx = brick_minmax(scene.vol, vmax=scene.v.vmax)
+        occ = occupancy((scene.v.nx, scene.v.ny, scene.v.nz), scene.tf, mn, mx, vmax=scene.v.vmax,
+                        value_mode=scene.v.value_mode, tf_fp16=bool(scene.t.fp16))
+    o = np.ascontiguousarray(occ, dtype=np.uint8)
     rgba = np.zeros((n, 4)); tfin = np.zeros(n); ns = np.zeros(n, dtype=np.int32)
     arr, ptr = _pix(pixels)
-    rc = lib().orc_importance(*scene.refs(), ptr, n, p.ctypes.data, float(lam), int(nimp),
+    rc = lib().orc_importance(*scene.refs(), ptr, n, p.ctypes.data, o.ctypes.data, int(nimp),
                               rgba.ctypes.data, tfin.ctypes.data, ns.ctypes.data,
                               nthreads or default_threads())
     if rc:
@@ -238,3 +246,15 @@ def occupancy(dims, tf, mn, mx, vmax=4095, value_mode=0, tf_fp16=False):
     lib().orc_occupancy(C.byref(desc), C.byref(tdesc), mn.ctypes.data, mx.ctypes.data,
                         occ.ctypes.data)
     return occ
+
+
+def proposal_features(scene: Scene, occ, pixels=None):
+    """The 112 features of the learned proposal per listed pixel (FP64)."""
+    n = scene.npix(pixels)
+    out = np.zeros((n, 112))
+    o = np.ascontiguousarray(occ, dtype=np.uint8)
+    arr, ptr = _pix(pixels)
+    rc = lib().orc_proposal_features(*scene.refs(), ptr, n, o.ctypes.data, out.ctypes.data)
+    if rc:
+        raise ValueError("oracle proposal_features failed")
+    return out

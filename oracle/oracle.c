@@ -490,7 +490,7 @@ struct job {
     const double *dimg;
     double *dtf_thread;     /* nthreads x K x 4 */
     const float *pdf;
-    float lambda;
+    const uint8_t *occ;
     int nimp;
     sample **scratch;       /* per thread */
     int *cap;               /* per thread: samples the scratch holds */
@@ -815,21 +815,37 @@ int orc_profiles(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
 /* ------------------------------------------------------------------------ */
 /* importance-sampled compositing from a per-ray opacity PDF                  */
 /* ------------------------------------------------------------------------ */
-/* The 32-bin PDF over [t_near, t_far] is mixed with the uniform density,
- * q_b = (1 - lambda) pdf_b + lambda / 32, and nimp stratified quantiles
- * (j + 0.5) / nimp of its piecewise-linear CDF give the sample distances t_j.
- * Sample j stands for the segment between the midpoints to its neighbours
- * (the first and last segments reach t_near and t_far), and its opacity is
- * corrected to that segment's length. Positions follow this FP32
- * specification (each operation rounds once):
- *   L = t_far - t_near; bw = L / 32; om = 1 - lambda; lu = lambda / 32;
- *   q_b = fmaf(om, pdf_b, lu); F_0 = 0, F_{b+1} = F_b + q_b;
- *   target_j = ((j + 0.5) / nimp) * F_32;
- *   b_j = last b in [0, 31] with F_b <= target_j;
- *   f_j = min(max((target_j - F_b) / q_b, 0), 1); t_j = fmaf(b_j + f_j, bw, t_near);
- *   m_j = (t_j + t_{j+1}) * 0.5 (m_{-1} = t_near, m_{nimp-1} = t_far);
- *   seg_j = m_j - m_{j-1}.
+/* The proposal's 32-bin PDF over [t_near, t_far] marks where the ray's
+ * contribution ends: b_end is one bin past the first bin >= b_start where its
+ * running sum reaches 1 - 1/64 (a margin for early predictions; 31 at most, and
+ * 31 if the sum never gets there). b_start is the first bin whose start, centre
+ * or end point lies in an occupied cell-brick (exact knowledge of where the
+ * opacity is zero; with no occupied point the range is the whole chord). nimp
+ * samples at the centres of nimp equal segments of [t_a, t_b] (the start of
+ * bin b_start to the end of bin b_end) replace the evenly spaced march; each
+ * stands for its segment, with its opacity corrected to that length (Eq. 3).
+ * FP32 specification (each operation rounds once):
+ *   bw = (t_far - t_near) / 32; point b: fmaf(b, bw, t_near),
+ *   fmaf(b + 0.5, bw, t_near), fmaf(b + 1, bw, t_near); P_{b+1} = P_b + pdf_b;
+ *   t_a = b_start == 0 ? t_near : fmaf(b_start, bw, t_near);
+ *   t_b = b_end == 31 ? t_far : fmaf(b_end + 1, bw, t_near);
+ *   seg = (t_b - t_a) / nimp; t_j = fmaf(j + 0.5, seg, t_a).
  * Compositing and early termination as in composite(). aux2 = T at the end. */
+static int occupied_at(const scene *S, const ray *R, const uint8_t *occ, float t) {
+    int nb[3];
+    for (int a = 0; a < 3; a++) nb[a] = (S->n[a] - 1 + 15) / 16;
+    double p[3];
+    for (int c = 0; c < 3; c++) p[c] = (double)fmaf(t, R->d[c], R->o[c]);
+    int idx[3];
+    for (int a = 0; a < 3; a++) {
+        int i;
+        double w;
+        cell(p[a], S->n[a], &i, &w);
+        idx[a] = i / 16;
+    }
+    return occ[(idx[2] * nb[1] + idx[1]) * nb[0] + idx[0]] != 0;
+}
+
 static void importance_pixel(job *J, int64_t idx, int tid) {
     (void)tid;
     const scene *S = J->S;
@@ -842,40 +858,39 @@ static void importance_pixel(job *J, int64_t idx, int tid) {
     int ns = 0;
     if (R.hit && J->nimp > 0) {
         const float *pdf = J->pdf + (size_t)PROF_BINS * idx;
-        float L = R.tf - R.tn;
-        float bw = L / (float)PROF_BINS;
-        float om = 1.0f - J->lambda;
-        float lu = J->lambda / (float)PROF_BINS;
-        float q[PROF_BINS], F[PROF_BINS + 1];
-        F[0] = 0.0f;
-        for (int b = 0; b < PROF_BINS; b++) {
-            q[b] = fmaf(om, pdf[b], lu);
-            F[b + 1] = F[b] + q[b];
+        float bw = (R.tf - R.tn) / (float)PROF_BINS;
+        int b0 = -1, b1 = PROF_BINS - 1;
+        for (int b = 0; b < PROF_BINS && b0 < 0; b++)
+            if (occupied_at(S, &R, J->occ, fmaf((float)b, bw, R.tn)) ||
+                occupied_at(S, &R, J->occ, fmaf((float)b + 0.5f, bw, R.tn)) ||
+                occupied_at(S, &R, J->occ, fmaf((float)b + 1.0f, bw, R.tn)))
+                b0 = b;
+        if (b0 < 0) {
+            b0 = 0;
+        } else {
+            float P = 0.0f;
+            for (int b = 0; b < PROF_BINS; b++) {
+                P = P + pdf[b];
+                if (b >= b0 && P >= 1.0f - 1.0f / 64.0f) {
+                    b1 = b + 1 < PROF_BINS - 1 ? b + 1 : PROF_BINS - 1;
+                    break;
+                }
+            }
         }
-        float *ts = (float *)malloc(sizeof(float) * (size_t)J->nimp);
-        for (int j = 0; j < J->nimp; j++) {
-            float target = (((float)j + 0.5f) / (float)J->nimp) * F[PROF_BINS];
-            int b = 0;
-            for (int c = 1; c < PROF_BINS; c++)
-                if (F[c] <= target) b = c;
-            float fr = (target - F[b]) / q[b];
-            fr = fminf(fmaxf(fr, 0.0f), 1.0f);
-            ts[j] = fmaf((float)b + fr, bw, R.tn);
-        }
+        float ta = b0 == 0 ? R.tn : fmaf((float)b0, bw, R.tn);
+        float tb = b1 == PROF_BINS - 1 ? R.tf : fmaf((float)(b1 + 1), bw, R.tn);
+        float seg = (tb - ta) / (float)J->nimp;
+        double ratio = (double)seg / (double)S->smin;
         double C[3] = {0, 0, 0};
-        float mprev = R.tn;
         for (int j = 0; j < J->nimp; j++) {
-            float mnext = j + 1 < J->nimp ? (ts[j] + ts[j + 1]) * 0.5f : R.tf;
-            float seg = mnext - mprev;
-            mprev = mnext;
+            float t = fmaf((float)j + 0.5f, seg, ta);
             sample s;
-            eval_sample(S, &R, (double)ts[j], (double)seg / (double)S->smin, &s);
+            eval_sample(S, &R, (double)t, ratio, &s);
             for (int c = 0; c < 3; c++) C[c] += T * s.a * s.col[c];
             T *= (1.0 - s.a);
             ns = j + 1;
             if (1.0 - T >= (double)S->P.term) break;
         }
-        free(ts);
         out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
     }
     for (int c = 0; c < 4; c++) J->rgba[4 * idx + c] = out[c];
@@ -885,7 +900,7 @@ static void importance_pixel(job *J, int64_t idx, int tid) {
 
 int orc_importance(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
                    const orc_params *prm, const int32_t *pix, int64_t npix, const float *pdf,
-                   float lambda, int nimp, double *rgba, double *tfinal, int32_t *nsamp,
+                   const uint8_t *occ, int nimp, double *rgba, double *tfinal, int32_t *nsamp,
                    int nthreads) {
     scene S;
     int rc = scene_init(&S, vol, tf, cam, prm);
@@ -897,12 +912,73 @@ int orc_importance(const orc_volume *vol, const orc_tf *tf, const orc_camera *ca
     J.npix = pix ? npix : (int64_t)cam->width * cam->height;
     J.fn = importance_pixel;
     J.pdf = pdf;
-    J.lambda = lambda;
+    J.occ = occ;
     J.nimp = nimp;
     J.rgba = rgba;
     J.aux2 = tfinal;
     J.nsamp = nsamp;
     run_job(&J, nthreads, 0);
+    scene_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* inputs of the learned proposal                                            */
+/* ------------------------------------------------------------------------ */
+/* Per ray 112 features: the entry point e = fma(t_near, d, o) / (N - 1) (FP32,
+ * as the ray specification) and the world direction, x = (e, dir); for each x_c
+ * and j = 0..5, sin(2^j pi x_c) and cos(2^j pi x_c) in FP64; for b = 0..31 the
+ * occupancy bit of the cell-brick holding the point at
+ * t = fma(b + 0.5, (t_far - t_near) / 32, t_near); two zeros. occ is the
+ * cell-brick occupancy (x fastest). Rays that miss give zeros. */
+static int brick_of_point(const scene *S, const double p[3], const int nb[3]) {
+    int idx[3];
+    for (int a = 0; a < 3; a++) {
+        int i;
+        double w;
+        cell(p[a], S->n[a], &i, &w);
+        idx[a] = i / 16;
+    }
+    return (idx[2] * nb[1] + idx[1]) * nb[0] + idx[0];
+}
+
+int orc_proposal_features(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
+                          const orc_params *prm, const int32_t *pix, int64_t npix,
+                          const uint8_t *occ, double *feat) {
+    scene S;
+    int rc = scene_init(&S, vol, tf, cam, prm);
+    if (rc) { scene_free(&S); return rc; }
+    int nb[3];
+    for (int a = 0; a < 3; a++) nb[a] = (S.n[a] - 1 + 15) / 16;
+    int64_t n = pix ? npix : (int64_t)cam->width * cam->height;
+    for (int64_t r = 0; r < n; r++) {
+        int64_t lin = pix ? (int64_t)pix[r] : r;
+        int x = (int)(lin % S.W), y = (int)(lin / S.W);
+        double *f = feat + 112 * r;
+        for (int i = 0; i < 112; i++) f[i] = 0.0;
+        ray R;
+        ray_setup_f32(&S, S.P.step_vox, x, y, &R);
+        if (!R.hit) continue;
+        float xs[6];
+        for (int c = 0; c < 3; c++) {
+            xs[c] = fmaf(R.tn, R.d[c], R.o[c]) / (float)(S.n[c] - 1);
+            xs[3 + c] = R.dir[c];
+        }
+        for (int c = 0; c < 6; c++) f[c] = (double)xs[c];
+        for (int c = 0; c < 6; c++)
+            for (int j = 0; j < 6; j++) {
+                double arg = 3.14159265358979323846 * ldexp((double)xs[c], j);
+                f[6 + 12 * c + 2 * j] = sin(arg);
+                f[7 + 12 * c + 2 * j] = cos(arg);
+            }
+        float bw = (R.tf - R.tn) / 32.0f;
+        for (int b = 0; b < 32; b++) {
+            float t = fmaf((float)b + 0.5f, bw, R.tn);
+            double p[3];
+            for (int c = 0; c < 3; c++) p[c] = (double)fmaf(t, R.d[c], R.o[c]);
+            f[78 + b] = occ[brick_of_point(&S, p, nb)] ? 1.0 : 0.0;
+        }
+    }
     scene_free(&S);
     return 0;
 }

@@ -41,7 +41,13 @@ class rc_render_params(C.Structure):
 
 class rc_stats(C.Structure):
     _fields_ = [("dense_samples", C.c_uint64), ("evaluated_samples", C.c_uint64),
-                ("rays_hit", C.c_uint64), ("rays_total", C.c_uint64)]
+                ("rays_hit", C.c_uint64), ("rays_total", C.c_uint64), ("fallback_rays", C.c_uint64)]
+
+
+RC_PROPOSAL_BINS = 32
+RC_PROPOSAL_FEATURES = 112
+RC_PROPOSAL_OUTPUTS = 33
+RC_PROPOSAL_PARAMS = 18152
 
 
 # Every symbol include/rc.h declares, with its ctypes signature.
@@ -66,6 +72,16 @@ SIGNATURES = {
     "rc_render_backward_noalloc": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
     "rc_brick_grid_get": (_I, [_P, _P, _P, _P]),
     "rc_skip_mask_get": (_I, [_P, _P, _P]),
+    "rc_proposal_load": (_I, [_P, _P, C.c_size_t]),
+    "rc_proposal_save": (_I, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "rc_profiles_generate": (_I, [_P, _P, C.POINTER(rc_render_params), _P]),
+    "rc_proposal_features": (_I, [_P, _P, C.POINTER(rc_render_params), _P]),
+    "rc_proposal_forward": (_I, [_P, _P, C.c_int64, _P]),
+    "rc_proposal_grad": (_I, [_P, _P, _P, C.c_int64, _P, _P]),
+    "rc_proposal_train_step": (_I, [_P, _P, _P, C.c_int64, C.c_float, _P]),
+    "rc_render_importance": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P, _I, C.c_float, _P, _P,
+                                  C.POINTER(rc_stats)]),
+    "rc_render_proposal": (_I, [_P, _P, C.POINTER(rc_render_params), _I, C.c_float, _P, _P, C.POINTER(rc_stats)]),
 }
 
 _lib = None
@@ -220,10 +236,14 @@ def rc_render(ctx, vol, params, out, stats=False):
     st = rc_stats() if stats else None
     _check(lib().rc_render(ctx, vol, C.byref(p), _ptr(out), C.byref(st) if st is not None else None),
            ctx, "rc_render")
+    return _stats_dict(st)
+
+
+def _stats_dict(st):
     if st is None:
         return None
     return dict(dense_samples=st.dense_samples, evaluated_samples=st.evaluated_samples,
-                rays_hit=st.rays_hit, rays_total=st.rays_total)
+                rays_hit=st.rays_hit, rays_total=st.rays_total, fallback_rays=st.fallback_rays)
 
 
 def rc_render_backward(ctx, vol, params, dimage, dtf):
@@ -246,3 +266,90 @@ def rc_brick_grid_get(ctx, vol, mn, mx):
 
 def rc_skip_mask_get(ctx, vol, occ):
     _check(lib().rc_skip_mask_get(ctx, vol, _ptr(occ)), ctx, "rc_skip_mask_get")
+
+
+# ---------------------------------------------------------------------------
+# learned proposal
+# ---------------------------------------------------------------------------
+_BLOB_MAGIC = b"RCPROP01"
+
+
+def pack_proposal_blob(params, m=None, v=None, adam_step=0) -> bytes:
+    """The rc_proposal_load blob of include/rc.h (little-endian)."""
+    import struct
+    p = np.ascontiguousarray(params, dtype="<f4").reshape(-1)
+    assert p.size == RC_PROPOSAL_PARAMS
+    has_adam = m is not None
+    head = _BLOB_MAGIC + struct.pack("<8IQ", 1, 112, 64, 3, 40, 33, RC_PROPOSAL_PARAMS, int(has_adam),
+                                     int(adam_step))
+    body = p.tobytes()
+    if has_adam:
+        body += np.ascontiguousarray(m, dtype="<f4").tobytes() + np.ascontiguousarray(v, dtype="<f4").tobytes()
+    return head + body
+
+
+def unpack_proposal_blob(blob: bytes) -> dict:
+    import struct
+    assert blob[:8] == _BLOB_MAGIC
+    vals = struct.unpack("<8IQ", blob[8:48])
+    n = vals[6]
+    arr = np.frombuffer(blob[48:], dtype="<f4")
+    out = dict(params=arr[:n].copy(), adam_step=vals[8])
+    if vals[7]:
+        out["m"] = arr[n:2 * n].copy()
+        out["v"] = arr[2 * n:3 * n].copy()
+    return out
+
+
+def rc_proposal_load(ctx, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(lib().rc_proposal_load(ctx, buf, len(blob)), ctx, "rc_proposal_load")
+
+
+def rc_proposal_save(ctx) -> bytes:
+    n = C.c_size_t(0)
+    _check(lib().rc_proposal_save(ctx, None, 0, C.byref(n)), ctx, "rc_proposal_save")
+    buf = C.create_string_buffer(n.value)
+    _check(lib().rc_proposal_save(ctx, buf, n.value, C.byref(n)), ctx, "rc_proposal_save")
+    return buf.raw[:n.value]
+
+
+def rc_profiles_generate(ctx, vol, params, out):
+    p = _params(params)
+    _check(lib().rc_profiles_generate(ctx, vol, C.byref(p), _ptr(out)), ctx, "rc_profiles_generate")
+
+
+def rc_proposal_features(ctx, vol, params, out):
+    p = _params(params)
+    _check(lib().rc_proposal_features(ctx, vol, C.byref(p), _ptr(out)), ctx, "rc_proposal_features")
+
+
+def rc_proposal_forward(ctx, features, n, out):
+    _check(lib().rc_proposal_forward(ctx, _ptr(features), int(n), _ptr(out)), ctx, "rc_proposal_forward")
+
+
+def rc_proposal_grad(ctx, features, targets, n, grad, loss=None):
+    _check(lib().rc_proposal_grad(ctx, _ptr(features), _ptr(targets), int(n), _ptr(grad), _ptr(loss)), ctx,
+           "rc_proposal_grad")
+
+
+def rc_proposal_train_step(ctx, features, targets, n, lr, loss=None):
+    _check(lib().rc_proposal_train_step(ctx, _ptr(features), _ptr(targets), int(n), float(lr), _ptr(loss)), ctx,
+           "rc_proposal_train_step")
+
+
+def rc_render_importance(ctx, vol, params, pdf, that, nimp, eps, out, fallback=None, stats=False):
+    p = _params(params)
+    st = rc_stats() if stats else None
+    _check(lib().rc_render_importance(ctx, vol, C.byref(p), _ptr(pdf), _ptr(that), int(nimp), float(eps), _ptr(out),
+                                      _ptr(fallback), C.byref(st) if st is not None else None), ctx,
+           "rc_render_importance")
+    return _stats_dict(st)
+
+
+def rc_render_proposal(ctx, vol, params, nimp, eps, out, fallback=None, stats=False):
+    p = _params(params)
+    st = rc_stats() if stats else None
+    _check(lib().rc_render_proposal(ctx, vol, C.byref(p), int(nimp), float(eps), _ptr(out), _ptr(fallback),
+                                    C.byref(st) if st is not None else None), ctx, "rc_render_proposal")
+    return _stats_dict(st)

@@ -34,6 +34,14 @@ struct rc_context {
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     int nvolumes = 0;
+    // learned proposal: FP32 master parameters, Adam moments, packed BF16
+    // fragments, gradient and per-block partials
+    bool net_loaded = false;
+    float *d_param = nullptr, *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr;
+    uint2 *d_frag = nullptr;
+    float *d_partial = nullptr, *d_loss_partial = nullptr;
+    int partial_blocks = 0;
+    long long adam_step = 0;
 };
 
 struct rc_volume {
@@ -120,8 +128,8 @@ rc_status rc_context_create(int device, void *cuda_stream, rc_context **out) {
     if (!ctx) return fail(nullptr, RC_ERR_OOM, "rc_context_create: host allocation");
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
-    if (cudaMalloc(&ctx->d_stats, 4 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_stats, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMalloc(&ctx->d_stats, 5 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_stats, 5 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaFree(ctx->d_stats);
         delete ctx;
         return fail(nullptr, RC_ERR_OOM, "rc_context_create: statistics buffers");
@@ -146,6 +154,13 @@ rc_status rc_context_destroy(rc_context *ctx) {
     cudaFree(ctx->d_stats);
     cudaFreeHost(ctx->h_stats);
     cudaFree(ctx->d_scratch);
+    cudaFree(ctx->d_param);
+    cudaFree(ctx->d_m);
+    cudaFree(ctx->d_v);
+    cudaFree(ctx->d_grad);
+    cudaFree(ctx->d_frag);
+    cudaFree(ctx->d_partial);
+    cudaFree(ctx->d_loss_partial);
     delete ctx;
     return RC_OK;
 }
@@ -423,6 +438,20 @@ static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v) {
     return RC_OK;
 }
 
+// Copies the device counters into *stats (synchronises the stream). The
+// importance kernels count fallback rays in the first slot.
+static rc_status read_stats(rc_context *ctx, rc_stats *stats, bool importance) {
+    RC_CUDA(ctx, cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    stats->dense_samples = importance ? 0 : ctx->h_stats[0];
+    stats->evaluated_samples = ctx->h_stats[1];
+    stats->rays_hit = ctx->h_stats[2];
+    stats->rays_total = ctx->h_stats[3];
+    stats->fallback_rays = importance ? ctx->h_stats[0] : 0;
+    return RC_OK;
+}
+
 static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render_params *p, float *out) {
     MarchArgs a;
     a.vol = vol_dev(v);
@@ -461,19 +490,11 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
     }
     MarchArgs a = march_args(ctx, v, p, out_rgba);
     if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
         a.stats = ctx->d_stats;
     }
     RC_CUDA(ctx, launch_march(a, ctx->stream));
-    if (stats) {
-        RC_CUDA(ctx, cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, 4 * sizeof(unsigned long long),
-                                     cudaMemcpyDeviceToHost, ctx->stream));
-        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        stats->dense_samples = ctx->h_stats[0];
-        stats->evaluated_samples = ctx->h_stats[1];
-        stats->rays_hit = ctx->h_stats[2];
-        stats->rays_total = ctx->h_stats[3];
-    }
+    if (stats) return read_stats(ctx, stats, false);
     return RC_OK;
 }
 
@@ -587,6 +608,243 @@ rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ) 
     if (st != RC_OK) return st;
     RC_CUDA(ctx, cudaMemcpyAsync(occ, v->d_occ, v->nbricks, cudaMemcpyDeviceToDevice, ctx->stream));
     return RC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned proposal
+// ---------------------------------------------------------------------------
+struct BlobHeader {
+    char magic[8];
+    uint32_t version, n_feat, n_hidden, n_layers, n_out, n_out_used, n_params, has_adam;
+    uint64_t adam_step;
+};
+static_assert(sizeof(BlobHeader) == 48, "blob header layout");
+
+static rc_status net_alloc(rc_context *ctx) {
+    if (ctx->d_param) return RC_OK;
+    float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+    uint2 *f = nullptr;
+    if (cudaMalloc(&p, kParams * sizeof(float)) != cudaSuccess || cudaMalloc(&m, kParams * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&v, kParams * sizeof(float)) != cudaSuccess || cudaMalloc(&g, kParams * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&f, kFragTotal * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        cudaFree(m);
+        cudaFree(v);
+        cudaFree(g);
+        cudaFree(f);
+        return fail(ctx, RC_ERR_OOM, "proposal: device allocation");
+    }
+    ctx->d_param = p;
+    ctx->d_m = m;
+    ctx->d_v = v;
+    ctx->d_grad = g;
+    ctx->d_frag = f;
+    return RC_OK;
+}
+
+rc_status rc_proposal_load(rc_context *ctx, const void *blob, size_t bytes) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_proposal_load: ctx is NULL");
+    if (!blob) return fail(ctx, RC_ERR_INVALID_ARG, "rc_proposal_load: blob is NULL");
+    if (bytes < sizeof(BlobHeader)) return fail(ctx, RC_ERR_FORMAT, "rc_proposal_load: %zu bytes, header is 48", bytes);
+    BlobHeader h;
+    memcpy(&h, blob, sizeof h);
+    if (memcmp(h.magic, "RCPROP01", 8) != 0 || h.version != 1)
+        return fail(ctx, RC_ERR_FORMAT, "rc_proposal_load: bad magic or version");
+    if (h.n_feat != (uint32_t)kFeat || h.n_hidden != (uint32_t)kHid || h.n_layers != 3 || h.n_out != (uint32_t)kOut ||
+        h.n_out_used != (uint32_t)kOutUsed || h.n_params != (uint32_t)kParams || h.has_adam > 1)
+        return fail(ctx, RC_ERR_FORMAT, "rc_proposal_load: dimensions do not match this library");
+    size_t need = sizeof h + (size_t)kParams * sizeof(float) * (h.has_adam ? 3 : 1);
+    if (bytes != need) return fail(ctx, RC_ERR_FORMAT, "rc_proposal_load: %zu bytes, expected %zu", bytes, need);
+    const float *vals = reinterpret_cast<const float *>(reinterpret_cast<const char *>(blob) + sizeof h);
+    for (size_t i = 0; i < (size_t)kParams * (h.has_adam ? 3 : 1); i++)
+        if (!isfinite(vals[i])) return fail(ctx, RC_ERR_FORMAT, "rc_proposal_load: non-finite value at %zu", i);
+    DeviceScope ds(ctx->device);
+    rc_status st = net_alloc(ctx);
+    if (st != RC_OK) return st;
+    RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_param, vals, kParams * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    if (h.has_adam) {
+        RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_m, vals + kParams, kParams * sizeof(float), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+        RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_v, vals + 2 * kParams, kParams * sizeof(float), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    } else {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_m, 0, kParams * sizeof(float), ctx->stream));
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_v, 0, kParams * sizeof(float), ctx->stream));
+    }
+    RC_CUDA(ctx, launch_pack(ctx->d_param, ctx->d_frag, ctx->stream));
+    RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the host blob may be freed at once
+    ctx->adam_step = h.has_adam ? (long long)h.adam_step : 0;
+    ctx->net_loaded = true;
+    return RC_OK;
+}
+
+rc_status rc_proposal_save(rc_context *ctx, void *blob, size_t capacity, size_t *bytes_out) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_proposal_save: ctx is NULL");
+    const size_t need = sizeof(BlobHeader) + (size_t)kParams * sizeof(float) * 3;
+    if (bytes_out) *bytes_out = need;
+    if (!blob) return RC_OK;
+    if (!ctx->net_loaded) return fail(ctx, RC_ERR_STATE, "rc_proposal_save: no network loaded");
+    if (capacity < need) return fail(ctx, RC_ERR_INVALID_ARG, "rc_proposal_save: capacity %zu < %zu", capacity, need);
+    BlobHeader h;
+    memcpy(h.magic, "RCPROP01", 8);
+    h.version = 1;
+    h.n_feat = kFeat;
+    h.n_hidden = kHid;
+    h.n_layers = 3;
+    h.n_out = kOut;
+    h.n_out_used = kOutUsed;
+    h.n_params = kParams;
+    h.has_adam = 1;
+    h.adam_step = (uint64_t)ctx->adam_step;
+    DeviceScope ds(ctx->device);
+    char *out = reinterpret_cast<char *>(blob);
+    memcpy(out, &h, sizeof h);
+    float *vals = reinterpret_cast<float *>(out + sizeof h);
+    RC_CUDA(ctx, cudaMemcpyAsync(vals, ctx->d_param, kParams * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    RC_CUDA(ctx, cudaMemcpyAsync(vals + kParams, ctx->d_m, kParams * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    RC_CUDA(ctx, cudaMemcpyAsync(vals + 2 * kParams, ctx->d_v, kParams * sizeof(float), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RC_OK;
+}
+
+rc_status rc_profiles_generate(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, float *out) {
+    rc_status st = check_render(ctx, vol, p, out, "rc_profiles_generate");
+    if (st != RC_OK) return st;
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    if (p->skip) {
+        st = ensure_occupancy(ctx, v);
+        if (st != RC_OK) return st;
+    }
+    MarchArgs a = march_args(ctx, v, p, nullptr);
+    RC_CUDA(ctx, launch_profiles(a, out, ctx->stream));
+    return RC_OK;
+}
+
+rc_status rc_proposal_features(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, float *out) {
+    rc_status st = check_render(ctx, vol, p, out, "rc_proposal_features");
+    if (st != RC_OK) return st;
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    st = ensure_occupancy(ctx, v);
+    if (st != RC_OK) return st;
+    MarchArgs a = march_args(ctx, v, p, nullptr);
+    RC_CUDA(ctx, launch_features(a, out, ctx->stream));
+    return RC_OK;
+}
+
+static rc_status check_net(rc_context *ctx, const void *a, const void *b, int64_t n, const char *who) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
+    if (!a || !b) return fail(ctx, RC_ERR_INVALID_ARG, "%s: NULL buffer", who);
+    if (n < 1 || n > (1ll << 31)) return fail(ctx, RC_ERR_INVALID_ARG, "%s: n = %lld", who, (long long)n);
+    if (!ctx->net_loaded) return fail(ctx, RC_ERR_STATE, "%s: no network (call rc_proposal_load)", who);
+    return RC_OK;
+}
+
+rc_status rc_proposal_forward(rc_context *ctx, const float *features, int64_t n, float *out) {
+    rc_status st = check_net(ctx, features, out, n, "rc_proposal_forward");
+    if (st != RC_OK) return st;
+    DeviceScope ds(ctx->device);
+    RC_CUDA(ctx, launch_net_forward(NetDev{ctx->d_frag, ctx->d_param}, features, n, out, ctx->stream));
+    return RC_OK;
+}
+
+static rc_status net_grad(rc_context *ctx, const float *features, const float *targets, int64_t n, float *grad,
+                          float *loss) {
+    const int grid = (int)(n / 32 + 1 < 152 ? n / 32 + 1 : 152);
+    if (ctx->partial_blocks < grid) {
+        float *pp = nullptr, *lp = nullptr;
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (cudaMalloc(&pp, (size_t)152 * kParams * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&lp, 152 * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(pp);
+            return fail(ctx, RC_ERR_OOM, "proposal: gradient partials");
+        }
+        cudaFree(ctx->d_partial);
+        cudaFree(ctx->d_loss_partial);
+        ctx->d_partial = pp;
+        ctx->d_loss_partial = lp;
+        ctx->partial_blocks = 152;
+    }
+    TrainArgs a;
+    a.feat = features;
+    a.target = targets;
+    a.n = n;
+    a.params = ctx->d_param;
+    a.partial = ctx->d_partial;
+    a.loss_partial = ctx->d_loss_partial;
+    a.inv_n = (float)(1.0 / (double)n);
+    RC_CUDA(ctx, launch_train_grad(a, grid, grad, loss, ctx->stream));
+    return RC_OK;
+}
+
+rc_status rc_proposal_grad(rc_context *ctx, const float *features, const float *targets, int64_t n, float *grad,
+                           float *loss) {
+    rc_status st = check_net(ctx, features, targets, n, "rc_proposal_grad");
+    if (st != RC_OK) return st;
+    if (!grad) return fail(ctx, RC_ERR_INVALID_ARG, "rc_proposal_grad: grad is NULL");
+    DeviceScope ds(ctx->device);
+    return net_grad(ctx, features, targets, n, grad, loss);
+}
+
+rc_status rc_proposal_train_step(rc_context *ctx, const float *features, const float *targets, int64_t n, float lr,
+                                 float *loss) {
+    rc_status st = check_net(ctx, features, targets, n, "rc_proposal_train_step");
+    if (st != RC_OK) return st;
+    if (!(lr > 0.0f) || !isfinite(lr)) return fail(ctx, RC_ERR_INVALID_ARG, "rc_proposal_train_step: lr %g", (double)lr);
+    DeviceScope ds(ctx->device);
+    st = net_grad(ctx, features, targets, n, ctx->d_grad, loss);
+    if (st != RC_OK) return st;
+    ctx->adam_step++;
+    RC_CUDA(ctx, launch_adam(ctx->d_param, ctx->d_m, ctx->d_v, ctx->d_grad, ctx->adam_step, lr, ctx->stream));
+    RC_CUDA(ctx, launch_pack(ctx->d_param, ctx->d_frag, ctx->stream));
+    return RC_OK;
+}
+
+static rc_status importance_common(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const float *pdf,
+                                   const float *that, int nimp, float eps, float *out, uint8_t *fallback,
+                                   rc_stats *stats, const char *who) {
+    rc_status st = check_render(ctx, vol, p, out, who);
+    if (st != RC_OK) return st;
+    if (p->func != RC_FUNC_COMPOSITE) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: compositing function only", who);
+    if (nimp < 1 || nimp > 4096) return fail(ctx, RC_ERR_INVALID_ARG, "%s: nimp %d", who, nimp);
+    if (!(eps >= 0.0f)) return fail(ctx, RC_ERR_INVALID_ARG, "%s: eps %g", who, (double)eps);
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    st = ensure_occupancy(ctx, v);
+    if (st != RC_OK) return st;
+    ImportanceArgs a;
+    a.m = march_args(ctx, v, p, out);
+    a.net = NetDev{ctx->d_frag, ctx->d_param};
+    a.pdf = pdf;
+    a.that = that;
+    a.nimp = nimp;
+    a.eps = eps;
+    a.fallback = fallback;
+    if (stats) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        a.m.stats = ctx->d_stats;
+    }
+    RC_CUDA(ctx, launch_importance(a, ctx->stream));
+    if (stats) return read_stats(ctx, stats, true);
+    return RC_OK;
+}
+
+rc_status rc_render_importance(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const float *pdf,
+                               const float *that, int nimp, float eps, float *out_rgba, uint8_t *fallback,
+                               rc_stats *stats) {
+    if (ctx && (!pdf || !that)) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_importance: pdf / that is NULL");
+    return importance_common(ctx, vol, p, pdf, that, nimp, eps, out_rgba, fallback, stats, "rc_render_importance");
+}
+
+rc_status rc_render_proposal(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, int nimp, float eps,
+                             float *out_rgba, uint8_t *fallback, rc_stats *stats) {
+    if (ctx && !ctx->net_loaded) return fail(ctx, RC_ERR_STATE, "rc_render_proposal: no network loaded");
+    return importance_common(ctx, vol, p, nullptr, nullptr, nimp, eps, out_rgba, fallback, stats,
+                             "rc_render_proposal");
 }
 
 }  // extern "C"

@@ -233,6 +233,38 @@ __device__ __forceinline__ void load_tf(const TFDev &tf, float4 *s_tf) {
         s_tf[e] = tf.fp16 ? half4_to_float4(tf.f16[e]) : tf.f32[e];
 }
 
+// One compositing sample (Sec. 4.1 step 2-3): resample at cell c, classify,
+// correct the opacity to the segment, shade. Returns straight colour and
+// corrected opacity; the caller composites. Shared by every march so that the
+// plain, fallback and importance marches evaluate a sample identically.
+template <int ST, bool SHADE>
+__device__ __forceinline__ float4 eval_sample(const VolDev &vol, const MarchParams &P, const float4 *s_tf, int K,
+                                              const float dir[3], const Cell &c, int rmode, float ratio) {
+    float val, g[3];
+    if (SHADE) val = value_grad<ST>(vol, c, g);
+    else val = trilinear<ST>(vol, c);
+    float4 e = classify(s_tf, K, tf_coord(vol, val, (float)(K - 1)));
+    float ap = correct_alpha(e.w, rmode, ratio);
+    if (SHADE) {
+        float sf, spec;
+        shade_factor(P, vol, g, dir, sf, spec);
+        e.x = fminf(1.0f, __fmaf_rn(e.x, sf, spec));
+        e.y = fminf(1.0f, __fmaf_rn(e.y, sf, spec));
+        e.z = fminf(1.0f, __fmaf_rn(e.z, sf, spec));
+    }
+    e.w = ap;
+    return e;
+}
+
+// Front-to-back compositing of one sample (Eq. 4): C += T a' c, T *= 1 - a'.
+__device__ __forceinline__ void composite_add(const float4 &e, float &C0, float &C1, float &C2, float &T) {
+    float ta = T * e.w;
+    C0 = __fmaf_rn(ta, e.x, C0);
+    C1 = __fmaf_rn(ta, e.y, C1);
+    C2 = __fmaf_rn(ta, e.z, C2);
+    T = T * (1.0f - e.w);
+}
+
 // Jump over a brick the occupancy mask marks empty. Returns the index of the
 // first sample that may lie outside brick(c): the sample m just before the
 // computed exit distance is verified to be in the same brick; since each

@@ -72,6 +72,54 @@ struct AdjointArgs {
     float acc_scale;               // fixed-point units per unit of gradient
 };
 
+// ---- learned proposal ----------------------------------------------------
+constexpr int kBins = 32;                 // opacity PDF bins over [t_near, t_far]
+constexpr int kProfSamples = 512;         // samples of the profile march (16 per bin)
+constexpr int kFeat = 112;                // 6 raw + 72 encoded + 32 occupancy + 2 padding
+constexpr int kHid = 64;
+constexpr int kOut = 40;                  // 32 PDF logits + 1 transmittance logit + 7 padding
+constexpr int kOutUsed = 33;
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kFeat * kHid;
+constexpr int kOffW2 = kOffB1 + kHid;
+constexpr int kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid;
+constexpr int kOffB3 = kOffW3 + kHid * kHid;
+constexpr int kOffW4 = kOffB3 + kHid;
+constexpr int kOffB4 = kOffW4 + kHid * kOut;
+constexpr int kParams = kOffB4 + kOut;    // 18152
+// BF16 B-operand fragments of mma.m16n8k16, per layer [k-tile][n-tile][lane] uint2
+constexpr int kFragL1 = 0;
+constexpr int kFragL2 = kFragL1 + (kFeat / 16) * (kHid / 8) * 32;
+constexpr int kFragL3 = kFragL2 + (kHid / 16) * (kHid / 8) * 32;
+constexpr int kFragL4 = kFragL3 + (kHid / 16) * (kHid / 8) * 32;
+constexpr int kFragTotal = kFragL4 + (kHid / 16) * (kOut / 8) * 32;
+
+struct NetDev {
+    const uint2 *frag;        // packed BF16 weights (kFragTotal)
+    const float *params;      // FP32 master parameters (biases read from here)
+};
+
+struct ImportanceArgs {
+    MarchArgs m;
+    NetDev net;               // fused form: network evaluated in-kernel
+    const float *pdf;         // given-PDF form: H*W*32 (null in the fused form)
+    const float *that;        // given-PDF form: H*W
+    int nimp;                 // importance samples per ray
+    float eps;                // fallback when |T_nimp - T^| > eps
+    uint8_t *fallback;        // per pixel flag (or null)
+};
+
+struct TrainArgs {
+    const float *feat;        // n x 112
+    const float *target;      // n x 33: 32 profile bins + final transmittance
+    long long n;
+    const float *params;      // FP32 master parameters
+    float *partial;           // gridDim x kParams gradient partials
+    float *loss_partial;      // gridDim
+    float inv_n;
+};
+
 // ---- launchers (return the launch error) --------------------------------
 cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, int nbv0, int nbv1,
                             int nbv2, cudaStream_t s);
@@ -82,5 +130,13 @@ cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks
 cudaError_t launch_march(const MarchArgs &a, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjointArgs &a, float *dL_dtf, cudaStream_t s);
 cudaError_t launch_absmax(const float *x, long long n, float *out, cudaStream_t s);
+cudaError_t launch_profiles(const MarchArgs &a, float *out, cudaStream_t s);
+cudaError_t launch_features(const MarchArgs &a, float *out, cudaStream_t s);
+cudaError_t launch_net_forward(const NetDev &net, const float *feat, long long n, float *out, cudaStream_t s);
+cudaError_t launch_importance(const ImportanceArgs &a, cudaStream_t s);
+cudaError_t launch_train_grad(const TrainArgs &a, int grid, float *grad, float *loss, cudaStream_t s);
+cudaError_t launch_adam(float *params, float *m, float *v, const float *grad, long long step, float lr,
+                        cudaStream_t s);
+cudaError_t launch_pack(const float *params, uint2 *frag, cudaStream_t s);
 
 }  // namespace rc

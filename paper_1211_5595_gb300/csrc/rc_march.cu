@@ -41,7 +41,6 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
     Ray R;
     const bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
     const int nsamp = hit ? R.nsamp : 0;
-    const float km1 = (float)(a.tf.K - 1);
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
     int k = 0;
     unsigned evald = 0;
@@ -57,24 +56,8 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
             active = k < nsamp;
             continue;
         }
-        float val, g[3];
-        if (SHADE) val = value_grad<ST>(a.vol, c, g);
-        else val = trilinear<ST>(a.vol, c);
-        float4 e = classify(s_tf, a.tf.K, tf_coord(a.vol, val, km1));
-        float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
-        float r = e.x, gg = e.y, b = e.z;
-        if (SHADE) {
-            float sf, spec;
-            shade_factor(a.p, a.vol, g, R.dir, sf, spec);
-            r = fminf(1.0f, __fmaf_rn(r, sf, spec));
-            gg = fminf(1.0f, __fmaf_rn(gg, sf, spec));
-            b = fminf(1.0f, __fmaf_rn(b, sf, spec));
-        }
-        float ta = T * ap;
-        C0 = __fmaf_rn(ta, r, C0);
-        C1 = __fmaf_rn(ta, gg, C1);
-        C2 = __fmaf_rn(ta, b, C2);
-        T = T * (1.0f - ap);
+        float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, R.dir, c, a.p.rmode, a.p.ratio);
+        composite_add(e, C0, C1, C2, T);
         evald++;
         k++;
         active = k < nsamp && (1.0f - T) < a.p.term;

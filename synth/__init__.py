@@ -292,3 +292,69 @@ def workload_phantom(name, **over):
     w = dict(WORKLOADS[name])
     w.update(over)
     return head_phantom(w["dims"], w["spacing"], w["seed"], tumor_radius_vox=w["tumor_radius_vox"])
+
+
+# --------------------------------------------------------------------------
+# initial parameters of the proposal network (seeded input)
+# --------------------------------------------------------------------------
+PROPOSAL_LAYERS = ((112, 64), (64, 64), (64, 64), (64, 40))
+PROPOSAL_PARAMS = 18152
+
+
+def proposal_init_params(seed, n_feat_used=110, n_out_used=33) -> np.ndarray:
+    """He-uniform weights (bound sqrt(6 / fan_in)) and zero biases, in the
+    parameter order W1, b1, W2, b2, W3, b3, W4, b4 (weights input-major).
+    Padding inputs (features 110, 111) and padding outputs (33..39) get zero
+    weights."""
+    out = []
+    off = 0
+    for li, (k, n) in enumerate(PROPOSAL_LAYERS):
+        fan_in = n_feat_used if li == 0 else k
+        u = uniform01(seed + 7919 * li, np.arange(k * n)).reshape(k, n)
+        w = (2.0 * u - 1.0) * np.sqrt(6.0 / fan_in)
+        if li == 0:
+            w[n_feat_used:, :] = 0.0
+        if li == len(PROPOSAL_LAYERS) - 1:
+            w[:, n_out_used:] = 0.0
+        out.append(w.reshape(-1))
+        out.append(np.zeros(n))
+        off += k * n + n
+    p = np.concatenate(out).astype(np.float32)
+    assert p.size == PROPOSAL_PARAMS
+    return p
+
+
+def proposal_batch(seed, n):
+    """Seeded feature rows and profile targets with the value ranges of real
+    rays (6 coordinates in [0, 1] or [-1, 1], 72 encodings in [-1, 1], 32 0/1
+    occupancy bits, 2 zeros) for unit tests of the network."""
+    u = uniform01(seed, np.arange(n * 78)).reshape(n, 78)
+    f = np.zeros((n, 112))
+    f[:, :3] = u[:, :3]
+    f[:, 3:78] = 2.0 * u[:, 3:78] - 1.0
+    bits = uniform01(seed + 1, np.arange(n * 32)).reshape(n, 32) < 0.6
+    f[:, 78:110] = bits
+    w = uniform01(seed + 2, np.arange(n * 32)).reshape(n, 32) ** 4
+    tot = uniform01(seed + 3, np.arange(n))
+    bins = w / w.sum(axis=1, keepdims=True) * tot[:, None]
+    bins[: max(1, n // 16)] = 0.0                          # some rays without opacity
+    tgt = np.concatenate([bins, (1.0 - bins.sum(axis=1))[:, None]], axis=1)
+    return f.astype(np.float32), tgt.astype(np.float32)
+
+
+def _proposal_vol(seed):
+    return proposal_phantom(seed).vol
+
+
+def proposal_phantoms(seeds, workers=None):
+    """proposal_phantom(seed).vol for every seed, generated in a pool of
+    spawned processes (safe to call after CUDA has been initialised)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    seeds = list(seeds)
+    workers = workers or max(1, min(len(seeds), (os.cpu_count() or 2) - 1, 16))
+    if workers == 1 or len(seeds) == 1:
+        return [_proposal_vol(s) for s in seeds]
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_proposal_vol, seeds))

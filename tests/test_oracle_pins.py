@@ -457,40 +457,71 @@ def test_profiles_constant_volume(orc):
     assert bins[0].sum() == pytest.approx(1.0 - tfin[0], abs=1e-12)
 
 
-@pytest.mark.parametrize("pdf_kind", ["uniform", "peaked", "random"])
-def test_importance_constant_volume_is_exact(orc, pdf_kind):
-    """The segments of the importance samples tile [t_near, t_far], so in a
-    constant medium the composite is the exact 1 - (1 - a)^(L / ds_ref) for any
-    PDF (Eq. 3 over the whole chord)."""
+@pytest.mark.parametrize("pdf_kind", ["uniform", "one_bin", "two_bins"])
+@pytest.mark.parametrize("nimp", [64, 100, 7])
+def test_importance_constant_volume_closed_form(orc, pdf_kind, nimp):
+    """In a constant medium (every brick occupied: the range starts at t_near)
+    the nimp equal segments tile [t_near, t_b], so the composite is
+    1 - (1 - a)^((t_b - t_near) / ds_ref) for any nimp (Eq. 3); the range ends
+    one bin past saturation. Uniform PDF: the running sum reaches 1 - 1/64 only
+    at bin 31, t_b = t_far. All mass on bin 7: t_b is the end of bin 8 (9 L/32).
+    Mass 0.3 on bin 3, 0.7 on bin 20: 22 L/32."""
     V0, a = 2000, 0.03
     vol = np.full((8, 8, 60), V0, dtype=np.uint16)
     tf = identity_tf({V0: (0.2, 0.4, 0.8, a)})
     sc = orc.Scene(vol, (1, 1, 1), tf, axis_camera(60, 3.0, 3.0), term=1.0)
     g = orc.ray_geometry(sc, 0, 0)
     L = g["tf"] - g["tn"]
+    pdf = np.zeros(32)
     if pdf_kind == "uniform":
-        pdf = np.full(32, 1 / 32)
-    elif pdf_kind == "peaked":
-        pdf = np.zeros(32); pdf[7] = 1.0
+        pdf[:], cover = 1 / 32, L
+    elif pdf_kind == "one_bin":
+        pdf[7], cover = 1.0, 9 * L / 32
     else:
-        pdf = np.random.default_rng(4).random(32); pdf /= pdf.sum()
-    lam = 0.0 if pdf_kind == "peaked" else 0.05
-    rgba, tfin, ns = orc.importance(sc, pdf[None, :], lam=lam, nimp=64)
-    expect = 1.0 - (1.0 - float(np.float32(a))) ** L
-    assert ns[0] == 64
-    assert rgba[0, 3] == pytest.approx(expect, abs=1e-5)
+        pdf[3], pdf[20], cover = 0.3, 0.7, 22 * L / 32
+    rgba, tfin, ns = orc.importance(sc, pdf[None, :], nimp=nimp)
+    expect = 1.0 - (1.0 - float(np.float32(a))) ** cover
+    assert ns[0] == nimp
+    assert rgba[0, 3] == pytest.approx(expect, abs=2e-6)
     np.testing.assert_allclose(rgba[0, :3], np.float32([0.2, 0.4, 0.8]) * rgba[0, 3], atol=1e-12)
 
 
+def test_importance_range_starts_at_first_occupied_bin(orc):
+    """Tissue in two slabs along the ray; a PDF that saturates early ends the
+    range right after the near slab, so the far slab is not sampled: removing
+    it changes nothing. A PDF that saturates only at the end samples both. The
+    empty stretch before the near slab is never sampled."""
+    vol = np.zeros((8, 8, 64), dtype=np.uint16)
+    vol[:, :, 40:48] = 2000                                  # near slab (the ray runs from x = 63 down)
+    vol[:, :, :8] = 2000                                     # far slab
+    near_only = vol.copy()
+    near_only[:, :, :8] = 0
+    tf = identity_tf({2000: (1.0, 1.0, 1.0, 0.1)})
+    cam = axis_camera(64, 3.0, 3.0)
+    early = np.zeros(32); early[11] = 1.0                   # range ends after bin 12 (x about 38)
+    late = np.full(32, 1 / 32)
+    a, _, _ = orc.importance(orc.Scene(vol, (1, 1, 1), tf, cam, term=1.0), early[None, :])
+    b, _, _ = orc.importance(orc.Scene(near_only, (1, 1, 1), tf, cam, term=1.0), early[None, :])
+    c, _, _ = orc.importance(orc.Scene(vol, (1, 1, 1), tf, cam, term=1.0), late[None, :])
+    assert a[0, 3] > 0.3 and a[0, 3] == b[0, 3]
+    assert c[0, 3] > a[0, 3] + 0.1
+    # 8 voxels of opacity 0.1 per voxel: the composite approaches 1 - 0.9^8
+    assert a[0, 3] == pytest.approx(1 - 0.9 ** 8, abs=0.06)
+
+
 def test_importance_uniform_pdf_is_midpoint_march(orc):
-    """A uniform PDF puts sample j at the centre of the j-th of nimp equal
-    segments: the same samples as a 64-segment profile march."""
-    ph = synth.head_phantom((40, 40, 30), (1, 1, 1), seed=5, tumor_radius_vox=4)
+    """In a medium with every brick occupied, a uniform PDF puts sample j at
+    the centre of the j-th of nimp equal segments of the chord: the same
+    samples as the 512-segment profile march."""
+    rng = np.random.default_rng(9)
+    vol = rng.integers(1000, 3200, size=(30, 40, 40)).astype(np.uint16)
     tf = synth.tf_table(256)
-    cam = synth.orbit_camera(ph.dims, ph.spacing, 0.0, width=8, height=8)
-    sc = orc.Scene(ph.vol, ph.spacing, tf, cam, term=1.0)
+    cam = synth.orbit_camera((40, 40, 30), (1, 1, 1), 0.0, width=8, height=8)
+    sc = orc.Scene(vol, (1, 1, 1), tf, cam, term=1.0)
     pdf = np.full((64, 32), 1 / 32)
-    rgba, tfin, ns = orc.importance(sc, pdf, lam=0.05, nimp=512)
+    rgba, tfin, ns = orc.importance(sc, pdf, nimp=512)
     bins, tprof = orc.profiles(sc)
-    np.testing.assert_allclose(tfin, tprof, atol=2e-6)
-    np.testing.assert_allclose(rgba[:, 3], bins.sum(axis=1), atol=2e-6)
+    hit = ns > 0
+    assert hit.sum() > 10
+    np.testing.assert_allclose(tfin, tprof, atol=1e-12)
+    np.testing.assert_allclose(rgba[:, 3], bins.sum(axis=1), atol=1e-12)
