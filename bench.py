@@ -163,6 +163,65 @@ def cpu_oracle_sample(ph, tf, w, cams, budget_s, pixels_per_view=None):
     return samples / dt / 1e9, cores, f"{what} {views} view(s), {samples} samples, {dt:.1f} s"
 
 
+def proposal_form(rc, ctx, vol, ph, w, cams, P, outs, frame_ms, flush, stream, n_train):
+    """Learned proposal on the bench workload: the network is trained on
+    n_train seeded phantoms (never the bench phantom), then every view is
+    rendered with 64 proposal samples per ray at several fallback thresholds
+    and compared with the FP32 plain march (PSNR, time)."""
+    import torch
+    from paper_1211_5595_gb300 import proposal
+    wp = synth.WORKLOADS["proposal_256x256x180"]
+    t0 = time.perf_counter()
+    vols = synth.proposal_phantoms(wp["train_seeds"][:n_train])
+    train_vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, rc.RC_STORE_F32)
+    rc.rc_proposal_load(ctx, rc.pack_proposal_blob(synth.proposal_init_params(61)))
+    tcams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=512, height=512) for az in wp["azimuths"][::3]]
+    feats, tgts = [], []
+    for i, v in enumerate(vols):
+        rc.rc_volume_upload(ctx, train_vol, v)
+        f, t = proposal.collect_rays(ctx, train_vol, tcams, P, 4096, seed=i)
+        feats.append(f)
+        tgts.append(t)
+    rc.rc_volume_destroy(ctx, train_vol)
+    F, T = torch.cat(feats), torch.cat(tgts)
+    curve = proposal.train(ctx, F, T, epochs=30, batch=8192, lr=3e-3, seed=0)
+    train_s = time.perf_counter() - t0
+    del F, T, feats, tgts
+    ref = outs
+    img = torch.empty_like(outs[0])
+    plain_ms = statistics.median(frame_ms)
+    sweep = []
+    for eps in (2.0, 0.02, 0.005, 0.0):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cams]
+        psnrs, fb, hit = [], 0, 0
+        for rep in range(2):
+            for v, cam in enumerate(cams):
+                rc.rc_camera_set(ctx, cam)
+                ev[v][0].record(stream)
+                rc.rc_render_proposal(ctx, vol, P, 64, eps, img)
+                ev[v][1].record(stream)
+                if rep == 1:
+                    mse = float(((img - ref[v]) ** 2).mean())
+                    psnrs.append(float("inf") if mse == 0 else 10 * np.log10(1.0 / mse))
+            flush.zero_()
+        torch.cuda.synchronize()
+        for v, cam in enumerate(cams[:4]):
+            rc.rc_camera_set(ctx, cam)
+            st = rc.rc_render_proposal(ctx, vol, P, 64, eps, img, stats=True)
+            fb += st["fallback_rays"]
+            hit += st["rays_hit"]
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        sweep.append({"eps": eps, "ms_per_frame_median": ms, "speedup_vs_f32": plain_ms / ms,
+                      "psnr_db_min": min(psnrs), "psnr_db_mean": float(np.mean([p for p in psnrs if np.isfinite(p)]))
+                      if any(np.isfinite(p) for p in psnrs) else float("inf"),
+                      "fallback_rate": fb / max(1, hit)})
+    ok = [r for r in sweep if r["psnr_db_min"] >= 45.0]
+    best = max(ok, key=lambda r: r["speedup_vs_f32"]) if ok else None
+    return {"nimp": 64, "train_phantoms": n_train, "train_s": train_s, "loss_first_last": [curve[0], curve[-1]], "sweep": sweep,
+            "speedup_at_psnr45": best["speedup_vs_f32"] if best else None,
+            "eps_at_psnr45": best["eps"] if best else None}
+
+
 def run_reference(args, w, world, rank):
     """The oracle as the reference arm (host cores, bounded sample per step)."""
     if rank != 0:
@@ -211,6 +270,8 @@ def main():
     ap.add_argument("--views", type=int, default=0, help="render only the first N orbit views (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / uint16 storage forms")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal form")
+    ap.add_argument("--proposal-phantoms", type=int, default=8, help="training phantoms of the proposal form")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -287,6 +348,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    fp32_imgs = outs.clone()                                # reference images of the other forms
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     frame_ms = [a.elapsed_time(b) for row in kern_ev for a, b in row]
     total_ms = sum(step_ms)
@@ -328,7 +390,7 @@ def main():
     # and raw uint16 volumes with the FP16 table, against the FP32 images
     forms = {}
     if not args.no_forms:
-        ref_imgs = outs.clone()
+        ref_imgs = fp32_imgs
         fp32_frame_ms = statistics.median(frame_ms)
         for name, storage in (("f16", rc.RC_STORE_F16), ("u16", rc.RC_STORE_U16)):
             v2 = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, storage)
@@ -351,6 +413,10 @@ def main():
                            "max_abs_vs_f32": float((outs - ref_imgs).abs().max())}
             rc.rc_volume_destroy(ctx, v2)
         rc.rc_tf_set_device(ctx, tf_dev)
+
+    if not args.no_proposal:
+        forms["proposal"] = proposal_form(rc, ctx, vol, ph, w, cams, P, fp32_imgs, frame_ms, flush, stream,
+                                          args.proposal_phantoms)
 
     hbm_peak, peak_kind = peaks()
     frame_avg_s = statistics.mean(frame_ms) / 1e3

@@ -122,9 +122,10 @@ rc_status rc_context_destroy(rc_context *ctx);
 
 /* Volume of nx x ny x nz voxels (each >= 2) with spacing sx, sy, sz mm (> 0) and
  * valid codes 0..vmax (>= 1; larger codes clamp to vmax) (Sec. 2.1, Sec. 1).
- * The device holds it in 16^3 bricks in the chosen storage, with a min/max
- * grid over cell-bricks (the trilinear cells whose base index lies in
- * 16b..16b+15 per axis, footprint voxels 16b..min(16b+16, N-1)). */
+ * The device holds it in cell-bricks (the trilinear cells whose base index
+ * lies in 16b..16b+15 per axis), each stored with an apron as the 19^3 voxels
+ * 16b-1..16b+17 (clamped to the volume) in the chosen storage, with a min/max
+ * grid over the cell-bricks (footprint voxels 16b..min(16b+16, N-1)). */
 rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz,
                            float sx, float sy, float sz, uint16_t vmax,
                            rc_storage storage, rc_volume **out);
@@ -140,7 +141,8 @@ rc_status rc_volume_brick_dims(const rc_volume *vol, int dims[3]);
 
 /* Transfer function (Sec. 2.6, Sec. 6): n_entries (2..4096) straight RGBA
  * entries in [0, 1], host memory, entry i at code i*vmax/(n_entries-1); a value
- * between entries is the linear interpolation of its two neighbours. fp16 = 1
+ * between entries is the linear interpolation of its two neighbours (table
+ * coordinate u = fl(v * fl((n_entries-1) / vmax)), see rc_skip_mask_get). fp16 = 1
  * stores the table as FP16 (the precision form). */
 rc_status rc_tf_set(rc_context *ctx, const float *rgba, int n_entries, int fp16);
 /* Same from device memory (asynchronous device-to-device copy). Values are not
@@ -195,7 +197,9 @@ rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *vol, uint16_t *mn,
  * caller device memory (one byte per cell-brick, 1 = may hold non-zero
  * opacity). A brick is empty when every table entry a sample inside it can
  * touch, floor(u(min)) .. min(floor(u(max)) + 1, K - 1), has opacity 0, with
- * u(v) = v (K-1) / vmax (raw codes) or fp16(v / vmax) (K-1) (F16 storage). */
+ * the table coordinate u(v) = fl(v * fl((K-1) / vmax)) of a raw code v, or
+ * u(v) = fl(h * (K-1)) with h = fp16(fl(v / vmax)) for F16 storage (FP32
+ * operations rounded once). */
 rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ);
 
 /* ---- learned sampling proposal -------------------------------------------

@@ -1016,22 +1016,26 @@ void orc_brick_minmax(const orc_volume *vol, uint16_t *mn, uint16_t *mx) {
 
 /* A brick is occupied unless every table entry a sample inside it can touch
  * has zero opacity. For values in [mn, mx] the lerp touches entries
- * lo = floor(u(mn)) .. hi = min(floor(u(mx)) + 1, K - 1). Raw values:
- * u(v) = v (K-1) / vmax, floored exactly in integers. FP16-normalised values:
- * u(v) = h(v) (K-1) with h(v) the FP16 rounding of the FP32 quotient v / vmax. */
+ * lo = floor(u(mn)) .. hi = min(floor(u(mx)) + 1, K - 1), with the table
+ * coordinate of the written FP32 specification u(v) = fl(v * c),
+ * c = fl((K - 1) / full scale): raw codes v with full scale vmax; FP16-
+ * normalised values v = h(code), the FP16 rounding of the FP32 quotient
+ * code / vmax, with full scale 1. u is monotone in v, so every sample inside
+ * the brick has its coordinate in [u(mn), u(mx)]. */
 void orc_occupancy(const orc_volume *vol, const orc_tf *tf, const uint16_t *mn,
                    const uint16_t *mx, uint8_t *occ) {
     int nb = ((vol->nx - 1 + 15) / 16) * ((vol->ny - 1 + 15) / 16) * ((vol->nz - 1 + 15) / 16);
     int K = tf->K;
+    float c = (float)(K - 1) / (vol->value_mode ? 1.0f : (float)vol->vmax);
     for (int b = 0; b < nb; b++) {
         long lo, hi;
+        float vmn = (float)mn[b], vmx = (float)mx[b];
         if (vol->value_mode) {
-            lo = (long)floor(half_round((float)mn[b] / (float)vol->vmax) * (double)(K - 1));
-            hi = (long)floor(half_round((float)mx[b] / (float)vol->vmax) * (double)(K - 1)) + 1;
-        } else {
-            lo = ((long)mn[b] * (K - 1)) / vol->vmax;
-            hi = ((long)mx[b] * (K - 1)) / vol->vmax + 1;
+            vmn = (float)half_round(vmn / (float)vol->vmax);
+            vmx = (float)half_round(vmx / (float)vol->vmax);
         }
+        lo = (long)floorf(vmn * c);
+        hi = (long)floorf(vmx * c) + 1;
         if (hi > K - 1) hi = K - 1;
         if (lo > K - 1) lo = K - 1;
         int any = 0;

@@ -61,7 +61,6 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
     float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (hit) g = A.dimg[(size_t)y * a.cam.W + x];
     if (hit && (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f)) {
-        const float km1 = (float)(K - 1);
         // pass 1: forward
         float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
         int n = 0;
@@ -72,7 +71,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
             cell_of(a.vol, p, c);
             if (SHADE) val = value_grad<ST>(a.vol, c, gr);
             else val = trilinear<ST>(a.vol, c);
-            float4 e = classify(s_tf, K, tf_coord(a.vol, val, km1));
+            float4 e = classify(s_tf, K, tf_coord(val, a.tf.ucoef));
             float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
             float r = e.x, gg = e.y, b = e.z;
             if (SHADE) {
@@ -103,7 +102,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
             else val = trilinear<ST>(a.vol, c);
             int i;
             float w;
-            float4 e = classify(s_tf, K, tf_coord(a.vol, val, km1), &i, &w);
+            float4 e = classify(s_tf, K, tf_coord(val, a.tf.ucoef), &i, &w);
             float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
             float r = e.x, gg = e.y, b = e.z;
             float d0 = 1.0f, d1 = 1.0f, d2 = 1.0f;

@@ -50,8 +50,7 @@ struct rc_volume {
     float s[3] = {0, 0, 0};
     int vmax = 0;
     rc_storage storage = RC_STORE_F32;
-    int nbv[3] = {0, 0, 0};      // storage bricks per axis
-    int cb[3] = {0, 0, 0};       // cell-bricks per axis
+    int cb[3] = {0, 0, 0};       // cell-bricks per axis (each stored as a 19^3 apron brick)
     int nbricks = 0;             // cell-bricks
     void *d_data = nullptr;
     uint16_t *d_stage = nullptr;
@@ -188,10 +187,10 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
     if (vmax < 1) return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_create: vmax must be >= 1");
     if (storage != RC_STORE_F32 && storage != RC_STORE_F16 && storage != RC_STORE_U16)
         return fail(ctx, RC_ERR_INVALID_ARG, "rc_volume_create: storage %d", (int)storage);
-    int nbv[3] = {(nx + 15) / 16, (ny + 15) / 16, (nz + 15) / 16};
-    long long padded = (long long)nbv[0] * nbv[1] * nbv[2] * kBrickVox;
+    const int cbx = (nx - 1 + 15) / 16, cby = (ny - 1 + 15) / 16, cbz = (nz - 1 + 15) / 16;
+    long long padded = (long long)cbx * cby * cbz * kApronVox;
     if (padded >= (1ll << 31))
-        return fail(ctx, RC_ERR_UNSUPPORTED, "rc_volume_create: %lld padded voxels (limit 2^31)", padded);
+        return fail(ctx, RC_ERR_UNSUPPORTED, "rc_volume_create: %lld stored voxels (limit 2^31)", padded);
     DeviceScope ds(ctx->device);
     rc_volume *v = new (std::nothrow) rc_volume();
     if (!v) return fail(ctx, RC_ERR_OOM, "rc_volume_create: host allocation");
@@ -200,10 +199,7 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
     v->s[0] = sx; v->s[1] = sy; v->s[2] = sz;
     v->vmax = vmax;
     v->storage = storage;
-    for (int a = 0; a < 3; a++) {
-        v->nbv[a] = nbv[a];
-        v->cb[a] = (v->n[a] - 1 + 15) / 16;
-    }
+    for (int a = 0; a < 3; a++) v->cb[a] = (v->n[a] - 1 + 15) / 16;
     v->nbricks = v->cb[0] * v->cb[1] * v->cb[2];
     size_t esz = storage == RC_STORE_F32 ? 4 : 2;
     size_t nvox = (size_t)nx * ny * nz;
@@ -233,8 +229,6 @@ static VolDev vol_dev(const rc_volume *v) {
         d.s[a] = v->s[a];
         d.inv2s[a] = 0.5f / v->s[a];
     }
-    d.sy = (unsigned)v->nbv[0] * kBrickVox;
-    d.sz = (unsigned)v->nbv[0] * v->nbv[1] * kBrickVox;
     d.smin = smin;
     d.vmax = v->vmax;
     d.vscale = v->storage == RC_STORE_F16 ? 1.0f : (float)v->vmax;
@@ -253,7 +247,7 @@ rc_status rc_volume_upload(rc_volume *v, const uint16_t *src, size_t n_voxels, i
     RC_CUDA(ctx, cudaMemcpyAsync(v->d_stage, src, nvox * sizeof(uint16_t),
                                  src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     VolDev d = vol_dev(v);
-    RC_CUDA(ctx, launch_relayout(v->d_stage, d, v->d_data, v->nbv[0], v->nbv[1], v->nbv[2], ctx->stream));
+    RC_CUDA(ctx, launch_relayout(v->d_stage, d, v->d_data, ctx->stream));
     RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, v->d_mn, v->d_mx, ctx->stream));
     v->uploaded = true;
     v->data_version++;
@@ -428,9 +422,15 @@ static rc_status check_render(rc_context *ctx, const rc_volume *v, const rc_rend
     return RC_OK;
 }
 
+// The table with its coordinate coefficient fl((K-1) / vscale) for volume v.
+static TFDev tf_dev(const rc_context *ctx, const rc_volume *v) {
+    const float vscale = v->storage == RC_STORE_F16 ? 1.0f : (float)v->vmax;
+    return TFDev{ctx->d_tf32, ctx->d_tf16, ctx->K, ctx->tf_fp16, (float)(ctx->K - 1) / vscale};
+}
+
 static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v) {
     if (v->occ_tf_version == ctx->tf_version && v->occ_data_version == v->data_version) return RC_OK;
-    TFDev tf{ctx->d_tf32, ctx->d_tf16, ctx->K, ctx->tf_fp16};
+    TFDev tf = tf_dev(ctx, v);
     RC_CUDA(ctx, launch_occupancy(v->d_mn, v->d_mx, v->nbricks, v->vmax, v->storage == RC_STORE_F16, tf,
                                   v->d_occ, ctx->stream));
     v->occ_tf_version = ctx->tf_version;
@@ -456,7 +456,7 @@ static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render
     MarchArgs a;
     a.vol = vol_dev(v);
     a.cam = camera_record(ctx->cam, v->s);
-    a.tf = TFDev{ctx->d_tf32, ctx->d_tf16, ctx->K, ctx->tf_fp16};
+    a.tf = tf_dev(ctx, v);
     a.p.step_vox = p->step_vox;
     a.p.term = p->term;
     a.p.shade = p->shade;

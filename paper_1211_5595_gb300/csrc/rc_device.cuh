@@ -95,13 +95,17 @@ __device__ __forceinline__ int brick_of(const VolDev &v, const Cell &c) {
     return ((c.i[2] >> 4) * v.cb[1] + (c.i[1] >> 4)) * v.cb[0] + (c.i[0] >> 4);
 }
 
-// Bricked addressing is separable: offset(x, y, z) = ox(x) + oy(y) + oz(z).
-__device__ __forceinline__ unsigned offx(int x) { return ((unsigned)(x >> 4) << 12) | (unsigned)(x & 15); }
-__device__ __forceinline__ unsigned offy(const VolDev &v, int y) {
-    return (unsigned)(y >> 4) * v.sy + ((unsigned)(y & 15) << 4);
-}
-__device__ __forceinline__ unsigned offz(const VolDev &v, int z) {
-    return (unsigned)(z >> 4) * v.sz + ((unsigned)(z & 15) << 8);
+// Apron bricks: cell-brick b stores the voxels 16b-1 .. 16b+17 of each axis
+// (clamped to the volume, so border voxels are replicated), 19^3 values. The
+// whole 4x4x4 neighbourhood of a cell is then one base address plus constant
+// offsets. Local coordinates of cell base i: (i & 15) + 1.
+constexpr unsigned kDX = 1, kDY = kApron, kDZ = kApron * kApron;
+
+__device__ __forceinline__ unsigned cell_address(const VolDev &v, const Cell &c) {
+    const unsigned b = (unsigned)brick_of(v, c);
+    const unsigned lx = (unsigned)(c.i[0] & 15) + 1, ly = (unsigned)(c.i[1] & 15) + 1,
+                   lz = (unsigned)(c.i[2] & 15) + 1;
+    return b * (unsigned)kApronVox + (lz * kApron + ly) * kApron + lx;
 }
 
 template <int ST>
@@ -117,14 +121,12 @@ __device__ __forceinline__ float lerp(float a, float b, float w) { return __fmaf
 
 template <int ST>
 __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
-    unsigned x0 = offx(c.i[0]), x1 = offx(c.i[0] + 1);
-    unsigned y0 = offy(v, c.i[1]), y1 = offy(v, c.i[1] + 1);
-    unsigned z0 = offz(v, c.i[2]), z1 = offz(v, c.i[2] + 1);
+    const unsigned a = cell_address(v, c);
     float wx = c.w[0], wy = c.w[1], wz = c.w[2];
-    float c00 = lerp(fetch<ST>(v, x0 + y0 + z0), fetch<ST>(v, x1 + y0 + z0), wx);
-    float c10 = lerp(fetch<ST>(v, x0 + y1 + z0), fetch<ST>(v, x1 + y1 + z0), wx);
-    float c01 = lerp(fetch<ST>(v, x0 + y0 + z1), fetch<ST>(v, x1 + y0 + z1), wx);
-    float c11 = lerp(fetch<ST>(v, x0 + y1 + z1), fetch<ST>(v, x1 + y1 + z1), wx);
+    float c00 = lerp(fetch<ST>(v, a), fetch<ST>(v, a + kDX), wx);
+    float c10 = lerp(fetch<ST>(v, a + kDY), fetch<ST>(v, a + kDY + kDX), wx);
+    float c01 = lerp(fetch<ST>(v, a + kDZ), fetch<ST>(v, a + kDZ + kDX), wx);
+    float c11 = lerp(fetch<ST>(v, a + kDZ + kDY), fetch<ST>(v, a + kDZ + kDY + kDX), wx);
     return lerp(lerp(c00, c10, wy), lerp(c01, c11, wy), wz);
 }
 
@@ -132,15 +134,14 @@ __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
 // one index unit per axis, from the 32 distinct voxels around the cell.
 // The samples at p -/+ e_a use the cells with base coordinates
 // {max(i-1, 0), i} and {i+1, min(i+2, N-1)} and the same weight, which equals
-// resampling the clamped positions p -/+ 1.
+// resampling the clamped positions p -/+ 1; the apron's replicated border
+// voxels give the clamped coordinates.
 template <int ST>
 __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, float g[3]) {
-    const int i = c.i[0], j = c.i[1], k = c.i[2];
-    const unsigned X0 = offx(max(i - 1, 0)), X1 = offx(i), X2 = offx(i + 1), X3 = offx(min(i + 2, v.n[0] - 1));
-    const unsigned Y0 = offy(v, max(j - 1, 0)), Y1 = offy(v, j), Y2 = offy(v, j + 1),
-                   Y3 = offy(v, min(j + 2, v.n[1] - 1));
-    const unsigned Z0 = offz(v, max(k - 1, 0)), Z1 = offz(v, k), Z2 = offz(v, k + 1),
-                   Z3 = offz(v, min(k + 2, v.n[2] - 1));
+    const unsigned a = cell_address(v, c);
+    const unsigned X1 = a, X0 = a - kDX, X2 = a + kDX, X3 = a + 2 * kDX;
+    const unsigned Y0 = 0u - kDY, Y1 = 0u, Y2 = kDY, Y3 = 2 * kDY;
+    const unsigned Z0 = 0u - kDZ, Z1 = 0u, Z2 = kDZ, Z3 = 2 * kDZ;
     const float wx = c.w[0], wy = c.w[1], wz = c.w[2];
 #define RC_F(X, Y, Z) fetch<ST>(v, (X) + (Y) + (Z))
 #define RC_LX(XA, XB, Y, Z) lerp(RC_F(XA, Y, Z), RC_F(XB, Y, Z), wx)
@@ -174,12 +175,10 @@ __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, floa
     return val;
 }
 
-// Table coordinate u = v (K-1) / vscale with the FP32 operations rounded once;
-// for integer codes floor(u) is the exact integer floor, and u is monotone in
-// v, which makes the brick occupancy test exact.
-__device__ __forceinline__ float tf_coord(const VolDev &v, float val, float km1) {
-    return v.storage == RC_STORE_F16 ? __fmul_rn(val, km1) : __fdiv_rn(__fmul_rn(val, km1), v.vscale);
-}
+// Table coordinate u = fl(v * fl((K-1) / vscale)): one rounded FP32 multiply,
+// monotone in v. The occupancy mask floors the same function at a brick's
+// integer min and max, which makes skipping exact.
+__device__ __forceinline__ float tf_coord(float val, float ucoef) { return __fmul_rn(val, ucoef); }
 
 // Sec. 2.6: linear interpolation of the two neighbouring table entries.
 __device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, int *i0 = nullptr,
@@ -239,11 +238,12 @@ __device__ __forceinline__ void load_tf(const TFDev &tf, float4 *s_tf) {
 // plain, fallback and importance marches evaluate a sample identically.
 template <int ST, bool SHADE>
 __device__ __forceinline__ float4 eval_sample(const VolDev &vol, const MarchParams &P, const float4 *s_tf, int K,
-                                              const float dir[3], const Cell &c, int rmode, float ratio) {
+                                              float ucoef, const float dir[3], const Cell &c, int rmode,
+                                              float ratio) {
     float val, g[3];
     if (SHADE) val = value_grad<ST>(vol, c, g);
     else val = trilinear<ST>(vol, c);
-    float4 e = classify(s_tf, K, tf_coord(vol, val, (float)(K - 1)));
+    float4 e = classify(s_tf, K, tf_coord(val, ucoef));
     float ap = correct_alpha(e.w, rmode, ratio);
     if (SHADE) {
         float sf, spec;

@@ -9,8 +9,9 @@
 
 namespace rc {
 
-constexpr int kBrick = 16;          // brick edge (voxels / cells)
-constexpr int kBrickVox = 4096;     // 16^3
+constexpr int kBrick = 16;          // cell-brick edge (trilinear cells)
+constexpr int kApron = 19;          // stored brick edge: cells 16b-1 .. 16b+17 (edges replicated)
+constexpr int kApronVox = kApron * kApron * kApron;   // 6859
 
 // Camera record: FP64 look-at basis rounded once to FP32, eye in index space.
 struct CamRec {
@@ -22,15 +23,14 @@ struct CamRec {
 
 // Device view of a bricked volume.
 struct VolDev {
-    const void *data;      // bricked [bz][by][bx][16][16][16], storage type
+    const void *data;      // [bz][by][bx][19][19][19] apron bricks, storage type
     int storage;           // rc_storage
     int n[3];              // voxels per axis
     int cb[3];             // cell-bricks per axis: ceil((n-1)/16)
-    unsigned sy, sz;       // element strides of one brick step in y and z
     float s[3];            // spacing (mm)
     float inv2s[3];        // 0.5 / spacing
     float smin;            // reference step: finest spacing
-    float vscale;          // FP32 code scale of the table coordinate: vmax (raw) or 1
+    float vscale;          // full scale of the stored values: vmax (raw codes) or 1 (FP16)
     float gmin;            // shading falls back to ambient+diffuse below this |gradient|
     int vmax;
 };
@@ -41,6 +41,7 @@ struct TFDev {
     const uint2 *f16;      // 4 halves per entry
     int K;
     int fp16;
+    float ucoef;           // table coordinate per stored value: fl((K-1) / vscale)
 };
 
 struct MarchParams {
@@ -121,8 +122,7 @@ struct TrainArgs {
 };
 
 // ---- launchers (return the launch error) --------------------------------
-cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, int nbv0, int nbv1,
-                            int nbv2, cudaStream_t s);
+cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStream_t s);
 cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax,
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);
 cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax,

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
             active = k < nsamp;
             continue;
         }
-        float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, R.dir, c, a.p.rmode, a.p.ratio);
+        float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, a.p.rmode, a.p.ratio);
         composite_add(e, C0, C1, C2, T);
         evald++;
         k++;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(128) function_kernel(const MarchArgs a) {
         } else if (v >= a.p.iso) {
             found = true;
             if (func == RC_FUNC_THRESHOLD) {
-                float4 e = classify(s_tf, a.tf.K, tf_coord(a.vol, v, (float)(a.tf.K - 1)));
+                float4 e = classify(s_tf, a.tf.K, tf_coord(v, a.tf.ucoef));
                 out = make_float4(e.x, e.y, e.z, 1.0f);
             } else {
                 float ts = k > 0 ? prev_t + (t - prev_t) * ((a.p.iso - prev_v) / (v - prev_v)) : t;

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(128) profiles_kernel(const MarchArgs a, float 
             Cell c;
             cell_of(a.vol, p, c);
             if (a.p.skip && !__ldg(a.occ + brick_of(a.vol, c))) continue;   // opacity exactly 0
-            float4 e = eval_sample<ST, false>(a.vol, a.p, s_tf, a.tf.K, R.dir, c, 3, ratio);
+            float4 e = eval_sample<ST, false>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, 3, ratio);
             acc = __fmaf_rn(T, e.w, acc);
             T = T * (1.0f - e.w);
         }
@@ -273,7 +273,7 @@ __device__ __forceinline__ void plain_ray(const MarchArgs &a, const float4 *s_tf
             k = jump_empty(R, a.vol, c, k);
             continue;
         }
-        float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, R.dir, c, a.p.rmode, a.p.ratio);
+        float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, a.p.rmode, a.p.ratio);
         composite_add(e, C0, C1, C2, T);
         evald++;
         k++;
@@ -332,7 +332,7 @@ __device__ __forceinline__ void importance_ray(const ImportanceArgs &A, const fl
         Cell c;
         cell_of(a.vol, p, c);
         if (a.p.skip && !__ldg(a.occ + brick_of(a.vol, c))) continue;   // opacity exactly 0
-        float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, R.dir, c, 3, ratio);
+        float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, 3, ratio);
         composite_add(e, C0, C1, C2, T);
         evald++;
         if ((1.0f - T) >= a.p.term) break;

@@ -1,46 +1,49 @@
-// Volume preparation: re-layout of the uint16 codes into 16^3 bricks in the
-// chosen storage, the cell-brick min/max grid and the occupancy mask of the
-// current transfer function (Sec. 2.1 volume data, Sec. 2.6 classification).
+// Volume preparation: re-layout of the uint16 codes into apron bricks (19^3
+// voxels per 16^3-cell brick) in the chosen storage, the cell-brick min/max
+// grid and the occupancy mask of the current transfer function (Sec. 2.1
+// volume data, Sec. 2.6 classification).
 #include "rc_device.cuh"
 
 namespace rc {
 
-// One thread per element of the padded bricked array; reads the linear
-// staging copy (x fastest) and converts: F32 keeps the code, F16 stores
-// fp16(code / vmax) (FP32 quotient, then round-to-nearest-even), U16 keeps the
-// code. Codes above vmax clamp; padding outside the volume is 0.
+// One thread per element of the apron-bricked array: cell-brick (bx, by, bz)
+// stores voxels 16b-1 .. 16b+17 per axis, clamped to the volume (border voxels
+// replicated). Reads the linear staging copy (x fastest) and converts: F32
+// keeps the code, F16 stores fp16(code / vmax) (FP32 quotient, then
+// round-to-nearest-even), U16 keeps the code. Codes above vmax clamp.
 template <int ST>
-__global__ void relayout_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax,
-                                int nbv0, int nbv1, void *dst, long long total) {
+__global__ void relayout_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int cb0,
+                                int cb1, void *dst, long long total) {
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= total) return;
-    int local = (int)(e & 4095);
-    long long brick = e >> 12;
-    int bx = (int)(brick % nbv0);
-    long long r = brick / nbv0;
-    int by = (int)(r % nbv1);
-    int bz = (int)(r / nbv1);
-    int x = bx * 16 + (local & 15), y = by * 16 + ((local >> 4) & 15), z = bz * 16 + (local >> 8);
-    int code = 0;
-    if (x < nx && y < ny && z < nz) code = min((int)stage[((size_t)z * ny + y) * nx + x], vmax);
+    const int local = (int)(e % kApronVox);
+    const long long brick = e / kApronVox;
+    const int bx = (int)(brick % cb0);
+    const long long r = brick / cb0;
+    const int by = (int)(r % cb1);
+    const int bz = (int)(r / cb1);
+    const int lx = local % kApron, ly = (local / kApron) % kApron, lz = local / (kApron * kApron);
+    const int x = min(max(bx * kBrick + lx - 1, 0), nx - 1);
+    const int y = min(max(by * kBrick + ly - 1, 0), ny - 1);
+    const int z = min(max(bz * kBrick + lz - 1, 0), nz - 1);
+    const int code = min((int)stage[((size_t)z * ny + y) * nx + x], vmax);
     if (ST == RC_STORE_F32) ((float *)dst)[e] = (float)code;
     else if (ST == RC_STORE_F16) ((__half *)dst)[e] = __float2half_rn(__fdiv_rn((float)code, (float)vmax));
     else ((uint16_t *)dst)[e] = (uint16_t)code;
 }
 
-cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, int nbv0, int nbv1, int nbv2,
-                            cudaStream_t s) {
-    long long total = (long long)nbv0 * nbv1 * nbv2 * kBrickVox;
-    unsigned blocks = (unsigned)((total + 255) / 256);
+cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStream_t s) {
+    const long long total = (long long)v.cb[0] * v.cb[1] * v.cb[2] * kApronVox;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
     switch (v.storage) {
         case RC_STORE_F32:
-            relayout_kernel<RC_STORE_F32><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, nbv0, nbv1, dst, total);
+            relayout_kernel<RC_STORE_F32><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0], v.cb[1], dst, total);
             break;
         case RC_STORE_F16:
-            relayout_kernel<RC_STORE_F16><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, nbv0, nbv1, dst, total);
+            relayout_kernel<RC_STORE_F16><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0], v.cb[1], dst, total);
             break;
         default:
-            relayout_kernel<RC_STORE_U16><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, nbv0, nbv1, dst, total);
+            relayout_kernel<RC_STORE_U16><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0], v.cb[1], dst, total);
     }
     return cudaGetLastError();
 }
@@ -90,23 +93,21 @@ cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3]
 }
 
 // A cell-brick is occupied unless every entry lo..hi its samples can touch has
-// zero opacity: raw codes u(v) = v (K-1) / vmax floored in integers; FP16
-// storage u(v) = fp16(v / vmax) (K-1), exact in FP32.
+// zero opacity, with the march's own coordinate u(v) = fl(v * ucoef): raw codes
+// v = min, max; FP16 storage v = fp16(min / vmax), fp16(max / vmax).
 __global__ void occupancy_kernel(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax, int f16_values,
                                  TFDev tf, uint8_t *occ) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbricks) return;
     const int K = tf.K;
     int lo, hi;
+    float vmn = (float)mn[b], vmx = (float)mx[b];
     if (f16_values) {
-        float hmn = __half2float(__float2half_rn(__fdiv_rn((float)mn[b], (float)vmax)));
-        float hmx = __half2float(__float2half_rn(__fdiv_rn((float)mx[b], (float)vmax)));
-        lo = (int)floorf(hmn * (float)(K - 1));
-        hi = (int)floorf(hmx * (float)(K - 1)) + 1;
-    } else {
-        lo = (int)(((long long)mn[b] * (K - 1)) / vmax);
-        hi = (int)(((long long)mx[b] * (K - 1)) / vmax) + 1;
+        vmn = __half2float(__float2half_rn(__fdiv_rn(vmn, (float)vmax)));
+        vmx = __half2float(__float2half_rn(__fdiv_rn(vmx, (float)vmax)));
     }
+    lo = (int)floorf(__fmul_rn(vmn, tf.ucoef));
+    hi = (int)floorf(__fmul_rn(vmx, tf.ucoef)) + 1;
     hi = min(hi, K - 1);
     lo = min(lo, K - 1);
     uint8_t any = 0;
