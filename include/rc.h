@@ -160,6 +160,15 @@ rc_status rc_camera_set(rc_context *ctx, const rc_camera *cam);
 rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                     float *out_rgba, rc_stats *stats);
 
+/* Renders nviews cameras (1..65535, all with the same image size) of vol in one
+ * launch: the same images as nviews rc_render calls, written view-major into
+ * out_rgba (device, nviews*H*W*4 floats, caller-owned). A whole orbit becomes
+ * one grid, so the GPU does not drain between frames (Sec. 1's interactive
+ * speed). stats (optional, synchronises) sums over the views. The context's
+ * own camera is not changed. */
+rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                          const rc_camera *cams, int nviews, float *out_rgba, rc_stats *stats);
+
 /* Gradient of a loss with respect to the transfer function entries, given the
  * gradient of the loss with respect to the composited image (Eq. 4-5 are
  * differentiable in the table). dL_dimage: device, width*height*4 floats;

@@ -68,6 +68,8 @@ SIGNATURES = {
     "rc_tf_set_device": (_I, [_P, _P, _I, _I]),
     "rc_camera_set": (_I, [_P, C.POINTER(rc_camera)]),
     "rc_render": (_I, [_P, _P, C.POINTER(rc_render_params), _P, C.POINTER(rc_stats)]),
+    "rc_render_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P,
+                             C.POINTER(rc_stats)]),
     "rc_render_backward": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
     "rc_render_backward_noalloc": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
     "rc_brick_grid_get": (_I, [_P, _P, _P, _P]),
@@ -244,6 +246,17 @@ def _stats_dict(st):
         return None
     return dict(dense_samples=st.dense_samples, evaluated_samples=st.evaluated_samples,
                 rays_hit=st.rays_hit, rays_total=st.rays_total, fallback_rays=st.fallback_rays)
+
+
+def rc_render_views(ctx, vol, params, cams, out, stats=False):
+    """Renders every camera in one launch into out (CUDA float32 tensor
+    n x H x W x 4)."""
+    p = _params(params)
+    arr = (rc_camera * len(cams))(*[c if isinstance(c, rc_camera) else make_camera(c) for c in cams])
+    st = rc_stats() if stats else None
+    _check(lib().rc_render_views(ctx, vol, C.byref(p), arr, len(cams), _ptr(out),
+                                 C.byref(st) if st is not None else None), ctx, "rc_render_views")
+    return _stats_dict(st)
 
 
 def rc_render_backward(ctx, vol, params, dimage, dtf):

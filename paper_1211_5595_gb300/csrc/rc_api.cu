@@ -30,6 +30,9 @@ struct rc_context {
     // statistics counters
     unsigned long long *d_stats = nullptr;
     unsigned long long *h_stats = nullptr;   // pinned
+    // camera records of a multi-view render
+    CamRec *d_cams = nullptr;
+    int cams_cap = 0;
     // scratch of the adjoint: 4K fixed-point accumulators + |dL/dI| maximum
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -151,6 +154,7 @@ rc_status rc_context_destroy(rc_context *ctx) {
     cudaFree(ctx->d_tf32);
     cudaFree(ctx->d_tf16);
     cudaFree(ctx->d_stats);
+    cudaFree(ctx->d_cams);
     cudaFreeHost(ctx->h_stats);
     cudaFree(ctx->d_scratch);
     cudaFree(ctx->d_param);
@@ -337,17 +341,15 @@ rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries
     return tf_common(ctx, rgba_dev, n_entries, fp16, true);
 }
 
-rc_status rc_camera_set(rc_context *ctx, const rc_camera *cam) {
-    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_camera_set: ctx is NULL");
-    if (!cam) return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: cam is NULL");
+static rc_status check_camera(rc_context *ctx, const rc_camera *cam, const char *who) {
     if (cam->width < 1 || cam->height < 1 || (long long)cam->width * cam->height > (1ll << 28))
-        return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: image %d x %d", cam->width, cam->height);
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: image %d x %d", who, cam->width, cam->height);
     if (!(cam->fovy_deg > 0.0f && cam->fovy_deg < 180.0f))
-        return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: fovy %g", (double)cam->fovy_deg);
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: fovy %g", who, (double)cam->fovy_deg);
     double f[3], up[3], c[3];
     for (int a = 0; a < 3; a++) {
         if (!isfinite(cam->eye[a]) || !isfinite(cam->target[a]) || !isfinite(cam->up[a]))
-            return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: non-finite vector");
+            return fail(ctx, RC_ERR_INVALID_ARG, "%s: non-finite vector", who);
         f[a] = (double)cam->target[a] - (double)cam->eye[a];
         up[a] = cam->up[a];
     }
@@ -355,7 +357,15 @@ rc_status rc_camera_set(rc_context *ctx, const rc_camera *cam) {
     c[1] = f[2] * up[0] - f[0] * up[2];
     c[2] = f[0] * up[1] - f[1] * up[0];
     if (f[0] * f[0] + f[1] * f[1] + f[2] * f[2] == 0.0 || c[0] * c[0] + c[1] * c[1] + c[2] * c[2] == 0.0)
-        return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: eye == target or up parallel to the view");
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: eye == target or up parallel to the view", who);
+    return RC_OK;
+}
+
+rc_status rc_camera_set(rc_context *ctx, const rc_camera *cam) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_camera_set: ctx is NULL");
+    if (!cam) return fail(ctx, RC_ERR_INVALID_ARG, "rc_camera_set: cam is NULL");
+    rc_status st = check_camera(ctx, cam, "rc_camera_set");
+    if (st != RC_OK) return st;
     ctx->cam = *cam;
     ctx->cam_set = true;
     return RC_OK;
@@ -475,6 +485,7 @@ static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render
     a.occ = v->d_occ;
     a.out = reinterpret_cast<float4 *>(out);
     a.stats = nullptr;
+    a.cams = nullptr;
     return a;
 }
 
@@ -493,7 +504,64 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
         a.stats = ctx->d_stats;
     }
-    RC_CUDA(ctx, launch_march(a, ctx->stream));
+    RC_CUDA(ctx, launch_march(a, 1, ctx->stream));
+    if (stats) return read_stats(ctx, stats, false);
+    return RC_OK;
+}
+
+rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const rc_camera *cams,
+                          int nviews, float *out_rgba, rc_stats *stats) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_render_views: ctx is NULL");
+    if (!cams || nviews < 1 || nviews > 65535)
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_views: %d cameras", cams ? nviews : 0);
+    for (int i = 0; i < nviews; i++) {
+        rc_status st = check_camera(ctx, &cams[i], "rc_render_views");
+        if (st != RC_OK) return st;
+        if (cams[i].width != cams[0].width || cams[i].height != cams[0].height)
+            return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_views: camera %d has another image size", i);
+    }
+    if ((long long)nviews * cams[0].width * cams[0].height > (1ll << 31))
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_views: %d views of %d x %d pixels", nviews, cams[0].width,
+                    cams[0].height);
+    // the render checks need a camera; the first view's is used only for them
+    const bool had = ctx->cam_set;
+    const rc_camera keep = ctx->cam;
+    ctx->cam = cams[0];
+    ctx->cam_set = true;
+    rc_status st = check_render(ctx, vol, p, out_rgba, "rc_render_views");
+    ctx->cam = keep;
+    ctx->cam_set = had;
+    if (st != RC_OK) return st;
+    DeviceScope ds(ctx->device);
+    if (ctx->cams_cap < nviews) {
+        CamRec *buf = nullptr;
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        RC_CUDA(ctx, cudaMalloc(&buf, (size_t)nviews * sizeof(CamRec)));
+        cudaFree(ctx->d_cams);
+        ctx->d_cams = buf;
+        ctx->cams_cap = nviews;
+    }
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    if (p->skip && p->func == RC_FUNC_COMPOSITE) {
+        st = ensure_occupancy(ctx, v);
+        if (st != RC_OK) return st;
+    }
+    CamRec *recs = new (std::nothrow) CamRec[nviews];
+    if (!recs) return fail(ctx, RC_ERR_OOM, "rc_render_views: host allocation");
+    for (int i = 0; i < nviews; i++) recs[i] = camera_record(cams[i], v->s);
+    // pageable source: the copy is staged before the call returns
+    cudaError_t ce = cudaMemcpyAsync(ctx->d_cams, recs, (size_t)nviews * sizeof(CamRec), cudaMemcpyHostToDevice,
+                                     ctx->stream);
+    MarchArgs a = march_args(ctx, v, p, out_rgba);
+    a.cam = recs[0];
+    delete[] recs;
+    RC_CUDA(ctx, ce);
+    a.cams = ctx->d_cams;
+    if (stats) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        a.stats = ctx->d_stats;
+    }
+    RC_CUDA(ctx, launch_march(a, nviews, ctx->stream));
     if (stats) return read_stats(ctx, stats, false);
     return RC_OK;
 }

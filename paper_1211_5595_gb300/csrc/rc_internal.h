@@ -61,8 +61,9 @@ struct MarchArgs {
     TFDev tf;
     MarchParams p;
     const uint8_t *occ;            // cell-brick occupancy (1 = may be non-empty)
-    float4 *out;                   // H x W RGBA
+    float4 *out;                   // H x W RGBA (view-major for several views)
     unsigned long long *stats;     // dense, evaluated, hit, total (or null)
+    const CamRec *cams;            // one record per view (blockIdx.z), or null: cam
 };
 
 // Adjoint arguments (compositing function only).
@@ -127,7 +128,7 @@ cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3]
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);
 cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax,
                              int f16_values, TFDev tf, uint8_t *occ, cudaStream_t s);
-cudaError_t launch_march(const MarchArgs &a, cudaStream_t s);
+cudaError_t launch_march(const MarchArgs &a, int nviews, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjointArgs &a, float *dL_dtf, cudaStream_t s);
 cudaError_t launch_absmax(const float *x, long long n, float *out, cudaStream_t s);
 cudaError_t launch_profiles(const MarchArgs &a, float *out, cudaStream_t s);

@@ -35,11 +35,13 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
     extern __shared__ float4 s_tf[];
     load_tf(a.tf, s_tf);
     __syncthreads();
+    const CamRec cam = a.cams ? a.cams[blockIdx.z] : a.cam;
+    float4 *out = a.out + (size_t)blockIdx.z * cam.W * cam.H;
     int x, y;
     pixel_of_thread(x, y);
-    const bool inimg = x < a.cam.W && y < a.cam.H;
+    const bool inimg = x < cam.W && y < cam.H;
     Ray R;
-    const bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
+    const bool hit = inimg && setup_ray(cam, a.vol, a.p.step_vox, x, y, R);
     const int nsamp = hit ? R.nsamp : 0;
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
     int k = 0;
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
         k++;
         active = k < nsamp && (1.0f - T) < a.p.term;
     }
-    if (inimg) a.out[(size_t)y * a.cam.W + x] = make_float4(C0, C1, C2, 1.0f - T);
+    if (inimg) out[(size_t)y * cam.W + x] = make_float4(C0, C1, C2, 1.0f - T);
     if (a.stats) add_stats(a.stats, (unsigned)min(k, nsamp), evald, hit ? 1u : 0u, inimg ? 1u : 0u);
 }
 
@@ -73,11 +75,13 @@ __global__ void __launch_bounds__(128) function_kernel(const MarchArgs a) {
     extern __shared__ float4 s_tf[];
     load_tf(a.tf, s_tf);
     __syncthreads();
+    const CamRec cam = a.cams ? a.cams[blockIdx.z] : a.cam;
+    float4 *outp = a.out + (size_t)blockIdx.z * cam.W * cam.H;
     int x, y;
     pixel_of_thread(x, y);
-    const bool inimg = x < a.cam.W && y < a.cam.H;
+    const bool inimg = x < cam.W && y < cam.H;
     Ray R;
-    const bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
+    const bool hit = inimg && setup_ray(cam, a.vol, a.p.step_vox, x, y, R);
     const int nsamp = hit ? R.nsamp : 0;
     const int func = a.p.func;
     float4 out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -121,37 +125,38 @@ __global__ void __launch_bounds__(128) function_kernel(const MarchArgs a) {
         else have = false;
         if (have) out = make_float4(m, m, m, 1.0f);
     }
-    if (inimg) a.out[(size_t)y * a.cam.W + x] = out;
+    if (inimg) outp[(size_t)y * cam.W + x] = out;
     if (a.stats) add_stats(a.stats, (unsigned)k, (unsigned)k, hit ? 1u : 0u, inimg ? 1u : 0u);
 }
 
 template <typename K>
-static cudaError_t launch_kernel(K kern, const MarchArgs &a, cudaStream_t s) {
+static cudaError_t launch_kernel(K kern, const MarchArgs &a, int nviews, cudaStream_t s) {
     size_t smem = (size_t)a.tf.K * sizeof(float4);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((a.cam.W + 15) / 16, (a.cam.H + 7) / 8);
+    dim3 grid((a.cam.W + 15) / 16, (a.cam.H + 7) / 8, nviews);
     kern<<<grid, 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_march(const MarchArgs &a, cudaStream_t s) {
+// a.cam gives the image size of every view; with a.cams, grid.z = nviews.
+cudaError_t launch_march(const MarchArgs &a, int nviews, cudaStream_t s) {
     if (a.p.func != RC_FUNC_COMPOSITE) {
         switch (a.vol.storage) {
-            case RC_STORE_F32: return launch_kernel(function_kernel<RC_STORE_F32>, a, s);
-            case RC_STORE_F16: return launch_kernel(function_kernel<RC_STORE_F16>, a, s);
-            default: return launch_kernel(function_kernel<RC_STORE_U16>, a, s);
+            case RC_STORE_F32: return launch_kernel(function_kernel<RC_STORE_F32>, a, nviews, s);
+            case RC_STORE_F16: return launch_kernel(function_kernel<RC_STORE_F16>, a, nviews, s);
+            default: return launch_kernel(function_kernel<RC_STORE_U16>, a, nviews, s);
         }
     }
     switch (a.vol.storage * 2 + (a.p.shade ? 1 : 0)) {
-        case RC_STORE_F32 * 2: return launch_kernel(composite_kernel<RC_STORE_F32, false>, a, s);
-        case RC_STORE_F32 * 2 + 1: return launch_kernel(composite_kernel<RC_STORE_F32, true>, a, s);
-        case RC_STORE_F16 * 2: return launch_kernel(composite_kernel<RC_STORE_F16, false>, a, s);
-        case RC_STORE_F16 * 2 + 1: return launch_kernel(composite_kernel<RC_STORE_F16, true>, a, s);
-        case RC_STORE_U16 * 2: return launch_kernel(composite_kernel<RC_STORE_U16, false>, a, s);
-        default: return launch_kernel(composite_kernel<RC_STORE_U16, true>, a, s);
+        case RC_STORE_F32 * 2: return launch_kernel(composite_kernel<RC_STORE_F32, false>, a, nviews, s);
+        case RC_STORE_F32 * 2 + 1: return launch_kernel(composite_kernel<RC_STORE_F32, true>, a, nviews, s);
+        case RC_STORE_F16 * 2: return launch_kernel(composite_kernel<RC_STORE_F16, false>, a, nviews, s);
+        case RC_STORE_F16 * 2 + 1: return launch_kernel(composite_kernel<RC_STORE_F16, true>, a, nviews, s);
+        case RC_STORE_U16 * 2: return launch_kernel(composite_kernel<RC_STORE_U16, false>, a, nviews, s);
+        default: return launch_kernel(composite_kernel<RC_STORE_U16, true>, a, nviews, s);
     }
 }
 

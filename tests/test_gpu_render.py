@@ -221,3 +221,26 @@ def test_ray_functions(rc, orc, c1, func):
         else:
             np.testing.assert_allclose(g[same], a[same], atol=2e-4)
         assert a[:, 3].sum() > 100
+
+
+# --------------------------------------------------------------------------
+# several views in one launch
+# --------------------------------------------------------------------------
+def test_render_views_equals_single_renders(rc, c1):
+    import torch
+    ph, tf, w, r = c1
+    cams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=96, height=72) for az in (0.0, 33.0, 200.0, 310.0)]
+    P = dict(step_vox=0.5, term=0.99, shade=True, skip=True)
+    out = torch.empty((4, 72, 96, 4), device="cuda")
+    st = rc.rc_render_views(r.ctx, r.vol, P, cams, out, stats=True)
+    torch.cuda.synchronize()
+    dense = 0
+    for v, cam in enumerate(cams):
+        img, s1 = r.render(cam, stats=True, **P)
+        assert np.array_equal(out[v].cpu().numpy(), img)
+        dense += s1["dense_samples"]
+    assert st["dense_samples"] == dense and st["rays_total"] == 4 * 96 * 72
+    bad = [cams[0], synth.orbit_camera(ph.dims, ph.spacing, 10.0, width=95, height=72)]
+    with pytest.raises(rc.RCError) as ei:
+        rc.rc_render_views(r.ctx, r.vol, P, bad, out)
+    assert ei.value.status == rc.RC_ERR_INVALID_ARG
