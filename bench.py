@@ -122,6 +122,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(value, world, device):
+    """The largest value over all ranks (every rank gets it)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank_step, steps, max_total_ms):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank_step * steps / (max_total_ms / 1e3)
+
+
 def setup_dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -161,6 +177,53 @@ def cpu_oracle_sample(ph, tf, w, cams, budget_s, pixels_per_view=None):
     dt = time.perf_counter() - t0
     what = f"{pixels_per_view} seeded pixels of each of" if pixels_per_view else "full 1024^2 frames of"
     return samples / dt / 1e9, cores, f"{what} {views} view(s), {samples} samples, {dt:.1f} s"
+
+
+def adjoint_form(rc, ctx, flush, stream):
+    """Transfer-function gradient on the differentiable workload (128x128x96,
+    8 views at 512^2, unshaded, step 0.5): time of rc_render_backward per view
+    against the forward render of the same view, with the samples each pass
+    marches (the backward recomputes the forward, then marches again)."""
+    import torch
+    wd = synth.WORKLOADS["diff_128x128x96"]
+    ph = synth.workload_phantom("diff_128x128x96")
+    vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, rc.RC_STORE_F32)
+    rc.rc_volume_upload(ctx, vol, ph.vol)
+    tf = torch.from_numpy(synth.noise_tf(wd["K"], wd["init_tf_seed"], alpha_max=0.1)).cuda()
+    rc.rc_tf_set_device(ctx, tf)
+    cams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=wd["width"], height=wd["height"])
+            for az in wd["azimuths"]]
+    P = rc.RenderParams(step_vox=wd["step"], term=wd["term"], shade=False, skip=False)
+    img = torch.empty((wd["height"], wd["width"], 4), device="cuda")
+    g = torch.randn(img.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    dtf = torch.empty_like(tf)
+    dense = 0
+    for cam in cams:
+        rc.rc_camera_set(ctx, cam)
+        dense += rc.rc_render(ctx, vol, P, img, stats=True)["dense_samples"]
+    fwd, bwd = [], []
+    for rep in range(3):
+        for cam in cams:
+            rc.rc_camera_set(ctx, cam)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            rc.rc_render(ctx, vol, P, img)
+            e[1].record(stream)
+            rc.rc_render_backward(ctx, vol, P, g, dtf)
+            e[2].record(stream)
+            if rep > 0:
+                fwd.append(e)
+        flush.zero_()
+    torch.cuda.synchronize()
+    f_ms = statistics.median(a.elapsed_time(b) for a, b, c in fwd)
+    b_ms = statistics.median(b.elapsed_time(c) for a, b, c in fwd)
+    rc.rc_volume_destroy(ctx, vol)
+    per_view = dense / len(cams)
+    return {"workload": "diff_128x128x96", "views": len(cams), "image": "512x512",
+            "forward_ms_per_view": f_ms, "backward_ms_per_view": b_ms, "backward_over_forward": b_ms / f_ms,
+            "dense_samples_per_view": per_view,
+            "backward_gsamples_s": 2 * per_view / (b_ms / 1e3) / 1e9,
+            "note": "exact skipping in the forward recompute, none in the gradient pass (an empty brick still has a gradient)"}
 
 
 def proposal_form(rc, ctx, vol, ph, w, cams, P, outs, frame_ms, flush, stream, n_train):
@@ -363,12 +426,8 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     launch_ms = [a.elapsed_time(b) for a, b in kern_ev]          # one launch renders every view
     frame_ms = [m / nviews for m in launch_ms]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * dense * args.steps / (total_ms / 1e3) / 1e9
+    total_ms = max_over_ranks(sum(step_ms), world, "cuda")
+    value = job_throughput(world, dense, args.steps, total_ms) / 1e9
     ms_per_step = total_ms / args.steps
 
     # end to end through the C-ABI with host buffers: pinned codes and table
@@ -420,6 +479,10 @@ def main():
                            "speedup_vs_f32": fp32_frame_ms / ms, "psnr_db_min_vs_f32": psnr,
                            "max_abs_vs_f32": float((outs - ref_imgs).abs().max())}
             rc.rc_volume_destroy(ctx, v2)
+        rc.rc_tf_set_device(ctx, tf_dev)
+
+    if not args.no_forms:
+        forms["adjoint"] = adjoint_form(rc, ctx, flush, stream)
         rc.rc_tf_set_device(ctx, tf_dev)
 
     if not args.no_proposal:

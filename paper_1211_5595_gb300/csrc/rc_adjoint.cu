@@ -41,6 +41,25 @@ __device__ __forceinline__ void acc_add(unsigned long long *acc, int idx, float 
     if (q != 0) atomicAdd(acc + idx, (unsigned long long)q);
 }
 
+// Sum of v over the lanes of this lane's group (lanes with the same key), in a
+// fixed pairwise-tree order over the group's lanes sorted by lane id; the sum
+// ends in the group's lowest lane (rank 0). Deterministic for a given key set.
+__device__ __forceinline__ void group_sum8(unsigned peers, float (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(peers);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+#pragma unroll 1
+    for (int s = 1; __any_sync(0xffffffffu, s < cnt); s <<= 1) {
+        const bool take = (rank % (2 * s)) == 0 && rank + s < cnt;
+        const int src = take ? (int)__fns(peers, 0, rank + s + 1) : lane;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const float o = __shfl_sync(0xffffffffu, v[c], src);
+            if (take) v[c] += o;
+        }
+    }
+}
+
 template <int ST, bool SHADE>
 __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const float *absmax) {
     const MarchArgs &a = A.m;
@@ -60,47 +79,45 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
     bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
     float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (hit) g = A.dimg[(size_t)y * a.cam.W + x];
-    if (hit && (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f)) {
-        // pass 1: forward
-        float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
-        int n = 0;
-        for (int k = 0; k < R.nsamp; k++) {
-            float p[3], gr[3], val;
+    const bool has_g = hit && (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f);
+    // pass 1: the forward march, with exact empty-space skipping (identical
+    // result), for C_final, T_final and the sample count n up to termination
+    float Cf0 = 0.0f, Cf1 = 0.0f, Cf2 = 0.0f, Tf = 1.0f;
+    int n = 0;
+    if (has_g) {
+        int k = 0;
+        while (k < R.nsamp) {
+            float p[3];
             position_at(R, sample_t(R, k), p);
             Cell c;
             cell_of(a.vol, p, c);
-            if (SHADE) val = value_grad<ST>(a.vol, c, gr);
-            else val = trilinear<ST>(a.vol, c);
-            float4 e = classify(s_tf, K, tf_coord(val, a.tf.ucoef));
-            float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
-            float r = e.x, gg = e.y, b = e.z;
-            if (SHADE) {
-                float sf, spec;
-                shade_factor(a.p, a.vol, gr, R.dir, sf, spec);
-                r = fminf(1.0f, __fmaf_rn(r, sf, spec));
-                gg = fminf(1.0f, __fmaf_rn(gg, sf, spec));
-                b = fminf(1.0f, __fmaf_rn(b, sf, spec));
+            if (!__ldg(a.occ + brick_of(a.vol, c))) {
+                k = jump_empty(R, a.vol, c, k);
+                continue;
             }
-            float ta = T * ap;
-            C0 = __fmaf_rn(ta, r, C0);
-            C1 = __fmaf_rn(ta, gg, C1);
-            C2 = __fmaf_rn(ta, b, C2);
-            T = T * (1.0f - ap);
-            n = k + 1;
-            if ((1.0f - T) >= a.p.term) break;
+            float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, K, a.tf.ucoef, R.dir, c, a.p.rmode, a.p.ratio);
+            composite_add(e, Cf0, Cf1, Cf2, Tf);
+            k++;
+            if ((1.0f - Tf) >= a.p.term) break;
         }
-        const float Cf0 = C0, Cf1 = C1, Cf2 = C2, Tf = T;
-        // pass 2: prefix sums again, gradient per sample
-        C0 = C1 = C2 = 0.0f;
-        T = 1.0f;
-        for (int k = 0; k < n; k++) {
+        n = min(k, R.nsamp);
+    }
+    // pass 2: every sample again (an empty brick still has a gradient), the
+    // prefix C_{<=k} rebuilt, one gradient contribution per sample; lanes that
+    // hit the same table entries are summed first, then one 64-bit fixed-point
+    // atomic per entry and channel
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
+    for (int k = 0; __any_sync(0xffffffffu, k < n); k++) {
+        const bool active = k < n;
+        int i = -1;
+        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (active) {
             float p[3], gr[3], val;
             position_at(R, sample_t(R, k), p);
             Cell c;
             cell_of(a.vol, p, c);
             if (SHADE) val = value_grad<ST>(a.vol, c, gr);
             else val = trilinear<ST>(a.vol, c);
-            int i;
             float w;
             float4 e = classify(s_tf, K, tf_coord(val, a.tf.ucoef), &i, &w);
             float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
@@ -133,14 +150,15 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
             else dal = dap * a.p.ratio * powf(1.0f - ac, a.p.ratio - 1.0f);
             float dr = g.x * ta * d0, dg = g.y * ta * d1, db = g.z * ta * d2;
             const float w0 = 1.0f - w;
-            acc_add(s_acc, 4 * i + 0, w0 * dr, scale);
-            acc_add(s_acc, 4 * i + 1, w0 * dg, scale);
-            acc_add(s_acc, 4 * i + 2, w0 * db, scale);
-            acc_add(s_acc, 4 * i + 3, w0 * dal, scale);
-            acc_add(s_acc, 4 * i + 4, w * dr, scale);
-            acc_add(s_acc, 4 * i + 5, w * dg, scale);
-            acc_add(s_acc, 4 * i + 6, w * db, scale);
-            acc_add(s_acc, 4 * i + 7, w * dal, scale);
+            v[0] = w0 * dr; v[1] = w0 * dg; v[2] = w0 * db; v[3] = w0 * dal;
+            v[4] = w * dr;  v[5] = w * dg;  v[6] = w * db;  v[7] = w * dal;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, active ? i : -1 - lane);
+        group_sum8(peers, v);
+        const bool leader = active && (peers & ((1u << lane) - 1u)) == 0u;
+        if (leader) {
+#pragma unroll
+            for (int c = 0; c < 8; c++) acc_add(s_acc, 4 * i + c, v[c], scale);
         }
     }
     __syncthreads();

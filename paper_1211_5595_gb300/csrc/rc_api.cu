@@ -67,6 +67,33 @@ struct rc_volume {
 
 static thread_local char g_err[512];
 
+// Host-side fault injection for tests: with RC_FAULT_ALLOC=n in the
+// environment, the n-th device allocation after the variable's text last
+// changed fails with cudaErrorMemoryAllocation (the allocation is not
+// attempted); "1", "01", "001" each re-arm for the first allocation. Off when
+// unset or empty.
+static std::mutex g_fault_mu;
+static char g_fault_env[32] = "";
+static long g_fault_left = -1;
+
+template <typename T>
+static cudaError_t dev_alloc(T **p, size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lock(g_fault_mu);
+        const char *e = getenv("RC_FAULT_ALLOC");
+        if (!e) e = "";
+        if (strncmp(e, g_fault_env, sizeof g_fault_env) != 0) {
+            snprintf(g_fault_env, sizeof g_fault_env, "%s", e);
+            g_fault_left = e[0] ? atol(e) : -1;
+        }
+        if (g_fault_left > 0 && --g_fault_left == 0) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+
 static rc_status fail(rc_context *ctx, rc_status s, const char *fmt, ...) {
     char *buf = ctx ? ctx->err : g_err;
     va_list ap;
@@ -130,7 +157,7 @@ rc_status rc_context_create(int device, void *cuda_stream, rc_context **out) {
     if (!ctx) return fail(nullptr, RC_ERR_OOM, "rc_context_create: host allocation");
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
-    if (cudaMalloc(&ctx->d_stats, 5 * sizeof(unsigned long long)) != cudaSuccess ||
+    if (dev_alloc(&ctx->d_stats, 5 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_stats, 5 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaFree(ctx->d_stats);
         delete ctx;
@@ -207,11 +234,11 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
     v->nbricks = v->cb[0] * v->cb[1] * v->cb[2];
     size_t esz = storage == RC_STORE_F32 ? 4 : 2;
     size_t nvox = (size_t)nx * ny * nz;
-    if (cudaMalloc(&v->d_data, (size_t)padded * esz) != cudaSuccess ||
-        cudaMalloc(&v->d_stage, nvox * sizeof(uint16_t)) != cudaSuccess ||
-        cudaMalloc(&v->d_mn, v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
-        cudaMalloc(&v->d_mx, v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
-        cudaMalloc(&v->d_occ, v->nbricks) != cudaSuccess) {
+    if (dev_alloc(&v->d_data, (size_t)padded * esz) != cudaSuccess ||
+        dev_alloc(&v->d_stage, nvox * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_mn, v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_mx, v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_occ, v->nbricks) != cudaSuccess) {
         cudaGetLastError();
         volume_free(v);
         delete v;
@@ -282,8 +309,8 @@ static rc_status tf_reserve(rc_context *ctx, int K) {
     if (K <= ctx->tf_cap) return RC_OK;
     float4 *a = nullptr;
     uint2 *b = nullptr;
-    if (cudaMalloc(&a, (size_t)K * sizeof(float4)) != cudaSuccess ||
-        cudaMalloc(&b, (size_t)K * sizeof(uint2)) != cudaSuccess) {
+    if (dev_alloc(&a, (size_t)K * sizeof(float4)) != cudaSuccess ||
+        dev_alloc(&b, (size_t)K * sizeof(uint2)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(a);
         return fail(ctx, RC_ERR_OOM, "rc_tf_set: device allocation");
@@ -536,7 +563,7 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
     if (ctx->cams_cap < nviews) {
         CamRec *buf = nullptr;
         RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        RC_CUDA(ctx, cudaMalloc(&buf, (size_t)nviews * sizeof(CamRec)));
+        RC_CUDA(ctx, dev_alloc(&buf, (size_t)nviews * sizeof(CamRec)));
         cudaFree(ctx->d_cams);
         ctx->d_cams = buf;
         ctx->cams_cap = nviews;
@@ -578,11 +605,13 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_ren
     if (ctx->scratch_bytes < need) {
         void *buf = nullptr;
         RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        RC_CUDA(ctx, cudaMalloc(&buf, need));
+        RC_CUDA(ctx, dev_alloc(&buf, need));
         cudaFree(ctx->d_scratch);
         ctx->d_scratch = buf;
         ctx->scratch_bytes = need;
     }
+    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol));
+    if (st != RC_OK) return st;
     AdjointArgs a;
     a.m = march_args(ctx, vol, p, nullptr);
     a.m.p.skip = 0;
@@ -645,6 +674,8 @@ rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, cons
     long long *scratch = nullptr;
     st = noalloc_scratch(ctx, &scratch);
     if (st != RC_OK) return st;
+    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol));
+    if (st != RC_OK) return st;
     AdjointArgs a;
     a.m = march_args(ctx, vol, p, nullptr);
     a.m.p.skip = 0;
@@ -692,9 +723,9 @@ static rc_status net_alloc(rc_context *ctx) {
     if (ctx->d_param) return RC_OK;
     float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
     uint2 *f = nullptr;
-    if (cudaMalloc(&p, kParams * sizeof(float)) != cudaSuccess || cudaMalloc(&m, kParams * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&v, kParams * sizeof(float)) != cudaSuccess || cudaMalloc(&g, kParams * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&f, kFragTotal * sizeof(uint2)) != cudaSuccess) {
+    if (dev_alloc(&p, kParams * sizeof(float)) != cudaSuccess || dev_alloc(&m, kParams * sizeof(float)) != cudaSuccess ||
+        dev_alloc(&v, kParams * sizeof(float)) != cudaSuccess || dev_alloc(&g, kParams * sizeof(float)) != cudaSuccess ||
+        dev_alloc(&f, kFragTotal * sizeof(uint2)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(p);
         cudaFree(m);
@@ -825,8 +856,8 @@ static rc_status net_grad(rc_context *ctx, const float *features, const float *t
     if (ctx->partial_blocks < grid) {
         float *pp = nullptr, *lp = nullptr;
         RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        if (cudaMalloc(&pp, (size_t)152 * kParams * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&lp, 152 * sizeof(float)) != cudaSuccess) {
+        if (dev_alloc(&pp, (size_t)152 * kParams * sizeof(float)) != cudaSuccess ||
+            dev_alloc(&lp, 152 * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(pp);
             return fail(ctx, RC_ERR_OOM, "proposal: gradient partials");

@@ -1,0 +1,127 @@
+"""Failure handling of the C-ABI, injected on the host (no GPU fault): every
+device allocation the library makes can be made to fail through
+RC_FAULT_ALLOC=n (the n-th allocation after the variable's text last changed;
+"1", "01", "001" each re-arm the first one); the calls must
+return RC_ERR_OOM, leave earlier state usable, and leak nothing that breaks
+later calls. Argument and state errors are status codes too."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rc():
+    from paper_1211_5595_gb300 import build
+    build.build()
+    import paper_1211_5595_gb300 as rc
+    return rc
+
+
+def render(rc, ctx, vol, cam):
+    import torch
+    rc.rc_camera_set(ctx, cam)
+    out = torch.empty((cam["height"], cam["width"], 4), device="cuda")
+    rc.rc_render(ctx, vol, dict(step_vox=0.5, term=0.99, shade=True, skip=True), out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_allocation_failures_are_clean(rc, monkeypatch):
+    import torch
+    ph = synth.head_phantom((48, 40, 32), (1, 1, 1), seed=3, tumor_radius_vox=4)
+    tf = synth.tf_table(256)
+    cam = synth.orbit_camera(ph.dims, ph.spacing, 20.0, width=64, height=48)
+    ctx = rc.rc_context_create(0)
+    try:
+        rc.rc_tf_set(ctx, tf)
+        # each of the five device allocations of rc_volume_create fails in turn
+        for n in range(1, 6):
+            monkeypatch.setenv("RC_FAULT_ALLOC", str(n))
+            with pytest.raises(rc.RCError) as ei:
+                rc.rc_volume_create(ctx, ph.dims, ph.spacing, 4095, rc.RC_STORE_F32)
+            assert ei.value.status == rc.RC_ERR_OOM
+        monkeypatch.delenv("RC_FAULT_ALLOC")
+        vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, 4095, rc.RC_STORE_F32)
+        rc.rc_volume_upload(ctx, vol, ph.vol)
+        ref = render(rc, ctx, vol, cam)
+        assert ref[..., 3].max() > 0.5
+        # a larger table whose buffers cannot be allocated keeps the old table
+        monkeypatch.setenv("RC_FAULT_ALLOC", "01")
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_tf_set(ctx, synth.tf_table(1024))
+        assert ei.value.status == rc.RC_ERR_OOM
+        monkeypatch.delenv("RC_FAULT_ALLOC")
+        assert np.array_equal(render(rc, ctx, vol, cam), ref)
+        # the gradient's scratch
+        g = torch.ones((48, 64, 4), device="cuda")
+        dtf = torch.empty((256, 4), device="cuda")
+        P = dict(step_vox=0.5, term=0.99, shade=False, skip=False)
+        monkeypatch.setenv("RC_FAULT_ALLOC", "001")
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_render_backward(ctx, vol, P, g, dtf)
+        assert ei.value.status == rc.RC_ERR_OOM
+        monkeypatch.delenv("RC_FAULT_ALLOC")
+        rc.rc_render_backward(ctx, vol, P, g, dtf)
+        torch.cuda.synchronize()
+        assert torch.isfinite(dtf).all() and dtf.abs().sum() > 0
+        # the network: a failed load leaves no network behind
+        monkeypatch.setenv("RC_FAULT_ALLOC", "0002")
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_proposal_load(ctx, rc.pack_proposal_blob(synth.proposal_init_params(1)))
+        assert ei.value.status == rc.RC_ERR_OOM
+        monkeypatch.delenv("RC_FAULT_ALLOC")
+        out = torch.empty((48, 64, 4), device="cuda")
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_render_proposal(ctx, vol, P, 64, 0.02, out)
+        assert ei.value.status == rc.RC_ERR_STATE
+        assert np.array_equal(render(rc, ctx, vol, cam), ref)
+        rc.rc_volume_destroy(ctx, vol)
+    finally:
+        monkeypatch.delenv("RC_FAULT_ALLOC", raising=False)
+        torch.cuda.synchronize()
+        rc.rc_context_destroy(ctx)
+
+
+def test_argument_and_state_errors(rc):
+    import torch
+    ctx = rc.rc_context_create(0)
+    try:
+        for dims, sp in (((1, 8, 8), (1, 1, 1)), ((8, 8, 8), (0, 1, 1)), ((8, 8, 8), (1, float("nan"), 1))):
+            with pytest.raises(rc.RCError) as ei:
+                rc.rc_volume_create(ctx, dims, sp)
+            assert ei.value.status == rc.RC_ERR_INVALID_ARG
+        vol = rc.rc_volume_create(ctx, (8, 8, 8), (1, 1, 1))
+        out = torch.empty((4, 4, 4), device="cuda")
+        P = dict(step_vox=0.5, term=0.99)
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_render(ctx, vol, P, out)            # no data, no table, no camera
+        assert ei.value.status == rc.RC_ERR_STATE
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_volume_upload(ctx, vol, np.zeros(7, np.uint16))
+        assert ei.value.status == rc.RC_ERR_INVALID_ARG and "voxels" in str(ei.value)
+        rc.rc_volume_upload(ctx, vol, np.full(512, 3000, np.uint16))
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_tf_set(ctx, np.full((4, 4), 1.5, np.float32))
+        assert ei.value.status == rc.RC_ERR_INVALID_ARG
+        rc.rc_tf_set(ctx, synth.tf_table(256))
+        with pytest.raises(rc.RCError):
+            rc.rc_camera_set(ctx, dict(eye=(0, 0, 0), target=(0, 0, 0), up=(0, 0, 1), fovy_deg=30,
+                                       width=4, height=4))
+        rc.rc_camera_set(ctx, synth.orbit_camera((8, 8, 8), (1, 1, 1), 0.0, width=4, height=4))
+        for bad in (dict(step_vox=0.0), dict(term=1.5), dict(func=9), dict(step_vox=float("inf"))):
+            with pytest.raises(rc.RCError) as ei:
+                rc.rc_render(ctx, vol, dict(P, **bad), out)
+            assert ei.value.status == rc.RC_ERR_INVALID_ARG
+        rc.rc_render(ctx, vol, P, out)
+        torch.cuda.synchronize()
+        assert out[..., 3].max() > 0.5
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_context_destroy(ctx)                 # a volume is still alive
+        assert ei.value.status == rc.RC_ERR_STATE
+        rc.rc_volume_destroy(ctx, vol)
+    finally:
+        torch.cuda.synchronize()
+        rc.rc_context_destroy(ctx)
