@@ -23,6 +23,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 
 COMPOSITE, MIP, AVERAGE, XRAY, ISO, THRESHOLD = range(6)
+TRILINEAR, BSPLINE = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -43,7 +44,8 @@ class _Volume(C.Structure):
 
 
 class _TF(C.Structure):
-    _fields_ = [("rgba", C.c_void_p), ("K", C.c_int32), ("fp16", C.c_int32)]
+    _fields_ = [("rgba", C.c_void_p), ("K", C.c_int32), ("fp16", C.c_int32), ("M", C.c_int32),
+                ("gmax", C.c_float)]
 
 
 class _Camera(C.Structure):
@@ -55,7 +57,7 @@ class _Params(C.Structure):
     _fields_ = [("step_vox", C.c_float), ("term", C.c_float), ("shade", C.c_int32),
                 ("ka", C.c_float), ("kd", C.c_float), ("ks", C.c_float),
                 ("func", C.c_int32), ("iso", C.c_float), ("fp64_rays", C.c_int32),
-                ("tie_band", C.c_float)]
+                ("tie_band", C.c_float), ("filter", C.c_int32)]
 
 
 _lib = None
@@ -76,6 +78,8 @@ def lib():
         L.orc_proposal_features.argtypes = [P, P, P, P, P, C.c_int64, P, P]
         L.orc_proposal_features.restype = C.c_int
         L.orc_brick_minmax.argtypes = [P, P, P]
+        L.orc_brick_minmax_filter.argtypes = [P, C.c_int, P, P]
+        L.orc_brick_minmax_filter.restype = None
         L.orc_occupancy.argtypes = [P, P, P, P, P]
         for f in ("orc_render", "orc_ray_samples", "orc_ray_geometry", "orc_render_grad",
                   "orc_profiles", "orc_importance"):
@@ -95,20 +99,27 @@ class Scene:
 
     def __init__(self, vol, spacing, tf, camera, *, step=0.5, term=0.99, shade=False,
                  ka=0.1, kd=0.7, ks=0.2, func=COMPOSITE, iso=0.0, fp64_rays=False,
-                 tie_band=2e-5, vmax=4095, value_mode=0, tf_fp16=False):
+                 tie_band=2e-5, vmax=4095, value_mode=0, tf_fp16=False, gmax=None,
+                 filter=TRILINEAR):
         self.vol = np.ascontiguousarray(vol, dtype=np.uint16)
         assert self.vol.ndim == 3
         nz, ny, nx = self.vol.shape
+        # tf: (K, 4) one-dimensional, or (M, K, 4) over (gradient magnitude, value)
         self.tf = np.ascontiguousarray(tf, dtype=np.float32)
-        assert self.tf.ndim == 2 and self.tf.shape[1] == 4
+        assert self.tf.ndim in (2, 3) and self.tf.shape[-1] == 4
+        K = self.tf.shape[-2]
+        M = self.tf.shape[0] if self.tf.ndim == 3 else 0
+        if M:
+            assert gmax is not None and gmax > 0
         self.v = _Volume(self.vol.ctypes.data, nx, ny, nz, *[float(s) for s in spacing],
                          int(vmax), int(value_mode))
-        self.t = _TF(self.tf.ctypes.data, self.tf.shape[0], int(bool(tf_fp16)))
+        self.t = _TF(self.tf.ctypes.data, K, int(bool(tf_fp16)), M, float(gmax or 0.0))
         self.c = _Camera((C.c_float * 3)(*camera["eye"]), (C.c_float * 3)(*camera["target"]),
                          (C.c_float * 3)(*camera["up"]), float(camera["fovy_deg"]),
                          int(camera["width"]), int(camera["height"]))
         self.p = _Params(float(step), float(term), int(bool(shade)), float(ka), float(kd),
-                         float(ks), int(func), float(iso), int(bool(fp64_rays)), float(tie_band))
+                         float(ks), int(func), float(iso), int(bool(fp64_rays)), float(tie_band),
+                         int(filter))
         self.width = int(camera["width"])
         self.height = int(camera["height"])
 
@@ -151,15 +162,18 @@ def render(scene: Scene, pixels=None, nthreads=None):
 
 def ray_samples(scene: Scene, x, y, max_samples=100000):
     """Every sample of one ray without termination: structured columns t,
-    px, py, pz, v, u, r, g, b, a, a_corr, col_r, col_g, col_b."""
-    out = np.zeros((max_samples, 14))
+    px, py, pz, v, u, r, g, b, a, a_corr, col_r, col_g, col_b, gm (|grad f|,
+    value units per mm) and gw (its 2-D table coordinate); gm and gw are 0
+    unless shading or a 2-D table needs the gradient."""
+    out = np.zeros((max_samples, 16))
     tot = C.c_int32(0)
     rc = lib().orc_ray_samples(*scene.refs(), int(x), int(y), max_samples, out.ctypes.data,
                                C.byref(tot))
     if rc:
         raise ValueError("oracle ray_samples failed")
     n = min(tot.value, max_samples)
-    names = ("t", "px", "py", "pz", "v", "u", "r", "g", "b", "a", "a_corr", "col_r", "col_g", "col_b")
+    names = ("t", "px", "py", "pz", "v", "u", "r", "g", "b", "a", "a_corr", "col_r", "col_g", "col_b",
+             "gm", "gw")
     return {k: out[:n, i].copy() for i, k in enumerate(names)}
 
 
@@ -174,7 +188,7 @@ def ray_geometry(scene: Scene, x, y):
 
 def render_grad(scene: Scene, dimg, pixels=None, nthreads=None):
     """dL/dTF (K x 4, FP64) of the compositing function for the upstream image
-    gradient dimg (per pixel RGBA); also returns the FP64 image."""
+    gradient dimg (per pixel RGBA); also returns the FP64 image. 1-D tables only."""
     n = scene.npix(pixels)
     g = np.ascontiguousarray(np.asarray(dimg, dtype=np.float64).reshape(n, 4))
     dtf = np.zeros((scene.tf.shape[0], 4)); rgba = np.zeros((n, 4))
@@ -205,7 +219,7 @@ def importance(scene: Scene, pdf, nimp=64, pixels=None, nthreads=None, occ=None)
     n = scene.npix(pixels)
     p = np.ascontiguousarray(np.asarray(pdf, dtype=np.float32).reshape(n, 32))
     if occ is None:
-        mn, mx = brick_minmax(scene.vol, vmax=scene.v.vmax)
+        mn, mx = brick_minmax(scene.vol, vmax=scene.v.vmax, filter=scene.p.filter)
         occ = occupancy((scene.v.nx, scene.v.ny, scene.v.nz), scene.tf, mn, mx, vmax=scene.v.vmax,
                         value_mode=scene.v.value_mode, tf_fp16=bool(scene.t.fp16))
     o = np.ascontiguousarray(occ, dtype=np.uint8)
@@ -224,25 +238,29 @@ def brick_grid_shape(dims):
     return ((nz - 1 + 15) // 16, (ny - 1 + 15) // 16, (nx - 1 + 15) // 16)
 
 
-def brick_minmax(vol, vmax=4095):
-    """Per cell-brick min and max over the 17^3 (clipped) voxel footprint."""
+def brick_minmax(vol, vmax=4095, filter=TRILINEAR):
+    """Per cell-brick min and max over the (clipped) voxel footprint of the
+    filter: 17^3 voxels 16b..16b+16 for trilinear, 19^3 voxels 16b-1..16b+17
+    for the cubic B-spline."""
     v = np.ascontiguousarray(vol, dtype=np.uint16)
     nz, ny, nx = v.shape
     shp = brick_grid_shape((nx, ny, nz))
     mn = np.zeros(shp, dtype=np.uint16); mx = np.zeros(shp, dtype=np.uint16)
     desc = _Volume(v.ctypes.data, nx, ny, nz, 1.0, 1.0, 1.0, int(vmax), 0)
-    lib().orc_brick_minmax(C.byref(desc), mn.ctypes.data, mx.ctypes.data)
+    lib().orc_brick_minmax_filter(C.byref(desc), int(filter), mn.ctypes.data, mx.ctypes.data)
     return mn, mx
 
 
 def occupancy(dims, tf, mn, mx, vmax=4095, value_mode=0, tf_fp16=False):
-    """1 where a brick can hold a sample of non-zero opacity, else 0."""
+    """1 where a brick can hold a sample of non-zero opacity, else 0. tf is a
+    (K, 4) table or an (M, K, 4) table over (gradient magnitude, value)."""
     nx, ny, nz = dims
     t = np.ascontiguousarray(tf, dtype=np.float32)
+    M = t.shape[0] if t.ndim == 3 else 0
     mn = np.ascontiguousarray(mn, dtype=np.uint16); mx = np.ascontiguousarray(mx, dtype=np.uint16)
     occ = np.zeros(mn.shape, dtype=np.uint8)
     desc = _Volume(None, nx, ny, nz, 1.0, 1.0, 1.0, int(vmax), int(value_mode))
-    tdesc = _TF(t.ctypes.data, t.shape[0], int(bool(tf_fp16)))
+    tdesc = _TF(t.ctypes.data, t.shape[-2], int(bool(tf_fp16)), M, 1.0)
     lib().orc_occupancy(C.byref(desc), C.byref(tdesc), mn.ctypes.data, mx.ctypes.data,
                         occ.ctypes.data)
     return occ

@@ -67,9 +67,13 @@ typedef struct {
 } orc_volume;
 
 typedef struct {
-    const float *rgba;      /* K x 4, straight colour + opacity per reference step */
+    const float *rgba;      /* straight colour + opacity per reference step: K x 4
+                               (1-D), or M rows of K entries x 4 (2-D; value index
+                               fastest, row j = gradient-magnitude index) */
     int32_t K;
     int32_t fp16;           /* 1: use the FP16 rounding of each entry */
+    int32_t M;              /* rows of a 2-D table; 0 or 1: 1-D table */
+    float gmax;             /* 2-D: gradient magnitude (codes per mm) of the last row */
 } orc_tf;
 
 typedef struct {
@@ -89,7 +93,10 @@ typedef struct {
     float iso;          /* iso-value / threshold in volume value units */
     int32_t fp64_rays;  /* 1: ray setup in FP64 (information only) */
     float tie_band;     /* half width of the termination tie band */
+    int32_t filter;     /* 0: trilinear; 1: uniform cubic B-spline */
 } orc_params;
+
+enum { ORC_TRILINEAR = 0, ORC_BSPLINE = 1 };
 
 /* ------------------------------------------------------------------------ */
 /* internal state                                                             */
@@ -100,8 +107,10 @@ typedef struct {
     float s[3];
     double vrange;          /* value of full scale: vmax (raw) or 1 (normalised) */
     double *lut;            /* value of each code, after the vmax clamp */
-    double *tf;             /* K x 4 */
+    double *tf;             /* M x K x 4 */
     int K;
+    int M;                  /* 1 for a 1-D table */
+    double gcoef;           /* 2-D: (M-1) / gmax in units of the stored values */
     float f[3], r[3], u[3], tx, ty, o[3];   /* FP32 camera record */
     double fd[3], rd[3], ud[3], txd, tyd, od[3];
     int W, H;
@@ -136,11 +145,15 @@ static int scene_init(scene *S, const orc_volume *vol, const orc_tf *tf,
     if (vol->nx < 2 || vol->ny < 2 || vol->nz < 2 || vol->vmax < 1) return 1;
     if (!(vol->sx > 0 && vol->sy > 0 && vol->sz > 0)) return 1;
     if (tf->K < 2 || cam->width < 1 || cam->height < 1) return 1;
+    if (tf->M >= 2 && !(tf->gmax > 0.0f)) return 1;
+    if (prm->filter != ORC_TRILINEAR && prm->filter != ORC_BSPLINE) return 1;
+    if (tf->M >= 2 && prm->func == ORC_THRESHOLD) return 3;   /* thresholding: 1-D tables only */
     S->v = vol->data;
     S->n[0] = vol->nx; S->n[1] = vol->ny; S->n[2] = vol->nz;
     S->s[0] = vol->sx; S->s[1] = vol->sy; S->s[2] = vol->sz;
     S->lut = (double *)malloc(65536 * sizeof(double));
-    S->tf = (double *)malloc((size_t)tf->K * 4 * sizeof(double));
+    S->M = tf->M >= 2 ? tf->M : 1;
+    S->tf = (double *)malloc((size_t)tf->K * S->M * 4 * sizeof(double));
     if (!S->lut || !S->tf) return 2;
     for (int code = 0; code < 65536; code++) {
         int c = code > vol->vmax ? vol->vmax : code;
@@ -148,8 +161,11 @@ static int scene_init(scene *S, const orc_volume *vol, const orc_tf *tf,
     }
     S->vrange = vol->value_mode ? 1.0 : (double)vol->vmax;
     S->K = tf->K;
-    for (int i = 0; i < 4 * tf->K; i++)
+    for (size_t i = 0; i < (size_t)4 * tf->K * S->M; i++)
         S->tf[i] = tf->fp16 ? half_round(tf->rgba[i]) : (double)tf->rgba[i];
+    /* the gradient coordinate is defined on code units: a normalised volume's
+     * gradient is scaled back by vmax */
+    S->gcoef = S->M >= 2 ? (double)(S->M - 1) * ((double)vol->vmax / S->vrange) / (double)tf->gmax : 0.0;
     S->P = *prm;
     S->W = cam->width; S->H = cam->height;
     S->smin = fminf(fminf(vol->sx, vol->sy), vol->sz);
@@ -328,6 +344,79 @@ static void gradient(const scene *S, const double p[3], double g[3]) {
     }
 }
 
+/* Uniform cubic B-spline reconstruction, the higher-order alternative to the
+ * trilinear filter (Sec. 3.2: quadratic or cubic filters for higher image
+ * quality). The textbook kernel
+ *   beta(x) = (4 - 6 x^2 + 3 |x|^3) / 6   for |x| < 1,
+ *             (2 - |x|)^3 / 6             for 1 <= |x| < 2,   0 beyond,
+ * is applied to the voxel values directly (no interpolating prefilter):
+ * f(p) = sum over voxels v of V(v) beta(p_x - v_x) beta(p_y - v_y) beta(p_z - v_z),
+ * with p clamped to the box and voxel indices outside it clamped to the
+ * nearest border voxel. Only the four voxels base-1 .. base+2 per axis around
+ * the trilinear cell base can have beta != 0. */
+static double bspline_beta(double x) {
+    double a = fabs(x);
+    if (a < 1.0) return (4.0 - 6.0 * a * a + 3.0 * a * a * a) / 6.0;
+    if (a < 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
+    return 0.0;
+}
+
+/* d beta / dx */
+static double bspline_dbeta(double x) {
+    double a = fabs(x), sg = x < 0.0 ? -1.0 : 1.0;
+    if (a < 1.0) return sg * (-12.0 * a + 9.0 * a * a) / 6.0;
+    if (a < 2.0) return -sg * (2.0 - a) * (2.0 - a) / 2.0;
+    return 0.0;
+}
+
+static int clampi(int i, int n) { return i < 0 ? 0 : (i > n - 1 ? n - 1 : i); }
+
+/* value and, when g != NULL, the analytic world-space gradient (value units
+ * per mm) of the B-spline field */
+static double bspline(const scene *S, const double p[3], double g[3]) {
+    double q[3], wb[3][4], wd[3][4];
+    int base[3];
+    for (int a = 0; a < 3; a++) {
+        double w;
+        cell(p[a], S->n[a], &base[a], &w);
+        q[a] = (double)base[a] + w;               /* the clamped position */
+        for (int o = 0; o < 4; o++) {
+            double x = q[a] - (double)(base[a] - 1 + o);
+            wb[a][o] = bspline_beta(x);
+            wd[a][o] = bspline_dbeta(x);
+        }
+    }
+    double f = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int oz = 0; oz < 4; oz++)
+        for (int oy = 0; oy < 4; oy++)
+            for (int ox = 0; ox < 4; ox++) {
+                double v = voxel(S, clampi(base[0] - 1 + ox, S->n[0]), clampi(base[1] - 1 + oy, S->n[1]),
+                                 clampi(base[2] - 1 + oz, S->n[2]));
+                f += v * wb[0][ox] * wb[1][oy] * wb[2][oz];
+                gx += v * wd[0][ox] * wb[1][oy] * wb[2][oz];
+                gy += v * wb[0][ox] * wd[1][oy] * wb[2][oz];
+                gz += v * wb[0][ox] * wb[1][oy] * wd[2][oz];
+            }
+    if (g) {
+        g[0] = gx / (double)S->s[0];
+        g[1] = gy / (double)S->s[1];
+        g[2] = gz / (double)S->s[2];
+    }
+    return f;
+}
+
+/* the reconstructed field at p under the selected filter */
+static double field(const scene *S, const double p[3]) {
+    return S->P.filter == ORC_BSPLINE ? bspline(S, p, NULL) : trilinear(S, p);
+}
+
+/* its world-space gradient: central differences of the trilinear field, the
+ * analytic derivative of the B-spline field */
+static void field_gradient(const scene *S, const double p[3], double g[3]) {
+    if (S->P.filter == ORC_BSPLINE) bspline(S, p, g);
+    else gradient(S, p, g);
+}
+
 /* ------------------------------------------------------------------------ */
 /* classification (Sec. 2.6) and shading                                      */
 /* ------------------------------------------------------------------------ */
@@ -342,6 +431,27 @@ static void classify(const scene *S, double u, double rgba[4], int *i0, double *
     for (int c = 0; c < 4; c++) rgba[c] = S->tf[4 * i + c] * (1 - w) + S->tf[4 * (i + 1) + c] * w;
     if (i0) *i0 = i;
     if (w0) *w0 = w;
+}
+
+/* Two-dimensional classification over (value, gradient magnitude), the
+ * boundary-emphasising transfer functions of Sec. 3.1: u is the value
+ * coordinate, w = |grad f| (M-1) / gmax the gradient-magnitude coordinate; each
+ * is clamped to its table axis and the four surrounding entries are blended
+ * bilinearly (value direction first, then gradient direction). */
+static void classify2(const scene *S, double u, double w, double rgba[4]) {
+    int K = S->K, M = S->M;
+    double qu = u < 0.0 ? 0.0 : (u > (double)(K - 1) ? (double)(K - 1) : u);
+    double qw = w < 0.0 ? 0.0 : (w > (double)(M - 1) ? (double)(M - 1) : w);
+    int i = (int)floor(qu), j = (int)floor(qw);
+    if (i > K - 2) i = K - 2;
+    if (j > M - 2) j = M - 2;
+    double a = qu - (double)i, b = qw - (double)j;
+    for (int c = 0; c < 4; c++) {
+        double t00 = S->tf[4 * ((size_t)j * K + i) + c], t10 = S->tf[4 * ((size_t)j * K + i + 1) + c];
+        double t01 = S->tf[4 * ((size_t)(j + 1) * K + i) + c], t11 = S->tf[4 * ((size_t)(j + 1) * K + i + 1) + c];
+        double r0 = t00 * (1 - a) + t10 * a, r1 = t01 * (1 - a) + t11 * a;
+        rgba[c] = r0 * (1 - b) + r1 * b;
+    }
 }
 
 /* headlight Blinn-Phong: light and view both along -dir, so the half vector is
@@ -373,19 +483,33 @@ static double correct_alpha(double a, double ratio) { return 1.0 - pow(1.0 - a, 
 /* all quantities of one sample */
 typedef struct {
     double t, p[3], v, u, rgba[4], a, col[3], dcol[3], w;
+    double gm, gw;      /* |grad f| (value units per mm) and its table coordinate (2-D) */
     int i;
 } sample;
 
 static void eval_sample(const scene *S, const ray *R, double t, double ratio, sample *s) {
     s->t = t;
     position_at_t(R, t, s->p);
-    s->v = trilinear(S, s->p);
+    s->v = field(S, s->p);
     s->u = tf_coord(S, s->v);
-    classify(S, s->u, s->rgba, &s->i, &s->w);
+    double g[3] = {0, 0, 0};
+    s->gm = 0.0;
+    s->gw = 0.0;
+    if (S->P.shade || S->M >= 2) {
+        field_gradient(S, s->p, g);
+        s->gm = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    }
+    if (S->M >= 2) {
+        s->gw = s->gm * S->gcoef;
+        classify2(S, s->u, s->gw, s->rgba);
+        s->i = -1;
+        s->w = 0.0;
+    } else {
+        classify(S, s->u, s->rgba, &s->i, &s->w);
+    }
     s->a = correct_alpha(s->rgba[3], ratio);
     if (S->P.shade) {
-        double g[3], dir[3];
-        gradient(S, s->p, g);
+        double dir[3];
         world_dir(R, dir);
         shade(S, s->rgba, g, dir, s->col, s->dcol);
     } else {
@@ -438,7 +562,7 @@ static void other_function(const scene *S, const ray *R, double out[4], int *nsa
     for (int k = 0; k < R->nsamp; k++) {
         double p[3], t = sample_t(R, k);
         position_at_t(R, t, p);
-        double v = trilinear(S, p);
+        double v = field(S, p);
         if (func == ORC_MIP) {
             if (k == 0 || v > acc) acc = v;
         } else if (func == ORC_AVERAGE || func == ORC_XRAY) {
@@ -453,7 +577,7 @@ static void other_function(const scene *S, const ray *R, double out[4], int *nsa
                 double ts = t;
                 if (k > 0) ts = prev_t + (t - prev_t) * ((double)S->P.iso - prev_v) / (v - prev_v);
                 double g[3], dir[3], white[3] = {1, 1, 1}, col[3], dcol[3];
-                gradient(S, p, g);
+                field_gradient(S, p, g);
                 world_dir(R, dir);
                 shade(S, white, g, dir, col, dcol);
                 out[0] = ts; out[1] = col[0]; out[2] = (double)k; out[3] = 1.0;
@@ -613,8 +737,10 @@ int orc_render(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
     return 0;
 }
 
-/* every sample of one ray, no termination; record of 14 doubles per sample:
- * t, px, py, pz, v, u, r, g, b, a, a', col r, col g, col b */
+/* every sample of one ray, no termination; record of 16 doubles per sample:
+ * t, px, py, pz, v, u, r, g, b, a, a', col r, col g, col b, |grad f|, w
+ * (|grad f| and its table coordinate w are 0 unless shading or a 2-D table
+ * needs the gradient) */
 int orc_ray_samples(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
                     const orc_params *prm, int x, int y, int max_samples, double *out,
                     int32_t *nsamp_total) {
@@ -628,11 +754,13 @@ int orc_ray_samples(const orc_volume *vol, const orc_tf *tf, const orc_camera *c
     for (int k = 0; R.hit && k < R.nsamp && k < max_samples; k++) {
         sample s;
         eval_sample(&S, &R, sample_t(&R, k), ratio, &s);
-        double *o = out + 14 * (size_t)k;
+        double *o = out + 16 * (size_t)k;
         o[0] = s.t; o[1] = s.p[0]; o[2] = s.p[1]; o[3] = s.p[2]; o[4] = s.v; o[5] = s.u;
         for (int c = 0; c < 4; c++) o[6 + c] = s.rgba[c];
         o[10] = s.a;
         for (int c = 0; c < 3; c++) o[11 + c] = s.col[c];
+        o[14] = s.gm;
+        o[15] = s.gw;
     }
     scene_free(&S);
     return 0;
@@ -731,6 +859,7 @@ int orc_render_grad(const orc_volume *vol, const orc_tf *tf, const orc_camera *c
     scene S;
     int rc = scene_init(&S, vol, tf, cam, prm);
     if (rc) { scene_free(&S); return rc; }
+    if (S.M >= 2) { scene_free(&S); return 3; }   /* gradient of 1-D tables only */
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     job J;
@@ -986,23 +1115,30 @@ int orc_proposal_features(const orc_volume *vol, const orc_tf *tf, const orc_cam
 /* ------------------------------------------------------------------------ */
 /* empty-space structures                                                     */
 /* ------------------------------------------------------------------------ */
-/* Cell-brick b along an axis holds the trilinear cells whose base index lies in
- * 16b..16b+15; its footprint is the voxels 16b..min(16b+16, n-1). There are
- * ceil((n-1)/16) cell-bricks per axis, x fastest. Values clamp to vmax. */
-void orc_brick_minmax(const orc_volume *vol, uint16_t *mn, uint16_t *mx) {
+/* Cell-brick b along an axis holds the cells whose base index lies in
+ * 16b..16b+15. A trilinear sample reads the voxels base..base+1, so the
+ * brick's footprint is the voxels 16b..min(16b+16, n-1); a B-spline sample
+ * reads base-1..base+2 (clamped), so its footprint is
+ * max(16b-1, 0)..min(16b+17, n-1). There are ceil((n-1)/16) cell-bricks per
+ * axis, x fastest. Values clamp to vmax. */
+void orc_brick_minmax_filter(const orc_volume *vol, int filter, uint16_t *mn, uint16_t *mx) {
     int n[3] = {vol->nx, vol->ny, vol->nz};
     int nb[3];
+    int before = filter == ORC_BSPLINE ? 1 : 0, after = filter == ORC_BSPLINE ? 17 : 16;
     for (int a = 0; a < 3; a++) nb[a] = (n[a] - 1 + 15) / 16;
     for (int bz = 0; bz < nb[2]; bz++)
         for (int by = 0; by < nb[1]; by++)
             for (int bx = 0; bx < nb[0]; bx++) {
                 int lo = 65535, hi = 0;
-                int z1 = 16 * bz + 16 < n[2] - 1 ? 16 * bz + 16 : n[2] - 1;
-                int y1 = 16 * by + 16 < n[1] - 1 ? 16 * by + 16 : n[1] - 1;
-                int x1 = 16 * bx + 16 < n[0] - 1 ? 16 * bx + 16 : n[0] - 1;
-                for (int z = 16 * bz; z <= z1; z++)
-                    for (int y = 16 * by; y <= y1; y++)
-                        for (int x = 16 * bx; x <= x1; x++) {
+                int z0 = 16 * bz - before > 0 ? 16 * bz - before : 0;
+                int y0 = 16 * by - before > 0 ? 16 * by - before : 0;
+                int x0 = 16 * bx - before > 0 ? 16 * bx - before : 0;
+                int z1 = 16 * bz + after < n[2] - 1 ? 16 * bz + after : n[2] - 1;
+                int y1 = 16 * by + after < n[1] - 1 ? 16 * by + after : n[1] - 1;
+                int x1 = 16 * bx + after < n[0] - 1 ? 16 * bx + after : n[0] - 1;
+                for (int z = z0; z <= z1; z++)
+                    for (int y = y0; y <= y1; y++)
+                        for (int x = x0; x <= x1; x++) {
                             int v = vol->data[((size_t)z * n[1] + y) * n[0] + x];
                             if (v > vol->vmax) v = vol->vmax;
                             if (v < lo) lo = v;
@@ -1014,6 +1150,10 @@ void orc_brick_minmax(const orc_volume *vol, uint16_t *mn, uint16_t *mx) {
             }
 }
 
+void orc_brick_minmax(const orc_volume *vol, uint16_t *mn, uint16_t *mx) {
+    orc_brick_minmax_filter(vol, ORC_TRILINEAR, mn, mx);
+}
+
 /* A brick is occupied unless every table entry a sample inside it can touch
  * has zero opacity. For values in [mn, mx] the lerp touches entries
  * lo = floor(u(mn)) .. hi = min(floor(u(mx)) + 1, K - 1), with the table
@@ -1021,7 +1161,9 @@ void orc_brick_minmax(const orc_volume *vol, uint16_t *mn, uint16_t *mx) {
  * c = fl((K - 1) / full scale): raw codes v with full scale vmax; FP16-
  * normalised values v = h(code), the FP16 rounding of the FP32 quotient
  * code / vmax, with full scale 1. u is monotone in v, so every sample inside
- * the brick has its coordinate in [u(mn), u(mx)]. */
+ * the brick has its coordinate in [u(mn), u(mx)]. With a 2-D table the
+ * gradient coordinate of a sample is not bounded by the grid, so every row of
+ * those entries must have zero opacity. */
 void orc_occupancy(const orc_volume *vol, const orc_tf *tf, const uint16_t *mn,
                    const uint16_t *mx, uint8_t *occ) {
     int nb = ((vol->nx - 1 + 15) / 16) * ((vol->ny - 1 + 15) / 16) * ((vol->nz - 1 + 15) / 16);
@@ -1039,10 +1181,13 @@ void orc_occupancy(const orc_volume *vol, const orc_tf *tf, const uint16_t *mn,
         if (hi > K - 1) hi = K - 1;
         if (lo > K - 1) lo = K - 1;
         int any = 0;
-        for (long i = lo; i <= hi; i++) {
-            double a = tf->fp16 ? half_round(tf->rgba[4 * i + 3]) : (double)tf->rgba[4 * i + 3];
-            if (a != 0.0) any = 1;
-        }
+        int rows = tf->M >= 2 ? tf->M : 1;
+        for (int j = 0; j < rows; j++)
+            for (long i = lo; i <= hi; i++) {
+                size_t e = 4 * ((size_t)j * K + (size_t)i) + 3;
+                double a = tf->fp16 ? half_round(tf->rgba[e]) : (double)tf->rgba[e];
+                if (a != 0.0) any = 1;
+            }
         occ[b] = (uint8_t)any;
     }
 }

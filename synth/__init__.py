@@ -188,6 +188,25 @@ def tf_table(K=256, points=DEFAULT_TF_POINTS, vmax=VMAX) -> np.ndarray:
     return np.clip(tab, 0.0, 1.0).astype(np.float32)
 
 
+def tf2d_table(K=256, M=32, gmax=1200.0, points=DEFAULT_TF_POINTS, vmax=VMAX, floor=0.3) -> np.ndarray:
+    """Two-dimensional table over (gradient magnitude, value): M rows of K
+    entries, float32 (M, K, 4); row j holds |grad f| = j*gmax/(M-1) codes per
+    mm, entry i the value i*vmax/(K-1). Colour is the 1-D table's; opacity is
+    the 1-D opacity times a boundary weight that rises from `floor` at
+    |grad f| = 0 to 1 at gmax/2 (smoothstep), so that tissue interfaces stand
+    out over homogeneous interiors. Rows are tinted slightly warmer with
+    gradient so the gradient axis changes colour as well as opacity."""
+    base = tf_table(K, points, vmax).astype(np.float64)
+    g = np.arange(M, dtype=np.float64) / (M - 1)
+    x = np.clip(g / 0.5, 0.0, 1.0)
+    wgt = floor + (1.0 - floor) * x * x * (3.0 - 2.0 * x)
+    tab = np.repeat(base[None], M, axis=0)
+    tab[..., 3] *= wgt[:, None]
+    tab[..., 0] = np.minimum(1.0, tab[..., 0] * (1.0 + 0.15 * g[:, None]))
+    tab[..., 2] *= (1.0 - 0.3 * g[:, None])
+    return np.clip(tab, 0.0, 1.0).astype(np.float32)
+
+
 def random_tf(K, seed, alpha_max=0.1, n_points=12, vmax=VMAX) -> np.ndarray:
     """Seeded smooth random table: n_points random control points over
     300..vmax (opacity 0 below 300), colours in [0,1], opacity in [0, alpha_max]."""
