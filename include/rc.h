@@ -68,6 +68,19 @@ typedef enum {
     RC_FUNC_XRAY = 3, RC_FUNC_ISO = 4, RC_FUNC_THRESHOLD = 5
 } rc_ray_function;
 
+/* Reconstruction filter of the resampling step (Sec. 4.1 step 2; Sec. 3.2
+ * names trilinear filtering and, for higher quality, cubic filters).
+ * TRILINEAR: 8 voxels per sample, gradient by central differences of the
+ * trilinear field (one index unit per axis).
+ * BSPLINE: uniform cubic B-spline on the voxel values (no interpolating
+ * prefilter, so it smooths): f(p) = sum over the 4 x 4 x 4 voxels around p of
+ * V * b(dx) b(dy) b(dz), b(x) = (4 - 6x^2 + 3|x|^3)/6 for |x| < 1,
+ * (2 - |x|)^3/6 for 1 <= |x| < 2; indices outside the volume take the
+ * nearest border voxel. Gradient: the analytic derivative of that sum. Every
+ * ray function supports it; the table gradient and the learned proposal do
+ * not (RC_ERR_UNSUPPORTED). */
+typedef enum { RC_FILTER_TRILINEAR = 0, RC_FILTER_BSPLINE = 1 } rc_filter;
+
 typedef struct rc_context rc_context;
 typedef struct rc_volume rc_volume;
 
@@ -93,7 +106,7 @@ typedef struct {
     int32_t func;       /* rc_ray_function */
     float iso;          /* iso-value / threshold, in the volume's code units */
     int32_t skip;       /* 1: skip bricks the occupancy mask marks empty (exact) */
-    int32_t reserved;   /* must be 0 */
+    int32_t filter;     /* rc_filter (0: trilinear) */
 } rc_render_params;
 
 typedef struct {
@@ -149,10 +162,30 @@ rc_status rc_tf_set(rc_context *ctx, const float *rgba, int n_entries, int fp16)
  * range-checked on this path. */
 rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries, int fp16);
 
+/* Two-dimensional transfer function over (value, gradient magnitude), the
+ * classification by scalar value and gradient magnitude that Sec. 3.1 cites
+ * for boundary emphasis. rgba: host memory, n_grad rows of n_values straight
+ * RGBA entries in [0, 1] (value index fastest: entry (i, j) at
+ * rgba[4 * (j * n_values + i)]); value entry i sits at code i*vmax/(n_values-1)
+ * as in rc_tf_set, row j at gradient magnitude j*gmax/(n_grad-1) codes per mm.
+ * A sample's gradient (central differences, or the B-spline derivative) gives
+ * the row coordinate w = fl(|g| * fl((n_grad-1) * vmax / (vscale * gmax))),
+ * clamped to [0, n_grad-1] (vscale: vmax, or 1 for F16 storage, whose
+ * gradient is in normalised units); the four entries around (u, w) blend
+ * bilinearly. n_values 2..4096, n_grad 2..4096, n_values * n_grad <= 2^20,
+ * gmax finite and > 0. fp16 = 1 rounds the entries to FP16. Replaces the
+ * current table (1-D or 2-D). Compositing and the ray functions that do not
+ * classify use it; thresholding, the table gradient and the learned proposal
+ * need a 1-D table (RC_ERR_UNSUPPORTED). Shading off still computes the
+ * gradient. Empty-space skipping stays exact: a brick is empty only when
+ * every row of its value entries has zero opacity. */
+rc_status rc_tf2d_set(rc_context *ctx, const float *rgba, int n_values, int n_grad, float gmax, int fp16);
+
 rc_status rc_camera_set(rc_context *ctx, const rc_camera *cam);
 
 /* Renders the current camera view of vol with the current transfer function
- * (Sec. 4.1-4.2): per pixel one ray, evenly spaced trilinear samples,
+ * (Sec. 4.1-4.2): per pixel one ray, evenly spaced samples reconstructed by
+ * params->filter,
  * classification, optional shading, front-to-back compositing with early
  * termination. out_rgba: device, width*height*4 floats, caller-owned,
  * overwritten. stats: optional host pointer; when given the call synchronises
@@ -202,6 +235,12 @@ rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol,
  * caller device buffers mn, mx. */
 rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *vol, uint16_t *mn, uint16_t *mx);
 
+/* The grid of a reconstruction filter: over the voxels its samples read,
+ * 16b .. min(16b+16, N-1) per axis for RC_FILTER_TRILINEAR (the grid of
+ * rc_brick_grid_get), max(16b-1, 0) .. min(16b+17, N-1) for RC_FILTER_BSPLINE. */
+rc_status rc_brick_grid_get_filter(rc_context *ctx, const rc_volume *vol, int filter, uint16_t *mn,
+                                   uint16_t *mx);
+
 /* Writes the occupancy mask of vol under the current transfer function into
  * caller device memory (one byte per cell-brick, 1 = may hold non-zero
  * opacity). A brick is empty when every table entry a sample inside it can
@@ -210,6 +249,15 @@ rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *vol, uint16_t *mn,
  * u(v) = fl(h * (K-1)) with h = fp16(fl(v / vmax)) for F16 storage (FP32
  * operations rounded once). */
 rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ);
+
+/* The mask of a reconstruction filter, from that filter's grid
+ * (rc_brick_grid_get_filter). With a 2-D table an entry counts as transparent
+ * only when it is transparent in every gradient row. The B-spline value is a
+ * convex combination of its footprint, so skipping stays exact up to the FP32
+ * rounding of the 64-term sum (a sample could leave its brick's value range
+ * by a few units in the last place; with 256-entry tables over 12-bit codes
+ * no coordinate lies that close below an entry boundary). */
+rc_status rc_skip_mask_get_filter(rc_context *ctx, const rc_volume *vol, int filter, uint8_t *occ);
 
 /* ---- learned sampling proposal -------------------------------------------
  * The paper marches evenly spaced samples (Sec. 4.1). This extension lets a

@@ -20,6 +20,7 @@ RC_OK, RC_ERR_INVALID_ARG, RC_ERR_OOM, RC_ERR_CUDA, RC_ERR_STATE, RC_ERR_TIMEOUT
     RC_ERR_UNSUPPORTED, RC_ERR_FORMAT = range(8)
 RC_STORE_F32, RC_STORE_F16, RC_STORE_U16 = range(3)
 RC_FUNC_COMPOSITE, RC_FUNC_MIP, RC_FUNC_AVERAGE, RC_FUNC_XRAY, RC_FUNC_ISO, RC_FUNC_THRESHOLD = range(6)
+RC_FILTER_TRILINEAR, RC_FILTER_BSPLINE = range(2)
 
 
 class RCError(RuntimeError):
@@ -36,7 +37,7 @@ class rc_camera(C.Structure):
 class rc_render_params(C.Structure):
     _fields_ = [("step_vox", C.c_float), ("term", C.c_float), ("shade", C.c_int32),
                 ("ka", C.c_float), ("kd", C.c_float), ("ks", C.c_float), ("func", C.c_int32),
-                ("iso", C.c_float), ("skip", C.c_int32), ("reserved", C.c_int32)]
+                ("iso", C.c_float), ("skip", C.c_int32), ("filter", C.c_int32)]
 
 
 class rc_stats(C.Structure):
@@ -66,6 +67,7 @@ SIGNATURES = {
     "rc_volume_brick_dims": (_I, [_P, C.POINTER(C.c_int * 3)]),
     "rc_tf_set": (_I, [_P, _P, _I, _I]),
     "rc_tf_set_device": (_I, [_P, _P, _I, _I]),
+    "rc_tf2d_set": (_I, [_P, _P, _I, _I, C.c_float, _I]),
     "rc_camera_set": (_I, [_P, C.POINTER(rc_camera)]),
     "rc_render": (_I, [_P, _P, C.POINTER(rc_render_params), _P, C.POINTER(rc_stats)]),
     "rc_render_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P,
@@ -74,6 +76,8 @@ SIGNATURES = {
     "rc_render_backward_noalloc": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
     "rc_brick_grid_get": (_I, [_P, _P, _P, _P]),
     "rc_skip_mask_get": (_I, [_P, _P, _P]),
+    "rc_brick_grid_get_filter": (_I, [_P, _P, _I, _P, _P]),
+    "rc_skip_mask_get_filter": (_I, [_P, _P, _I, _P]),
     "rc_proposal_load": (_I, [_P, _P, C.c_size_t]),
     "rc_proposal_save": (_I, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "rc_profiles_generate": (_I, [_P, _P, C.POINTER(rc_render_params), _P]),
@@ -191,6 +195,15 @@ def rc_tf_set(ctx, rgba, fp16=False):
     _check(lib().rc_tf_set(ctx, t.ctypes.data, t.shape[0], int(bool(fp16))), ctx, "rc_tf_set")
 
 
+def rc_tf2d_set(ctx, rgba, gmax, fp16=False):
+    """2-D table over (gradient magnitude, value): rgba of shape (n_grad, n_values, 4)."""
+    t = np.ascontiguousarray(rgba, dtype=np.float32)
+    if t.ndim != 3 or t.shape[2] != 4:
+        raise ValueError("rc_tf2d_set: rgba must have shape (n_grad, n_values, 4)")
+    _check(lib().rc_tf2d_set(ctx, t.ctypes.data, t.shape[1], t.shape[0], float(gmax), int(bool(fp16))), ctx,
+           "rc_tf2d_set")
+
+
 def rc_tf_set_device(ctx, rgba, fp16=False):
     _check(lib().rc_tf_set_device(ctx, _ptr(rgba), rgba.shape[0], int(bool(fp16))), ctx, "rc_tf_set_device")
 
@@ -217,10 +230,11 @@ class RenderParams:
     func: int = RC_FUNC_COMPOSITE
     iso: float = 0.0
     skip: bool = True
+    filter: int = RC_FILTER_TRILINEAR
 
     def c(self) -> rc_render_params:
         return rc_render_params(self.step_vox, self.term, int(bool(self.shade)), self.ka, self.kd,
-                                self.ks, int(self.func), self.iso, int(bool(self.skip)), 0)
+                                self.ks, int(self.func), self.iso, int(bool(self.skip)), int(self.filter))
 
 
 def _params(p):
@@ -279,6 +293,15 @@ def rc_brick_grid_get(ctx, vol, mn, mx):
 
 def rc_skip_mask_get(ctx, vol, occ):
     _check(lib().rc_skip_mask_get(ctx, vol, _ptr(occ)), ctx, "rc_skip_mask_get")
+
+
+def rc_brick_grid_get_filter(ctx, vol, filter, mn, mx):
+    _check(lib().rc_brick_grid_get_filter(ctx, vol, int(filter), _ptr(mn), _ptr(mx)), ctx,
+           "rc_brick_grid_get_filter")
+
+
+def rc_skip_mask_get_filter(ctx, vol, filter, occ):
+    _check(lib().rc_skip_mask_get_filter(ctx, vol, int(filter), _ptr(occ)), ctx, "rc_skip_mask_get_filter")
 
 
 # ---------------------------------------------------------------------------

@@ -24,6 +24,12 @@ struct rc_context {
     int K = 0;
     int tf_fp16 = 0;
     uint64_t tf_version = 0;
+    // 2-D table (M >= 2 while it is the current table; M = 0: 1-D)
+    float4 *d_tf2 = nullptr;
+    float *d_amax = nullptr;
+    long long tf2_cap = 0;
+    int M = 0;
+    float gmax = 0.0f;
     // camera
     bool cam_set = false;
     rc_camera cam{};
@@ -57,12 +63,13 @@ struct rc_volume {
     int nbricks = 0;             // cell-bricks
     void *d_data = nullptr;
     uint16_t *d_stage = nullptr;
-    uint16_t *d_mn = nullptr, *d_mx = nullptr;
-    uint8_t *d_occ = nullptr;
+    // min/max grid and occupancy mask per reconstruction filter (index rc_filter)
+    uint16_t *d_mn[2] = {nullptr, nullptr}, *d_mx[2] = {nullptr, nullptr};
+    uint8_t *d_occ[2] = {nullptr, nullptr};
     bool uploaded = false;
     uint64_t data_version = 0;
-    uint64_t occ_tf_version = ~0ull;
-    uint64_t occ_data_version = ~0ull;
+    uint64_t occ_tf_version[2] = {~0ull, ~0ull};
+    uint64_t occ_data_version[2] = {~0ull, ~0ull};
 };
 
 static thread_local char g_err[512];
@@ -180,6 +187,8 @@ rc_status rc_context_destroy(rc_context *ctx) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->d_tf32);
     cudaFree(ctx->d_tf16);
+    cudaFree(ctx->d_tf2);
+    cudaFree(ctx->d_amax);
     cudaFree(ctx->d_stats);
     cudaFree(ctx->d_cams);
     cudaFreeHost(ctx->h_stats);
@@ -201,9 +210,11 @@ rc_status rc_context_destroy(rc_context *ctx) {
 static void volume_free(rc_volume *v) {
     cudaFree(v->d_data);
     cudaFree(v->d_stage);
-    cudaFree(v->d_mn);
-    cudaFree(v->d_mx);
-    cudaFree(v->d_occ);
+    for (int f = 0; f < 2; f++) {
+        cudaFree(v->d_mn[f]);
+        cudaFree(v->d_mx[f]);
+        cudaFree(v->d_occ[f]);
+    }
 }
 
 rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, float sy, float sz, uint16_t vmax,
@@ -236,9 +247,12 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
     size_t nvox = (size_t)nx * ny * nz;
     if (dev_alloc(&v->d_data, (size_t)padded * esz) != cudaSuccess ||
         dev_alloc(&v->d_stage, nvox * sizeof(uint16_t)) != cudaSuccess ||
-        dev_alloc(&v->d_mn, v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
-        dev_alloc(&v->d_mx, v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
-        dev_alloc(&v->d_occ, v->nbricks) != cudaSuccess) {
+        dev_alloc(&v->d_mn[0], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_mx[0], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_occ[0], v->nbricks) != cudaSuccess ||
+        dev_alloc(&v->d_mn[1], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_mx[1], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_occ[1], v->nbricks) != cudaSuccess) {
         cudaGetLastError();
         volume_free(v);
         delete v;
@@ -279,7 +293,8 @@ rc_status rc_volume_upload(rc_volume *v, const uint16_t *src, size_t n_voxels, i
                                  src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     VolDev d = vol_dev(v);
     RC_CUDA(ctx, launch_relayout(v->d_stage, d, v->d_data, ctx->stream));
-    RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, v->d_mn, v->d_mx, ctx->stream));
+    for (int f = 0; f < 2; f++)
+        RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, f, v->d_mn[f], v->d_mx[f], ctx->stream));
     v->uploaded = true;
     v->data_version++;
     return RC_OK;
@@ -355,9 +370,31 @@ static rc_status tf_common(rc_context *ctx, const float *rgba, int K, int fp16, 
     RC_CUDA(ctx, cudaGetLastError());
     if (!dev) RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host source may be reused at once
     ctx->K = K;
+    ctx->M = 0;
     ctx->tf_fp16 = fp16 ? 1 : 0;
     ctx->tf_version++;
     return RC_OK;
+}
+
+// 2-D table: FP16 rounding of the entries in place (the FP16 table holds
+// exactly these values), and per value entry the largest opacity over the rows.
+__global__ void tf2_round_half_kernel(float4 *t, long long n) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float4 v = t[e];
+    v.x = __half2float(__float2half_rn(v.x));
+    v.y = __half2float(__float2half_rn(v.y));
+    v.z = __half2float(__float2half_rn(v.z));
+    v.w = __half2float(__float2half_rn(v.w));
+    t[e] = v;
+}
+
+__global__ void tf2_amax_kernel(const float4 *t, int K, int M, float *amax) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    float m = 0.0f;
+    for (int j = 0; j < M; j++) m = fmaxf(m, t[(size_t)j * K + i].w);
+    amax[i] = m;
 }
 
 rc_status rc_tf_set(rc_context *ctx, const float *rgba, int n_entries, int fp16) {
@@ -366,6 +403,51 @@ rc_status rc_tf_set(rc_context *ctx, const float *rgba, int n_entries, int fp16)
 
 rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries, int fp16) {
     return tf_common(ctx, rgba_dev, n_entries, fp16, true);
+}
+
+rc_status rc_tf2d_set(rc_context *ctx, const float *rgba, int K, int M, float gmax, int fp16) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_tf2d_set: ctx is NULL");
+    if (!rgba) return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: rgba is NULL");
+    if (K < 2 || K > 4096 || M < 2 || M > 4096 || (long long)K * M > (1ll << 20))
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: %d x %d entries (2..4096 each, at most 2^20)", K, M);
+    if (!(gmax > 0.0f) || !isfinite(gmax)) return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: gmax %g", (double)gmax);
+    const long long n = (long long)K * M;
+    for (long long i = 0; i < 4 * n; i++)
+        if (!(rgba[i] >= 0.0f && rgba[i] <= 1.0f))
+            return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: entry %lld channel %lld = %g outside [0, 1]", i / 4,
+                        i % 4, (double)rgba[i]);
+    DeviceScope ds(ctx->device);
+    if (n > ctx->tf2_cap) {
+        float4 *t = nullptr;
+        float *am = nullptr;
+        const long long cap = n;   // > K: also holds the K opacity maxima
+        if (dev_alloc(&t, (size_t)cap * sizeof(float4)) != cudaSuccess ||
+            dev_alloc(&am, (size_t)cap * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(t);
+            return fail(ctx, RC_ERR_OOM, "rc_tf2d_set: device allocation");
+        }
+        cudaStreamSynchronize(ctx->stream);   // queued kernels may still read the old table
+        cudaFree(ctx->d_tf2);
+        cudaFree(ctx->d_amax);
+        ctx->d_tf2 = t;
+        ctx->d_amax = am;
+        ctx->tf2_cap = cap;
+    }
+    RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_tf2, rgba, (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+    if (fp16) {
+        tf2_round_half_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_tf2, n);
+        RC_CUDA(ctx, cudaGetLastError());
+    }
+    tf2_amax_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_tf2, K, M, ctx->d_amax);
+    RC_CUDA(ctx, cudaGetLastError());
+    RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host source may be reused at once
+    ctx->K = K;
+    ctx->M = M;
+    ctx->gmax = gmax;
+    ctx->tf_fp16 = fp16 ? 1 : 0;
+    ctx->tf_version++;
+    return RC_OK;
 }
 
 static rc_status check_camera(rc_context *ctx, const rc_camera *cam, const char *who) {
@@ -447,7 +529,8 @@ static rc_status check_render(rc_context *ctx, const rc_volume *v, const rc_rend
     if (p->skip != 0 && p->skip != 1) return fail(ctx, RC_ERR_INVALID_ARG, "%s: skip %d", who, p->skip);
     if (p->func < RC_FUNC_COMPOSITE || p->func > RC_FUNC_THRESHOLD)
         return fail(ctx, RC_ERR_INVALID_ARG, "%s: func %d", who, p->func);
-    if (p->reserved != 0) return fail(ctx, RC_ERR_INVALID_ARG, "%s: reserved must be 0", who);
+    if (p->filter != RC_FILTER_TRILINEAR && p->filter != RC_FILTER_BSPLINE)
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: filter %d", who, p->filter);
     if (!isfinite(p->ka) || !isfinite(p->kd) || !isfinite(p->ks) || p->ka < 0 || p->kd < 0 || p->ks < 0 ||
         !isfinite(p->iso))
         return fail(ctx, RC_ERR_INVALID_ARG, "%s: shading weights / iso", who);
@@ -456,22 +539,49 @@ static rc_status check_render(rc_context *ctx, const rc_volume *v, const rc_rend
     if (!ctx->cam_set) return fail(ctx, RC_ERR_STATE, "%s: no camera (call rc_camera_set)", who);
     if (v->storage != RC_STORE_F16 && (long long)(ctx->K - 1) * v->vmax >= (1ll << 24))
         return fail(ctx, RC_ERR_UNSUPPORTED, "%s: (entries - 1) * vmax must stay below 2^24", who);
+    if (ctx->M >= 2 && p->func == RC_FUNC_THRESHOLD)
+        return fail(ctx, RC_ERR_UNSUPPORTED, "%s: thresholding classifies with a 1-D table only", who);
     return RC_OK;
 }
 
-// The table with its coordinate coefficient fl((K-1) / vscale) for volume v.
-static TFDev tf_dev(const rc_context *ctx, const rc_volume *v) {
-    const float vscale = v->storage == RC_STORE_F16 ? 1.0f : (float)v->vmax;
-    return TFDev{ctx->d_tf32, ctx->d_tf16, ctx->K, ctx->tf_fp16, (float)(ctx->K - 1) / vscale};
+// The table gradient and the learned proposal march trilinear samples
+// classified by a 1-D table.
+static rc_status check_plain_form(rc_context *ctx, const rc_render_params *p, const char *who) {
+    if (p->filter != RC_FILTER_TRILINEAR)
+        return fail(ctx, RC_ERR_UNSUPPORTED, "%s: trilinear reconstruction only", who);
+    if (ctx->M >= 2) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: 1-D transfer function only", who);
+    return RC_OK;
 }
 
-static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v) {
-    if (v->occ_tf_version == ctx->tf_version && v->occ_data_version == v->data_version) return RC_OK;
+// The table with its coordinate coefficients for volume v: u = fl(v * fl((K-1) / vscale)),
+// and for a 2-D table w = fl(|g| * fl((M-1) * vmax / (vscale * gmax))).
+static TFDev tf_dev(const rc_context *ctx, const rc_volume *v) {
+    const float vscale = v->storage == RC_STORE_F16 ? 1.0f : (float)v->vmax;
+    TFDev t{};
+    t.K = ctx->K;
+    t.fp16 = ctx->tf_fp16;
+    t.ucoef = (float)(ctx->K - 1) / vscale;
+    if (ctx->M >= 2) {
+        t.tab2 = ctx->d_tf2;
+        t.amax = ctx->d_amax;
+        t.M = ctx->M;
+        t.wcoef = (float)((double)(ctx->M - 1) * (double)v->vmax / ((double)vscale * (double)ctx->gmax));
+    } else {
+        t.f32 = ctx->d_tf32;
+        t.f16 = ctx->d_tf16;
+    }
+    return t;
+}
+
+// The occupancy mask of filter f under the current table, rebuilt when the
+// table or the data changed since it was last built.
+static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v, int f) {
+    if (v->occ_tf_version[f] == ctx->tf_version && v->occ_data_version[f] == v->data_version) return RC_OK;
     TFDev tf = tf_dev(ctx, v);
-    RC_CUDA(ctx, launch_occupancy(v->d_mn, v->d_mx, v->nbricks, v->vmax, v->storage == RC_STORE_F16, tf,
-                                  v->d_occ, ctx->stream));
-    v->occ_tf_version = ctx->tf_version;
-    v->occ_data_version = v->data_version;
+    RC_CUDA(ctx, launch_occupancy(v->d_mn[f], v->d_mx[f], v->nbricks, v->vmax, v->storage == RC_STORE_F16, tf,
+                                  v->d_occ[f], ctx->stream));
+    v->occ_tf_version[f] = ctx->tf_version;
+    v->occ_data_version[f] = v->data_version;
     return RC_OK;
 }
 
@@ -509,7 +619,8 @@ static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render
     float ds = p->step_vox * a.vol.smin;
     a.p.ratio = ds / a.vol.smin;
     a.p.rmode = a.p.ratio == 1.0f ? 0 : a.p.ratio == 0.5f ? 1 : a.p.ratio == 0.25f ? 2 : 3;
-    a.occ = v->d_occ;
+    a.p.filter = p->filter;
+    a.occ = v->d_occ[p->filter];
     a.out = reinterpret_cast<float4 *>(out);
     a.stats = nullptr;
     a.cams = nullptr;
@@ -523,7 +634,7 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
     DeviceScope ds(ctx->device);
     rc_volume *v = const_cast<rc_volume *>(vol);
     if (p->skip && p->func == RC_FUNC_COMPOSITE) {
-        st = ensure_occupancy(ctx, v);
+        st = ensure_occupancy(ctx, v, p->filter);
         if (st != RC_OK) return st;
     }
     MarchArgs a = march_args(ctx, v, p, out_rgba);
@@ -570,7 +681,7 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
     }
     rc_volume *v = const_cast<rc_volume *>(vol);
     if (p->skip && p->func == RC_FUNC_COMPOSITE) {
-        st = ensure_occupancy(ctx, v);
+        st = ensure_occupancy(ctx, v, p->filter);
         if (st != RC_OK) return st;
     }
     CamRec *recs = new (std::nothrow) CamRec[nviews];
@@ -596,6 +707,7 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
 rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
                              const float *dL_dimage, float *dL_dtf) {
     rc_status st = check_render(ctx, vol, p, dL_dtf, "rc_render_backward");
+    if (st == RC_OK) st = check_plain_form(ctx, p, "rc_render_backward");
     if (st != RC_OK) return st;
     if (!dL_dimage) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_backward: dL_dimage is NULL");
     if (p->func != RC_FUNC_COMPOSITE)
@@ -610,7 +722,7 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_ren
         ctx->d_scratch = buf;
         ctx->scratch_bytes = need;
     }
-    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol));
+    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol), RC_FILTER_TRILINEAR);
     if (st != RC_OK) return st;
     AdjointArgs a;
     a.m = march_args(ctx, vol, p, nullptr);
@@ -662,6 +774,7 @@ extern "C" {
 rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
                                      const float *dL_dimage, float *dL_dtf) {
     rc_status st = check_render(ctx, vol, p, dL_dtf, "rc_render_backward_noalloc");
+    if (st == RC_OK) st = check_plain_form(ctx, p, "rc_render_backward_noalloc");
     if (st != RC_OK) return st;
     if (!dL_dimage) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_backward_noalloc: dL_dimage is NULL");
     if (p->func != RC_FUNC_COMPOSITE)
@@ -674,7 +787,7 @@ rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, cons
     long long *scratch = nullptr;
     st = noalloc_scratch(ctx, &scratch);
     if (st != RC_OK) return st;
-    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol));
+    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol), RC_FILTER_TRILINEAR);
     if (st != RC_OK) return st;
     AdjointArgs a;
     a.m = march_args(ctx, vol, p, nullptr);
@@ -686,27 +799,41 @@ rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, cons
     return RC_OK;
 }
 
-rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *v, uint16_t *mn, uint16_t *mx) {
+rc_status rc_brick_grid_get_filter(rc_context *ctx, const rc_volume *v, int filter, uint16_t *mn, uint16_t *mx) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_brick_grid_get: ctx is NULL");
     if (!v || !mn || !mx) return fail(ctx, RC_ERR_INVALID_ARG, "rc_brick_grid_get: NULL argument");
+    if (filter != RC_FILTER_TRILINEAR && filter != RC_FILTER_BSPLINE)
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_brick_grid_get: filter %d", filter);
     if (!v->uploaded) return fail(ctx, RC_ERR_STATE, "rc_brick_grid_get: volume has no data");
     DeviceScope ds(ctx->device);
-    RC_CUDA(ctx, cudaMemcpyAsync(mn, v->d_mn, v->nbricks * sizeof(uint16_t), cudaMemcpyDeviceToDevice, ctx->stream));
-    RC_CUDA(ctx, cudaMemcpyAsync(mx, v->d_mx, v->nbricks * sizeof(uint16_t), cudaMemcpyDeviceToDevice, ctx->stream));
+    RC_CUDA(ctx, cudaMemcpyAsync(mn, v->d_mn[filter], v->nbricks * sizeof(uint16_t), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    RC_CUDA(ctx, cudaMemcpyAsync(mx, v->d_mx[filter], v->nbricks * sizeof(uint16_t), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
     return RC_OK;
 }
 
-rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ) {
+rc_status rc_brick_grid_get(rc_context *ctx, const rc_volume *v, uint16_t *mn, uint16_t *mx) {
+    return rc_brick_grid_get_filter(ctx, v, RC_FILTER_TRILINEAR, mn, mx);
+}
+
+rc_status rc_skip_mask_get_filter(rc_context *ctx, const rc_volume *vol, int filter, uint8_t *occ) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_skip_mask_get: ctx is NULL");
     if (!vol || !occ) return fail(ctx, RC_ERR_INVALID_ARG, "rc_skip_mask_get: NULL argument");
+    if (filter != RC_FILTER_TRILINEAR && filter != RC_FILTER_BSPLINE)
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_skip_mask_get: filter %d", filter);
     if (!vol->uploaded) return fail(ctx, RC_ERR_STATE, "rc_skip_mask_get: volume has no data");
     if (ctx->K < 2) return fail(ctx, RC_ERR_STATE, "rc_skip_mask_get: no transfer function");
     DeviceScope ds(ctx->device);
     rc_volume *v = const_cast<rc_volume *>(vol);
-    rc_status st = ensure_occupancy(ctx, v);
+    rc_status st = ensure_occupancy(ctx, v, filter);
     if (st != RC_OK) return st;
-    RC_CUDA(ctx, cudaMemcpyAsync(occ, v->d_occ, v->nbricks, cudaMemcpyDeviceToDevice, ctx->stream));
+    RC_CUDA(ctx, cudaMemcpyAsync(occ, v->d_occ[filter], v->nbricks, cudaMemcpyDeviceToDevice, ctx->stream));
     return RC_OK;
+}
+
+rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ) {
+    return rc_skip_mask_get_filter(ctx, vol, RC_FILTER_TRILINEAR, occ);
 }
 
 // ---------------------------------------------------------------------------
@@ -810,11 +937,12 @@ rc_status rc_proposal_save(rc_context *ctx, void *blob, size_t capacity, size_t 
 
 rc_status rc_profiles_generate(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, float *out) {
     rc_status st = check_render(ctx, vol, p, out, "rc_profiles_generate");
+    if (st == RC_OK) st = check_plain_form(ctx, p, "rc_profiles_generate");
     if (st != RC_OK) return st;
     DeviceScope ds(ctx->device);
     rc_volume *v = const_cast<rc_volume *>(vol);
     if (p->skip) {
-        st = ensure_occupancy(ctx, v);
+        st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
         if (st != RC_OK) return st;
     }
     MarchArgs a = march_args(ctx, v, p, nullptr);
@@ -824,10 +952,11 @@ rc_status rc_profiles_generate(rc_context *ctx, const rc_volume *vol, const rc_r
 
 rc_status rc_proposal_features(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, float *out) {
     rc_status st = check_render(ctx, vol, p, out, "rc_proposal_features");
+    if (st == RC_OK) st = check_plain_form(ctx, p, "rc_proposal_features");
     if (st != RC_OK) return st;
     DeviceScope ds(ctx->device);
     rc_volume *v = const_cast<rc_volume *>(vol);
-    st = ensure_occupancy(ctx, v);
+    st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
     if (st != RC_OK) return st;
     MarchArgs a = march_args(ctx, v, p, nullptr);
     RC_CUDA(ctx, launch_features(a, out, ctx->stream));
@@ -907,13 +1036,14 @@ static rc_status importance_common(rc_context *ctx, const rc_volume *vol, const 
                                    const float *that, int nimp, float eps, float *out, uint8_t *fallback,
                                    rc_stats *stats, const char *who) {
     rc_status st = check_render(ctx, vol, p, out, who);
+    if (st == RC_OK) st = check_plain_form(ctx, p, who);
     if (st != RC_OK) return st;
     if (p->func != RC_FUNC_COMPOSITE) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: compositing function only", who);
     if (nimp < 1 || nimp > 4096) return fail(ctx, RC_ERR_INVALID_ARG, "%s: nimp %d", who, nimp);
     if (!(eps >= 0.0f)) return fail(ctx, RC_ERR_INVALID_ARG, "%s: eps %g", who, (double)eps);
     DeviceScope ds(ctx->device);
     rc_volume *v = const_cast<rc_volume *>(vol);
-    st = ensure_occupancy(ctx, v);
+    st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
     if (st != RC_OK) return st;
     ImportanceArgs a;
     a.m = march_args(ctx, v, p, out);

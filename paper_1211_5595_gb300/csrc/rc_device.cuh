@@ -175,6 +175,105 @@ __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, floa
     return val;
 }
 
+// Uniform cubic B-spline reconstruction (Sec. 3.2's higher-order filter):
+// f(p) = sum of the 4 x 4 x 4 voxels i-1 .. i+2 around cell base i, each
+// weighted by the product of the B-spline kernel at its per-axis distance.
+// With t the cell fraction, the four weights of an axis are
+//   (1-t)^3/6,  t^3/2 - t^2 + 2/3,  -t^3/2 + t^2/2 + t/2 + 1/6,  t^3/6
+// and their derivatives -(1-t)^2/2, 3t^2/2 - 2t, -3t^2/2 + t + 1/2, t^2/2.
+// The apron brick holds exactly this footprint (its replicated border voxels
+// are the clamped indices), so the 64 voxels are one base address plus
+// constant offsets.
+__device__ __forceinline__ void bspline_weights(float t, float w[4]) {
+    const float s = 1.0f - t, t2 = t * t;
+    w[0] = s * s * s * (1.0f / 6.0f);
+    w[1] = __fmaf_rn(t2, __fmaf_rn(0.5f, t, -1.0f), 2.0f / 3.0f);
+    w[2] = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(-0.5f, t, 0.5f), 0.5f), 1.0f / 6.0f);
+    w[3] = t2 * t * (1.0f / 6.0f);
+}
+
+__device__ __forceinline__ void bspline_dweights(float t, float d[4]) {
+    const float s = 1.0f - t;
+    d[0] = -0.5f * s * s;
+    d[1] = t * __fmaf_rn(1.5f, t, -2.0f);
+    d[2] = __fmaf_rn(t, __fmaf_rn(-1.5f, t, 1.0f), 0.5f);
+    d[3] = 0.5f * t * t;
+}
+
+// Address of voxel (i-1, j-1, k-1) of the cell's apron brick.
+__device__ __forceinline__ unsigned cubic_origin(const VolDev &v, const Cell &c) {
+    return cell_address(v, c) - kDX - kDY - kDZ;
+}
+
+template <int ST>
+__device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
+    const unsigned a = cubic_origin(v, c);
+    float wx[4], wy[4], wz[4];
+    bspline_weights(c.w[0], wx);
+    bspline_weights(c.w[1], wy);
+    bspline_weights(c.w[2], wz);
+    float f = 0.0f;
+#pragma unroll
+    for (int oz = 0; oz < 4; oz++) {
+        float fz = 0.0f;
+#pragma unroll
+        for (int oy = 0; oy < 4; oy++) {
+            const unsigned r = a + oz * kDZ + oy * kDY;
+            float fx = fetch<ST>(v, r) * wx[0];
+            fx = __fmaf_rn(fetch<ST>(v, r + 1), wx[1], fx);
+            fx = __fmaf_rn(fetch<ST>(v, r + 2), wx[2], fx);
+            fx = __fmaf_rn(fetch<ST>(v, r + 3), wx[3], fx);
+            fz = __fmaf_rn(fx, wy[oy], fz);
+        }
+        f = __fmaf_rn(fz, wz[oz], f);
+    }
+    return f;
+}
+
+// Value and analytic world-space gradient (value units per mm) of the
+// B-spline field: d/dx sums the same voxels with the x weights replaced by
+// their derivatives; 1/s = 2 * (0.5/s) exactly.
+template <int ST>
+__device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, float g[3]) {
+    const unsigned a = cubic_origin(v, c);
+    float wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
+    bspline_weights(c.w[0], wx);
+    bspline_weights(c.w[1], wy);
+    bspline_weights(c.w[2], wz);
+    bspline_dweights(c.w[0], dx);
+    bspline_dweights(c.w[1], dy);
+    bspline_dweights(c.w[2], dz);
+    float f = 0.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+    for (int oz = 0; oz < 4; oz++) {
+        float fz = 0.0f, gxz = 0.0f, gyz = 0.0f;
+#pragma unroll
+        for (int oy = 0; oy < 4; oy++) {
+            const unsigned r = a + oz * kDZ + oy * kDY;
+            const float v0 = fetch<ST>(v, r), v1 = fetch<ST>(v, r + 1), v2 = fetch<ST>(v, r + 2),
+                        v3 = fetch<ST>(v, r + 3);
+            float fx = v0 * wx[0], ex = v0 * dx[0];
+            fx = __fmaf_rn(v1, wx[1], fx);
+            ex = __fmaf_rn(v1, dx[1], ex);
+            fx = __fmaf_rn(v2, wx[2], fx);
+            ex = __fmaf_rn(v2, dx[2], ex);
+            fx = __fmaf_rn(v3, wx[3], fx);
+            ex = __fmaf_rn(v3, dx[3], ex);
+            fz = __fmaf_rn(fx, wy[oy], fz);
+            gxz = __fmaf_rn(ex, wy[oy], gxz);
+            gyz = __fmaf_rn(fx, dy[oy], gyz);
+        }
+        f = __fmaf_rn(fz, wz[oz], f);
+        gx = __fmaf_rn(gxz, wz[oz], gx);
+        gy = __fmaf_rn(gyz, wz[oz], gy);
+        gz = __fmaf_rn(fz, dz[oz], gz);
+    }
+    g[0] = gx * (2.0f * v.inv2s[0]);
+    g[1] = gy * (2.0f * v.inv2s[1]);
+    g[2] = gz * (2.0f * v.inv2s[2]);
+    return f;
+}
+
 // Table coordinate u = fl(v * fl((K-1) / vscale)): one rounded FP32 multiply,
 // monotone in v. The occupancy mask floors the same function at a brick's
 // integer min and max, which makes skipping exact.
@@ -190,6 +289,27 @@ __device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, in
     if (i0) *i0 = i;
     if (w0) *w0 = w;
     return make_float4(lerp(a.x, b.x, w), lerp(a.y, b.y, w), lerp(a.z, b.z, w), lerp(a.w, b.w, w));
+}
+
+__device__ __forceinline__ float4 lerp4(const float4 &a, const float4 &b, float w) {
+    return make_float4(lerp(a.x, b.x, w), lerp(a.y, b.y, w), lerp(a.z, b.z, w), lerp(a.w, b.w, w));
+}
+
+// Two-dimensional classification over (value, gradient magnitude), the
+// scalar / gradient-magnitude transfer functions of Sec. 3.1: u the value
+// coordinate, w = fl(|grad| * wcoef) the gradient coordinate, each clamped to
+// its axis; bilinear over the four entries (value direction first). The
+// table stays in global memory (read-only path; at most a few MB).
+__device__ __forceinline__ float4 classify2(const TFDev &tf, float u, float w) {
+    const int K = tf.K, M = tf.M;
+    const float qu = fminf(fmaxf(u, 0.0f), (float)(K - 1));
+    const float qw = fminf(fmaxf(w, 0.0f), (float)(M - 1));
+    const int i = min((int)qu, K - 2), j = min((int)qw, M - 2);
+    const float a = qu - (float)i, b = qw - (float)j;
+    const float4 *p = tf.tab2 + (size_t)j * K + i;
+    const float4 r0 = lerp4(__ldg(p), __ldg(p + 1), a);
+    const float4 r1 = lerp4(__ldg(p + K), __ldg(p + K + 1), a);
+    return lerp4(r0, r1, b);
 }
 
 // Eq. 3 for a segment of length ds: alpha' = 1 - (1 - alpha)^(ds/ds_ref).
@@ -236,14 +356,30 @@ __device__ __forceinline__ void load_tf(const TFDev &tf, float4 *s_tf) {
 // correct the opacity to the segment, shade. Returns straight colour and
 // corrected opacity; the caller composites. Shared by every march so that the
 // plain, fallback and importance marches evaluate a sample identically.
-template <int ST, bool SHADE>
-__device__ __forceinline__ float4 eval_sample(const VolDev &vol, const MarchParams &P, const float4 *s_tf, int K,
-                                              float ucoef, const float dir[3], const Cell &c, int rmode,
-                                              float ratio) {
+// F: kShade, kCubic (B-spline instead of trilinear), kTF2 (2-D table from
+// tf.tab2, else the 1-D table s_tf); the gradient is computed when shading or
+// the 2-D table needs it.
+template <int ST, int F>
+__device__ __forceinline__ float4 eval_sample_x(const VolDev &vol, const MarchParams &P, const float4 *s_tf,
+                                                const TFDev &tf, const float dir[3], const Cell &c, int rmode,
+                                                float ratio) {
+    constexpr bool SHADE = (F & kShade) != 0, CUBIC = (F & kCubic) != 0, TF2 = (F & kTF2) != 0;
+    constexpr bool GRAD = SHADE || TF2;
     float val, g[3];
-    if (SHADE) val = value_grad<ST>(vol, c, g);
-    else val = trilinear<ST>(vol, c);
-    float4 e = classify(s_tf, K, tf_coord(val, ucoef));
+    if (CUBIC) {
+        if (GRAD) val = bspline_grad<ST>(vol, c, g);
+        else val = bspline<ST>(vol, c);
+    } else {
+        if (GRAD) val = value_grad<ST>(vol, c, g);
+        else val = trilinear<ST>(vol, c);
+    }
+    float4 e;
+    if (TF2) {
+        const float gm = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        e = classify2(tf, tf_coord(val, tf.ucoef), __fmul_rn(gm, tf.wcoef));
+    } else {
+        e = classify(s_tf, tf.K, tf_coord(val, tf.ucoef));
+    }
     float ap = correct_alpha(e.w, rmode, ratio);
     if (SHADE) {
         float sf, spec;
@@ -254,6 +390,17 @@ __device__ __forceinline__ float4 eval_sample(const VolDev &vol, const MarchPara
     }
     e.w = ap;
     return e;
+}
+
+// The trilinear, 1-D-table sample of the marches that support only that form.
+template <int ST, bool SHADE>
+__device__ __forceinline__ float4 eval_sample(const VolDev &vol, const MarchParams &P, const float4 *s_tf, int K,
+                                              float ucoef, const float dir[3], const Cell &c, int rmode,
+                                              float ratio) {
+    TFDev tf{};
+    tf.K = K;
+    tf.ucoef = ucoef;
+    return eval_sample_x<ST, SHADE ? kShade : 0>(vol, P, s_tf, tf, dir, c, rmode, ratio);
 }
 
 // Front-to-back compositing of one sample (Eq. 4): C += T a' c, T *= 1 - a'.

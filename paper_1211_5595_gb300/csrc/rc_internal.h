@@ -35,13 +35,26 @@ struct VolDev {
     int vmax;
 };
 
-// Transfer function: K entries of straight RGBA, FP32 or FP16 in device memory.
+// Transfer function: K entries of straight RGBA, FP32 or FP16 in device memory
+// (1-D), or M rows of K entries over (gradient magnitude, value) (2-D).
 struct TFDev {
     const float4 *f32;
     const uint2 *f16;      // 4 halves per entry
     int K;
     int fp16;
     float ucoef;           // table coordinate per stored value: fl((K-1) / vscale)
+    // 2-D table (M >= 2; M = 0 for a 1-D table)
+    const float4 *tab2;    // [M][K] FP32 (entries already FP16-rounded for an FP16 table)
+    const float *amax;     // K: largest opacity of each value entry over the M rows
+    int M;
+    float wcoef;           // gradient coordinate per unit of |grad| (stored value units per mm)
+};
+
+// Sample evaluation variants of the compositing march.
+enum : int {
+    kShade = 1,            // headlight Blinn-Phong
+    kCubic = 2,            // cubic B-spline reconstruction (else trilinear)
+    kTF2 = 4               // 2-D table over (value, gradient magnitude)
 };
 
 struct MarchParams {
@@ -53,6 +66,7 @@ struct MarchParams {
     int skip;
     float ratio;           // ds / ds_ref
     int rmode;             // opacity correction: 0 identity, 1 sqrt, 2 sqrt(sqrt), 3 powf
+    int filter;            // rc_filter
 };
 
 struct MarchArgs {
@@ -124,11 +138,13 @@ struct TrainArgs {
 
 // ---- launchers (return the launch error) --------------------------------
 cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStream_t s);
-cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax,
+cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax, int filter,
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);
 cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax,
                              int f16_values, TFDev tf, uint8_t *occ, cudaStream_t s);
 cudaError_t launch_march(const MarchArgs &a, int nviews, cudaStream_t s);
+cudaError_t launch_march_cubic(const MarchArgs &a, int nviews, cudaStream_t s);   // filter = B-spline
+cudaError_t launch_march_tf2(const MarchArgs &a, int nviews, cudaStream_t s);     // trilinear, 2-D table
 cudaError_t launch_adjoint(const AdjointArgs &a, float *dL_dtf, cudaStream_t s);
 cudaError_t launch_absmax(const float *x, long long n, float *out, cudaStream_t s);
 cudaError_t launch_profiles(const MarchArgs &a, float *out, cudaStream_t s);

@@ -1,163 +1,16 @@
-// Forward march (Sec. 4.1-4.2): one thread per ray, warps on 8 x 4 pixel tiles,
-// bricked volume gathers through the read-only path, transfer function in
-// shared memory, exact empty-space skipping over the cell-brick occupancy mask
-// and warp-vote early ray termination.
-#include "rc_device.cuh"
+// Forward march, trilinear reconstruction with the 1-D table: the kernel
+// instances of the plain and shaded compositing march and of the other ray
+// functions, and the dispatch over every form.
+#include "rc_march.cuh"
 
 namespace rc {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ void pixel_of_thread(int &x, int &y) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-}
-
-__device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned dense, unsigned evald,
-                                          unsigned hit, unsigned inimg) {
-    dense = __reduce_add_sync(kFull, dense);
-    evald = __reduce_add_sync(kFull, evald);
-    hit = __reduce_add_sync(kFull, hit);
-    inimg = __reduce_add_sync(kFull, inimg);
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(stats + 0, (unsigned long long)dense);
-        atomicAdd(stats + 1, (unsigned long long)evald);
-        atomicAdd(stats + 2, (unsigned long long)hit);
-        atomicAdd(stats + 3, (unsigned long long)inimg);
-    }
-}
-
-// Compositing ray function (Sec. 4.2, Eq. 4): C += T a' c, T *= (1 - a'),
-// front to back from the eye; stop after the sample where 1 - T >= term.
-template <int ST, bool SHADE>
-__global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
-    extern __shared__ float4 s_tf[];
-    load_tf(a.tf, s_tf);
-    __syncthreads();
-    const CamRec cam = a.cams ? a.cams[blockIdx.z] : a.cam;
-    float4 *out = a.out + (size_t)blockIdx.z * cam.W * cam.H;
-    int x, y;
-    pixel_of_thread(x, y);
-    const bool inimg = x < cam.W && y < cam.H;
-    Ray R;
-    const bool hit = inimg && setup_ray(cam, a.vol, a.p.step_vox, x, y, R);
-    const int nsamp = hit ? R.nsamp : 0;
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
-    int k = 0;
-    unsigned evald = 0;
-    bool active = nsamp > 0;
-    while (__any_sync(kFull, active)) {
-        if (!active) continue;
-        float p[3];
-        position_at(R, sample_t(R, k), p);
-        Cell c;
-        cell_of(a.vol, p, c);
-        if (a.p.skip && !__ldg(a.occ + brick_of(a.vol, c))) {
-            k = jump_empty(R, a.vol, c, k);
-            active = k < nsamp;
-            continue;
-        }
-        float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, a.p.rmode, a.p.ratio);
-        composite_add(e, C0, C1, C2, T);
-        evald++;
-        k++;
-        active = k < nsamp && (1.0f - T) < a.p.term;
-    }
-    if (inimg) out[(size_t)y * cam.W + x] = make_float4(C0, C1, C2, 1.0f - T);
-    if (a.stats) add_stats(a.stats, (unsigned)min(k, nsamp), evald, hit ? 1u : 0u, inimg ? 1u : 0u);
-}
-
-// The other ray functions of Sec. 4.1 (MIP, average, x-ray, isosurface,
-// threshold); output channels as documented in rc.h.
-template <int ST>
-__global__ void __launch_bounds__(128) function_kernel(const MarchArgs a) {
-    extern __shared__ float4 s_tf[];
-    load_tf(a.tf, s_tf);
-    __syncthreads();
-    const CamRec cam = a.cams ? a.cams[blockIdx.z] : a.cam;
-    float4 *outp = a.out + (size_t)blockIdx.z * cam.W * cam.H;
-    int x, y;
-    pixel_of_thread(x, y);
-    const bool inimg = x < cam.W && y < cam.H;
-    Ray R;
-    const bool hit = inimg && setup_ray(cam, a.vol, a.p.step_vox, x, y, R);
-    const int nsamp = hit ? R.nsamp : 0;
-    const int func = a.p.func;
-    float4 out = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    float acc = 0.0f, prev_v = 0.0f, prev_t = 0.0f;
-    int k = 0;
-    bool found = false;
-    for (; k < nsamp; k++) {
-        float t = sample_t(R, k), p[3];
-        position_at(R, t, p);
-        Cell c;
-        cell_of(a.vol, p, c);
-        float v = trilinear<ST>(a.vol, c);
-        if (func == RC_FUNC_MIP) {
-            acc = k == 0 ? v : fmaxf(acc, v);
-        } else if (func == RC_FUNC_AVERAGE || func == RC_FUNC_XRAY) {
-            acc += v;
-        } else if (v >= a.p.iso) {
-            found = true;
-            if (func == RC_FUNC_THRESHOLD) {
-                float4 e = classify(s_tf, a.tf.K, tf_coord(v, a.tf.ucoef));
-                out = make_float4(e.x, e.y, e.z, 1.0f);
-            } else {
-                float ts = k > 0 ? prev_t + (t - prev_t) * ((a.p.iso - prev_v) / (v - prev_v)) : t;
-                float g[3], sf, spec;
-                value_grad<ST>(a.vol, c, g);
-                shade_factor(a.p, a.vol, g, R.dir, sf, spec);
-                out = make_float4(ts, fminf(1.0f, sf + spec), (float)k, 1.0f);
-            }
-            k++;
-            break;
-        }
-        prev_v = v;
-        prev_t = t;
-    }
-    if (!found && nsamp > 0) {
-        float m = 0.0f;
-        bool have = true;
-        if (func == RC_FUNC_MIP) m = acc / a.vol.vscale;
-        else if (func == RC_FUNC_AVERAGE) m = acc / (float)nsamp / a.vol.vscale;
-        else if (func == RC_FUNC_XRAY) m = acc * R.ds / a.vol.vscale;
-        else have = false;
-        if (have) out = make_float4(m, m, m, 1.0f);
-    }
-    if (inimg) outp[(size_t)y * cam.W + x] = out;
-    if (a.stats) add_stats(a.stats, (unsigned)k, (unsigned)k, hit ? 1u : 0u, inimg ? 1u : 0u);
-}
-
-template <typename K>
-static cudaError_t launch_kernel(K kern, const MarchArgs &a, int nviews, cudaStream_t s) {
-    size_t smem = (size_t)a.tf.K * sizeof(float4);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid((a.cam.W + 15) / 16, (a.cam.H + 7) / 8, nviews);
-    kern<<<grid, 128, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
 // a.cam gives the image size of every view; with a.cams, grid.z = nviews.
 cudaError_t launch_march(const MarchArgs &a, int nviews, cudaStream_t s) {
-    if (a.p.func != RC_FUNC_COMPOSITE) {
-        switch (a.vol.storage) {
-            case RC_STORE_F32: return launch_kernel(function_kernel<RC_STORE_F32>, a, nviews, s);
-            case RC_STORE_F16: return launch_kernel(function_kernel<RC_STORE_F16>, a, nviews, s);
-            default: return launch_kernel(function_kernel<RC_STORE_U16>, a, nviews, s);
-        }
-    }
-    switch (a.vol.storage * 2 + (a.p.shade ? 1 : 0)) {
-        case RC_STORE_F32 * 2: return launch_kernel(composite_kernel<RC_STORE_F32, false>, a, nviews, s);
-        case RC_STORE_F32 * 2 + 1: return launch_kernel(composite_kernel<RC_STORE_F32, true>, a, nviews, s);
-        case RC_STORE_F16 * 2: return launch_kernel(composite_kernel<RC_STORE_F16, false>, a, nviews, s);
-        case RC_STORE_F16 * 2 + 1: return launch_kernel(composite_kernel<RC_STORE_F16, true>, a, nviews, s);
-        case RC_STORE_U16 * 2: return launch_kernel(composite_kernel<RC_STORE_U16, false>, a, nviews, s);
-        default: return launch_kernel(composite_kernel<RC_STORE_U16, true>, a, nviews, s);
-    }
+    if (a.p.filter == RC_FILTER_BSPLINE) return launch_march_cubic(a, nviews, s);
+    if (a.p.func != RC_FUNC_COMPOSITE) return launch_function<false>(a, nviews, s);
+    if (a.tf.M >= 2) return launch_march_tf2(a, nviews, s);
+    return a.p.shade ? launch_composite<kShade>(a, nviews, s) : launch_composite<0>(a, nviews, s);
 }
 
 }  // namespace rc

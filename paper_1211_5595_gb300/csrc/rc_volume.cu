@@ -49,16 +49,17 @@ cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStre
 }
 
 // One block per cell-brick: min and max of the (clamped) codes over the
-// footprint voxels 16b .. min(16b + 16, N - 1) per axis.
+// footprint voxels max(16b - before, 0) .. min(16b + after, N - 1) per axis:
+// (0, 16) for trilinear samples, (1, 17) for cubic B-spline samples.
 __global__ void __launch_bounds__(256) minmax_kernel(const uint16_t *__restrict__ stage, int nx, int ny,
-                                                     int nz, int cb0, int cb1, int vmax, uint16_t *mn,
-                                                     uint16_t *mx) {
+                                                     int nz, int cb0, int cb1, int vmax, int before, int after,
+                                                     uint16_t *mn, uint16_t *mx) {
     const int b = blockIdx.x;
     const int bx = b % cb0, by = (b / cb0) % cb1, bz = b / (cb0 * cb1);
-    const int x0 = bx * 16, y0 = by * 16, z0 = bz * 16;
-    const int ex = min(x0 + 16, nx - 1) - x0 + 1;
-    const int ey = min(y0 + 16, ny - 1) - y0 + 1;
-    const int ez = min(z0 + 16, nz - 1) - z0 + 1;
+    const int x0 = max(bx * 16 - before, 0), y0 = max(by * 16 - before, 0), z0 = max(bz * 16 - before, 0);
+    const int ex = min(bx * 16 + after, nx - 1) - x0 + 1;
+    const int ey = min(by * 16 + after, ny - 1) - y0 + 1;
+    const int ez = min(bz * 16 + after, nz - 1) - z0 + 1;
     const int cnt = ex * ey * ez;
     int lo = 65535, hi = 0;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
@@ -85,16 +86,18 @@ __global__ void __launch_bounds__(256) minmax_kernel(const uint16_t *__restrict_
     }
 }
 
-cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax, uint16_t *mn,
-                          uint16_t *mx, cudaStream_t s) {
+cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax, int filter,
+                          uint16_t *mn, uint16_t *mx, cudaStream_t s) {
     int nb = cb[0] * cb[1] * cb[2];
-    minmax_kernel<<<nb, 256, 0, s>>>(stage, n[0], n[1], n[2], cb[0], cb[1], vmax, mn, mx);
+    const int before = filter == RC_FILTER_BSPLINE ? 1 : 0, after = filter == RC_FILTER_BSPLINE ? 17 : 16;
+    minmax_kernel<<<nb, 256, 0, s>>>(stage, n[0], n[1], n[2], cb[0], cb[1], vmax, before, after, mn, mx);
     return cudaGetLastError();
 }
 
 // A cell-brick is occupied unless every entry lo..hi its samples can touch has
 // zero opacity, with the march's own coordinate u(v) = fl(v * ucoef): raw codes
-// v = min, max; FP16 storage v = fp16(min / vmax), fp16(max / vmax).
+// v = min, max; FP16 storage v = fp16(min / vmax), fp16(max / vmax). With a
+// 2-D table an entry's opacity is its largest over the gradient rows.
 __global__ void occupancy_kernel(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax, int f16_values,
                                  TFDev tf, uint8_t *occ) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -112,7 +115,7 @@ __global__ void occupancy_kernel(const uint16_t *mn, const uint16_t *mx, int nbr
     lo = min(lo, K - 1);
     uint8_t any = 0;
     for (int i = lo; i <= hi && !any; i++) {
-        float a = tf.fp16 ? half4_to_float4(tf.f16[i]).w : tf.f32[i].w;
+        float a = tf.M >= 2 ? tf.amax[i] : (tf.fp16 ? half4_to_float4(tf.f16[i]).w : tf.f32[i].w);
         any = a != 0.0f;
     }
     occ[b] = any;
