@@ -36,6 +36,7 @@ import synth  # noqa: E402
 WORKLOAD = "shaded_256x256x180"
 METRIC = "Gsamples/s (dense-equivalent), 1024^2 of 256x256x180 u16, shaded, 36-view orbit"
 BYTES_PER_SAMPLE = 128          # 32 distinct FP32 voxels per shaded sample
+TF2_GMAX = 1200.0               # gradient magnitude (codes per mm) of the 2-D table's last row
 L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
 
 
@@ -48,12 +49,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# the files composite_kernel<F32, shaded> is compiled from
+MARCH_SOURCES = ("include/rc.h", "paper_1211_5595_gb300/csrc/rc_internal.h",
+                 "paper_1211_5595_gb300/csrc/rc_device.cuh", "paper_1211_5595_gb300/csrc/rc_march.cuh",
+                 "paper_1211_5595_gb300/csrc/rc_march.cu")
+
+
 def kernel_sources_hash():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1211_5595_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in MARCH_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -66,7 +71,7 @@ def profiled_traffic():
         for line in open(path):
             if line.startswith("- ") and ":" in line:
                 k, v = line[2:].split(":", 1)
-                kv[k.strip()] = v.strip()
+                kv[k.strip()] = (v.split() or [""])[0]
         if kv.get("sources_sha256_16") != kernel_sources_hash():
             return None
         return float(kv["dram_bytes_per_launch"])
@@ -177,6 +182,46 @@ def cpu_oracle_sample(ph, tf, w, cams, budget_s, pixels_per_view=None):
     dt = time.perf_counter() - t0
     what = f"{pixels_per_view} seeded pixels of each of" if pixels_per_view else "full 1024^2 frames of"
     return samples / dt / 1e9, cores, f"{what} {views} view(s), {samples} samples, {dt:.1f} s"
+
+
+def filter_forms(rc, ctx, vol, w, P, cam_structs, outs, ref_imgs, flush, stream, hbm_peak):
+    """The reconstruction / classification variants on the FP32 volume, every
+    view in one launch: cubic B-spline (64 distinct FP32 voxels = 256 B per
+    evaluated sample, value and analytic gradient from the same footprint),
+    the 2-D value x gradient-magnitude table (trilinear, 128 B per sample plus
+    four table entries from L1/L2), and both. Each form's own dense and
+    evaluated counts; PSNR against the trilinear 1-D images is a difference
+    by design (another filter, another table), reported for context."""
+    import torch
+    tab2 = synth.tf2d_table(w["K"], 32, TF2_GMAX)
+    out = {}
+    for name, filt, two_d in (("bspline", rc.RC_FILTER_BSPLINE, False), ("tf2d", rc.RC_FILTER_TRILINEAR, True),
+                              ("bspline_tf2d", rc.RC_FILTER_BSPLINE, True)):
+        if two_d:
+            rc.rc_tf2d_set(ctx, tab2, TF2_GMAX)
+        else:
+            rc.rc_tf_set(ctx, synth.tf_table(w["K"]))
+        P2 = rc.RenderParams(**{**P.__dict__, "filter": filt})
+        st = rc.rc_render_views(ctx, vol, P2, cam_structs, outs, stats=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        for rep in range(3):
+            ev[rep][0].record(stream)
+            rc.rc_render_views(ctx, vol, P2, cam_structs, outs)
+            ev[rep][1].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        launch_ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        n = len(cam_structs)
+        bps = 256 if filt == rc.RC_FILTER_BSPLINE else BYTES_PER_SAMPLE
+        achieved = st["evaluated_samples"] * bps / (launch_ms / 1e3) / 1e9
+        mse = ((outs - ref_imgs) ** 2).mean(dim=(1, 2, 3))
+        out[name] = {"ms_per_frame_median": launch_ms / n,
+                     "gsamples_s": st["dense_samples"] / (launch_ms / 1e3) / 1e9,
+                     "dense_samples": st["dense_samples"], "evaluated_samples": st["evaluated_samples"],
+                     "bytes_per_evaluated_sample": bps, "achieved_gbs": achieved,
+                     "frac_of_hbm": achieved / hbm_peak,
+                     "psnr_db_min_vs_trilinear_1d": float((10 * torch.log10(1.0 / mse.clamp_min(1e-30))).min())}
+    return out
 
 
 def adjoint_form(rc, ctx, flush, stream):
@@ -455,6 +500,7 @@ def main():
                "h2d_bytes_per_step": codes_host.numel() * 2 + tf.nbytes,
                "d2h_bytes_per_step": img_host.numel() * 4}
 
+    hbm_peak, peak_kind = peaks()
     # reduced-precision storage forms on the same workload: FP16 (normalised)
     # and raw uint16 volumes with the FP16 table, against the FP32 images
     forms = {}
@@ -480,6 +526,8 @@ def main():
                            "max_abs_vs_f32": float((outs - ref_imgs).abs().max())}
             rc.rc_volume_destroy(ctx, v2)
         rc.rc_tf_set_device(ctx, tf_dev)
+        forms.update(filter_forms(rc, ctx, vol, w, P, cam_structs, outs, fp32_imgs, flush, stream, hbm_peak))
+        rc.rc_tf_set_device(ctx, tf_dev)
 
     if not args.no_forms:
         forms["adjoint"] = adjoint_form(rc, ctx, flush, stream)
@@ -489,7 +537,6 @@ def main():
         forms["proposal"] = proposal_form(rc, ctx, vol, ph, w, cams, P, fp32_imgs, frame_ms, flush, stream,
                                           args.proposal_phantoms)
 
-    hbm_peak, peak_kind = peaks()
     launch_avg_s = statistics.mean(launch_ms) / 1e3
     achieved = evald * BYTES_PER_SAMPLE / launch_avg_s / 1e9
     traffic = profiled_traffic()

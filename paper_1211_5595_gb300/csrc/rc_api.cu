@@ -68,6 +68,7 @@ struct rc_volume {
     uint8_t *d_occ[2] = {nullptr, nullptr};
     bool uploaded = false;
     uint64_t data_version = 0;
+    uint64_t grid_data_version[2] = {~0ull, ~0ull};
     uint64_t occ_tf_version[2] = {~0ull, ~0ull};
     uint64_t occ_data_version[2] = {~0ull, ~0ull};
 };
@@ -293,10 +294,11 @@ rc_status rc_volume_upload(rc_volume *v, const uint16_t *src, size_t n_voxels, i
                                  src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     VolDev d = vol_dev(v);
     RC_CUDA(ctx, launch_relayout(v->d_stage, d, v->d_data, ctx->stream));
-    for (int f = 0; f < 2; f++)
-        RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, f, v->d_mn[f], v->d_mx[f], ctx->stream));
+    RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, RC_FILTER_TRILINEAR, v->d_mn[0], v->d_mx[0],
+                               ctx->stream));
     v->uploaded = true;
     v->data_version++;
+    v->grid_data_version[RC_FILTER_TRILINEAR] = v->data_version;   // the B-spline grid is built on first use
     return RC_OK;
 }
 
@@ -573,10 +575,21 @@ static TFDev tf_dev(const rc_context *ctx, const rc_volume *v) {
     return t;
 }
 
+// The min/max grid of filter f, built from the staging copy of the codes when
+// the data changed since it was last built.
+static rc_status ensure_grid(rc_context *ctx, rc_volume *v, int f) {
+    if (v->grid_data_version[f] == v->data_version) return RC_OK;
+    RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, f, v->d_mn[f], v->d_mx[f], ctx->stream));
+    v->grid_data_version[f] = v->data_version;
+    return RC_OK;
+}
+
 // The occupancy mask of filter f under the current table, rebuilt when the
 // table or the data changed since it was last built.
 static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v, int f) {
     if (v->occ_tf_version[f] == ctx->tf_version && v->occ_data_version[f] == v->data_version) return RC_OK;
+    rc_status st = ensure_grid(ctx, v, f);
+    if (st != RC_OK) return st;
     TFDev tf = tf_dev(ctx, v);
     RC_CUDA(ctx, launch_occupancy(v->d_mn[f], v->d_mx[f], v->nbricks, v->vmax, v->storage == RC_STORE_F16, tf,
                                   v->d_occ[f], ctx->stream));
@@ -806,6 +819,8 @@ rc_status rc_brick_grid_get_filter(rc_context *ctx, const rc_volume *v, int filt
         return fail(ctx, RC_ERR_INVALID_ARG, "rc_brick_grid_get: filter %d", filter);
     if (!v->uploaded) return fail(ctx, RC_ERR_STATE, "rc_brick_grid_get: volume has no data");
     DeviceScope ds(ctx->device);
+    rc_status st = ensure_grid(ctx, const_cast<rc_volume *>(v), filter);
+    if (st != RC_OK) return st;
     RC_CUDA(ctx, cudaMemcpyAsync(mn, v->d_mn[filter], v->nbricks * sizeof(uint16_t), cudaMemcpyDeviceToDevice,
                                  ctx->stream));
     RC_CUDA(ctx, cudaMemcpyAsync(mx, v->d_mx[filter], v->nbricks * sizeof(uint16_t), cudaMemcpyDeviceToDevice,
