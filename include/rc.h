@@ -129,6 +129,12 @@ const char *rc_last_error(const rc_context *ctx);
  * cudaStream_t; NULL = the legacy default stream). */
 rc_status rc_context_create(int device, void *cuda_stream, rc_context **out);
 rc_status rc_context_set_stream(rc_context *ctx, void *cuda_stream);
+/* Synchronises the context's stream and reports device-side failures of the
+ * calls queued since the last check: RC_ERR_TIMEOUT when a kernel's bounded
+ * wait (the tensor-core network's MMA or weight-copy completion) gave up,
+ * in which case that launch's outputs are invalid. Calls that return
+ * statistics make the same check. */
+rc_status rc_context_sync(rc_context *ctx);
 /* Synchronises the context's stream and frees everything the context owns.
  * Volumes must be destroyed first (RC_ERR_STATE otherwise). */
 rc_status rc_context_destroy(rc_context *ctx);
@@ -312,7 +318,10 @@ rc_status rc_profiles_generate(rc_context *ctx, const rc_volume *vol,
 /* Features of every pixel's ray for the current camera (device, H*W*112). */
 rc_status rc_proposal_features(rc_context *ctx, const rc_volume *vol,
                                const rc_render_params *params, float *out);
-/* Network on n feature rows (device n*112) -> n rows of (PDF[32], T^) (device). */
+/* Network on n feature rows (device n*112) -> n rows of (PDF[32], T^) (device).
+ * Runs on the tcgen05 tensor cores: BF16 features and weights, FP32
+ * accumulators in tensor memory, one 128-ray tile per MMA, bias + ReLU +
+ * BF16 rounding of every hidden layer, softmax / sigmoid in FP32. */
 rc_status rc_proposal_forward(rc_context *ctx, const float *features, int64_t n, float *out);
 /* Gradient of the mean loss over n rays with respect to the FP32 parameters
  * (device RC_PROPOSAL_PARAMS floats) and the loss (device float, may be NULL).
@@ -333,10 +342,23 @@ rc_status rc_proposal_train_step(rc_context *ctx, const float *features, const f
 rc_status rc_render_importance(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                                const float *pdf, const float *that, int nimp, float eps,
                                float *out_rgba, uint8_t *fallback, rc_stats *stats);
-/* The same with the loaded network evaluated in the kernel (features, network,
- * importance march and fallback fused in one launch). */
+/* The same with the loaded network choosing the samples: a tensor-core kernel
+ * encodes each ray's features, runs the network (as rc_proposal_forward) and
+ * keeps per ray only its sample range (from the PDF and the occupancy, as in
+ * rc_render_importance) and T^; the importance march then renders from those
+ * 8-byte records, with the same fallback. The result equals
+ * rc_render_importance fed with rc_proposal_forward's outputs for the rays'
+ * rc_proposal_features. */
 rc_status rc_render_proposal(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                              int nimp, float eps, float *out_rgba, uint8_t *fallback, rc_stats *stats);
+/* rc_render_proposal for nviews cameras (1..65535, one image size) in two
+ * launches: the network kernel over every view's rays, then one importance
+ * march over all views. out_rgba: device nviews*H*W*4 floats, view-major;
+ * fallback (optional): device nviews*H*W bytes. stats sum over the views. The
+ * context's own camera is not changed. */
+rc_status rc_render_proposal_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                                   const rc_camera *cams, int nviews, int nimp, float eps, float *out_rgba,
+                                   uint8_t *fallback, rc_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -59,6 +59,7 @@ SIGNATURES = {
     "rc_last_error": (C.c_char_p, [_P]),
     "rc_context_create": (_I, [_I, _P, C.POINTER(_P)]),
     "rc_context_set_stream": (_I, [_P, _P]),
+    "rc_context_sync": (_I, [_P]),
     "rc_context_destroy": (_I, [_P]),
     "rc_volume_create": (_I, [_P, _I, _I, _I, C.c_float, C.c_float, C.c_float, C.c_uint16, _I,
                               C.POINTER(_P)]),
@@ -88,6 +89,8 @@ SIGNATURES = {
     "rc_render_importance": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P, _I, C.c_float, _P, _P,
                                   C.POINTER(rc_stats)]),
     "rc_render_proposal": (_I, [_P, _P, C.POINTER(rc_render_params), _I, C.c_float, _P, _P, C.POINTER(rc_stats)]),
+    "rc_render_proposal_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _I, C.c_float,
+                                      _P, _P, C.POINTER(rc_stats)]),
 }
 
 _lib = None
@@ -152,6 +155,10 @@ def rc_context_create(device: int = 0, stream=None):
     s = _default_stream(device) if stream is None else stream
     _check(lib().rc_context_create(device, s, C.byref(out)), None, "rc_context_create")
     return out.value
+
+
+def rc_context_sync(ctx):
+    _check(lib().rc_context_sync(ctx), ctx, "rc_context_sync")
 
 
 def rc_context_set_stream(ctx, stream):
@@ -388,4 +395,15 @@ def rc_render_proposal(ctx, vol, params, nimp, eps, out, fallback=None, stats=Fa
     st = rc_stats() if stats else None
     _check(lib().rc_render_proposal(ctx, vol, C.byref(p), int(nimp), float(eps), _ptr(out), _ptr(fallback),
                                     C.byref(st) if st is not None else None), ctx, "rc_render_proposal")
+    return _stats_dict(st)
+
+
+def rc_render_proposal_views(ctx, vol, params, cams, nimp, eps, out, fallback=None, stats=False):
+    """Learned-proposal render of every camera (out: CUDA float32 n x H x W x 4)."""
+    p = _params(params)
+    arr = (rc_camera * len(cams))(*[c if isinstance(c, rc_camera) else make_camera(c) for c in cams])
+    st = rc_stats() if stats else None
+    _check(lib().rc_render_proposal_views(ctx, vol, C.byref(p), arr, len(cams), int(nimp), float(eps), _ptr(out),
+                                          _ptr(fallback), C.byref(st) if st is not None else None), ctx,
+           "rc_render_proposal_views")
     return _stats_dict(st)

@@ -33,7 +33,8 @@ struct rc_context {
     // camera
     bool cam_set = false;
     rc_camera cam{};
-    // statistics counters
+    // statistics counters (slots 0-4) and the device error word (slot 5:
+    // bit 0 = a bounded wait of a kernel gave up)
     unsigned long long *d_stats = nullptr;
     unsigned long long *h_stats = nullptr;   // pinned
     // camera records of a multi-view render
@@ -47,7 +48,9 @@ struct rc_context {
     // fragments, gradient and per-block partials
     bool net_loaded = false;
     float *d_param = nullptr, *d_m = nullptr, *d_v = nullptr, *d_grad = nullptr;
-    uint2 *d_frag = nullptr;
+    uint8_t *d_umma = nullptr;               // BF16 B operands of the tcgen05 network
+    uint2 *d_range = nullptr;                // range records of the proposal render
+    long long range_cap = 0;
     float *d_partial = nullptr, *d_loss_partial = nullptr;
     int partial_blocks = 0;
     long long adam_step = 0;
@@ -133,6 +136,33 @@ struct DeviceScope {
     }
 };
 
+constexpr int kStatSlots = 6;       // dense, evaluated, hit, total, (spare), error word
+
+static int *error_word(rc_context *ctx) { return reinterpret_cast<int *>(ctx->d_stats + 5); }
+
+// Clock budget of the tensor-core kernels' waits (about 1 s at 2 GHz). With
+// RC_FAULT_MMA_WAIT set (tests only) the network kernel issues no MMA and
+// waits 1 ms for a completion that never comes, so the timeout path runs.
+static long long wait_budget(int *issue_mma) {
+    const char *e = getenv("RC_FAULT_MMA_WAIT");
+    const bool fault = e && *e;
+    *issue_mma = fault ? 0 : 1;
+    return fault ? 2000000ll : 2000000000ll;
+}
+
+// Reads and clears the device error word (synchronises the stream).
+static rc_status check_device_errors(rc_context *ctx, const char *who) {
+    RC_CUDA(ctx, cudaMemcpyAsync(ctx->h_stats + 5, ctx->d_stats + 5, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_stats[5] != 0) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats + 5, 0, sizeof(unsigned long long), ctx->stream));
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return fail(ctx, RC_ERR_TIMEOUT, "%s: a tensor-core wait gave up (outputs of that launch are invalid)", who);
+    }
+    return RC_OK;
+}
+
 extern "C" {
 
 const char *rc_status_string(rc_status s) {
@@ -165,9 +195,11 @@ rc_status rc_context_create(int device, void *cuda_stream, rc_context **out) {
     if (!ctx) return fail(nullptr, RC_ERR_OOM, "rc_context_create: host allocation");
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
-    if (dev_alloc(&ctx->d_stats, 5 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&ctx->h_stats, 5 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (dev_alloc(&ctx->d_stats, kStatSlots * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_stats, kStatSlots * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_stats, 0, kStatSlots * sizeof(unsigned long long)) != cudaSuccess) {
         cudaFree(ctx->d_stats);
+        cudaFreeHost(ctx->h_stats);
         delete ctx;
         return fail(nullptr, RC_ERR_OOM, "rc_context_create: statistics buffers");
     }
@@ -198,7 +230,8 @@ rc_status rc_context_destroy(rc_context *ctx) {
     cudaFree(ctx->d_m);
     cudaFree(ctx->d_v);
     cudaFree(ctx->d_grad);
-    cudaFree(ctx->d_frag);
+    cudaFree(ctx->d_umma);
+    cudaFree(ctx->d_range);
     cudaFree(ctx->d_partial);
     cudaFree(ctx->d_loss_partial);
     delete ctx;
@@ -603,7 +636,8 @@ static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v, int f) {
 static rc_status read_stats(rc_context *ctx, rc_stats *stats, bool importance) {
     RC_CUDA(ctx, cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                  ctx->stream));
-    RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    rc_status st = check_device_errors(ctx, "statistics");
+    if (st != RC_OK) return st;
     stats->dense_samples = importance ? 0 : ctx->h_stats[0];
     stats->evaluated_samples = ctx->h_stats[1];
     stats->rays_hit = ctx->h_stats[2];
@@ -864,10 +898,10 @@ static_assert(sizeof(BlobHeader) == 48, "blob header layout");
 static rc_status net_alloc(rc_context *ctx) {
     if (ctx->d_param) return RC_OK;
     float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
-    uint2 *f = nullptr;
+    uint8_t *f = nullptr;
     if (dev_alloc(&p, kParams * sizeof(float)) != cudaSuccess || dev_alloc(&m, kParams * sizeof(float)) != cudaSuccess ||
         dev_alloc(&v, kParams * sizeof(float)) != cudaSuccess || dev_alloc(&g, kParams * sizeof(float)) != cudaSuccess ||
-        dev_alloc(&f, kFragTotal * sizeof(uint2)) != cudaSuccess) {
+        dev_alloc(&f, kUmmaBytes) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(p);
         cudaFree(m);
@@ -880,7 +914,7 @@ static rc_status net_alloc(rc_context *ctx) {
     ctx->d_m = m;
     ctx->d_v = v;
     ctx->d_grad = g;
-    ctx->d_frag = f;
+    ctx->d_umma = f;
     return RC_OK;
 }
 
@@ -913,7 +947,7 @@ rc_status rc_proposal_load(rc_context *ctx, const void *blob, size_t bytes) {
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_m, 0, kParams * sizeof(float), ctx->stream));
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_v, 0, kParams * sizeof(float), ctx->stream));
     }
-    RC_CUDA(ctx, launch_pack(ctx->d_param, ctx->d_frag, ctx->stream));
+    RC_CUDA(ctx, launch_pack(ctx->d_param, ctx->d_umma, ctx->stream));
     RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the host blob may be freed at once
     ctx->adam_step = h.has_adam ? (long long)h.adam_step : 0;
     ctx->net_loaded = true;
@@ -990,7 +1024,15 @@ rc_status rc_proposal_forward(rc_context *ctx, const float *features, int64_t n,
     rc_status st = check_net(ctx, features, out, n, "rc_proposal_forward");
     if (st != RC_OK) return st;
     DeviceScope ds(ctx->device);
-    RC_CUDA(ctx, launch_net_forward(NetDev{ctx->d_frag, ctx->d_param}, features, n, out, ctx->stream));
+    TcNetArgs a{};
+    a.net = NetDev{ctx->d_umma, ctx->d_param};
+    a.feat = features;
+    a.net_out = out;
+    a.n = n;
+    a.ntiles = (n + 127) / 128;
+    a.budget = wait_budget(&a.issue_mma);
+    a.err = error_word(ctx);
+    RC_CUDA(ctx, launch_tc_net(a, ctx->stream));
     return RC_OK;
 }
 
@@ -1043,52 +1085,156 @@ rc_status rc_proposal_train_step(rc_context *ctx, const float *features, const f
     if (st != RC_OK) return st;
     ctx->adam_step++;
     RC_CUDA(ctx, launch_adam(ctx->d_param, ctx->d_m, ctx->d_v, ctx->d_grad, ctx->adam_step, lr, ctx->stream));
-    RC_CUDA(ctx, launch_pack(ctx->d_param, ctx->d_frag, ctx->stream));
+    RC_CUDA(ctx, launch_pack(ctx->d_param, ctx->d_umma, ctx->stream));
     return RC_OK;
 }
 
-static rc_status importance_common(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const float *pdf,
-                                   const float *that, int nimp, float eps, float *out, uint8_t *fallback,
-                                   rc_stats *stats, const char *who) {
+// Shared checks of the importance-sampled renders.
+static rc_status check_importance(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, float *out,
+                                  int nimp, float eps, const char *who) {
     rc_status st = check_render(ctx, vol, p, out, who);
     if (st == RC_OK) st = check_plain_form(ctx, p, who);
     if (st != RC_OK) return st;
     if (p->func != RC_FUNC_COMPOSITE) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: compositing function only", who);
     if (nimp < 1 || nimp > 4096) return fail(ctx, RC_ERR_INVALID_ARG, "%s: nimp %d", who, nimp);
     if (!(eps >= 0.0f)) return fail(ctx, RC_ERR_INVALID_ARG, "%s: eps %g", who, (double)eps);
-    DeviceScope ds(ctx->device);
-    rc_volume *v = const_cast<rc_volume *>(vol);
-    st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
-    if (st != RC_OK) return st;
+    return RC_OK;
+}
+
+static ImportanceArgs importance_args(rc_context *ctx, rc_volume *v, const rc_render_params *p, int nimp, float eps,
+                                      float *out, uint8_t *fallback) {
     ImportanceArgs a;
     a.m = march_args(ctx, v, p, out);
-    a.net = NetDev{ctx->d_frag, ctx->d_param};
-    a.pdf = pdf;
-    a.that = that;
+    a.pdf = nullptr;
+    a.that = nullptr;
+    a.range = nullptr;
     a.nimp = nimp;
     a.eps = eps;
     a.fallback = fallback;
-    if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
-        a.m.stats = ctx->d_stats;
-    }
-    RC_CUDA(ctx, launch_importance(a, ctx->stream));
-    if (stats) return read_stats(ctx, stats, true);
-    return RC_OK;
+    return a;
 }
 
 rc_status rc_render_importance(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const float *pdf,
                                const float *that, int nimp, float eps, float *out_rgba, uint8_t *fallback,
                                rc_stats *stats) {
-    if (ctx && (!pdf || !that)) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_importance: pdf / that is NULL");
-    return importance_common(ctx, vol, p, pdf, that, nimp, eps, out_rgba, fallback, stats, "rc_render_importance");
+    const char *who = "rc_render_importance";
+    if (ctx && (!pdf || !that)) return fail(ctx, RC_ERR_INVALID_ARG, "%s: pdf / that is NULL", who);
+    rc_status st = check_importance(ctx, vol, p, out_rgba, nimp, eps, who);
+    if (st != RC_OK) return st;
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
+    if (st != RC_OK) return st;
+    ImportanceArgs a = importance_args(ctx, v, p, nimp, eps, out_rgba, fallback);
+    a.pdf = pdf;
+    a.that = that;
+    if (stats) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        a.m.stats = ctx->d_stats;
+    }
+    RC_CUDA(ctx, launch_importance(a, 1, ctx->stream));
+    if (stats) return read_stats(ctx, stats, true);
+    return RC_OK;
+}
+
+// The network kernel writes each ray's sample range and T^ (8 bytes per ray),
+// then the importance march renders every view from those records.
+static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const rc_camera *cams,
+                                int nviews, int nimp, float eps, float *out, uint8_t *fallback, rc_stats *stats,
+                                const char *who) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
+    if (!ctx->net_loaded) return fail(ctx, RC_ERR_STATE, "%s: no network loaded", who);
+    if (!cams || nviews < 1 || nviews > 65535)
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: %d cameras", who, cams ? nviews : 0);
+    for (int i = 0; i < nviews; i++) {
+        rc_status st = check_camera(ctx, &cams[i], who);
+        if (st != RC_OK) return st;
+        if (cams[i].width != cams[0].width || cams[i].height != cams[0].height)
+            return fail(ctx, RC_ERR_INVALID_ARG, "%s: camera %d has another image size", who, i);
+    }
+    const long long nrays = (long long)nviews * cams[0].width * cams[0].height;
+    if (nrays > (1ll << 31)) return fail(ctx, RC_ERR_INVALID_ARG, "%s: %lld rays", who, nrays);
+    const bool had = ctx->cam_set;
+    const rc_camera keep = ctx->cam;
+    ctx->cam = cams[0];
+    ctx->cam_set = true;
+    rc_status st = check_importance(ctx, vol, p, out, nimp, eps, who);
+    ctx->cam = keep;
+    ctx->cam_set = had;
+    if (st != RC_OK) return st;
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
+    if (st != RC_OK) return st;
+    if (ctx->cams_cap < nviews || ctx->range_cap < nrays) {
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // queued kernels may still use the old buffers
+        if (ctx->cams_cap < nviews) {
+            CamRec *buf = nullptr;
+            RC_CUDA(ctx, dev_alloc(&buf, (size_t)nviews * sizeof(CamRec)));
+            cudaFree(ctx->d_cams);
+            ctx->d_cams = buf;
+            ctx->cams_cap = nviews;
+        }
+        if (ctx->range_cap < nrays) {
+            uint2 *buf = nullptr;
+            RC_CUDA(ctx, dev_alloc(&buf, (size_t)nrays * sizeof(uint2)));
+            cudaFree(ctx->d_range);
+            ctx->d_range = buf;
+            ctx->range_cap = nrays;
+        }
+    }
+    CamRec *recs = new (std::nothrow) CamRec[nviews];
+    if (!recs) return fail(ctx, RC_ERR_OOM, "%s: host allocation", who);
+    for (int i = 0; i < nviews; i++) recs[i] = camera_record(cams[i], v->s);
+    cudaError_t ce = cudaMemcpyAsync(ctx->d_cams, recs, (size_t)nviews * sizeof(CamRec), cudaMemcpyHostToDevice,
+                                     ctx->stream);
+    const CamRec first = recs[0];
+    delete[] recs;
+    RC_CUDA(ctx, ce);
+    TcNetArgs n{};
+    n.m = march_args(ctx, v, p, nullptr);
+    n.m.cam = first;
+    n.m.cams = ctx->d_cams;
+    n.net = NetDev{ctx->d_umma, ctx->d_param};
+    n.range = ctx->d_range;
+    n.tiles_x = (first.W + 15) / 16;
+    n.tiles_y = (first.H + 7) / 8;
+    n.ntiles = (long long)n.tiles_x * n.tiles_y * nviews;
+    n.budget = wait_budget(&n.issue_mma);
+    n.err = error_word(ctx);
+    RC_CUDA(ctx, launch_tc_net(n, ctx->stream));
+    ImportanceArgs a = importance_args(ctx, v, p, nimp, eps, out, fallback);
+    a.m.cam = first;
+    a.m.cams = ctx->d_cams;
+    a.range = ctx->d_range;
+    if (stats) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        a.m.stats = ctx->d_stats;
+    }
+    RC_CUDA(ctx, launch_importance(a, nviews, ctx->stream));
+    if (stats) return read_stats(ctx, stats, true);
+    return RC_OK;
 }
 
 rc_status rc_render_proposal(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, int nimp, float eps,
                              float *out_rgba, uint8_t *fallback, rc_stats *stats) {
-    if (ctx && !ctx->net_loaded) return fail(ctx, RC_ERR_STATE, "rc_render_proposal: no network loaded");
-    return importance_common(ctx, vol, p, nullptr, nullptr, nimp, eps, out_rgba, fallback, stats,
-                             "rc_render_proposal");
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_render_proposal: ctx is NULL");
+    if (!ctx->cam_set) return fail(ctx, RC_ERR_STATE, "rc_render_proposal: no camera (call rc_camera_set)");
+    const rc_camera cam = ctx->cam;
+    return proposal_views(ctx, vol, p, &cam, 1, nimp, eps, out_rgba, fallback, stats, "rc_render_proposal");
+}
+
+rc_status rc_render_proposal_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                   const rc_camera *cams, int nviews, int nimp, float eps, float *out_rgba,
+                                   uint8_t *fallback, rc_stats *stats) {
+    return proposal_views(ctx, vol, p, cams, nviews, nimp, eps, out_rgba, fallback, stats,
+                          "rc_render_proposal_views");
+}
+
+rc_status rc_context_sync(rc_context *ctx) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_context_sync: ctx is NULL");
+    DeviceScope ds(ctx->device);
+    return check_device_errors(ctx, "rc_context_sync");
 }
 
 }  // extern "C"

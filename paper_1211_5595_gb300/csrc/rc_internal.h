@@ -104,26 +104,46 @@ constexpr int kOffB3 = kOffW3 + kHid * kHid;
 constexpr int kOffW4 = kOffB3 + kHid;
 constexpr int kOffB4 = kOffW4 + kHid * kOut;
 constexpr int kParams = kOffB4 + kOut;    // 18152
-// BF16 B-operand fragments of mma.m16n8k16, per layer [k-tile][n-tile][lane] uint2
-constexpr int kFragL1 = 0;
-constexpr int kFragL2 = kFragL1 + (kFeat / 16) * (kHid / 8) * 32;
-constexpr int kFragL3 = kFragL2 + (kHid / 16) * (kHid / 8) * 32;
-constexpr int kFragL4 = kFragL3 + (kHid / 16) * (kHid / 8) * 32;
-constexpr int kFragTotal = kFragL4 + (kHid / 16) * (kOut / 8) * 32;
+// BF16 B operands of the four layers for the tcgen05 MMA (N x K, K-major,
+// core-matrix layout): W1^T 64 x 112, W2^T 64 x 64, W3^T 64 x 64 and W4^T with
+// its 40 outputs padded to 48 rows (N of an M = 128 MMA is a multiple of 16).
+constexpr int kN4 = 48;
+constexpr unsigned kUmmaL1 = 0;
+constexpr unsigned kUmmaL2 = kUmmaL1 + kHid * kFeat * 2;
+constexpr unsigned kUmmaL3 = kUmmaL2 + kHid * kHid * 2;
+constexpr unsigned kUmmaL4 = kUmmaL3 + kHid * kHid * 2;
+constexpr unsigned kUmmaBytes = kUmmaL4 + kN4 * kHid * 2;   // 36864
 
 struct NetDev {
-    const uint2 *frag;        // packed BF16 weights (kFragTotal)
+    const uint8_t *umma;      // packed BF16 B operands (kUmmaBytes, 16-byte aligned)
     const float *params;      // FP32 master parameters (biases read from here)
+};
+
+// The network kernel: 128 rays per tile (one M = 128 MMA tile, TMEM lane =
+// ray), persistent CTAs. Rays from cameras (range records for the importance
+// march) or from a feature matrix (network outputs).
+struct TcNetArgs {
+    MarchArgs m;              // rays: cameras (m.cams, grid of views), volume, occupancy
+    NetDev net;
+    const float *feat;        // feature-matrix form: n x 112 FP32 (else null)
+    float *net_out;           // feature-matrix form: n x 33
+    uint2 *range;             // camera form: per ray (b_start | b_end << 8, T^ bits), view-major
+    long long n;              // feature-matrix form: rays
+    long long ntiles;         // tiles of 128 rays
+    int tiles_x, tiles_y;     // camera form: 16 x 8 pixel tiles per view
+    long long budget;         // clock cycles a wait may take before it gives up
+    int *err;                 // bit 0: a wait gave up (the call reports RC_ERR_TIMEOUT)
+    int issue_mma;            // 0 only in the timeout test: nothing is issued, the wait runs out
 };
 
 struct ImportanceArgs {
     MarchArgs m;
-    NetDev net;               // fused form: network evaluated in-kernel
-    const float *pdf;         // given-PDF form: H*W*32 (null in the fused form)
+    const float *pdf;         // given-PDF form: H*W*32
     const float *that;        // given-PDF form: H*W
+    const uint2 *range;       // range form: records of the network kernel (view-major)
     int nimp;                 // importance samples per ray
     float eps;                // fallback when |T_nimp - T^| > eps
-    uint8_t *fallback;        // per pixel flag (or null)
+    uint8_t *fallback;        // per pixel flag (or null), view-major
 };
 
 struct TrainArgs {
@@ -149,11 +169,11 @@ cudaError_t launch_adjoint(const AdjointArgs &a, float *dL_dtf, cudaStream_t s);
 cudaError_t launch_absmax(const float *x, long long n, float *out, cudaStream_t s);
 cudaError_t launch_profiles(const MarchArgs &a, float *out, cudaStream_t s);
 cudaError_t launch_features(const MarchArgs &a, float *out, cudaStream_t s);
-cudaError_t launch_net_forward(const NetDev &net, const float *feat, long long n, float *out, cudaStream_t s);
-cudaError_t launch_importance(const ImportanceArgs &a, cudaStream_t s);
+cudaError_t launch_tc_net(const TcNetArgs &a, cudaStream_t s);                  // feat != null: outputs, else ranges
+cudaError_t launch_importance(const ImportanceArgs &a, int nviews, cudaStream_t s); // pdf != null: given PDFs, else ranges
 cudaError_t launch_train_grad(const TrainArgs &a, int grid, float *grad, float *loss, cudaStream_t s);
 cudaError_t launch_adam(float *params, float *m, float *v, const float *grad, long long step, float lr,
                         cudaStream_t s);
-cudaError_t launch_pack(const float *params, uint2 *frag, cudaStream_t s);
+cudaError_t launch_pack(const float *params, uint8_t *umma, cudaStream_t s);
 
 }  // namespace rc

@@ -1,8 +1,9 @@
 // Learned sampling proposal: opacity profiles of the plain march (training
 // targets), the per-ray feature encoder, a 112-64-64-64-40 BF16 network on the
-// tensor cores (mma.sync m16n8k16, FP32 accumulation, activations chained in
-// registers), its SIMT training kernels (deterministic gradient reduction,
-// Adam), and the importance-sampled march with fallback to the plain march.
+// fifth-generation tensor cores (tcgen05 MMA, FP32 accumulators in tensor
+// memory, one M = 128 tile of rays per CTA), its SIMT training kernels
+// (deterministic gradient reduction, Adam), and the importance-sampled march
+// with fallback to the plain march.
 //
 // The paper has no learned part: the proposal replaces the evenly spaced
 // samples of Sec. 4.1 by 64 samples drawn where the network expects opacity,
@@ -11,11 +12,10 @@
 #include <cuda_bf16.h>
 
 #include "rc_device.cuh"
+#include "rc_tcgen05.cuh"
 
 namespace rc {
 
-constexpr int kFeatStride = 120;   // BF16 per feature row in shared memory (conflict-free fragments)
-constexpr int kResStride = 33;     // floats per network-output row in shared memory
 
 __device__ __forceinline__ void tile_pixel(int &x, int &y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -115,143 +115,213 @@ __global__ void __launch_bounds__(128) features_kernel(const MarchArgs a, float 
 }
 
 // ---------------------------------------------------------------------------
-// the network on the tensor cores, one warp per 32 rays
+// the network on the tensor cores: one M = 128 tile of rays per MMA
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
+// Shared memory of a network CTA. The A operand holds the tile's features
+// (128 x 112 BF16) and then, layer by layer, its hidden activations
+// (128 x 64): every layer's MMA has completed before its output overwrites
+// the operand it read.
+struct NetSmem {
+    uint8_t w[kUmmaBytes];                 // B operands of the four layers
+    uint8_t a[128 * kFeat * 2];            // A operand
+    float bias[3 * kHid + kN4];
+    unsigned long long bar_w, bar_mma;
+    uint32_t tmem;
+};
+constexpr int kTmemCols = 64;              // FP32 accumulators: 128 lanes x 64 columns
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint2 b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
-}
-
-// c[m][j] = bias + sum over k-tiles of A[m][i] * B[i][j] for two 16-row m-tiles.
-template <int KT, int NT>
-__device__ __forceinline__ void dense_layer(const uint32_t (&a)[2][KT][4], const uint2 *__restrict__ frag,
-                                            const float *__restrict__ bias, float (&c)[2][NT][4]) {
-    const int lane = threadIdx.x & 31, t = lane & 3;
-#pragma unroll
-    for (int j = 0; j < NT; j++) {
-        const float b0 = __ldg(bias + 8 * j + 2 * t), b1 = __ldg(bias + 8 * j + 2 * t + 1);
-#pragma unroll
-        for (int m = 0; m < 2; m++) {
-            c[m][j][0] = b0;
-            c[m][j][1] = b1;
-            c[m][j][2] = b0;
-            c[m][j][3] = b1;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < KT; i++) {
-#pragma unroll
-        for (int j = 0; j < NT; j++) {
-            const uint2 b = __ldg(frag + (i * NT + j) * 32 + lane);
-            mma_bf16_16816(c[0][j], a[0][i], b);
-            mma_bf16_16816(c[1][j], a[1][i], b);
-        }
+struct NetLayer {
+    unsigned b_off;                        // B operand offset in NetSmem::w
+    int K, N;
+};
+__device__ __forceinline__ NetLayer net_layer(int l) {
+    switch (l) {
+        case 0: return NetLayer{kUmmaL1, kFeat, kHid};
+        case 1: return NetLayer{kUmmaL2, kHid, kHid};
+        case 2: return NetLayer{kUmmaL3, kHid, kHid};
+        default: return NetLayer{kUmmaL4, kHid, kN4};
     }
 }
 
-// ReLU, round to BF16 and re-pack: the accumulators of n-tiles 2i, 2i+1 are
-// exactly the A fragment of k-tile i of the next layer.
-template <int NT>
-__device__ __forceinline__ void relu_pack(const float (&c)[2][NT][4], uint32_t (&a)[2][NT / 2][4]) {
-#pragma unroll
-    for (int m = 0; m < 2; m++) {
-#pragma unroll
-        for (int i = 0; i < NT / 2; i++) {
-            a[m][i][0] = pack_bf16x2(fmaxf(c[m][2 * i][0], 0.0f), fmaxf(c[m][2 * i][1], 0.0f));
-            a[m][i][1] = pack_bf16x2(fmaxf(c[m][2 * i][2], 0.0f), fmaxf(c[m][2 * i][3], 0.0f));
-            a[m][i][2] = pack_bf16x2(fmaxf(c[m][2 * i + 1][0], 0.0f), fmaxf(c[m][2 * i + 1][1], 0.0f));
-            a[m][i][3] = pack_bf16x2(fmaxf(c[m][2 * i + 1][2], 0.0f), fmaxf(c[m][2 * i + 1][3], 0.0f));
-        }
-    }
+// One layer, issued by one thread: D[128 x N] = A[128 x K] * W^T, K / 16 MMAs,
+// then a commit that arrives on the MMA barrier when they are done.
+__device__ __forceinline__ void issue_layer(const NetSmem &S, int l, uint32_t tmem, uint32_t bar) {
+    const NetLayer L = net_layer(l);
+    const uint32_t a0 = tc::smem_addr(S.a), b0 = tc::smem_addr(S.w) + L.b_off;
+    const uint32_t lbo_a = (128 / 8) * 128, lbo_b = (uint32_t)(L.N / 8) * 128;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, L.N);
+    for (int ks = 0; ks < L.K / 16; ks++)
+        tc::mma_bf16(tmem, tc::smem_desc(a0 + ks * 2 * lbo_a, lbo_a, 128),
+                     tc::smem_desc(b0 + ks * 2 * lbo_b, lbo_b, 128), idesc, ks > 0);
+    tc::commit(bar);
 }
 
-// feat: 32 rows (rays) of kFeatStride BF16; res: 32 rows of kResStride floats
-// receiving the 32-bin PDF (softmax) and T^ (sigmoid). All 32 lanes must call.
-__device__ __forceinline__ void warp_network(const NetDev &net, const __nv_bfloat16 *feat, float *res) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    uint32_t a1[2][kFeat / 16][4];
+// Bias, ReLU and BF16 rounding of this thread's 64 hidden values, written as
+// row `row` of the next layer's A operand (K = 64).
+__device__ __forceinline__ void store_hidden(NetSmem &S, uint32_t taddr, const float *bias, int row) {
 #pragma unroll
-    for (int m = 0; m < 2; m++) {
+    for (int c = 0; c < kHid; c += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + c, v);
 #pragma unroll
-        for (int i = 0; i < kFeat / 16; i++) {
-            const __nv_bfloat16 *r0 = feat + (16 * m + g) * kFeatStride + 16 * i + 2 * t;
-            const __nv_bfloat16 *r1 = r0 + 8 * kFeatStride;
-            a1[m][i][0] = *reinterpret_cast<const uint32_t *>(r0);
-            a1[m][i][1] = *reinterpret_cast<const uint32_t *>(r1);
-            a1[m][i][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-            a1[m][i][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
-        }
-    }
-    float c1[2][kHid / 8][4];
-    dense_layer<kFeat / 16, kHid / 8>(a1, net.frag + kFragL1, net.params + kOffB1, c1);
-    uint32_t a2[2][kHid / 16][4];
-    relu_pack<kHid / 8>(c1, a2);
-    float c2[2][kHid / 8][4];
-    dense_layer<kHid / 16, kHid / 8>(a2, net.frag + kFragL2, net.params + kOffB2, c2);
-    uint32_t a3[2][kHid / 16][4];
-    relu_pack<kHid / 8>(c2, a3);
-    float c3[2][kHid / 8][4];
-    dense_layer<kHid / 16, kHid / 8>(a3, net.frag + kFragL3, net.params + kOffB3, c3);
-    uint32_t a4[2][kHid / 16][4];
-    relu_pack<kHid / 8>(c3, a4);
-    float c4[2][kOut / 8][4];
-    dense_layer<kHid / 16, kOut / 8>(a4, net.frag + kFragL4, net.params + kOffB4, c4);
+        for (int j = 0; j < 16; j += 8) {
+            uint4 q;
+            uint32_t *w = reinterpret_cast<uint32_t *>(&q);
 #pragma unroll
-    for (int m = 0; m < 2; m++) {
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            float mx = -INFINITY;
-#pragma unroll
-            for (int j = 0; j < kBins / 8; j++) mx = fmaxf(mx, fmaxf(c4[m][j][2 * h], c4[m][j][2 * h + 1]));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-            float e[kBins / 8][2], sum = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kBins / 8; j++) {
-                e[j][0] = expf(c4[m][j][2 * h] - mx);
-                e[j][1] = expf(c4[m][j][2 * h + 1] - mx);
-                sum += e[j][0] + e[j][1];
+            for (int h = 0; h < 4; h++) {
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(v[j + 2 * h] + bias[c + j + 2 * h], 0.0f),
+                                                          fmaxf(v[j + 2 * h + 1] + bias[c + j + 2 * h + 1], 0.0f));
+                w[h] = *reinterpret_cast<uint32_t *>(&b2);
             }
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-            const float inv = 1.0f / sum;
-            float *row = res + (16 * m + g + 8 * h) * kResStride;
-#pragma unroll
-            for (int j = 0; j < kBins / 8; j++) {
-                row[8 * j + 2 * t] = e[j][0] * inv;
-                row[8 * j + 2 * t + 1] = e[j][1] * inv;
-            }
-            if (t == 0) row[kBins] = 1.0f / (1.0f + expf(-c4[m][kBins / 8][2 * h]));
+            *reinterpret_cast<uint4 *>(S.a + tc::core_offset(row, c + j, 128)) = q;
         }
     }
 }
 
-__global__ void __launch_bounds__(128) net_forward_kernel(const NetDev net, const float *__restrict__ feat,
-                                                          long long n, float *__restrict__ out) {
-    __shared__ __align__(16) __nv_bfloat16 s_feat[4][32 * kFeatStride];
-    __shared__ float s_res[4][32 * kResStride];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long base = ((long long)blockIdx.x * 4 + warp) * 32;
-    for (int e = lane; e < 32 * kFeat; e += 32) {
-        const int r = e / kFeat, k = e % kFeat;
-        const float v = base + r < n ? feat[(base + r) * kFeat + k] : 0.0f;
-        s_feat[warp][r * kFeatStride + k] = __float2bfloat16_rn(v);
+// Network head: 32 logits -> PDF (softmax), logit 32 -> T^ (sigmoid).
+__device__ __forceinline__ void net_head(uint32_t taddr, const float *bias, float (&pdf)[kBins], float &that) {
+    float z[kN4];
+#pragma unroll
+    for (int c = 0; c < kN4; c += 16) {
+        float v[16];
+        tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+        for (int j = 0; j < 16; j++) z[c + j] = v[j] + bias[c + j];
     }
-    __syncwarp();
-    warp_network(net, s_feat[warp], s_res[warp]);
-    __syncwarp();
-    for (int e = lane; e < 32 * kOutUsed; e += 32) {
-        const int r = e / kOutUsed, k = e % kOutUsed;
-        if (base + r < n) out[(base + r) * kOutUsed + k] = s_res[warp][r * kResStride + k];
+    float mx = z[0];
+#pragma unroll
+    for (int b = 1; b < kBins; b++) mx = fmaxf(mx, z[b]);
+    float sum = 0.0f;
+#pragma unroll
+    for (int b = 0; b < kBins; b++) {
+        pdf[b] = expf(z[b] - mx);
+        sum += pdf[b];
     }
+    const float inv = 1.0f / sum;
+#pragma unroll
+    for (int b = 0; b < kBins; b++) pdf[b] *= inv;
+    that = 1.0f / (1.0f + expf(-z[kBins]));
+}
+
+// Runs the four layers on the A operand already in shared memory (all 128
+// threads call; thread t's ray is TMEM lane t). Returns false when a wait gave
+// up; the caller then stops.
+__device__ __forceinline__ bool run_network(const TcNetArgs &A, NetSmem &S, uint32_t tmem, uint32_t bar,
+                                            uint32_t &phase, float (&pdf)[kBins], float &that) {
+    const int tid = threadIdx.x;
+    const uint32_t taddr = tmem + ((uint32_t)(tid & ~31) << 16);    // this warp's 32 lanes
+#pragma unroll 1
+    for (int l = 0; l < 4; l++) {
+        tc::fence_async_smem();           // A written by ordinary stores -> visible to the MMA
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0 && A.issue_mma) issue_layer(S, l, tmem, bar);
+        const bool ok = __syncthreads_and(tc::bar_wait(bar, phase, A.budget));
+        if (!ok) return false;
+        phase ^= 1u;
+        tc::fence_after();
+        if (l < 3) store_hidden(S, taddr, S.bias + l * kHid, tid);
+        else net_head(taddr, S.bias + 3 * kHid, pdf, that);
+    }
+    return true;
+}
+
+// Features of one ray as BF16 row `row` of the A operand.
+__device__ __forceinline__ void put_features(NetSmem &S, const VolDev &v, const uint8_t *occ, const Ray &R, bool hit,
+                                             int row) {
+    ray_features(v, occ, R, hit, [&](int i, float x) {
+        *reinterpret_cast<__nv_bfloat16 *>(S.a + tc::core_offset(row, i, 128)) = __float2bfloat16_rn(x);
+    });
+}
+
+__device__ __forceinline__ void range_of(const MarchArgs &a, const Ray &R, const float (&pdf)[kBins], int &b0,
+                                         int &b1);
+
+// FEAT: rays are rows of a feature matrix (outputs: the 33 network outputs);
+// otherwise rays are the pixels of the cameras' views (outputs: the range
+// record of each ray for the importance march).
+template <bool FEAT>
+__global__ void __launch_bounds__(128) tc_net_kernel(const TcNetArgs A) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    NetSmem &S = *reinterpret_cast<NetSmem *>(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar_w = tc::smem_addr(&S.bar_w), bar_m = tc::smem_addr(&S.bar_mma);
+    if (warp == 0) tc::tmem_alloc<kTmemCols>(tc::smem_addr(&S.tmem));
+    if (tid == 0) {
+        tc::bar_init(bar_w, 1);
+        tc::bar_init(bar_m, 1);
+    }
+    for (int i = tid; i < 3 * kHid + kN4; i += blockDim.x) {
+        const int l = i / kHid, j = i % kHid;
+        float b = 0.0f;
+        if (l < 3) b = A.net.params[(l == 0 ? kOffB1 : l == 1 ? kOffB2 : kOffB3) + j];
+        else if (j < kOut) b = A.net.params[kOffB4 + j];
+        S.bias[i] = b;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = S.tmem;
+    if (tid == 0) tc::bulk_g2s(tc::smem_addr(S.w), A.net.umma, kUmmaBytes, bar_w);
+    bool ok = __syncthreads_and(tc::bar_wait(bar_w, 0, A.budget));
+    if (!ok) {
+        // the weight copy may still be in flight: one more bounded wait
+        tc::bar_wait(bar_w, 0, A.budget);
+    }
+    uint32_t phase = 0;
+    bool mma_waited_out = false;
+#pragma unroll 1
+    for (long long tile = blockIdx.x; ok && tile < A.ntiles; tile += gridDim.x) {
+        Ray R;
+        bool hit = false;
+        long long out_idx = -1;
+        if (FEAT) {
+            const long long r = tile * 128 + tid;
+            for (int k = 0; k < kFeat; k++) {
+                const float x = r < A.n ? __ldg(A.feat + r * kFeat + k) : 0.0f;
+                *reinterpret_cast<__nv_bfloat16 *>(S.a + tc::core_offset(tid, k, 128)) = __float2bfloat16_rn(x);
+            }
+            if (r < A.n) out_idx = r;
+        } else {
+            const int per_view = A.tiles_x * A.tiles_y;
+            const int view = (int)(tile / per_view), t = (int)(tile % per_view);
+            const CamRec &cam = A.m.cams[view];
+            const int x = (t % A.tiles_x) * 16 + (warp & 1) * 8 + (lane & 7);
+            const int y = (t / A.tiles_x) * 8 + (warp >> 1) * 4 + (lane >> 3);
+            if (x < cam.W && y < cam.H) {
+                hit = setup_ray(cam, A.m.vol, A.m.p.step_vox, x, y, R);
+                out_idx = ((long long)view * cam.H + y) * cam.W + x;
+            }
+            put_features(S, A.m.vol, A.m.occ, R, hit, tid);
+        }
+        float pdf[kBins], that;
+        ok = run_network(A, S, tmem, bar_m, phase, pdf, that);
+        if (!ok) {
+            mma_waited_out = true;
+            break;
+        }
+        if (out_idx >= 0) {
+            if (FEAT) {
+                float *o = A.net_out + out_idx * kOutUsed;
+#pragma unroll
+                for (int b = 0; b < kBins; b++) o[b] = pdf[b];
+                o[kBins] = that;
+            } else {
+                int b0 = 0, b1 = kBins - 1;
+                if (hit) range_of(A.m, R, pdf, b0, b1);
+                A.range[out_idx] = make_uint2((unsigned)b0 | ((unsigned)b1 << 8), __float_as_uint(that));
+            }
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(A.err, 1);
+        if (mma_waited_out && A.issue_mma) tc::bar_wait(bar_m, phase, A.budget);   // MMAs may still be in flight
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_free<kTmemCols>(tmem);
 }
 
 // ---------------------------------------------------------------------------
@@ -293,16 +363,12 @@ __device__ __forceinline__ bool occupied_at(const VolDev &v, const uint8_t *occ,
 // first bin >= b_start where its running sum reaches 1 - 1/64 (a margin for
 // early predictions; at most 31, and 31 if never); b_start is the
 // first bin whose start, centre or end lies in an occupied cell-brick (the
-// whole chord when none does). nimp samples at the centres of nimp equal
-// segments of [t_a, t_b] (start of bin b_start to end of bin b_end), each with
-// its opacity corrected to the segment. FP32 operations as written.
-template <int ST, bool SHADE>
-__device__ __forceinline__ void importance_ray(const ImportanceArgs &A, const float4 *s_tf, const Ray &R,
-                                               const float *pdf, float &C0, float &C1, float &C2, float &T,
-                                               unsigned &evald) {
-    const MarchArgs &a = A.m;
+// whole chord when none does). FP32 operations as written.
+__device__ __forceinline__ void range_of(const MarchArgs &a, const Ray &R, const float (&pdf)[kBins], int &b0,
+                                         int &b1) {
     const float bw = __fdiv_rn(__fsub_rn(R.tf, R.tn), (float)kBins);
-    int b0 = -1, b1 = kBins - 1;
+    b0 = -1;
+    b1 = kBins - 1;
     for (int b = 0; b < kBins && b0 < 0; b++)
         if (occupied_at(a.vol, a.occ, R, __fmaf_rn((float)b, bw, R.tn)) ||
             occupied_at(a.vol, a.occ, R, __fmaf_rn((float)b + 0.5f, bw, R.tn)) ||
@@ -310,16 +376,27 @@ __device__ __forceinline__ void importance_ray(const ImportanceArgs &A, const fl
             b0 = b;
     if (b0 < 0) {
         b0 = 0;
-    } else {
-        float P = 0.0f;
-        for (int b = 0; b < kBins; b++) {
-            P = __fadd_rn(P, pdf[b]);
-            if (b >= b0 && P >= 1.0f - 1.0f / 64.0f) {
-                b1 = min(b + 1, kBins - 1);
-                break;
-            }
+        return;
+    }
+    float P = 0.0f;
+    bool found = false;
+#pragma unroll
+    for (int b = 0; b < kBins; b++) {
+        P = __fadd_rn(P, pdf[b]);
+        if (!found && b >= b0 && P >= 1.0f - 1.0f / 64.0f) {
+            b1 = min(b + 1, kBins - 1);
+            found = true;
         }
     }
+}
+
+// nimp samples at the centres of nimp equal segments of [t_a, t_b] (start of
+// bin b0 to end of bin b1), each with its opacity corrected to the segment.
+template <int ST, bool SHADE>
+__device__ __forceinline__ void march_range(const ImportanceArgs &A, const float4 *s_tf, const Ray &R, int b0, int b1,
+                                            float &C0, float &C1, float &C2, float &T, unsigned &evald) {
+    const MarchArgs &a = A.m;
+    const float bw = __fdiv_rn(__fsub_rn(R.tf, R.tn), (float)kBins);
     const float ta = b0 == 0 ? R.tn : __fmaf_rn((float)b0, bw, R.tn);
     const float tb = b1 == kBins - 1 ? R.tf : __fmaf_rn((float)(b1 + 1), bw, R.tn);
     const float seg = __fdiv_rn(__fsub_rn(tb, ta), (float)A.nimp);
@@ -339,38 +416,55 @@ __device__ __forceinline__ void importance_ray(const ImportanceArgs &A, const fl
     }
 }
 
-template <int ST, bool SHADE, bool FUSED>
+__device__ __forceinline__ void importance_stats(const MarchArgs &a, unsigned evald, unsigned fb, bool hit,
+                                                 bool inimg) {
+    unsigned e = __reduce_add_sync(0xffffffffu, evald), f = __reduce_add_sync(0xffffffffu, fb);
+    unsigned h = __reduce_add_sync(0xffffffffu, hit ? 1u : 0u), n = __reduce_add_sync(0xffffffffu, inimg ? 1u : 0u);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(a.stats + 0, (unsigned long long)f);     // fallback rays in the dense slot
+        atomicAdd(a.stats + 1, (unsigned long long)e);
+        atomicAdd(a.stats + 2, (unsigned long long)h);
+        atomicAdd(a.stats + 3, (unsigned long long)n);
+    }
+}
+
+// RANGE: the sample range and T^ of each ray come from the network kernel's
+// records (several views, grid.z = view); otherwise from the given per-pixel
+// PDF and T^ (one view). Rays with |T_nimp - T^| > eps are re-marched by the
+// plain march.
+template <int ST, bool SHADE, bool RANGE>
 __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A) {
     const MarchArgs &a = A.m;
-    extern __shared__ float4 smem[];
-    float4 *s_tf = smem;
-    float *s_res = reinterpret_cast<float *>(smem + a.tf.K);                   // 128 x 33
-    __nv_bfloat16 *s_feat = reinterpret_cast<__nv_bfloat16 *>(s_res + 128 * kResStride);   // 4 x 32 x 120
+    extern __shared__ float4 s_tf[];
     load_tf(a.tf, s_tf);
+    __syncthreads();
+    const CamRec cam = a.cams ? a.cams[blockIdx.z] : a.cam;
+    const size_t view_off = (size_t)blockIdx.z * cam.W * cam.H;
     int x, y;
     tile_pixel(x, y);
-    const bool inimg = x < a.cam.W && y < a.cam.H;
+    const bool inimg = x < cam.W && y < cam.H;
     Ray R;
-    const bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
-    const size_t pix = (size_t)y * a.cam.W + x;
-    float *mine = s_res + threadIdx.x * kResStride;
-    if (FUSED) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        __nv_bfloat16 *row = s_feat + (warp * 32 + lane) * kFeatStride;
-        ray_features(a.vol, a.occ, R, hit, [&](int i, float v) { row[i] = __float2bfloat16_rn(v); });
-        __syncwarp();
-        warp_network(A.net, s_feat + warp * 32 * kFeatStride, s_res + warp * 32 * kResStride);
-        __syncwarp();
-    } else if (hit) {
-        for (int b = 0; b < kBins; b++) mine[b] = A.pdf[pix * kBins + b];
-        mine[kBins] = A.that[pix];
-    }
-    __syncthreads();
+    const bool hit = inimg && setup_ray(cam, a.vol, a.p.step_vox, x, y, R);
+    const size_t pix = view_off + (size_t)y * cam.W + x;
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
     unsigned evald = 0, fb = 0;
     if (hit) {
-        importance_ray<ST, SHADE>(A, s_tf, R, mine, C0, C1, C2, T, evald);
-        if (fabsf(T - mine[kBins]) > A.eps) {
+        int b0, b1;
+        float that;
+        if (RANGE) {
+            const uint2 rec = A.range[pix];
+            b0 = min((int)(rec.x & 255u), kBins - 1);
+            b1 = min(max((int)((rec.x >> 8) & 255u), b0), kBins - 1);
+            that = __uint_as_float(rec.y);
+        } else {
+            float pdf[kBins];
+#pragma unroll
+            for (int b = 0; b < kBins; b++) pdf[b] = A.pdf[pix * kBins + b];
+            that = A.that[pix];
+            range_of(a, R, pdf, b0, b1);
+        }
+        march_range<ST, SHADE>(A, s_tf, R, b0, b1, C0, C1, C2, T, evald);
+        if (fabsf(T - that) > A.eps) {
             fb = 1;
             plain_ray<ST, SHADE>(a, s_tf, R, C0, C1, C2, T, evald);
         }
@@ -379,16 +473,7 @@ __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A)
         a.out[pix] = make_float4(C0, C1, C2, 1.0f - T);
         if (A.fallback) A.fallback[pix] = (uint8_t)fb;
     }
-    if (a.stats) {
-        unsigned e = __reduce_add_sync(0xffffffffu, evald), f = __reduce_add_sync(0xffffffffu, fb);
-        unsigned h = __reduce_add_sync(0xffffffffu, hit ? 1u : 0u), n = __reduce_add_sync(0xffffffffu, inimg ? 1u : 0u);
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(a.stats + 0, (unsigned long long)f);     // fallback rays in the dense slot
-            atomicAdd(a.stats + 1, (unsigned long long)e);
-            atomicAdd(a.stats + 2, (unsigned long long)h);
-            atomicAdd(a.stats + 3, (unsigned long long)n);
-        }
-    }
+    if (a.stats) importance_stats(a, evald, fb, hit, inimg);
 }
 
 // ---------------------------------------------------------------------------
@@ -571,28 +656,26 @@ cudaError_t launch_adam(float *params, float *m, float *v, const float *grad, lo
     return cudaGetLastError();
 }
 
-// BF16 B fragments: for k-tile i, n-tile j, lane (g, t): (W[16i+2t][8j+g],
-// W[16i+2t+1][8j+g]) and (W[16i+2t+8][8j+g], W[16i+2t+9][8j+g]).
-__global__ void pack_kernel(const float *params, uint2 *frag) {
+// B operands of the four layers in the core-matrix layout: element (n, k) of
+// layer l is bf16(W_l[k][n]) (0 for the padding rows n >= 40 of layer 4).
+__global__ void pack_umma_kernel(const float *params, uint8_t *umma) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= kFragTotal) return;
-    int off, N, base;
-    if (idx < kFragL2) { off = kOffW1; N = kHid; base = kFragL1; }
-    else if (idx < kFragL3) { off = kOffW2; N = kHid; base = kFragL2; }
-    else if (idx < kFragL4) { off = kOffW3; N = kHid; base = kFragL3; }
-    else { off = kOffW4; N = kOut; base = kFragL4; }
-    const int r = idx - base, lane = r & 31, tile = r >> 5, NT = N / 8;
-    const int i = tile / NT, j = tile % NT, g = lane >> 2, t = lane & 3;
-    const float *W = params + off;
-    const int n = 8 * j + g, k0 = 16 * i + 2 * t;
-    uint2 o;
-    o.x = pack_bf16x2(W[k0 * N + n], W[(k0 + 1) * N + n]);
-    o.y = pack_bf16x2(W[(k0 + 8) * N + n], W[(k0 + 9) * N + n]);
-    frag[idx] = o;
+    constexpr int n1 = kHid * kFeat, n2 = kHid * kHid, n4 = kN4 * kHid;
+    if (idx >= n1 + 2 * n2 + n4) return;
+    int r, K, N, nw, woff;
+    unsigned boff;
+    if (idx < n1) { r = idx; K = kFeat; N = kHid; nw = kHid; woff = kOffW1; boff = kUmmaL1; }
+    else if (idx < n1 + n2) { r = idx - n1; K = kHid; N = kHid; nw = kHid; woff = kOffW2; boff = kUmmaL2; }
+    else if (idx < n1 + 2 * n2) { r = idx - n1 - n2; K = kHid; N = kHid; nw = kHid; woff = kOffW3; boff = kUmmaL3; }
+    else { r = idx - n1 - 2 * n2; K = kHid; N = kN4; nw = kOut; woff = kOffW4; boff = kUmmaL4; }
+    const int n = r / K, k = r % K;
+    const float w = n < nw ? params[woff + k * nw + n] : 0.0f;
+    *reinterpret_cast<__nv_bfloat16 *>(umma + boff + tc::core_offset(n, k, N)) = __float2bfloat16_rn(w);
 }
 
-cudaError_t launch_pack(const float *params, uint2 *frag, cudaStream_t s) {
-    pack_kernel<<<(kFragTotal + 255) / 256, 256, 0, s>>>(params, frag);
+cudaError_t launch_pack(const float *params, uint8_t *umma, cudaStream_t s) {
+    constexpr int total = kHid * kFeat + 2 * kHid * kHid + kN4 * kHid;
+    pack_umma_kernel<<<(total + 255) / 256, 256, 0, s>>>(params, umma);
     return cudaGetLastError();
 }
 
@@ -623,36 +706,53 @@ cudaError_t launch_features(const MarchArgs &a, float *out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_net_forward(const NetDev &net, const float *feat, long long n, float *out, cudaStream_t s) {
-    const long long blocks = (n + 127) / 128;
-    net_forward_kernel<<<(unsigned)blocks, 128, 0, s>>>(net, feat, n, out);
+// Persistent network CTAs: as many as fit on the device at once (each holds
+// 64 TMEM columns and about 65 KB of shared memory), at most one per tile.
+template <bool FEAT>
+static cudaError_t launch_tc(const TcNetArgs &a, cudaStream_t s) {
+    auto kern = tc_net_kernel<FEAT>;
+    const int smem = (int)sizeof(NetSmem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess) return e;
+    per_sm = max(1, min(per_sm, 512 / kTmemCols));
+    const long long grid = min((long long)sms * per_sm, a.ntiles);
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+cudaError_t launch_tc_net(const TcNetArgs &a, cudaStream_t s) {
+    return a.feat ? launch_tc<true>(a, s) : launch_tc<false>(a, s);
+}
+
 template <int ST, bool SHADE>
-static cudaError_t launch_imp_st(const ImportanceArgs &a, cudaStream_t s) {
-    const bool fused = a.pdf == nullptr;
-    size_t smem = (size_t)a.m.tf.K * sizeof(float4) + 128 * kResStride * sizeof(float);
-    if (fused) smem += 128 * kFeatStride * sizeof(__nv_bfloat16);
+static cudaError_t launch_imp_st(const ImportanceArgs &a, int nviews, cudaStream_t s) {
+    const size_t smem = (size_t)a.m.tf.K * sizeof(float4);
     auto go = [&](auto kern) -> cudaError_t {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        kern<<<image_grid(a.m.cam), 128, smem, s>>>(a);
+        dim3 grid = image_grid(a.m.cam);
+        grid.z = nviews;
+        kern<<<grid, 128, smem, s>>>(a);
         return cudaGetLastError();
     };
-    return fused ? go(importance_kernel<ST, SHADE, true>) : go(importance_kernel<ST, SHADE, false>);
+    return a.range ? go(importance_kernel<ST, SHADE, true>) : go(importance_kernel<ST, SHADE, false>);
 }
 
-cudaError_t launch_importance(const ImportanceArgs &a, cudaStream_t s) {
+cudaError_t launch_importance(const ImportanceArgs &a, int nviews, cudaStream_t s) {
     switch (a.m.vol.storage * 2 + (a.m.p.shade ? 1 : 0)) {
-        case RC_STORE_F32 * 2: return launch_imp_st<RC_STORE_F32, false>(a, s);
-        case RC_STORE_F32 * 2 + 1: return launch_imp_st<RC_STORE_F32, true>(a, s);
-        case RC_STORE_F16 * 2: return launch_imp_st<RC_STORE_F16, false>(a, s);
-        case RC_STORE_F16 * 2 + 1: return launch_imp_st<RC_STORE_F16, true>(a, s);
-        case RC_STORE_U16 * 2: return launch_imp_st<RC_STORE_U16, false>(a, s);
-        default: return launch_imp_st<RC_STORE_U16, true>(a, s);
+        case RC_STORE_F32 * 2: return launch_imp_st<RC_STORE_F32, false>(a, nviews, s);
+        case RC_STORE_F32 * 2 + 1: return launch_imp_st<RC_STORE_F32, true>(a, nviews, s);
+        case RC_STORE_F16 * 2: return launch_imp_st<RC_STORE_F16, false>(a, nviews, s);
+        case RC_STORE_F16 * 2 + 1: return launch_imp_st<RC_STORE_F16, true>(a, nviews, s);
+        case RC_STORE_U16 * 2: return launch_imp_st<RC_STORE_U16, false>(a, nviews, s);
+        default: return launch_imp_st<RC_STORE_U16, true>(a, nviews, s);
     }
 }
 

@@ -225,8 +225,9 @@ def test_fallback_rays_equal_the_plain_march(rc, small):
 
 
 def test_fused_render_matches_network_pdfs(rc, small):
-    """The fused launch (features + network + importance march) equals the
-    importance march fed with the network's PDFs for the same rays."""
+    """The proposal render (tensor-core network kernel writing each ray's
+    range record, then the importance march) equals the importance march fed
+    with the network's PDFs for the same rays."""
     import torch
     ph, tf, r = small
     rc.rc_proposal_load(r.ctx, rc.pack_proposal_blob(synth.proposal_init_params(51)))
@@ -318,3 +319,56 @@ def test_trained_proposal_gain(rc):
         torch.cuda.synchronize()
         rc.rc_volume_destroy(ctx, vol)
         rc.rc_context_destroy(ctx)
+
+
+def test_proposal_views_equal_single_views(rc, small):
+    """Several views in two launches give the per-view renders exactly."""
+    import torch
+    ph, tf, r = small
+    rc.rc_proposal_load(r.ctx, rc.pack_proposal_blob(synth.proposal_init_params(52)))
+    cams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=72, height=56) for az in (15.0, 140.0, 255.0)]
+    out = torch.empty((3, 56, 72, 4), device="cuda")
+    fb = torch.empty((3, 56 * 72), dtype=torch.uint8, device="cuda")
+    st = rc.rc_render_proposal_views(r.ctx, r.vol, params_for(), cams, 64, 0.02, out, fb, stats=True)
+    one = torch.empty((56, 72, 4), device="cuda")
+    fb1 = torch.empty(56 * 72, dtype=torch.uint8, device="cuda")
+    total_fb = 0
+    for v, cam in enumerate(cams):
+        rc.rc_camera_set(r.ctx, cam)
+        s1 = rc.rc_render_proposal(r.ctx, r.vol, params_for(), 64, 0.02, one, fb1, stats=True)
+        torch.cuda.synchronize()
+        assert torch.equal(out[v], one) and torch.equal(fb[v], fb1)
+        total_fb += s1["fallback_rays"]
+    assert st["fallback_rays"] == total_fb
+    assert st["rays_total"] == 3 * 56 * 72
+
+
+def test_network_wait_timeout_is_reported(rc, small, monkeypatch):
+    """A network launch whose MMA completion never arrives (the test hook
+    issues no MMA) gives up after its bounded wait, frees its tensor memory
+    and reports RC_ERR_TIMEOUT at the next sync; the context stays usable."""
+    import torch
+    ph, tf, r = small
+    rc.rc_proposal_load(r.ctx, rc.pack_proposal_blob(synth.proposal_init_params(53)))
+    cam = synth.orbit_camera(ph.dims, ph.spacing, 60.0, width=64, height=48)
+    rc.rc_camera_set(r.ctx, cam)
+    out = torch.empty((48, 64, 4), device="cuda")
+    monkeypatch.setenv("RC_FAULT_MMA_WAIT", "1")
+    rc.rc_render_proposal(r.ctx, r.vol, params_for(), 64, 0.02, out)
+    with pytest.raises(rc.RCError) as ei:
+        rc.rc_context_sync(r.ctx)
+    assert ei.value.status == rc.RC_ERR_TIMEOUT
+    monkeypatch.delenv("RC_FAULT_MMA_WAIT")
+    rc.rc_context_sync(r.ctx)                       # the flag was cleared
+    ref = torch.empty_like(out)
+    st = rc.rc_render_proposal(r.ctx, r.vol, params_for(), 64, 0.02, out, stats=True)
+    F = torch.empty((64 * 48, 112), device="cuda")
+    rc.rc_proposal_features(r.ctx, r.vol, params_for(), F)
+    net = torch.empty((64 * 48, 33), device="cuda")
+    rc.rc_proposal_forward(r.ctx, F, 64 * 48, net)
+    rc.rc_render_importance(r.ctx, r.vol, params_for(), net[:, :32].contiguous(), net[:, 32].contiguous(), 64,
+                            0.02, ref)
+    rc.rc_context_sync(r.ctx)
+    hit = F[:, 3:6].abs().sum(dim=1) > 0
+    assert torch.equal(out.view(-1, 4)[hit], ref.view(-1, 4)[hit])
+    assert st["rays_total"] == 64 * 48
