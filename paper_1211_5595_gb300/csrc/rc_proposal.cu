@@ -68,11 +68,26 @@ __global__ void __launch_bounds__(128) profiles_kernel(const MarchArgs a, float 
 // features: entry point (normalised to the box) and world direction, their
 // sin/cos encodings at 6 octaves, 32 occupancy bits along the chord, 2 zeros
 // ---------------------------------------------------------------------------
-template <typename Put>
-__device__ __forceinline__ void ray_features(const VolDev &v, const uint8_t *occ, const Ray &R, bool hit, Put put) {
+// Emits the 112 features in 14 chunks of 8 (emit(chunk, v) in chunk order) and
+// returns the occupancy bits at the bin centres as a mask (bit b = bin b).
+// Feature order: 0-5 entry point and direction; 6 + 12c + 2j and 7 + 12c + 2j
+// sin and cos of pi 2^j x_c; 78 + b occupancy of bin b's centre; 110-111 zero.
+template <typename Emit>
+__device__ __forceinline__ uint32_t ray_features(const VolDev &v, const uint8_t *occ, const Ray &R, bool hit,
+                                                 Emit emit) {
+    float buf[8];
+    int fill = 0, chunk = 0;
+    auto put = [&](float x) {
+        buf[fill++] = x;
+        if (fill == 8) {
+            emit(chunk++, buf);
+            fill = 0;
+        }
+    };
     if (!hit) {
-        for (int i = 0; i < kFeat; i++) put(i, 0.0f);
-        return;
+#pragma unroll
+        for (int i = 0; i < kFeat; i++) put(0.0f);
+        return 0u;
     }
     float xs[6];
 #pragma unroll
@@ -81,27 +96,41 @@ __device__ __forceinline__ void ray_features(const VolDev &v, const uint8_t *occ
         xs[3 + c] = R.dir[c];
     }
 #pragma unroll
-    for (int c = 0; c < 6; c++) put(c, xs[c]);
+    for (int c = 0; c < 6; c++) put(xs[c]);
+    // sin and cos of pi 2^j x for j = 0 and 3 directly; j = 1, 2 and 4, 5 by
+    // angle doubling, sin 2a = 2 sin a cos a, cos 2a = (cos a - sin a)(cos a + sin a)
+    // (two doublings keep the error below 1e-6)
 #pragma unroll
     for (int c = 0; c < 6; c++) {
+        float s, co;
 #pragma unroll
         for (int j = 0; j < 6; j++) {
-            float s, co;
-            sincospif(ldexpf(xs[c], j), &s, &co);
-            put(6 + 12 * c + 2 * j, s);
-            put(7 + 12 * c + 2 * j, co);
+            if (j == 0 || j == 3) {
+                sincospif(ldexpf(xs[c], j), &s, &co);
+            } else {
+                const float s2 = 2.0f * s * co;
+                co = (co - s) * (co + s);
+                s = s2;
+            }
+            put(s);
+            put(co);
         }
     }
     const float bw = __fdiv_rn(__fsub_rn(R.tf, R.tn), (float)kBins);
+    uint32_t mask = 0;
+#pragma unroll
     for (int b = 0; b < kBins; b++) {
         float p[3];
         position_at(R, __fmaf_rn((float)b + 0.5f, bw, R.tn), p);
         Cell c;
         cell_of(v, p, c);
-        put(78 + b, __ldg(occ + brick_of(v, c)) ? 1.0f : 0.0f);
+        const bool o = __ldg(occ + brick_of(v, c)) != 0;
+        mask |= (uint32_t)o << b;
+        put(o ? 1.0f : 0.0f);
     }
-    put(110, 0.0f);
-    put(111, 0.0f);
+    put(0.0f);
+    put(0.0f);
+    return mask;
 }
 
 __global__ void __launch_bounds__(128) features_kernel(const MarchArgs a, float *out) {
@@ -111,24 +140,32 @@ __global__ void __launch_bounds__(128) features_kernel(const MarchArgs a, float 
     Ray R;
     const bool hit = setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
     float *o = out + ((size_t)y * a.cam.W + x) * kFeat;
-    ray_features(a.vol, a.occ, R, hit, [&](int i, float v) { o[i] = v; });
+    ray_features(a.vol, a.occ, R, hit, [&](int chunk, const float (&v)[8]) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) o[8 * chunk + i] = v[i];
+    });
 }
 
 // ---------------------------------------------------------------------------
 // the network on the tensor cores: one M = 128 tile of rays per MMA
 // ---------------------------------------------------------------------------
-// Shared memory of a network CTA. The A operand holds the tile's features
-// (128 x 112 BF16) and then, layer by layer, its hidden activations
-// (128 x 64): every layer's MMA has completed before its output overwrites
-// the operand it read.
+// A network CTA runs two independent groups of 128 threads, each on its own
+// tiles of 128 rays with its own A operand, MMA barrier and 64 TMEM columns
+// (TMEM lane = ray); the weights and biases are shared. The A operand holds a
+// tile's features (128 x 112 BF16) and then, layer by layer, its hidden
+// activations (128 x 64): every layer's MMA has completed before its output
+// overwrites the operand it read.
+constexpr int kGroups = 2;
+constexpr int kGroupThreads = 128;
+constexpr int kTmemCols = 64 * kGroups;    // FP32 accumulators: 128 lanes x 64 columns per group
+
 struct NetSmem {
     uint8_t w[kUmmaBytes];                 // B operands of the four layers
-    uint8_t a[128 * kFeat * 2];            // A operand
+    uint8_t a[kGroups][128 * kFeat * 2];   // A operands
     float bias[3 * kHid + kN4];
-    unsigned long long bar_w, bar_mma;
+    unsigned long long bar_w, bar_mma[kGroups];
     uint32_t tmem;
 };
-constexpr int kTmemCols = 64;              // FP32 accumulators: 128 lanes x 64 columns
 
 struct NetLayer {
     unsigned b_off;                        // B operand offset in NetSmem::w
@@ -143,22 +180,38 @@ __device__ __forceinline__ NetLayer net_layer(int l) {
     }
 }
 
+// Barrier of one group (named barrier 1 + g, 128 threads); returns the AND of
+// every thread's `ok`.
+__device__ __forceinline__ bool group_sync_and(int g, bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "r"(1 + g), "r"(kGroupThreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kGroupThreads) : "memory");
+}
+
 // One layer, issued by one thread: D[128 x N] = A[128 x K] * W^T, K / 16 MMAs,
-// then a commit that arrives on the MMA barrier when they are done.
-__device__ __forceinline__ void issue_layer(const NetSmem &S, int l, uint32_t tmem, uint32_t bar) {
+// then a commit that arrives on the group's MMA barrier when they are done.
+__device__ __forceinline__ void issue_layer(const NetSmem &S, int g, int l, uint32_t tmem_d, uint32_t bar) {
     const NetLayer L = net_layer(l);
-    const uint32_t a0 = tc::smem_addr(S.a), b0 = tc::smem_addr(S.w) + L.b_off;
+    const uint32_t a0 = tc::smem_addr(S.a[g]), b0 = tc::smem_addr(S.w) + L.b_off;
     const uint32_t lbo_a = (128 / 8) * 128, lbo_b = (uint32_t)(L.N / 8) * 128;
     const uint32_t idesc = tc::idesc_bf16_f32(128, L.N);
     for (int ks = 0; ks < L.K / 16; ks++)
-        tc::mma_bf16(tmem, tc::smem_desc(a0 + ks * 2 * lbo_a, lbo_a, 128),
+        tc::mma_bf16(tmem_d, tc::smem_desc(a0 + ks * 2 * lbo_a, lbo_a, 128),
                      tc::smem_desc(b0 + ks * 2 * lbo_b, lbo_b, 128), idesc, ks > 0);
     tc::commit(bar);
 }
 
 // Bias, ReLU and BF16 rounding of this thread's 64 hidden values, written as
 // row `row` of the next layer's A operand (K = 64).
-__device__ __forceinline__ void store_hidden(NetSmem &S, uint32_t taddr, const float *bias, int row) {
+__device__ __forceinline__ void store_hidden(uint8_t *A, uint32_t taddr, const float *bias, int row) {
 #pragma unroll
     for (int c = 0; c < kHid; c += 16) {
         float v[16];
@@ -173,9 +226,22 @@ __device__ __forceinline__ void store_hidden(NetSmem &S, uint32_t taddr, const f
                                                           fmaxf(v[j + 2 * h + 1] + bias[c + j + 2 * h + 1], 0.0f));
                 w[h] = *reinterpret_cast<uint32_t *>(&b2);
             }
-            *reinterpret_cast<uint4 *>(S.a + tc::core_offset(row, c + j, 128)) = q;
+            *reinterpret_cast<uint4 *>(A + tc::core_offset(row, c + j, 128)) = q;
         }
     }
+}
+
+// Eight values as BF16 at (row, 8 * chunk .. 8 * chunk + 7) of an A operand:
+// one 16-byte store (a warp's 32 rows fill 512 contiguous bytes).
+__device__ __forceinline__ void store_chunk(uint8_t *A, int row, int chunk, const float (&v)[8]) {
+    uint4 q;
+    uint32_t *w = reinterpret_cast<uint32_t *>(&q);
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+        w[h] = *reinterpret_cast<uint32_t *>(&b2);
+    }
+    *reinterpret_cast<uint4 *>(A + tc::core_offset(row, 8 * chunk, 128)) = q;
 }
 
 // Network head: 32 logits -> PDF (softmax), logit 32 -> T^ (sigmoid).
@@ -203,54 +269,48 @@ __device__ __forceinline__ void net_head(uint32_t taddr, const float *bias, floa
     that = 1.0f / (1.0f + expf(-z[kBins]));
 }
 
-// Runs the four layers on the A operand already in shared memory (all 128
-// threads call; thread t's ray is TMEM lane t). Returns false when a wait gave
+// Runs the four layers of group g on its A operand (the group's 128 threads
+// call; thread t of the group is TMEM lane t). Returns false when a wait gave
 // up; the caller then stops.
-__device__ __forceinline__ bool run_network(const TcNetArgs &A, NetSmem &S, uint32_t tmem, uint32_t bar,
+__device__ __forceinline__ bool run_network(const TcNetArgs &A, NetSmem &S, int g, uint32_t tmem, uint32_t bar,
                                             uint32_t &phase, float (&pdf)[kBins], float &that) {
-    const int tid = threadIdx.x;
-    const uint32_t taddr = tmem + ((uint32_t)(tid & ~31) << 16);    // this warp's 32 lanes
+    const int t = threadIdx.x - g * kGroupThreads;
+    const uint32_t tmem_d = tmem + 64u * (uint32_t)g;
+    const uint32_t taddr = tmem_d + ((uint32_t)(t & ~31) << 16);    // this warp's 32 lanes
 #pragma unroll 1
     for (int l = 0; l < 4; l++) {
         tc::fence_async_smem();           // A written by ordinary stores -> visible to the MMA
         tc::fence_before();
-        __syncthreads();
+        group_sync(g);
         tc::fence_after();
-        if (tid == 0 && A.issue_mma) issue_layer(S, l, tmem, bar);
-        const bool ok = __syncthreads_and(tc::bar_wait(bar, phase, A.budget));
+        if (t == 0 && A.issue_mma) issue_layer(S, g, l, tmem_d, bar);
+        const bool ok = group_sync_and(g, tc::bar_wait(bar, phase, A.budget));
         if (!ok) return false;
         phase ^= 1u;
         tc::fence_after();
-        if (l < 3) store_hidden(S, taddr, S.bias + l * kHid, tid);
+        if (l < 3) store_hidden(S.a[g], taddr, S.bias + l * kHid, t);
         else net_head(taddr, S.bias + 3 * kHid, pdf, that);
     }
     return true;
 }
 
-// Features of one ray as BF16 row `row` of the A operand.
-__device__ __forceinline__ void put_features(NetSmem &S, const VolDev &v, const uint8_t *occ, const Ray &R, bool hit,
-                                             int row) {
-    ray_features(v, occ, R, hit, [&](int i, float x) {
-        *reinterpret_cast<__nv_bfloat16 *>(S.a + tc::core_offset(row, i, 128)) = __float2bfloat16_rn(x);
-    });
-}
-
-__device__ __forceinline__ void range_of(const MarchArgs &a, const Ray &R, const float (&pdf)[kBins], int &b0,
-                                         int &b1);
+__device__ __forceinline__ void range_of(const MarchArgs &a, const Ray &R, const float (&pdf)[kBins], uint32_t centre,
+                                         bool have_centre, int &b0, int &b1);
 
 // FEAT: rays are rows of a feature matrix (outputs: the 33 network outputs);
 // otherwise rays are the pixels of the cameras' views (outputs: the range
 // record of each ray for the importance march).
 template <bool FEAT>
-__global__ void __launch_bounds__(128) tc_net_kernel(const TcNetArgs A) {
+__global__ void __launch_bounds__(kGroups * kGroupThreads) tc_net_kernel(const TcNetArgs A) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     NetSmem &S = *reinterpret_cast<NetSmem *>(smem_raw);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t bar_w = tc::smem_addr(&S.bar_w), bar_m = tc::smem_addr(&S.bar_mma);
-    if (warp == 0) tc::tmem_alloc<kTmemCols>(tc::smem_addr(&S.tmem));
+    const int tid = threadIdx.x, g = tid / kGroupThreads, t = tid % kGroupThreads;
+    const int warp = t >> 5, lane = t & 31;
+    const uint32_t bar_w = tc::smem_addr(&S.bar_w), bar_m = tc::smem_addr(&S.bar_mma[g]);
+    if (tid < 32) tc::tmem_alloc<kTmemCols>(tc::smem_addr(&S.tmem));
     if (tid == 0) {
         tc::bar_init(bar_w, 1);
-        tc::bar_init(bar_m, 1);
+        for (int i = 0; i < kGroups; i++) tc::bar_init(tc::smem_addr(&S.bar_mma[i]), 1);
     }
     for (int i = tid; i < 3 * kHid + kN4; i += blockDim.x) {
         const int l = i / kHid, j = i % kHid;
@@ -265,38 +325,49 @@ __global__ void __launch_bounds__(128) tc_net_kernel(const TcNetArgs A) {
     const uint32_t tmem = S.tmem;
     if (tid == 0) tc::bulk_g2s(tc::smem_addr(S.w), A.net.umma, kUmmaBytes, bar_w);
     bool ok = __syncthreads_and(tc::bar_wait(bar_w, 0, A.budget));
-    if (!ok) {
-        // the weight copy may still be in flight: one more bounded wait
-        tc::bar_wait(bar_w, 0, A.budget);
-    }
+    if (!ok) tc::bar_wait(bar_w, 0, A.budget);      // the weight copy may still be in flight
     uint32_t phase = 0;
     bool mma_waited_out = false;
+    uint8_t *Ag = S.a[g];
+    const long long stride = (long long)gridDim.x * kGroups;
 #pragma unroll 1
-    for (long long tile = blockIdx.x; ok && tile < A.ntiles; tile += gridDim.x) {
+    for (long long tile = (long long)blockIdx.x * kGroups + g; ok && tile < A.ntiles; tile += stride) {
         Ray R;
         bool hit = false;
         long long out_idx = -1;
+        uint32_t centre = 0;
         if (FEAT) {
-            const long long r = tile * 128 + tid;
-            for (int k = 0; k < kFeat; k++) {
-                const float x = r < A.n ? __ldg(A.feat + r * kFeat + k) : 0.0f;
-                *reinterpret_cast<__nv_bfloat16 *>(S.a + tc::core_offset(tid, k, 128)) = __float2bfloat16_rn(x);
+            const long long r = tile * 128 + t;
+            const float4 *src = reinterpret_cast<const float4 *>(A.feat + r * kFeat);
+#pragma unroll 7
+            for (int c = 0; c < kFeat / 8; c++) {
+                float v[8];
+                if (r < A.n) {
+                    const float4 lo = __ldg(src + 2 * c), hi = __ldg(src + 2 * c + 1);
+                    v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+                    v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; i++) v[i] = 0.0f;
+                }
+                store_chunk(Ag, t, c, v);
             }
             if (r < A.n) out_idx = r;
         } else {
             const int per_view = A.tiles_x * A.tiles_y;
-            const int view = (int)(tile / per_view), t = (int)(tile % per_view);
+            const int view = (int)(tile / per_view), tl = (int)(tile % per_view);
             const CamRec &cam = A.m.cams[view];
-            const int x = (t % A.tiles_x) * 16 + (warp & 1) * 8 + (lane & 7);
-            const int y = (t / A.tiles_x) * 8 + (warp >> 1) * 4 + (lane >> 3);
+            const int x = (tl % A.tiles_x) * 16 + (warp & 1) * 8 + (lane & 7);
+            const int y = (tl / A.tiles_x) * 8 + (warp >> 1) * 4 + (lane >> 3);
             if (x < cam.W && y < cam.H) {
                 hit = setup_ray(cam, A.m.vol, A.m.p.step_vox, x, y, R);
                 out_idx = ((long long)view * cam.H + y) * cam.W + x;
             }
-            put_features(S, A.m.vol, A.m.occ, R, hit, tid);
+            centre = ray_features(A.m.vol, A.m.occ, R, hit,
+                                  [&](int chunk, const float (&v)[8]) { store_chunk(Ag, t, chunk, v); });
         }
         float pdf[kBins], that;
-        ok = run_network(A, S, tmem, bar_m, phase, pdf, that);
+        ok = run_network(A, S, g, tmem, bar_m, phase, pdf, that);
         if (!ok) {
             mma_waited_out = true;
             break;
@@ -309,19 +380,19 @@ __global__ void __launch_bounds__(128) tc_net_kernel(const TcNetArgs A) {
                 o[kBins] = that;
             } else {
                 int b0 = 0, b1 = kBins - 1;
-                if (hit) range_of(A.m, R, pdf, b0, b1);
+                if (hit) range_of(A.m, R, pdf, centre, true, b0, b1);
                 A.range[out_idx] = make_uint2((unsigned)b0 | ((unsigned)b1 << 8), __float_as_uint(that));
             }
         }
     }
     if (!ok) {
-        if (tid == 0) atomicOr(A.err, 1);
+        if (t == 0) atomicOr(A.err, 1);
         if (mma_waited_out && A.issue_mma) tc::bar_wait(bar_m, phase, A.budget);   // MMAs may still be in flight
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_free<kTmemCols>(tmem);
+    if (tid < 32) tc::tmem_free<kTmemCols>(tmem);
 }
 
 // ---------------------------------------------------------------------------
@@ -364,16 +435,25 @@ __device__ __forceinline__ bool occupied_at(const VolDev &v, const uint8_t *occ,
 // early predictions; at most 31, and 31 if never); b_start is the
 // first bin whose start, centre or end lies in an occupied cell-brick (the
 // whole chord when none does). FP32 operations as written.
-__device__ __forceinline__ void range_of(const MarchArgs &a, const Ray &R, const float (&pdf)[kBins], int &b0,
-                                         int &b1) {
+__device__ __forceinline__ void range_of(const MarchArgs &a, const Ray &R, const float (&pdf)[kBins], uint32_t centre,
+                                         bool have_centre, int &b0, int &b1) {
     const float bw = __fdiv_rn(__fsub_rn(R.tf, R.tn), (float)kBins);
+    // bin b's start is boundary b, its end boundary b + 1 (both at
+    // fma(k, bw, t_near)); its centre bit comes from the features when known
     b0 = -1;
     b1 = kBins - 1;
-    for (int b = 0; b < kBins && b0 < 0; b++)
-        if (occupied_at(a.vol, a.occ, R, __fmaf_rn((float)b, bw, R.tn)) ||
-            occupied_at(a.vol, a.occ, R, __fmaf_rn((float)b + 0.5f, bw, R.tn)) ||
-            occupied_at(a.vol, a.occ, R, __fmaf_rn((float)b + 1.0f, bw, R.tn)))
+    bool start = occupied_at(a.vol, a.occ, R, R.tn);
+    for (int b = 0; b < kBins && b0 < 0; b++) {
+        const bool mid = have_centre ? ((centre >> b) & 1u) != 0
+                                     : occupied_at(a.vol, a.occ, R, __fmaf_rn((float)b + 0.5f, bw, R.tn));
+        if (start || mid) {
             b0 = b;
+            break;
+        }
+        const bool end = occupied_at(a.vol, a.occ, R, __fmaf_rn((float)(b + 1), bw, R.tn));
+        if (end) b0 = b;
+        start = end;
+    }
     if (b0 < 0) {
         b0 = 0;
         return;
@@ -461,7 +541,7 @@ __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A)
 #pragma unroll
             for (int b = 0; b < kBins; b++) pdf[b] = A.pdf[pix * kBins + b];
             that = A.that[pix];
-            range_of(a, R, pdf, b0, b1);
+            range_of(a, R, pdf, 0u, false, b0, b1);
         }
         march_range<ST, SHADE>(A, s_tf, R, b0, b1, C0, C1, C2, T, evald);
         if (fabsf(T - that) > A.eps) {
@@ -714,14 +794,25 @@ static cudaError_t launch_tc(const TcNetArgs &a, cudaStream_t s) {
     const int smem = (int)sizeof(NetSmem);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+    // CTAs per SM from the SM's shared memory and registers (the occupancy
+    // query does not see the carveout preference and answers 1), at most as
+    // many as the 512 TMEM columns hold
+    int dev = 0, sms = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess) return e;
-    per_sm = max(1, min(per_sm, 512 / kTmemCols));
-    const long long grid = min((long long)sms * per_sm, a.ntiles);
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    const int threads = kGroups * kGroupThreads;
+    const int by_smem = smem_sm / (smem + smem_rsv);
+    const int by_regs = regs_sm / max(1, fa.numRegs * threads);
+    const int per_sm = max(1, min(min(by_smem, by_regs), 512 / kTmemCols));
+    const long long grid = min((long long)sms * per_sm, (a.ntiles + kGroups - 1) / kGroups);
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, 128, smem, s>>>(a);
+    kern<<<(unsigned)grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
