@@ -108,11 +108,26 @@ __device__ __forceinline__ unsigned cell_address(const VolDev &v, const Cell &c)
     return b * (unsigned)kApronVox + (lz * kApron + ly) * kApron + lx;
 }
 
+// Element type of each storage.
+template <int ST> struct Voxel;
+template <> struct Voxel<RC_STORE_F32> { using T = float; };
+template <> struct Voxel<RC_STORE_F16> { using T = __half; };
+template <> struct Voxel<RC_STORE_U16> { using T = unsigned short; };
+
+// Pointer to voxel (i, j, k) of the cell's apron brick. Neighbours are read
+// as p[dx + dy + dz] with compile-time offsets (dx in -1..2, dy in
+// -19..38, dz in -361..722), which stay inside the apron brick and become
+// immediate offsets of one 64-bit address.
 template <int ST>
-__device__ __forceinline__ float fetch(const VolDev &v, unsigned off) {
-    if (ST == RC_STORE_F32) return __ldg((const float *)v.data + off);
-    if (ST == RC_STORE_F16) return __half2float(__ldg((const __half *)v.data + off));
-    return (float)__ldg((const unsigned short *)v.data + off);
+__device__ __forceinline__ const typename Voxel<ST>::T *cell_ptr(const VolDev &v, const Cell &c) {
+    return reinterpret_cast<const typename Voxel<ST>::T *>(v.data) + cell_address(v, c);
+}
+
+template <int ST>
+__device__ __forceinline__ float ldv(const typename Voxel<ST>::T *p) {
+    if (ST == RC_STORE_F32) return __ldg(reinterpret_cast<const float *>(p));
+    if (ST == RC_STORE_F16) return __half2float(__ldg(reinterpret_cast<const __half *>(p)));
+    return (float)__ldg(reinterpret_cast<const unsigned short *>(p));
 }
 
 // a + w (b - a): one rounding, stays inside [min(a,b), max(a,b)] when b - a is
@@ -121,12 +136,13 @@ __device__ __forceinline__ float lerp(float a, float b, float w) { return __fmaf
 
 template <int ST>
 __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
-    const unsigned a = cell_address(v, c);
+    const auto *p = cell_ptr<ST>(v, c);
+    constexpr int DX = (int)kDX, DY = (int)kDY, DZ = (int)kDZ;
     float wx = c.w[0], wy = c.w[1], wz = c.w[2];
-    float c00 = lerp(fetch<ST>(v, a), fetch<ST>(v, a + kDX), wx);
-    float c10 = lerp(fetch<ST>(v, a + kDY), fetch<ST>(v, a + kDY + kDX), wx);
-    float c01 = lerp(fetch<ST>(v, a + kDZ), fetch<ST>(v, a + kDZ + kDX), wx);
-    float c11 = lerp(fetch<ST>(v, a + kDZ + kDY), fetch<ST>(v, a + kDZ + kDY + kDX), wx);
+    float c00 = lerp(ldv<ST>(p), ldv<ST>(p + DX), wx);
+    float c10 = lerp(ldv<ST>(p + DY), ldv<ST>(p + DY + DX), wx);
+    float c01 = lerp(ldv<ST>(p + DZ), ldv<ST>(p + DZ + DX), wx);
+    float c11 = lerp(ldv<ST>(p + DZ + DY), ldv<ST>(p + DZ + DY + DX), wx);
     return lerp(lerp(c00, c10, wy), lerp(c01, c11, wy), wz);
 }
 
@@ -138,12 +154,12 @@ __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
 // voxels give the clamped coordinates.
 template <int ST>
 __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, float g[3]) {
-    const unsigned a = cell_address(v, c);
-    const unsigned X1 = a, X0 = a - kDX, X2 = a + kDX, X3 = a + 2 * kDX;
-    const unsigned Y0 = 0u - kDY, Y1 = 0u, Y2 = kDY, Y3 = 2 * kDY;
-    const unsigned Z0 = 0u - kDZ, Z1 = 0u, Z2 = kDZ, Z3 = 2 * kDZ;
+    const auto *p = cell_ptr<ST>(v, c);
+    constexpr int X0 = -(int)kDX, X1 = 0, X2 = (int)kDX, X3 = 2 * (int)kDX;
+    constexpr int Y0 = -(int)kDY, Y1 = 0, Y2 = (int)kDY, Y3 = 2 * (int)kDY;
+    constexpr int Z0 = -(int)kDZ, Z1 = 0, Z2 = (int)kDZ, Z3 = 2 * (int)kDZ;
     const float wx = c.w[0], wy = c.w[1], wz = c.w[2];
-#define RC_F(X, Y, Z) fetch<ST>(v, (X) + (Y) + (Z))
+#define RC_F(X, Y, Z) ldv<ST>(p + ((X) + (Y) + (Z)))
 #define RC_LX(XA, XB, Y, Z) lerp(RC_F(XA, Y, Z), RC_F(XB, Y, Z), wx)
     // rows along x (y, z) through the centre cell
     float L11 = RC_LX(X1, X2, Y1, Z1), L21 = RC_LX(X1, X2, Y2, Z1);
@@ -200,14 +216,10 @@ __device__ __forceinline__ void bspline_dweights(float t, float d[4]) {
     d[3] = 0.5f * t * t;
 }
 
-// Address of voxel (i-1, j-1, k-1) of the cell's apron brick.
-__device__ __forceinline__ unsigned cubic_origin(const VolDev &v, const Cell &c) {
-    return cell_address(v, c) - kDX - kDY - kDZ;
-}
 
 template <int ST>
 __device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
-    const unsigned a = cubic_origin(v, c);
+    const auto *a = cell_ptr<ST>(v, c) - (int)(kDX + kDY + kDZ);     // voxel (i-1, j-1, k-1)
     float wx[4], wy[4], wz[4];
     bspline_weights(c.w[0], wx);
     bspline_weights(c.w[1], wy);
@@ -218,11 +230,11 @@ __device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
         float fz = 0.0f;
 #pragma unroll
         for (int oy = 0; oy < 4; oy++) {
-            const unsigned r = a + oz * kDZ + oy * kDY;
-            float fx = fetch<ST>(v, r) * wx[0];
-            fx = __fmaf_rn(fetch<ST>(v, r + 1), wx[1], fx);
-            fx = __fmaf_rn(fetch<ST>(v, r + 2), wx[2], fx);
-            fx = __fmaf_rn(fetch<ST>(v, r + 3), wx[3], fx);
+            const auto *r = a + (oz * (int)kDZ + oy * (int)kDY);
+            float fx = ldv<ST>(r) * wx[0];
+            fx = __fmaf_rn(ldv<ST>(r + 1), wx[1], fx);
+            fx = __fmaf_rn(ldv<ST>(r + 2), wx[2], fx);
+            fx = __fmaf_rn(ldv<ST>(r + 3), wx[3], fx);
             fz = __fmaf_rn(fx, wy[oy], fz);
         }
         f = __fmaf_rn(fz, wz[oz], f);
@@ -235,7 +247,7 @@ __device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
 // their derivatives; 1/s = 2 * (0.5/s) exactly.
 template <int ST>
 __device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, float g[3]) {
-    const unsigned a = cubic_origin(v, c);
+    const auto *a = cell_ptr<ST>(v, c) - (int)(kDX + kDY + kDZ);     // voxel (i-1, j-1, k-1)
     float wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
     bspline_weights(c.w[0], wx);
     bspline_weights(c.w[1], wy);
@@ -249,9 +261,8 @@ __device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, fl
         float fz = 0.0f, gxz = 0.0f, gyz = 0.0f;
 #pragma unroll
         for (int oy = 0; oy < 4; oy++) {
-            const unsigned r = a + oz * kDZ + oy * kDY;
-            const float v0 = fetch<ST>(v, r), v1 = fetch<ST>(v, r + 1), v2 = fetch<ST>(v, r + 2),
-                        v3 = fetch<ST>(v, r + 3);
+            const auto *r = a + (oz * (int)kDZ + oy * (int)kDY);
+            const float v0 = ldv<ST>(r), v1 = ldv<ST>(r + 1), v2 = ldv<ST>(r + 2), v3 = ldv<ST>(r + 3);
             float fx = v0 * wx[0], ex = v0 * dx[0];
             fx = __fmaf_rn(v1, wx[1], fx);
             ex = __fmaf_rn(v1, dx[1], ex);

@@ -337,22 +337,25 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads) tc_net_kernel(const T
         long long out_idx = -1;
         uint32_t centre = 0;
         if (FEAT) {
-            const long long r = tile * 128 + t;
-            const float4 *src = reinterpret_cast<const float4 *>(A.feat + r * kFeat);
+            // the tile's rows are one contiguous block of 128 x 112 floats:
+            // coalesced float4 loads, each 4 features of one row -> 8 bytes
+            // of BF16 in the A operand
+            const long long r0 = tile * 128;
+            const long long valid = min((long long)128, A.n - r0);
+            const float4 *src = reinterpret_cast<const float4 *>(A.feat + r0 * kFeat);
 #pragma unroll 7
-            for (int c = 0; c < kFeat / 8; c++) {
-                float v[8];
-                if (r < A.n) {
-                    const float4 lo = __ldg(src + 2 * c), hi = __ldg(src + 2 * c + 1);
-                    v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
-                    v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; i++) v[i] = 0.0f;
-                }
-                store_chunk(Ag, t, c, v);
+            for (int i = 0; i < 128 * kFeat / 4 / kGroupThreads; i++) {
+                const int e = i * kGroupThreads + t;          // float4 index within the tile
+                const int row = e / (kFeat / 4), k = (e % (kFeat / 4)) * 4;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (row < valid) v = __ldg(src + e);
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+                uint2 q;
+                q.x = *reinterpret_cast<uint32_t *>(&lo);
+                q.y = *reinterpret_cast<uint32_t *>(&hi);
+                *reinterpret_cast<uint2 *>(Ag + tc::core_offset(row, k, 128)) = q;
             }
-            if (r < A.n) out_idx = r;
+            if (t < valid) out_idx = r0 + t;
         } else {
             const int per_view = A.tiles_x * A.tiles_y;
             const int view = (int)(tile / per_view), tl = (int)(tile % per_view);
