@@ -65,6 +65,7 @@ struct rc_volume {
     int cb[3] = {0, 0, 0};       // cell-bricks per axis (each stored as a 19^3 apron brick)
     int nbricks = 0;             // cell-bricks
     void *d_data = nullptr;
+    float4 *d_vg = nullptr;      // F32 storage: value+gradient bricks
     uint16_t *d_stage = nullptr;
     // min/max grid and occupancy mask per reconstruction filter (index rc_filter)
     uint16_t *d_mn[2] = {nullptr, nullptr}, *d_mx[2] = {nullptr, nullptr};
@@ -243,6 +244,7 @@ rc_status rc_context_destroy(rc_context *ctx) {
 // ---------------------------------------------------------------------------
 static void volume_free(rc_volume *v) {
     cudaFree(v->d_data);
+    cudaFree(v->d_vg);
     cudaFree(v->d_stage);
     for (int f = 0; f < 2; f++) {
         cudaFree(v->d_mn[f]);
@@ -279,7 +281,9 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
     v->nbricks = v->cb[0] * v->cb[1] * v->cb[2];
     size_t esz = storage == RC_STORE_F32 ? 4 : 2;
     size_t nvox = (size_t)nx * ny * nz;
+    const size_t vg_bytes = storage == RC_STORE_F32 ? (size_t)v->nbricks * kGradVox * sizeof(float4) : 0;
     if (dev_alloc(&v->d_data, (size_t)padded * esz) != cudaSuccess ||
+        (vg_bytes && dev_alloc(&v->d_vg, vg_bytes) != cudaSuccess) ||
         dev_alloc(&v->d_stage, nvox * sizeof(uint16_t)) != cudaSuccess ||
         dev_alloc(&v->d_mn[0], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
         dev_alloc(&v->d_mx[0], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
@@ -300,6 +304,7 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
 static VolDev vol_dev(const rc_volume *v) {
     VolDev d;
     d.data = v->d_data;
+    d.vg = v->d_vg;
     d.storage = (int)v->storage;
     float smin = fminf(fminf(v->s[0], v->s[1]), v->s[2]);
     for (int a = 0; a < 3; a++) {
@@ -327,6 +332,7 @@ rc_status rc_volume_upload(rc_volume *v, const uint16_t *src, size_t n_voxels, i
                                  src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     VolDev d = vol_dev(v);
     RC_CUDA(ctx, launch_relayout(v->d_stage, d, v->d_data, ctx->stream));
+    if (v->d_vg) RC_CUDA(ctx, launch_gradvol(v->d_stage, d, v->d_vg, ctx->stream));
     RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, RC_FILTER_TRILINEAR, v->d_mn[0], v->d_mx[0],
                                ctx->stream));
     v->uploaded = true;

@@ -134,6 +134,10 @@ __device__ __forceinline__ float ldv(const typename Voxel<ST>::T *p) {
 // exact (true for integer codes and for FP16 values in [0, 1]).
 __device__ __forceinline__ float lerp(float a, float b, float w) { return __fmaf_rn(w, b - a, a); }
 
+__device__ __forceinline__ float4 lerp4(const float4 &a, const float4 &b, float w) {
+    return make_float4(lerp(a.x, b.x, w), lerp(a.y, b.y, w), lerp(a.z, b.z, w), lerp(a.w, b.w, w));
+}
+
 template <int ST>
 __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
     const auto *p = cell_ptr<ST>(v, c);
@@ -146,6 +150,29 @@ __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
     return lerp(lerp(c00, c10, wy), lerp(c01, c11, wy), wz);
 }
 
+// Value and world-space gradient from the value+gradient bricks (FP32
+// storage): each voxel holds (V, D_x, D_y, D_z) with D_a = V(+1 along a) -
+// V(-1 along a), neighbour indices clamped to the volume, all exact integers.
+// Central differences of the trilinear field are linear in the voxels, so
+// (f(p + e_a) - f(p - e_a)) / 2 equals the trilinear interpolation of D_a / 2
+// at p, the clamped border included; 8 four-wide loads replace 32 scalar
+// loads. The value is interpolated in the same order as trilinear().
+__device__ __forceinline__ float value_grad_vg(const VolDev &v, const Cell &c, float g[3]) {
+    const float4 *p = v.vg + (size_t)brick_of(v, c) * kGradVox +
+                      (((c.i[2] & 15) * kGradEdge + (c.i[1] & 15)) * kGradEdge + (c.i[0] & 15));
+    constexpr int DY = kGradEdge, DZ = kGradEdge * kGradEdge;
+    const float wx = c.w[0], wy = c.w[1], wz = c.w[2];
+    const float4 c00 = lerp4(__ldg(p), __ldg(p + 1), wx);
+    const float4 c10 = lerp4(__ldg(p + DY), __ldg(p + DY + 1), wx);
+    const float4 c01 = lerp4(__ldg(p + DZ), __ldg(p + DZ + 1), wx);
+    const float4 c11 = lerp4(__ldg(p + DZ + DY), __ldg(p + DZ + DY + 1), wx);
+    const float4 r = lerp4(lerp4(c00, c10, wy), lerp4(c01, c11, wy), wz);
+    g[0] = r.y * v.inv2s[0];
+    g[1] = r.z * v.inv2s[1];
+    g[2] = r.w * v.inv2s[2];
+    return r.x;
+}
+
 // Value and world-space central-difference gradient of the trilinear field,
 // one index unit per axis, from the 32 distinct voxels around the cell.
 // The samples at p -/+ e_a use the cells with base coordinates
@@ -154,6 +181,7 @@ __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
 // voxels give the clamped coordinates.
 template <int ST>
 __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, float g[3]) {
+    if (ST == RC_STORE_F32) return value_grad_vg(v, c, g);
     const auto *p = cell_ptr<ST>(v, c);
     constexpr int X0 = -(int)kDX, X1 = 0, X2 = (int)kDX, X3 = 2 * (int)kDX;
     constexpr int Y0 = -(int)kDY, Y1 = 0, Y2 = (int)kDY, Y3 = 2 * (int)kDY;
@@ -299,10 +327,6 @@ __device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, in
     float4 a = tab[i], b = tab[i + 1];
     if (i0) *i0 = i;
     if (w0) *w0 = w;
-    return make_float4(lerp(a.x, b.x, w), lerp(a.y, b.y, w), lerp(a.z, b.z, w), lerp(a.w, b.w, w));
-}
-
-__device__ __forceinline__ float4 lerp4(const float4 &a, const float4 &b, float w) {
     return make_float4(lerp(a.x, b.x, w), lerp(a.y, b.y, w), lerp(a.z, b.z, w), lerp(a.w, b.w, w));
 }
 

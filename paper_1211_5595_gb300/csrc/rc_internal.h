@@ -12,6 +12,8 @@ namespace rc {
 constexpr int kBrick = 16;          // cell-brick edge (trilinear cells)
 constexpr int kApron = 19;          // stored brick edge: cells 16b-1 .. 16b+17 (edges replicated)
 constexpr int kApronVox = kApron * kApron * kApron;   // 6859
+constexpr int kGradEdge = 17;       // value+gradient brick edge: voxels 16b .. 16b+16 (the trilinear footprint)
+constexpr int kGradVox = kGradEdge * kGradEdge * kGradEdge;   // 4913
 
 // Camera record: FP64 look-at basis rounded once to FP32, eye in index space.
 struct CamRec {
@@ -24,6 +26,7 @@ struct CamRec {
 // Device view of a bricked volume.
 struct VolDev {
     const void *data;      // [bz][by][bx][19][19][19] apron bricks, storage type
+    const float4 *vg;      // F32 storage: [bz][by][bx][17][17][17] (value, central differences x2), else null
     int storage;           // rc_storage
     int n[3];              // voxels per axis
     int cb[3];             // cell-bricks per axis: ceil((n-1)/16)
@@ -158,6 +161,7 @@ struct TrainArgs {
 
 // ---- launchers (return the launch error) --------------------------------
 cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStream_t s);
+cudaError_t launch_gradvol(const uint16_t *stage, VolDev v, float4 *dst, cudaStream_t s);
 cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax, int filter,
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);
 cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax,

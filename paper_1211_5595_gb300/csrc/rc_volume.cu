@@ -48,6 +48,40 @@ cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStre
     return cudaGetLastError();
 }
 
+// One thread per element of the value+gradient bricks (FP32 storage): brick b
+// holds voxels 16b .. 16b+16 per axis (clamped to the volume) as
+// (V, V(x+1) - V(x-1), V(y+1) - V(y-1), V(z+1) - V(z-1)), neighbour
+// indices clamped to the volume, codes clamped to vmax; exact in FP32.
+__global__ void gradvol_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int cb0, int cb1,
+                               float4 *dst, long long total) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int local = (int)(e % kGradVox);
+    const long long brick = e / kGradVox;
+    const int bx = (int)(brick % cb0);
+    const long long r = brick / cb0;
+    const int by = (int)(r % cb1);
+    const int bz = (int)(r / cb1);
+    const int lx = local % kGradEdge, ly = (local / kGradEdge) % kGradEdge, lz = local / (kGradEdge * kGradEdge);
+    const int x = min(bx * kBrick + lx, nx - 1), y = min(by * kBrick + ly, ny - 1), z = min(bz * kBrick + lz, nz - 1);
+    auto code = [&](int xx, int yy, int zz) {
+        return (float)min((int)stage[((size_t)zz * ny + yy) * nx + xx], vmax);
+    };
+    float4 o;
+    o.x = code(x, y, z);
+    o.y = code(min(x + 1, nx - 1), y, z) - code(max(x - 1, 0), y, z);
+    o.z = code(x, min(y + 1, ny - 1), z) - code(x, max(y - 1, 0), z);
+    o.w = code(x, y, min(z + 1, nz - 1)) - code(x, y, max(z - 1, 0));
+    dst[e] = o;
+}
+
+cudaError_t launch_gradvol(const uint16_t *stage, VolDev v, float4 *dst, cudaStream_t s) {
+    const long long total = (long long)v.cb[0] * v.cb[1] * v.cb[2] * kGradVox;
+    gradvol_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0],
+                                                                     v.cb[1], dst, total);
+    return cudaGetLastError();
+}
+
 // One block per cell-brick: min and max of the (clamped) codes over the
 // footprint voxels max(16b - before, 0) .. min(16b + after, N - 1) per axis:
 // (0, 16) for trilinear samples, (1, 17) for cubic B-spline samples.
