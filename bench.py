@@ -3,8 +3,9 @@
 16^3 min/max brick grid for empty-space skipping, early termination at 0.99).
 
 One step = one pass of the whole hot path over the resident phantom: re-layout
-and min/max grid from the device copy of the codes, occupancy mask for the
-transfer function, then the 36 views rendered. Metric: dense-equivalent
+into apron bricks and value+gradient bricks and the min/max grid from the
+device copy of the codes, occupancy mask for the transfer function, then the
+36 views rendered in one launch. Metric: dense-equivalent
 Gsamples/s (samples of the plain march up to termination, skipped ones
 included) and ms/frame.
 
@@ -35,7 +36,7 @@ import synth  # noqa: E402
 
 WORKLOAD = "shaded_256x256x180"
 METRIC = "Gsamples/s (dense-equivalent), 1024^2 of 256x256x180 u16, shaded, 36-view orbit"
-BYTES_PER_SAMPLE = 128          # 32 distinct FP32 voxels per shaded sample
+BYTES_PER_SAMPLE = 128          # 32 distinct FP32 voxels per shaded sample (8 value+gradient float4)
 TF2_GMAX = 1200.0               # gradient magnitude (codes per mm) of the 2-D table's last row
 L2_FLUSH_BYTES = 256 << 20      # > 129 MB L2
 
@@ -560,7 +561,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded head phantom, Rician noise)",
-        "config": {"workload": WORKLOAD, "volume": "256x256x180 u16 -> FP32 16^3 bricks", "image": "1024x1024",
+        "config": {"workload": WORKLOAD, "volume": "256x256x180 u16 -> FP32 19^3 apron bricks + 17^3 value+gradient bricks", "image": "1024x1024",
                    "views": nviews, "step_vox": w["step"], "shading": "Blinn-Phong headlight",
                    "skip": "16^3 min/max brick grid", "term": w["term"],
                    "l2": "flushed between steps (256 MB write, outside the step events)",
@@ -569,11 +570,11 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "kernel": "composite_kernel<F32, shaded>, one launch per step for all views",
-                     "model": f"{BYTES_PER_SAMPLE} B per evaluated sample (32 distinct FP32 voxels) / mean launch time",
+                     "model": f"{BYTES_PER_SAMPLE} B per evaluated sample (32 distinct FP32 voxels = 8 value+gradient float4) / mean launch time",
                      "peak_kind": f"{peak_kind} copy bandwidth"},
         "e2e": e2e,
         "forms": forms,
-        "gpu_launches": args.steps * (2 + 1 + 1 + 1),
+        "gpu_launches": args.steps * 6,     # per step: re-layout, value+gradient bricks, min/max grid, table, occupancy, march
         "clocks": clocks.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
