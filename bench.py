@@ -227,8 +227,9 @@ def filter_forms(rc, ctx, vol, w, P, cam_structs, outs, ref_imgs, flush, stream,
 
 def adjoint_form(rc, ctx, flush, stream):
     """Transfer-function gradient on the differentiable workload (128x128x96,
-    8 views at 512^2, unshaded, step 0.5): time of rc_render_backward per view
-    against the forward render of the same view, with the samples each pass
+    8 views at 512^2, unshaded, step 0.5): time of rc_render_backward_views
+    over the 8 views (one launch, gradient summed) per view against the
+    forward rc_render_views of the same views, with the samples each pass
     marches (the backward recomputes the forward, then marches again)."""
     import torch
     wd = synth.WORKLOADS["diff_128x128x96"]
@@ -247,22 +248,26 @@ def adjoint_form(rc, ctx, flush, stream):
     for cam in cams:
         rc.rc_camera_set(ctx, cam)
         dense += rc.rc_render(ctx, vol, P, img, stats=True)["dense_samples"]
-    fwd, bwd = [], []
-    for rep in range(3):
-        for cam in cams:
-            rc.rc_camera_set(ctx, cam)
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            e[0].record(stream)
-            rc.rc_render(ctx, vol, P, img)
-            e[1].record(stream)
-            rc.rc_render_backward(ctx, vol, P, g, dtf)
-            e[2].record(stream)
-            if rep > 0:
-                fwd.append(e)
+    # every view in one launch: the forward render and the gradient summed
+    # over the views (the loss of a table fit to the orbit)
+    n = len(cams)
+    cam_structs = [rc.make_camera(c) for c in cams]
+    imgs = torch.empty((n, wd["height"], wd["width"], 4), device="cuda")
+    G = torch.randn(imgs.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    ev = []
+    for rep in range(4):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        rc.rc_render_views(ctx, vol, P, cam_structs, imgs)
+        e[1].record(stream)
+        rc.rc_render_backward_views(ctx, vol, P, cam_structs, G, dtf)
+        e[2].record(stream)
+        if rep > 0:
+            ev.append(e)
         flush.zero_()
     torch.cuda.synchronize()
-    f_ms = statistics.median(a.elapsed_time(b) for a, b, c in fwd)
-    b_ms = statistics.median(b.elapsed_time(c) for a, b, c in fwd)
+    f_ms = statistics.median(a.elapsed_time(b) for a, b, c in ev) / n
+    b_ms = statistics.median(b.elapsed_time(c) for a, b, c in ev) / n
     rc.rc_volume_destroy(ctx, vol)
     per_view = dense / len(cams)
     return {"workload": "diff_128x128x96", "views": len(cams), "image": "512x512",

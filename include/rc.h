@@ -219,6 +219,15 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol,
                              const rc_render_params *params, const float *dL_dimage,
                              float *dL_dtf);
 
+/* The gradient summed over nviews cameras (1..65535, one image size) in one
+ * launch, for a loss over several views of the same volume and table (the
+ * fitting of a table to an orbit): dL_dimages device nviews*H*W*4 floats,
+ * view-major; dL_dtf as above, overwritten with the sum. Same per-view
+ * arithmetic as rc_render_backward; the fixed-point scale is set by the
+ * largest |dL/dI| over all views. The context's own camera is not changed. */
+rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                                   const rc_camera *cams, int nviews, const float *dL_dimages, float *dL_dtf);
+
 /* The gradient of rc_render_backward for callers that cannot allocate device
  * memory once they are running: for example a host application whose device
  * memory is all handed out up front by its own allocator, or a frame loop in

@@ -88,6 +88,7 @@ SIGNATURES = {
     "rc_proposal_train_step": (_I, [_P, _P, _P, C.c_int64, C.c_float, _P]),
     "rc_render_importance": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P, _I, C.c_float, _P, _P,
                                   C.POINTER(rc_stats)]),
+    "rc_render_backward_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P, _P]),
     "rc_render_proposal": (_I, [_P, _P, C.POINTER(rc_render_params), _I, C.c_float, _P, _P, C.POINTER(rc_stats)]),
     "rc_render_proposal_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _I, C.c_float,
                                       _P, _P, C.POINTER(rc_stats)]),
@@ -284,6 +285,14 @@ def rc_render_backward(ctx, vol, params, dimage, dtf):
     p = _params(params)
     _check(lib().rc_render_backward(ctx, vol, C.byref(p), _ptr(dimage), _ptr(dtf)), ctx,
            "rc_render_backward")
+
+
+def rc_render_backward_views(ctx, vol, params, cams, dimages, dtf):
+    """Table gradient summed over every camera's view (dimages: CUDA float32 n x H x W x 4)."""
+    p = _params(params)
+    arr = (rc_camera * len(cams))(*[c if isinstance(c, rc_camera) else make_camera(c) for c in cams])
+    _check(lib().rc_render_backward_views(ctx, vol, C.byref(p), arr, len(cams), _ptr(dimages), _ptr(dtf)), ctx,
+           "rc_render_backward_views")
 
 
 def rc_render_backward_noalloc(ctx, vol, params, dimage, dtf):

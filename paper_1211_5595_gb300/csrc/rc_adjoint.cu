@@ -72,13 +72,14 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
     __syncthreads();
     const float scale = fixed_scale(absmax);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const CamRec cam = a.cams ? a.cams[blockIdx.z] : a.cam;
     const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-    const bool inimg = x < a.cam.W && y < a.cam.H;
+    const bool inimg = x < cam.W && y < cam.H;
     Ray R;
-    bool hit = inimg && setup_ray(a.cam, a.vol, a.p.step_vox, x, y, R);
+    bool hit = inimg && setup_ray(cam, a.vol, a.p.step_vox, x, y, R);
     float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (hit) g = A.dimg[(size_t)y * a.cam.W + x];
+    if (hit) g = A.dimg[((size_t)blockIdx.z * cam.H + y) * cam.W + x];
     const bool has_g = hit && (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f);
     // pass 1: the forward march, with exact empty-space skipping (identical
     // result), for C_final, T_final and the sample count n up to termination
@@ -176,33 +177,35 @@ __global__ void finalize_kernel(const long long *acc, int n, const float *absmax
 }
 
 template <typename Kern>
-static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, const float *absmax, cudaStream_t s) {
+static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
     size_t smem = (size_t)a.m.tf.K * (sizeof(float4) + 4 * sizeof(long long));
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((a.m.cam.W + 15) / 16, (a.m.cam.H + 7) / 8);
+    dim3 grid((a.m.cam.W + 15) / 16, (a.m.cam.H + 7) / 8, nviews);
     kern<<<grid, 128, smem, s>>>(a, absmax);
     return cudaGetLastError();
 }
 
 // acc must hold 4K long longs followed by one float (the |dL/dI| maximum).
-cudaError_t launch_adjoint(const AdjointArgs &a, float *dL_dtf, cudaStream_t s) {
+// With a.m.cams, nviews views (grid.z), dimg view-major; the gradient is the
+// sum over the views.
+cudaError_t launch_adjoint(const AdjointArgs &a, int nviews, float *dL_dtf, cudaStream_t s) {
     const int K = a.m.tf.K;
     float *absmax = reinterpret_cast<float *>(a.acc + 4 * K);
-    cudaError_t e = launch_absmax(reinterpret_cast<const float *>(a.dimg), (long long)a.m.cam.W * a.m.cam.H * 4,
-                                  absmax, s);
+    cudaError_t e = launch_absmax(reinterpret_cast<const float *>(a.dimg),
+                                  (long long)nviews * a.m.cam.W * a.m.cam.H * 4, absmax, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * K, s);
     if (e != cudaSuccess) return e;
     switch (a.m.vol.storage * 2 + (a.m.p.shade ? 1 : 0)) {
-        case RC_STORE_F32 * 2: e = launch_adj(adjoint_kernel<RC_STORE_F32, false>, a, absmax, s); break;
-        case RC_STORE_F32 * 2 + 1: e = launch_adj(adjoint_kernel<RC_STORE_F32, true>, a, absmax, s); break;
-        case RC_STORE_F16 * 2: e = launch_adj(adjoint_kernel<RC_STORE_F16, false>, a, absmax, s); break;
-        case RC_STORE_F16 * 2 + 1: e = launch_adj(adjoint_kernel<RC_STORE_F16, true>, a, absmax, s); break;
-        case RC_STORE_U16 * 2: e = launch_adj(adjoint_kernel<RC_STORE_U16, false>, a, absmax, s); break;
-        default: e = launch_adj(adjoint_kernel<RC_STORE_U16, true>, a, absmax, s);
+        case RC_STORE_F32 * 2: e = launch_adj(adjoint_kernel<RC_STORE_F32, false>, a, nviews, absmax, s); break;
+        case RC_STORE_F32 * 2 + 1: e = launch_adj(adjoint_kernel<RC_STORE_F32, true>, a, nviews, absmax, s); break;
+        case RC_STORE_F16 * 2: e = launch_adj(adjoint_kernel<RC_STORE_F16, false>, a, nviews, absmax, s); break;
+        case RC_STORE_F16 * 2 + 1: e = launch_adj(adjoint_kernel<RC_STORE_F16, true>, a, nviews, absmax, s); break;
+        case RC_STORE_U16 * 2: e = launch_adj(adjoint_kernel<RC_STORE_U16, false>, a, nviews, absmax, s); break;
+        default: e = launch_adj(adjoint_kernel<RC_STORE_U16, true>, a, nviews, absmax, s);
     }
     if (e != cudaSuccess) return e;
     finalize_kernel<<<(4 * K + 255) / 256, 256, 0, s>>>(a.acc, 4 * K, absmax, dL_dtf);

@@ -585,6 +585,60 @@ static rc_status check_render(rc_context *ctx, const rc_volume *v, const rc_rend
     return RC_OK;
 }
 
+// A set of views: 1..65535 valid cameras of one image size, at most 2^31
+// pixels in all.
+static rc_status check_views(rc_context *ctx, const rc_camera *cams, int nviews, const char *who) {
+    if (!cams || nviews < 1 || nviews > 65535)
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: %d cameras", who, cams ? nviews : 0);
+    for (int i = 0; i < nviews; i++) {
+        rc_status st = check_camera(ctx, &cams[i], who);
+        if (st != RC_OK) return st;
+        if (cams[i].width != cams[0].width || cams[i].height != cams[0].height)
+            return fail(ctx, RC_ERR_INVALID_ARG, "%s: camera %d has another image size", who, i);
+    }
+    if ((long long)nviews * cams[0].width * cams[0].height > (1ll << 31))
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: %d views of %d x %d pixels", who, nviews, cams[0].width,
+                    cams[0].height);
+    return RC_OK;
+}
+
+// Copies the views' camera records (for volume v) to the context's device
+// array, growing it when needed; *first receives record 0.
+static rc_status upload_views(rc_context *ctx, const rc_volume *v, const rc_camera *cams, int nviews, CamRec *first,
+                              const char *who) {
+    if (ctx->cams_cap < nviews) {
+        CamRec *buf = nullptr;
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // queued kernels may still read the old records
+        RC_CUDA(ctx, dev_alloc(&buf, (size_t)nviews * sizeof(CamRec)));
+        cudaFree(ctx->d_cams);
+        ctx->d_cams = buf;
+        ctx->cams_cap = nviews;
+    }
+    CamRec *recs = new (std::nothrow) CamRec[nviews];
+    if (!recs) return fail(ctx, RC_ERR_OOM, "%s: host allocation", who);
+    for (int i = 0; i < nviews; i++) recs[i] = camera_record(cams[i], v->s);
+    // pageable source: the copy is staged before the call returns
+    cudaError_t ce = cudaMemcpyAsync(ctx->d_cams, recs, (size_t)nviews * sizeof(CamRec), cudaMemcpyHostToDevice,
+                                     ctx->stream);
+    *first = recs[0];
+    delete[] recs;
+    RC_CUDA(ctx, ce);
+    return RC_OK;
+}
+
+// The render checks with cams[0] standing in for the context's camera.
+static rc_status check_render_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                    const rc_camera *cams, const void *out, const char *who) {
+    const bool had = ctx->cam_set;
+    const rc_camera keep = ctx->cam;
+    ctx->cam = cams[0];
+    ctx->cam_set = true;
+    rc_status st = check_render(ctx, vol, p, out, who);
+    ctx->cam = keep;
+    ctx->cam_set = had;
+    return st;
+}
+
 // The table gradient and the learned proposal march trilinear samples
 // classified by a 1-D table.
 static rc_status check_plain_form(rc_context *ctx, const rc_render_params *p, const char *who) {
@@ -702,51 +756,22 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
 
 rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const rc_camera *cams,
                           int nviews, float *out_rgba, rc_stats *stats) {
-    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_render_views: ctx is NULL");
-    if (!cams || nviews < 1 || nviews > 65535)
-        return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_views: %d cameras", cams ? nviews : 0);
-    for (int i = 0; i < nviews; i++) {
-        rc_status st = check_camera(ctx, &cams[i], "rc_render_views");
-        if (st != RC_OK) return st;
-        if (cams[i].width != cams[0].width || cams[i].height != cams[0].height)
-            return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_views: camera %d has another image size", i);
-    }
-    if ((long long)nviews * cams[0].width * cams[0].height > (1ll << 31))
-        return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_views: %d views of %d x %d pixels", nviews, cams[0].width,
-                    cams[0].height);
-    // the render checks need a camera; the first view's is used only for them
-    const bool had = ctx->cam_set;
-    const rc_camera keep = ctx->cam;
-    ctx->cam = cams[0];
-    ctx->cam_set = true;
-    rc_status st = check_render(ctx, vol, p, out_rgba, "rc_render_views");
-    ctx->cam = keep;
-    ctx->cam_set = had;
+    const char *who = "rc_render_views";
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
+    rc_status st = check_views(ctx, cams, nviews, who);
+    if (st == RC_OK) st = check_render_views(ctx, vol, p, cams, out_rgba, who);
     if (st != RC_OK) return st;
     DeviceScope ds(ctx->device);
-    if (ctx->cams_cap < nviews) {
-        CamRec *buf = nullptr;
-        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        RC_CUDA(ctx, dev_alloc(&buf, (size_t)nviews * sizeof(CamRec)));
-        cudaFree(ctx->d_cams);
-        ctx->d_cams = buf;
-        ctx->cams_cap = nviews;
-    }
     rc_volume *v = const_cast<rc_volume *>(vol);
     if (p->skip && p->func == RC_FUNC_COMPOSITE) {
         st = ensure_occupancy(ctx, v, p->filter);
         if (st != RC_OK) return st;
     }
-    CamRec *recs = new (std::nothrow) CamRec[nviews];
-    if (!recs) return fail(ctx, RC_ERR_OOM, "rc_render_views: host allocation");
-    for (int i = 0; i < nviews; i++) recs[i] = camera_record(cams[i], v->s);
-    // pageable source: the copy is staged before the call returns
-    cudaError_t ce = cudaMemcpyAsync(ctx->d_cams, recs, (size_t)nviews * sizeof(CamRec), cudaMemcpyHostToDevice,
-                                     ctx->stream);
+    CamRec first;
+    st = upload_views(ctx, v, cams, nviews, &first, who);
+    if (st != RC_OK) return st;
     MarchArgs a = march_args(ctx, v, p, out_rgba);
-    a.cam = recs[0];
-    delete[] recs;
-    RC_CUDA(ctx, ce);
+    a.cam = first;
     a.cams = ctx->d_cams;
     if (stats) {
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
@@ -783,7 +808,45 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_ren
     a.dimg = reinterpret_cast<const float4 *>(dL_dimage);
     a.acc = reinterpret_cast<long long *>(ctx->d_scratch);
     a.acc_scale = 0.0f;
-    RC_CUDA(ctx, launch_adjoint(a, dL_dtf, ctx->stream));
+    RC_CUDA(ctx, launch_adjoint(a, 1, dL_dtf, ctx->stream));
+    return RC_OK;
+}
+
+rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                   const rc_camera *cams, int nviews, const float *dL_dimages, float *dL_dtf) {
+    const char *who = "rc_render_backward_views";
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
+    rc_status st = check_views(ctx, cams, nviews, who);
+    if (st == RC_OK) st = check_render_views(ctx, vol, p, cams, dL_dtf, who);
+    if (st == RC_OK) st = check_plain_form(ctx, p, who);
+    if (st != RC_OK) return st;
+    if (!dL_dimages) return fail(ctx, RC_ERR_INVALID_ARG, "%s: dL_dimages is NULL", who);
+    if (p->func != RC_FUNC_COMPOSITE) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: compositing function only", who);
+    DeviceScope ds(ctx->device);
+    size_t need = (size_t)4 * ctx->K * sizeof(long long) + 16;
+    if (ctx->scratch_bytes < need) {
+        void *buf = nullptr;
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        RC_CUDA(ctx, dev_alloc(&buf, need));
+        cudaFree(ctx->d_scratch);
+        ctx->d_scratch = buf;
+        ctx->scratch_bytes = need;
+    }
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
+    if (st != RC_OK) return st;
+    CamRec first;
+    st = upload_views(ctx, v, cams, nviews, &first, who);
+    if (st != RC_OK) return st;
+    AdjointArgs a;
+    a.m = march_args(ctx, v, p, nullptr);
+    a.m.p.skip = 0;
+    a.m.cam = first;
+    a.m.cams = ctx->d_cams;
+    a.dimg = reinterpret_cast<const float4 *>(dL_dimages);
+    a.acc = reinterpret_cast<long long *>(ctx->d_scratch);
+    a.acc_scale = 0.0f;
+    RC_CUDA(ctx, launch_adjoint(a, nviews, dL_dtf, ctx->stream));
     return RC_OK;
 }
 
@@ -848,7 +911,7 @@ rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, cons
     a.dimg = reinterpret_cast<const float4 *>(dL_dimage);
     a.acc = scratch;            // cleared on the stream before the kernel runs
     a.acc_scale = 0.0f;
-    RC_CUDA(ctx, launch_adjoint(a, dL_dtf, ctx->stream));
+    RC_CUDA(ctx, launch_adjoint(a, 1, dL_dtf, ctx->stream));
     return RC_OK;
 }
 
@@ -1150,21 +1213,14 @@ static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_
                                 const char *who) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
     if (!ctx->net_loaded) return fail(ctx, RC_ERR_STATE, "%s: no network loaded", who);
-    if (!cams || nviews < 1 || nviews > 65535)
-        return fail(ctx, RC_ERR_INVALID_ARG, "%s: %d cameras", who, cams ? nviews : 0);
-    for (int i = 0; i < nviews; i++) {
-        rc_status st = check_camera(ctx, &cams[i], who);
-        if (st != RC_OK) return st;
-        if (cams[i].width != cams[0].width || cams[i].height != cams[0].height)
-            return fail(ctx, RC_ERR_INVALID_ARG, "%s: camera %d has another image size", who, i);
-    }
+    rc_status st = check_views(ctx, cams, nviews, who);
+    if (st != RC_OK) return st;
     const long long nrays = (long long)nviews * cams[0].width * cams[0].height;
-    if (nrays > (1ll << 31)) return fail(ctx, RC_ERR_INVALID_ARG, "%s: %lld rays", who, nrays);
     const bool had = ctx->cam_set;
     const rc_camera keep = ctx->cam;
     ctx->cam = cams[0];
     ctx->cam_set = true;
-    rc_status st = check_importance(ctx, vol, p, out, nimp, eps, who);
+    st = check_importance(ctx, vol, p, out, nimp, eps, who);
     ctx->cam = keep;
     ctx->cam_set = had;
     if (st != RC_OK) return st;
@@ -1172,31 +1228,17 @@ static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_
     rc_volume *v = const_cast<rc_volume *>(vol);
     st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
     if (st != RC_OK) return st;
-    if (ctx->cams_cap < nviews || ctx->range_cap < nrays) {
-        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // queued kernels may still use the old buffers
-        if (ctx->cams_cap < nviews) {
-            CamRec *buf = nullptr;
-            RC_CUDA(ctx, dev_alloc(&buf, (size_t)nviews * sizeof(CamRec)));
-            cudaFree(ctx->d_cams);
-            ctx->d_cams = buf;
-            ctx->cams_cap = nviews;
-        }
-        if (ctx->range_cap < nrays) {
-            uint2 *buf = nullptr;
-            RC_CUDA(ctx, dev_alloc(&buf, (size_t)nrays * sizeof(uint2)));
-            cudaFree(ctx->d_range);
-            ctx->d_range = buf;
-            ctx->range_cap = nrays;
-        }
+    if (ctx->range_cap < nrays) {
+        uint2 *buf = nullptr;
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // queued kernels may still use the old records
+        RC_CUDA(ctx, dev_alloc(&buf, (size_t)nrays * sizeof(uint2)));
+        cudaFree(ctx->d_range);
+        ctx->d_range = buf;
+        ctx->range_cap = nrays;
     }
-    CamRec *recs = new (std::nothrow) CamRec[nviews];
-    if (!recs) return fail(ctx, RC_ERR_OOM, "%s: host allocation", who);
-    for (int i = 0; i < nviews; i++) recs[i] = camera_record(cams[i], v->s);
-    cudaError_t ce = cudaMemcpyAsync(ctx->d_cams, recs, (size_t)nviews * sizeof(CamRec), cudaMemcpyHostToDevice,
-                                     ctx->stream);
-    const CamRec first = recs[0];
-    delete[] recs;
-    RC_CUDA(ctx, ce);
+    CamRec first;
+    st = upload_views(ctx, v, cams, nviews, &first, who);
+    if (st != RC_OK) return st;
     TcNetArgs n{};
     n.m = march_args(ctx, v, p, nullptr);
     n.m.cam = first;

@@ -169,7 +169,7 @@ cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks
 cudaError_t launch_march(const MarchArgs &a, int nviews, cudaStream_t s);
 cudaError_t launch_march_cubic(const MarchArgs &a, int nviews, cudaStream_t s);   // filter = B-spline
 cudaError_t launch_march_tf2(const MarchArgs &a, int nviews, cudaStream_t s);     // trilinear, 2-D table
-cudaError_t launch_adjoint(const AdjointArgs &a, float *dL_dtf, cudaStream_t s);
+cudaError_t launch_adjoint(const AdjointArgs &a, int nviews, float *dL_dtf, cudaStream_t s);
 cudaError_t launch_absmax(const float *x, long long n, float *out, cudaStream_t s);
 cudaError_t launch_profiles(const MarchArgs &a, float *out, cudaStream_t s);
 cudaError_t launch_features(const MarchArgs &a, float *out, cudaStream_t s);

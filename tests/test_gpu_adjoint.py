@@ -84,6 +84,40 @@ def test_gradient_matches_oracle(rc, orc, c4, shade, term):
     assert np.abs(total_o).sum() > 0
 
 
+def test_views_gradient_matches_oracle_and_single_views(rc, orc, c4):
+    """One launch over all 8 views: the summed gradient equals the oracle's
+    sum over the views, and the sum of the per-view gradients (to the
+    fixed-point resolution: the views call has one scale for all views)."""
+    import torch
+    ph, ctx, vol, cams = c4
+    tf = init_tf()
+    term = 0.99
+    gs, total_o, total_1 = [], np.zeros((W["K"], 4)), np.zeros((W["K"], 4))
+    for v, cam in enumerate(cams):
+        pix = synth.sample_pixels(W["width"], W["height"], 2048, seed=900 + v)
+        sc = orc.Scene(ph.vol, ph.spacing, tf, cam, step=W["step"], term=term)
+        keep = pix[~orc.render(sc, pixels=pix)["tie"]]
+        g = seeded_upstream(950 + v, keep, (W["height"], W["width"]))
+        gs.append(g)
+        og, _ = orc.render_grad(sc, g[keep], pixels=keep)
+        total_o += og
+        total_1 += gpu_grad(rc, ctx, vol, cam, tf, g, term)
+    rc.rc_tf_set(ctx, tf)
+    G = torch.from_numpy(np.stack(gs).astype(np.float32).reshape(len(cams), W["height"], W["width"], 4)).cuda()
+    dtf = torch.empty((W["K"], 4), device="cuda", dtype=torch.float32)
+    p = rc.RenderParams(step_vox=W["step"], term=term, shade=False, skip=False)
+    rc.rc_render_backward_views(ctx, vol, p, cams, G, dtf)
+    torch.cuda.synchronize()
+    got = dtf.cpu().numpy().astype(np.float64)
+    scale = np.abs(total_o).max()
+    assert np.abs(got - total_o).max() / scale < 2e-4
+    assert np.abs(got - total_1).max() / scale < 1e-5
+    # deterministic
+    rc.rc_render_backward_views(ctx, vol, p, cams, G, dtf)
+    torch.cuda.synchronize()
+    assert np.array_equal(dtf.cpu().numpy().astype(np.float64), got)
+
+
 def test_gradient_matches_central_differences(rc, orc, c4):
     """Central differences (h = 1e-3) of <I(tf), G> with the FP64 oracle,
     termination off so that h cannot flip a stop decision, on the 32 entries
