@@ -348,12 +348,18 @@ __device__ __forceinline__ float4 classify2(const TFDev &tf, float u, float w) {
 }
 
 // Eq. 3 for a segment of length ds: alpha' = 1 - (1 - alpha)^(ds/ds_ref).
+// A general ratio (per-ray segments of the importance and profile marches)
+// uses t^r = 2^(r log2 t) on the special-function unit: relative error about
+// r * 2^-21 (below 1e-5 for segments up to 8 reference steps), with the end
+// points exact (alpha 0 -> 0, alpha 1 -> 1).
 __device__ __forceinline__ float correct_alpha(float a, int rmode, float ratio) {
     float t = 1.0f - a;
     if (rmode == 0) return a;
     if (rmode == 1) return 1.0f - sqrtf(t);
     if (rmode == 2) return 1.0f - sqrtf(sqrtf(t));
-    return 1.0f - powf(t, ratio);
+    if (t >= 1.0f) return 0.0f;
+    if (t <= 0.0f) return 1.0f;
+    return 1.0f - exp2f(ratio * __log2f(t));
 }
 
 // Headlight Blinn-Phong with a two-sided diffuse term: light and view along
