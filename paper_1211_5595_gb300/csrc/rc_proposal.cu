@@ -210,8 +210,24 @@ __device__ __forceinline__ void issue_layer(const NetSmem &S, int g, int l, uint
 }
 
 // Bias, ReLU and BF16 rounding of this thread's 64 hidden values, written as
-// row `row` of the next layer's A operand (K = 64).
+// row `row` of the next layer's A operand (K = 64). Pairs of values: FP32x2
+// bias add, one rounding to a BF16 pair, ReLU on the pair (max with +0 after
+// rounding gives the same values as rounding after the ReLU).
+__device__ __forceinline__ uint32_t bias_relu_bf16x2(float lo, float hi, float2 b) {
+    uint64_t x, y, z;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(lo), "f"(hi));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+    float zl, zh;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(zl), "=f"(zh) : "l"(z));
+    uint32_t p, r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p) : "f"(zh), "f"(zl));
+    asm("max.bf16x2 %0, %1, %2;" : "=r"(r) : "r"(p), "r"(0u));
+    return r;
+}
+
 __device__ __forceinline__ void store_hidden(uint8_t *A, uint32_t taddr, const float *bias, int row) {
+    const float2 *b2 = reinterpret_cast<const float2 *>(bias);
 #pragma unroll
     for (int c = 0; c < kHid; c += 16) {
         float v[16];
@@ -221,11 +237,8 @@ __device__ __forceinline__ void store_hidden(uint8_t *A, uint32_t taddr, const f
             uint4 q;
             uint32_t *w = reinterpret_cast<uint32_t *>(&q);
 #pragma unroll
-            for (int h = 0; h < 4; h++) {
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(v[j + 2 * h] + bias[c + j + 2 * h], 0.0f),
-                                                          fmaxf(v[j + 2 * h + 1] + bias[c + j + 2 * h + 1], 0.0f));
-                w[h] = *reinterpret_cast<uint32_t *>(&b2);
-            }
+            for (int h = 0; h < 4; h++)
+                w[h] = bias_relu_bf16x2(v[j + 2 * h], v[j + 2 * h + 1], b2[(c + j) / 2 + h]);
             *reinterpret_cast<uint4 *>(A + tc::core_offset(row, c + j, 128)) = q;
         }
     }
@@ -257,16 +270,18 @@ __device__ __forceinline__ void net_head(uint32_t taddr, const float *bias, floa
     float mx = z[0];
 #pragma unroll
     for (int b = 1; b < kBins; b++) mx = fmaxf(mx, z[b]);
+    // exponentials on the special-function unit (relative error ~2^-21,
+    // far below the network's BF16 rounding)
     float sum = 0.0f;
 #pragma unroll
     for (int b = 0; b < kBins; b++) {
-        pdf[b] = expf(z[b] - mx);
+        pdf[b] = __expf(z[b] - mx);
         sum += pdf[b];
     }
     const float inv = 1.0f / sum;
 #pragma unroll
     for (int b = 0; b < kBins; b++) pdf[b] *= inv;
-    that = 1.0f / (1.0f + expf(-z[kBins]));
+    that = 1.0f / (1.0f + __expf(-z[kBins]));
 }
 
 // Runs the four layers of group g on its A operand (the group's 128 threads
@@ -355,7 +370,6 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads) tc_net_kernel(const T
                 q.y = *reinterpret_cast<uint32_t *>(&hi);
                 *reinterpret_cast<uint2 *>(Ag + tc::core_offset(row, k, 128)) = q;
             }
-            if (t < valid) out_idx = r0 + t;
         } else {
             const int per_view = A.tiles_x * A.tiles_y;
             const int view = (int)(tile / per_view), tl = (int)(tile % per_view);
@@ -375,17 +389,24 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads) tc_net_kernel(const T
             mma_waited_out = true;
             break;
         }
-        if (out_idx >= 0) {
-            if (FEAT) {
-                float *o = A.net_out + out_idx * kOutUsed;
+        if (FEAT) {
+            // stage the tile's 128 x 33 outputs in the A operand (its last
+            // reader, the head layer's MMA, has completed), then store the
+            // contiguous block with coalesced writes
+            float *stage = reinterpret_cast<float *>(Ag);
 #pragma unroll
-                for (int b = 0; b < kBins; b++) o[b] = pdf[b];
-                o[kBins] = that;
-            } else {
-                int b0 = 0, b1 = kBins - 1;
-                if (hit) range_of(A.m, R, pdf, centre, true, b0, b1);
-                A.range[out_idx] = make_uint2((unsigned)b0 | ((unsigned)b1 << 8), __float_as_uint(that));
-            }
+            for (int b = 0; b < kBins; b++) stage[t * kOutUsed + b] = pdf[b];
+            stage[t * kOutUsed + kBins] = that;
+            group_sync(g);
+            const long long r0 = tile * 128;
+            const int valid = (int)min((long long)128, A.n - r0);
+            float *o = A.net_out + r0 * kOutUsed;
+            for (int e = t; e < valid * kOutUsed; e += kGroupThreads) o[e] = stage[e];
+            group_sync(g);                  // before the next tile's features overwrite the stage
+        } else if (out_idx >= 0) {
+            int b0 = 0, b1 = kBins - 1;
+            if (hit) range_of(A.m, R, pdf, centre, true, b0, b1);
+            A.range[out_idx] = make_uint2((unsigned)b0 | ((unsigned)b1 << 8), __float_as_uint(that));
         }
     }
     if (!ok) {
