@@ -63,9 +63,10 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the march from the committed ncu summary, if
-    it was captured on the current kernel sources (else None)."""
+def profiled_counters():
+    """Per-launch counters of the march from the committed ncu summary
+    (DRAM bytes, L2-to-L1 bytes, warp instructions), if it was captured on
+    the current kernel sources (else an empty dict)."""
     path = os.path.join(ROOT, "profiles", "march_shaded_256x256x180.md")
     try:
         kv = {}
@@ -74,10 +75,31 @@ def profiled_traffic():
                 k, v = line[2:].split(":", 1)
                 kv[k.strip()] = (v.split() or [""])[0]
         if kv.get("sources_sha256_16") != kernel_sources_hash():
-            return None
-        return float(kv["dram_bytes_per_launch"])
+            return {}
+        return {k: float(kv[k]) for k in ("dram_bytes_per_launch", "l2_to_l1_bytes_per_launch",
+                                          "warp_instructions_per_launch") if k in kv}
     except Exception:
-        return None
+        return {}
+
+
+def profiled_traffic():
+    return profiled_counters().get("dram_bytes_per_launch")
+
+
+def l2_read_peak(stream):
+    """L2 read bandwidth probe: a 48 MB FP32 buffer (L2-resident after the
+    first pass) summed 20 times, CUDA events; bytes read / time."""
+    import torch
+    buf = torch.ones(12 << 20, device="cuda", dtype=torch.float32)
+    for _ in range(3):
+        buf.sum()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(20):
+        buf.sum()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    return 20 * buf.numel() * 4 / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e9
 
 
 class ClockSampler:
@@ -561,7 +583,24 @@ def main():
 
     launch_avg_s = statistics.mean(launch_ms) / 1e3
     achieved = evald * BYTES_PER_SAMPLE / launch_avg_s / 1e9
-    traffic = profiled_traffic()
+    counters = profiled_counters() if nviews == 36 else {}
+    traffic = counters.get("dram_bytes_per_launch")
+    # where the gathered bytes come from: L2 -> L1 bytes against a measured L2
+    # read peak, and the instruction issue rate against 4 schedulers per SM
+    # x the SM count x the sampled clock (the kernel's real limiter)
+    l2_peak = l2_read_peak(stream)
+    clk = clocks.summary()
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    issue_peak = torch.cuda.get_device_properties(local).multi_processor_count * 4 * sm_mhz * 1e6
+    l2 = issue = None
+    if "l2_to_l1_bytes_per_launch" in counters:
+        a = counters["l2_to_l1_bytes_per_launch"] / launch_avg_s / 1e9
+        l2 = {"achieved_gbs": a, "peak_gbs": l2_peak, "frac": a / l2_peak,
+              "peak_kind": "measured: 48 MB L2-resident buffer read by a reduction"}
+    if "warp_instructions_per_launch" in counters:
+        a = counters["warp_instructions_per_launch"] / launch_avg_s
+        issue = {"achieved_warp_inst_s": a, "peak_warp_inst_s": issue_peak, "frac": a / issue_peak,
+                 "peak_kind": "4 issue slots per SM per clock x SMs x median SM clock under load"}
     line = {
         "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -576,11 +615,13 @@ def main():
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "kernel": "composite_kernel<F32, shaded>, one launch per step for all views",
                      "model": f"{BYTES_PER_SAMPLE} B per evaluated sample (32 distinct FP32 voxels = 8 value+gradient float4) / mean launch time",
-                     "peak_kind": f"{peak_kind} copy bandwidth"},
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "note": "the gather bytes are served by L1 (95% of sectors); see l2 and issue",
+                     "l2": l2, "issue": issue},
         "e2e": e2e,
         "forms": forms,
         "gpu_launches": args.steps * 6,     # per step: re-layout, value+gradient bricks, min/max grid, table, occupancy, march
-        "clocks": clocks.summary(),
+        "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, cores, desc = cpu_oracle_sample(ph, tf, w, cams, args.cpu_budget)
