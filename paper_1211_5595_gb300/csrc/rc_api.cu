@@ -70,6 +70,9 @@ struct rc_volume {
     // min/max grid and occupancy mask per reconstruction filter (index rc_filter)
     uint16_t *d_mn[2] = {nullptr, nullptr}, *d_mx[2] = {nullptr, nullptr};
     uint8_t *d_occ[2] = {nullptr, nullptr};
+    // 4^3 sub-block min/max grid and the fine mask of the trilinear compositing march
+    uint16_t *d_mn4 = nullptr, *d_mx4 = nullptr;
+    unsigned long long *d_fine = nullptr;
     bool uploaded = false;
     uint64_t data_version = 0;
     uint64_t grid_data_version[2] = {~0ull, ~0ull};
@@ -251,6 +254,9 @@ static void volume_free(rc_volume *v) {
         cudaFree(v->d_mx[f]);
         cudaFree(v->d_occ[f]);
     }
+    cudaFree(v->d_mn4);
+    cudaFree(v->d_mx4);
+    cudaFree(v->d_fine);
 }
 
 rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, float sy, float sz, uint16_t vmax,
@@ -282,6 +288,7 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
     size_t esz = storage == RC_STORE_F32 ? 4 : 2;
     size_t nvox = (size_t)nx * ny * nz;
     const size_t vg_bytes = storage == RC_STORE_F32 ? (size_t)v->nbricks * kGradVox * sizeof(float4) : 0;
+    const size_t n4 = (size_t)((nx - 1 + 3) / 4) * ((ny - 1 + 3) / 4) * ((nz - 1 + 3) / 4);
     if (dev_alloc(&v->d_data, (size_t)padded * esz) != cudaSuccess ||
         (vg_bytes && dev_alloc(&v->d_vg, vg_bytes) != cudaSuccess) ||
         dev_alloc(&v->d_stage, nvox * sizeof(uint16_t)) != cudaSuccess ||
@@ -290,7 +297,10 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
         dev_alloc(&v->d_occ[0], v->nbricks) != cudaSuccess ||
         dev_alloc(&v->d_mn[1], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
         dev_alloc(&v->d_mx[1], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
-        dev_alloc(&v->d_occ[1], v->nbricks) != cudaSuccess) {
+        dev_alloc(&v->d_occ[1], v->nbricks) != cudaSuccess ||
+        dev_alloc(&v->d_mn4, n4 * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_mx4, n4 * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_fine, v->nbricks * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         volume_free(v);
         delete v;
@@ -335,6 +345,7 @@ rc_status rc_volume_upload(rc_volume *v, const uint16_t *src, size_t n_voxels, i
     if (v->d_vg) RC_CUDA(ctx, launch_gradvol(v->d_stage, d, v->d_vg, ctx->stream));
     RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, RC_FILTER_TRILINEAR, v->d_mn[0], v->d_mx[0],
                                ctx->stream));
+    RC_CUDA(ctx, launch_minmax4(v->d_stage, v->n, v->vmax, v->d_mn4, v->d_mx4, ctx->stream));
     v->uploaded = true;
     v->data_version++;
     v->grid_data_version[RC_FILTER_TRILINEAR] = v->data_version;   // the B-spline grid is built on first use
@@ -686,6 +697,9 @@ static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v, int f) {
     TFDev tf = tf_dev(ctx, v);
     RC_CUDA(ctx, launch_occupancy(v->d_mn[f], v->d_mx[f], v->nbricks, v->vmax, v->storage == RC_STORE_F16, tf,
                                   v->d_occ[f], ctx->stream));
+    if (f == RC_FILTER_TRILINEAR)
+        RC_CUDA(ctx, launch_finemask(v->d_mn4, v->d_mx4, v->n, v->cb, v->vmax, v->storage == RC_STORE_F16, tf,
+                                     v->d_fine, ctx->stream));
     v->occ_tf_version[f] = ctx->tf_version;
     v->occ_data_version[f] = v->data_version;
     return RC_OK;
@@ -728,6 +742,7 @@ static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render
     a.p.rmode = a.p.ratio == 1.0f ? 0 : a.p.ratio == 0.5f ? 1 : a.p.ratio == 0.25f ? 2 : 3;
     a.p.filter = p->filter;
     a.occ = v->d_occ[p->filter];
+    a.fine = p->filter == RC_FILTER_TRILINEAR ? v->d_fine : nullptr;
     a.out = reinterpret_cast<float4 *>(out);
     a.stats = nullptr;
     a.cams = nullptr;

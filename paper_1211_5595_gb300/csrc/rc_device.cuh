@@ -453,6 +453,54 @@ __device__ __forceinline__ void composite_add(const float4 &e, float &C0, float 
     T = T * (1.0f - e.w);
 }
 
+// Jump over an empty axis-aligned block of 2^s cells per axis containing
+// cell c (s = 4: the cell-brick; 3 and 2: its octants and 4^3 sub-blocks).
+// Returns the index of the first sample that may lie outside the block: the
+// sample m just before the computed exit distance is verified to be in the
+// same block (cell bases agree above bit s on every axis); since each
+// coordinate of the computed positions is monotone in k, every sample between
+// k and m is then inside too. Falls back to k + 1 when the check fails, so
+// the exit estimate needs no exact rounding.
+__device__ __forceinline__ int jump_block(const Ray &R, const VolDev &v, const Cell &c, int k, int s) {
+    const float INF = __int_as_float(0x7f800000);
+    float texit = INF;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int lo = (c.i[a] >> s) << s, hi = lo + (1 << s);
+        if (R.d[a] > 0.0f && hi <= v.n[a] - 2)
+            texit = fminf(texit, __fdiv_rn((float)hi - R.o[a], R.d[a]));
+        else if (R.d[a] < 0.0f && lo > 0)
+            texit = fminf(texit, __fdiv_rn((float)lo - R.o[a], R.d[a]));
+    }
+    if (texit == INF) return R.nsamp;
+    float fm = floorf(__fdiv_rn(texit - R.tn, R.ds));
+    int m = fm >= (float)R.nsamp ? R.nsamp - 1 : (int)fm;
+    if (m <= k) return k + 1;
+#pragma unroll 1
+    for (int tries = 0; tries < 2 && m > k; tries++, m--) {
+        float p[3];
+        position_at(R, sample_t(R, m), p);
+        Cell cm;
+        cell_of(v, p, cm);
+        if (((cm.i[0] ^ c.i[0]) >> s) == 0 && ((cm.i[1] ^ c.i[1]) >> s) == 0 && ((cm.i[2] ^ c.i[2]) >> s) == 0)
+            return m + 1;
+    }
+    return k + 1;
+}
+
+// The empty block around cell c by the fine mask of its cell-brick (one bit
+// per 4^3 sub-block, bit sz*16 + sy*4 + sx): 4 when the whole brick is empty,
+// 3 when its octant is, 2 when the sub-block is, -1 when the sample may have
+// non-zero opacity.
+__device__ __forceinline__ int empty_block(unsigned long long m, const Cell &c) {
+    if (m == 0ull) return 4;
+    const int sx = (c.i[0] >> 2) & 3, sy = (c.i[1] >> 2) & 3, sz = (c.i[2] >> 2) & 3;
+    const int oct = (sz & 2) * 16 + (sy & 2) * 4 + (sx & 2);          // bit of the octant's first sub-block
+    if (((m >> oct) & 0x330033ull) == 0ull) return 3;                   // sub-blocks {0,1} x {0,1} x {0,1} of it
+    if (((m >> (sz * 16 + sy * 4 + sx)) & 1ull) == 0ull) return 2;
+    return -1;
+}
+
 // Jump over a brick the occupancy mask marks empty. Returns the index of the
 // first sample that may lie outside brick(c): the sample m just before the
 // computed exit distance is verified to be in the same brick; since each

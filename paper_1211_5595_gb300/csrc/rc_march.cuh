@@ -60,10 +60,16 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
         position_at(R, sample_t(R, k), p);
         Cell c;
         cell_of(a.vol, p, c);
-        if (a.p.skip && !__ldg(a.occ + brick_of(a.vol, c))) {
-            k = jump_empty(R, a.vol, c, k);
-            active = k < nsamp;
-            continue;
+        if (a.p.skip) {
+            // the largest empty block around the sample: with the fine mask
+            // the cell-brick, its octant or its 4^3 sub-block; else the brick
+            const int b = brick_of(a.vol, c);
+            const int s = a.fine ? empty_block(__ldg(a.fine + b), c) : (__ldg(a.occ + b) ? -1 : 4);
+            if (s >= 0) {
+                k = jump_block(R, a.vol, c, k, s);
+                active = k < nsamp;
+                continue;
+            }
         }
         float4 e = eval_sample_x<ST, F>(a.vol, a.p, s_tf, a.tf, R.dir, c, a.p.rmode, a.p.ratio);
         composite_add(e, C0, C1, C2, T);

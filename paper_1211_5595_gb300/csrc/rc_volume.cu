@@ -128,6 +128,79 @@ cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3]
     return cudaGetLastError();
 }
 
+// One thread per 4^3 sub-block: min and max of the (clamped) codes over its
+// footprint voxels 4j .. min(4j + 4, N - 1) per axis; ceil((N-1)/4) per axis.
+__global__ void minmax4_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int c0,
+                               int c1, int c2, uint16_t *mn, uint16_t *mx) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c0 * c1 * c2) return;
+    const int jx = j % c0, jy = (j / c0) % c1, jz = j / (c0 * c1);
+    int lo = 65535, hi = 0;
+    for (int z = 4 * jz; z <= min(4 * jz + 4, nz - 1); z++)
+        for (int y = 4 * jy; y <= min(4 * jy + 4, ny - 1); y++)
+            for (int x = 4 * jx; x <= min(4 * jx + 4, nx - 1); x++) {
+                const int v = min((int)stage[((size_t)z * ny + y) * nx + x], vmax);
+                lo = min(lo, v);
+                hi = max(hi, v);
+            }
+    mn[j] = (uint16_t)lo;
+    mx[j] = (uint16_t)hi;
+}
+
+cudaError_t launch_minmax4(const uint16_t *stage, const int n[3], int vmax, uint16_t *mn, uint16_t *mx,
+                           cudaStream_t s) {
+    const int c0 = (n[0] - 1 + 3) / 4, c1 = (n[1] - 1 + 3) / 4, c2 = (n[2] - 1 + 3) / 4;
+    const int total = c0 * c1 * c2;
+    minmax4_kernel<<<(total + 127) / 128, 128, 0, s>>>(stage, n[0], n[1], n[2], vmax, c0, c1, c2, mn, mx);
+    return cudaGetLastError();
+}
+
+// Whether any table entry a value in [vmn, vmx] can touch has non-zero
+// opacity, with the march's coordinate u(v) = fl(v * ucoef).
+__device__ __forceinline__ bool range_visible(float vmn, float vmx, int vmax, int f16_values, const TFDev &tf) {
+    const int K = tf.K;
+    if (f16_values) {
+        vmn = __half2float(__float2half_rn(__fdiv_rn(vmn, (float)vmax)));
+        vmx = __half2float(__float2half_rn(__fdiv_rn(vmx, (float)vmax)));
+    }
+    const int lo = min((int)floorf(__fmul_rn(vmn, tf.ucoef)), K - 1);
+    const int hi = min((int)floorf(__fmul_rn(vmx, tf.ucoef)) + 1, K - 1);
+    for (int i = lo; i <= hi; i++) {
+        const float a = tf.M >= 2 ? tf.amax[i] : (tf.fp16 ? half4_to_float4(tf.f16[i]).w : tf.f32[i].w);
+        if (a != 0.0f) return true;
+    }
+    return false;
+}
+
+// One thread per cell-brick: bit sz*16 + sy*4 + sx set when sub-block
+// (4*bx + sx, 4*by + sy, 4*bz + sz) exists and may hold non-zero opacity.
+__global__ void finemask_kernel(const uint16_t *mn4, const uint16_t *mx4, int c0, int c1, int c2, int cb0, int cb1,
+                                int nbricks, int vmax, int f16_values, TFDev tf, unsigned long long *fine) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbricks) return;
+    const int bx = b % cb0, by = (b / cb0) % cb1, bz = b / (cb0 * cb1);
+    unsigned long long m = 0ull;
+    for (int sz = 0; sz < 4; sz++)
+        for (int sy = 0; sy < 4; sy++)
+            for (int sx = 0; sx < 4; sx++) {
+                const int jx = 4 * bx + sx, jy = 4 * by + sy, jz = 4 * bz + sz;
+                if (jx >= c0 || jy >= c1 || jz >= c2) continue;
+                const int j = (jz * c1 + jy) * c0 + jx;
+                if (range_visible((float)mn4[j], (float)mx4[j], vmax, f16_values, tf))
+                    m |= 1ull << (sz * 16 + sy * 4 + sx);
+            }
+    fine[b] = m;
+}
+
+cudaError_t launch_finemask(const uint16_t *mn4, const uint16_t *mx4, const int n[3], const int cb[3], int vmax,
+                            int f16_values, TFDev tf, unsigned long long *fine, cudaStream_t s) {
+    const int c0 = (n[0] - 1 + 3) / 4, c1 = (n[1] - 1 + 3) / 4, c2 = (n[2] - 1 + 3) / 4;
+    const int nb = cb[0] * cb[1] * cb[2];
+    finemask_kernel<<<(nb + 127) / 128, 128, 0, s>>>(mn4, mx4, c0, c1, c2, cb[0], cb[1], nb, vmax, f16_values, tf,
+                                                     fine);
+    return cudaGetLastError();
+}
+
 // A cell-brick is occupied unless every entry lo..hi its samples can touch has
 // zero opacity, with the march's own coordinate u(v) = fl(v * ucoef): raw codes
 // v = min, max; FP16 storage v = fp16(min / vmax), fp16(max / vmax). With a
