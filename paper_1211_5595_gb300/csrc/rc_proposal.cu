@@ -54,7 +54,10 @@ __global__ void __launch_bounds__(128) profiles_kernel(const MarchArgs a, float 
             position_at(R, __fmaf_rn((float)k + 0.5f, delta, R.tn), p);
             Cell c;
             cell_of(a.vol, p, c);
-            if (a.p.skip && !__ldg(a.occ + brick_of(a.vol, c))) continue;   // opacity exactly 0
+            if (a.p.skip) {                                                   // opacity exactly 0
+            const int b = brick_of(a.vol, c);
+            if (a.fine ? empty_block(__ldg(a.fine + b), c) >= 0 : !__ldg(a.occ + b)) continue;
+        }
             float4 e = eval_sample<ST, false>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, 3, ratio);
             acc = __fmaf_rn(T, e.w, acc);
             T = T * (1.0f - e.w);
@@ -434,9 +437,13 @@ __device__ __forceinline__ void plain_ray(const MarchArgs &a, const float4 *s_tf
         position_at(R, sample_t(R, k), p);
         Cell c;
         cell_of(a.vol, p, c);
-        if (a.p.skip && !__ldg(a.occ + brick_of(a.vol, c))) {
-            k = jump_empty(R, a.vol, c, k);
-            continue;
+        if (a.p.skip) {
+            const int b = brick_of(a.vol, c);
+            const int s = a.fine ? empty_block(__ldg(a.fine + b), c) : (__ldg(a.occ + b) ? -1 : 4);
+            if (s >= 0) {
+                k = jump_block(R, a.vol, c, k, s);
+                continue;
+            }
         }
         float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, a.p.rmode, a.p.ratio);
         composite_add(e, C0, C1, C2, T);
@@ -512,7 +519,10 @@ __device__ __forceinline__ void march_range(const ImportanceArgs &A, const float
         position_at(R, __fmaf_rn((float)j + 0.5f, seg, ta), p);
         Cell c;
         cell_of(a.vol, p, c);
-        if (a.p.skip && !__ldg(a.occ + brick_of(a.vol, c))) continue;   // opacity exactly 0
+        if (a.p.skip) {                                                   // opacity exactly 0
+            const int b = brick_of(a.vol, c);
+            if (a.fine ? empty_block(__ldg(a.fine + b), c) >= 0 : !__ldg(a.occ + b)) continue;
+        }
         float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, 3, ratio);
         composite_add(e, C0, C1, C2, T);
         evald++;
