@@ -71,8 +71,8 @@ struct rc_volume {
     uint16_t *d_mn[2] = {nullptr, nullptr}, *d_mx[2] = {nullptr, nullptr};
     uint8_t *d_occ[2] = {nullptr, nullptr};
     // 4^3 sub-block min/max grid and the fine mask of the trilinear compositing march
-    uint16_t *d_mn4 = nullptr, *d_mx4 = nullptr;
-    unsigned long long *d_fine = nullptr;
+    uint16_t *d_mn4[2] = {nullptr, nullptr}, *d_mx4[2] = {nullptr, nullptr};
+    unsigned long long *d_fine[2] = {nullptr, nullptr};
     bool uploaded = false;
     uint64_t data_version = 0;
     uint64_t grid_data_version[2] = {~0ull, ~0ull};
@@ -254,9 +254,11 @@ static void volume_free(rc_volume *v) {
         cudaFree(v->d_mx[f]);
         cudaFree(v->d_occ[f]);
     }
-    cudaFree(v->d_mn4);
-    cudaFree(v->d_mx4);
-    cudaFree(v->d_fine);
+    for (int f = 0; f < 2; f++) {
+        cudaFree(v->d_mn4[f]);
+        cudaFree(v->d_mx4[f]);
+        cudaFree(v->d_fine[f]);
+    }
 }
 
 rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, float sy, float sz, uint16_t vmax,
@@ -298,9 +300,12 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
         dev_alloc(&v->d_mn[1], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
         dev_alloc(&v->d_mx[1], v->nbricks * sizeof(uint16_t)) != cudaSuccess ||
         dev_alloc(&v->d_occ[1], v->nbricks) != cudaSuccess ||
-        dev_alloc(&v->d_mn4, n4 * sizeof(uint16_t)) != cudaSuccess ||
-        dev_alloc(&v->d_mx4, n4 * sizeof(uint16_t)) != cudaSuccess ||
-        dev_alloc(&v->d_fine, v->nbricks * sizeof(unsigned long long)) != cudaSuccess) {
+        dev_alloc(&v->d_mn4[0], n4 * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_mx4[0], n4 * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_fine[0], v->nbricks * sizeof(unsigned long long)) != cudaSuccess ||
+        dev_alloc(&v->d_mn4[1], n4 * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_mx4[1], n4 * sizeof(uint16_t)) != cudaSuccess ||
+        dev_alloc(&v->d_fine[1], v->nbricks * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         volume_free(v);
         delete v;
@@ -345,7 +350,8 @@ rc_status rc_volume_upload(rc_volume *v, const uint16_t *src, size_t n_voxels, i
     if (v->d_vg) RC_CUDA(ctx, launch_gradvol(v->d_stage, d, v->d_vg, ctx->stream));
     RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, RC_FILTER_TRILINEAR, v->d_mn[0], v->d_mx[0],
                                ctx->stream));
-    RC_CUDA(ctx, launch_minmax4(v->d_stage, v->n, v->vmax, v->d_mn4, v->d_mx4, ctx->stream));
+    RC_CUDA(ctx, launch_minmax4(v->d_stage, v->n, v->vmax, RC_FILTER_TRILINEAR, v->d_mn4[0], v->d_mx4[0],
+                                ctx->stream));
     v->uploaded = true;
     v->data_version++;
     v->grid_data_version[RC_FILTER_TRILINEAR] = v->data_version;   // the B-spline grid is built on first use
@@ -684,6 +690,7 @@ static TFDev tf_dev(const rc_context *ctx, const rc_volume *v) {
 static rc_status ensure_grid(rc_context *ctx, rc_volume *v, int f) {
     if (v->grid_data_version[f] == v->data_version) return RC_OK;
     RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, f, v->d_mn[f], v->d_mx[f], ctx->stream));
+    RC_CUDA(ctx, launch_minmax4(v->d_stage, v->n, v->vmax, f, v->d_mn4[f], v->d_mx4[f], ctx->stream));
     v->grid_data_version[f] = v->data_version;
     return RC_OK;
 }
@@ -697,9 +704,8 @@ static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v, int f) {
     TFDev tf = tf_dev(ctx, v);
     RC_CUDA(ctx, launch_occupancy(v->d_mn[f], v->d_mx[f], v->nbricks, v->vmax, v->storage == RC_STORE_F16, tf,
                                   v->d_occ[f], ctx->stream));
-    if (f == RC_FILTER_TRILINEAR)
-        RC_CUDA(ctx, launch_finemask(v->d_mn4, v->d_mx4, v->n, v->cb, v->vmax, v->storage == RC_STORE_F16, tf,
-                                     v->d_fine, ctx->stream));
+    RC_CUDA(ctx, launch_finemask(v->d_mn4[f], v->d_mx4[f], v->n, v->cb, v->vmax, v->storage == RC_STORE_F16, tf,
+                                 v->d_fine[f], ctx->stream));
     v->occ_tf_version[f] = ctx->tf_version;
     v->occ_data_version[f] = v->data_version;
     return RC_OK;
@@ -742,7 +748,7 @@ static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render
     a.p.rmode = a.p.ratio == 1.0f ? 0 : a.p.ratio == 0.5f ? 1 : a.p.ratio == 0.25f ? 2 : 3;
     a.p.filter = p->filter;
     a.occ = v->d_occ[p->filter];
-    a.fine = p->filter == RC_FILTER_TRILINEAR ? v->d_fine : nullptr;
+    a.fine = v->d_fine[p->filter];
     a.out = reinterpret_cast<float4 *>(out);
     a.stats = nullptr;
     a.cams = nullptr;

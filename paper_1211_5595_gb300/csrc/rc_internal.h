@@ -78,7 +78,7 @@ struct MarchArgs {
     TFDev tf;
     MarchParams p;
     const uint8_t *occ;            // cell-brick occupancy (1 = may be non-empty)
-    const unsigned long long *fine;   // trilinear compositing: per cell-brick, one bit per 4^3 sub-block (or null)
+    const unsigned long long *fine;   // compositing: per cell-brick, one bit per 4^3 sub-block (or null)
     float4 *out;                   // H x W RGBA (view-major for several views)
     unsigned long long *stats;     // dense, evaluated, hit, total (or null)
     const CamRec *cams;            // one record per view (blockIdx.z), or null: cam
@@ -167,9 +167,10 @@ cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3]
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);
 cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax,
                              int f16_values, TFDev tf, uint8_t *occ, cudaStream_t s);
-// 4^3 sub-block min/max grid (cells 4j..4j+3, footprint voxels 4j..min(4j+4, N-1))
-// and the fine mask built from it: per cell-brick one bit per sub-block.
-cudaError_t launch_minmax4(const uint16_t *stage, const int n[3], int vmax, uint16_t *mn, uint16_t *mx,
+// 4^3 sub-block min/max grid of a filter (cells 4j..4j+3; footprint voxels
+// 4j..4j+4, or 4j-1..4j+5 for the B-spline, clamped) and the fine mask built
+// from it: per cell-brick one bit per sub-block.
+cudaError_t launch_minmax4(const uint16_t *stage, const int n[3], int vmax, int filter, uint16_t *mn, uint16_t *mx,
                            cudaStream_t s);
 cudaError_t launch_finemask(const uint16_t *mn4, const uint16_t *mx4, const int n[3], const int cb[3], int vmax,
                             int f16_values, TFDev tf, unsigned long long *fine, cudaStream_t s);

@@ -129,16 +129,18 @@ cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3]
 }
 
 // One thread per 4^3 sub-block: min and max of the (clamped) codes over its
-// footprint voxels 4j .. min(4j + 4, N - 1) per axis; ceil((N-1)/4) per axis.
+// footprint voxels max(4j - before, 0) .. min(4j + after, N - 1) per axis,
+// (0, 4) for trilinear samples and (1, 5) for cubic B-spline samples;
+// ceil((N-1)/4) sub-blocks per axis.
 __global__ void minmax4_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int c0,
-                               int c1, int c2, uint16_t *mn, uint16_t *mx) {
+                               int c1, int c2, int before, int after, uint16_t *mn, uint16_t *mx) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= c0 * c1 * c2) return;
     const int jx = j % c0, jy = (j / c0) % c1, jz = j / (c0 * c1);
     int lo = 65535, hi = 0;
-    for (int z = 4 * jz; z <= min(4 * jz + 4, nz - 1); z++)
-        for (int y = 4 * jy; y <= min(4 * jy + 4, ny - 1); y++)
-            for (int x = 4 * jx; x <= min(4 * jx + 4, nx - 1); x++) {
+    for (int z = max(4 * jz - before, 0); z <= min(4 * jz + after, nz - 1); z++)
+        for (int y = max(4 * jy - before, 0); y <= min(4 * jy + after, ny - 1); y++)
+            for (int x = max(4 * jx - before, 0); x <= min(4 * jx + after, nx - 1); x++) {
                 const int v = min((int)stage[((size_t)z * ny + y) * nx + x], vmax);
                 lo = min(lo, v);
                 hi = max(hi, v);
@@ -147,11 +149,13 @@ __global__ void minmax4_kernel(const uint16_t *__restrict__ stage, int nx, int n
     mx[j] = (uint16_t)hi;
 }
 
-cudaError_t launch_minmax4(const uint16_t *stage, const int n[3], int vmax, uint16_t *mn, uint16_t *mx,
+cudaError_t launch_minmax4(const uint16_t *stage, const int n[3], int vmax, int filter, uint16_t *mn, uint16_t *mx,
                            cudaStream_t s) {
     const int c0 = (n[0] - 1 + 3) / 4, c1 = (n[1] - 1 + 3) / 4, c2 = (n[2] - 1 + 3) / 4;
     const int total = c0 * c1 * c2;
-    minmax4_kernel<<<(total + 127) / 128, 128, 0, s>>>(stage, n[0], n[1], n[2], vmax, c0, c1, c2, mn, mx);
+    const int before = filter == RC_FILTER_BSPLINE ? 1 : 0, after = filter == RC_FILTER_BSPLINE ? 5 : 4;
+    minmax4_kernel<<<(total + 127) / 128, 128, 0, s>>>(stage, n[0], n[1], n[2], vmax, c0, c1, c2, before, after, mn,
+                                                       mx);
     return cudaGetLastError();
 }
 

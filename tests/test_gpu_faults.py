@@ -37,11 +37,11 @@ def test_allocation_failures_are_clean(rc, monkeypatch):
     ctx = rc.rc_context_create(0)
     try:
         rc.rc_tf_set(ctx, tf)
-        # each of the twelve device allocations of an FP32 rc_volume_create
-        # fails in turn (apron bricks, value+gradient bricks, staging copy, per
-        # filter the min, max and mask arrays, the 4^3 min/max grid and the
+        # each of the fifteen device allocations of an FP32 rc_volume_create
+        # fails in turn (apron bricks, value+gradient bricks, staging copy, and
+        # per filter the min, max and mask arrays, the 4^3 min/max grid and the
         # fine mask)
-        for n in range(1, 13):
+        for n in range(1, 16):
             monkeypatch.setenv("RC_FAULT_ALLOC", str(n))
             with pytest.raises(rc.RCError) as ei:
                 rc.rc_volume_create(ctx, ph.dims, ph.spacing, 4095, rc.RC_STORE_F32)
