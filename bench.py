@@ -620,7 +620,9 @@ def main():
                      "l2": l2, "issue": issue},
         "e2e": e2e,
         "forms": forms,
-        "gpu_launches": args.steps * 6,     # per step: re-layout, value+gradient bricks, min/max grid, table, occupancy, march
+        # per step: re-layout, value+gradient bricks, 16^3 and 4^3 min/max grids,
+        # table, brick and sub-block occupancy masks, march
+        "gpu_launches": args.steps * 8,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -81,8 +81,9 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
     float4 g = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (hit) g = A.dimg[((size_t)blockIdx.z * cam.H + y) * cam.W + x];
     const bool has_g = hit && (g.x != 0.0f || g.y != 0.0f || g.z != 0.0f || g.w != 0.0f);
-    // pass 1: the forward march, with exact empty-space skipping (identical
-    // result), for C_final, T_final and the sample count n up to termination
+    // pass 1: the forward march, with exact empty-space skipping over empty
+    // bricks, octants and 4^3 sub-blocks (identical result), for C_final,
+    // T_final and the sample count n up to termination
     float Cf0 = 0.0f, Cf1 = 0.0f, Cf2 = 0.0f, Tf = 1.0f;
     int n = 0;
     if (has_g) {
@@ -92,8 +93,10 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
             position_at(R, sample_t(R, k), p);
             Cell c;
             cell_of(a.vol, p, c);
-            if (!__ldg(a.occ + brick_of(a.vol, c))) {
-                k = jump_empty(R, a.vol, c, k);
+            const int b = brick_of(a.vol, c);
+            const int s = a.fine ? empty_block(__ldg(a.fine + b), c) : (__ldg(a.occ + b) ? -1 : 4);
+            if (s >= 0) {
+                k = jump_block(R, a.vol, c, k, s);
                 continue;
             }
             float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, K, a.tf.ucoef, R.dir, c, a.p.rmode, a.p.ratio);

@@ -176,32 +176,35 @@ __device__ __forceinline__ bool range_visible(float vmn, float vmx, int vmax, in
     return false;
 }
 
-// One thread per cell-brick: bit sz*16 + sy*4 + sx set when sub-block
-// (4*bx + sx, 4*by + sy, 4*bz + sz) exists and may hold non-zero opacity.
-__global__ void finemask_kernel(const uint16_t *mn4, const uint16_t *mx4, int c0, int c1, int c2, int cb0, int cb1,
-                                int nbricks, int vmax, int f16_values, TFDev tf, unsigned long long *fine) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbricks) return;
-    const int bx = b % cb0, by = (b / cb0) % cb1, bz = b / (cb0 * cb1);
-    unsigned long long m = 0ull;
-    for (int sz = 0; sz < 4; sz++)
-        for (int sy = 0; sy < 4; sy++)
-            for (int sx = 0; sx < 4; sx++) {
-                const int jx = 4 * bx + sx, jy = 4 * by + sy, jz = 4 * bz + sz;
-                if (jx >= c0 || jy >= c1 || jz >= c2) continue;
-                const int j = (jz * c1 + jy) * c0 + jx;
-                if (range_visible((float)mn4[j], (float)mx4[j], vmax, f16_values, tf))
-                    m |= 1ull << (sz * 16 + sy * 4 + sx);
-            }
-    fine[b] = m;
+// One thread per sub-block, 64 per cell-brick: bit t = sz*16 + sy*4 + sx of
+// the brick's mask is set when sub-block (4*bx + sx, 4*by + sy, 4*bz + sz)
+// exists and may hold non-zero opacity; each warp's ballot is one 32-bit half.
+__global__ void __launch_bounds__(128) finemask_kernel(const uint16_t *mn4, const uint16_t *mx4, int c0, int c1,
+                                                       int c2, int cb0, int cb1, int nbricks, int vmax,
+                                                       int f16_values, TFDev tf, uint32_t *fine) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = (int)(e >> 6), t = (int)(e & 63);
+    bool vis = false;
+    if (b < nbricks) {
+        const int bx = b % cb0, by = (b / cb0) % cb1, bz = b / (cb0 * cb1);
+        const int jx = 4 * bx + (t & 3), jy = 4 * by + ((t >> 2) & 3), jz = 4 * bz + (t >> 4);
+        if (jx < c0 && jy < c1 && jz < c2) {
+            const int j = (jz * c1 + jy) * c0 + jx;
+            vis = range_visible((float)mn4[j], (float)mx4[j], vmax, f16_values, tf);
+        }
+    }
+    const unsigned bits = __ballot_sync(0xffffffffu, vis);
+    if ((threadIdx.x & 31) == 0 && b < nbricks) fine[2 * b + (t >> 5)] = bits;
 }
 
 cudaError_t launch_finemask(const uint16_t *mn4, const uint16_t *mx4, const int n[3], const int cb[3], int vmax,
                             int f16_values, TFDev tf, unsigned long long *fine, cudaStream_t s) {
     const int c0 = (n[0] - 1 + 3) / 4, c1 = (n[1] - 1 + 3) / 4, c2 = (n[2] - 1 + 3) / 4;
     const int nb = cb[0] * cb[1] * cb[2];
-    finemask_kernel<<<(nb + 127) / 128, 128, 0, s>>>(mn4, mx4, c0, c1, c2, cb[0], cb[1], nb, vmax, f16_values, tf,
-                                                     fine);
+    const long long threads = (long long)nb * 64;
+    finemask_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(mn4, mx4, c0, c1, c2, cb[0], cb[1], nb, vmax,
+                                                                      f16_values, tf,
+                                                                      reinterpret_cast<uint32_t *>(fine));
     return cudaGetLastError();
 }
 
