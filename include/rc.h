@@ -135,6 +135,14 @@ rc_status rc_context_set_stream(rc_context *ctx, void *cuda_stream);
  * in which case that launch's outputs are invalid. Calls that return
  * statistics make the same check. */
 rc_status rc_context_sync(rc_context *ctx);
+
+/* Measurement aid for the rooflines of the gather kernels (the paper has no
+ * counterpart): one launch on the context's stream reads the device buffer
+ * buf (bytes, a multiple of 16, 16-byte aligned) reps times with 16-byte
+ * loads that bypass L1, so a buffer smaller than L2 (129 MB on GB300)
+ * measures the L2 read rate. Time it with events on the stream; it writes
+ * nothing the caller can see. */
+rc_status rc_probe_read_bandwidth(rc_context *ctx, const void *buf, size_t bytes, int reps);
 /* Synchronises the context's stream and frees everything the context owns.
  * Volumes must be destroyed first (RC_ERR_STATE otherwise). */
 rc_status rc_context_destroy(rc_context *ctx);

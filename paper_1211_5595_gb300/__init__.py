@@ -60,6 +60,7 @@ SIGNATURES = {
     "rc_context_create": (_I, [_I, _P, C.POINTER(_P)]),
     "rc_context_set_stream": (_I, [_P, _P]),
     "rc_context_sync": (_I, [_P]),
+    "rc_probe_read_bandwidth": (_I, [_P, _P, C.c_size_t, _I]),
     "rc_context_destroy": (_I, [_P]),
     "rc_volume_create": (_I, [_P, _I, _I, _I, C.c_float, C.c_float, C.c_float, C.c_uint16, _I,
                               C.POINTER(_P)]),
@@ -160,6 +161,12 @@ def rc_context_create(device: int = 0, stream=None):
 
 def rc_context_sync(ctx):
     _check(lib().rc_context_sync(ctx), ctx, "rc_context_sync")
+
+
+def rc_probe_read_bandwidth(ctx, buf, reps):
+    """One launch reading the CUDA tensor buf reps times through L2 (L1 bypassed)."""
+    _check(lib().rc_probe_read_bandwidth(ctx, _ptr(buf), buf.numel() * buf.element_size(), int(reps)), ctx,
+           "rc_probe_read_bandwidth")
 
 
 def rc_context_set_stream(ctx, stream):

@@ -1300,6 +1300,15 @@ rc_status rc_render_proposal_views(rc_context *ctx, const rc_volume *vol, const 
                           "rc_render_proposal_views");
 }
 
+rc_status rc_probe_read_bandwidth(rc_context *ctx, const void *buf, size_t bytes, int reps) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_probe_read_bandwidth: ctx is NULL");
+    if (!buf || bytes < 16 || bytes % 16 != 0 || (reinterpret_cast<uintptr_t>(buf) & 15) != 0 || reps < 1)
+        return fail(ctx, RC_ERR_INVALID_ARG, "rc_probe_read_bandwidth: 16-byte aligned buffer, size a multiple of 16, reps >= 1");
+    DeviceScope ds(ctx->device);
+    RC_CUDA(ctx, launch_read_probe(buf, bytes, reps, reinterpret_cast<float *>(ctx->d_stats + 4), ctx->stream));
+    return RC_OK;
+}
+
 rc_status rc_context_sync(rc_context *ctx) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_context_sync: ctx is NULL");
     DeviceScope ds(ctx->device);

@@ -175,6 +175,7 @@ cudaError_t launch_minmax4(const uint16_t *stage, const int n[3], int vmax, int 
 cudaError_t launch_finemask(const uint16_t *mn4, const uint16_t *mx4, const int n[3], const int cb[3], int vmax,
                             int f16_values, TFDev tf, unsigned long long *fine, cudaStream_t s);
 cudaError_t launch_march(const MarchArgs &a, int nviews, cudaStream_t s);
+cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, float *sink, cudaStream_t s);
 cudaError_t launch_march_cubic(const MarchArgs &a, int nviews, cudaStream_t s);   // filter = B-spline
 cudaError_t launch_march_tf2(const MarchArgs &a, int nviews, cudaStream_t s);     // trilinear, 2-D table
 cudaError_t launch_adjoint(const AdjointArgs &a, int nviews, float *dL_dtf, cudaStream_t s);

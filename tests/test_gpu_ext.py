@@ -260,3 +260,39 @@ def test_unsupported_forms(rc, small):
     rc.rc_render(r.ctx, r.vol, dict(), out)
     torch.cuda.synchronize()
     assert out[..., 3].max() > 0.1
+
+
+def gapped_tf(K, seed):
+    """Opacity in narrow bands separated by transparent gaps, so that many
+    4^3 sub-blocks, octants and bricks are empty next to occupied ones."""
+    tab = synth.noise_tf(K, seed, alpha_max=0.2)
+    u = np.random.default_rng(seed).random(K)
+    tab[u < 0.7, 3] = 0.0          # 70% of the entries transparent
+    tab[: K // 10, 3] = 0.0         # background transparent
+    return tab
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_hierarchical_skip_exact_on_adversarial_data(rc, storage):
+    """Skipping over empty bricks, octants and 4^3 sub-blocks is exact: with
+    a noise volume (values change at every voxel) and a table of narrow
+    opaque bands, every form renders the same image with skipping on and
+    off, and skips part of the samples."""
+    rng = np.random.default_rng(7 + storage)
+    dims = (70, 61, 45)
+    vol = rng.integers(0, 4096, size=dims[::-1]).astype(np.uint16)
+    vol[:, :, :30] //= 16                    # a low-valued (transparent) half
+    r = GPURenderer(rc, vol, (1.0, 1.2, 0.9), storage=storage)
+    try:
+        cam = synth.orbit_camera(dims, (1.0, 1.2, 0.9), 33.0, width=64, height=56)
+        for K, seed in ((256, 3), (1024, 4)):
+            r.set_tf(gapped_tf(K, seed), fp16=storage == 1)
+            for shade in (False, True):
+                for filt in (0, 1):
+                    P = dict(step_vox=0.37, term=0.995, shade=shade, filter=filt)
+                    on, st = r.render(cam, stats=True, skip=True, **P)
+                    off = r.render(cam, skip=False, **P)
+                    assert np.array_equal(on, off), (K, shade, filt)
+                    assert st["evaluated_samples"] < st["dense_samples"]
+    finally:
+        r.close()

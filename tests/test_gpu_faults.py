@@ -128,3 +128,23 @@ def test_argument_and_state_errors(rc):
     finally:
         torch.cuda.synchronize()
         rc.rc_context_destroy(ctx)
+
+
+def test_read_probe(rc):
+    """The read-bandwidth probe runs on the context's stream and checks its
+    arguments."""
+    import torch
+    ctx = rc.rc_context_create(0)
+    try:
+        buf = torch.ones(1 << 20, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        rc.rc_probe_read_bandwidth(ctx, buf, 4)
+        ev[1].record()
+        rc.rc_context_sync(ctx)
+        assert ev[0].elapsed_time(ev[1]) > 0
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_probe_read_bandwidth(ctx, buf[1:], 4)          # not 16-byte aligned
+        assert ei.value.status == rc.RC_ERR_INVALID_ARG
+    finally:
+        rc.rc_context_destroy(ctx)
