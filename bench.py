@@ -250,6 +250,49 @@ def filter_forms(rc, ctx, vol, w, P, cam_structs, outs, ref_imgs, flush, stream,
     return out
 
 
+def precision_form(rc, ctx, flush, stream, hbm_peak):
+    """The precision configuration: 512x512x256 phantom, 2048^2 image, step
+    0.25, shaded, 1024-entry table; FP32 storage (FP32 table) against FP16
+    (normalised) and uint16 storage with the FP16 table. One view; ms per
+    frame, dense-equivalent Gsamples/s, evaluated samples, PSNR against the
+    FP32 image."""
+    import torch
+    wp = synth.WORKLOADS["precision_512x512x256"]
+    ph = synth.workload_phantom("precision_512x512x256")
+    tf = synth.tf_table(wp["K"])
+    cam = synth.orbit_camera(ph.dims, ph.spacing, wp["azimuths"][0], width=wp["width"], height=wp["height"])
+    P = rc.RenderParams(step_vox=wp["step"], term=wp["term"], shade=wp["shade"], skip=True)
+    img = torch.empty((wp["height"], wp["width"], 4), device="cuda")
+    ref = None
+    out = {"workload": "precision_512x512x256", "image": "2048x2048", "step_vox": wp["step"], "table_entries": wp["K"]}
+    for name, storage, fp16 in (("f32", rc.RC_STORE_F32, False), ("f16", rc.RC_STORE_F16, True),
+                                ("u16", rc.RC_STORE_U16, True)):
+        vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, storage)
+        rc.rc_volume_upload(ctx, vol, ph.vol)
+        rc.rc_tf_set(ctx, tf, fp16)
+        rc.rc_camera_set(ctx, cam)
+        st = rc.rc_render(ctx, vol, P, img, stats=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        for e in ev:
+            e[0].record(stream)
+            rc.rc_render(ctx, vol, P, img)
+            e[1].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        res = {"ms_per_frame": ms, "gsamples_s": st["dense_samples"] / (ms / 1e3) / 1e9,
+               "dense_samples": st["dense_samples"], "evaluated_samples": st["evaluated_samples"]}
+        if ref is None:
+            ref = img.clone()
+        else:
+            mse = float(((img - ref) ** 2).mean())
+            res["psnr_db_vs_f32"] = float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)
+            res["speedup_vs_f32"] = out["f32"]["ms_per_frame"] / ms
+        out[name] = res
+        rc.rc_volume_destroy(ctx, vol)
+    return out
+
+
 def adjoint_form(rc, ctx, flush, stream):
     """Transfer-function gradient on the differentiable workload (128x128x96,
     8 views at 512^2, unshaded, step 0.5): time of rc_render_backward_views
@@ -438,6 +481,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16 / uint16 storage forms")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal form")
+    ap.add_argument("--no-precision", action="store_true", help="skip the 512x512x256 precision form")
     ap.add_argument("--proposal-phantoms", type=int, default=8, help="training phantoms of the proposal form")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -578,6 +622,8 @@ def main():
 
     if not args.no_forms:
         forms["adjoint"] = adjoint_form(rc, ctx, flush, stream)
+        if not args.no_precision:
+            forms["precision"] = precision_form(rc, ctx, flush, stream, hbm_peak)
         rc.rc_tf_set_device(ctx, tf_dev)
 
     if not args.no_proposal:
