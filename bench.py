@@ -293,6 +293,45 @@ def precision_form(rc, ctx, flush, stream, hbm_peak):
     return out
 
 
+def batch_form(rc, ctx, vol, ph, P, cam_structs, flush, stream, n_extra=3):
+    """Several volumes in one launch: the bench phantom and n_extra seeded
+    phantoms of the learned-proposal family (same shape), every orbit view of
+    each, against one multi-view launch per volume."""
+    import torch
+    wp = synth.WORKLOADS["proposal_256x256x180"]
+    extra = synth.proposal_phantoms(wp["train_seeds"][:n_extra])
+    vols = [vol]
+    for v in extra:
+        h = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, rc.RC_STORE_F32)
+        rc.rc_volume_upload(ctx, h, v)
+        vols.append(h)
+    n = len(cam_structs)
+    H, W = cam_structs[0].height, cam_structs[0].width
+    out = torch.empty((len(vols), n, H, W, 4), device="cuda")
+    st = rc.rc_render_batch(ctx, vols, P, cam_structs, out, stats=True)
+    one = []
+    batch = []
+    for rep in range(3):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        rc.rc_render_batch(ctx, vols, P, cam_structs, out)
+        e[1].record(stream)
+        for i, h in enumerate(vols):
+            rc.rc_render_views(ctx, h, P, cam_structs, out[i])
+        e[2].record(stream)
+        flush.zero_()
+        batch.append(e)
+    torch.cuda.synchronize()
+    b_ms = statistics.median(a.elapsed_time(b) for a, b, c in batch)
+    s_ms = statistics.median(b.elapsed_time(c) for a, b, c in batch)
+    for h in vols[1:]:
+        rc.rc_volume_destroy(ctx, h)
+    frames = len(vols) * n
+    return {"volumes": len(vols), "views_per_volume": n, "ms_per_frame_batch": b_ms / frames,
+            "ms_per_frame_per_volume_launches": s_ms / frames,
+            "gsamples_s_batch": st["dense_samples"] / (b_ms / 1e3) / 1e9}
+
+
 def adjoint_form(rc, ctx, flush, stream):
     """Transfer-function gradient on the differentiable workload (128x128x96,
     8 views at 512^2, unshaded, step 0.5): time of rc_render_backward_views
@@ -619,6 +658,7 @@ def main():
         rc.rc_tf_set_device(ctx, tf_dev)
         forms.update(filter_forms(rc, ctx, vol, w, P, cam_structs, outs, fp32_imgs, flush, stream, hbm_peak))
         rc.rc_tf_set_device(ctx, tf_dev)
+        forms["volume_batch"] = batch_form(rc, ctx, vol, ph, P, cam_structs, flush, stream)
 
     if not args.no_forms:
         forms["adjoint"] = adjoint_form(rc, ctx, flush, stream)

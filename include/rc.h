@@ -216,6 +216,16 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
 rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                           const rc_camera *cams, int nviews, float *out_rgba, rc_stats *stats);
 
+/* Renders nviews cameras of each of nvols volumes in one launch (the
+ * compositing function): the volumes must share shape, spacing, vmax and
+ * storage (RC_ERR_INVALID_ARG otherwise), and the context's table and the
+ * cameras apply to all; nvols * nviews <= 65535. out_rgba: device
+ * nvols*nviews*H*W*4 floats, volume-major then view-major; each image equals
+ * rc_render_views of its volume. stats (optional, synchronises) sums over
+ * everything. */
+rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvols, const rc_render_params *params,
+                          const rc_camera *cams, int nviews, float *out_rgba, rc_stats *stats);
+
 /* Gradient of a loss with respect to the transfer function entries, given the
  * gradient of the loss with respect to the composited image (Eq. 4-5 are
  * differentiable in the table). dL_dimage: device, width*height*4 floats;

@@ -89,6 +89,8 @@ SIGNATURES = {
     "rc_proposal_train_step": (_I, [_P, _P, _P, C.c_int64, C.c_float, _P]),
     "rc_render_importance": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P, _I, C.c_float, _P, _P,
                                   C.POINTER(rc_stats)]),
+    "rc_render_batch": (_I, [_P, _P, _I, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P,
+                             C.POINTER(rc_stats)]),
     "rc_render_backward_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P, _P]),
     "rc_render_proposal": (_I, [_P, _P, C.POINTER(rc_render_params), _I, C.c_float, _P, _P, C.POINTER(rc_stats)]),
     "rc_render_proposal_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _I, C.c_float,
@@ -285,6 +287,18 @@ def rc_render_views(ctx, vol, params, cams, out, stats=False):
     st = rc_stats() if stats else None
     _check(lib().rc_render_views(ctx, vol, C.byref(p), arr, len(cams), _ptr(out),
                                  C.byref(st) if st is not None else None), ctx, "rc_render_views")
+    return _stats_dict(st)
+
+
+def rc_render_batch(ctx, vols, params, cams, out, stats=False):
+    """Every camera of every volume in one launch (out: CUDA float32
+    nvols x nviews x H x W x 4)."""
+    p = _params(params)
+    varr = (C.c_void_p * len(vols))(*vols)
+    arr = (rc_camera * len(cams))(*[c if isinstance(c, rc_camera) else make_camera(c) for c in cams])
+    st = rc_stats() if stats else None
+    _check(lib().rc_render_batch(ctx, varr, len(vols), C.byref(p), arr, len(cams), _ptr(out),
+                                 C.byref(st) if st is not None else None), ctx, "rc_render_batch")
     return _stats_dict(st)
 
 

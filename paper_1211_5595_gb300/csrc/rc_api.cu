@@ -40,6 +40,9 @@ struct rc_context {
     // camera records of a multi-view render
     CamRec *d_cams = nullptr;
     int cams_cap = 0;
+    // per-volume pointers of a batch render
+    BatchVol *d_batch = nullptr;
+    int batch_cap = 0;
     // scratch of the adjoint: 4K fixed-point accumulators + |dL/dI| maximum
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -228,6 +231,7 @@ rc_status rc_context_destroy(rc_context *ctx) {
     cudaFree(ctx->d_amax);
     cudaFree(ctx->d_stats);
     cudaFree(ctx->d_cams);
+    cudaFree(ctx->d_batch);
     cudaFreeHost(ctx->h_stats);
     cudaFree(ctx->d_scratch);
     cudaFree(ctx->d_param);
@@ -752,6 +756,8 @@ static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render
     a.out = reinterpret_cast<float4 *>(out);
     a.stats = nullptr;
     a.cams = nullptr;
+    a.batch = nullptr;
+    a.views = 1;
     return a;
 }
 
@@ -799,6 +805,65 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
         a.stats = ctx->d_stats;
     }
     RC_CUDA(ctx, launch_march(a, nviews, ctx->stream));
+    if (stats) return read_stats(ctx, stats, false);
+    return RC_OK;
+}
+
+rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvols, const rc_render_params *p,
+                          const rc_camera *cams, int nviews, float *out_rgba, rc_stats *stats) {
+    const char *who = "rc_render_batch";
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
+    if (!vols || nvols < 1) return fail(ctx, RC_ERR_INVALID_ARG, "%s: %d volumes", who, vols ? nvols : 0);
+    rc_status st = check_views(ctx, cams, nviews, who);
+    if (st != RC_OK) return st;
+    if ((long long)nvols * nviews > 65535)
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: %d volumes x %d views (at most 65535)", who, nvols, nviews);
+    if ((long long)nvols * nviews * cams[0].width * cams[0].height > (1ll << 31))
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: more than 2^31 pixels", who);
+    for (int i = 0; i < nvols; i++) {
+        st = check_render_views(ctx, vols[i], p, cams, out_rgba, who);
+        if (st != RC_OK) return st;
+        const rc_volume *v = vols[i], *v0 = vols[0];
+        if (v->storage != v0->storage || v->vmax != v0->vmax || v->n[0] != v0->n[0] || v->n[1] != v0->n[1] ||
+            v->n[2] != v0->n[2] || v->s[0] != v0->s[0] || v->s[1] != v0->s[1] || v->s[2] != v0->s[2])
+            return fail(ctx, RC_ERR_INVALID_ARG, "%s: volume %d differs from volume 0 in shape, spacing, vmax or "
+                        "storage", who, i);
+    }
+    if (p->func != RC_FUNC_COMPOSITE) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: compositing function only", who);
+    DeviceScope ds(ctx->device);
+    for (int i = 0; i < nvols; i++) {
+        st = ensure_occupancy(ctx, const_cast<rc_volume *>(vols[i]), p->filter);
+        if (st != RC_OK) return st;
+    }
+    CamRec first;
+    st = upload_views(ctx, vols[0], cams, nviews, &first, who);
+    if (st != RC_OK) return st;
+    if (ctx->batch_cap < nvols) {
+        BatchVol *buf = nullptr;
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // queued kernels may still read the old records
+        RC_CUDA(ctx, dev_alloc(&buf, (size_t)nvols * sizeof(BatchVol)));
+        cudaFree(ctx->d_batch);
+        ctx->d_batch = buf;
+        ctx->batch_cap = nvols;
+    }
+    BatchVol *recs = new (std::nothrow) BatchVol[nvols];
+    if (!recs) return fail(ctx, RC_ERR_OOM, "%s: host allocation", who);
+    for (int i = 0; i < nvols; i++)
+        recs[i] = BatchVol{vols[i]->d_data, vols[i]->d_vg, vols[i]->d_occ[p->filter], vols[i]->d_fine[p->filter]};
+    cudaError_t ce = cudaMemcpyAsync(ctx->d_batch, recs, (size_t)nvols * sizeof(BatchVol), cudaMemcpyHostToDevice,
+                                     ctx->stream);
+    delete[] recs;
+    RC_CUDA(ctx, ce);
+    MarchArgs a = march_args(ctx, vols[0], p, out_rgba);
+    a.cam = first;
+    a.cams = ctx->d_cams;
+    a.batch = ctx->d_batch;
+    a.views = nviews;
+    if (stats) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        a.stats = ctx->d_stats;
+    }
+    RC_CUDA(ctx, launch_march(a, nvols * nviews, ctx->stream));
     if (stats) return read_stats(ctx, stats, false);
     return RC_OK;
 }

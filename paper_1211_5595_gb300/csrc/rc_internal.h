@@ -72,6 +72,15 @@ struct MarchParams {
     int filter;            // rc_filter
 };
 
+// Per-volume pointers of a batch of volumes with one shape, spacing and
+// storage (the rest of the volume record is shared).
+struct BatchVol {
+    const void *data;
+    const float4 *vg;
+    const uint8_t *occ;
+    const unsigned long long *fine;
+};
+
 struct MarchArgs {
     CamRec cam;
     VolDev vol;
@@ -82,6 +91,8 @@ struct MarchArgs {
     float4 *out;                   // H x W RGBA (view-major for several views)
     unsigned long long *stats;     // dense, evaluated, hit, total (or null)
     const CamRec *cams;            // one record per view (blockIdx.z), or null: cam
+    const BatchVol *batch;         // compositing: blockIdx.z = volume * views + view (or null)
+    int views;                     // views per volume of a batch
 };
 
 // Adjoint arguments (compositing function only).

@@ -42,13 +42,27 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
         load_tf(a.tf, s_tf);
         __syncthreads();
     }
-    const CamRec cam = a.cams ? a.cams[blockIdx.z] : a.cam;
+    // a batch of volumes: the volume's own data and masks, the shared record
+    VolDev vol = a.vol;
+    const uint8_t *occ = a.occ;
+    const unsigned long long *fine = a.fine;
+    int view = blockIdx.z;
+    if (a.batch) {
+        const int vi = blockIdx.z / a.views;
+        view = blockIdx.z - vi * a.views;
+        const BatchVol bv = a.batch[vi];
+        vol.data = bv.data;
+        vol.vg = bv.vg;
+        occ = bv.occ;
+        fine = bv.fine;
+    }
+    const CamRec cam = a.cams ? a.cams[view] : a.cam;
     float4 *out = a.out + (size_t)blockIdx.z * cam.W * cam.H;
     int x, y;
     pixel_of_thread(x, y);
     const bool inimg = x < cam.W && y < cam.H;
     Ray R;
-    const bool hit = inimg && setup_ray(cam, a.vol, a.p.step_vox, x, y, R);
+    const bool hit = inimg && setup_ray(cam, vol, a.p.step_vox, x, y, R);
     const int nsamp = hit ? R.nsamp : 0;
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
     int k = 0;
@@ -59,19 +73,19 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
         float p[3];
         position_at(R, sample_t(R, k), p);
         Cell c;
-        cell_of(a.vol, p, c);
+        cell_of(vol, p, c);
         if (a.p.skip) {
             // the largest empty block around the sample: with the fine mask
             // the cell-brick, its octant or its 4^3 sub-block; else the brick
-            const int b = brick_of(a.vol, c);
-            const int s = a.fine ? empty_block(__ldg(a.fine + b), c) : (__ldg(a.occ + b) ? -1 : 4);
+            const int b = brick_of(vol, c);
+            const int s = fine ? empty_block(__ldg(fine + b), c) : (__ldg(occ + b) ? -1 : 4);
             if (s >= 0) {
-                k = jump_block(R, a.vol, c, k, s);
+                k = jump_block(R, vol, c, k, s);
                 active = k < nsamp;
                 continue;
             }
         }
-        float4 e = eval_sample_x<ST, F>(a.vol, a.p, s_tf, a.tf, R.dir, c, a.p.rmode, a.p.ratio);
+        float4 e = eval_sample_x<ST, F>(vol, a.p, s_tf, a.tf, R.dir, c, a.p.rmode, a.p.ratio);
         composite_add(e, C0, C1, C2, T);
         evald++;
         k++;

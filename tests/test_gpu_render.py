@@ -244,3 +244,45 @@ def test_render_views_equals_single_renders(rc, c1):
     with pytest.raises(rc.RCError) as ei:
         rc.rc_render_views(r.ctx, r.vol, P, bad, out)
     assert ei.value.status == rc.RC_ERR_INVALID_ARG
+
+
+def test_render_batch_equals_views(rc):
+    """Several volumes x several views in one launch: every image equals the
+    multi-view render of its volume; mismatched volumes are refused."""
+    import torch
+    ctx = rc.rc_context_create(0)
+    vols = []
+    try:
+        rc.rc_tf_set(ctx, synth.tf_table(256))
+        dims, sp = (72, 60, 44), (1.0, 1.0, 1.5)
+        for seed in (31, 32, 33):
+            ph = synth.head_phantom(dims, sp, seed=seed, tumor_radius_vox=3 + seed % 4)
+            v = rc.rc_volume_create(ctx, dims, sp, 4095, rc.RC_STORE_F32)
+            rc.rc_volume_upload(ctx, v, ph.vol)
+            vols.append(v)
+        cams = [synth.orbit_camera(dims, sp, az, width=64, height=48) for az in (10.0, 100.0, 250.0, 333.0)]
+        P = dict(step_vox=0.5, term=0.99, shade=True, skip=True)
+        out = torch.empty((3, 4, 48, 64, 4), device="cuda")
+        st = rc.rc_render_batch(ctx, vols, P, cams, out, stats=True)
+        one = torch.empty((4, 48, 64, 4), device="cuda")
+        dense = 0
+        for i, v in enumerate(vols):
+            s1 = rc.rc_render_views(ctx, v, P, cams, one, stats=True)
+            torch.cuda.synchronize()
+            assert torch.equal(out[i], one)
+            dense += s1["dense_samples"]
+        assert st["dense_samples"] == dense and st["rays_total"] == 3 * 4 * 48 * 64
+        other = rc.rc_volume_create(ctx, (72, 60, 45), sp, 4095, rc.RC_STORE_F32)
+        vols.append(other)
+        rc.rc_volume_upload(ctx, other, np.zeros(72 * 60 * 45, np.uint16))
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_render_batch(ctx, vols, P, cams, torch.empty((4, 4, 48, 64, 4), device="cuda"))
+        assert ei.value.status == rc.RC_ERR_INVALID_ARG
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_render_batch(ctx, vols[:3], dict(P, func=rc.RC_FUNC_MIP), cams, out)
+        assert ei.value.status == rc.RC_ERR_UNSUPPORTED
+    finally:
+        torch.cuda.synchronize()
+        for v in vols:
+            rc.rc_volume_destroy(ctx, v)
+        rc.rc_context_destroy(ctx)
