@@ -533,6 +533,10 @@ def main():
     world, rank, local = setup_dist()
     if args.impl == "reference":
         return run_reference(args, w, world, rank)
+    if world > 1:
+        # the scaling line needs the main metric and e2e only: the forms
+        # (identical on every rank) would only multiply host work per rank
+        args.no_forms = args.no_proposal = args.no_precision = True
 
     import torch
     import torch.distributed as dist
