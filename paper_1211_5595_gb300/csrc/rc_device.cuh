@@ -501,36 +501,4 @@ __device__ __forceinline__ int empty_block(unsigned long long m, const Cell &c) 
     return -1;
 }
 
-// Jump over a brick the occupancy mask marks empty. Returns the index of the
-// first sample that may lie outside brick(c): the sample m just before the
-// computed exit distance is verified to be in the same brick; since each
-// coordinate of the computed positions is monotone in k, every sample between
-// k and m is then inside too. Falls back to k + 1 when the check fails.
-__device__ __forceinline__ int jump_empty(const Ray &R, const VolDev &v, const Cell &c, int k) {
-    const float INF = __int_as_float(0x7f800000);
-    float texit = INF;
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        int b = c.i[a] >> 4;
-        if (R.d[a] > 0.0f && b < v.cb[a] - 1)
-            texit = fminf(texit, __fdiv_rn((float)(16 * b + 16) - R.o[a], R.d[a]));
-        else if (R.d[a] < 0.0f && b > 0)
-            texit = fminf(texit, __fdiv_rn((float)(16 * b) - R.o[a], R.d[a]));
-    }
-    if (texit == INF) return R.nsamp;
-    float fm = floorf(__fdiv_rn(texit - R.tn, R.ds));
-    int m = fm >= (float)R.nsamp ? R.nsamp - 1 : (int)fm;
-    if (m <= k) return k + 1;
-    const int b0 = brick_of(v, c);
-#pragma unroll 1
-    for (int tries = 0; tries < 2 && m > k; tries++, m--) {
-        float p[3];
-        position_at(R, sample_t(R, m), p);
-        Cell cm;
-        cell_of(v, p, cm);
-        if (brick_of(v, cm) == b0) return m + 1;
-    }
-    return k + 1;
-}
-
 }  // namespace rc
