@@ -1056,7 +1056,7 @@ static rc_status net_alloc(rc_context *ctx) {
     uint8_t *f = nullptr;
     if (dev_alloc(&p, kParams * sizeof(float)) != cudaSuccess || dev_alloc(&m, kParams * sizeof(float)) != cudaSuccess ||
         dev_alloc(&v, kParams * sizeof(float)) != cudaSuccess || dev_alloc(&g, kParams * sizeof(float)) != cudaSuccess ||
-        dev_alloc(&f, kUmmaBytes) != cudaSuccess) {
+        dev_alloc(&f, kUmmaAllBytes) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(p);
         cudaFree(m);
@@ -1193,12 +1193,12 @@ rc_status rc_proposal_forward(rc_context *ctx, const float *features, int64_t n,
 
 static rc_status net_grad(rc_context *ctx, const float *features, const float *targets, int64_t n, float *grad,
                           float *loss) {
-    const int grid = (int)(n / 32 + 1 < 152 ? n / 32 + 1 : 152);
+    const int grid = train_grid(n);
     if (ctx->partial_blocks < grid) {
         float *pp = nullptr, *lp = nullptr;
         RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        if (dev_alloc(&pp, (size_t)152 * kParams * sizeof(float)) != cudaSuccess ||
-            dev_alloc(&lp, 152 * sizeof(float)) != cudaSuccess) {
+        if (dev_alloc(&pp, (size_t)grid * kParams * sizeof(float)) != cudaSuccess ||
+            dev_alloc(&lp, grid * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(pp);
             return fail(ctx, RC_ERR_OOM, "proposal: gradient partials");
@@ -1207,16 +1207,19 @@ static rc_status net_grad(rc_context *ctx, const float *features, const float *t
         cudaFree(ctx->d_loss_partial);
         ctx->d_partial = pp;
         ctx->d_loss_partial = lp;
-        ctx->partial_blocks = 152;
+        ctx->partial_blocks = grid;
     }
     TrainArgs a;
     a.feat = features;
     a.target = targets;
     a.n = n;
     a.params = ctx->d_param;
+    a.umma = ctx->d_umma;
     a.partial = ctx->d_partial;
     a.loss_partial = ctx->d_loss_partial;
     a.inv_n = (float)(1.0 / (double)n);
+    a.budget = wait_budget(&a.issue_mma);
+    a.err = error_word(ctx);
     RC_CUDA(ctx, launch_train_grad(a, grid, grad, loss, ctx->stream));
     return RC_OK;
 }

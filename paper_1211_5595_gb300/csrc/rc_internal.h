@@ -128,6 +128,13 @@ constexpr unsigned kUmmaL2 = kUmmaL1 + kHid * kFeat * 2;
 constexpr unsigned kUmmaL3 = kUmmaL2 + kHid * kHid * 2;
 constexpr unsigned kUmmaL4 = kUmmaL3 + kHid * kHid * 2;
 constexpr unsigned kUmmaBytes = kUmmaL4 + kN4 * kHid * 2;   // 36864
+// B operands of the training backward's input gradients (dH = dZ W^T): W4 as
+// 64 x 48 (outputs padded), W3 and W2 as 64 x 64, N = the layer's inputs,
+// K = its outputs; stored after the forward operands.
+constexpr unsigned kUmmaB4 = kUmmaBytes;
+constexpr unsigned kUmmaB3 = kUmmaB4 + kHid * kN4 * 2;
+constexpr unsigned kUmmaB2 = kUmmaB3 + kHid * kHid * 2;
+constexpr unsigned kUmmaAllBytes = kUmmaB2 + kHid * kHid * 2;   // 59392
 
 struct NetDev {
     const uint8_t *umma;      // packed BF16 B operands (kUmmaBytes, 16-byte aligned)
@@ -165,10 +172,14 @@ struct TrainArgs {
     const float *feat;        // n x 112
     const float *target;      // n x 33: 32 profile bins + final transmittance
     long long n;
-    const float *params;      // FP32 master parameters
+    const float *params;      // FP32 master parameters (biases)
+    const uint8_t *umma;      // packed BF16 B operands, forward and backward (kUmmaAllBytes)
     float *partial;           // gridDim x kParams gradient partials
     float *loss_partial;      // gridDim
     float inv_n;
+    long long budget;         // clock cycles a wait may take before it gives up
+    int *err;                 // bit 0: a wait gave up
+    int issue_mma;            // 0 only in the timeout test
 };
 
 // ---- launchers (return the launch error) --------------------------------
@@ -196,6 +207,7 @@ cudaError_t launch_features(const MarchArgs &a, float *out, cudaStream_t s);
 cudaError_t launch_tc_net(const TcNetArgs &a, cudaStream_t s);                  // feat != null: outputs, else ranges
 cudaError_t launch_importance(const ImportanceArgs &a, int nviews, cudaStream_t s); // pdf != null: given PDFs, else ranges
 cudaError_t launch_train_grad(const TrainArgs &a, int grid, float *grad, float *loss, cudaStream_t s);
+int train_grid(long long n);      // CTAs of the training kernel for n rays (one per SM at most)
 cudaError_t launch_adam(float *params, float *m, float *v, const float *grad, long long step, float lr,
                         cudaStream_t s);
 cudaError_t launch_pack(const float *params, uint8_t *umma, cudaStream_t s);

@@ -591,137 +591,266 @@ __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A)
 }
 
 // ---------------------------------------------------------------------------
-// training (SIMT FP32 with the inference's BF16 rounding points)
+// training on the tensor cores: forward as the inference, then per layer the
+// weight gradient (rays as K, accumulated in TMEM over the CTA's tiles) and
+// the input gradient (rays as M)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+// Weight gradient of layer l: dW_l = H_{l-1}^T dZ_l over the tile's 128 rays,
+// an M = 128 MMA whose A rows are the layer's inputs (H^T, written here with
+// the rays contiguous), a row of ones (its D row is the bias gradient
+// sum_rays dZ) and zero rows; B is dZ^T (outputs x rays). Input gradient:
+// dH_{l-1} = dZ_l W_l^T, A = dZ (rays x outputs), B = W_l (inputs x outputs).
+// All operands BF16 (dZ rounded once), FP32 accumulation.
+struct TrainSmem {
+    uint8_t w[kUmmaAllBytes];              // forward and backward B operands
+    uint8_t x[128 * kFeat * 2];            // A: features (rays x 112)
+    uint8_t h[3][128 * kHid * 2];          // A: H1, H2, H3 (rays x 64)
+    uint8_t adz[128 * kHid * 2];           // A: dZ (rays x outputs)
+    uint8_t bdz[kHid * 128 * 2];           // B: dZ^T (outputs x rays)
+    uint8_t at[128 * 128 * 2];             // A: inputs^T + ones row (128 rows x rays)
+    float bias[3 * kHid + kN4];
+    float wloss[4];
+    unsigned long long bar_w, bar_m;
+    uint32_t tmem;
+};
+constexpr int kTrainCols = 512;            // D (64) | dW4 (48) | dW3 | dW2 | dW1 (64 each)
+constexpr uint32_t kColD = 0, kColW4 = 64, kColW3 = 128, kColW2 = 192, kColW1 = 256;
 
-constexpr int kTileRays = 32;
-constexpr int kTrainThreads = 128;
-constexpr int kTrainSmemFloats = kParams + kTileRays * (kFeat + 3 * kHid + kOut + 2 * kHid) + kTileRays;
-
-// out[r][j] = act(bias[j] + sum_k in[r][k] * bf16(W[k][j])), rays r < 32.
-template <int K, int N, bool RELU>
-__device__ __forceinline__ void train_dense(const float *in, const float *__restrict__ W, const float *__restrict__ bias,
-                                            float *out) {
-    for (int o = threadIdx.x; o < kTileRays * N; o += kTrainThreads) {
-        const int r = o / N, j = o % N;
-        float acc = __ldg(bias + j);
-        for (int k = 0; k < K; k++) acc = __fmaf_rn(in[r * K + k], bf16r(__ldg(W + k * N + j)), acc);
-        out[r * N + j] = RELU ? bf16r(fmaxf(acc, 0.0f)) : acc;
-    }
+// D (+)= A B^T over K / 16 MMAs, A with `rows_a` rows, B with n rows.
+__device__ __forceinline__ void issue_mma(uint32_t a0, int rows_a, uint32_t b0, int n, int K, uint32_t tmem_d,
+                                          bool accumulate) {
+    const uint32_t lbo_a = (uint32_t)(rows_a / 8) * 128, lbo_b = (uint32_t)(n / 8) * 128;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, n);
+    for (int ks = 0; ks < K / 16; ks++)
+        tc::mma_bf16(tmem_d, tc::smem_desc(a0 + ks * 2 * lbo_a, lbo_a, 128), tc::smem_desc(b0 + ks * 2 * lbo_b, lbo_b, 128),
+                     idesc, accumulate || ks > 0);
 }
 
-// g[W] += in^T dz, g[b] += sum_r dz (rays in order: deterministic)
-template <int K, int N>
-__device__ __forceinline__ void train_wgrad(const float *in, const float *dz, float *gW, float *gb) {
-    for (int o = threadIdx.x; o < K * N; o += kTrainThreads) {
-        const int k = o / N, j = o % N;
-        float acc = 0.0f;
-        for (int r = 0; r < kTileRays; r++) acc = __fmaf_rn(in[r * K + k], dz[r * N + j], acc);
-        gW[o] += acc;
-    }
-    for (int j = threadIdx.x; j < N; j += kTrainThreads) {
-        float acc = 0.0f;
-        for (int r = 0; r < kTileRays; r++) acc += dz[r * N + j];
-        gb[j] += acc;
-    }
+// A bounded wait for the CTA's committed MMAs (all 128 threads).
+__device__ __forceinline__ bool train_sync_mma(const TrainArgs &A, uint32_t bar, uint32_t &phase) {
+    const bool ok = __syncthreads_and(tc::bar_wait(bar, phase, A.budget));
+    if (ok) phase ^= 1u;
+    tc::fence_after();
+    return ok;
 }
 
-// dx[r][k] = (sum_j dz[r][j] bf16(W[k][j])) * [x[r][k] > 0]
-template <int K, int N>
-__device__ __forceinline__ void train_dgrad(const float *dz, const float *__restrict__ W, const float *x, float *dx) {
-    for (int o = threadIdx.x; o < kTileRays * K; o += kTrainThreads) {
-        const int r = o / K, k = o % K;
-        float acc = 0.0f;
-        for (int j = 0; j < N; j++) acc = __fmaf_rn(dz[r * N + j], bf16r(__ldg(W + k * N + j)), acc);
-        dx[o] = x[o] > 0.0f ? acc : 0.0f;
-    }
-}
-
-// Loss per ray: w KL(q || p) + (T^ - T)^2 with q = bins / sum(bins), w = sum(bins).
-__global__ void __launch_bounds__(kTrainThreads) train_grad_kernel(const TrainArgs A) {
-    extern __shared__ float sm[];
-    float *g = sm;
-    float *x = g + kParams;
-    float *h1 = x + kTileRays * kFeat;
-    float *h2 = h1 + kTileRays * kHid;
-    float *h3 = h2 + kTileRays * kHid;
-    float *z4 = h3 + kTileRays * kHid;
-    float *dA = z4 + kTileRays * kOut;
-    float *dB = dA + kTileRays * kHid;
-    float *lossr = dB + kTileRays * kHid;
-    const float *P = A.params;
-    for (int i = threadIdx.x; i < kParams; i += kTrainThreads) g[i] = 0.0f;
-    float block_loss = 0.0f;
-    for (long long tile = blockIdx.x; tile * kTileRays < A.n; tile += gridDim.x) {
-        const long long r0 = tile * kTileRays;
-        __syncthreads();
-        for (int e = threadIdx.x; e < kTileRays * kFeat; e += kTrainThreads) {
-            const int r = e / kFeat;
-            x[e] = r0 + r < A.n ? bf16r(A.feat[r0 * kFeat + e]) : 0.0f;
-        }
-        __syncthreads();
-        train_dense<kFeat, kHid, true>(x, P + kOffW1, P + kOffB1, h1);
-        __syncthreads();
-        train_dense<kHid, kHid, true>(h1, P + kOffW2, P + kOffB2, h2);
-        __syncthreads();
-        train_dense<kHid, kHid, true>(h2, P + kOffW3, P + kOffB3, h3);
-        __syncthreads();
-        train_dense<kHid, kOut, false>(h3, P + kOffW4, P + kOffB4, z4);
-        __syncthreads();
-        if (threadIdx.x < kTileRays) {
-            const int r = threadIdx.x;
-            float *z = z4 + r * kOut;
-            float loss = 0.0f;
-            if (r0 + r < A.n) {
-                const float *y = A.target + (r0 + r) * kOutUsed;
-                float mx = -INFINITY, S = 0.0f;
-                for (int b = 0; b < kBins; b++) {
-                    mx = fmaxf(mx, z[b]);
-                    S += y[b];
-                }
-                float se = 0.0f;
-                for (int b = 0; b < kBins; b++) se += expf(z[b] - mx);
-                const float lse = mx + logf(se);
-                for (int b = 0; b < kBins; b++) {
-                    const float p = expf(z[b] - lse);
-                    float d = 0.0f;
-                    if (S > 0.0f) {
-                        const float q = y[b] / S;
-                        d = S * (p - q);
-                        if (q > 0.0f) loss += S * q * (logf(q) - (z[b] - lse));
-                    }
-                    z[b] = d * A.inv_n;
-                }
-                const float th = 1.0f / (1.0f + expf(-z[kBins]));
-                const float dt = th - y[kBins];
-                loss += dt * dt;
-                z[kBins] = 2.0f * dt * th * (1.0f - th) * A.inv_n;
-            } else {
-                for (int b = 0; b <= kBins; b++) z[b] = 0.0f;
-            }
-            for (int b = kOutUsed; b < kOut; b++) z[b] = 0.0f;
-            lossr[r] = loss;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0)
-            for (int r = 0; r < kTileRays; r++) block_loss += lossr[r];
-        // backward: z4 now holds dL/dz4
-        train_wgrad<kHid, kOut>(h3, z4, g + kOffW4, g + kOffB4);
-        train_dgrad<kHid, kOut>(z4, P + kOffW4, h3, dA);
-        __syncthreads();
-        train_wgrad<kHid, kHid>(h2, dA, g + kOffW3, g + kOffB3);
-        train_dgrad<kHid, kHid>(dA, P + kOffW3, h2, dB);
-        __syncthreads();
-        train_wgrad<kHid, kHid>(h1, dB, g + kOffW2, g + kOffB2);
-        train_dgrad<kHid, kHid>(dB, P + kOffW2, h1, dA);
-        __syncthreads();
-        train_wgrad<kFeat, kHid>(x, dA, g + kOffW1, g + kOffB1);
-    }
+__device__ __forceinline__ void operands_ready() {
+    tc::fence_async_smem();
+    tc::fence_before();
     __syncthreads();
+    tc::fence_after();
+}
+
+// One BF16 value at (row, k) of a K-major operand with `rows` rows.
+__device__ __forceinline__ void put_bf16(uint8_t *M, int row, int k, int rows, float v) {
+    *reinterpret_cast<__nv_bfloat16 *>(M + tc::core_offset(row, k, rows)) = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ float get_bf16(const uint8_t *M, int row, int k, int rows) {
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(M + tc::core_offset(row, k, rows)));
+}
+
+// Column t of the weight-gradient A operand: the thread's n inputs (BF16,
+// already rounded) in rows 0..n-1, 1 in row n; rows n+1 .. zero_to-1 zeroed.
+__device__ __forceinline__ void put_inputs_t(uint8_t *at, const uint8_t *src, int n, int t, int zero_to) {
+    for (int r = 0; r < n; r++)
+        *reinterpret_cast<__nv_bfloat16 *>(at + tc::core_offset(r, t, 128)) =
+            *reinterpret_cast<const __nv_bfloat16 *>(src + tc::core_offset(t, r, 128));
+    put_bf16(at, n, t, 128, 1.0f);
+    for (int r = n + 1; r < zero_to; r++) put_bf16(at, r, t, 128, 0.0f);
+}
+
+// dZ of this thread's ray (n values) as row t of A (K = k_pad) and column t of B^T.
+__device__ __forceinline__ void put_dz(TrainSmem &S, const float (&dz)[kHid], int n, int k_pad, int t, bool as_a) {
+#pragma unroll
+    for (int j = 0; j < kHid; j++) {
+        if (j >= k_pad) break;
+        const float v = j < n ? dz[j] : 0.0f;
+        if (as_a) put_bf16(S.adz, t, j, 128, v);
+        put_bf16(S.bdz, j, t, k_pad, v);
+    }
+}
+
+__global__ void __launch_bounds__(128) tc_train_kernel(const TrainArgs A) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint32_t bar_w = tc::smem_addr(&S.bar_w), bar_m = tc::smem_addr(&S.bar_m);
+    if (warp == 0) tc::tmem_alloc<kTrainCols>(tc::smem_addr(&S.tmem));
+    if (t == 0) {
+        tc::bar_init(bar_w, 1);
+        tc::bar_init(bar_m, 1);
+    }
+    for (int i = t; i < 3 * kHid + kN4; i += blockDim.x) {
+        const int l = i / kHid, j = i % kHid;
+        float b = 0.0f;
+        if (l < 3) b = A.params[(l == 0 ? kOffB1 : l == 1 ? kOffB2 : kOffB3) + j];
+        else if (j < kOut) b = A.params[kOffB4 + j];
+        S.bias[i] = b;
+    }
+    // the weight-gradient A operand starts all zero (rows beyond the ones row)
+    for (int i = t; i < 128 * 128 * 2 / 16; i += blockDim.x) reinterpret_cast<uint4 *>(S.at)[i] = make_uint4(0, 0, 0, 0);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = S.tmem;
+    if (t == 0) tc::bulk_g2s(tc::smem_addr(S.w), A.umma, kUmmaAllBytes, bar_w);
+    bool ok = __syncthreads_and(tc::bar_wait(bar_w, 0, A.budget));
+    if (!ok) tc::bar_wait(bar_w, 0, A.budget);
+    uint32_t phase = 0;
+    bool mma_waited_out = false, first = true;
+    float loss_sum = 0.0f;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);      // this warp's lanes
+    const long long ntiles = (A.n + 127) / 128;
+#pragma unroll 1
+    for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const long long r0 = tile * 128, r = r0 + t;
+        const bool valid = r < A.n;
+        // features: coalesced float4 loads of the contiguous tile -> BF16
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(A.feat + r0 * kFeat);
+            const long long nvalid = min((long long)128, A.n - r0);
+#pragma unroll 7
+            for (int i = 0; i < 128 * kFeat / 4 / 128; i++) {
+                const int e = i * 128 + t, row = e / (kFeat / 4), k = (e % (kFeat / 4)) * 4;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (row < nvalid) v = __ldg(src + e);
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+                uint2 q;
+                q.x = *reinterpret_cast<uint32_t *>(&lo);
+                q.y = *reinterpret_cast<uint32_t *>(&hi);
+                *reinterpret_cast<uint2 *>(S.x + tc::core_offset(row, k, 128)) = q;
+            }
+        }
+        // forward: layers 1-3 into H1..H3, layer 4 -> logits
+        float z[kN4];
+#pragma unroll 1
+        for (int l = 0; l < 4 && ok; l++) {
+            operands_ready();
+            const NetLayer L = net_layer(l);
+            const uint8_t *Ain = l == 0 ? S.x : S.h[l - 1];
+            if (t == 0 && A.issue_mma) {
+                issue_mma(tc::smem_addr(Ain), 128, tc::smem_addr(S.w) + L.b_off, L.N, L.K, tmem + kColD, false);
+                tc::commit(bar_m);
+            }
+            ok = train_sync_mma(A, bar_m, phase);
+            if (!ok) {
+                mma_waited_out = true;
+                break;
+            }
+            if (l < 3) {
+                store_hidden(S.h[l], taddr + kColD, S.bias + l * kHid, t);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kN4; c += 16) {
+                    float v[16];
+                    tc::tmem_ld16(taddr + kColD + c, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) z[c + j] = v[j] + S.bias[3 * kHid + c + j];
+                }
+            }
+        }
+        if (!ok) break;
+        // loss per ray: w KL(q || p) + (T^ - T)^2, q = bins / w, w = sum(bins);
+        // dZ4 = dL/dz scaled by 1/n
+        float dz[kHid];
+        float loss = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kN4; j++) dz[j] = 0.0f;
+        if (valid) {
+            const float *y = A.target + r * kOutUsed;
+            float mx = z[0], W = 0.0f;
+#pragma unroll
+            for (int b = 0; b < kBins; b++) {
+                mx = fmaxf(mx, z[b]);
+                W += y[b];
+            }
+            float se = 0.0f;
+#pragma unroll
+            for (int b = 0; b < kBins; b++) se += expf(z[b] - mx);
+            const float lse = mx + logf(se);
+#pragma unroll
+            for (int b = 0; b < kBins; b++) {
+                const float p = expf(z[b] - lse);
+                if (W > 0.0f) {
+                    const float q = y[b] / W;
+                    dz[b] = W * (p - q) * A.inv_n;
+                    if (q > 0.0f) loss += W * q * (logf(q) - (z[b] - lse));
+                }
+            }
+            const float th = 1.0f / (1.0f + expf(-z[kBins]));
+            const float dt = th - y[kBins];
+            loss += dt * dt;
+            dz[kBins] = 2.0f * dt * th * (1.0f - th) * A.inv_n;
+        }
+        loss_sum += loss;
+        // backward, layer 4 .. 1
+#pragma unroll 1
+        for (int l = 3; l >= 0 && ok; l--) {
+            const int n_out = l == 3 ? kN4 : kHid, n_in = l == 0 ? kFeat : kHid;
+            put_dz(S, dz, l == 3 ? kOut : kHid, n_out, t, l > 0);
+            // inputs^T with the ones row; rows up to 113 are cleared when the
+            // previous layer (layer 1 of the previous tile) used more rows
+            put_inputs_t(S.at, l == 0 ? S.x : S.h[l - 1], n_in, t, l == 3 ? kFeat + 1 : n_in + 1);
+            operands_ready();
+            const uint32_t wcol = l == 3 ? kColW4 : l == 2 ? kColW3 : l == 1 ? kColW2 : kColW1;
+            if (t == 0 && A.issue_mma) {
+                issue_mma(tc::smem_addr(S.at), 128, tc::smem_addr(S.bdz), n_out, 128, tmem + wcol, !first);
+                if (l > 0) {
+                    const uint32_t bb = l == 3 ? kUmmaB4 : l == 2 ? kUmmaB3 : kUmmaB2;
+                    issue_mma(tc::smem_addr(S.adz), 128, tc::smem_addr(S.w) + bb, kHid, n_out, tmem + kColD, false);
+                }
+                tc::commit(bar_m);
+            }
+            ok = train_sync_mma(A, bar_m, phase);
+            if (!ok) {
+                mma_waited_out = true;
+                break;
+            }
+            if (l > 0) {
+                // dZ_{l-1} = dH * [H_{l-1} > 0]
+#pragma unroll
+                for (int c = 0; c < kHid; c += 16) {
+                    float v[16];
+                    tc::tmem_ld16(taddr + kColD + c, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) dz[c + j] = get_bf16(S.h[l - 1], t, c + j, 128) > 0.0f ? v[j] : 0.0f;
+                }
+            }
+        }
+        first = false;
+    }
+    if (!ok) {
+        if (t == 0) atomicOr(A.err, 1);
+        if (mma_waited_out && A.issue_mma) tc::bar_wait(bar_m, phase, A.budget);
+    }
+    // the CTA's gradient: lane = input row (or the bias at row n_in), column = output
     float *part = A.partial + (size_t)blockIdx.x * kParams;
-    for (int i = threadIdx.x; i < kParams; i += kTrainThreads) part[i] = g[i];
-    if (threadIdx.x == 0) A.loss_partial[blockIdx.x] = block_loss;
+    const int row = warp * 32 + lane;
+#pragma unroll 1
+    for (int l = 0; l < 4; l++) {
+        const int n_in = l == 0 ? kFeat : kHid, n_out = l == 3 ? kOut : kHid, n_cols = l == 3 ? kN4 : kHid;
+        const uint32_t wcol = l == 3 ? kColW4 : l == 2 ? kColW3 : l == 1 ? kColW2 : kColW1;
+        const int offW = l == 0 ? kOffW1 : l == 1 ? kOffW2 : l == 2 ? kOffW3 : kOffW4;
+        const int offB = l == 0 ? kOffB1 : l == 1 ? kOffB2 : l == 2 ? kOffB3 : kOffB4;
+        for (int c = 0; c < n_cols; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + wcol + c, v);
+            for (int j = 0; j < 16 && c + j < n_out; j++) {
+                const float g = (first || !ok) ? 0.0f : v[j];
+                if (row < n_in) part[offW + row * n_out + c + j] = g;
+                else if (row == n_in) part[offB + c + j] = g;
+            }
+        }
+    }
+    // loss: per-warp sums in a fixed order, then the CTA's
+    for (int o = 16; o > 0; o >>= 1) loss_sum += __shfl_xor_sync(0xffffffffu, loss_sum, o);
+    if (lane == 0) S.wloss[warp] = loss_sum;
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (t == 0) A.loss_partial[blockIdx.x] = ((S.wloss[0] + S.wloss[1]) + S.wloss[2]) + S.wloss[3];
+    if (warp == 0) tc::tmem_free<kTrainCols>(tmem);
 }
 
 __global__ void reduce_grad_kernel(const float *partial, const float *loss_partial, int nblocks, float inv_n,
@@ -739,11 +868,18 @@ __global__ void reduce_grad_kernel(const float *partial, const float *loss_parti
     }
 }
 
+int train_grid(long long n) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (n + 127) / 128;
+    return (int)max(1ll, min((long long)sms, tiles));
+}
+
 cudaError_t launch_train_grad(const TrainArgs &a, int grid, float *grad, float *loss, cudaStream_t s) {
-    const size_t smem = (size_t)kTrainSmemFloats * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(train_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int smem = (int)sizeof(TrainSmem);
+    cudaError_t e = cudaFuncSetAttribute(tc_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    train_grad_kernel<<<grid, kTrainThreads, smem, s>>>(a);
+    tc_train_kernel<<<grid, 128, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     reduce_grad_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(a.partial, a.loss_partial, grid, a.inv_n, grad, loss);
@@ -787,9 +923,30 @@ __global__ void pack_umma_kernel(const float *params, uint8_t *umma) {
     *reinterpret_cast<__nv_bfloat16 *>(umma + boff + tc::core_offset(n, k, N)) = __float2bfloat16_rn(w);
 }
 
+// B operands of the training backward: element (n, k) of layer l is
+// bf16(W_l[n][k]) (inputs x outputs, as stored; 0 for the padding outputs
+// k >= 40 of layer 4).
+__global__ void pack_umma_back_kernel(const float *params, uint8_t *umma) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int n4 = kHid * kN4, n3 = kHid * kHid;
+    if (idx >= n4 + 2 * n3) return;
+    int r, K, nw, woff;
+    unsigned boff;
+    if (idx < n4) { r = idx; K = kN4; nw = kOut; woff = kOffW4; boff = kUmmaB4; }
+    else if (idx < n4 + n3) { r = idx - n4; K = kHid; nw = kHid; woff = kOffW3; boff = kUmmaB3; }
+    else { r = idx - n4 - n3; K = kHid; nw = kHid; woff = kOffW2; boff = kUmmaB2; }
+    const int n = r / K, k = r % K;
+    const float w = k < nw ? params[woff + n * nw + k] : 0.0f;
+    *reinterpret_cast<__nv_bfloat16 *>(umma + boff + tc::core_offset(n, k, kHid)) = __float2bfloat16_rn(w);
+}
+
 cudaError_t launch_pack(const float *params, uint8_t *umma, cudaStream_t s) {
     constexpr int total = kHid * kFeat + 2 * kHid * kHid + kN4 * kHid;
     pack_umma_kernel<<<(total + 255) / 256, 256, 0, s>>>(params, umma);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    constexpr int back = kHid * kN4 + 2 * kHid * kHid;
+    pack_umma_back_kernel<<<(back + 255) / 256, 256, 0, s>>>(params, umma);
     return cudaGetLastError();
 }
 
