@@ -466,9 +466,27 @@ def network_throughput(rc, ctx, stream, n=1 << 20):
             bf16 = float(json.load(f)["bf16_tflops"])
     except Exception:
         pass
+    # training gradient (rc_proposal_grad): forward, weight gradients of all
+    # four layers and data gradients of layers 2-4, 46,592 MACs per ray, plus
+    # the deterministic cross-CTA reduction
+    tgt = torch.rand((n, 33), device="cuda", generator=g)
+    grad = torch.empty(18152, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    for _ in range(3):
+        rc.rc_proposal_grad(ctx, feat, tgt, n, grad, loss)
+    for e in ev:
+        e[0].record(stream)
+        rc.rc_proposal_grad(ctx, feat, tgt, n, grad, loss)
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    gms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    gflops = 2.0 * 46592 * n
+    del tgt, grad, loss
     return {"rays": n, "ms": ms, "tflops_s": flops / (ms / 1e3) / 1e12, "gbs": nbytes / (ms / 1e3) / 1e9,
             "frac_of_bf16_peak": (flops / (ms / 1e3) / 1e12 / bf16) if bf16 else None,
-            "note": "feature matrix in HBM: 580 B per ray against 35.8 kFLOP, so the launch is memory-bound"}
+            "note": "feature matrix in HBM: 580 B per ray against 35.8 kFLOP, so the launch is memory-bound",
+            "grad_ms": gms, "grad_mrays_s": n / (gms / 1e3) / 1e6, "grad_tflops_s": gflops / (gms / 1e3) / 1e12,
+            "grad_frac_of_bf16_peak": (gflops / (gms / 1e3) / 1e12 / bf16) if bf16 else None}
 
 
 def run_reference(args, w, world, rank):

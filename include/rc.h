@@ -354,7 +354,12 @@ rc_status rc_proposal_forward(rc_context *ctx, const float *features, int64_t n,
  * (device RC_PROPOSAL_PARAMS floats) and the loss (device float, may be NULL).
  * targets: n rows of 33 (profile bins, final transmittance). Loss per ray:
  * w KL(q || p) + (T^ - T)^2 with q = bins / sum(bins), w = sum(bins); BF16
- * rounding treated as identity in the backward. Deterministic. */
+ * rounding treated as identity in the backward. Runs on the tcgen05 tensor
+ * cores: the forward as in rc_proposal_forward, then per 128-ray tile the
+ * weight gradients (H^T dZ, accumulated in tensor memory over the tiles of a
+ * CTA) and the data gradients (dZ W^T) as BF16 MMAs with FP32 accumulation;
+ * dZ is rounded to BF16 as an MMA operand. Per-CTA partial sums are reduced
+ * in a fixed order: deterministic for a given n. */
 rc_status rc_proposal_grad(rc_context *ctx, const float *features, const float *targets, int64_t n,
                            float *grad, float *loss);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on that

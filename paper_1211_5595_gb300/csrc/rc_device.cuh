@@ -134,8 +134,44 @@ __device__ __forceinline__ float ldv(const typename Voxel<ST>::T *p) {
 // exact (true for integer codes and for FP16 values in [0, 1]).
 __device__ __forceinline__ float lerp(float a, float b, float w) { return __fmaf_rn(w, b - a, a); }
 
+// Packed FP32 pairs of the sm_100 family (sub / fma .rn.f32x2): each lane
+// rounds exactly as the scalar operation, so lerp2 on a pair equals lerp on
+// each element bit for bit, in half the instructions. A pair is a 64-bit
+// register holding (lo, hi).
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long lerp2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long w) {
+    unsigned long long d, r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(b), "l"(a));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(w), "l"(d), "l"(a));
+    return r;
+}
+
+// Four channels as two pairs: (x, y) in .x, (z, w) in .y.
+__device__ __forceinline__ ulonglong2 lerp4p(const ulonglong2 &a, const ulonglong2 &b, unsigned long long w) {
+    return make_ulonglong2(lerp2(a.x, b.x, w), lerp2(a.y, b.y, w));
+}
+
+__device__ __forceinline__ float4 unpack4(const ulonglong2 &v) {
+    const float2 lo = unpack2(v.x), hi = unpack2(v.y);
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 __device__ __forceinline__ float4 lerp4(const float4 &a, const float4 &b, float w) {
-    return make_float4(lerp(a.x, b.x, w), lerp(a.y, b.y, w), lerp(a.z, b.z, w), lerp(a.w, b.w, w));
+    const unsigned long long W = pack2(w, w);
+    return unpack4(lerp4p(make_ulonglong2(pack2(a.x, a.y), pack2(a.z, a.w)),
+                          make_ulonglong2(pack2(b.x, b.y), pack2(b.z, b.w)), W));
 }
 
 template <int ST>
@@ -158,15 +194,15 @@ __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
 // at p, the clamped border included; 8 four-wide loads replace 32 scalar
 // loads. The value is interpolated in the same order as trilinear().
 __device__ __forceinline__ float value_grad_vg(const VolDev &v, const Cell &c, float g[3]) {
-    const float4 *p = v.vg + (size_t)brick_of(v, c) * kGradVox +
-                      (((c.i[2] & 15) * kGradEdge + (c.i[1] & 15)) * kGradEdge + (c.i[0] & 15));
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(v.vg) + (size_t)brick_of(v, c) * kGradVox +
+                          (((c.i[2] & 15) * kGradEdge + (c.i[1] & 15)) * kGradEdge + (c.i[0] & 15));
     constexpr int DY = kGradEdge, DZ = kGradEdge * kGradEdge;
-    const float wx = c.w[0], wy = c.w[1], wz = c.w[2];
-    const float4 c00 = lerp4(__ldg(p), __ldg(p + 1), wx);
-    const float4 c10 = lerp4(__ldg(p + DY), __ldg(p + DY + 1), wx);
-    const float4 c01 = lerp4(__ldg(p + DZ), __ldg(p + DZ + 1), wx);
-    const float4 c11 = lerp4(__ldg(p + DZ + DY), __ldg(p + DZ + DY + 1), wx);
-    const float4 r = lerp4(lerp4(c00, c10, wy), lerp4(c01, c11, wy), wz);
+    const unsigned long long wx = pack2(c.w[0], c.w[0]), wy = pack2(c.w[1], c.w[1]), wz = pack2(c.w[2], c.w[2]);
+    const ulonglong2 c00 = lerp4p(__ldg(p), __ldg(p + 1), wx);
+    const ulonglong2 c10 = lerp4p(__ldg(p + DY), __ldg(p + DY + 1), wx);
+    const ulonglong2 c01 = lerp4p(__ldg(p + DZ), __ldg(p + DZ + 1), wx);
+    const ulonglong2 c11 = lerp4p(__ldg(p + DZ + DY), __ldg(p + DZ + DY + 1), wx);
+    const float4 r = unpack4(lerp4p(lerp4p(c00, c10, wy), lerp4p(c01, c11, wy), wz));
     g[0] = r.y * v.inv2s[0];
     g[1] = r.z * v.inv2s[1];
     g[2] = r.w * v.inv2s[2];
@@ -324,10 +360,10 @@ __device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, in
     float q = fminf(fmaxf(u, 0.0f), (float)(K - 1));
     int i = min((int)q, K - 2);
     float w = q - (float)i;
-    float4 a = tab[i], b = tab[i + 1];
+    const ulonglong2 *t2 = reinterpret_cast<const ulonglong2 *>(tab);
     if (i0) *i0 = i;
     if (w0) *w0 = w;
-    return make_float4(lerp(a.x, b.x, w), lerp(a.y, b.y, w), lerp(a.z, b.z, w), lerp(a.w, b.w, w));
+    return unpack4(lerp4p(t2[i], t2[i + 1], pack2(w, w)));
 }
 
 // Two-dimensional classification over (value, gradient magnitude), the
@@ -341,10 +377,11 @@ __device__ __forceinline__ float4 classify2(const TFDev &tf, float u, float w) {
     const float qw = fminf(fmaxf(w, 0.0f), (float)(M - 1));
     const int i = min((int)qu, K - 2), j = min((int)qw, M - 2);
     const float a = qu - (float)i, b = qw - (float)j;
-    const float4 *p = tf.tab2 + (size_t)j * K + i;
-    const float4 r0 = lerp4(__ldg(p), __ldg(p + 1), a);
-    const float4 r1 = lerp4(__ldg(p + K), __ldg(p + K + 1), a);
-    return lerp4(r0, r1, b);
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(tf.tab2) + (size_t)j * K + i;
+    const unsigned long long A = pack2(a, a);
+    const ulonglong2 r0 = lerp4p(__ldg(p), __ldg(p + 1), A);
+    const ulonglong2 r1 = lerp4p(__ldg(p + K), __ldg(p + K + 1), A);
+    return unpack4(lerp4p(r0, r1, pack2(b, b)));
 }
 
 // Eq. 3 for a segment of length ds: alpha' = 1 - (1 - alpha)^(ds/ds_ref).
