@@ -529,13 +529,16 @@ __device__ __forceinline__ int jump_block(const Ray &R, const VolDev &v, const C
 // per 4^3 sub-block, bit sz*16 + sy*4 + sx): 4 when the whole brick is empty,
 // 3 when its octant is, 2 when the sub-block is, -1 when the sample may have
 // non-zero opacity.
+// The sub-block's own bit is tested first: most evaluated samples lie in an
+// occupied sub-block and need nothing else.
 __device__ __forceinline__ int empty_block(unsigned long long m, const Cell &c) {
+    const int bit = ((c.i[0] >> 2) & 3) | (c.i[1] & 12) | ((c.i[2] & 12) << 2);   // sz*16 + sy*4 + sx
+    const unsigned half = (bit & 32) ? (unsigned)(m >> 32) : (unsigned)m;
+    if ((half >> (bit & 31)) & 1u) return -1;
     if (m == 0ull) return 4;
-    const int sx = (c.i[0] >> 2) & 3, sy = (c.i[1] >> 2) & 3, sz = (c.i[2] >> 2) & 3;
-    const int oct = (sz & 2) * 16 + (sy & 2) * 4 + (sx & 2);          // bit of the octant's first sub-block
+    const int oct = bit & 0x2A;                                          // bit of the octant's first sub-block
     if (((m >> oct) & 0x330033ull) == 0ull) return 3;                   // sub-blocks {0,1} x {0,1} x {0,1} of it
-    if (((m >> (sz * 16 + sy * 4 + sx)) & 1ull) == 0ull) return 2;
-    return -1;
+    return 2;
 }
 
 }  // namespace rc
