@@ -194,8 +194,11 @@ __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
 // at p, the clamped border included; 8 four-wide loads replace 32 scalar
 // loads. The value is interpolated in the same order as trilinear().
 __device__ __forceinline__ float value_grad_vg(const VolDev &v, const Cell &c, float g[3]) {
-    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(v.vg) + (size_t)brick_of(v, c) * kGradVox +
-                          (((c.i[2] & 15) * kGradEdge + (c.i[1] & 15)) * kGradEdge + (c.i[0] & 15));
+    // 32-bit index: a volume has fewer than 2^31 apron voxels (19^3 per
+    // brick), so fewer value+gradient entries (17^3 per brick)
+    const unsigned idx = (unsigned)brick_of(v, c) * (unsigned)kGradVox +
+                         (unsigned)(((c.i[2] & 15) * kGradEdge + (c.i[1] & 15)) * kGradEdge + (c.i[0] & 15));
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(v.vg) + idx;
     constexpr int DY = kGradEdge, DZ = kGradEdge * kGradEdge;
     const unsigned long long wx = pack2(c.w[0], c.w[0]), wy = pack2(c.w[1], c.w[1]), wz = pack2(c.w[2], c.w[2]);
     const ulonglong2 c00 = lerp4p(__ldg(p), __ldg(p + 1), wx);
@@ -389,11 +392,15 @@ __device__ __forceinline__ float4 classify2(const TFDev &tf, float u, float w) {
 // uses t^r = 2^(r log2 t) on the special-function unit: relative error about
 // r * 2^-21 (below 1e-5 for segments up to 8 reference steps), with the end
 // points exact (alpha 0 -> 0, alpha 1 -> 1).
+// RM >= 0 fixes the mode at compile time (the march instances per mode);
+// RM = -1 takes the runtime rmode.
+template <int RM = -1>
 __device__ __forceinline__ float correct_alpha(float a, int rmode, float ratio) {
+    const int m = RM >= 0 ? RM : rmode;
     float t = 1.0f - a;
-    if (rmode == 0) return a;
-    if (rmode == 1) return 1.0f - sqrtf(t);
-    if (rmode == 2) return 1.0f - sqrtf(sqrtf(t));
+    if (m == 0) return a;
+    if (m == 1) return 1.0f - sqrtf(t);
+    if (m == 2) return 1.0f - sqrtf(sqrtf(t));
     if (t >= 1.0f) return 0.0f;
     if (t <= 0.0f) return 1.0f;
     return 1.0f - exp2f(ratio * __log2f(t));
@@ -405,16 +412,14 @@ __device__ __forceinline__ float correct_alpha(float a, int rmode, float ratio) 
 __device__ __forceinline__ void shade_factor(const MarchParams &P, const VolDev &v, const float g[3],
                                              const float dir[3], float &sf, float &spec) {
     float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-    if (g2 < v.gmin * v.gmin) {
-        sf = P.ka + P.kd;
-        spec = 0.0f;
-        return;
-    }
+    const bool flat = g2 < v.gmin * v.gmin;
+    // selects instead of a branch; for g2 = 0 the product is NaN and fminf
+    // returns 1, a value the select then discards
     float ndl = fabsf(g[0] * dir[0] + g[1] * dir[1] + g[2] * dir[2]) * rsqrtf(g2);
     ndl = fminf(ndl, 1.0f);
     float n2 = ndl * ndl, n4 = n2 * n2, n8 = n4 * n4;
-    sf = P.ka + P.kd * ndl;
-    spec = P.ks * (n8 * n8);
+    sf = flat ? P.ka + P.kd : P.ka + P.kd * ndl;
+    spec = flat ? 0.0f : P.ks * (n8 * n8);
 }
 
 __device__ __forceinline__ float4 half4_to_float4(uint2 h) {
@@ -437,7 +442,7 @@ __device__ __forceinline__ void load_tf(const TFDev &tf, float4 *s_tf) {
 // F: kShade, kCubic (B-spline instead of trilinear), kTF2 (2-D table from
 // tf.tab2, else the 1-D table s_tf); the gradient is computed when shading or
 // the 2-D table needs it.
-template <int ST, int F>
+template <int ST, int F, int RM = -1>
 __device__ __forceinline__ float4 eval_sample_x(const VolDev &vol, const MarchParams &P, const float4 *s_tf,
                                                 const TFDev &tf, const float dir[3], const Cell &c, int rmode,
                                                 float ratio) {
@@ -458,7 +463,7 @@ __device__ __forceinline__ float4 eval_sample_x(const VolDev &vol, const MarchPa
     } else {
         e = classify(s_tf, tf.K, tf_coord(val, tf.ucoef));
     }
-    float ap = correct_alpha(e.w, rmode, ratio);
+    float ap = correct_alpha<RM>(e.w, rmode, ratio);
     if (SHADE) {
         float sf, spec;
         shade_factor(P, vol, g, dir, sf, spec);

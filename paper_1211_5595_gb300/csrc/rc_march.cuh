@@ -35,7 +35,7 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned de
 // Compositing ray function (Sec. 4.2, Eq. 4): C += T a' c, T *= (1 - a'),
 // front to back from the eye; stop after the sample where 1 - T >= term.
 // F selects the sample form (kShade, kCubic, kTF2).
-template <int ST, int F>
+template <int ST, int F, int RM>
 __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
     extern __shared__ float4 s_tf[];
     if (!(F & kTF2)) {
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
                 continue;
             }
         }
-        float4 e = eval_sample_x<ST, F>(vol, a.p, s_tf, a.tf, R.dir, c, a.p.rmode, a.p.ratio);
+        float4 e = eval_sample_x<ST, F, RM>(vol, a.p, s_tf, a.tf, R.dir, c, a.p.rmode, a.p.ratio);
         composite_add(e, C0, C1, C2, T);
         evald++;
         k++;
@@ -172,14 +172,26 @@ static cudaError_t launch_kernel(K kern, const MarchArgs &a, int nviews, bool ta
     return cudaGetLastError();
 }
 
-// Composite march with sample form F for the volume's storage type.
-template <int F>
-static cudaError_t launch_composite(const MarchArgs &a, int nviews, cudaStream_t s) {
+// Composite march with sample form F and opacity-correction mode RM for the
+// volume's storage type.
+template <int F, int RM>
+static cudaError_t launch_composite_rm(const MarchArgs &a, int nviews, cudaStream_t s) {
     const bool smem = !(F & kTF2);
     switch (a.vol.storage) {
-        case RC_STORE_F32: return launch_kernel(composite_kernel<RC_STORE_F32, F>, a, nviews, smem, s);
-        case RC_STORE_F16: return launch_kernel(composite_kernel<RC_STORE_F16, F>, a, nviews, smem, s);
-        default: return launch_kernel(composite_kernel<RC_STORE_U16, F>, a, nviews, smem, s);
+        case RC_STORE_F32: return launch_kernel(composite_kernel<RC_STORE_F32, F, RM>, a, nviews, smem, s);
+        case RC_STORE_F16: return launch_kernel(composite_kernel<RC_STORE_F16, F, RM>, a, nviews, smem, s);
+        default: return launch_kernel(composite_kernel<RC_STORE_U16, F, RM>, a, nviews, smem, s);
+    }
+}
+
+// The step ratios of the fixed modes (1, 1/2, 1/4) get their own instances.
+template <int F>
+static cudaError_t launch_composite(const MarchArgs &a, int nviews, cudaStream_t s) {
+    switch (a.p.rmode) {
+        case 0: return launch_composite_rm<F, 0>(a, nviews, s);
+        case 1: return launch_composite_rm<F, 1>(a, nviews, s);
+        case 2: return launch_composite_rm<F, 2>(a, nviews, s);
+        default: return launch_composite_rm<F, 3>(a, nviews, s);
     }
 }
 
