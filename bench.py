@@ -639,11 +639,11 @@ def main():
         codes_np = codes_host.numpy().view(np.uint16)
 
         def e2e_step():
+            # host codes in, host images out: the views are rendered in groups
+            # whose device-to-host copies overlap the next group's march
             rc.rc_volume_upload(ctx, vol, codes_np)
             rc.rc_tf_set(ctx, tf)
-            rc.rc_render_views(ctx, vol, P, cam_structs, outs)
-            img_host.copy_(outs, non_blocking=True)
-            stream.synchronize()
+            rc.rc_render_views_host(ctx, vol, P, cam_structs, img_host)
 
         for _ in range(args.warmup):
             e2e_step()

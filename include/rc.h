@@ -216,6 +216,21 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
 rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                           const rc_camera *cams, int nviews, float *out_rgba, rc_stats *stats);
 
+/* rc_render_views with the images delivered to host memory: host_rgba
+ * (nviews*H*W*4 floats, view-major, caller-owned). The views are rendered in
+ * groups of `group` views (0: groups of at least 2 M pixels), alternately on
+ * the context's stream and a second stream of the library, each into its own
+ * device buffer, and each group's images are copied to host_rgba on a third
+ * stream while the next groups render. With
+ * page-locked host_rgba (cudaHostAlloc / cudaHostRegister) the copies overlap
+ * the rendering; pageable memory gives the same images without the overlap.
+ * Each image equals rc_render_views'. Synchronises: the images are in
+ * host_rgba when the call returns RC_OK (on an error its contents are
+ * undefined). stats (optional) sums over the views. The context's own camera
+ * is not changed. */
+rc_status rc_render_views_host(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                               const rc_camera *cams, int nviews, int group, float *host_rgba, rc_stats *stats);
+
 /* Renders nviews cameras of each of nvols volumes in one launch (the
  * compositing function): the volumes must share shape, spacing, vmax and
  * storage (RC_ERR_INVALID_ARG otherwise), and the context's table and the

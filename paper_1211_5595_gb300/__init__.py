@@ -74,6 +74,8 @@ SIGNATURES = {
     "rc_render": (_I, [_P, _P, C.POINTER(rc_render_params), _P, C.POINTER(rc_stats)]),
     "rc_render_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P,
                              C.POINTER(rc_stats)]),
+    "rc_render_views_host": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _I, _P,
+                                  C.POINTER(rc_stats)]),
     "rc_render_backward": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
     "rc_render_backward_noalloc": (_I, [_P, _P, C.POINTER(rc_render_params), _P, _P]),
     "rc_brick_grid_get": (_I, [_P, _P, _P, _P]),
@@ -287,6 +289,18 @@ def rc_render_views(ctx, vol, params, cams, out, stats=False):
     st = rc_stats() if stats else None
     _check(lib().rc_render_views(ctx, vol, C.byref(p), arr, len(cams), _ptr(out),
                                  C.byref(st) if st is not None else None), ctx, "rc_render_views")
+    return _stats_dict(st)
+
+
+def rc_render_views_host(ctx, vol, params, cams, out, group=0, stats=False):
+    """Renders every camera into out, a host float32 tensor n x H x W x 4
+    (page-locked for the copies to overlap the rendering), in groups of
+    `group` views (0: automatic); returns when the images are in out."""
+    p = _params(params)
+    arr = (rc_camera * len(cams))(*[c if isinstance(c, rc_camera) else make_camera(c) for c in cams])
+    st = rc_stats() if stats else None
+    _check(lib().rc_render_views_host(ctx, vol, C.byref(p), arr, len(cams), int(group), _ptr(out),
+                                      C.byref(st) if st is not None else None), ctx, "rc_render_views_host")
     return _stats_dict(st)
 
 

@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/rc.h: validation, object
 // lifetimes, camera records, lazy occupancy rebuilds and kernel dispatch.
+#include <algorithm>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -57,6 +58,14 @@ struct rc_context {
     float *d_partial = nullptr, *d_loss_partial = nullptr;
     int partial_blocks = 0;
     long long adam_step = 0;
+    // host delivery of multi-view renders: a stream for the device-to-host
+    // copies, two image buffers (pixels each) and their events
+    cudaStream_t copy_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;       // renders every other group
+    float4 *d_img[2] = {nullptr, nullptr};
+    size_t img_cap = 0;
+    cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr;
 };
 
 struct rc_volume {
@@ -242,6 +251,16 @@ rc_status rc_context_destroy(rc_context *ctx) {
     cudaFree(ctx->d_range);
     cudaFree(ctx->d_partial);
     cudaFree(ctx->d_loss_partial);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    if (ctx->aux_stream) cudaStreamSynchronize(ctx->aux_stream);
+    for (int b = 0; b < 2; b++) {
+        cudaFree(ctx->d_img[b]);
+        if (ctx->ev_rendered[b]) cudaEventDestroy(ctx->ev_rendered[b]);
+        if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
+    }
+    if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
     delete ctx;
     return RC_OK;
 }
@@ -807,6 +826,89 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
     RC_CUDA(ctx, launch_march(a, nviews, ctx->stream));
     if (stats) return read_stats(ctx, stats, false);
     return RC_OK;
+}
+
+// The copy and second render streams, events and two image buffers of
+// `pixels` each.
+static rc_status ensure_host_path(rc_context *ctx, size_t pixels) {
+    if (!ctx->copy_stream) RC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    if (!ctx->aux_stream) RC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+    if (!ctx->ev_start) RC_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
+    for (int b = 0; b < 2; b++) {
+        if (!ctx->ev_rendered[b]) RC_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_rendered[b], cudaEventDisableTiming));
+        if (!ctx->ev_copied[b]) RC_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming));
+    }
+    if (ctx->img_cap < pixels) {
+        // earlier copies may still read the old buffers
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->aux_stream));
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int b = 0; b < 2; b++) {
+            cudaFree(ctx->d_img[b]);
+            ctx->d_img[b] = nullptr;
+        }
+        ctx->img_cap = 0;
+        for (int b = 0; b < 2; b++) RC_CUDA(ctx, dev_alloc(&ctx->d_img[b], pixels * sizeof(float4)));
+        ctx->img_cap = pixels;
+    }
+    return RC_OK;
+}
+
+constexpr long long kHostGroupPixels = 1ll << 21;
+
+rc_status rc_render_views_host(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const rc_camera *cams,
+                               int nviews, int group, float *host_rgba, rc_stats *stats) {
+    const char *who = "rc_render_views_host";
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
+    rc_status st = check_views(ctx, cams, nviews, who);
+    if (st == RC_OK) st = check_render_views(ctx, vol, p, cams, host_rgba, who);
+    if (st != RC_OK) return st;
+    if (group < 0) return fail(ctx, RC_ERR_INVALID_ARG, "%s: group %d", who, group);
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    if (p->skip && p->func == RC_FUNC_COMPOSITE) {
+        st = ensure_occupancy(ctx, v, p->filter);
+        if (st != RC_OK) return st;
+    }
+    CamRec first;
+    st = upload_views(ctx, v, cams, nviews, &first, who);
+    if (st != RC_OK) return st;
+    const long long px = (long long)cams[0].width * cams[0].height;
+    const int g = group > 0 ? std::min(group, nviews)
+                            : (int)std::min<long long>(nviews, std::max<long long>(1, (kHostGroupPixels + px - 1) / px));
+    st = ensure_host_path(ctx, (size_t)g * px);
+    if (st != RC_OK) return st;
+    MarchArgs a = march_args(ctx, v, p, nullptr);
+    a.cam = first;
+    if (stats) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        a.stats = ctx->d_stats;
+    }
+    // groups alternate between the context's stream and the second render
+    // stream (each with its own image buffer), so a group starts while the
+    // previous one drains; the second stream starts after the work queued so far
+    RC_CUDA(ctx, cudaEventRecord(ctx->ev_start, ctx->stream));
+    RC_CUDA(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_start, 0));
+    const int ngroups = (nviews + g - 1) / g;
+    for (int j = 0; j < ngroups; j++) {
+        const int b = j & 1, v0 = j * g, nv = std::min(g, nviews - v0);
+        cudaStream_t rs = b ? ctx->aux_stream : ctx->stream;
+        // buffer b is free once the copy of group j - 2 is done
+        if (j >= 2) RC_CUDA(ctx, cudaStreamWaitEvent(rs, ctx->ev_copied[b], 0));
+        a.cams = ctx->d_cams + v0;
+        a.out = ctx->d_img[b];
+        RC_CUDA(ctx, launch_march(a, nv, rs));
+        RC_CUDA(ctx, cudaEventRecord(ctx->ev_rendered[b], rs));
+        RC_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_rendered[b], 0));
+        RC_CUDA(ctx, cudaMemcpyAsync(host_rgba + (size_t)v0 * px * 4, ctx->d_img[b], (size_t)nv * px * sizeof(float4),
+                                     cudaMemcpyDeviceToHost, ctx->copy_stream));
+        RC_CUDA(ctx, cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+    }
+    // the context's stream continues after the last copy (copies complete in
+    // order, each after its group's render)
+    RC_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[(ngroups - 1) & 1], 0));
+    if (stats) return read_stats(ctx, stats, false);
+    return check_device_errors(ctx, who);
 }
 
 rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvols, const rc_render_params *p,

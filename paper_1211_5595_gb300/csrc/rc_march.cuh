@@ -12,10 +12,15 @@ namespace rc {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// A CTA renders a tile of kTileW x kTileH pixels, each warp an 8 x 4 block
+// of it.
+constexpr int kWarpsX = 2, kWarpsY = 2;
+constexpr int kTileW = 8 * kWarpsX, kTileH = 4 * kWarpsY, kMarchThreads = 32 * kWarpsX * kWarpsY;
+
 __device__ __forceinline__ void pixel_of_thread(int &x, int &y) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    x = blockIdx.x * kTileW + (warp % kWarpsX) * 8 + (lane & 7);
+    y = blockIdx.y * kTileH + (warp / kWarpsX) * 4 + (lane >> 3);
 }
 
 __device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned dense, unsigned evald,
@@ -36,7 +41,7 @@ __device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned de
 // front to back from the eye; stop after the sample where 1 - T >= term.
 // F selects the sample form (kShade, kCubic, kTF2).
 template <int ST, int F, int RM>
-__global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
+__global__ void __launch_bounds__(kMarchThreads) composite_kernel(const MarchArgs a) {
     extern __shared__ float4 s_tf[];
     if (!(F & kTF2)) {
         load_tf(a.tf, s_tf);
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(128) composite_kernel(const MarchArgs a) {
 // threshold); output channels as documented in rc.h. CUBIC: B-spline values
 // and analytic gradient instead of trilinear values and central differences.
 template <int ST, bool CUBIC>
-__global__ void __launch_bounds__(128) function_kernel(const MarchArgs a) {
+__global__ void __launch_bounds__(kMarchThreads) function_kernel(const MarchArgs a) {
     extern __shared__ float4 s_tf[];
     if (a.p.func == RC_FUNC_THRESHOLD) {   // the only one that classifies (1-D table)
         load_tf(a.tf, s_tf);
@@ -167,8 +172,8 @@ static cudaError_t launch_kernel(K kern, const MarchArgs &a, int nviews, bool ta
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((a.cam.W + 15) / 16, (a.cam.H + 7) / 8, nviews);
-    kern<<<grid, 128, smem, s>>>(a);
+    dim3 grid((a.cam.W + kTileW - 1) / kTileW, (a.cam.H + kTileH - 1) / kTileH, nviews);
+    kern<<<grid, kMarchThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

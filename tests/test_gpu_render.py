@@ -246,6 +246,36 @@ def test_render_views_equals_single_renders(rc, c1):
     assert ei.value.status == rc.RC_ERR_INVALID_ARG
 
 
+def test_render_views_host_equals_device_render(rc, c1):
+    """Host delivery: groups rendered into two device buffers in turn and
+    copied on a second stream give the device render's images bit for bit,
+    for page-locked and pageable host memory, one group, one view per group
+    and a ragged last group; the statistics equal the one-launch render's."""
+    import torch
+    ph, tf, w, r = c1
+    cams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=96, height=72)
+            for az in (0.0, 33.0, 120.0, 200.0, 310.0)]
+    P = dict(step_vox=0.5, term=0.99, shade=True, skip=True)
+    dev = torch.empty((5, 72, 96, 4), device="cuda")
+    st = rc.rc_render_views(r.ctx, r.vol, P, cams, dev, stats=True)
+    ref = dev.cpu()
+    for pinned in (True, False):
+        for group in (0, 1, 3, 7):
+            host = torch.full((5, 72, 96, 4), -1.0)
+            if pinned:
+                host = host.pin_memory()
+            sh = rc.rc_render_views_host(r.ctx, r.vol, P, cams, host, group=group, stats=group == 3)
+            assert torch.equal(host, ref), (pinned, group)
+            if group == 3:
+                assert sh == st
+    # the device render is unchanged after the host path used the context
+    rc.rc_render_views(r.ctx, r.vol, P, cams, dev)
+    assert torch.equal(dev.cpu(), ref)
+    with pytest.raises(rc.RCError) as ei:
+        rc.rc_render_views_host(r.ctx, r.vol, P, cams, torch.empty((5, 72, 96, 4)), group=-1)
+    assert ei.value.status == rc.RC_ERR_INVALID_ARG
+
+
 def test_render_batch_equals_views(rc):
     """Several volumes x several views in one launch: every image equals the
     multi-view render of its volume; mismatched volumes are refused."""
