@@ -544,6 +544,9 @@ def main():
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal form")
     ap.add_argument("--no-precision", action="store_true", help="skip the 512x512x256 precision form")
     ap.add_argument("--proposal-phantoms", type=int, default=8, help="training phantoms of the proposal form")
+    ap.add_argument("--case", choices=["adjoint", "network"], default=None,
+                    help="run only the table-gradient form or the network throughput (forward and training "
+                         "gradient, seeded initial network) and print its JSON (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -574,6 +577,18 @@ def main():
     H, W = w["height"], w["width"]
     stream = torch.cuda.current_stream()
     ctx = rc.rc_context_create(local, stream.cuda_stream)
+    if args.case:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda", dtype=torch.float32)
+        if args.case == "adjoint":
+            out = adjoint_form(rc, ctx, flush, stream)
+        else:
+            rc.rc_proposal_load(ctx, rc.pack_proposal_blob(synth.proposal_init_params(61)))
+            out = network_throughput(rc, ctx, stream)
+        torch.cuda.synchronize()
+        rc.rc_context_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"case": args.case, **out}))
+        return 0
     vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, rc.RC_STORE_F32)
     codes_host = torch.from_numpy(ph.vol.view(np.int16).reshape(-1)).pin_memory()
     codes_dev = codes_host.to("cuda", non_blocking=True)

@@ -60,7 +60,20 @@ __device__ __forceinline__ void group_sum8(unsigned peers, float (&v)[8]) {
     }
 }
 
-template <int ST, bool SHADE>
+// d a' / d a = r (1 - a)^(r - 1) for the step ratio r of mode RM, with
+// x = 1 - a >= 1e-6: r = 1/2 and 1/4 as reciprocal square roots, else
+// through log2 / exp2.
+template <int RM>
+__device__ __forceinline__ float dalpha_factor(float x, float ratio) {
+    if (RM == 1) return 0.5f * rsqrtf(x);
+    if (RM == 2) {
+        const float q = rsqrtf(x);
+        return 0.25f * q * sqrtf(q);
+    }
+    return ratio * exp2f((ratio - 1.0f) * __log2f(x));
+}
+
+template <int ST, bool SHADE, int RM>
 __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const float *absmax) {
     const MarchArgs &a = A.m;
     const int K = a.tf.K;
@@ -99,7 +112,8 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
                 k = jump_block(R, a.vol, c, k, s);
                 continue;
             }
-            float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, K, a.tf.ucoef, R.dir, c, a.p.rmode, a.p.ratio);
+            float4 e = eval_sample_x<ST, SHADE ? kShade : 0, RM>(a.vol, a.p, s_tf, a.tf, R.dir, c, a.p.rmode,
+                                                               a.p.ratio);
             composite_add(e, Cf0, Cf1, Cf2, Tf);
             k++;
             if ((1.0f - Tf) >= a.p.term) break;
@@ -124,7 +138,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
             else val = trilinear<ST>(a.vol, c);
             float w;
             float4 e = classify(s_tf, K, tf_coord(val, a.tf.ucoef), &i, &w);
-            float ap = correct_alpha(e.w, a.p.rmode, a.p.ratio);
+            float ap = correct_alpha<RM>(e.w, a.p.rmode, a.p.ratio);
             float r = e.x, gg = e.y, b = e.z;
             float d0 = 1.0f, d1 = 1.0f, d2 = 1.0f;
             if (SHADE) {
@@ -149,9 +163,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
             float dap = g.x * (Tk * r - (Cf0 - C0) * inv) + g.y * (Tk * gg - (Cf1 - C1) * inv) +
                         g.z * (Tk * b - (Cf2 - C2) * inv) + g.w * (Tk - (T - Tf) * inv);
             float ac = fminf(e.w, 1.0f - 1e-6f);
-            float dal;
-            if (a.p.rmode == 0) dal = dap;
-            else dal = dap * a.p.ratio * powf(1.0f - ac, a.p.ratio - 1.0f);
+            const float dal = RM == 0 ? dap : dap * dalpha_factor<RM>(1.0f - ac, a.p.ratio);
             float dr = g.x * ta * d0, dg = g.y * ta * d1, db = g.z * ta * d2;
             const float w0 = 1.0f - w;
             v[0] = w0 * dr; v[1] = w0 * dg; v[2] = w0 * db; v[3] = w0 * dal;
@@ -191,6 +203,19 @@ static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, int nviews, const
     return cudaGetLastError();
 }
 
+// The instance for the volume's storage, shading and opacity-correction mode RM.
+template <int RM>
+static cudaError_t launch_adj_rm(const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
+    switch (a.m.vol.storage * 2 + (a.m.p.shade ? 1 : 0)) {
+        case RC_STORE_F32 * 2: return launch_adj(adjoint_kernel<RC_STORE_F32, false, RM>, a, nviews, absmax, s);
+        case RC_STORE_F32 * 2 + 1: return launch_adj(adjoint_kernel<RC_STORE_F32, true, RM>, a, nviews, absmax, s);
+        case RC_STORE_F16 * 2: return launch_adj(adjoint_kernel<RC_STORE_F16, false, RM>, a, nviews, absmax, s);
+        case RC_STORE_F16 * 2 + 1: return launch_adj(adjoint_kernel<RC_STORE_F16, true, RM>, a, nviews, absmax, s);
+        case RC_STORE_U16 * 2: return launch_adj(adjoint_kernel<RC_STORE_U16, false, RM>, a, nviews, absmax, s);
+        default: return launch_adj(adjoint_kernel<RC_STORE_U16, true, RM>, a, nviews, absmax, s);
+    }
+}
+
 // acc must hold 4K long longs followed by one float (the |dL/dI| maximum).
 // With a.m.cams, nviews views (grid.z), dimg view-major; the gradient is the
 // sum over the views.
@@ -202,13 +227,11 @@ cudaError_t launch_adjoint(const AdjointArgs &a, int nviews, float *dL_dtf, cuda
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * K, s);
     if (e != cudaSuccess) return e;
-    switch (a.m.vol.storage * 2 + (a.m.p.shade ? 1 : 0)) {
-        case RC_STORE_F32 * 2: e = launch_adj(adjoint_kernel<RC_STORE_F32, false>, a, nviews, absmax, s); break;
-        case RC_STORE_F32 * 2 + 1: e = launch_adj(adjoint_kernel<RC_STORE_F32, true>, a, nviews, absmax, s); break;
-        case RC_STORE_F16 * 2: e = launch_adj(adjoint_kernel<RC_STORE_F16, false>, a, nviews, absmax, s); break;
-        case RC_STORE_F16 * 2 + 1: e = launch_adj(adjoint_kernel<RC_STORE_F16, true>, a, nviews, absmax, s); break;
-        case RC_STORE_U16 * 2: e = launch_adj(adjoint_kernel<RC_STORE_U16, false>, a, nviews, absmax, s); break;
-        default: e = launch_adj(adjoint_kernel<RC_STORE_U16, true>, a, nviews, absmax, s);
+    switch (a.m.p.rmode) {
+        case 0: e = launch_adj_rm<0>(a, nviews, absmax, s); break;
+        case 1: e = launch_adj_rm<1>(a, nviews, absmax, s); break;
+        case 2: e = launch_adj_rm<2>(a, nviews, absmax, s); break;
+        default: e = launch_adj_rm<3>(a, nviews, absmax, s);
     }
     if (e != cudaSuccess) return e;
     finalize_kernel<<<(4 * K + 255) / 256, 256, 0, s>>>(a.acc, 4 * K, absmax, dL_dtf);
