@@ -856,6 +856,35 @@ static rc_status ensure_host_path(rc_context *ctx, size_t pixels) {
 
 constexpr long long kHostGroupPixels = 1ll << 21;
 
+// Groups of g views alternate between the context's stream and the second
+// render stream (each with its own image buffer), so a group starts while the
+// previous one drains; each group is copied to the host on the copy stream.
+// The context's stream continues after the last copy.
+static rc_status render_groups_to_host(rc_context *ctx, MarchArgs a, int nviews, int g, long long px,
+                                       float *host_rgba) {
+    // the second stream starts after the work queued so far
+    RC_CUDA(ctx, cudaEventRecord(ctx->ev_start, ctx->stream));
+    RC_CUDA(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_start, 0));
+    const int ngroups = (nviews + g - 1) / g;
+    for (int j = 0; j < ngroups; j++) {
+        const int b = j & 1, v0 = j * g, nv = std::min(g, nviews - v0);
+        cudaStream_t rs = b ? ctx->aux_stream : ctx->stream;
+        // buffer b is free once the copy of group j - 2 is done
+        if (j >= 2) RC_CUDA(ctx, cudaStreamWaitEvent(rs, ctx->ev_copied[b], 0));
+        a.cams = ctx->d_cams + v0;
+        a.out = ctx->d_img[b];
+        RC_CUDA(ctx, launch_march(a, nv, rs));
+        RC_CUDA(ctx, cudaEventRecord(ctx->ev_rendered[b], rs));
+        RC_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_rendered[b], 0));
+        RC_CUDA(ctx, cudaMemcpyAsync(host_rgba + (size_t)v0 * px * 4, ctx->d_img[b], (size_t)nv * px * sizeof(float4),
+                                     cudaMemcpyDeviceToHost, ctx->copy_stream));
+        RC_CUDA(ctx, cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+    }
+    // copies complete in order, each after its group's render
+    RC_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[(ngroups - 1) & 1], 0));
+    return RC_OK;
+}
+
 rc_status rc_render_views_host(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const rc_camera *cams,
                                int nviews, int group, float *host_rgba, rc_stats *stats) {
     const char *who = "rc_render_views_host";
@@ -884,29 +913,14 @@ rc_status rc_render_views_host(rc_context *ctx, const rc_volume *vol, const rc_r
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
         a.stats = ctx->d_stats;
     }
-    // groups alternate between the context's stream and the second render
-    // stream (each with its own image buffer), so a group starts while the
-    // previous one drains; the second stream starts after the work queued so far
-    RC_CUDA(ctx, cudaEventRecord(ctx->ev_start, ctx->stream));
-    RC_CUDA(ctx, cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_start, 0));
-    const int ngroups = (nviews + g - 1) / g;
-    for (int j = 0; j < ngroups; j++) {
-        const int b = j & 1, v0 = j * g, nv = std::min(g, nviews - v0);
-        cudaStream_t rs = b ? ctx->aux_stream : ctx->stream;
-        // buffer b is free once the copy of group j - 2 is done
-        if (j >= 2) RC_CUDA(ctx, cudaStreamWaitEvent(rs, ctx->ev_copied[b], 0));
-        a.cams = ctx->d_cams + v0;
-        a.out = ctx->d_img[b];
-        RC_CUDA(ctx, launch_march(a, nv, rs));
-        RC_CUDA(ctx, cudaEventRecord(ctx->ev_rendered[b], rs));
-        RC_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_rendered[b], 0));
-        RC_CUDA(ctx, cudaMemcpyAsync(host_rgba + (size_t)v0 * px * 4, ctx->d_img[b], (size_t)nv * px * sizeof(float4),
-                                     cudaMemcpyDeviceToHost, ctx->copy_stream));
-        RC_CUDA(ctx, cudaEventRecord(ctx->ev_copied[b], ctx->copy_stream));
+    st = render_groups_to_host(ctx, a, nviews, g, px, host_rgba);
+    if (st != RC_OK) {
+        // no copy into the caller's memory may outlive the call
+        cudaStreamSynchronize(ctx->stream);
+        cudaStreamSynchronize(ctx->aux_stream);
+        cudaStreamSynchronize(ctx->copy_stream);
+        return st;
     }
-    // the context's stream continues after the last copy (copies complete in
-    // order, each after its group's render)
-    RC_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[(ngroups - 1) & 1], 0));
     if (stats) return read_stats(ctx, stats, false);
     return check_device_errors(ctx, who);
 }
