@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -51,15 +52,23 @@ def peaks():
 
 
 # the files composite_kernel<F32, shaded> is compiled from
-MARCH_SOURCES = ("include/rc.h", "paper_1211_5595_gb300/csrc/rc_internal.h",
-                 "paper_1211_5595_gb300/csrc/rc_device.cuh", "paper_1211_5595_gb300/csrc/rc_march.cuh",
-                 "paper_1211_5595_gb300/csrc/rc_march.cu")
+# the files compiled into the march kernel (the public header only declares
+# the C API around it; its constants reach the kernel through rc_internal.h)
+MARCH_SOURCES = ("paper_1211_5595_gb300/csrc/rc_internal.h", "paper_1211_5595_gb300/csrc/rc_device.cuh",
+                 "paper_1211_5595_gb300/csrc/rc_march.cuh", "paper_1211_5595_gb300/csrc/rc_march.cu")
+
+
+def strip_comments(src):
+    """C/C++ source without comments and blank lines (string literals kept)."""
+    src = re.sub(r"//[^\n]*|/\*.*?\*/", "", src, flags=re.S)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
 
 
 def kernel_sources_hash():
+    """Hash of the march kernel's code: comment edits do not change it."""
     h = hashlib.sha256()
     for f in MARCH_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(strip_comments(open(os.path.join(ROOT, f)).read()).encode())
     return h.hexdigest()[:16]
 
 
