@@ -48,15 +48,20 @@ __device__ __forceinline__ void group_sum8(unsigned peers, float (&v)[8]) {
     const int lane = threadIdx.x & 31;
     const int cnt = __popc(peers);
     const int rank = __popc(peers & ((1u << lane) - 1u));
+    // the lane of rank + s, by pointer jumping: first the next member above
+    // this lane (or this lane itself when there is none)
+    const unsigned above = peers & ~((2u << lane) - 1u);
+    int nxt = above ? __ffs(above) - 1 : lane;
 #pragma unroll 1
     for (int s = 1; __any_sync(0xffffffffu, s < cnt); s <<= 1) {
         const bool take = (rank % (2 * s)) == 0 && rank + s < cnt;
-        const int src = take ? (int)__fns(peers, 0, rank + s + 1) : lane;
+        const int src = take ? nxt : lane;
 #pragma unroll
         for (int c = 0; c < 8; c++) {
             const float o = __shfl_sync(0xffffffffu, v[c], src);
             if (take) v[c] += o;
         }
+        nxt = __shfl_sync(0xffffffffu, nxt, nxt);          // rank + 2s
     }
 }
 
