@@ -276,6 +276,41 @@ def test_render_views_host_equals_device_render(rc, c1):
     assert ei.value.status == rc.RC_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("form", ["bspline", "mip", "tf2d"])
+def test_render_views_host_other_forms(rc, form):
+    """Host delivery with the other marches (B-spline filter, a non-composite
+    ray function, the 2-D table): images equal the device render's."""
+    import torch
+    ctx = rc.rc_context_create(0)
+    vol = None
+    try:
+        dims, sp = (60, 52, 40), (1.0, 1.0, 1.5)
+        ph = synth.head_phantom(dims, sp, seed=41, tumor_radius_vox=4)
+        vol = rc.rc_volume_create(ctx, dims, sp, 4095, rc.RC_STORE_F32)
+        rc.rc_volume_upload(ctx, vol, ph.vol)
+        P = dict(step_vox=0.5, term=0.99, shade=True, skip=True)
+        if form == "tf2d":
+            rc.rc_tf2d_set(ctx, synth.tf2d_table(256, 16, 1200.0), 1200.0)
+        else:
+            rc.rc_tf_set(ctx, synth.tf_table(256))
+        if form == "bspline":
+            P["filter"] = rc.RC_FILTER_BSPLINE
+        if form == "mip":
+            P["func"] = rc.RC_FUNC_MIP
+        cams = [synth.orbit_camera(dims, sp, az, width=40, height=36) for az in (5.0, 95.0, 185.0)]
+        dev = torch.empty((3, 36, 40, 4), device="cuda")
+        rc.rc_render_views(ctx, vol, P, cams, dev)
+        host = torch.full((3, 36, 40, 4), -1.0).pin_memory()
+        rc.rc_render_views_host(ctx, vol, P, cams, host, group=2)
+        assert torch.equal(host, dev.cpu())
+        assert float(host[..., 3].max()) > 0.0
+    finally:
+        torch.cuda.synchronize()
+        if vol is not None:
+            rc.rc_volume_destroy(ctx, vol)
+        rc.rc_context_destroy(ctx)
+
+
 def test_render_batch_equals_views(rc):
     """Several volumes x several views in one launch: every image equals the
     multi-view render of its volume; mismatched volumes are refused."""
