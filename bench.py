@@ -74,8 +74,8 @@ def kernel_sources_hash():
 
 def profiled_counters():
     """Per-launch counters of the march from the committed ncu summary
-    (DRAM bytes, L2-to-L1 bytes, warp instructions), if it was captured on
-    the current kernel sources (else an empty dict)."""
+    (DRAM bytes, L2-to-L1 bytes, warp instructions, L1 data-pipe use), if it
+    was captured on the current kernel sources (else an empty dict)."""
     path = os.path.join(ROOT, "profiles", "march_shaded_256x256x180.md")
     try:
         kv = {}
@@ -86,7 +86,7 @@ def profiled_counters():
         if kv.get("sources_sha256_16") != kernel_sources_hash():
             return {}
         return {k: float(kv[k]) for k in ("dram_bytes_per_launch", "l2_to_l1_bytes_per_launch",
-                                          "warp_instructions_per_launch") if k in kv}
+                                          "warp_instructions_per_launch", "l1_data_pipe_pct") if k in kv}
     except Exception:
         return {}
 
@@ -731,7 +731,10 @@ def main():
     clk = clocks.summary()
     sm_mhz = clk.get("sm_mhz") or 2070.0
     issue_peak = torch.cuda.get_device_properties(local).multi_processor_count * 4 * sm_mhz * 1e6
-    l2 = issue = None
+    l2 = issue = l1 = None
+    if "l1_data_pipe_pct" in counters:
+        l1 = {"data_pipe_frac": counters["l1_data_pipe_pct"] / 100.0,
+              "source": "ncu LSU data-pipe wavefronts of the same kernel (profiles/march_shaded_256x256x180.md)"}
     if "l2_to_l1_bytes_per_launch" in counters:
         a = counters["l2_to_l1_bytes_per_launch"] / launch_avg_s / 1e9
         l2 = {"achieved_gbs": a, "peak_gbs": l2_peak, "frac": a / l2_peak,
@@ -746,7 +749,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded head phantom, Rician noise)",
         "config": {"workload": WORKLOAD, "volume": "256x256x180 u16 -> FP32 19^3 apron bricks + 17^3 value+gradient bricks", "image": "1024x1024",
                    "views": nviews, "step_vox": w["step"], "shading": "Blinn-Phong headlight",
-                   "skip": "16^3 min/max brick grid", "term": w["term"],
+                   "skip": "16^3 min/max brick grid + 4^3 sub-block mask (exact)", "term": w["term"],
                    "l2": "flushed between steps (256 MB write, outside the step events)",
                    "ms_per_frame_median": statistics.median(frame_ms),
                    "dense_samples_per_step": dense, "evaluated_samples_per_step": evald},
@@ -755,8 +758,9 @@ def main():
                      "kernel": "composite_kernel<F32, shaded>, one launch per step for all views",
                      "model": f"{BYTES_PER_SAMPLE} B per evaluated sample (32 distinct FP32 voxels = 8 value+gradient float4) / mean launch time",
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "note": "the gather bytes are served by L1 (95% of sectors); see l2 and issue",
-                     "l2": l2, "issue": issue},
+                     "note": "the gather bytes are served by L1 (95% of sectors): the L1 data path (l1) "
+                             "and instruction issue (issue) are the limits, not HBM or L2",
+                     "l1": l1, "l2": l2, "issue": issue},
         "e2e": e2e,
         "forms": forms,
         # per step: re-layout, value+gradient bricks, 16^3 and 4^3 min/max grids,
