@@ -152,6 +152,32 @@ def test_tiny_volume_and_single_pixel(rc, orc):
         r.close()
 
 
+def test_eye_inside_and_axis_aligned_rays(rc, orc):
+    """The eye at the volume centre (t_near clamps to 0, the first sample is
+    inside the box) and cameras whose middle pixel's ray is parallel to an
+    axis (zero direction components in the slab test), shaded and unshaded."""
+    ph = synth.head_phantom((40, 36, 28), (1.0, 1.2, 1.5), seed=23, tumor_radius_vox=4)
+    tf = synth.tf_table(256)
+    E = (np.array(ph.dims) - 1) * np.array(ph.spacing)
+    c = [float(np.float32(v / 2)) for v in E]
+    cams = [dict(eye=tuple(c), target=(c[0] + 10.0, c[1], c[2]), up=(0.0, 0.0, 1.0), fovy_deg=60.0,
+                 width=33, height=17),
+            dict(eye=(c[0], c[1], c[2] + 100.0), target=tuple(c), up=(0.0, 1.0, 0.0), fovy_deg=30.0,
+                 width=31, height=25)]
+    r = GPURenderer(rc, ph.vol, ph.spacing)
+    try:
+        r.set_tf(tf)
+        for cam in cams:
+            for shade in (False, True):
+                img = r.render(cam, step_vox=0.5, term=0.99, shade=shade, skip=True)
+                o = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cam, step=0.5, term=0.99, shade=shade))
+                compare(img, o, TOL_FP32)
+                assert np.array_equal(img, r.render(cam, step_vox=0.5, term=0.99, shade=shade, skip=False))
+                assert img[..., 3].max() > 0.5
+    finally:
+        r.close()
+
+
 def test_empty_transfer_function_renders_black(c1):
     ph, tf, w, r = c1
     try:
