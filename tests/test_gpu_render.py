@@ -178,6 +178,33 @@ def test_eye_inside_and_axis_aligned_rays(rc, orc):
         r.close()
 
 
+@pytest.mark.parametrize("K", [2, 4096])
+def test_table_size_limits(rc, orc, K):
+    """The smallest table (2 entries: one linear ramp over the code range) and
+    the largest (4096 entries, 64 KB of shared memory per block, above the
+    default 48 KB): images against the oracle, skip on = off, occupancy
+    bit-exact."""
+    ph = synth.head_phantom((48, 44, 30), (1.0, 1.0, 1.5), seed=29, tumor_radius_vox=4)
+    if K == 2:
+        tf = np.array([[0.0, 0.0, 0.0, 0.0], [1.0, 0.7, 0.4, 0.05]], np.float32)
+    else:
+        tf = synth.tf_table(K)
+    r = GPURenderer(rc, ph.vol, ph.spacing)
+    try:
+        r.set_tf(tf)
+        cam = synth.orbit_camera(ph.dims, ph.spacing, 40.0, width=57, height=43)
+        for shade in (False, True):
+            img = r.render(cam, step_vox=0.5, term=0.99, shade=shade, skip=True)
+            o = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cam, step=0.5, term=0.99, shade=shade))
+            compare(img, o, TOL_FP32)
+            assert np.array_equal(img, r.render(cam, step_vox=0.5, term=0.99, shade=shade, skip=False))
+            assert img[..., 3].max() > 0.3
+        omn, omx = orc.brick_minmax(ph.vol)
+        assert np.array_equal(r.occupancy(), orc.occupancy(ph.dims, tf, omn, omx))
+    finally:
+        r.close()
+
+
 def test_empty_transfer_function_renders_black(c1):
     ph, tf, w, r = c1
     try:
