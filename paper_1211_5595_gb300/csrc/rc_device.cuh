@@ -266,7 +266,8 @@ __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, floa
 // and their derivatives -(1-t)^2/2, 3t^2/2 - 2t, -3t^2/2 + t + 1/2, t^2/2.
 // The apron brick holds exactly this footprint (its replicated border voxels
 // are the clamped indices), so the 64 voxels are one base address plus
-// constant offsets.
+// constant offsets; with FP32 storage they come from the pair bricks, two
+// 8-byte loads per row.
 __device__ __forceinline__ void bspline_weights(float t, float w[4]) {
     const float s = 1.0f - t, t2 = t * t;
     w[0] = s * s * s * (1.0f / 6.0f);
@@ -284,9 +285,38 @@ __device__ __forceinline__ void bspline_dweights(float t, float d[4]) {
 }
 
 
-template <int ST>
-__device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
+// Entry of the B-spline pair bricks holding voxels (i-1, i) of the cell's
+// first footprint row (FP32 storage with the pairs built).
+__device__ __forceinline__ const float2 *bspline_pairs(const VolDev &v, const Cell &c) {
+    return v.bsp + ((unsigned)brick_of(v, c) * (unsigned)kBspVox +
+                    (unsigned)((((c.i[2] & 15) * kApron + (c.i[1] & 15)) * kBspRow) + (c.i[0] & 15)));
+}
+
+// The four voxels x = i-1 .. i+2 of footprint row (oy, oz): PAIRS, two pair
+// loads; else four scalar loads from the apron brick.
+template <int ST, bool PAIRS>
+__device__ __forceinline__ void bspline_row(const typename Voxel<ST>::T *a, const float2 *pb, int oz, int oy,
+                                            float &v0, float &v1, float &v2, float &v3) {
+    if (PAIRS) {
+        const float2 *q = pb + (oz * kApron + oy) * kBspRow;
+        const float2 p0 = __ldg(q), p1 = __ldg(q + 2);
+        v0 = p0.x;
+        v1 = p0.y;
+        v2 = p1.x;
+        v3 = p1.y;
+    } else {
+        const auto *r = a + (oz * (int)kDZ + oy * (int)kDY);
+        v0 = ldv<ST>(r);
+        v1 = ldv<ST>(r + 1);
+        v2 = ldv<ST>(r + 2);
+        v3 = ldv<ST>(r + 3);
+    }
+}
+
+template <int ST, bool PAIRS>
+__device__ __forceinline__ float bspline_x(const VolDev &v, const Cell &c) {
     const auto *a = cell_ptr<ST>(v, c) - (int)(kDX + kDY + kDZ);     // voxel (i-1, j-1, k-1)
+    const float2 *pb = PAIRS ? bspline_pairs(v, c) : nullptr;
     float wx[4], wy[4], wz[4];
     bspline_weights(c.w[0], wx);
     bspline_weights(c.w[1], wy);
@@ -297,11 +327,12 @@ __device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
         float fz = 0.0f;
 #pragma unroll
         for (int oy = 0; oy < 4; oy++) {
-            const auto *r = a + (oz * (int)kDZ + oy * (int)kDY);
-            float fx = ldv<ST>(r) * wx[0];
-            fx = __fmaf_rn(ldv<ST>(r + 1), wx[1], fx);
-            fx = __fmaf_rn(ldv<ST>(r + 2), wx[2], fx);
-            fx = __fmaf_rn(ldv<ST>(r + 3), wx[3], fx);
+            float v0, v1, v2, v3;
+            bspline_row<ST, PAIRS>(a, pb, oz, oy, v0, v1, v2, v3);
+            float fx = v0 * wx[0];
+            fx = __fmaf_rn(v1, wx[1], fx);
+            fx = __fmaf_rn(v2, wx[2], fx);
+            fx = __fmaf_rn(v3, wx[3], fx);
             fz = __fmaf_rn(fx, wy[oy], fz);
         }
         f = __fmaf_rn(fz, wz[oz], f);
@@ -312,9 +343,10 @@ __device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
 // Value and analytic world-space gradient (value units per mm) of the
 // B-spline field: d/dx sums the same voxels with the x weights replaced by
 // their derivatives; 1/s = 2 * (0.5/s) exactly.
-template <int ST>
-__device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, float g[3]) {
+template <int ST, bool PAIRS>
+__device__ __forceinline__ float bspline_grad_x(const VolDev &v, const Cell &c, float g[3]) {
     const auto *a = cell_ptr<ST>(v, c) - (int)(kDX + kDY + kDZ);     // voxel (i-1, j-1, k-1)
+    const float2 *pb = PAIRS ? bspline_pairs(v, c) : nullptr;
     float wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
     bspline_weights(c.w[0], wx);
     bspline_weights(c.w[1], wy);
@@ -328,8 +360,8 @@ __device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, fl
         float fz = 0.0f, gxz = 0.0f, gyz = 0.0f;
 #pragma unroll
         for (int oy = 0; oy < 4; oy++) {
-            const auto *r = a + (oz * (int)kDZ + oy * (int)kDY);
-            const float v0 = ldv<ST>(r), v1 = ldv<ST>(r + 1), v2 = ldv<ST>(r + 2), v3 = ldv<ST>(r + 3);
+            float v0, v1, v2, v3;
+            bspline_row<ST, PAIRS>(a, pb, oz, oy, v0, v1, v2, v3);
             float fx = v0 * wx[0], ex = v0 * dx[0];
             fx = __fmaf_rn(v1, wx[1], fx);
             ex = __fmaf_rn(v1, dx[1], ex);
@@ -350,6 +382,21 @@ __device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, fl
     g[1] = gy * (2.0f * v.inv2s[1]);
     g[2] = gz * (2.0f * v.inv2s[2]);
     return f;
+}
+
+// The B-spline value (and gradient) with the footprint from the pair bricks
+// when the volume has them (one uniform branch per sample), else from the
+// apron brick.
+template <int ST>
+__device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
+    if (ST == RC_STORE_F32 && v.bsp != nullptr) return bspline_x<ST, true>(v, c);
+    return bspline_x<ST, false>(v, c);
+}
+
+template <int ST>
+__device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, float g[3]) {
+    if (ST == RC_STORE_F32 && v.bsp != nullptr) return bspline_grad_x<ST, true>(v, c, g);
+    return bspline_grad_x<ST, false>(v, c, g);
 }
 
 // Table coordinate u = fl(v * fl((K-1) / vscale)): one rounded FP32 multiply,

@@ -91,6 +91,33 @@ def test_tf2d_occupancy_bit_exact(rc, orc, storage, fp16):
 # --------------------------------------------------------------------------
 # images
 # --------------------------------------------------------------------------
+def test_bspline_after_new_data(rc, orc):
+    """FP32 volumes read the B-spline footprint from pair bricks built on the
+    first B-spline render; new data must rebuild them (against the oracle
+    before and after the re-upload, F16 storage from the apron bricks alike)."""
+    dims, sp = (50, 46, 34), (1.0, 1.1, 1.4)
+    tf = synth.tf_table(256)
+    cam = synth.orbit_camera(dims, sp, 61.0, width=45, height=39)
+    P = dict(step_vox=0.5, term=0.99, shade=True, filter=rc.RC_FILTER_BSPLINE)
+    for storage in (rc.RC_STORE_F32, rc.RC_STORE_F16):
+        a = synth.head_phantom(dims, sp, seed=51, tumor_radius_vox=4)
+        b = synth.head_phantom(dims, sp, seed=52, tumor_radius_vox=7)
+        r = GPURenderer(rc, a.vol, sp, storage=storage)
+        try:
+            r.set_tf(tf)
+            vm = int(storage == rc.RC_STORE_F16)
+            for ph in (a, b):
+                if ph is b:
+                    rc.rc_volume_upload(r.ctx, r.vol, b.vol)
+                img = r.render(cam, skip=True, **P)
+                o = orc.render(orc.Scene(ph.vol, sp, tf, cam, step=0.5, term=0.99, shade=True,
+                                         filter=orc.BSPLINE, value_mode=vm))
+                compare(img, o, TOL_FP32)
+                assert np.array_equal(img, r.render(cam, skip=False, **P))
+        finally:
+            r.close()
+
+
 @pytest.mark.parametrize("shade", [False, True])
 def test_bspline_parity(rc, orc, small, shade):
     ph, r = small
