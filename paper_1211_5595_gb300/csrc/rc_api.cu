@@ -78,8 +78,8 @@ struct rc_volume {
     int nbricks = 0;             // cell-bricks
     void *d_data = nullptr;
     float4 *d_vg = nullptr;      // F32 storage: value+gradient bricks
-    float2 *d_bsp = nullptr;     // F32 storage: B-spline pair bricks, built on the first B-spline render
-    uint64_t bsp_data_version = ~0ull;
+    void *d_pairs = nullptr;     // pair bricks (storage type), built on the first render that reads them
+    uint64_t pairs_data_version = ~0ull;
     uint16_t *d_stage = nullptr;
     // min/max grid and occupancy mask per reconstruction filter (index rc_filter)
     uint16_t *d_mn[2] = {nullptr, nullptr}, *d_mx[2] = {nullptr, nullptr};
@@ -273,7 +273,7 @@ rc_status rc_context_destroy(rc_context *ctx) {
 static void volume_free(rc_volume *v) {
     cudaFree(v->d_data);
     cudaFree(v->d_vg);
-    cudaFree(v->d_bsp);
+    cudaFree(v->d_pairs);
     cudaFree(v->d_stage);
     for (int f = 0; f < 2; f++) {
         cudaFree(v->d_mn[f]);
@@ -346,7 +346,7 @@ static VolDev vol_dev(const rc_volume *v) {
     VolDev d;
     d.data = v->d_data;
     d.vg = v->d_vg;
-    d.bsp = v->bsp_data_version == v->data_version ? v->d_bsp : nullptr;
+    d.pairs = v->pairs_data_version == v->data_version ? v->d_pairs : nullptr;
     d.storage = (int)v->storage;
     float smin = fminf(fminf(v->s[0], v->s[1]), v->s[2]);
     for (int a = 0; a < 3; a++) {
@@ -722,14 +722,21 @@ static rc_status ensure_grid(rc_context *ctx, rc_volume *v, int f) {
     return RC_OK;
 }
 
-// The B-spline pair bricks of an FP32 volume (allocated on first use,
-// rebuilt after new data); other storage reads the apron bricks.
-static rc_status prepare_filter(rc_context *ctx, rc_volume *v, int filter) {
-    if (filter != RC_FILTER_BSPLINE || v->storage != RC_STORE_F32 || v->bsp_data_version == v->data_version)
-        return RC_OK;
-    if (!v->d_bsp) RC_CUDA(ctx, dev_alloc(&v->d_bsp, (size_t)v->nbricks * kBspVox * sizeof(float2)));
-    RC_CUDA(ctx, launch_bsppair(v->d_stage, vol_dev(v), v->d_bsp, ctx->stream));
-    v->bsp_data_version = v->data_version;
+// The pair bricks of FP32 and FP16 volumes, allocated on the first render
+// that reads them and rebuilt after new data: B-spline renders, and
+// trilinear renders of FP16 volumes that need the gradient footprint
+// (shading, a 2-D table, the isosurface's shading). FP32 trilinear renders
+// read the value+gradient bricks; uint16 volumes read the apron bricks
+// (widening 16-bit integer pairs cost more than the loads they save).
+static rc_status prepare_filter(rc_context *ctx, rc_volume *v, const rc_render_params *p) {
+    const bool grad = p->shade || ctx->M >= 2 || p->func == RC_FUNC_ISO;
+    const bool need = v->storage != RC_STORE_U16 &&
+                      (p->filter == RC_FILTER_BSPLINE || (v->storage == RC_STORE_F16 && grad));
+    if (!need || v->pairs_data_version == v->data_version) return RC_OK;
+    const size_t esz = v->storage == RC_STORE_F32 ? 4 : 2;
+    if (!v->d_pairs) RC_CUDA(ctx, dev_alloc(&v->d_pairs, (size_t)v->nbricks * kPairVox * 2 * esz));
+    RC_CUDA(ctx, launch_pairs(vol_dev(v), v->d_pairs, ctx->stream));
+    v->pairs_data_version = v->data_version;
     return RC_OK;
 }
 
@@ -805,7 +812,7 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
         st = ensure_occupancy(ctx, v, p->filter);
         if (st != RC_OK) return st;
     }
-    st = prepare_filter(ctx, v, p->filter);
+    st = prepare_filter(ctx, v, p);
     if (st != RC_OK) return st;
     MarchArgs a = march_args(ctx, v, p, out_rgba);
     if (stats) {
@@ -830,7 +837,7 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
         st = ensure_occupancy(ctx, v, p->filter);
         if (st != RC_OK) return st;
     }
-    st = prepare_filter(ctx, v, p->filter);
+    st = prepare_filter(ctx, v, p);
     if (st != RC_OK) return st;
     CamRec first;
     st = upload_views(ctx, v, cams, nviews, &first, who);
@@ -918,7 +925,7 @@ rc_status rc_render_views_host(rc_context *ctx, const rc_volume *vol, const rc_r
         st = ensure_occupancy(ctx, v, p->filter);
         if (st != RC_OK) return st;
     }
-    st = prepare_filter(ctx, v, p->filter);
+    st = prepare_filter(ctx, v, p);
     if (st != RC_OK) return st;
     CamRec first;
     st = upload_views(ctx, v, cams, nviews, &first, who);
@@ -970,7 +977,7 @@ rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvo
     DeviceScope ds(ctx->device);
     for (int i = 0; i < nvols; i++) {
         st = ensure_occupancy(ctx, const_cast<rc_volume *>(vols[i]), p->filter);
-        if (st == RC_OK) st = prepare_filter(ctx, const_cast<rc_volume *>(vols[i]), p->filter);
+        if (st == RC_OK) st = prepare_filter(ctx, const_cast<rc_volume *>(vols[i]), p);
         if (st != RC_OK) return st;
     }
     CamRec first;
@@ -987,7 +994,7 @@ rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvo
     BatchVol *recs = new (std::nothrow) BatchVol[nvols];
     if (!recs) return fail(ctx, RC_ERR_OOM, "%s: host allocation", who);
     for (int i = 0; i < nvols; i++)
-        recs[i] = BatchVol{vols[i]->d_data, vols[i]->d_vg, vol_dev(vols[i]).bsp, vols[i]->d_occ[p->filter],
+        recs[i] = BatchVol{vols[i]->d_data, vols[i]->d_vg, vol_dev(vols[i]).pairs, vols[i]->d_occ[p->filter],
                            vols[i]->d_fine[p->filter]};
     cudaError_t ce = cudaMemcpyAsync(ctx->d_batch, recs, (size_t)nvols * sizeof(BatchVol), cudaMemcpyHostToDevice,
                                      ctx->stream);

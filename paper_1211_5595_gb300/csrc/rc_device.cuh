@@ -186,6 +186,36 @@ __device__ __forceinline__ float trilinear(const VolDev &v, const Cell &c) {
     return lerp(lerp(c00, c10, wy), lerp(c01, c11, wy), wz);
 }
 
+// Pair entries by storage: two stored elements, aligned to their size.
+template <int ST> struct Pair;
+template <> struct Pair<RC_STORE_F32> { using T = float2; };
+template <> struct Pair<RC_STORE_F16> { using T = __half2; };
+template <> struct Pair<RC_STORE_U16> { using T = ushort2; };
+
+// Pointer to the pair entry of voxels (i-1, i) in the footprint row
+// (j-1, k-1) of the cell: rows (oy, oz) and pairs starting at x = i-1+ox are
+// the compile-time offsets (oz * 19 + oy) * 18 + ox from it.
+template <int ST>
+__device__ __forceinline__ const typename Pair<ST>::T *pair_ptr(const VolDev &v, const Cell &c) {
+    return reinterpret_cast<const typename Pair<ST>::T *>(v.pairs) +
+           ((unsigned)brick_of(v, c) * (unsigned)kPairVox +
+            (unsigned)((((c.i[2] & 15) * kApron + (c.i[1] & 15)) * kPairRow) + (c.i[0] & 15)));
+}
+
+// The two voxels of a pair entry as FP32 (the stored values converted as ldv does).
+template <int ST>
+__device__ __forceinline__ float2 ld_pair(const typename Pair<ST>::T *q) {
+    if constexpr (ST == RC_STORE_F32) return __ldg(q);
+    else if constexpr (ST == RC_STORE_F16) return __half22float2(__ldg(q));
+    else {
+        const ushort2 u = __ldg(q);
+        return make_float2((float)u.x, (float)u.y);
+    }
+}
+
+template <int OY, int OZ, int OX>
+constexpr int pair_off() { return (OZ * kApron + OY) * kPairRow + OX; }
+
 // Value and world-space gradient from the value+gradient bricks (FP32
 // storage): each voxel holds (V, D_x, D_y, D_z) with D_a = V(+1 along a) -
 // V(-1 along a), neighbour indices clamped to the volume, all exact integers.
@@ -218,31 +248,58 @@ __device__ __forceinline__ float value_grad_vg(const VolDev &v, const Cell &c, f
 // {max(i-1, 0), i} and {i+1, min(i+2, N-1)} and the same weight, which equals
 // resampling the clamped positions p -/+ 1; the apron's replicated border
 // voxels give the clamped coordinates.
-template <int ST>
-__device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, float g[3]) {
-    if (ST == RC_STORE_F32) return value_grad_vg(v, c, g);
-    const auto *p = cell_ptr<ST>(v, c);
-    constexpr int X0 = -(int)kDX, X1 = 0, X2 = (int)kDX, X3 = 2 * (int)kDX;
-    constexpr int Y0 = -(int)kDY, Y1 = 0, Y2 = (int)kDY, Y3 = 2 * (int)kDY;
-    constexpr int Z0 = -(int)kDZ, Z1 = 0, Z2 = (int)kDZ, Z3 = 2 * (int)kDZ;
+template <int ST, bool PAIRS>
+__device__ __forceinline__ float value_grad_x(const VolDev &v, const Cell &c, float g[3]) {
     const float wx = c.w[0], wy = c.w[1], wz = c.w[2];
+    // rows along x at (y, z) = (j-1+oy, k-1+oz): L the centre cell's x edge,
+    // M and P those of the -x and +x cells
+    float L11, L21, L12, L22, M11, M21, M12, M22, P11, P21, P12, P22, L01, L02, L31, L32, L10, L20, L13, L23;
+    if (PAIRS) {
+        // pairs (i-1, i) and (i+1, i+2) of the 4 centre rows, (i, i+1) of the
+        // 8 side rows: 16 loads
+        const auto *pp = pair_ptr<ST>(v, c);
+        auto row4 = [&](int off, float &M, float &L, float &P) {
+            const float2 a = ld_pair<ST>(pp + off), b = ld_pair<ST>(pp + off + 2);
+            M = lerp(a.x, a.y, wx);
+            L = lerp(a.y, b.x, wx);
+            P = lerp(b.x, b.y, wx);
+        };
+        auto row2 = [&](int off) {
+            const float2 a = ld_pair<ST>(pp + off + 1);
+            return lerp(a.x, a.y, wx);
+        };
+        row4(pair_off<1, 1, 0>(), M11, L11, P11);
+        row4(pair_off<2, 1, 0>(), M21, L21, P21);
+        row4(pair_off<1, 2, 0>(), M12, L12, P12);
+        row4(pair_off<2, 2, 0>(), M22, L22, P22);
+        L01 = row2(pair_off<0, 1, 0>());
+        L02 = row2(pair_off<0, 2, 0>());
+        L31 = row2(pair_off<3, 1, 0>());
+        L32 = row2(pair_off<3, 2, 0>());
+        L10 = row2(pair_off<1, 0, 0>());
+        L20 = row2(pair_off<2, 0, 0>());
+        L13 = row2(pair_off<1, 3, 0>());
+        L23 = row2(pair_off<2, 3, 0>());
+    } else {
+        const auto *p = cell_ptr<ST>(v, c);
+        constexpr int X0 = -(int)kDX, X1 = 0, X2 = (int)kDX, X3 = 2 * (int)kDX;
+        constexpr int Y0 = -(int)kDY, Y1 = 0, Y2 = (int)kDY, Y3 = 2 * (int)kDY;
+        constexpr int Z0 = -(int)kDZ, Z1 = 0, Z2 = (int)kDZ, Z3 = 2 * (int)kDZ;
 #define RC_F(X, Y, Z) ldv<ST>(p + ((X) + (Y) + (Z)))
 #define RC_LX(XA, XB, Y, Z) lerp(RC_F(XA, Y, Z), RC_F(XB, Y, Z), wx)
-    // rows along x (y, z) through the centre cell
-    float L11 = RC_LX(X1, X2, Y1, Z1), L21 = RC_LX(X1, X2, Y2, Z1);
-    float L12 = RC_LX(X1, X2, Y1, Z2), L22 = RC_LX(X1, X2, Y2, Z2);
-    // -x and +x cells
-    float M11 = RC_LX(X0, X1, Y1, Z1), M21 = RC_LX(X0, X1, Y2, Z1);
-    float M12 = RC_LX(X0, X1, Y1, Z2), M22 = RC_LX(X0, X1, Y2, Z2);
-    float P11 = RC_LX(X2, X3, Y1, Z1), P21 = RC_LX(X2, X3, Y2, Z1);
-    float P12 = RC_LX(X2, X3, Y1, Z2), P22 = RC_LX(X2, X3, Y2, Z2);
-    // rows of the -y/+y and -z/+z cells
-    float L01 = RC_LX(X1, X2, Y0, Z1), L02 = RC_LX(X1, X2, Y0, Z2);
-    float L31 = RC_LX(X1, X2, Y3, Z1), L32 = RC_LX(X1, X2, Y3, Z2);
-    float L10 = RC_LX(X1, X2, Y1, Z0), L20 = RC_LX(X1, X2, Y2, Z0);
-    float L13 = RC_LX(X1, X2, Y1, Z3), L23 = RC_LX(X1, X2, Y2, Z3);
+        L11 = RC_LX(X1, X2, Y1, Z1); L21 = RC_LX(X1, X2, Y2, Z1);
+        L12 = RC_LX(X1, X2, Y1, Z2); L22 = RC_LX(X1, X2, Y2, Z2);
+        M11 = RC_LX(X0, X1, Y1, Z1); M21 = RC_LX(X0, X1, Y2, Z1);
+        M12 = RC_LX(X0, X1, Y1, Z2); M22 = RC_LX(X0, X1, Y2, Z2);
+        P11 = RC_LX(X2, X3, Y1, Z1); P21 = RC_LX(X2, X3, Y2, Z1);
+        P12 = RC_LX(X2, X3, Y1, Z2); P22 = RC_LX(X2, X3, Y2, Z2);
+        L01 = RC_LX(X1, X2, Y0, Z1); L02 = RC_LX(X1, X2, Y0, Z2);
+        L31 = RC_LX(X1, X2, Y3, Z1); L32 = RC_LX(X1, X2, Y3, Z2);
+        L10 = RC_LX(X1, X2, Y1, Z0); L20 = RC_LX(X1, X2, Y2, Z0);
+        L13 = RC_LX(X1, X2, Y1, Z3); L23 = RC_LX(X1, X2, Y2, Z3);
 #undef RC_LX
 #undef RC_F
+    }
     float a1 = lerp(L11, L21, wy), a2 = lerp(L12, L22, wy);
     float val = lerp(a1, a2, wz);
     float xm = lerp(lerp(M11, M21, wy), lerp(M12, M22, wy), wz);
@@ -256,6 +313,17 @@ __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, floa
     g[1] = (yp - ym) * v.inv2s[1];
     g[2] = (zp - zm) * v.inv2s[2];
     return val;
+}
+
+// Value and gradient of the trilinear field: FP32 storage from the
+// value+gradient bricks; FP16 from the pair bricks when the volume has them
+// (one uniform branch per sample), else, and for uint16, from the apron
+// brick; the same stored values and operations either way.
+template <int ST>
+__device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, float g[3]) {
+    if (ST == RC_STORE_F32) return value_grad_vg(v, c, g);
+    if (ST == RC_STORE_F16 && v.pairs != nullptr) return value_grad_x<ST, true>(v, c, g);
+    return value_grad_x<ST, false>(v, c, g);
 }
 
 // Uniform cubic B-spline reconstruction (Sec. 3.2's higher-order filter):
@@ -285,21 +353,15 @@ __device__ __forceinline__ void bspline_dweights(float t, float d[4]) {
 }
 
 
-// Entry of the B-spline pair bricks holding voxels (i-1, i) of the cell's
-// first footprint row (FP32 storage with the pairs built).
-__device__ __forceinline__ const float2 *bspline_pairs(const VolDev &v, const Cell &c) {
-    return v.bsp + ((unsigned)brick_of(v, c) * (unsigned)kBspVox +
-                    (unsigned)((((c.i[2] & 15) * kApron + (c.i[1] & 15)) * kBspRow) + (c.i[0] & 15)));
-}
 
 // The four voxels x = i-1 .. i+2 of footprint row (oy, oz): PAIRS, two pair
 // loads; else four scalar loads from the apron brick.
 template <int ST, bool PAIRS>
-__device__ __forceinline__ void bspline_row(const typename Voxel<ST>::T *a, const float2 *pb, int oz, int oy,
-                                            float &v0, float &v1, float &v2, float &v3) {
+__device__ __forceinline__ void bspline_row(const typename Voxel<ST>::T *a, const typename Pair<ST>::T *pp, int oz,
+                                            int oy, float &v0, float &v1, float &v2, float &v3) {
     if (PAIRS) {
-        const float2 *q = pb + (oz * kApron + oy) * kBspRow;
-        const float2 p0 = __ldg(q), p1 = __ldg(q + 2);
+        const auto *q = pp + (oz * kApron + oy) * kPairRow;
+        const float2 p0 = ld_pair<ST>(q), p1 = ld_pair<ST>(q + 2);
         v0 = p0.x;
         v1 = p0.y;
         v2 = p1.x;
@@ -316,7 +378,7 @@ __device__ __forceinline__ void bspline_row(const typename Voxel<ST>::T *a, cons
 template <int ST, bool PAIRS>
 __device__ __forceinline__ float bspline_x(const VolDev &v, const Cell &c) {
     const auto *a = cell_ptr<ST>(v, c) - (int)(kDX + kDY + kDZ);     // voxel (i-1, j-1, k-1)
-    const float2 *pb = PAIRS ? bspline_pairs(v, c) : nullptr;
+    const typename Pair<ST>::T *pp = PAIRS ? pair_ptr<ST>(v, c) : nullptr;
     float wx[4], wy[4], wz[4];
     bspline_weights(c.w[0], wx);
     bspline_weights(c.w[1], wy);
@@ -328,7 +390,7 @@ __device__ __forceinline__ float bspline_x(const VolDev &v, const Cell &c) {
 #pragma unroll
         for (int oy = 0; oy < 4; oy++) {
             float v0, v1, v2, v3;
-            bspline_row<ST, PAIRS>(a, pb, oz, oy, v0, v1, v2, v3);
+            bspline_row<ST, PAIRS>(a, pp, oz, oy, v0, v1, v2, v3);
             float fx = v0 * wx[0];
             fx = __fmaf_rn(v1, wx[1], fx);
             fx = __fmaf_rn(v2, wx[2], fx);
@@ -346,7 +408,7 @@ __device__ __forceinline__ float bspline_x(const VolDev &v, const Cell &c) {
 template <int ST, bool PAIRS>
 __device__ __forceinline__ float bspline_grad_x(const VolDev &v, const Cell &c, float g[3]) {
     const auto *a = cell_ptr<ST>(v, c) - (int)(kDX + kDY + kDZ);     // voxel (i-1, j-1, k-1)
-    const float2 *pb = PAIRS ? bspline_pairs(v, c) : nullptr;
+    const typename Pair<ST>::T *pp = PAIRS ? pair_ptr<ST>(v, c) : nullptr;
     float wx[4], wy[4], wz[4], dx[4], dy[4], dz[4];
     bspline_weights(c.w[0], wx);
     bspline_weights(c.w[1], wy);
@@ -361,7 +423,7 @@ __device__ __forceinline__ float bspline_grad_x(const VolDev &v, const Cell &c, 
 #pragma unroll
         for (int oy = 0; oy < 4; oy++) {
             float v0, v1, v2, v3;
-            bspline_row<ST, PAIRS>(a, pb, oz, oy, v0, v1, v2, v3);
+            bspline_row<ST, PAIRS>(a, pp, oz, oy, v0, v1, v2, v3);
             float fx = v0 * wx[0], ex = v0 * dx[0];
             fx = __fmaf_rn(v1, wx[1], fx);
             ex = __fmaf_rn(v1, dx[1], ex);
@@ -385,17 +447,17 @@ __device__ __forceinline__ float bspline_grad_x(const VolDev &v, const Cell &c, 
 }
 
 // The B-spline value (and gradient) with the footprint from the pair bricks
-// when the volume has them (one uniform branch per sample), else from the
-// apron brick.
+// when the volume has them (FP32 and FP16 storage; one uniform branch per
+// sample), else from the apron brick; both read the same stored values.
 template <int ST>
 __device__ __forceinline__ float bspline(const VolDev &v, const Cell &c) {
-    if (ST == RC_STORE_F32 && v.bsp != nullptr) return bspline_x<ST, true>(v, c);
+    if (ST != RC_STORE_U16 && v.pairs != nullptr) return bspline_x<ST, true>(v, c);
     return bspline_x<ST, false>(v, c);
 }
 
 template <int ST>
 __device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, float g[3]) {
-    if (ST == RC_STORE_F32 && v.bsp != nullptr) return bspline_grad_x<ST, true>(v, c, g);
+    if (ST != RC_STORE_U16 && v.pairs != nullptr) return bspline_grad_x<ST, true>(v, c, g);
     return bspline_grad_x<ST, false>(v, c, g);
 }
 

@@ -14,11 +14,12 @@ constexpr int kApron = 19;          // stored brick edge: cells 16b-1 .. 16b+17 
 constexpr int kApronVox = kApron * kApron * kApron;   // 6859
 constexpr int kGradEdge = 17;       // value+gradient brick edge: voxels 16b .. 16b+16 (the trilinear footprint)
 constexpr int kGradVox = kGradEdge * kGradEdge * kGradEdge;   // 4913
-// B-spline pair bricks (FP32 storage): per cell-brick the apron rows
-// (lz, ly in 0..18) as 18 entries (V[16b-1+e], V[16b+e]), e = 0..17, so a
-// row of the 4 x 4 x 4 footprint is two aligned 8-byte loads.
-constexpr int kBspRow = 18;
-constexpr int kBspVox = kApron * kApron * kBspRow;            // 6498
+// Pair bricks: per cell-brick the apron rows (lz, ly in 0..18) as 18
+// entries (V[16b-1+e], V[16b+e]), e = 0..17, in the storage type (two
+// elements, aligned to their size), so two x-adjacent voxels of any footprint
+// row arrive in one load.
+constexpr int kPairRow = 18;
+constexpr int kPairVox = kApron * kApron * kPairRow;          // 6498
 
 // Camera record: FP64 look-at basis rounded once to FP32, eye in index space.
 struct CamRec {
@@ -31,7 +32,7 @@ struct CamRec {
 // Device view of a bricked volume.
 struct VolDev {
     const void *data;      // [bz][by][bx][19][19][19] apron bricks, storage type
-    const float2 *bsp;     // F32 storage, once a B-spline render needed it: pair bricks, else null
+    const void *pairs;     // pair bricks (storage type) once a render needed them, else null
     const float4 *vg;      // F32 storage: [bz][by][bx][17][17][17] (value, central differences x2), else null
     int storage;           // rc_storage
     int n[3];              // voxels per axis
@@ -83,7 +84,7 @@ struct MarchParams {
 struct BatchVol {
     const void *data;
     const float4 *vg;
-    const float2 *bsp;
+    const void *pairs;
     const uint8_t *occ;
     const unsigned long long *fine;
 };
@@ -192,7 +193,7 @@ struct TrainArgs {
 // ---- launchers (return the launch error) --------------------------------
 cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStream_t s);
 cudaError_t launch_gradvol(const uint16_t *stage, VolDev v, float4 *dst, cudaStream_t s);
-cudaError_t launch_bsppair(const uint16_t *stage, VolDev v, float2 *dst, cudaStream_t s);
+cudaError_t launch_pairs(VolDev v, void *dst, cudaStream_t s);
 cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax, int filter,
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);
 cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax,

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kMarchThreads) composite_kernel(const MarchArg
         const BatchVol bv = a.batch[vi];
         vol.data = bv.data;
         vol.vg = bv.vg;
-        vol.bsp = bv.bsp;
+        vol.pairs = bv.pairs;
         occ = bv.occ;
         fine = bv.fine;
     }

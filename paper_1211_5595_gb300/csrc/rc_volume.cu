@@ -82,30 +82,28 @@ cudaError_t launch_gradvol(const uint16_t *stage, VolDev v, float4 *dst, cudaStr
     return cudaGetLastError();
 }
 
-// One thread per entry of the B-spline pair bricks (FP32 storage): entry
-// (lz, ly, e) of brick b holds the voxels x = 16b-1+e and x+1 of the apron
-// row (16b-1+ly, 16b-1+lz), every index clamped to the volume (the apron's
-// replicated border), codes clamped to vmax; exact in FP32.
-__global__ void bsppair_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int cb0, int cb1,
-                               float2 *dst, long long total) {
+// One thread per entry of the pair bricks: entry (lz, ly, e) of brick b is
+// the apron elements e and e + 1 of row (ly, lz), copied bit for bit (so the
+// pairs hold exactly the stored values of every storage type).
+template <typename T>
+__global__ void pairs_kernel(const T *__restrict__ apron, T *__restrict__ dst, long long total) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= total) return;
-    const int local = (int)(e % kBspVox);
-    const long long brick = e / kBspVox;
-    const int bx = (int)(brick % cb0);
-    const long long r = brick / cb0;
-    const int by = (int)(r % cb1), bz = (int)(r / cb1);
-    const int ex = local % kBspRow, ly = (local / kBspRow) % kApron, lz = local / (kBspRow * kApron);
-    const int x0 = min(max(bx * kBrick - 1 + ex, 0), nx - 1), x1 = min(max(bx * kBrick + ex, 0), nx - 1);
-    const int y = min(max(by * kBrick - 1 + ly, 0), ny - 1), z = min(max(bz * kBrick - 1 + lz, 0), nz - 1);
-    const size_t row = ((size_t)z * ny + y) * nx;
-    dst[e] = make_float2((float)min((int)stage[row + x0], vmax), (float)min((int)stage[row + x1], vmax));
+    const int local = (int)(e % kPairVox);
+    const long long brick = e / kPairVox;
+    const int ex = local % kPairRow, row = local / kPairRow;          // row = lz * 19 + ly
+    const T *src = apron + brick * kApronVox + (long long)row * kApron + ex;
+    dst[2 * e] = src[0];
+    dst[2 * e + 1] = src[1];
 }
 
-cudaError_t launch_bsppair(const uint16_t *stage, VolDev v, float2 *dst, cudaStream_t s) {
-    const long long total = (long long)v.cb[0] * v.cb[1] * v.cb[2] * kBspVox;
-    bsppair_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0],
-                                                                     v.cb[1], dst, total);
+cudaError_t launch_pairs(VolDev v, void *dst, cudaStream_t s) {
+    const long long total = (long long)v.cb[0] * v.cb[1] * v.cb[2] * kPairVox;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (v.storage == RC_STORE_F32)
+        pairs_kernel<float><<<blocks, 256, 0, s>>>((const float *)v.data, (float *)dst, total);
+    else
+        pairs_kernel<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t *)v.data, (uint16_t *)dst, total);
     return cudaGetLastError();
 }
 
