@@ -81,6 +81,18 @@ def test_allocation_failures_are_clean(rc, monkeypatch):
             rc.rc_render_proposal(ctx, vol, P, 64, 0.02, out)
         assert ei.value.status == rc.RC_ERR_STATE
         assert np.array_equal(render(rc, ctx, vol, cam), ref)
+        # the pair bricks, allocated by the first B-spline render: a failure
+        # refuses that render and the next one allocates them
+        Pb = dict(step_vox=0.5, term=0.99, shade=True, skip=True, filter=rc.RC_FILTER_BSPLINE)
+        monkeypatch.setenv("RC_FAULT_ALLOC", "00001")
+        with pytest.raises(rc.RCError) as ei:
+            rc.rc_render(ctx, vol, Pb, out)
+        assert ei.value.status == rc.RC_ERR_OOM
+        monkeypatch.delenv("RC_FAULT_ALLOC")
+        rc.rc_render(ctx, vol, Pb, out)
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all() and float(out[..., 3].max()) > 0.5
+        assert np.array_equal(render(rc, ctx, vol, cam), ref)
         rc.rc_volume_destroy(ctx, vol)
     finally:
         monkeypatch.delenv("RC_FAULT_ALLOC", raising=False)
