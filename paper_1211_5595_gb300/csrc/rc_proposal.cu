@@ -706,6 +706,13 @@ __global__ void __launch_bounds__(128) tc_train_kernel(const TrainArgs A) {
     for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const long long r0 = tile * 128, r = r0 + t;
         const bool valid = r < A.n;
+        // the CTA's next tile (features and targets) into L2
+        const long long nt = tile + gridDim.x;
+        if (t == 0 && nt < ntiles) {
+            const long long nrows = min((long long)128, A.n - nt * 128);
+            tc::prefetch_l2(A.feat + nt * 128 * kFeat, (uint32_t)(nrows * kFeat * sizeof(float)));
+            tc::prefetch_l2(A.target + nt * 128 * kOutUsed, (uint32_t)((nrows * kOutUsed * sizeof(float)) & ~15ull));
+        }
         // features: coalesced float4 loads of the contiguous tile -> BF16
         {
             const float4 *src = reinterpret_cast<const float4 *>(A.feat + r0 * kFeat);

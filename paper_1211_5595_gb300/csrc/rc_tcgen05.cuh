@@ -95,6 +95,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16) from global memory into L2,
+// no completion to wait for; skipped unless the source is 16-byte aligned.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) != 0u || bytes == 0u) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // TMEM allocation (whole warp): writes the base address to *slot.
 template <int COLS>
 __device__ __forceinline__ void tmem_alloc(uint32_t slot) {
