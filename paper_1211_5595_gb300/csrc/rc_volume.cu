@@ -14,15 +14,16 @@ namespace rc {
 template <int ST>
 __global__ void relayout_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int cb0,
                                 int cb1, void *dst, long long total) {
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    const int local = (int)(e % kApronVox);
-    const long long brick = e / kApronVox;
-    const int bx = (int)(brick % cb0);
-    const long long r = brick / cb0;
-    const int by = (int)(r % cb1);
-    const int bz = (int)(r / cb1);
-    const int lx = local % kApron, ly = (local / kApron) % kApron, lz = local / (kApron * kApron);
+    // 32-bit indices: a volume has fewer than 2^31 stored voxels (checked
+    // at creation), and the divisions by constants become multiply-shifts
+    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((long long)e >= total) return;
+    const unsigned local = e % (unsigned)kApronVox, brick = e / (unsigned)kApronVox;
+    const int bx = (int)(brick % (unsigned)cb0);
+    const unsigned r = brick / (unsigned)cb0;
+    const int by = (int)(r % (unsigned)cb1);
+    const int bz = (int)(r / (unsigned)cb1);
+    const int lx = (int)(local % kApron), ly = (int)((local / kApron) % kApron), lz = (int)(local / (kApron * kApron));
     const int x = min(max(bx * kBrick + lx - 1, 0), nx - 1);
     const int y = min(max(by * kBrick + ly - 1, 0), ny - 1);
     const int z = min(max(bz * kBrick + lz - 1, 0), nz - 1);
@@ -54,15 +55,15 @@ cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStre
 // indices clamped to the volume, codes clamped to vmax; exact in FP32.
 __global__ void gradvol_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int cb0, int cb1,
                                float4 *dst, long long total) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    const int local = (int)(e % kGradVox);
-    const long long brick = e / kGradVox;
-    const int bx = (int)(brick % cb0);
-    const long long r = brick / cb0;
-    const int by = (int)(r % cb1);
-    const int bz = (int)(r / cb1);
-    const int lx = local % kGradEdge, ly = (local / kGradEdge) % kGradEdge, lz = local / (kGradEdge * kGradEdge);
+    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;     // fewer than 2^31 entries
+    if ((long long)e >= total) return;
+    const unsigned local = e % (unsigned)kGradVox, brick = e / (unsigned)kGradVox;
+    const int bx = (int)(brick % (unsigned)cb0);
+    const unsigned r = brick / (unsigned)cb0;
+    const int by = (int)(r % (unsigned)cb1);
+    const int bz = (int)(r / (unsigned)cb1);
+    const int lx = (int)(local % kGradEdge), ly = (int)((local / kGradEdge) % kGradEdge),
+              lz = (int)(local / (kGradEdge * kGradEdge));
     const int x = min(bx * kBrick + lx, nx - 1), y = min(by * kBrick + ly, ny - 1), z = min(bz * kBrick + lz, nz - 1);
     auto code = [&](int xx, int yy, int zz) {
         return (float)min((int)stage[((size_t)zz * ny + yy) * nx + xx], vmax);
@@ -87,12 +88,11 @@ cudaError_t launch_gradvol(const uint16_t *stage, VolDev v, float4 *dst, cudaStr
 // pairs hold exactly the stored values of every storage type).
 template <typename T>
 __global__ void pairs_kernel(const T *__restrict__ apron, T *__restrict__ dst, long long total) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= total) return;
-    const int local = (int)(e % kPairVox);
-    const long long brick = e / kPairVox;
-    const int ex = local % kPairRow, row = local / kPairRow;          // row = lz * 19 + ly
-    const T *src = apron + brick * kApronVox + (long long)row * kApron + ex;
+    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;     // fewer than 2^31 entries
+    if ((long long)e >= total) return;
+    const unsigned local = e % (unsigned)kPairVox, brick = e / (unsigned)kPairVox;
+    const unsigned ex = local % kPairRow, row = local / kPairRow;     // row = lz * 19 + ly
+    const T *src = apron + (size_t)brick * kApronVox + row * kApron + ex;
     dst[2 * e] = src[0];
     dst[2 * e + 1] = src[1];
 }
