@@ -372,13 +372,10 @@ rc_status rc_volume_upload(rc_volume *v, const uint16_t *src, size_t n_voxels, i
     DeviceScope ds(ctx->device);
     RC_CUDA(ctx, cudaMemcpyAsync(v->d_stage, src, nvox * sizeof(uint16_t),
                                  src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
-    VolDev d = vol_dev(v);
-    RC_CUDA(ctx, launch_relayout(v->d_stage, d, v->d_data, ctx->stream));
-    if (v->d_vg) RC_CUDA(ctx, launch_gradvol(v->d_stage, d, v->d_vg, ctx->stream));
-    RC_CUDA(ctx, launch_minmax(v->d_stage, v->n, v->cb, v->vmax, RC_FILTER_TRILINEAR, v->d_mn[0], v->d_mx[0],
-                               ctx->stream));
-    RC_CUDA(ctx, launch_minmax4(v->d_stage, v->n, v->vmax, RC_FILTER_TRILINEAR, v->d_mn4[0], v->d_mx4[0],
-                                ctx->stream));
+    // apron bricks, value+gradient bricks and the trilinear grids in one pass
+    // over the staged codes (one block per cell-brick)
+    RC_CUDA(ctx, launch_prep(v->d_stage, vol_dev(v), v->d_data, v->d_vg, v->d_mn[0], v->d_mx[0], v->d_mn4[0],
+                             v->d_mx4[0], ctx->stream));
     v->uploaded = true;
     v->data_version++;
     v->grid_data_version[RC_FILTER_TRILINEAR] = v->data_version;   // the B-spline grid is built on first use

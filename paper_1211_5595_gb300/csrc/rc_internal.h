@@ -191,9 +191,9 @@ struct TrainArgs {
 };
 
 // ---- launchers (return the launch error) --------------------------------
-cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStream_t s);
-cudaError_t launch_gradvol(const uint16_t *stage, VolDev v, float4 *dst, cudaStream_t s);
 cudaError_t launch_pairs(VolDev v, void *dst, cudaStream_t s);
+cudaError_t launch_prep(const uint16_t *stage, VolDev v, void *apron, float4 *vg, uint16_t *mn, uint16_t *mx,
+                        uint16_t *mn4, uint16_t *mx4, cudaStream_t s);
 cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax, int filter,
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);
 cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax,

@@ -1,87 +1,10 @@
 // Volume preparation: re-layout of the uint16 codes into apron bricks (19^3
-// voxels per 16^3-cell brick) in the chosen storage, the cell-brick min/max
-// grid and the occupancy mask of the current transfer function (Sec. 2.1
-// volume data, Sec. 2.6 classification).
+// voxels per 16^3-cell brick) in the chosen storage, value+gradient and pair
+// bricks, the min/max grids and the occupancy masks of the current transfer
+// function (Sec. 2.1 volume data, Sec. 2.6 classification).
 #include "rc_device.cuh"
 
 namespace rc {
-
-// One thread per element of the apron-bricked array: cell-brick (bx, by, bz)
-// stores voxels 16b-1 .. 16b+17 per axis, clamped to the volume (border voxels
-// replicated). Reads the linear staging copy (x fastest) and converts: F32
-// keeps the code, F16 stores fp16(code / vmax) (FP32 quotient, then
-// round-to-nearest-even), U16 keeps the code. Codes above vmax clamp.
-template <int ST>
-__global__ void relayout_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int cb0,
-                                int cb1, void *dst, long long total) {
-    // 32-bit indices: a volume has fewer than 2^31 stored voxels (checked
-    // at creation), and the divisions by constants become multiply-shifts
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;
-    if ((long long)e >= total) return;
-    const unsigned local = e % (unsigned)kApronVox, brick = e / (unsigned)kApronVox;
-    const int bx = (int)(brick % (unsigned)cb0);
-    const unsigned r = brick / (unsigned)cb0;
-    const int by = (int)(r % (unsigned)cb1);
-    const int bz = (int)(r / (unsigned)cb1);
-    const int lx = (int)(local % kApron), ly = (int)((local / kApron) % kApron), lz = (int)(local / (kApron * kApron));
-    const int x = min(max(bx * kBrick + lx - 1, 0), nx - 1);
-    const int y = min(max(by * kBrick + ly - 1, 0), ny - 1);
-    const int z = min(max(bz * kBrick + lz - 1, 0), nz - 1);
-    const int code = min((int)stage[((size_t)z * ny + y) * nx + x], vmax);
-    if (ST == RC_STORE_F32) ((float *)dst)[e] = (float)code;
-    else if (ST == RC_STORE_F16) ((__half *)dst)[e] = __float2half_rn(__fdiv_rn((float)code, (float)vmax));
-    else ((uint16_t *)dst)[e] = (uint16_t)code;
-}
-
-cudaError_t launch_relayout(const uint16_t *stage, VolDev v, void *dst, cudaStream_t s) {
-    const long long total = (long long)v.cb[0] * v.cb[1] * v.cb[2] * kApronVox;
-    const unsigned blocks = (unsigned)((total + 255) / 256);
-    switch (v.storage) {
-        case RC_STORE_F32:
-            relayout_kernel<RC_STORE_F32><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0], v.cb[1], dst, total);
-            break;
-        case RC_STORE_F16:
-            relayout_kernel<RC_STORE_F16><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0], v.cb[1], dst, total);
-            break;
-        default:
-            relayout_kernel<RC_STORE_U16><<<blocks, 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0], v.cb[1], dst, total);
-    }
-    return cudaGetLastError();
-}
-
-// One thread per element of the value+gradient bricks (FP32 storage): brick b
-// holds voxels 16b .. 16b+16 per axis (clamped to the volume) as
-// (V, V(x+1) - V(x-1), V(y+1) - V(y-1), V(z+1) - V(z-1)), neighbour
-// indices clamped to the volume, codes clamped to vmax; exact in FP32.
-__global__ void gradvol_kernel(const uint16_t *__restrict__ stage, int nx, int ny, int nz, int vmax, int cb0, int cb1,
-                               float4 *dst, long long total) {
-    const unsigned e = blockIdx.x * blockDim.x + threadIdx.x;     // fewer than 2^31 entries
-    if ((long long)e >= total) return;
-    const unsigned local = e % (unsigned)kGradVox, brick = e / (unsigned)kGradVox;
-    const int bx = (int)(brick % (unsigned)cb0);
-    const unsigned r = brick / (unsigned)cb0;
-    const int by = (int)(r % (unsigned)cb1);
-    const int bz = (int)(r / (unsigned)cb1);
-    const int lx = (int)(local % kGradEdge), ly = (int)((local / kGradEdge) % kGradEdge),
-              lz = (int)(local / (kGradEdge * kGradEdge));
-    const int x = min(bx * kBrick + lx, nx - 1), y = min(by * kBrick + ly, ny - 1), z = min(bz * kBrick + lz, nz - 1);
-    auto code = [&](int xx, int yy, int zz) {
-        return (float)min((int)stage[((size_t)zz * ny + yy) * nx + xx], vmax);
-    };
-    float4 o;
-    o.x = code(x, y, z);
-    o.y = code(min(x + 1, nx - 1), y, z) - code(max(x - 1, 0), y, z);
-    o.z = code(x, min(y + 1, ny - 1), z) - code(x, max(y - 1, 0), z);
-    o.w = code(x, y, min(z + 1, nz - 1)) - code(x, y, max(z - 1, 0));
-    dst[e] = o;
-}
-
-cudaError_t launch_gradvol(const uint16_t *stage, VolDev v, float4 *dst, cudaStream_t s) {
-    const long long total = (long long)v.cb[0] * v.cb[1] * v.cb[2] * kGradVox;
-    gradvol_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(stage, v.n[0], v.n[1], v.n[2], v.vmax, v.cb[0],
-                                                                     v.cb[1], dst, total);
-    return cudaGetLastError();
-}
 
 // One thread per entry of the pair bricks: entry (lz, ly, e) of brick b is
 // the apron elements e and e + 1 of row (ly, lz), copied bit for bit (so the
@@ -104,6 +27,152 @@ cudaError_t launch_pairs(VolDev v, void *dst, cudaStream_t s) {
         pairs_kernel<float><<<blocks, 256, 0, s>>>((const float *)v.data, (float *)dst, total);
     else
         pairs_kernel<uint16_t><<<blocks, 256, 0, s>>>((const uint16_t *)v.data, (uint16_t *)dst, total);
+    return cudaGetLastError();
+}
+
+// The whole preparation of one cell-brick from one staged copy of its
+// footprint (one block of 256 threads per cell-brick): the codes of the
+// brick's 19^3 apron box (voxels 16b-1 .. 16b+17 per axis, clamped to the
+// volume so border voxels are replicated; codes clamped to vmax) are read once
+// into shared memory and written out as
+//   - the apron brick in the storage type: F32 keeps the code, F16 stores
+//     fp16(code / vmax) (FP32 quotient, round-to-nearest-even), U16 the code;
+//   - FP32 storage: the 17^3 value+gradient entries of voxels 16b .. 16b+16
+//     (clamped) as (V, V(x+1) - V(x-1), V(y+1) - V(y-1), V(z+1) - V(z-1)),
+//     neighbour indices clamped to the volume (exact in FP32);
+//   - the trilinear cell-brick min / max over voxels max(16b, 0) .. min(16b+16, N-1);
+//   - the trilinear min / max of the brick's 4^3 sub-blocks j over voxels
+//     4j .. min(4j+4, N-1) (ceil((N-1)/4) sub-blocks per axis).
+// minmax_kernel and minmax4_kernel compute the same grids for the B-spline
+// footprints, on first use.
+struct PrepArgs {
+    const uint16_t *stage;
+    int n[3], cb[3], c4[3];
+    int vmax;
+    void *apron;
+    float4 *vg;                  // null unless FP32 storage
+    uint16_t *mn, *mx, *mn4, *mx4;
+};
+
+template <int ST>
+__global__ void __launch_bounds__(256) prep_kernel(const PrepArgs A) {
+    __shared__ uint16_t s_code[kApronVox];
+    __shared__ int s_lo[8], s_hi[8];
+    const unsigned b = blockIdx.x;
+    const int bx = (int)(b % (unsigned)A.cb[0]), by = (int)((b / (unsigned)A.cb[0]) % (unsigned)A.cb[1]),
+              bz = (int)(b / ((unsigned)A.cb[0] * (unsigned)A.cb[1]));
+    const int x0 = bx * kBrick - 1, y0 = by * kBrick - 1, z0 = bz * kBrick - 1;     // box origin
+    const int nx = A.n[0], ny = A.n[1], nz = A.n[2];
+    // box codes, and the apron brick from them
+    for (unsigned e = threadIdx.x; e < (unsigned)kApronVox; e += blockDim.x) {
+        const int lx = (int)(e % kApron), ly = (int)((e / kApron) % kApron), lz = (int)(e / (kApron * kApron));
+        const int x = min(max(x0 + lx, 0), nx - 1), y = min(max(y0 + ly, 0), ny - 1), z = min(max(z0 + lz, 0), nz - 1);
+        const int code = min((int)A.stage[((size_t)z * ny + y) * nx + x], A.vmax);
+        s_code[e] = (uint16_t)code;
+        const size_t o = (size_t)b * kApronVox + e;
+        if (ST == RC_STORE_F32) ((float *)A.apron)[o] = (float)code;
+        else if (ST == RC_STORE_F16) ((__half *)A.apron)[o] = __float2half_rn(__fdiv_rn((float)code, (float)A.vmax));
+        else ((uint16_t *)A.apron)[o] = (uint16_t)code;
+    }
+    __syncthreads();
+    // the code at volume coordinate (x, y, z) inside the box
+    auto at = [&](int x, int y, int z) {
+        return (int)s_code[((z - z0) * kApron + (y - y0)) * kApron + (x - x0)];
+    };
+    if (ST == RC_STORE_F32 && A.vg != nullptr) {
+        for (unsigned e = threadIdx.x; e < (unsigned)kGradVox; e += blockDim.x) {
+            const int lx = (int)(e % kGradEdge), ly = (int)((e / kGradEdge) % kGradEdge),
+                      lz = (int)(e / (kGradEdge * kGradEdge));
+            const int x = min(bx * kBrick + lx, nx - 1), y = min(by * kBrick + ly, ny - 1),
+                      z = min(bz * kBrick + lz, nz - 1);
+            float4 o;
+            o.x = (float)at(x, y, z);
+            o.y = (float)(at(min(x + 1, nx - 1), y, z) - at(max(x - 1, 0), y, z));
+            o.z = (float)(at(x, min(y + 1, ny - 1), z) - at(x, max(y - 1, 0), z));
+            o.w = (float)(at(x, y, min(z + 1, nz - 1)) - at(x, y, max(z - 1, 0)));
+            A.vg[(size_t)b * kGradVox + e] = o;
+        }
+    }
+    // cell-brick min / max over voxels max(16b, 0) .. min(16b + 16, N - 1)
+    {
+        const int xa = bx * kBrick, ya = by * kBrick, za = bz * kBrick;
+        const int ex = min(xa + 16, nx - 1) - xa + 1, ey = min(ya + 16, ny - 1) - ya + 1,
+                  ez = min(za + 16, nz - 1) - za + 1;
+        int lo = 65535, hi = 0;
+        for (int t = threadIdx.x; t < ex * ey * ez; t += blockDim.x) {
+            const int v = at(xa + t % ex, ya + (t / ex) % ey, za + t / (ex * ey));
+            lo = min(lo, v);
+            hi = max(hi, v);
+        }
+        lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)lo);
+        hi = (int)__reduce_max_sync(0xffffffffu, (unsigned)hi);
+        if ((threadIdx.x & 31) == 0) {
+            s_lo[threadIdx.x >> 5] = lo;
+            s_hi[threadIdx.x >> 5] = hi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+                lo = min(lo, s_lo[w]);
+                hi = max(hi, s_hi[w]);
+            }
+            A.mn[b] = (uint16_t)lo;
+            A.mx[b] = (uint16_t)hi;
+        }
+    }
+    // the 4^3 sub-blocks j = 4b + s of the brick, four threads each, over
+    // voxels 4j .. min(4j + 4, N - 1)
+    {
+        const int sb = threadIdx.x >> 2, q = threadIdx.x & 3;               // sub-block 0..63, quarter
+        const int sx = sb & 3, sy = (sb >> 2) & 3, sz = sb >> 4;
+        const int jx = 4 * bx + sx, jy = 4 * by + sy, jz = 4 * bz + sz;
+        const bool exists = jx < A.c4[0] && jy < A.c4[1] && jz < A.c4[2];
+        int lo = 65535, hi = 0;
+        if (exists) {
+            const int xa = 4 * jx, ya = 4 * jy, za = 4 * jz;
+            const int ex = min(xa + 4, nx - 1) - xa + 1, ey = min(ya + 4, ny - 1) - ya + 1,
+                      ez = min(za + 4, nz - 1) - za + 1;
+            for (int t = q; t < ex * ey * ez; t += 4) {
+                const int v = at(xa + t % ex, ya + (t / ex) % ey, za + t / (ex * ey));
+                lo = min(lo, v);
+                hi = max(hi, v);
+            }
+        }
+        // the four threads of a sub-block are lanes 4k .. 4k+3 of one warp
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, 1));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, 1));
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, 2));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, 2));
+        if (exists && q == 0) {
+            const size_t j = ((size_t)jz * A.c4[1] + jy) * A.c4[0] + jx;
+            A.mn4[j] = (uint16_t)lo;
+            A.mx4[j] = (uint16_t)hi;
+        }
+    }
+}
+
+cudaError_t launch_prep(const uint16_t *stage, VolDev v, void *apron, float4 *vg, uint16_t *mn, uint16_t *mx,
+                        uint16_t *mn4, uint16_t *mx4, cudaStream_t s) {
+    PrepArgs a;
+    a.stage = stage;
+    for (int i = 0; i < 3; i++) {
+        a.n[i] = v.n[i];
+        a.cb[i] = v.cb[i];
+        a.c4[i] = (v.n[i] - 1 + 3) / 4;
+    }
+    a.vmax = v.vmax;
+    a.apron = apron;
+    a.vg = vg;
+    a.mn = mn;
+    a.mx = mx;
+    a.mn4 = mn4;
+    a.mx4 = mx4;
+    const unsigned nb = (unsigned)(v.cb[0] * v.cb[1] * v.cb[2]);
+    switch (v.storage) {
+        case RC_STORE_F32: prep_kernel<RC_STORE_F32><<<nb, 256, 0, s>>>(a); break;
+        case RC_STORE_F16: prep_kernel<RC_STORE_F16><<<nb, 256, 0, s>>>(a); break;
+        default: prep_kernel<RC_STORE_U16><<<nb, 256, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
