@@ -99,10 +99,13 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs A) {
         const int ex = min(xa + 16, nx - 1) - xa + 1, ey = min(ya + 16, ny - 1) - ya + 1,
                   ez = min(za + 16, nz - 1) - za + 1;
         int lo = 65535, hi = 0;
-        for (int t = threadIdx.x; t < ex * ey * ez; t += blockDim.x) {
-            const int v = at(xa + t % ex, ya + (t / ex) % ey, za + t / (ex * ey));
-            lo = min(lo, v);
-            hi = max(hi, v);
+        for (int row = threadIdx.x; row < ey * ez; row += blockDim.x) {      // rows (y, z), then along x
+            const int y = ya + row % ey, z = za + row / ey;
+            for (int x = xa; x < xa + ex; x++) {
+                const int v = at(x, y, z);
+                lo = min(lo, v);
+                hi = max(hi, v);
+            }
         }
         lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)lo);
         hi = (int)__reduce_max_sync(0xffffffffu, (unsigned)hi);
@@ -132,10 +135,13 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs A) {
             const int xa = 4 * jx, ya = 4 * jy, za = 4 * jz;
             const int ex = min(xa + 4, nx - 1) - xa + 1, ey = min(ya + 4, ny - 1) - ya + 1,
                       ez = min(za + 4, nz - 1) - za + 1;
-            for (int t = q; t < ex * ey * ez; t += 4) {
-                const int v = at(xa + t % ex, ya + (t / ex) % ey, za + t / (ex * ey));
-                lo = min(lo, v);
-                hi = max(hi, v);
+            for (int row = q; row < ey * ez; row += 4) {                      // rows (y, z), then along x
+                const int y = ya + row % ey, z = za + row / ey;
+                for (int x = xa; x < xa + ex; x++) {
+                    const int v = at(x, y, z);
+                    lo = min(lo, v);
+                    hi = max(hi, v);
+                }
             }
         }
         // the four threads of a sub-block are lanes 4k .. 4k+3 of one warp
