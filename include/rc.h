@@ -224,9 +224,9 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
  * stream while the next groups render. With
  * page-locked host_rgba (cudaHostAlloc / cudaHostRegister) the copies overlap
  * the rendering; pageable memory gives the same images without the overlap.
- * Each image equals rc_render_views'. Synchronises: the images are in
- * host_rgba when the call returns RC_OK (on an error its contents are
- * undefined). stats (optional) sums over the views. The context's own camera
+ * Each image equals rc_render_views'. host_rgba in device or managed memory
+ * is refused (RC_ERR_INVALID_ARG). Synchronises: the images are in host_rgba
+ * when the call returns RC_OK (on an error its contents are undefined). stats (optional) sums over the views. The context's own camera
  * is not changed. */
 rc_status rc_render_views_host(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                                const rc_camera *cams, int nviews, int group, float *host_rgba, rc_stats *stats);

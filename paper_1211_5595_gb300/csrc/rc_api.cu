@@ -917,6 +917,12 @@ rc_status rc_render_views_host(rc_context *ctx, const rc_volume *vol, const rc_r
     if (st != RC_OK) return st;
     if (group < 0) return fail(ctx, RC_ERR_INVALID_ARG, "%s: group %d", who, group);
     DeviceScope ds(ctx->device);
+    {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, host_rgba) != cudaSuccess) cudaGetLastError();
+        else if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)
+            return fail(ctx, RC_ERR_INVALID_ARG, "%s: host_rgba is device memory (use rc_render_views)", who);
+    }
     rc_volume *v = const_cast<rc_volume *>(vol);
     if (p->skip && p->func == RC_FUNC_COMPOSITE) {
         st = ensure_occupancy(ctx, v, p->filter);

@@ -327,6 +327,9 @@ def test_render_views_host_equals_device_render(rc, c1):
     with pytest.raises(rc.RCError) as ei:
         rc.rc_render_views_host(r.ctx, r.vol, P, cams, torch.empty((5, 72, 96, 4)), group=-1)
     assert ei.value.status == rc.RC_ERR_INVALID_ARG
+    with pytest.raises(rc.RCError) as ei:                 # device memory is not a host buffer
+        rc.rc_render_views_host(r.ctx, r.vol, P, cams, dev)
+    assert ei.value.status == rc.RC_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("form", ["bspline", "mip", "tf2d"])
