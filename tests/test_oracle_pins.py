@@ -402,7 +402,12 @@ def test_occupancy_hand_case(orc):
 # --------------------------------------------------------------------------
 # transfer-function gradient: reverse mode against central differences
 # --------------------------------------------------------------------------
-def test_tf_gradient_matches_finite_differences(orc):
+@pytest.mark.parametrize("bspline", [False, True])
+def test_tf_gradient_matches_finite_differences(orc, bspline):
+    """Reverse mode against central differences, with trilinear and with
+    cubic B-spline reconstruction (the table gradient does not depend on
+    how the sample value was reconstructed)."""
+    filt = orc.BSPLINE if bspline else orc.TRILINEAR
     ph = synth.head_phantom((32, 32, 24), (1, 1, 1), seed=31, tumor_radius_vox=4)
     # every entry strictly inside (0, 1) so +-h stays a valid table
     tf = synth.noise_tf(256, 7, alpha_max=0.2)
@@ -413,11 +418,11 @@ def test_tf_gradient_matches_finite_differences(orc):
     dimg = rng.normal(size=(16 * 16, 4))
 
     def loss(t):
-        sc = orc.Scene(ph.vol, ph.spacing, t, cam, term=1.0, shade=True)
+        sc = orc.Scene(ph.vol, ph.spacing, t, cam, term=1.0, shade=True, filter=filt)
         img = orc.render(sc)["rgba"].reshape(-1, 4)
         return float((img * dimg).sum())
 
-    sc = orc.Scene(ph.vol, ph.spacing, tf, cam, term=1.0, shade=True)
+    sc = orc.Scene(ph.vol, ph.spacing, tf, cam, term=1.0, shade=True, filter=filt)
     dtf, _ = orc.render_grad(sc, dimg)
     # table entries actually used by the rays, plus unused ones (gradient 0)
     used = np.argsort(-np.abs(dtf).sum(axis=1))[:6]
