@@ -244,10 +244,12 @@ rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvo
 /* Gradient of a loss with respect to the transfer function entries, given the
  * gradient of the loss with respect to the composited image (Eq. 4-5 are
  * differentiable in the table). dL_dimage: device, width*height*4 floats;
- * dL_dtf: device, n_entries*4 floats, overwritten. Compositing function only;
- * empty-space skipping is not used (an empty brick still has a gradient). The
- * forward march is recomputed per ray; nothing is stored per sample. The
- * result does not depend on thread scheduling (fixed-point accumulation). */
+ * dL_dtf: device, n_entries*4 floats, overwritten. Compositing function and
+ * a 1-D table only (RC_ERR_UNSUPPORTED for a 2-D table); trilinear or cubic
+ * B-spline reconstruction. The gradient pass does not skip empty space (an
+ * empty brick still has a gradient). The forward march is recomputed per ray;
+ * nothing is stored per sample. The result does not depend on thread
+ * scheduling (fixed-point accumulation). */
 rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol,
                              const rc_render_params *params, const float *dL_dimage,
                              float *dL_dtf);

@@ -78,7 +78,9 @@ __device__ __forceinline__ float dalpha_factor(float x, float ratio) {
     return ratio * exp2f((ratio - 1.0f) * __log2f(x));
 }
 
-template <int ST, bool SHADE, int RM>
+// CUBIC: cubic B-spline reconstruction (value and analytic gradient) instead
+// of trilinear values and central differences; the table scatter is the same.
+template <int ST, bool SHADE, int RM, bool CUBIC>
 __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const float *absmax) {
     const MarchArgs &a = A.m;
     const int K = a.tf.K;
@@ -117,7 +119,8 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
                 k = jump_block(R, a.vol, c, k, s);
                 continue;
             }
-            float4 e = eval_sample_x<ST, SHADE ? kShade : 0, RM>(a.vol, a.p, s_tf, a.tf, R.dir, c, a.p.rmode,
+            float4 e = eval_sample_x<ST, (SHADE ? kShade : 0) | (CUBIC ? kCubic : 0), RM>(a.vol, a.p, s_tf, a.tf,
+                                                                                          R.dir, c, a.p.rmode,
                                                                a.p.ratio);
             composite_add(e, Cf0, Cf1, Cf2, Tf);
             k++;
@@ -139,8 +142,8 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
             position_at(R, sample_t(R, k), p);
             Cell c;
             cell_of(a.vol, p, c);
-            if (SHADE) val = value_grad<ST>(a.vol, c, gr);
-            else val = trilinear<ST>(a.vol, c);
+            if (CUBIC) val = SHADE ? bspline_grad<ST>(a.vol, c, gr) : bspline<ST>(a.vol, c);
+            else val = SHADE ? value_grad<ST>(a.vol, c, gr) : trilinear<ST>(a.vol, c);
             float w;
             float4 e = classify(s_tf, K, tf_coord(val, a.tf.ucoef), &i, &w);
             float ap = correct_alpha<RM>(e.w, a.p.rmode, a.p.ratio);
@@ -208,16 +211,27 @@ static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, int nviews, const
     return cudaGetLastError();
 }
 
-// The instance for the volume's storage, shading and opacity-correction mode RM.
-template <int RM>
+// The instance for the volume's storage, shading, opacity-correction mode RM
+// and reconstruction filter.
+template <int RM, bool CUBIC>
 static cudaError_t launch_adj_rm(const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
     switch (a.m.vol.storage * 2 + (a.m.p.shade ? 1 : 0)) {
-        case RC_STORE_F32 * 2: return launch_adj(adjoint_kernel<RC_STORE_F32, false, RM>, a, nviews, absmax, s);
-        case RC_STORE_F32 * 2 + 1: return launch_adj(adjoint_kernel<RC_STORE_F32, true, RM>, a, nviews, absmax, s);
-        case RC_STORE_F16 * 2: return launch_adj(adjoint_kernel<RC_STORE_F16, false, RM>, a, nviews, absmax, s);
-        case RC_STORE_F16 * 2 + 1: return launch_adj(adjoint_kernel<RC_STORE_F16, true, RM>, a, nviews, absmax, s);
-        case RC_STORE_U16 * 2: return launch_adj(adjoint_kernel<RC_STORE_U16, false, RM>, a, nviews, absmax, s);
-        default: return launch_adj(adjoint_kernel<RC_STORE_U16, true, RM>, a, nviews, absmax, s);
+        case RC_STORE_F32 * 2: return launch_adj(adjoint_kernel<RC_STORE_F32, false, RM, CUBIC>, a, nviews, absmax, s);
+        case RC_STORE_F32 * 2 + 1: return launch_adj(adjoint_kernel<RC_STORE_F32, true, RM, CUBIC>, a, nviews, absmax, s);
+        case RC_STORE_F16 * 2: return launch_adj(adjoint_kernel<RC_STORE_F16, false, RM, CUBIC>, a, nviews, absmax, s);
+        case RC_STORE_F16 * 2 + 1: return launch_adj(adjoint_kernel<RC_STORE_F16, true, RM, CUBIC>, a, nviews, absmax, s);
+        case RC_STORE_U16 * 2: return launch_adj(adjoint_kernel<RC_STORE_U16, false, RM, CUBIC>, a, nviews, absmax, s);
+        default: return launch_adj(adjoint_kernel<RC_STORE_U16, true, RM, CUBIC>, a, nviews, absmax, s);
+    }
+}
+
+template <bool CUBIC>
+static cudaError_t launch_adj_filter(const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
+    switch (a.m.p.rmode) {
+        case 0: return launch_adj_rm<0, CUBIC>(a, nviews, absmax, s);
+        case 1: return launch_adj_rm<1, CUBIC>(a, nviews, absmax, s);
+        case 2: return launch_adj_rm<2, CUBIC>(a, nviews, absmax, s);
+        default: return launch_adj_rm<3, CUBIC>(a, nviews, absmax, s);
     }
 }
 
@@ -232,12 +246,8 @@ cudaError_t launch_adjoint(const AdjointArgs &a, int nviews, float *dL_dtf, cuda
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * K, s);
     if (e != cudaSuccess) return e;
-    switch (a.m.p.rmode) {
-        case 0: e = launch_adj_rm<0>(a, nviews, absmax, s); break;
-        case 1: e = launch_adj_rm<1>(a, nviews, absmax, s); break;
-        case 2: e = launch_adj_rm<2>(a, nviews, absmax, s); break;
-        default: e = launch_adj_rm<3>(a, nviews, absmax, s);
-    }
+    e = a.m.p.filter == RC_FILTER_BSPLINE ? launch_adj_filter<true>(a, nviews, absmax, s)
+                                          : launch_adj_filter<false>(a, nviews, absmax, s);
     if (e != cudaSuccess) return e;
     finalize_kernel<<<(4 * K + 255) / 256, 256, 0, s>>>(a.acc, 4 * K, absmax, dL_dtf);
     return cudaGetLastError();

@@ -680,8 +680,13 @@ static rc_status check_render_views(rc_context *ctx, const rc_volume *vol, const
     return st;
 }
 
-// The table gradient and the learned proposal march trilinear samples
-// classified by a 1-D table.
+// The table gradient: either reconstruction filter, a 1-D table.
+static rc_status check_gradient_form(rc_context *ctx, const char *who) {
+    if (ctx->M >= 2) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: 1-D transfer function only", who);
+    return RC_OK;
+}
+
+// The learned proposal marches trilinear samples classified by a 1-D table.
 static rc_status check_plain_form(rc_context *ctx, const rc_render_params *p, const char *who) {
     if (p->filter != RC_FILTER_TRILINEAR)
         return fail(ctx, RC_ERR_UNSUPPORTED, "%s: trilinear reconstruction only", who);
@@ -1020,7 +1025,7 @@ rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvo
 rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
                              const float *dL_dimage, float *dL_dtf) {
     rc_status st = check_render(ctx, vol, p, dL_dtf, "rc_render_backward");
-    if (st == RC_OK) st = check_plain_form(ctx, p, "rc_render_backward");
+    if (st == RC_OK) st = check_gradient_form(ctx, "rc_render_backward");
     if (st != RC_OK) return st;
     if (!dL_dimage) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_backward: dL_dimage is NULL");
     if (p->func != RC_FUNC_COMPOSITE)
@@ -1035,7 +1040,8 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_ren
         ctx->d_scratch = buf;
         ctx->scratch_bytes = need;
     }
-    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol), RC_FILTER_TRILINEAR);
+    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol), p->filter);
+    if (st == RC_OK) st = prepare_filter(ctx, const_cast<rc_volume *>(vol), p);
     if (st != RC_OK) return st;
     AdjointArgs a;
     a.m = march_args(ctx, vol, p, nullptr);
@@ -1053,7 +1059,7 @@ rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const 
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
     rc_status st = check_views(ctx, cams, nviews, who);
     if (st == RC_OK) st = check_render_views(ctx, vol, p, cams, dL_dtf, who);
-    if (st == RC_OK) st = check_plain_form(ctx, p, who);
+    if (st == RC_OK) st = check_gradient_form(ctx, who);
     if (st != RC_OK) return st;
     if (!dL_dimages) return fail(ctx, RC_ERR_INVALID_ARG, "%s: dL_dimages is NULL", who);
     if (p->func != RC_FUNC_COMPOSITE) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: compositing function only", who);
@@ -1068,7 +1074,8 @@ rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const 
         ctx->scratch_bytes = need;
     }
     rc_volume *v = const_cast<rc_volume *>(vol);
-    st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
+    st = ensure_occupancy(ctx, v, p->filter);
+    if (st == RC_OK) st = prepare_filter(ctx, v, p);
     if (st != RC_OK) return st;
     CamRec first;
     st = upload_views(ctx, v, cams, nviews, &first, who);
@@ -1125,7 +1132,7 @@ extern "C" {
 rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
                                      const float *dL_dimage, float *dL_dtf) {
     rc_status st = check_render(ctx, vol, p, dL_dtf, "rc_render_backward_noalloc");
-    if (st == RC_OK) st = check_plain_form(ctx, p, "rc_render_backward_noalloc");
+    if (st == RC_OK) st = check_gradient_form(ctx, "rc_render_backward_noalloc");
     if (st != RC_OK) return st;
     if (!dL_dimage) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_backward_noalloc: dL_dimage is NULL");
     if (p->func != RC_FUNC_COMPOSITE)
@@ -1138,7 +1145,7 @@ rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, cons
     long long *scratch = nullptr;
     st = noalloc_scratch(ctx, &scratch);
     if (st != RC_OK) return st;
-    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol), RC_FILTER_TRILINEAR);
+    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol), p->filter);   // no allocation: grids exist
     if (st != RC_OK) return st;
     AdjointArgs a;
     a.m = march_args(ctx, vol, p, nullptr);

@@ -44,14 +44,14 @@ def hidden_tf():
     return synth.random_tf(W["K"], W["hidden_tf_seed"], alpha_max=0.1)
 
 
-def gpu_grad(rc, ctx, vol, cam, tf, g, term, shade=False):
+def gpu_grad(rc, ctx, vol, cam, tf, g, term, shade=False, filt=0, noalloc=False):
     import torch
     rc.rc_tf_set(ctx, tf)
     rc.rc_camera_set(ctx, cam)
     gd = torch.from_numpy(g.astype(np.float32)).cuda()
     dtf = torch.empty((tf.shape[0], 4), device="cuda", dtype=torch.float32)
-    p = rc.RenderParams(step_vox=W["step"], term=term, shade=shade, skip=False)
-    rc.rc_render_backward(ctx, vol, p, gd, dtf)
+    p = rc.RenderParams(step_vox=W["step"], term=term, shade=shade, skip=False, filter=filt)
+    (rc.rc_render_backward_noalloc if noalloc else rc.rc_render_backward)(ctx, vol, p, gd, dtf)
     torch.cuda.synchronize()
     return dtf.cpu().numpy().astype(np.float64)
 
@@ -63,19 +63,25 @@ def seeded_upstream(seed, pixels, shape):
     return g
 
 
-@pytest.mark.parametrize("shade,term", [(False, 0.99), (False, 1.0), (True, 0.99)])
-def test_gradient_matches_oracle(rc, orc, c4, shade, term):
+@pytest.mark.parametrize("shade,term,bspline", [(False, 0.99, False), (False, 1.0, False), (True, 0.99, False),
+                                                (False, 0.99, True), (True, 0.99, True)])
+def test_gradient_matches_oracle(rc, orc, c4, shade, term, bspline):
+    """Against the FP64 oracle's reverse mode, with trilinear or cubic
+    B-spline reconstruction (the B-spline also through the entry point that
+    allocates nothing, which reads the apron bricks instead of the pairs)."""
     ph, ctx, vol, cams = c4
     tf = init_tf()
+    filt = rc.RC_FILTER_BSPLINE if bspline else rc.RC_FILTER_TRILINEAR
     total_g = np.zeros((W["K"], 4))
     total_o = np.zeros((W["K"], 4))
     for v, cam in enumerate(cams):
         pix = synth.sample_pixels(W["width"], W["height"], 4096, seed=400 + v)
-        sc = orc.Scene(ph.vol, ph.spacing, tf, cam, step=W["step"], term=term, shade=shade)
+        sc = orc.Scene(ph.vol, ph.spacing, tf, cam, step=W["step"], term=term, shade=shade,
+                       filter=orc.BSPLINE if bspline else orc.TRILINEAR)
         fwd = orc.render(sc, pixels=pix)
         keep = pix[~fwd["tie"]]                    # termination ties: either branch is right
         g = seeded_upstream(50 + v, keep, (W["height"], W["width"]))
-        total_g += gpu_grad(rc, ctx, vol, cam, tf, g, term, shade)
+        total_g += gpu_grad(rc, ctx, vol, cam, tf, g, term, shade, filt, noalloc=bspline and v % 2 == 1)
         og, _ = orc.render_grad(sc, g[keep], pixels=keep)
         total_o += og
     scale = np.abs(total_o).max()
