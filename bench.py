@@ -384,12 +384,30 @@ def adjoint_form(rc, ctx, flush, stream):
     torch.cuda.synchronize()
     f_ms = statistics.median(a.elapsed_time(b) for a, b, c in ev) / n
     b_ms = statistics.median(b.elapsed_time(c) for a, b, c in ev) / n
+    # the same with cubic B-spline reconstruction
+    Pb = rc.RenderParams(step_vox=wd["step"], term=wd["term"], shade=False, skip=False, filter=rc.RC_FILTER_BSPLINE)
+    rc.rc_render_backward_views(ctx, vol, Pb, cam_structs, G, dtf)       # builds the pair bricks
+    evb = []
+    for rep in range(3):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        rc.rc_render_views(ctx, vol, Pb, cam_structs, imgs)
+        e[1].record(stream)
+        rc.rc_render_backward_views(ctx, vol, Pb, cam_structs, G, dtf)
+        e[2].record(stream)
+        evb.append(e)
+        flush.zero_()
+    torch.cuda.synchronize()
+    fb_ms = statistics.median(a.elapsed_time(b) for a, b, c in evb) / n
+    bb_ms = statistics.median(b.elapsed_time(c) for a, b, c in evb) / n
     rc.rc_volume_destroy(ctx, vol)
     per_view = dense / len(cams)
     return {"workload": "diff_128x128x96", "views": len(cams), "image": "512x512",
             "forward_ms_per_view": f_ms, "backward_ms_per_view": b_ms, "backward_over_forward": b_ms / f_ms,
             "dense_samples_per_view": per_view,
             "backward_gsamples_s": 2 * per_view / (b_ms / 1e3) / 1e9,
+            "bspline": {"forward_ms_per_view": fb_ms, "backward_ms_per_view": bb_ms,
+                        "backward_over_forward": bb_ms / fb_ms},
             "note": "exact skipping in the forward recompute, none in the gradient pass (an empty brick still has a gradient)"}
 
 
