@@ -187,11 +187,12 @@ def ray_geometry(scene: Scene, x, y):
 
 
 def render_grad(scene: Scene, dimg, pixels=None, nthreads=None):
-    """dL/dTF (K x 4, FP64) of the compositing function for the upstream image
-    gradient dimg (per pixel RGBA); also returns the FP64 image. 1-D tables only."""
+    """dL/dTF (FP64, the table's shape: K x 4, or M x K x 4 for a 2-D table)
+    of the compositing function for the upstream image gradient dimg (per
+    pixel RGBA); also returns the FP64 image."""
     n = scene.npix(pixels)
     g = np.ascontiguousarray(np.asarray(dimg, dtype=np.float64).reshape(n, 4))
-    dtf = np.zeros((scene.tf.shape[0], 4)); rgba = np.zeros((n, 4))
+    dtf = np.zeros(scene.tf.shape[:-1] + (4,)); rgba = np.zeros((n, 4))
     arr, ptr = _pix(pixels)
     rc = lib().orc_render_grad(*scene.refs(), ptr, n, g.ctypes.data, dtf.ctypes.data,
                                rgba.ctypes.data, nthreads or default_threads())

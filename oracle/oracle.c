@@ -438,7 +438,8 @@ static void classify(const scene *S, double u, double rgba[4], int *i0, double *
  * coordinate, w = |grad f| (M-1) / gmax the gradient-magnitude coordinate; each
  * is clamped to its table axis and the four surrounding entries are blended
  * bilinearly (value direction first, then gradient direction). */
-static void classify2(const scene *S, double u, double w, double rgba[4]) {
+static void classify2(const scene *S, double u, double w, double rgba[4], int *i0, int *j0, double *a0,
+                      double *b0) {
     int K = S->K, M = S->M;
     double qu = u < 0.0 ? 0.0 : (u > (double)(K - 1) ? (double)(K - 1) : u);
     double qw = w < 0.0 ? 0.0 : (w > (double)(M - 1) ? (double)(M - 1) : w);
@@ -446,6 +447,10 @@ static void classify2(const scene *S, double u, double w, double rgba[4]) {
     if (i > K - 2) i = K - 2;
     if (j > M - 2) j = M - 2;
     double a = qu - (double)i, b = qw - (double)j;
+    *i0 = i;
+    *j0 = j;
+    *a0 = a;
+    *b0 = b;
     for (int c = 0; c < 4; c++) {
         double t00 = S->tf[4 * ((size_t)j * K + i) + c], t10 = S->tf[4 * ((size_t)j * K + i + 1) + c];
         double t01 = S->tf[4 * ((size_t)(j + 1) * K + i) + c], t11 = S->tf[4 * ((size_t)(j + 1) * K + i + 1) + c];
@@ -484,7 +489,8 @@ static double correct_alpha(double a, double ratio) { return 1.0 - pow(1.0 - a, 
 typedef struct {
     double t, p[3], v, u, rgba[4], a, col[3], dcol[3], w;
     double gm, gw;      /* |grad f| (value units per mm) and its table coordinate (2-D) */
-    int i;
+    double wb;          /* 2-D table: weight along the gradient axis (entry rows j, j + 1) */
+    int i, j;           /* table cell: value index i (and gradient row j for a 2-D table) */
 } sample;
 
 static void eval_sample(const scene *S, const ray *R, double t, double ratio, sample *s) {
@@ -501,11 +507,11 @@ static void eval_sample(const scene *S, const ray *R, double t, double ratio, sa
     }
     if (S->M >= 2) {
         s->gw = s->gm * S->gcoef;
-        classify2(S, s->u, s->gw, s->rgba);
-        s->i = -1;
-        s->w = 0.0;
+        classify2(S, s->u, s->gw, s->rgba, &s->i, &s->j, &s->w, &s->wb);
     } else {
         classify(S, s->u, s->rgba, &s->i, &s->w);
+        s->j = 0;
+        s->wb = 0.0;
     }
     s->a = correct_alpha(s->rgba[3], ratio);
     if (S->P.shade) {
@@ -807,7 +813,7 @@ static void grad_pixel(job *J, int64_t idx, int tid) {
     ray R;
     ray_setup(S, x, y, &R);
     double out[4] = {0, 0, 0, 0};
-    double *dtf = J->dtf_thread + (size_t)tid * S->K * 4;
+    double *dtf = J->dtf_thread + (size_t)tid * S->K * (S->M >= 2 ? S->M : 1) * 4;
     if (!R.hit) {
         if (J->rgba) for (int c = 0; c < 4; c++) J->rgba[4 * idx + c] = 0.0;
         return;
@@ -843,13 +849,27 @@ static void grad_pixel(job *J, int64_t idx, int tid) {
         G = s->a * gc + G * (1.0 - s->a);
         double ac = s->rgba[3] < 1.0 - 1e-6 ? s->rgba[3] : 1.0 - 1e-6;
         double dalpha = dA * ratio * pow(1.0 - ac, ratio - 1.0);
-        for (int c = 0; c < 3; c++) {
-            double dcol = g[c] * T[k] * s->a * s->dcol[c];
-            dtf[4 * s->i + c] += (1.0 - s->w) * dcol;
-            dtf[4 * (s->i + 1) + c] += s->w * dcol;
+        double d[4];
+        for (int c = 0; c < 3; c++) d[c] = g[c] * T[k] * s->a * s->dcol[c];
+        d[3] = dalpha;
+        /* the entries the sample interpolated, with their lerp weights:
+         * i, i + 1 of a 1-D table; (i, j) .. (i + 1, j + 1) of a 2-D one */
+        if (S->M >= 2) {
+            const size_t e00 = (size_t)s->j * S->K + s->i, e01 = e00 + S->K;
+            const double w00 = (1.0 - s->w) * (1.0 - s->wb), w10 = s->w * (1.0 - s->wb);
+            const double w01 = (1.0 - s->w) * s->wb, w11 = s->w * s->wb;
+            for (int c = 0; c < 4; c++) {
+                dtf[4 * e00 + c] += w00 * d[c];
+                dtf[4 * (e00 + 1) + c] += w10 * d[c];
+                dtf[4 * e01 + c] += w01 * d[c];
+                dtf[4 * (e01 + 1) + c] += w11 * d[c];
+            }
+        } else {
+            for (int c = 0; c < 4; c++) {
+                dtf[4 * s->i + c] += (1.0 - s->w) * d[c];
+                dtf[4 * (s->i + 1) + c] += s->w * d[c];
+            }
         }
-        dtf[4 * s->i + 3] += (1.0 - s->w) * dalpha;
-        dtf[4 * (s->i + 1) + 3] += s->w * dalpha;
     }
 }
 
@@ -859,7 +879,7 @@ int orc_render_grad(const orc_volume *vol, const orc_tf *tf, const orc_camera *c
     scene S;
     int rc = scene_init(&S, vol, tf, cam, prm);
     if (rc) { scene_free(&S); return rc; }
-    if (S.M >= 2) { scene_free(&S); return 3; }   /* gradient of 1-D tables only */
+    const size_t nent = (size_t)S.K * (S.M >= 2 ? S.M : 1);     /* table entries */
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     job J;
@@ -870,15 +890,15 @@ int orc_render_grad(const orc_volume *vol, const orc_tf *tf, const orc_camera *c
     J.fn = grad_pixel;
     J.dimg = dimg;
     J.rgba = rgba;
-    J.dtf_thread = (double *)calloc((size_t)nthreads * S.K * 4, sizeof(double));
+    J.dtf_thread = (double *)calloc((size_t)nthreads * nent * 4, sizeof(double));
     J.scratch = (sample **)calloc((size_t)nthreads, sizeof(sample *));
     J.cap = (int *)calloc((size_t)nthreads, sizeof(int));
     int ok = J.dtf_thread && J.scratch && J.cap;
     if (ok) {
         run_job(&J, nthreads, 1);
-        memset(dtf, 0, (size_t)S.K * 4 * sizeof(double));
+        memset(dtf, 0, nent * 4 * sizeof(double));
         for (int t = 0; t < nthreads; t++)
-            for (int i = 0; i < S.K * 4; i++) dtf[i] += J.dtf_thread[(size_t)t * S.K * 4 + i];
+            for (size_t i = 0; i < nent * 4; i++) dtf[i] += J.dtf_thread[(size_t)t * nent * 4 + i];
     }
     for (int t = 0; J.scratch && t < nthreads; t++) free(J.scratch[t]);
     free(J.scratch);

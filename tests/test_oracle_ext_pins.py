@@ -263,12 +263,45 @@ def test_tf2d_occupancy_is_sound(orc):
 
 
 def test_tf2d_rejected_where_undefined(orc):
-    """Thresholding and the table gradient are defined for 1-D tables only."""
+    """Thresholding is defined for 1-D tables only."""
     vol = np.full((8, 8, 8), 1000, dtype=np.uint16)
     cam = synth.orbit_camera((8, 8, 8), (1, 1, 1), 0.0, width=4, height=4)
     sc = orc.Scene(vol, (1, 1, 1), synth.tf2d_table(16, 4), cam, func=orc.THRESHOLD, iso=500, gmax=100.0)
     with pytest.raises(ValueError):
         orc.render(sc)
-    sc = orc.Scene(vol, (1, 1, 1), synth.tf2d_table(16, 4), cam, gmax=100.0)
-    with pytest.raises(ValueError):
-        orc.render_grad(sc, np.ones((16, 4)))
+
+
+@pytest.mark.parametrize("shade", [False, True])
+def test_tf2d_gradient_matches_finite_differences(orc, shade):
+    """The table gradient of a 2-D table (each sample scatters into the four
+    entries of its bilinear cell) against central differences of the render,
+    on the entries the rays use most and on unused ones (gradient 0)."""
+    ph = synth.head_phantom((30, 28, 22), (1, 1, 1.2), seed=37, tumor_radius_vox=4)
+    tab = synth.tf2d_table(64, 8, 1200.0)
+    tab = (0.05 + 0.9 * tab).astype(np.float32)           # entries strictly inside (0, 1)
+    tab[..., 3] *= 0.3
+    cam = synth.orbit_camera(ph.dims, ph.spacing, 40.0, width=14, height=12)
+    dimg = np.random.default_rng(5).normal(size=(14 * 12, 4))
+
+    def loss(t):
+        sc = orc.Scene(ph.vol, ph.spacing, t, cam, term=1.0, shade=shade, gmax=1200.0)
+        return float((orc.render(sc)["rgba"].reshape(-1, 4) * dimg).sum())
+
+    sc = orc.Scene(ph.vol, ph.spacing, tab, cam, term=1.0, shade=shade, gmax=1200.0)
+    dtf, _ = orc.render_grad(sc, dimg)
+    assert dtf.shape == (8, 64, 4)
+    flat = np.abs(dtf).sum(axis=2).ravel()
+    used = [divmod(int(e), 64) for e in np.argsort(-flat)[:5]]
+    unused = [divmod(int(e), 64) for e in np.nonzero(flat == 0)[0][:2]]
+    assert len(unused) == 2
+    h = 1e-3
+    checked = 0
+    for (j, i) in used + unused:
+        for c in range(4):
+            tp = tab.astype(np.float64).copy(); tp[j, i, c] += h
+            tm = tab.astype(np.float64).copy(); tm[j, i, c] -= h
+            fd = (loss(tp.astype(np.float32)) - loss(tm.astype(np.float32))) / (
+                float(np.float32(tp[j, i, c])) - float(np.float32(tm[j, i, c])))
+            assert dtf[j, i, c] == pytest.approx(fd, rel=2e-3, abs=1e-6)
+            checked += 1
+    assert checked == 28
