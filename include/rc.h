@@ -244,9 +244,13 @@ rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvo
 /* Gradient of a loss with respect to the transfer function entries, given the
  * gradient of the loss with respect to the composited image (Eq. 4-5 are
  * differentiable in the table). dL_dimage: device, width*height*4 floats;
- * dL_dtf: device, n_entries*4 floats, overwritten. Compositing function and
- * a 1-D table only (RC_ERR_UNSUPPORTED for a 2-D table); trilinear or cubic
- * B-spline reconstruction. The gradient pass does not skip empty space (an
+ * dL_dtf: device, 4 floats per table entry (K*4 for a 1-D table, M*K*4 for
+ * a 2-D table, row-major like the table), overwritten. Compositing function
+ * only; trilinear or cubic B-spline reconstruction. A 2-D table's gradient
+ * flows into the four entries of each sample's bilinear cell (value and
+ * gradient-magnitude weights); the gradient-magnitude coordinate itself is
+ * not differentiated (it does not depend on the table). The gradient pass
+ * does not skip empty space (an
  * empty brick still has a gradient). The forward march is recomputed per ray;
  * nothing is stored per sample. The result does not depend on thread
  * scheduling (fixed-point accumulation). */
@@ -270,7 +274,7 @@ rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const 
  * The paper has no counterpart; this is a service of the library.
  * Same arguments and result as rc_render_backward. It allocates nothing: the
  * fixed-point accumulators live in one file-scope device array sized for
- * tables of at most 1024 entries (32 KB + 256 B, held on every GPU that loads
+ * tables of at most 1024 entries, K or M*K (32 KB + 256 B, held on every GPU that loads
  * the library until the process exits); a larger table returns
  * RC_ERR_UNSUPPORTED. The first call on a device looks up that array's device
  * address (and may load the library's device code), so make the first call

@@ -41,10 +41,11 @@ __device__ __forceinline__ void acc_add(unsigned long long *acc, int idx, float 
     if (q != 0) atomicAdd(acc + idx, (unsigned long long)q);
 }
 
-// Sum of v over the lanes of this lane's group (lanes with the same key), in a
+// Sum of v (N values) over the lanes of this lane's group (lanes with the same key), in a
 // fixed pairwise-tree order over the group's lanes sorted by lane id; the sum
 // ends in the group's lowest lane (rank 0). Deterministic for a given key set.
-__device__ __forceinline__ void group_sum8(unsigned peers, float (&v)[8]) {
+template <int N>
+__device__ __forceinline__ void group_sum(unsigned peers, float (&v)[N]) {
     const int lane = threadIdx.x & 31;
     const int cnt = __popc(peers);
     const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -57,7 +58,7 @@ __device__ __forceinline__ void group_sum8(unsigned peers, float (&v)[8]) {
         const bool take = (rank % (2 * s)) == 0 && rank + s < cnt;
         const int src = take ? nxt : lane;
 #pragma unroll
-        for (int c = 0; c < 8; c++) {
+        for (int c = 0; c < N; c++) {
             const float o = __shfl_sync(0xffffffffu, v[c], src);
             if (take) v[c] += o;
         }
@@ -69,9 +70,10 @@ __device__ __forceinline__ void group_sum8(unsigned peers, float (&v)[8]) {
 // x = 1 - a >= 1e-6: r = 1/2 and 1/4 as reciprocal square roots, else
 // through log2 / exp2.
 template <int RM>
-__device__ __forceinline__ float dalpha_factor(float x, float ratio) {
-    if (RM == 1) return 0.5f * rsqrtf(x);
-    if (RM == 2) {
+__device__ __forceinline__ float dalpha_factor(float x, float ratio, int rmode) {
+    const int m = RM >= 0 ? RM : rmode;
+    if (m == 1) return 0.5f * rsqrtf(x);
+    if (m == 2) {
         const float q = rsqrtf(x);
         return 0.25f * q * sqrtf(q);
     }
@@ -80,16 +82,24 @@ __device__ __forceinline__ float dalpha_factor(float x, float ratio) {
 
 // CUBIC: cubic B-spline reconstruction (value and analytic gradient) instead
 // of trilinear values and central differences; the table scatter is the same.
-template <int ST, bool SHADE, int RM, bool CUBIC>
+// TF2: a 2-D table over (value, gradient magnitude) in global memory; each
+// sample scatters into the four entries of its bilinear cell, and the group
+// leaders add to the global fixed-point accumulators directly (the M x K
+// table's accumulators do not fit in shared memory).
+template <int ST, bool SHADE, int RM, bool CUBIC, bool TF2>
 __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const float *absmax) {
     const MarchArgs &a = A.m;
     const int K = a.tf.K;
+    constexpr bool GRAD = SHADE || TF2;
+    constexpr int NV = TF2 ? 16 : 8;                  // contributions per sample
     extern __shared__ float4 smem[];
     float4 *s_tf = smem;
     unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(smem + K);
-    load_tf(a.tf, s_tf);
-    for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) s_acc[e] = 0ull;
-    __syncthreads();
+    if (!TF2) {
+        load_tf(a.tf, s_tf);
+        for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) s_acc[e] = 0ull;
+        __syncthreads();
+    }
     const float scale = fixed_scale(absmax);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const CamRec cam = a.cams ? a.cams[blockIdx.z] : a.cam;
@@ -119,7 +129,8 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
                 k = jump_block(R, a.vol, c, k, s);
                 continue;
             }
-            float4 e = eval_sample_x<ST, (SHADE ? kShade : 0) | (CUBIC ? kCubic : 0), RM>(a.vol, a.p, s_tf, a.tf,
+            float4 e = eval_sample_x<ST, (SHADE ? kShade : 0) | (CUBIC ? kCubic : 0) | (TF2 ? kTF2 : 0), RM>(
+                a.vol, a.p, s_tf, a.tf,
                                                                                           R.dir, c, a.p.rmode,
                                                                a.p.ratio);
             composite_add(e, Cf0, Cf1, Cf2, Tf);
@@ -136,16 +147,25 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
     for (int k = 0; __any_sync(0xffffffffu, k < n); k++) {
         const bool active = k < n;
         int i = -1;
-        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        float v[NV];
+#pragma unroll
+        for (int c = 0; c < NV; c++) v[c] = 0.0f;
         if (active) {
             float p[3], gr[3], val;
             position_at(R, sample_t(R, k), p);
             Cell c;
             cell_of(a.vol, p, c);
-            if (CUBIC) val = SHADE ? bspline_grad<ST>(a.vol, c, gr) : bspline<ST>(a.vol, c);
-            else val = SHADE ? value_grad<ST>(a.vol, c, gr) : trilinear<ST>(a.vol, c);
-            float w;
-            float4 e = classify(s_tf, K, tf_coord(val, a.tf.ucoef), &i, &w);
+            if (CUBIC) val = GRAD ? bspline_grad<ST>(a.vol, c, gr) : bspline<ST>(a.vol, c);
+            else val = GRAD ? value_grad<ST>(a.vol, c, gr) : trilinear<ST>(a.vol, c);
+            float w, wb = 0.0f;
+            float4 e;
+            if (TF2) {
+                int j;
+                e = classify2_at(a.tf, tf_coord(val, a.tf.ucoef), tf2_row_coord(a.tf, gr), i, j, w, wb);
+                i += j * K;                           // entry (i, j) of the M x K table
+            } else {
+                e = classify(s_tf, K, tf_coord(val, a.tf.ucoef), &i, &w);
+            }
             float ap = correct_alpha<RM>(e.w, a.p.rmode, a.p.ratio);
             float r = e.x, gg = e.y, b = e.z;
             float d0 = 1.0f, d1 = 1.0f, d2 = 1.0f;
@@ -171,24 +191,44 @@ __global__ void __launch_bounds__(128) adjoint_kernel(const AdjointArgs A, const
             float dap = g.x * (Tk * r - (Cf0 - C0) * inv) + g.y * (Tk * gg - (Cf1 - C1) * inv) +
                         g.z * (Tk * b - (Cf2 - C2) * inv) + g.w * (Tk - (T - Tf) * inv);
             float ac = fminf(e.w, 1.0f - 1e-6f);
-            const float dal = RM == 0 ? dap : dap * dalpha_factor<RM>(1.0f - ac, a.p.ratio);
+            const int m = RM >= 0 ? RM : a.p.rmode;
+            const float dal = m == 0 ? dap : dap * dalpha_factor<RM>(1.0f - ac, a.p.ratio, m);
             float dr = g.x * ta * d0, dg = g.y * ta * d1, db = g.z * ta * d2;
+            // bilinear weights of the cell's entries: (i, j), (i + 1, j), then
+            // the next row (i, j + 1), (i + 1, j + 1) for a 2-D table
             const float w0 = 1.0f - w;
-            v[0] = w0 * dr; v[1] = w0 * dg; v[2] = w0 * db; v[3] = w0 * dal;
-            v[4] = w * dr;  v[5] = w * dg;  v[6] = w * db;  v[7] = w * dal;
+            const float wr[4] = {w0 * (1.0f - wb), w * (1.0f - wb), w0 * wb, w * wb};
+#pragma unroll
+            for (int q = 0; q < NV / 4; q++) {
+                v[4 * q + 0] = wr[q] * dr;
+                v[4 * q + 1] = wr[q] * dg;
+                v[4 * q + 2] = wr[q] * db;
+                v[4 * q + 3] = wr[q] * dal;
+            }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, active ? i : -1 - lane);
-        group_sum8(peers, v);
+        group_sum<NV>(peers, v);
         const bool leader = active && (peers & ((1u << lane) - 1u)) == 0u;
         if (leader) {
+            if (TF2) {
+                unsigned long long *g_acc = reinterpret_cast<unsigned long long *>(A.acc);
 #pragma unroll
-            for (int c = 0; c < 8; c++) acc_add(s_acc, 4 * i + c, v[c], scale);
+                for (int c = 0; c < 8; c++) {
+                    acc_add(g_acc, 4 * i + c, v[c], scale);
+                    acc_add(g_acc, 4 * (i + K) + c, v[8 + c], scale);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; c++) acc_add(s_acc, 4 * i + c, v[c], scale);
+            }
         }
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) {
-        unsigned long long v = s_acc[e];
-        if (v != 0ull) atomicAdd(reinterpret_cast<unsigned long long *>(A.acc) + e, v);
+    if (!TF2) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) {
+            unsigned long long v = s_acc[e];
+            if (v != 0ull) atomicAdd(reinterpret_cast<unsigned long long *>(A.acc) + e, v);
+        }
     }
 }
 
@@ -201,7 +241,8 @@ __global__ void finalize_kernel(const long long *acc, int n, const float *absmax
 
 template <typename Kern>
 static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
-    size_t smem = (size_t)a.m.tf.K * (sizeof(float4) + 4 * sizeof(long long));
+    // the 1-D table and its accumulators in shared memory; none for a 2-D table
+    size_t smem = a.m.tf.M >= 2 ? 0 : (size_t)a.m.tf.K * (sizeof(float4) + 4 * sizeof(long long));
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -212,44 +253,52 @@ static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, int nviews, const
 }
 
 // The instance for the volume's storage, shading, opacity-correction mode RM
-// and reconstruction filter.
-template <int RM, bool CUBIC>
+// (RM = -1: read at run time) and reconstruction filter.
+template <int RM, bool CUBIC, bool TF2>
 static cudaError_t launch_adj_rm(const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
     switch (a.m.vol.storage * 2 + (a.m.p.shade ? 1 : 0)) {
-        case RC_STORE_F32 * 2: return launch_adj(adjoint_kernel<RC_STORE_F32, false, RM, CUBIC>, a, nviews, absmax, s);
-        case RC_STORE_F32 * 2 + 1: return launch_adj(adjoint_kernel<RC_STORE_F32, true, RM, CUBIC>, a, nviews, absmax, s);
-        case RC_STORE_F16 * 2: return launch_adj(adjoint_kernel<RC_STORE_F16, false, RM, CUBIC>, a, nviews, absmax, s);
-        case RC_STORE_F16 * 2 + 1: return launch_adj(adjoint_kernel<RC_STORE_F16, true, RM, CUBIC>, a, nviews, absmax, s);
-        case RC_STORE_U16 * 2: return launch_adj(adjoint_kernel<RC_STORE_U16, false, RM, CUBIC>, a, nviews, absmax, s);
-        default: return launch_adj(adjoint_kernel<RC_STORE_U16, true, RM, CUBIC>, a, nviews, absmax, s);
+        case RC_STORE_F32 * 2:
+            return launch_adj(adjoint_kernel<RC_STORE_F32, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
+        case RC_STORE_F32 * 2 + 1:
+            return launch_adj(adjoint_kernel<RC_STORE_F32, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
+        case RC_STORE_F16 * 2:
+            return launch_adj(adjoint_kernel<RC_STORE_F16, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
+        case RC_STORE_F16 * 2 + 1:
+            return launch_adj(adjoint_kernel<RC_STORE_F16, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
+        case RC_STORE_U16 * 2:
+            return launch_adj(adjoint_kernel<RC_STORE_U16, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
+        default: return launch_adj(adjoint_kernel<RC_STORE_U16, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
     }
 }
 
+// 1-D tables: one instance per opacity-correction mode; 2-D tables: the mode
+// read at run time (the table lookup and the global atomics dominate there).
 template <bool CUBIC>
 static cudaError_t launch_adj_filter(const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
+    if (a.m.tf.M >= 2) return launch_adj_rm<-1, CUBIC, true>(a, nviews, absmax, s);
     switch (a.m.p.rmode) {
-        case 0: return launch_adj_rm<0, CUBIC>(a, nviews, absmax, s);
-        case 1: return launch_adj_rm<1, CUBIC>(a, nviews, absmax, s);
-        case 2: return launch_adj_rm<2, CUBIC>(a, nviews, absmax, s);
-        default: return launch_adj_rm<3, CUBIC>(a, nviews, absmax, s);
+        case 0: return launch_adj_rm<0, CUBIC, false>(a, nviews, absmax, s);
+        case 1: return launch_adj_rm<1, CUBIC, false>(a, nviews, absmax, s);
+        case 2: return launch_adj_rm<2, CUBIC, false>(a, nviews, absmax, s);
+        default: return launch_adj_rm<3, CUBIC, false>(a, nviews, absmax, s);
     }
 }
 
-// acc must hold 4K long longs followed by one float (the |dL/dI| maximum).
-// With a.m.cams, nviews views (grid.z), dimg view-major; the gradient is the
-// sum over the views.
+// acc must hold 4 K max(M, 1) long longs (one per table entry and channel)
+// followed by one float (the |dL/dI| maximum). With a.m.cams, nviews views
+// (grid.z), dimg view-major; the gradient is the sum over the views.
 cudaError_t launch_adjoint(const AdjointArgs &a, int nviews, float *dL_dtf, cudaStream_t s) {
-    const int K = a.m.tf.K;
-    float *absmax = reinterpret_cast<float *>(a.acc + 4 * K);
+    const int nent = a.m.tf.K * (a.m.tf.M >= 2 ? a.m.tf.M : 1);
+    float *absmax = reinterpret_cast<float *>(a.acc + 4 * (size_t)nent);
     cudaError_t e = launch_absmax(reinterpret_cast<const float *>(a.dimg),
                                   (long long)nviews * a.m.cam.W * a.m.cam.H * 4, absmax, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * K, s);
+    e = cudaMemsetAsync(a.acc, 0, sizeof(long long) * 4 * (size_t)nent, s);
     if (e != cudaSuccess) return e;
     e = a.m.p.filter == RC_FILTER_BSPLINE ? launch_adj_filter<true>(a, nviews, absmax, s)
                                           : launch_adj_filter<false>(a, nviews, absmax, s);
     if (e != cudaSuccess) return e;
-    finalize_kernel<<<(4 * K + 255) / 256, 256, 0, s>>>(a.acc, 4 * K, absmax, dL_dtf);
+    finalize_kernel<<<(4 * nent + 255) / 256, 256, 0, s>>>(a.acc, 4 * nent, absmax, dL_dtf);
     return cudaGetLastError();
 }
 

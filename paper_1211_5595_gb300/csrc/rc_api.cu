@@ -680,10 +680,9 @@ static rc_status check_render_views(rc_context *ctx, const rc_volume *vol, const
     return st;
 }
 
-// The table gradient: either reconstruction filter, a 1-D table.
-static rc_status check_gradient_form(rc_context *ctx, const char *who) {
-    if (ctx->M >= 2) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: 1-D transfer function only", who);
-    return RC_OK;
+// Entries of the current table: K for a 1-D table, M x K for a 2-D one.
+static size_t tf_entries(const rc_context *ctx) {
+    return (size_t)ctx->K * (ctx->M >= 2 ? ctx->M : 1);
 }
 
 // The learned proposal marches trilinear samples classified by a 1-D table.
@@ -1025,13 +1024,12 @@ rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvo
 rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
                              const float *dL_dimage, float *dL_dtf) {
     rc_status st = check_render(ctx, vol, p, dL_dtf, "rc_render_backward");
-    if (st == RC_OK) st = check_gradient_form(ctx, "rc_render_backward");
     if (st != RC_OK) return st;
     if (!dL_dimage) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_backward: dL_dimage is NULL");
     if (p->func != RC_FUNC_COMPOSITE)
         return fail(ctx, RC_ERR_UNSUPPORTED, "rc_render_backward: compositing function only");
     DeviceScope ds(ctx->device);
-    size_t need = (size_t)4 * ctx->K * sizeof(long long) + 16;
+    size_t need = 4 * tf_entries(ctx) * sizeof(long long) + 16;
     if (ctx->scratch_bytes < need) {
         void *buf = nullptr;
         RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1059,12 +1057,11 @@ rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const 
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
     rc_status st = check_views(ctx, cams, nviews, who);
     if (st == RC_OK) st = check_render_views(ctx, vol, p, cams, dL_dtf, who);
-    if (st == RC_OK) st = check_gradient_form(ctx, who);
     if (st != RC_OK) return st;
     if (!dL_dimages) return fail(ctx, RC_ERR_INVALID_ARG, "%s: dL_dimages is NULL", who);
     if (p->func != RC_FUNC_COMPOSITE) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: compositing function only", who);
     DeviceScope ds(ctx->device);
-    size_t need = (size_t)4 * ctx->K * sizeof(long long) + 16;
+    size_t need = 4 * tf_entries(ctx) * sizeof(long long) + 16;
     if (ctx->scratch_bytes < need) {
         void *buf = nullptr;
         RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1097,7 +1094,7 @@ rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const 
 // ---------------------------------------------------------------------------
 // transfer-function gradient without device allocation
 // ---------------------------------------------------------------------------
-// Scratch of rc_render_backward_noalloc: the 4K fixed-point accumulators and
+// Scratch of rc_render_backward_noalloc: the 4 per entry fixed-point accumulators and
 // the |dL/dI| maximum for tables of at most kNoAllocMaxEntries entries. It is a
 // file-scope device array, so every GPU that loads this library holds it
 // (32 KB + 256 B) until the process exits. Host code must not use the symbol
@@ -1132,15 +1129,14 @@ extern "C" {
 rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
                                      const float *dL_dimage, float *dL_dtf) {
     rc_status st = check_render(ctx, vol, p, dL_dtf, "rc_render_backward_noalloc");
-    if (st == RC_OK) st = check_gradient_form(ctx, "rc_render_backward_noalloc");
     if (st != RC_OK) return st;
     if (!dL_dimage) return fail(ctx, RC_ERR_INVALID_ARG, "rc_render_backward_noalloc: dL_dimage is NULL");
     if (p->func != RC_FUNC_COMPOSITE)
         return fail(ctx, RC_ERR_UNSUPPORTED, "rc_render_backward_noalloc: compositing function only");
-    if (ctx->K > kNoAllocMaxEntries)
+    if (tf_entries(ctx) > (size_t)kNoAllocMaxEntries)
         return fail(ctx, RC_ERR_UNSUPPORTED,
-                    "rc_render_backward_noalloc: table of %d entries exceeds the static scratch (at most %d)",
-                    ctx->K, kNoAllocMaxEntries);
+                    "rc_render_backward_noalloc: table of %zu entries exceeds the static scratch (at most %d)",
+                    tf_entries(ctx), kNoAllocMaxEntries);
     DeviceScope ds(ctx->device);
     long long *scratch = nullptr;
     st = noalloc_scratch(ctx, &scratch);

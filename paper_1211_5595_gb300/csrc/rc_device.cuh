@@ -483,17 +483,33 @@ __device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, in
 // coordinate, w = fl(|grad| * wcoef) the gradient coordinate, each clamped to
 // its axis; bilinear over the four entries (value direction first). The
 // table stays in global memory (read-only path; at most a few MB).
-__device__ __forceinline__ float4 classify2(const TFDev &tf, float u, float w) {
+// The bilinear cell (i, j) and weights (a, b) are returned for the gradient.
+__device__ __forceinline__ float4 classify2_at(const TFDev &tf, float u, float w, int &i, int &j, float &a,
+                                               float &b) {
     const int K = tf.K, M = tf.M;
     const float qu = fminf(fmaxf(u, 0.0f), (float)(K - 1));
     const float qw = fminf(fmaxf(w, 0.0f), (float)(M - 1));
-    const int i = min((int)qu, K - 2), j = min((int)qw, M - 2);
-    const float a = qu - (float)i, b = qw - (float)j;
+    i = min((int)qu, K - 2);
+    j = min((int)qw, M - 2);
+    a = qu - (float)i;
+    b = qw - (float)j;
     const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(tf.tab2) + (size_t)j * K + i;
     const unsigned long long A = pack2(a, a);
     const ulonglong2 r0 = lerp4p(__ldg(p), __ldg(p + 1), A);
     const ulonglong2 r1 = lerp4p(__ldg(p + K), __ldg(p + K + 1), A);
     return unpack4(lerp4p(r0, r1, pack2(b, b)));
+}
+
+__device__ __forceinline__ float4 classify2(const TFDev &tf, float u, float w) {
+    int i, j;
+    float a, b;
+    return classify2_at(tf, u, w, i, j, a, b);
+}
+
+// The gradient-magnitude coordinate of a 2-D table: fl(|g| * wcoef).
+__device__ __forceinline__ float tf2_row_coord(const TFDev &tf, const float g[3]) {
+    const float gm = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    return __fmul_rn(gm, tf.wcoef);
 }
 
 // Eq. 3 for a segment of length ds: alpha' = 1 - (1 - alpha)^(ds/ds_ref).
@@ -567,8 +583,7 @@ __device__ __forceinline__ float4 eval_sample_x(const VolDev &vol, const MarchPa
     }
     float4 e;
     if (TF2) {
-        const float gm = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-        e = classify2(tf, tf_coord(val, tf.ucoef), __fmul_rn(gm, tf.wcoef));
+        e = classify2(tf, tf_coord(val, tf.ucoef), tf2_row_coord(tf, g));
     } else {
         e = classify(s_tf, tf.K, tf_coord(val, tf.ucoef));
     }

@@ -1,8 +1,9 @@
 """Differentiable form: the hand-written transfer-function adjoint on a
 128x128x96 phantom, 8 views at 512^2, checked against the FP64 oracle gradient
 and against central finite differences (h = 1e-3, FP64 oracle) on 32 table
-entries; determinism; the autograd wrapper; and a table fit that lowers the
-L2 loss against images rendered with a hidden seeded table."""
+entries; the gradient of a 2-D table; determinism; the autograd wrapper; and a
+table fit that lowers the L2 loss against images rendered with a hidden seeded
+table."""
 import numpy as np
 import pytest
 
@@ -120,6 +121,86 @@ def test_views_gradient_matches_oracle_and_single_views(rc, orc, c4):
     assert np.abs(got - total_1).max() / scale < 1e-5
     # deterministic
     rc.rc_render_backward_views(ctx, vol, p, cams, G, dtf)
+    torch.cuda.synchronize()
+    assert np.array_equal(dtf.cpu().numpy().astype(np.float64), got)
+
+
+GMAX = 1200.0
+
+
+def init_tf2d(M):
+    """The seeded noise table repeated over M gradient-magnitude rows, its
+    opacity rising and its blue falling with the row, so that every row
+    carries a different gradient."""
+    g = np.arange(M, dtype=np.float64)[:, None] / (M - 1)
+    tab = np.repeat(init_tf().astype(np.float64)[None], M, axis=0)
+    tab[..., 3] *= 0.4 + 0.6 * g
+    tab[..., 2] *= 1.0 - 0.4 * g
+    return np.clip(tab, 0.0, 1.0).astype(np.float32)
+
+
+@pytest.mark.parametrize("shade,bspline,M", [(False, False, 8), (True, False, 8), (True, True, 8),
+                                             (False, False, 4)])
+def test_tf2d_gradient_matches_oracle(rc, orc, c4, shade, bspline, M):
+    """The gradient of a 2-D (value x gradient magnitude) table against the
+    FP64 oracle's reverse mode, summed over four views; M = 4 (1024 entries,
+    the largest table the non-allocating entry point takes) goes through
+    that entry point."""
+    import torch
+    ph, ctx, vol, cams = c4
+    tab = init_tf2d(M)
+    term = 0.99
+    filt = rc.RC_FILTER_BSPLINE if bspline else rc.RC_FILTER_TRILINEAR
+    noalloc = M * W["K"] <= 1024
+    total_g = np.zeros((M, W["K"], 4))
+    total_o = np.zeros((M, W["K"], 4))
+    rc.rc_tf2d_set(ctx, tab, GMAX)
+    for v, cam in enumerate(cams[:4]):
+        pix = synth.sample_pixels(W["width"], W["height"], 4096, seed=1400 + v)
+        sc = orc.Scene(ph.vol, ph.spacing, tab, cam, step=W["step"], term=term, shade=shade,
+                       filter=orc.BSPLINE if bspline else orc.TRILINEAR, gmax=GMAX)
+        keep = pix[~orc.render(sc, pixels=pix)["tie"]]
+        g = seeded_upstream(1450 + v, keep, (W["height"], W["width"]))
+        og, _ = orc.render_grad(sc, g[keep], pixels=keep)
+        assert og.shape == (M, W["K"], 4)
+        total_o += og
+        rc.rc_camera_set(ctx, cam)
+        gd = torch.from_numpy(g.astype(np.float32)).cuda()
+        dtf = torch.empty((M, W["K"], 4), device="cuda", dtype=torch.float32)
+        p = rc.RenderParams(step_vox=W["step"], term=term, shade=shade, skip=False, filter=filt)
+        (rc.rc_render_backward_noalloc if noalloc else rc.rc_render_backward)(ctx, vol, p, gd, dtf)
+        torch.cuda.synchronize()
+        total_g += dtf.cpu().numpy().astype(np.float64)
+    scale = np.abs(total_o).max()
+    err = np.abs(total_g - total_o).max() / scale
+    assert err < 2e-4, f"relative gradient error {err:.2e}"
+    # the gradient reaches several rows of the table
+    assert (np.abs(total_o).sum(axis=(1, 2)) > 1e-3 * scale).sum() >= 3
+
+
+def test_tf2d_views_gradient_is_the_sum_and_deterministic(rc, c4):
+    """One launch over the views of a 2-D table equals the sum of the
+    single-view gradients (to the fixed-point resolution) and repeats bit for bit."""
+    import torch
+    ph, ctx, vol, cams = c4
+    tab = init_tf2d(8)
+    rc.rc_tf2d_set(ctx, tab, GMAX)
+    rng = np.random.default_rng(12)
+    gs = [rng.normal(size=(W["height"], W["width"], 4)).astype(np.float32) for _ in cams[:3]]
+    p = rc.RenderParams(step_vox=W["step"], term=0.99, shade=True, skip=False)
+    total = np.zeros((8, W["K"], 4))
+    dtf = torch.empty((8, W["K"], 4), device="cuda", dtype=torch.float32)
+    for cam, g in zip(cams, gs):
+        rc.rc_camera_set(ctx, cam)
+        rc.rc_render_backward(ctx, vol, p, torch.from_numpy(g).cuda(), dtf)
+        torch.cuda.synchronize()
+        total += dtf.cpu().numpy()
+    G = torch.from_numpy(np.stack(gs)).cuda()
+    rc.rc_render_backward_views(ctx, vol, p, cams[:3], G, dtf)
+    torch.cuda.synchronize()
+    got = dtf.cpu().numpy().astype(np.float64)
+    assert np.abs(got - total).max() / np.abs(total).max() < 1e-5
+    rc.rc_render_backward_views(ctx, vol, p, cams[:3], G, dtf)
     torch.cuda.synchronize()
     assert np.array_equal(dtf.cpu().numpy().astype(np.float64), got)
 

@@ -251,8 +251,9 @@ def test_full_workload_sampled(rc, orc):
 
 
 def test_unsupported_forms(rc, small):
-    """The learned proposal takes trilinear samples and 1-D tables; the table
-    gradient and thresholding take 1-D tables (the gradient either filter)."""
+    """The learned proposal takes trilinear samples and 1-D tables;
+    thresholding takes 1-D tables; the non-allocating table gradient takes
+    at most 1024 entries (here 8 x 256)."""
     import torch
     ph, r = small
     cam = synth.orbit_camera(ph.dims, ph.spacing, 0.0, width=32, height=24)
@@ -266,7 +267,8 @@ def test_unsupported_forms(rc, small):
         rc.rc_proposal_features(r.ctx, r.vol, dict(filter=1), feat)
     assert ei.value.status == rc.RC_ERR_UNSUPPORTED
     rc.rc_tf2d_set(r.ctx, synth.tf2d_table(256, 8, GMAX), GMAX)
-    for call in (lambda: rc.rc_render_backward(r.ctx, r.vol, dict(), g, dtf),
+    dtf2 = torch.empty((8, 256, 4), device="cuda")
+    for call in (lambda: rc.rc_render_backward_noalloc(r.ctx, r.vol, dict(), g, dtf2),
                  lambda: rc.rc_render(r.ctx, r.vol, dict(func=rc.RC_FUNC_THRESHOLD, iso=100.0), out),
                  lambda: rc.rc_proposal_features(r.ctx, r.vol, dict(), feat)):
         with pytest.raises(rc.RCError) as ei:
