@@ -370,36 +370,36 @@ def adjoint_form(rc, ctx, flush, stream):
     cam_structs = [rc.make_camera(c) for c in cams]
     imgs = torch.empty((n, wd["height"], wd["width"], 4), device="cuda")
     G = torch.randn(imgs.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
-    ev = []
-    for rep in range(4):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record(stream)
-        rc.rc_render_views(ctx, vol, P, cam_structs, imgs)
-        e[1].record(stream)
-        rc.rc_render_backward_views(ctx, vol, P, cam_structs, G, dtf)
-        e[2].record(stream)
-        if rep > 0:
+
+    def pair_ms(Pf, dt, reps):
+        """Median forward and backward time per view over reps runs."""
+        rc.rc_render_backward_views(ctx, vol, Pf, cam_structs, G, dt)    # builds what the form needs
+        ev = []
+        for rep in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            rc.rc_render_views(ctx, vol, Pf, cam_structs, imgs)
+            e[1].record(stream)
+            rc.rc_render_backward_views(ctx, vol, Pf, cam_structs, G, dt)
+            e[2].record(stream)
             ev.append(e)
-        flush.zero_()
-    torch.cuda.synchronize()
-    f_ms = statistics.median(a.elapsed_time(b) for a, b, c in ev) / n
-    b_ms = statistics.median(b.elapsed_time(c) for a, b, c in ev) / n
+            flush.zero_()
+        torch.cuda.synchronize()
+        return (statistics.median(a.elapsed_time(b) for a, b, c in ev) / n,
+                statistics.median(b.elapsed_time(c) for a, b, c in ev) / n)
+
+    f_ms, b_ms = pair_ms(P, dtf, 3)
     # the same with cubic B-spline reconstruction
     Pb = rc.RenderParams(step_vox=wd["step"], term=wd["term"], shade=False, skip=False, filter=rc.RC_FILTER_BSPLINE)
-    rc.rc_render_backward_views(ctx, vol, Pb, cam_structs, G, dtf)       # builds the pair bricks
-    evb = []
-    for rep in range(3):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record(stream)
-        rc.rc_render_views(ctx, vol, Pb, cam_structs, imgs)
-        e[1].record(stream)
-        rc.rc_render_backward_views(ctx, vol, Pb, cam_structs, G, dtf)
-        e[2].record(stream)
-        evb.append(e)
-        flush.zero_()
-    torch.cuda.synchronize()
-    fb_ms = statistics.median(a.elapsed_time(b) for a, b, c in evb) / n
-    bb_ms = statistics.median(b.elapsed_time(c) for a, b, c in evb) / n
+    fb_ms, bb_ms = pair_ms(Pb, dtf, 3)
+    # a 2-D table (the same rows, opacity rising with gradient magnitude):
+    # the gradient scatters into four entries per sample in global memory
+    M2 = 32
+    tab2 = np.repeat(synth.noise_tf(wd["K"], wd["init_tf_seed"], alpha_max=0.1)[None], M2, axis=0)
+    tab2[..., 3] *= np.linspace(0.4, 1.0, M2, dtype=np.float32)[:, None]
+    rc.rc_tf2d_set(ctx, tab2, 1200.0)
+    dtf2 = torch.empty((M2, wd["K"], 4), device="cuda")
+    f2_ms, b2_ms = pair_ms(P, dtf2, 3)
     rc.rc_volume_destroy(ctx, vol)
     per_view = dense / len(cams)
     return {"workload": "diff_128x128x96", "views": len(cams), "image": "512x512",
@@ -408,6 +408,8 @@ def adjoint_form(rc, ctx, flush, stream):
             "backward_gsamples_s": 2 * per_view / (b_ms / 1e3) / 1e9,
             "bspline": {"forward_ms_per_view": fb_ms, "backward_ms_per_view": bb_ms,
                         "backward_over_forward": bb_ms / fb_ms},
+            "tf2d": {"table": f"{M2}x{wd['K']}", "forward_ms_per_view": f2_ms, "backward_ms_per_view": b2_ms,
+                     "backward_over_forward": b2_ms / f2_ms},
             "note": "exact skipping in the forward recompute, none in the gradient pass (an empty brick still has a gradient)"}
 
 
