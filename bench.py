@@ -219,6 +219,40 @@ def cpu_oracle_sample(ph, tf, w, cams, budget_s, pixels_per_view=None):
     return samples / dt / 1e9, cores, f"{what} {views} view(s), {samples} samples, {dt:.1f} s"
 
 
+def cpu_model():
+    """The host CPU's name from /proc/cpuinfo (x86 'model name', else the Arm
+    implementer / part codes), or the machine type."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model Name"):
+        m = re.search(rf"^{key}\s*:\s*(.+)$", info, re.M)
+        if m:
+            return m.group(1).strip()
+    imp = re.search(r"^CPU implementer\s*:\s*(\S+)", info, re.M)
+    part = re.search(r"^CPU part\s*:\s*(\S+)", info, re.M)
+    if imp and part:
+        return f"{platform.machine()} (implementer {imp.group(1)}, part {part.group(1)})"
+    return platform.machine()
+
+
+def cpu_oracle_one_core(ph, tf, w, cam, budget_s=3.0, npix=4096):
+    """The oracle on one host thread: seeded pixel sets of one view until
+    budget_s of work is done. Returns (Gsamples/s, desc)."""
+    import oracle
+    sc = oracle.Scene(ph.vol, ph.spacing, tf, cam, step=w["step"], term=w["term"], shade=w["shade"])
+    samples, sets = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        pix = synth.sample_pixels(w["width"], w["height"], npix, seed=9500 + sets)
+        samples += int(oracle.render(sc, pixels=pix, nthreads=1)["nsamp"].sum())
+        sets += 1
+    dt = time.perf_counter() - t0
+    return samples / dt / 1e9, f"{sets} x {npix} seeded pixels of one view, {samples} samples, {dt:.1f} s"
+
+
 def filter_forms(rc, ctx, vol, w, P, cam_structs, outs, ref_imgs, flush, stream, hbm_peak):
     """The reconstruction / classification variants on the FP32 volume, every
     view in one launch: cubic B-spline (64 distinct FP32 voxels = 256 B per
@@ -790,7 +824,9 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, cores, desc = cpu_oracle_sample(ph, tf, w, cams, args.cpu_budget)
-        line["cpu_baseline"] = {"value": val, "unit": "Gsamples/s", "cores": cores, "kind": "oracle", "sample": desc}
+        v1, d1 = cpu_oracle_one_core(ph, tf, w, cams[0])
+        line["cpu_baseline"] = {"value": val, "unit": "Gsamples/s", "cores": cores, "kind": "oracle", "sample": desc,
+                                "cpu": cpu_model(), "one_core": {"value": v1, "sample": d1}}
     rc.rc_volume_destroy(ctx, vol)
     rc.rc_context_destroy(ctx)
     if rank == 0:
