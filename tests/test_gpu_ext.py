@@ -183,6 +183,42 @@ def test_reduced_storage_forms(rc, orc, storage, fp16):
         r.close()
 
 
+@pytest.mark.parametrize("storage,fp16,filt", [(1, True, 0), (2, True, 1), (2, False, 0)])
+def test_reduced_storage_gradients(rc, orc, storage, fp16, filt):
+    """The table gradient (2-D and 1-D tables) on F16 / U16 storage against
+    the oracle's reverse mode on the same stored values and table, within
+    2e-4 of the largest entry, on a ragged 66 x 45 image (partial tiles in
+    both directions); pixels whose termination is a tie are left out."""
+    import torch
+    ph = synth.head_phantom((70, 64, 48), (1.0, 1.0, 1.25), seed=33, tumor_radius_vox=4)
+    r = GPURenderer(rc, ph.vol, ph.spacing, storage=storage)
+    try:
+        cam = synth.orbit_camera(ph.dims, ph.spacing, 70.0, width=66, height=45)
+        rc.rc_camera_set(r.ctx, cam)
+        for tab in (synth.tf2d_table(256, 16, GMAX), synth.tf_table(256)):
+            if tab.ndim == 3:
+                rc.rc_tf2d_set(r.ctx, tab, GMAX, fp16)
+            else:
+                r.set_tf(tab, fp16)
+            sc = orc.Scene(ph.vol, ph.spacing, tab, cam, step=0.5, term=0.99, shade=True, filter=filt,
+                           gmax=GMAX, value_mode=int(storage == 1), tf_fp16=fp16)
+            fwd = orc.render(sc)
+            keep = np.nonzero(~fwd["tie"].reshape(-1))[0]
+            g = np.zeros((45 * 66, 4))
+            g[keep] = np.random.default_rng(34).normal(size=(len(keep), 4))
+            og, _ = orc.render_grad(sc, g[keep], pixels=keep)
+            dtf = torch.empty(tab.shape, device="cuda")
+            rc.rc_render_backward(r.ctx, r.vol, dict(step_vox=0.5, term=0.99, shade=True, filter=filt),
+                                  torch.from_numpy(g.astype(np.float32)).cuda(), dtf)
+            torch.cuda.synchronize()
+            got = dtf.cpu().numpy().astype(np.float64)
+            scale = np.abs(og).max()
+            assert scale > 0
+            assert np.abs(got - og).max() / scale < 2e-4
+    finally:
+        r.close()
+
+
 @pytest.mark.parametrize("func", ["MIP", "AVERAGE", "XRAY", "ISO", "THRESHOLD"])
 def test_bspline_ray_functions(rc, orc, small, func):
     ph, r = small
