@@ -188,12 +188,17 @@ rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries
  * gradient is in normalised units); the four entries around (u, w) blend
  * bilinearly. n_values 2..4096, n_grad 2..4096, n_values * n_grad <= 2^20,
  * gmax finite and > 0. fp16 = 1 rounds the entries to FP16. Replaces the
- * current table (1-D or 2-D). Compositing and the ray functions that do not
- * classify use it; thresholding, the table gradient and the learned proposal
- * need a 1-D table (RC_ERR_UNSUPPORTED). Shading off still computes the
- * gradient. Empty-space skipping stays exact: a brick is empty only when
+ * current table (1-D or 2-D). Compositing, the table gradient and the ray
+ * functions that do not classify use it; thresholding and the learned
+ * proposal need a 1-D table (RC_ERR_UNSUPPORTED). Shading off still computes
+ * the gradient. Empty-space skipping stays exact: a brick is empty only when
  * every row of its value entries has zero opacity. */
 rc_status rc_tf2d_set(rc_context *ctx, const float *rgba, int n_values, int n_grad, float gmax, int fp16);
+/* Same from device memory (asynchronous device-to-device copy; the opacity
+ * maxima and the FP16 rounding are computed on the context's stream). Values
+ * are not range-checked on this path. */
+rc_status rc_tf2d_set_device(rc_context *ctx, const float *rgba_dev, int n_values, int n_grad, float gmax,
+                             int fp16);
 
 rc_status rc_camera_set(rc_context *ctx, const rc_camera *cam);
 

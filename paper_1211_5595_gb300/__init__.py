@@ -70,6 +70,7 @@ SIGNATURES = {
     "rc_tf_set": (_I, [_P, _P, _I, _I]),
     "rc_tf_set_device": (_I, [_P, _P, _I, _I]),
     "rc_tf2d_set": (_I, [_P, _P, _I, _I, C.c_float, _I]),
+    "rc_tf2d_set_device": (_I, [_P, _P, _I, _I, C.c_float, _I]),
     "rc_camera_set": (_I, [_P, C.POINTER(rc_camera)]),
     "rc_render": (_I, [_P, _P, C.POINTER(rc_render_params), _P, C.POINTER(rc_stats)]),
     "rc_render_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P,
@@ -225,6 +226,14 @@ def rc_tf2d_set(ctx, rgba, gmax, fp16=False):
 
 def rc_tf_set_device(ctx, rgba, fp16=False):
     _check(lib().rc_tf_set_device(ctx, _ptr(rgba), rgba.shape[0], int(bool(fp16))), ctx, "rc_tf_set_device")
+
+
+def rc_tf2d_set_device(ctx, rgba, gmax, fp16=False):
+    """2-D table from a CUDA float32 tensor of shape (n_grad, n_values, 4)."""
+    if rgba.dim() != 3 or rgba.shape[2] != 4:
+        raise ValueError("rc_tf2d_set_device: rgba must have shape (n_grad, n_values, 4)")
+    _check(lib().rc_tf2d_set_device(ctx, _ptr(rgba), rgba.shape[1], rgba.shape[0], float(gmax), int(bool(fp16))),
+           ctx, "rc_tf2d_set_device")
 
 
 def make_camera(cam) -> rc_camera:

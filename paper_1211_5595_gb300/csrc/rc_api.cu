@@ -487,17 +487,19 @@ rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries
     return tf_common(ctx, rgba_dev, n_entries, fp16, true);
 }
 
-rc_status rc_tf2d_set(rc_context *ctx, const float *rgba, int K, int M, float gmax, int fp16) {
+static rc_status tf2_common(rc_context *ctx, const float *rgba, int K, int M, float gmax, int fp16, bool dev) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_tf2d_set: ctx is NULL");
     if (!rgba) return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: rgba is NULL");
     if (K < 2 || K > 4096 || M < 2 || M > 4096 || (long long)K * M > (1ll << 20))
         return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: %d x %d entries (2..4096 each, at most 2^20)", K, M);
     if (!(gmax > 0.0f) || !isfinite(gmax)) return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: gmax %g", (double)gmax);
     const long long n = (long long)K * M;
-    for (long long i = 0; i < 4 * n; i++)
-        if (!(rgba[i] >= 0.0f && rgba[i] <= 1.0f))
-            return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: entry %lld channel %lld = %g outside [0, 1]", i / 4,
-                        i % 4, (double)rgba[i]);
+    if (!dev) {
+        for (long long i = 0; i < 4 * n; i++)
+            if (!(rgba[i] >= 0.0f && rgba[i] <= 1.0f))
+                return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf2d_set: entry %lld channel %lld = %g outside [0, 1]",
+                            i / 4, i % 4, (double)rgba[i]);
+    }
     DeviceScope ds(ctx->device);
     if (n > ctx->tf2_cap) {
         float4 *t = nullptr;
@@ -516,20 +518,29 @@ rc_status rc_tf2d_set(rc_context *ctx, const float *rgba, int K, int M, float gm
         ctx->d_amax = am;
         ctx->tf2_cap = cap;
     }
-    RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_tf2, rgba, (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+    RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_tf2, rgba, (size_t)n * sizeof(float4),
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     if (fp16) {
         tf2_round_half_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_tf2, n);
         RC_CUDA(ctx, cudaGetLastError());
     }
     tf2_amax_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_tf2, K, M, ctx->d_amax);
     RC_CUDA(ctx, cudaGetLastError());
-    RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host source may be reused at once
+    if (!dev) RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host source may be reused at once
     ctx->K = K;
     ctx->M = M;
     ctx->gmax = gmax;
     ctx->tf_fp16 = fp16 ? 1 : 0;
     ctx->tf_version++;
     return RC_OK;
+}
+
+rc_status rc_tf2d_set(rc_context *ctx, const float *rgba, int K, int M, float gmax, int fp16) {
+    return tf2_common(ctx, rgba, K, M, gmax, fp16, false);
+}
+
+rc_status rc_tf2d_set_device(rc_context *ctx, const float *rgba_dev, int K, int M, float gmax, int fp16) {
+    return tf2_common(ctx, rgba_dev, K, M, gmax, fp16, true);
 }
 
 static rc_status check_camera(rc_context *ctx, const rc_camera *cam, const char *who) {
