@@ -242,6 +242,44 @@ __device__ __forceinline__ float value_grad_vg(const VolDev &v, const Cell &c, f
     return r.x;
 }
 
+// A uint16 value+gradient entry as the FP32 pairs (V, D_x) and (D_y, D_z),
+// exactly: a byte permute places each 16-bit field in the mantissa of 2^23,
+// and one packed subtraction per pair removes 2^23 (the value) or
+// 2^23 + 32768 (the offset differences).
+__device__ __forceinline__ ulonglong2 vg16_decode(uint2 q) {
+    unsigned long long a, b, r0, r1;
+    asm("mov.b64 %0, {%1, %2};"
+        : "=l"(a)
+        : "r"(__byte_perm(q.x, 0x4B000000u, 0x7610)), "r"(__byte_perm(q.x, 0x4B000000u, 0x7632)));
+    asm("mov.b64 %0, {%1, %2};"
+        : "=l"(b)
+        : "r"(__byte_perm(q.y, 0x4B000000u, 0x7610)), "r"(__byte_perm(q.y, 0x4B000000u, 0x7632)));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r0) : "l"(a), "l"(pack2(8388608.0f, 8421376.0f)));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r1) : "l"(b), "l"(pack2(8421376.0f, 8421376.0f)));
+    return make_ulonglong2(r0, r1);
+}
+
+// value_grad_vg for uint16 storage: the same integers from 8-byte entries
+// (half the bytes of the float4 entries), so the same operations give the
+// FP32 storage's result bit for bit.
+__device__ __forceinline__ float value_grad_vg16(const VolDev &v, const Cell &c, float g[3]) {
+    const unsigned idx = (unsigned)brick_of(v, c) * (unsigned)kGradVox +
+                         (unsigned)(((c.i[2] & 15) * kGradEdge + (c.i[1] & 15)) * kGradEdge + (c.i[0] & 15));
+    const uint2 *p = reinterpret_cast<const uint2 *>(v.vg) + idx;
+    constexpr int DY = kGradEdge, DZ = kGradEdge * kGradEdge;
+    const unsigned long long wx = pack2(c.w[0], c.w[0]), wy = pack2(c.w[1], c.w[1]), wz = pack2(c.w[2], c.w[2]);
+    auto ld = [&](int o) { return vg16_decode(__ldg(p + o)); };
+    const ulonglong2 c00 = lerp4p(ld(0), ld(1), wx);
+    const ulonglong2 c10 = lerp4p(ld(DY), ld(DY + 1), wx);
+    const ulonglong2 c01 = lerp4p(ld(DZ), ld(DZ + 1), wx);
+    const ulonglong2 c11 = lerp4p(ld(DZ + DY), ld(DZ + DY + 1), wx);
+    const float4 r = unpack4(lerp4p(lerp4p(c00, c10, wy), lerp4p(c01, c11, wy), wz));
+    g[0] = r.y * v.inv2s[0];
+    g[1] = r.z * v.inv2s[1];
+    g[2] = r.w * v.inv2s[2];
+    return r.x;
+}
+
 // Value and world-space central-difference gradient of the trilinear field,
 // one index unit per axis, from the 32 distinct voxels around the cell.
 // The samples at p -/+ e_a use the cells with base coordinates
@@ -316,12 +354,13 @@ __device__ __forceinline__ float value_grad_x(const VolDev &v, const Cell &c, fl
 }
 
 // Value and gradient of the trilinear field: FP32 storage from the
-// value+gradient bricks; FP16 from the pair bricks when the volume has them
-// (one uniform branch per sample), else, and for uint16, from the apron
-// brick; the same stored values and operations either way.
+// value+gradient bricks, uint16 from its 8-byte value+gradient bricks when
+// the volume has them (vmax < 32768); FP16 from the pair bricks when the
+// volume has them (one uniform branch per sample), else from the apron brick.
 template <int ST>
 __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, float g[3]) {
     if (ST == RC_STORE_F32) return value_grad_vg(v, c, g);
+    if (ST == RC_STORE_U16 && v.vg != nullptr) return value_grad_vg16(v, c, g);
     if (ST == RC_STORE_F16 && v.pairs != nullptr) return value_grad_x<ST, true>(v, c, g);
     return value_grad_x<ST, false>(v, c, g);
 }

@@ -33,7 +33,10 @@ struct CamRec {
 struct VolDev {
     const void *data;      // [bz][by][bx][19][19][19] apron bricks, storage type
     const void *pairs;     // pair bricks (storage type) once a render needed them, else null
-    const float4 *vg;      // F32 storage: [bz][by][bx][17][17][17] (value, central differences x2), else null
+    // value+gradient bricks [bz][by][bx][17][17][17] of (value, central
+    // differences x2): F32 storage float4 entries, U16 storage uint2 entries
+    // (value | (D_x + 32768) << 16, (D_y + 32768) | (D_z + 32768) << 16); F16: null
+    const void *vg;
     int storage;           // rc_storage
     int n[3];              // voxels per axis
     int cb[3];             // cell-bricks per axis: ceil((n-1)/16)
@@ -83,7 +86,7 @@ struct MarchParams {
 // storage (the rest of the volume record is shared).
 struct BatchVol {
     const void *data;
-    const float4 *vg;
+    const void *vg;
     const void *pairs;
     const uint8_t *occ;
     const unsigned long long *fine;
@@ -192,7 +195,7 @@ struct TrainArgs {
 
 // ---- launchers (return the launch error) --------------------------------
 cudaError_t launch_pairs(VolDev v, void *dst, cudaStream_t s);
-cudaError_t launch_prep(const uint16_t *stage, VolDev v, void *apron, float4 *vg, uint16_t *mn, uint16_t *mx,
+cudaError_t launch_prep(const uint16_t *stage, VolDev v, void *apron, void *vg, uint16_t *mn, uint16_t *mx,
                         uint16_t *mn4, uint16_t *mx4, cudaStream_t s);
 cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax, int filter,
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);

@@ -37,9 +37,11 @@ cudaError_t launch_pairs(VolDev v, void *dst, cudaStream_t s) {
 // into shared memory and written out as
 //   - the apron brick in the storage type: F32 keeps the code, F16 stores
 //     fp16(code / vmax) (FP32 quotient, round-to-nearest-even), U16 the code;
-//   - FP32 storage: the 17^3 value+gradient entries of voxels 16b .. 16b+16
-//     (clamped) as (V, V(x+1) - V(x-1), V(y+1) - V(y-1), V(z+1) - V(z-1)),
-//     neighbour indices clamped to the volume (exact in FP32);
+//   - FP32 and uint16 storage: the 17^3 value+gradient entries of voxels
+//     16b .. 16b+16 (clamped) as (V, V(x+1) - V(x-1), V(y+1) - V(y-1),
+//     V(z+1) - V(z-1)), neighbour indices clamped to the volume: exact in FP32
+//     (float4), and for uint16 as 16-bit fields with the differences offset by
+//     32768 (uint2: V | Dx << 16, Dy | Dz << 16);
 //   - the trilinear cell-brick min / max over voxels max(16b, 0) .. min(16b+16, N-1);
 //   - the trilinear min / max of the brick's 4^3 sub-blocks j over voxels
 //     4j .. min(4j+4, N-1) (ceil((N-1)/4) sub-blocks per axis).
@@ -50,7 +52,7 @@ struct PrepArgs {
     int n[3], cb[3], c4[3];
     int vmax;
     void *apron;
-    float4 *vg;                  // null unless FP32 storage
+    void *vg;                    // float4 (FP32 storage), uint2 (uint16 storage), null (FP16)
     uint16_t *mn, *mx, *mn4, *mx4;
 };
 
@@ -79,18 +81,25 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs A) {
     auto at = [&](int x, int y, int z) {
         return (int)s_code[((z - z0) * kApron + (y - y0)) * kApron + (x - x0)];
     };
-    if (ST == RC_STORE_F32 && A.vg != nullptr) {
+    if (ST != RC_STORE_F16 && A.vg != nullptr) {
         for (unsigned e = threadIdx.x; e < (unsigned)kGradVox; e += blockDim.x) {
             const int lx = (int)(e % kGradEdge), ly = (int)((e / kGradEdge) % kGradEdge),
                       lz = (int)(e / (kGradEdge * kGradEdge));
             const int x = min(bx * kBrick + lx, nx - 1), y = min(by * kBrick + ly, ny - 1),
                       z = min(bz * kBrick + lz, nz - 1);
-            float4 o;
-            o.x = (float)at(x, y, z);
-            o.y = (float)(at(min(x + 1, nx - 1), y, z) - at(max(x - 1, 0), y, z));
-            o.z = (float)(at(x, min(y + 1, ny - 1), z) - at(x, max(y - 1, 0), z));
-            o.w = (float)(at(x, y, min(z + 1, nz - 1)) - at(x, y, max(z - 1, 0)));
-            A.vg[(size_t)b * kGradVox + e] = o;
+            const int V = at(x, y, z);
+            const int dx = at(min(x + 1, nx - 1), y, z) - at(max(x - 1, 0), y, z);
+            const int dy = at(x, min(y + 1, ny - 1), z) - at(x, max(y - 1, 0), z);
+            const int dz = at(x, y, min(z + 1, nz - 1)) - at(x, y, max(z - 1, 0));
+            if (ST == RC_STORE_F32) {
+                reinterpret_cast<float4 *>(A.vg)[(size_t)b * kGradVox + e] =
+                    make_float4((float)V, (float)dx, (float)dy, (float)dz);
+            } else {
+                // codes <= 65535 and differences in (-32768, 32768): 16-bit fields
+                reinterpret_cast<uint2 *>(A.vg)[(size_t)b * kGradVox + e] =
+                    make_uint2((unsigned)V | ((unsigned)(dx + 32768) << 16),
+                               (unsigned)(dy + 32768) | ((unsigned)(dz + 32768) << 16));
+            }
         }
     }
     // cell-brick min / max over voxels max(16b, 0) .. min(16b + 16, N - 1)
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs A) {
     }
 }
 
-cudaError_t launch_prep(const uint16_t *stage, VolDev v, void *apron, float4 *vg, uint16_t *mn, uint16_t *mx,
+cudaError_t launch_prep(const uint16_t *stage, VolDev v, void *apron, void *vg, uint16_t *mn, uint16_t *mx,
                         uint16_t *mn4, uint16_t *mx4, cudaStream_t s) {
     PrepArgs a;
     a.stage = stage;

@@ -89,3 +89,46 @@ def test_fp32_storage_with_fp16_table_matches_diagnostic(rc, orc):
         compare(img, o, TOL_FP32)
     finally:
         r.close()
+
+
+def test_u16_value_gradient_bricks_equal_fp32_storage(rc, orc):
+    """uint16 storage with vmax < 32768 reads the gradient from 8-byte
+    value+gradient bricks holding the same integers as the FP32 storage's
+    float4 bricks: shaded images (1-D and 2-D tables, isosurface) equal the
+    FP32 storage's bit for bit. With vmax >= 32768 the differences do not fit
+    16 bits and the apron path is used: it still matches the oracle."""
+    ph = synth.head_phantom((70, 58, 41), (1.0, 0.9, 1.3), seed=35, tumor_radius_vox=4)
+    tf = synth.tf_table(256)
+    cam = synth.orbit_camera(ph.dims, ph.spacing, 200.0, width=75, height=53)
+    a = GPURenderer(rc, ph.vol, ph.spacing)
+    b = GPURenderer(rc, ph.vol, ph.spacing, storage=rc.RC_STORE_U16)
+    try:
+        for r in (a, b):
+            r.set_tf(tf)
+        P = dict(step_vox=0.5, term=0.99, shade=True, skip=True)
+        assert np.array_equal(a.render(cam, **P), b.render(cam, **P))
+        # isosurface: the same hit sample and shading; the hit distance is a
+        # division the compiler may schedule differently per storage instance
+        iso = dict(step_vox=0.5, term=0.99, shade=True, skip=True, func=rc.RC_FUNC_ISO, iso=1500.0)
+        ia, ib = a.render(cam, **iso), b.render(cam, **iso)
+        assert np.array_equal(ia[..., 2:], ib[..., 2:])
+        np.testing.assert_allclose(ib[..., :2], ia[..., :2], rtol=1e-6, atol=1e-6)
+        tab = synth.tf2d_table(256, 16, 1200.0)
+        for r in (a, b):
+            rc.rc_tf2d_set(r.ctx, tab, 1200.0)
+        P2 = dict(step_vox=0.5, term=0.99, shade=False, skip=True)
+        assert np.array_equal(a.render(cam, **P2), b.render(cam, **P2))
+    finally:
+        a.close()
+        b.close()
+    # codes scaled to a 16-bit range: vmax 40000
+    big = np.minimum((ph.vol.astype(np.int64) * 9), 40000).astype(np.uint16)
+    c = GPURenderer(rc, big, ph.spacing, storage=rc.RC_STORE_U16, vmax=40000)
+    try:
+        c.set_tf(tf)
+        img = c.render(cam, step_vox=0.5, term=0.99, shade=True, skip=True)
+        o = orc.render(orc.Scene(big, ph.spacing, tf, cam, step=0.5, term=0.99, shade=True, vmax=40000))
+        compare(img, o, TOL_FP32)
+        assert o["rgba"][..., 3].max() > 0.3
+    finally:
+        c.close()
