@@ -46,6 +46,13 @@ def test_allocation_failures_are_clean(rc, monkeypatch):
             with pytest.raises(rc.RCError) as ei:
                 rc.rc_volume_create(ctx, ph.dims, ph.spacing, 4095, rc.RC_STORE_F32)
             assert ei.value.status == rc.RC_ERR_OOM
+        # uint16 storage with vmax < 32768 has the same fifteen (its
+        # value+gradient bricks hold 8-byte entries)
+        for n in range(1, 16):
+            monkeypatch.setenv("RC_FAULT_ALLOC", "0" * (n % 2) + str(n))
+            with pytest.raises(rc.RCError) as ei:
+                rc.rc_volume_create(ctx, ph.dims, ph.spacing, 4095, rc.RC_STORE_U16)
+            assert ei.value.status == rc.RC_ERR_OOM
         monkeypatch.delenv("RC_FAULT_ALLOC")
         vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, 4095, rc.RC_STORE_F32)
         rc.rc_volume_upload(ctx, vol, ph.vol)
