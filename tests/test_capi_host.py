@@ -56,6 +56,8 @@ def test_null_arguments_are_status_codes(rc):
     assert L.rc_render(None, None, C.byref(p), None, None) == rc.RC_ERR_INVALID_ARG
     assert L.rc_render_backward(None, None, C.byref(p), None, None) == rc.RC_ERR_INVALID_ARG
     assert L.rc_tf_set(None, None, 0, 0) == rc.RC_ERR_INVALID_ARG
+    assert L.rc_tf2d_set(None, None, 0, 0, C.c_float(1.0), 0) == rc.RC_ERR_INVALID_ARG
+    assert L.rc_tf2d_set_device(None, None, 0, 0, C.c_float(1.0), 0) == rc.RC_ERR_INVALID_ARG
     assert L.rc_camera_set(None, None) == rc.RC_ERR_INVALID_ARG
     assert L.rc_volume_brick_dims(None, None) == rc.RC_ERR_INVALID_ARG
     assert L.rc_context_destroy(None) == rc.RC_OK
