@@ -700,6 +700,21 @@ static size_t tf_entries(const rc_context *ctx) {
     return (size_t)ctx->K * (ctx->M >= 2 ? ctx->M : 1);
 }
 
+// The table gradient's scratch: 4 fixed-point accumulators per table entry
+// and the |dL/dI| maximum, grown (never shrunk) after the stream drains.
+static rc_status ensure_grad_scratch(rc_context *ctx) {
+    const size_t need = 4 * tf_entries(ctx) * sizeof(long long) + 16;
+    if (ctx->scratch_bytes < need) {
+        void *buf = nullptr;
+        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        RC_CUDA(ctx, dev_alloc(&buf, need));
+        cudaFree(ctx->d_scratch);
+        ctx->d_scratch = buf;
+        ctx->scratch_bytes = need;
+    }
+    return RC_OK;
+}
+
 // The learned proposal marches trilinear samples classified by a 1-D table.
 static rc_status check_plain_form(rc_context *ctx, const rc_render_params *p, const char *who) {
     if (p->filter != RC_FILTER_TRILINEAR)
@@ -1044,15 +1059,8 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_ren
     if (p->func != RC_FUNC_COMPOSITE)
         return fail(ctx, RC_ERR_UNSUPPORTED, "rc_render_backward: compositing function only");
     DeviceScope ds(ctx->device);
-    size_t need = 4 * tf_entries(ctx) * sizeof(long long) + 16;
-    if (ctx->scratch_bytes < need) {
-        void *buf = nullptr;
-        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        RC_CUDA(ctx, dev_alloc(&buf, need));
-        cudaFree(ctx->d_scratch);
-        ctx->d_scratch = buf;
-        ctx->scratch_bytes = need;
-    }
+    st = ensure_grad_scratch(ctx);
+    if (st != RC_OK) return st;
     st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol), p->filter);
     if (st == RC_OK) st = prepare_filter(ctx, const_cast<rc_volume *>(vol), p);
     if (st != RC_OK) return st;
@@ -1076,15 +1084,8 @@ rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const 
     if (!dL_dimages) return fail(ctx, RC_ERR_INVALID_ARG, "%s: dL_dimages is NULL", who);
     if (p->func != RC_FUNC_COMPOSITE) return fail(ctx, RC_ERR_UNSUPPORTED, "%s: compositing function only", who);
     DeviceScope ds(ctx->device);
-    size_t need = 4 * tf_entries(ctx) * sizeof(long long) + 16;
-    if (ctx->scratch_bytes < need) {
-        void *buf = nullptr;
-        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        RC_CUDA(ctx, dev_alloc(&buf, need));
-        cudaFree(ctx->d_scratch);
-        ctx->d_scratch = buf;
-        ctx->scratch_bytes = need;
-    }
+    st = ensure_grad_scratch(ctx);
+    if (st != RC_OK) return st;
     rc_volume *v = const_cast<rc_volume *>(vol);
     st = ensure_occupancy(ctx, v, p->filter);
     if (st == RC_OK) st = prepare_filter(ctx, v, p);
