@@ -443,6 +443,53 @@ def test_tf_gradient_matches_finite_differences(orc, bspline):
     assert checked >= 20
 
 
+@pytest.mark.parametrize("tf2", [False, True])
+def test_tf_gradient_constant_medium_closed_form(orc, tf2):
+    """A ray along -x through a volume that varies only in y meets the same
+    value (1105) and gradient (30 codes/mm along y) at every sample, so each
+    of its n samples is classified alike (alpha, c) and the pixel is
+    C = c (1 - (1 - a')^n), A = 1 - (1 - a')^n with a' = 1 - (1 - alpha)^r.
+    The table gradient is the chain rule of that closed form, spread over the
+    two lerp entries (1-D table) or the four bilinear entries of the cell
+    (2-D table: row coordinate 30 (M-1) / gmax = 1.2)."""
+    nx, K, M, gmax, r = 60, 256, 5, 100.0, 0.5
+    vol = np.broadcast_to((1000 + 30 * np.arange(8))[None, :, None], (8, 8, nx)).astype(np.uint16)
+    rng = np.random.default_rng(11)
+    shape = (M, K, 4) if tf2 else (K, 4)
+    tab = rng.uniform(0.05, 0.95, size=shape).astype(np.float32)
+    tab[..., 3] = rng.uniform(0.02, 0.2, size=shape[:-1]).astype(np.float32)
+    sc = orc.Scene(vol, (1, 1, 1), tab, axis_camera(nx, 3.5, 4.25), step=r, term=1.0,
+                   gmax=gmax if tf2 else None)
+    g = np.array([[0.3, -0.7, 0.5, 1.1]])
+    dtf, rgba = orc.render_grad(sc, g)
+    n = int(orc.render(sc)["nsamp"][0, 0])
+    assert n == 119                                    # floor(59 / 0.5) + 1
+    u = 1105.0 * (K - 1) / 4095.0
+    i = int(np.floor(u)); a = u - i
+    t = tab.astype(np.float64)
+    if tf2:
+        w = 30.0 * (M - 1) / gmax
+        j = int(np.floor(w)); b = w - j
+        cells = [((j, i), (1 - a) * (1 - b)), ((j, i + 1), a * (1 - b)),
+                 ((j + 1, i), (1 - a) * b), ((j + 1, i + 1), a * b)]
+    else:
+        cells = [((i,), 1 - a), ((i + 1,), a)]
+    e = sum(q * t[idx] for idx, q in cells)
+    alpha, c = e[3], e[:3]
+    ap = 1.0 - (1.0 - alpha) ** r
+    Tn = (1.0 - ap) ** n
+    np.testing.assert_allclose(rgba[0, :3], c * (1.0 - Tn), rtol=1e-12)
+    assert rgba[0, 3] == pytest.approx(1.0 - Tn, rel=1e-12)
+    dc = g[0, :3] * (1.0 - Tn)
+    dalpha = (g[0, :3] @ c + g[0, 3]) * n * (1.0 - ap) ** (n - 1) * r * (1.0 - alpha) ** (r - 1.0)
+    expect = np.zeros_like(dtf)
+    for idx, q in cells:
+        expect[idx + (slice(0, 3),)] += q * dc
+        expect[idx + (3,)] += q * dalpha
+    np.testing.assert_allclose(dtf, expect, rtol=1e-9, atol=1e-14)
+    assert np.count_nonzero(np.abs(dtf).sum(axis=-1)) == len(cells)
+
+
 # --------------------------------------------------------------------------
 # opacity profiles and importance-sampled compositing
 # --------------------------------------------------------------------------
