@@ -95,23 +95,55 @@ def profiled_traffic():
     return profiled_counters().get("dram_bytes_per_launch")
 
 
-def l2_read_peak(rc, ctx, stream, reps=40):
-    """L2 read bandwidth: the library's probe reads a 96 MB buffer (below the
-    129 MB L2) reps times in one launch with loads that bypass L1; best of 5,
-    CUDA events; bytes read / time."""
+def probe_lib():
+    """librc_probe.so (include/rc_probe.h): the read-bandwidth probes."""
+    import ctypes as C
+    from paper_1211_5595_gb300 import build
+    L = C.CDLL(build.build_probe())
+    for f in ("rc_probe_read_l1", "rc_probe_read_l2"):
+        getattr(L, f).argtypes = [C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]
+        getattr(L, f).restype = C.c_int
+    L.rc_probe_l1_bytes.argtypes = [C.c_size_t, C.c_int]
+    L.rc_probe_l1_bytes.restype = C.c_size_t
+    return L
+
+
+def _probe_best_ms(fn, stream, tries=5):
     import torch
-    buf = torch.ones(24 << 20, device="cuda", dtype=torch.float32)
     for _ in range(2):
-        rc.rc_probe_read_bandwidth(ctx, buf, reps)
+        assert fn() == 0
     best = float("inf")
-    for _ in range(5):
+    for _ in range(tries):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record(stream)
-        rc.rc_probe_read_bandwidth(ctx, buf, reps)
+        assert fn() == 0
         ev[1].record(stream)
         torch.cuda.synchronize()
         best = min(best, ev[0].elapsed_time(ev[1]))
-    return reps * buf.numel() * 4 / (best / 1e3) / 1e9
+    return best
+
+
+def l2_read_peak(stream, reps=40):
+    """L2 read bandwidth: the probe reads a 96 MB buffer (below the 129 MB L2)
+    reps times in one launch with loads that bypass L1; best of 5, CUDA
+    events; bytes read / time (GB/s)."""
+    import torch
+    L = probe_lib()
+    buf = torch.ones(24 << 20, device="cuda", dtype=torch.float32)
+    nbytes = buf.numel() * 4
+    ms = _probe_best_ms(lambda: L.rc_probe_read_l2(buf.data_ptr(), nbytes, reps, stream.cuda_stream), stream)
+    return reps * nbytes / (ms / 1e3) / 1e9
+
+
+def l1_read_peak(stream, reps=2000, nbytes=32 << 10):
+    """L1 load bandwidth of the whole GPU: every CTA (4 per SM) reads the same
+    32 KB buffer reps times with 16-byte read-only loads (the march's load
+    form), coalesced 512 bytes per warp; best of 5, CUDA events; GB/s."""
+    import torch
+    L = probe_lib()
+    buf = torch.ones(nbytes // 4, device="cuda", dtype=torch.float32)
+    ms = _probe_best_ms(lambda: L.rc_probe_read_l1(buf.data_ptr(), nbytes, reps, stream.cuda_stream), stream)
+    return L.rc_probe_l1_bytes(nbytes, reps) / (ms / 1e3) / 1e9
 
 
 class ClockSampler:
@@ -296,17 +328,23 @@ def filter_forms(rc, ctx, vol, w, P, cam_structs, outs, ref_imgs, flush, stream,
 def precision_form(rc, ctx, flush, stream, hbm_peak):
     """The precision configuration: 512x512x256 phantom, 2048^2 image, step
     0.25, shaded, 1024-entry table; FP32 storage (FP32 table) against FP16
-    (normalised) and uint16 storage with the FP16 table. One view; ms per
-    frame, dense-equivalent Gsamples/s, evaluated samples, PSNR against the
-    FP32 image."""
+    (offset-normalised) and uint16 storage with the FP16 table. One view; ms
+    per frame, dense-equivalent Gsamples/s, evaluated samples, PSNR against the
+    FP32 image. Also returns, for the error against the FP64 oracle (computed
+    in the CPU-baseline leg), each form's colours at the 4096 seeded pixels of
+    the 2048^2 frame and its full 512^2 frame."""
     import torch
     wp = synth.WORKLOADS["precision_512x512x256"]
     ph = synth.workload_phantom("precision_512x512x256")
     tf = synth.tf_table(wp["K"])
     cam = synth.orbit_camera(ph.dims, ph.spacing, wp["azimuths"][0], width=wp["width"], height=wp["height"])
+    cs = synth.orbit_camera(ph.dims, ph.spacing, wp["azimuths"][0], width=wp["small_width"], height=wp["small_width"])
+    pix = synth.sample_pixels(wp["width"], wp["height"], wp["n_rays"], seed=wp["ray_seed"])
     P = rc.RenderParams(step_vox=wp["step"], term=wp["term"], shade=wp["shade"], skip=True)
     img = torch.empty((wp["height"], wp["width"], 4), device="cuda")
+    small = torch.empty((wp["small_width"], wp["small_width"], 4), device="cuda")
     ref = None
+    capture = {"ph": ph, "tf": tf, "cam": cam, "cam_small": cs, "pix": pix, "w": wp, "images": {}}
     out = {"workload": "precision_512x512x256", "image": "2048x2048", "step_vox": wp["step"], "table_entries": wp["K"]}
     for name, storage, fp16 in (("f32", rc.RC_STORE_F32, False), ("f16", rc.RC_STORE_F16, True),
                                 ("u16", rc.RC_STORE_U16, True)):
@@ -331,9 +369,52 @@ def precision_form(rc, ctx, flush, stream, hbm_peak):
             mse = float(((img - ref) ** 2).mean())
             res["psnr_db_vs_f32"] = float("inf") if mse == 0 else 10 * np.log10(1.0 / mse)
             res["speedup_vs_f32"] = out["f32"]["ms_per_frame"] / ms
+        rc.rc_camera_set(ctx, cs)
+        rc.rc_render(ctx, vol, P, small)
+        torch.cuda.synchronize()
+        capture["images"][name] = (img.view(-1, 4)[torch.from_numpy(pix).long().cuda()].cpu().numpy(),
+                                   small.cpu().numpy())
         out[name] = res
         rc.rc_volume_destroy(ctx, vol)
-    return out
+    return out, capture
+
+
+def oracle_errors(gpu, o):
+    """Max-abs per channel of GPU colours against the oracle's (a ray whose
+    stop decision is a termination tie takes the nearer branch) and the PSNR
+    over the four channels (peak 1)."""
+    g = gpu.reshape(-1, 4).astype(np.float64)
+    a, b, tie = o["rgba"].reshape(-1, 4), o["alt"].reshape(-1, 4), o["tie"].reshape(-1)
+    d1, d2 = np.abs(g - a).max(axis=1), np.abs(g - b).max(axis=1)
+    use_b = tie & (d2 < d1)
+    d = np.where(use_b, d2, d1)
+    ref = np.where(use_b[:, None], b, a)
+    mse = float(np.mean((g - ref) ** 2))
+    return {"max_abs": float(d.max()), "psnr_db": float("inf") if mse == 0 else 10 * np.log10(1.0 / mse),
+            "pixels": int(len(d)), "pixels_above_4e-3": int((d > 4e-3).sum()), "tie_rays": int(tie.sum())}
+
+
+def precision_oracle_leg(cap, cores):
+    """The FP64 oracle on the precision workload's original uint16 codes and
+    FP32 table (total error of each form) on the machine's host cores: the 4096
+    seeded pixels of the 2048^2 frame and the full 512^2 frame. Returns the
+    per-image errors of every storage form and the oracle's own timing."""
+    import oracle
+    oracle.build()
+    wp, ph, tf = cap["w"], cap["ph"], cap["tf"]
+    kw = dict(step=wp["step"], term=wp["term"], shade=wp["shade"])
+    t0 = time.perf_counter()
+    o_rays = oracle.render(oracle.Scene(ph.vol, ph.spacing, tf, cap["cam"], **kw), pixels=cap["pix"], nthreads=cores)
+    t1 = time.perf_counter()
+    o_small = oracle.render(oracle.Scene(ph.vol, ph.spacing, tf, cap["cam_small"], **kw), nthreads=cores)
+    t2 = time.perf_counter()
+    res = {"oracle": "FP64, original uint16 codes and FP32 table (total error)", "tolerance": 4e-3}
+    for name, (rays, small) in cap["images"].items():
+        res[name] = {"rays_4096_of_2048sq": oracle_errors(rays, o_rays), "frame_512sq": oracle_errors(small, o_small)}
+    samples = int(o_rays["nsamp"].sum()) + int(o_small["nsamp"].sum())
+    res["oracle_time"] = {"rays_s": t1 - t0, "frame_512_s": t2 - t1, "cores": cores,
+                          "gsamples_s": samples / (t2 - t0) / 1e9}
+    return res
 
 
 def batch_form(rc, ctx, vol, ph, P, cam_structs, flush, stream, n_extra=3):
@@ -476,30 +557,61 @@ def proposal_form(rc, ctx, vol, ph, w, cams, P, outs, frame_ms, flush, stream, n
     cam_structs = [rc.make_camera(c) for c in cams]
     imgs = torch.empty_like(outs)
     plain_frame_ms = statistics.median(frame_ms)      # the plain march, all views in one launch
-    sweep = []
-    for eps in (2.0, 0.02, 0.005, 0.0):
+
+    def measure(render, **rec):
+        """Median time per frame of render() over 3 runs (every view in one
+        call), PSNR of each view against the plain march, fallback rate."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
         for rep in range(3):
             ev[rep][0].record(stream)
-            rc.rc_render_proposal_views(ctx, vol, P, cam_structs, 64, eps, imgs)   # network launch + march launch
+            render(False)
             ev[rep][1].record(stream)
             flush.zero_()
         torch.cuda.synchronize()
         ms = statistics.median(a.elapsed_time(b) for a, b in ev) / n
         mse = ((imgs - ref) ** 2).mean(dim=(1, 2, 3)).double().cpu().numpy()
         psnrs = [float("inf") if m == 0 else 10 * np.log10(1.0 / m) for m in mse]
-        st = rc.rc_render_proposal_views(ctx, vol, P, cam_structs, 64, eps, imgs, stats=True)
+        st = render(True)
         finite = [p for p in psnrs if np.isfinite(p)]
-        sweep.append({"eps": eps, "ms_per_frame_median": ms, "speedup_vs_f32": plain_frame_ms / ms,
-                      "psnr_db_min": min(psnrs), "psnr_db_mean": float(np.mean(finite)) if finite else float("inf"),
-                      "fallback_rate": st["fallback_rays"] / max(1, st["rays_hit"]),
-                      "evaluated_samples": st["evaluated_samples"]})
-    ok = [r for r in sweep if r["psnr_db_min"] >= 45.0]
+        rec.update({"ms_per_frame_median": ms, "speedup_vs_f32": plain_frame_ms / ms,
+                    "psnr_db_min": min(psnrs), "psnr_db_mean": float(np.mean(finite)) if finite else float("inf"),
+                    "max_abs": float((imgs - ref).abs().max()),
+                    "fallback_rate": st["fallback_rays"] / max(1, st["rays_hit"]),
+                    "evaluated_samples": st["evaluated_samples"]})
+        return rec
+
+    def proposal(sampling, lam, nimp, eps):
+        # network launch (range records or PDFs) + importance-march launch
+        return lambda stats: rc.rc_render_proposal_sampled(ctx, vol, P, cam_structs, sampling, lam, nimp, eps, imgs,
+                                                           stats=stats)
+
+    def uniform(nimp):
+        # no network: nimp samples at the centres of nimp equal segments of the chord
+        return lambda stats: rc.rc_render_importance_views(ctx, vol, P, cam_structs, rc.RC_SAMPLING_INVCDF, 1.0,
+                                                           None, None, nimp, 2.0, imgs, stats=stats)
+
+    # fallback thresholds of the range reading at 64 samples per ray
+    sweep = [measure(proposal(rc.RC_SAMPLING_RANGE, 0.0, 64, eps), sampling="range", nimp=64, eps=eps)
+             for eps in (2.0, 0.02, 0.005, 0.0)]
+    sweep += [measure(proposal(rc.RC_SAMPLING_INVCDF, 0.05, 64, eps), sampling="invcdf", lam=0.05, nimp=64, eps=eps)
+              for eps in (0.02, 0.0)]
+    # the readings of "few importance samples" at equal sample counts, no fallback
+    readings = []
+    for nimp in (16, 32, 64, 128):
+        readings.append(measure(proposal(rc.RC_SAMPLING_RANGE, 0.0, nimp, 2.0), sampling="range", nimp=nimp))
+        readings.append(measure(proposal(rc.RC_SAMPLING_INVCDF, 0.05, nimp, 2.0), sampling="invcdf", lam=0.05,
+                                nimp=nimp))
+        readings.append(measure(uniform(nimp), sampling="uniform_chord", nimp=nimp))
+    ok = [r for r in sweep + readings if r["psnr_db_min"] >= 45.0]
     best = max(ok, key=lambda r: r["speedup_vs_f32"]) if ok else None
     return {"nimp": 64, "train_phantoms": n_train, "train_s": train_s, "views_per_launch": n,
             "plain_ms_per_frame": plain_frame_ms, "loss_first_last": [curve[0], curve[-1]], "sweep": sweep,
+            "readings": readings,
+            "readings_note": "eps 2 (no fallback): range = nimp equal segments of the range the network's PDF "
+                             "marks; invcdf = stratified inverse CDF of 0.95 PDF + 0.05 uniform, midpoint "
+                             "segments; uniform_chord = nimp equal segments of the whole chord (no network)",
             "speedup_at_psnr45": best["speedup_vs_f32"] if best else None,
-            "eps_at_psnr45": best["eps"] if best else None,
+            "config_at_psnr45": {k: best.get(k) for k in ("sampling", "nimp", "eps")} if best else None,
             "network": network_throughput(rc, ctx, stream)}
 
 
@@ -738,6 +850,7 @@ def main():
     # reduced-precision storage forms on the same workload: FP16 (normalised)
     # and raw uint16 volumes with the FP16 table, against the FP32 images
     forms = {}
+    precision_capture = None
     if not args.no_forms:
         ref_imgs = fp32_imgs
         fp32_frame_ms = statistics.median(frame_ms)
@@ -767,7 +880,7 @@ def main():
     if not args.no_forms:
         forms["adjoint"] = adjoint_form(rc, ctx, flush, stream)
         if not args.no_precision:
-            forms["precision"] = precision_form(rc, ctx, flush, stream, hbm_peak)
+            forms["precision"], precision_capture = precision_form(rc, ctx, flush, stream, hbm_peak)
         rc.rc_tf_set_device(ctx, tf_dev)
 
     if not args.no_proposal:
@@ -778,21 +891,24 @@ def main():
     achieved = evald * BYTES_PER_SAMPLE / launch_avg_s / 1e9
     counters = profiled_counters() if nviews == 36 else {}
     traffic = counters.get("dram_bytes_per_launch")
-    # where the gathered bytes come from: L2 -> L1 bytes against a measured L2
-    # read peak, and the instruction issue rate against 4 schedulers per SM
-    # x the SM count x the sampled clock (the kernel's real limiter)
-    l2_peak = l2_read_peak(rc, ctx, stream)
+    # the memory level that serves the gathers: L1 (95% of the sectors hit
+    # there), measured live with the L1 probe; beside it the DRAM and L2->L1
+    # rates from the ncu counters of the same kernel, and the instruction issue
+    # rate against 4 schedulers per SM x the SM count x the sampled clock
+    l1_peak = l1_read_peak(stream)
+    l2_peak = l2_read_peak(stream)
     clk = clocks.summary()
     sm_mhz = clk.get("sm_mhz") or 2070.0
     issue_peak = torch.cuda.get_device_properties(local).multi_processor_count * 4 * sm_mhz * 1e6
-    l2 = issue = l1 = None
-    if "l1_data_pipe_pct" in counters:
-        l1 = {"data_pipe_frac": counters["l1_data_pipe_pct"] / 100.0,
-              "source": "ncu LSU data-pipe wavefronts of the same kernel (profiles/march_shaded_256x256x180.md)"}
+    dram = l2 = issue = None
+    if traffic is not None:
+        a = traffic / launch_avg_s / 1e9
+        dram = {"achieved_gbs": a, "peak_gbs": hbm_peak, "frac": a / hbm_peak,
+                "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch over the live launch time"}
     if "l2_to_l1_bytes_per_launch" in counters:
         a = counters["l2_to_l1_bytes_per_launch"] / launch_avg_s / 1e9
         l2 = {"achieved_gbs": a, "peak_gbs": l2_peak, "frac": a / l2_peak,
-              "peak_kind": "measured: rc_probe_read_bandwidth, a 96 MB buffer read 40 times through L2"}
+              "peak_kind": "measured in this run: rc_probe_read_l2, a 96 MB buffer read 40 times through L2"}
     if "warp_instructions_per_launch" in counters:
         a = counters["warp_instructions_per_launch"] / launch_avg_s
         issue = {"achieved_warp_inst_s": a, "peak_warp_inst_s": issue_peak, "frac": a / issue_peak,
@@ -807,14 +923,21 @@ def main():
                    "l2": "flushed between steps (256 MB write, outside the step events)",
                    "ms_per_frame_median": statistics.median(frame_ms),
                    "dense_samples_per_step": dense, "evaluated_samples_per_step": evald},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic,
+        "roofline": {"bound": "l1", "achieved": achieved, "peak": l1_peak, "unit": "GB/s",
+                     "frac": achieved / l1_peak, "traffic": traffic,
                      "kernel": "composite_kernel<F32, shaded>, one launch per step for all views",
                      "model": f"{BYTES_PER_SAMPLE} B per evaluated sample (32 distinct FP32 voxels = 8 value+gradient float4) / mean launch time",
-                     "peak_kind": f"{peak_kind} copy bandwidth",
-                     "note": "the gather bytes are served by L1 (95% of sectors): the L1 data path (l1) "
-                             "and instruction issue (issue) are the limits, not HBM or L2",
-                     "l1": l1, "l2": l2, "issue": issue},
+                     "peak_kind": "measured in this run: rc_probe_read_l1, coalesced 16-byte read-only loads of "
+                                  "an L1-resident 32 KB buffer by 4 CTAs per SM",
+                     "note": "95% of the gather sectors hit L1, so L1 is the memory level that serves the "
+                             "algorithmic bytes; scattered 16-byte gathers use fewer bytes per L1 wavefront "
+                             "than the probe's coalesced loads (ncu: L1 data pipe l1_data_pipe_frac), and "
+                             "instruction issue (issue) is the co-limit",
+                     "model_bytes_frac_of_hbm": achieved / hbm_peak,
+                     "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
+                     "l1_data_pipe_frac": (counters["l1_data_pipe_pct"] / 100.0) if "l1_data_pipe_pct" in counters
+                     else None,
+                     "dram": dram, "l2": l2, "issue": issue},
         "e2e": e2e,
         "forms": forms,
         # per step: re-layout, value+gradient bricks, 16^3 and 4^3 min/max grids,
@@ -827,6 +950,10 @@ def main():
         v1, d1 = cpu_oracle_one_core(ph, tf, w, cams[0])
         line["cpu_baseline"] = {"value": val, "unit": "Gsamples/s", "cores": cores, "kind": "oracle", "sample": desc,
                                 "cpu": cpu_model(), "one_core": {"value": v1, "sample": d1}}
+        if precision_capture is not None:
+            # the same oracle on the precision workload: each storage form's
+            # error against the FP64 oracle, per image
+            forms["precision"]["oracle_error"] = precision_oracle_leg(precision_capture, cores)
     rc.rc_volume_destroy(ctx, vol)
     rc.rc_context_destroy(ctx)
     if rank == 0:

@@ -50,7 +50,10 @@ typedef enum {
 
 /* How the volume is held on the device (Sec. 2.1 scalar data):
  * F32: FP32 codes (exact copies of the uint16 codes);
- * F16: FP16 of code / vmax (normalised to [0, 1]);
+ * F16: FP16 of (code - o) / o, normalised to [-1, 1] by the offset o, the
+ *      smallest power of two (>= 1) with 2o >= vmax (2048 for 12-bit data):
+ *      |code - o| <= 2048 is an integer FP16 holds exactly, so every code of
+ *      a volume with vmax <= 4096 is stored exactly in 2 bytes;
  * U16: the raw uint16 codes. */
 typedef enum { RC_STORE_F32 = 0, RC_STORE_F16 = 1, RC_STORE_U16 = 2 } rc_storage;
 
@@ -136,13 +139,6 @@ rc_status rc_context_set_stream(rc_context *ctx, void *cuda_stream);
  * statistics make the same check. */
 rc_status rc_context_sync(rc_context *ctx);
 
-/* Measurement aid for the rooflines of the gather kernels (the paper has no
- * counterpart): one launch on the context's stream reads the device buffer
- * buf (bytes, a multiple of 16, 16-byte aligned) reps times with 16-byte
- * loads that bypass L1, so a buffer smaller than L2 (129 MB on GB300)
- * measures the L2 read rate. Time it with events on the stream; it writes
- * nothing the caller can see. */
-rc_status rc_probe_read_bandwidth(rc_context *ctx, const void *buf, size_t bytes, int reps);
 /* Synchronises the context's stream and frees everything the context owns.
  * Volumes must be destroyed first (RC_ERR_STATE otherwise). */
 rc_status rc_context_destroy(rc_context *ctx);
@@ -187,8 +183,9 @@ rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries
  * as in rc_tf_set, row j at gradient magnitude j*gmax/(n_grad-1) codes per mm.
  * A sample's gradient (central differences, or the B-spline derivative) gives
  * the row coordinate w = fl(|g| * fl((n_grad-1) * vmax / (vscale * gmax))),
- * clamped to [0, n_grad-1] (vscale: vmax, or 1 for F16 storage, whose
- * gradient is in normalised units); the four entries around (u, w) blend
+ * clamped to [0, n_grad-1] (vscale: the full scale in stored units, vmax,
+ * or vmax / o for F16 storage, whose gradient is in units of o codes); the
+ * four entries around (u, w) blend
  * bilinearly. n_values 2..4096, n_grad 2..4096, n_values * n_grad <= 2^20,
  * gmax finite and > 0. fp16 = 1 rounds the entries to FP16. Replaces the
  * current table (1-D or 2-D). Compositing, the table gradient and the ray
@@ -288,7 +285,11 @@ rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const 
  * address (and may load the library's device code), so make the first call
  * before any stream capture. Every call shares the one array and clears it on
  * the stream before use; calls whose work overlaps on the GPU (other streams or
- * contexts on the same device) race on it and must be serialised by the caller. */
+ * contexts on the same device) race on it and must be serialised by the caller.
+ * It reads the same stored values as rc_render_backward: a volume whose pair
+ * bricks an earlier render allocated has them refreshed in place, and a volume
+ * that never had them is read from its apron bricks (the same voxels in the
+ * same arithmetic, so the same gradient). */
 rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol,
                                      const rc_render_params *params, const float *dL_dimage,
                                      float *dL_dtf);
@@ -308,8 +309,8 @@ rc_status rc_brick_grid_get_filter(rc_context *ctx, const rc_volume *vol, int fi
  * opacity). A brick is empty when every table entry a sample inside it can
  * touch, floor(u(min)) .. min(floor(u(max)) + 1, K - 1), has opacity 0, with
  * the table coordinate u(v) = fl(v * fl((K-1) / vmax)) of a raw code v, or
- * u(v) = fl(h * (K-1)) with h = fp16(fl(v / vmax)) for F16 storage (FP32
- * operations rounded once). */
+ * u(v) = fl((h + 1) * fl((K-1) / fl(vmax / o))) with h = fp16(fl((v - o) / o))
+ * for F16 storage (FP32 operations rounded once). */
 rc_status rc_skip_mask_get(rc_context *ctx, const rc_volume *vol, uint8_t *occ);
 
 /* The mask of a reconstruction filter, from that filter's grid
@@ -395,6 +396,25 @@ rc_status rc_proposal_grad(rc_context *ctx, const float *features, const float *
  * gradient; loss as above (device, may be NULL). */
 rc_status rc_proposal_train_step(rc_context *ctx, const float *features, const float *targets, int64_t n,
                                  float lr, float *loss);
+/* Placement of the importance samples along a ray's chord (the learned
+ * proposal's two readings of "few samples where the opacity is"):
+ * RANGE: nimp samples at the centres of nimp equal segments of the range the
+ * PDF marks (described above); the default of rc_render_proposal and
+ * rc_render_importance.
+ * INVCDF: stratified inverse-CDF sampling of the mixture
+ * q_b = (1 - lambda) pdf_b + lambda / 32 (piecewise constant over the 32 bins
+ * of the chord): sample j where the mixture's CDF reaches (j + 0.5) / nimp of
+ * its total; each sample stands for the stretch between the midpoints to its
+ * neighbours (t_near and t_far at the ends), so the segments tile the chord,
+ * with its opacity corrected to that length (Eq. 3). lambda = 1 is the
+ * uniform march of nimp samples over the whole chord. FP32 specification:
+ * q_b = fma(1 - lambda, pdf_b, lambda / 32); Q_0 = 0, Q_{b+1} = Q_b + q_b;
+ * y_j = ((j + 0.5) / nimp) * Q_32; b = the first bin with Q_{b+1} > y_j (31 if
+ * none); f = q_b > 0 ? clamp((y_j - Q_b) / q_b, 0, 1) : 0;
+ * t_j = fma(b + f, (t_far - t_near) / 32, t_near); midpoints
+ * (t_{j-1} + t_j) * 0.5. */
+typedef enum { RC_SAMPLING_RANGE = 0, RC_SAMPLING_INVCDF = 1 } rc_sampling;
+
 /* Importance-sampled render from given per-pixel PDFs (device H*W*32) and
  * transmittances T^ (device H*W): nimp (1..4096) samples per ray over the range
  * described above; rays with |T - T^| > eps fall back to the plain march
@@ -403,6 +423,18 @@ rc_status rc_proposal_train_step(rc_context *ctx, const float *features, const f
 rc_status rc_render_importance(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                                const float *pdf, const float *that, int nimp, float eps,
                                float *out_rgba, uint8_t *fallback, rc_stats *stats);
+/* The importance-sampled render of nviews cameras (1..65535, one image size)
+ * in one launch with a choice of placement (rc_sampling; lambda in [0, 1] for
+ * INVCDF, ignored for RANGE). pdf: device nviews*H*W*32 floats, view-major (may
+ * be NULL for INVCDF with lambda = 1); that: device nviews*H*W floats, or NULL
+ * for no fallback (eps is then ignored; RANGE needs it). out_rgba device
+ * nviews*H*W*4, fallback (optional) nviews*H*W bytes. With RANGE each image
+ * equals rc_render_importance's for that view. The context's own camera is
+ * not changed. */
+rc_status rc_render_importance_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                                     const rc_camera *cams, int nviews, int sampling, float lambda,
+                                     const float *pdf, const float *that, int nimp, float eps,
+                                     float *out_rgba, uint8_t *fallback, rc_stats *stats);
 /* The same with the loaded network choosing the samples: a tensor-core kernel
  * encodes each ray's features, runs the network (as rc_proposal_forward) and
  * keeps per ray only its sample range (from the PDF and the occupancy, as in
@@ -420,6 +452,15 @@ rc_status rc_render_proposal(rc_context *ctx, const rc_volume *vol, const rc_ren
 rc_status rc_render_proposal_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                                    const rc_camera *cams, int nviews, int nimp, float eps, float *out_rgba,
                                    uint8_t *fallback, rc_stats *stats);
+/* rc_render_proposal_views with a choice of placement: RC_SAMPLING_RANGE is
+ * rc_render_proposal_views; with RC_SAMPLING_INVCDF (lambda in [0, 1]) the
+ * network kernel writes every ray's PDF and T^ (132 bytes per ray, in a
+ * buffer the context owns and grows) and the inverse-CDF march renders every
+ * view from them: the result equals rc_render_importance_views fed with the
+ * network's outputs. */
+rc_status rc_render_proposal_sampled(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
+                                     const rc_camera *cams, int nviews, int sampling, float lambda, int nimp,
+                                     float eps, float *out_rgba, uint8_t *fallback, rc_stats *stats);
 
 #ifdef __cplusplus
 }

@@ -74,7 +74,10 @@ def lib():
         L.orc_ray_geometry.argtypes = [P, P, P, P, C.c_int, C.c_int, P]
         L.orc_render_grad.argtypes = [P, P, P, P, P, C.c_int64, P, P, P, C.c_int]
         L.orc_profiles.argtypes = [P, P, P, P, P, C.c_int64, P, P, C.c_int]
-        L.orc_importance.argtypes = [P, P, P, P, P, C.c_int64, P, P, C.c_int, P, P, P, C.c_int]
+        L.orc_importance.argtypes = [P, P, P, P, P, C.c_int64, P, P, C.c_int, C.c_int, C.c_float, P, P, P, P, P,
+                                     C.c_int]
+        L.orc_importance_positions.argtypes = [P, P, P, P, C.c_int, C.c_int, P, P, C.c_int, C.c_int, C.c_float,
+                                               P, P]
         L.orc_proposal_features.argtypes = [P, P, P, P, P, C.c_int64, P, P]
         L.orc_proposal_features.restype = C.c_int
         L.orc_brick_minmax.argtypes = [P, P, P]
@@ -82,7 +85,7 @@ def lib():
         L.orc_brick_minmax_filter.restype = None
         L.orc_occupancy.argtypes = [P, P, P, P, P]
         for f in ("orc_render", "orc_ray_samples", "orc_ray_geometry", "orc_render_grad",
-                  "orc_profiles", "orc_importance"):
+                  "orc_profiles", "orc_importance", "orc_importance_positions"):
             getattr(L, f).restype = C.c_int
         L.orc_brick_minmax.restype = None
         L.orc_occupancy.restype = None
@@ -213,25 +216,57 @@ def profiles(scene: Scene, pixels=None, nthreads=None):
     return bins, tfin
 
 
-def importance(scene: Scene, pdf, nimp=64, pixels=None, nthreads=None, occ=None):
-    """Composite of nimp samples per ray evenly spaced over the range from the
-    first occupied bin to the bin where the ray's 32-bin PDF saturates.
-    occ: cell-brick occupancy (computed from the scene when not given)."""
-    n = scene.npix(pixels)
-    p = np.ascontiguousarray(np.asarray(pdf, dtype=np.float32).reshape(n, 32))
-    if occ is None:
+SAMPLING = {"range": 0, "invcdf": 1}
+
+
+def _importance_inputs(scene, pdf, n, occ, sampling, lam):
+    if sampling not in SAMPLING:
+        raise ValueError(f"sampling {sampling!r}")
+    p = None
+    if pdf is not None:
+        p = np.ascontiguousarray(np.asarray(pdf, dtype=np.float32).reshape(n, 32))
+    if occ is None and sampling == "range":
         mn, mx = brick_minmax(scene.vol, vmax=scene.v.vmax, filter=scene.p.filter)
         occ = occupancy((scene.v.nx, scene.v.ny, scene.v.nz), scene.tf, mn, mx, vmax=scene.v.vmax,
                         value_mode=scene.v.value_mode, tf_fp16=bool(scene.t.fp16))
-    o = np.ascontiguousarray(occ, dtype=np.uint8)
-    rgba = np.zeros((n, 4)); tfin = np.zeros(n); ns = np.zeros(n, dtype=np.int32)
+    o = None if occ is None else np.ascontiguousarray(occ, dtype=np.uint8)
+    return p, o
+
+
+def importance(scene: Scene, pdf, nimp=64, pixels=None, nthreads=None, occ=None, sampling="range", lam=0.05):
+    """Composite of nimp samples per ray placed by the ray's 32-bin PDF.
+    sampling "range": evenly spaced over the range from the first occupied bin
+    to the bin where the PDF saturates (occ: cell-brick occupancy, computed
+    from the scene when not given); "invcdf": stratified inverse CDF of the
+    mixture (1 - lam) PDF + lam uniform, each sample standing for the stretch
+    between the midpoints to its neighbours (pdf may be None for lam = 1).
+    Returns rgba, alt (the other branch of a termination tie), tie, tfinal and
+    nsamp, like render()."""
+    n = scene.npix(pixels)
+    p, o = _importance_inputs(scene, pdf, n, occ, sampling, lam)
+    rgba = np.zeros((n, 4)); alt = np.zeros((n, 4)); tie = np.zeros(n, dtype=np.uint8)
+    tfin = np.zeros(n); ns = np.zeros(n, dtype=np.int32)
     arr, ptr = _pix(pixels)
-    rc = lib().orc_importance(*scene.refs(), ptr, n, p.ctypes.data, o.ctypes.data, int(nimp),
-                              rgba.ctypes.data, tfin.ctypes.data, ns.ctypes.data,
+    rc = lib().orc_importance(*scene.refs(), ptr, n, None if p is None else p.ctypes.data,
+                              None if o is None else o.ctypes.data, int(nimp), SAMPLING[sampling], float(lam),
+                              rgba.ctypes.data, alt.ctypes.data, tie.ctypes.data, tfin.ctypes.data, ns.ctypes.data,
                               nthreads or default_threads())
     if rc:
         raise ValueError("oracle importance failed")
-    return rgba, tfin, ns
+    return {"rgba": rgba, "alt": alt, "tie": tie.astype(bool), "tfinal": tfin, "nsamp": ns}
+
+
+def importance_positions(scene: Scene, x, y, pdf, nimp=64, occ=None, sampling="range", lam=0.05):
+    """Sample positions t (along the ray, mm) and the segment lengths of pixel
+    (x, y)'s importance samples; empty arrays for a ray that misses."""
+    p, o = _importance_inputs(scene, pdf, 1, occ, sampling, lam)
+    t = np.zeros(nimp, dtype=np.float32); ln = np.zeros(nimp, dtype=np.float32)
+    k = lib().orc_importance_positions(*scene.refs(), int(x), int(y), None if p is None else p.ctypes.data,
+                                       None if o is None else o.ctypes.data, int(nimp), SAMPLING[sampling],
+                                       float(lam), t.ctypes.data, ln.ctypes.data)
+    if k < 0:
+        raise ValueError("oracle importance_positions failed")
+    return t[:k].astype(np.float64), ln[:k].astype(np.float64)
 
 
 def brick_grid_shape(dims):

@@ -63,7 +63,9 @@ typedef struct {
     int32_t nx, ny, nz;
     float sx, sy, sz;       /* voxel spacing, mm */
     int32_t vmax;           /* largest valid code; larger codes clamp to it */
-    int32_t value_mode;     /* 0: raw codes; 1: FP16 of code/vmax (normalised) */
+    int32_t value_mode;     /* 0: raw codes; 1: the code as FP16 storage holds it,
+                               h = fp16((code - o) / o) with the offset o of
+                               f16_offset, read back as (h + 1) o */
 } orc_volume;
 
 typedef struct {
@@ -105,7 +107,7 @@ typedef struct {
     const uint16_t *v;
     int n[3];
     float s[3];
-    double vrange;          /* value of full scale: vmax (raw) or 1 (normalised) */
+    double vrange;          /* value of full scale (vmax; every value is in code units) */
     double *lut;            /* value of each code, after the vmax clamp */
     double *tf;             /* M x K x 4 */
     int K;
@@ -127,6 +129,23 @@ typedef struct {
 } ray;
 
 static double half_round(float x) { return (double)(_Float16)x; }
+
+/* The offset of the FP16 storage form: the smallest power of two o >= 1 with
+ * 2o >= vmax. A code c is held as h = fp16((c - o) / o); for vmax <= 4096 the
+ * integer c - o lies in [-2048, 2048], where FP16 represents every integer, so
+ * the stored value is exact (the representation reading of the precision
+ * form; an FP16 of c / vmax keeps codes above 2048 only to +-1). */
+static int f16_offset(int vmax) {
+    int o = 1;
+    while (2 * o < vmax) o *= 2;
+    return o;
+}
+
+/* FP16 value of code c (value_mode 1), as a float. */
+static float f16_value(int c, int vmax) {
+    int o = f16_offset(vmax);
+    return (float)half_round((float)(c - o) / (float)o);
+}
 
 static void normalize3(double v[3]) {
     double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
@@ -157,15 +176,16 @@ static int scene_init(scene *S, const orc_volume *vol, const orc_tf *tf,
     if (!S->lut || !S->tf) return 2;
     for (int code = 0; code < 65536; code++) {
         int c = code > vol->vmax ? vol->vmax : code;
-        S->lut[code] = vol->value_mode ? half_round((float)c / (float)vol->vmax) : (double)c;
+        /* value_mode 1: the code recovered from its FP16 form, (h + 1) o */
+        S->lut[code] = vol->value_mode ? ((double)f16_value(c, vol->vmax) + 1.0) * (double)f16_offset(vol->vmax)
+                                       : (double)c;
     }
-    S->vrange = vol->value_mode ? 1.0 : (double)vol->vmax;
+    S->vrange = (double)vol->vmax;
     S->K = tf->K;
     for (size_t i = 0; i < (size_t)4 * tf->K * S->M; i++)
         S->tf[i] = tf->fp16 ? half_round(tf->rgba[i]) : (double)tf->rgba[i];
-    /* the gradient coordinate is defined on code units: a normalised volume's
-     * gradient is scaled back by vmax */
-    S->gcoef = S->M >= 2 ? (double)(S->M - 1) * ((double)vol->vmax / S->vrange) / (double)tf->gmax : 0.0;
+    /* the gradient coordinate is defined on code units */
+    S->gcoef = S->M >= 2 ? (double)(S->M - 1) / (double)tf->gmax : 0.0;
     S->P = *prm;
     S->W = cam->width; S->H = cam->height;
     S->smin = fminf(fminf(vol->sx, vol->sy), vol->sz);
@@ -622,6 +642,9 @@ struct job {
     const float *pdf;
     const uint8_t *occ;
     int nimp;
+    int sampling;           /* importance march: ORC_SAMPLING_* */
+    float lambda;           /* importance march, INVCDF: uniform weight */
+    float **fbuf;           /* per thread: 2 nimp floats */
     sample **scratch;       /* per thread */
     int *cap;               /* per thread: samples the scratch holds */
 };
@@ -964,22 +987,46 @@ int orc_profiles(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
 /* ------------------------------------------------------------------------ */
 /* importance-sampled compositing from a per-ray opacity PDF                  */
 /* ------------------------------------------------------------------------ */
-/* The proposal's 32-bin PDF over [t_near, t_far] marks where the ray's
- * contribution ends: b_end is one bin past the first bin >= b_start where its
- * running sum reaches 1 - 1/64 (a margin for early predictions; 31 at most, and
- * 31 if the sum never gets there). b_start is the first bin whose start, centre
- * or end point lies in an occupied cell-brick (exact knowledge of where the
- * opacity is zero; with no occupied point the range is the whole chord). nimp
- * samples at the centres of nimp equal segments of [t_a, t_b] (the start of
- * bin b_start to the end of bin b_end) replace the evenly spaced march; each
- * stands for its segment, with its opacity corrected to that length (Eq. 3).
- * FP32 specification (each operation rounds once):
- *   bw = (t_far - t_near) / 32; point b: fmaf(b, bw, t_near),
- *   fmaf(b + 0.5, bw, t_near), fmaf(b + 1, bw, t_near); P_{b+1} = P_b + pdf_b;
+/* The proposal's 32-bin PDF over the chord [t_near, t_far] (bin width
+ * bw = (t_far - t_near) / 32) chooses nimp samples that replace the evenly
+ * spaced march of Sec. 4.1; each sample stands for a segment of the ray and
+ * its opacity is corrected to that segment's length (Eq. 3). Two readings of
+ * how the samples follow the PDF:
+ *
+ * RANGE: the PDF marks where the ray's contribution ends. b_end is one bin
+ * past the first bin >= b_start where its running sum reaches 1 - 1/64 (a
+ * margin for early predictions; 31 at most, and 31 if the sum never gets
+ * there). b_start is the first bin whose start, centre or end point lies in
+ * an occupied cell-brick (exact knowledge of where the opacity is zero; with
+ * no occupied point the range is the whole chord). The samples sit at the
+ * centres of nimp equal segments of [t_a, t_b] (the start of bin b_start to
+ * the end of bin b_end), each standing for its segment. FP32 specification
+ * (each operation rounds once):
+ *   point b: fmaf(b, bw, t_near), fmaf(b + 0.5, bw, t_near),
+ *   fmaf(b + 1, bw, t_near); P_{b+1} = P_b + pdf_b;
  *   t_a = b_start == 0 ? t_near : fmaf(b_start, bw, t_near);
  *   t_b = b_end == 31 ? t_far : fmaf(b_end + 1, bw, t_near);
- *   seg = (t_b - t_a) / nimp; t_j = fmaf(j + 0.5, seg, t_a).
- * Compositing and early termination as in composite(). aux2 = T at the end. */
+ *   seg = (t_b - t_a) / nimp; t_j = fmaf(j + 0.5, seg, t_a); len_j = seg.
+ *
+ * INVCDF: stratified inverse-CDF sampling of the PDF mixed with a uniform
+ * density, q_b = (1 - lambda) pdf_b + lambda / 32 (piecewise constant over
+ * the bins): sample j sits where the mixture's CDF reaches
+ * u_j = (j + 0.5) / nimp of its total, and stands for the stretch between the
+ * midpoints to its neighbours (the first from t_near, the last to t_far), so
+ * the segments tile the chord. lambda = 1 gives nimp samples at the centres of
+ * nimp equal segments of the whole chord (the uniform march the method
+ * replaces). FP32 specification:
+ *   q_b = fmaf(1 - lambda, pdf_b, lambda / 32); Q_0 = 0, Q_{b+1} = Q_b + q_b;
+ *   y_j = ((j + 0.5) / nimp) * Q_32; b = the first bin with Q_{b+1} > y_j
+ *   (31 if none); f = q_b > 0 ? min(max((y_j - Q_b) / q_b, 0), 1) : 0;
+ *   t_j = fmaf(b + f, bw, t_near);
+ *   m_0 = t_near, m_j = (t_{j-1} + t_j) * 0.5, m_nimp = t_far;
+ *   len_j = m_{j+1} - m_j.
+ *
+ * Compositing and early termination as in composite(), with the same
+ * termination tie report and alternative branch. */
+enum { ORC_SAMPLING_RANGE = 0, ORC_SAMPLING_INVCDF = 1 };
+
 static int occupied_at(const scene *S, const ray *R, const uint8_t *occ, float t) {
     int nb[3];
     for (int a = 0; a < 3; a++) nb[a] = (S->n[a] - 1 + 15) / 16;
@@ -995,62 +1042,125 @@ static int occupied_at(const scene *S, const ray *R, const uint8_t *occ, float t
     return occ[(idx[2] * nb[1] + idx[1]) * nb[0] + idx[0]] != 0;
 }
 
+/* Positions t[j] and segment lengths len[j] of the nimp samples of ray R. */
+static void importance_positions(const scene *S, const ray *R, const float *pdf, const uint8_t *occ, int nimp,
+                                 int sampling, float lambda, float *t, float *len) {
+    float bw = (R->tf - R->tn) / (float)PROF_BINS;
+    if (sampling == ORC_SAMPLING_INVCDF) {
+        float Q[PROF_BINS + 1], q[PROF_BINS];
+        float wp = 1.0f - lambda, wu = lambda / (float)PROF_BINS;
+        Q[0] = 0.0f;
+        for (int b = 0; b < PROF_BINS; b++) {
+            q[b] = fmaf(wp, pdf ? pdf[b] : 0.0f, wu);
+            Q[b + 1] = Q[b] + q[b];
+        }
+        for (int j = 0; j < nimp; j++) {
+            float y = (((float)j + 0.5f) / (float)nimp) * Q[PROF_BINS];
+            int b = 0;
+            while (b < PROF_BINS - 1 && !(Q[b + 1] > y)) b++;
+            float f = 0.0f;
+            if (q[b] > 0.0f) {
+                f = (y - Q[b]) / q[b];
+                f = f < 0.0f ? 0.0f : (f > 1.0f ? 1.0f : f);
+            }
+            t[j] = fmaf((float)b + f, bw, R->tn);
+        }
+        float m = R->tn;
+        for (int j = 0; j < nimp; j++) {
+            float next = j + 1 < nimp ? (t[j] + t[j + 1]) * 0.5f : R->tf;
+            len[j] = next - m;
+            m = next;
+        }
+        return;
+    }
+    int b0 = -1, b1 = PROF_BINS - 1;
+    for (int b = 0; b < PROF_BINS && b0 < 0; b++)
+        if (occupied_at(S, R, occ, fmaf((float)b, bw, R->tn)) ||
+            occupied_at(S, R, occ, fmaf((float)b + 0.5f, bw, R->tn)) ||
+            occupied_at(S, R, occ, fmaf((float)b + 1.0f, bw, R->tn)))
+            b0 = b;
+    if (b0 < 0) {
+        b0 = 0;
+    } else {
+        float P = 0.0f;
+        for (int b = 0; b < PROF_BINS; b++) {
+            P = P + pdf[b];
+            if (b >= b0 && P >= 1.0f - 1.0f / 64.0f) {
+                b1 = b + 1 < PROF_BINS - 1 ? b + 1 : PROF_BINS - 1;
+                break;
+            }
+        }
+    }
+    float ta = b0 == 0 ? R->tn : fmaf((float)b0, bw, R->tn);
+    float tb = b1 == PROF_BINS - 1 ? R->tf : fmaf((float)(b1 + 1), bw, R->tn);
+    float seg = (tb - ta) / (float)nimp;
+    for (int j = 0; j < nimp; j++) {
+        t[j] = fmaf((float)j + 0.5f, seg, ta);
+        len[j] = seg;
+    }
+}
+
+/* Eq. 4 over the given samples, front to back, stopped after the first sample
+ * whose opacity reaches term; flip_k >= 0 inverts the stop decision at that
+ * sample, and *tie_k (when given) receives the first decision within the tie
+ * band, as in composite(). */
+static void importance_composite(const scene *S, const ray *R, const float *t, const float *len, int nimp,
+                                 int flip_k, double out[4], double *Tend, int *nsamp, int *tie_k) {
+    double C[3] = {0, 0, 0}, T = 1.0;
+    int k = 0;
+    if (tie_k) *tie_k = -1;
+    for (; k < nimp; k++) {
+        sample s;
+        eval_sample(S, R, (double)t[k], (double)len[k] / (double)S->smin, &s);
+        for (int c = 0; c < 3; c++) C[c] += T * s.a * s.col[c];
+        T *= (1.0 - s.a);
+        double opacity = 1.0 - T;
+        int stop = opacity >= (double)S->P.term;
+        if (tie_k && *tie_k < 0 && fabs(opacity - (double)S->P.term) < (double)S->P.tie_band) *tie_k = k;
+        if (k == flip_k) stop = !stop;
+        if (stop) { k++; break; }
+    }
+    out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
+    *Tend = T;
+    *nsamp = k;
+}
+
 static void importance_pixel(job *J, int64_t idx, int tid) {
-    (void)tid;
     const scene *S = J->S;
     int x, y;
     pixel_xy(J, idx, &x, &y);
     ray R;
     ray_setup_f32(S, S->P.step_vox, x, y, &R);
-    double out[4] = {0, 0, 0, 0};
-    double T = 1.0;
-    int ns = 0;
+    double out[4] = {0, 0, 0, 0}, alt[4] = {0, 0, 0, 0};
+    double T = 1.0, T2;
+    int ns = 0, ns2, tie_k = -1;
     if (R.hit && J->nimp > 0) {
-        const float *pdf = J->pdf + (size_t)PROF_BINS * idx;
-        float bw = (R.tf - R.tn) / (float)PROF_BINS;
-        int b0 = -1, b1 = PROF_BINS - 1;
-        for (int b = 0; b < PROF_BINS && b0 < 0; b++)
-            if (occupied_at(S, &R, J->occ, fmaf((float)b, bw, R.tn)) ||
-                occupied_at(S, &R, J->occ, fmaf((float)b + 0.5f, bw, R.tn)) ||
-                occupied_at(S, &R, J->occ, fmaf((float)b + 1.0f, bw, R.tn)))
-                b0 = b;
-        if (b0 < 0) {
-            b0 = 0;
-        } else {
-            float P = 0.0f;
-            for (int b = 0; b < PROF_BINS; b++) {
-                P = P + pdf[b];
-                if (b >= b0 && P >= 1.0f - 1.0f / 64.0f) {
-                    b1 = b + 1 < PROF_BINS - 1 ? b + 1 : PROF_BINS - 1;
-                    break;
-                }
-            }
-        }
-        float ta = b0 == 0 ? R.tn : fmaf((float)b0, bw, R.tn);
-        float tb = b1 == PROF_BINS - 1 ? R.tf : fmaf((float)(b1 + 1), bw, R.tn);
-        float seg = (tb - ta) / (float)J->nimp;
-        double ratio = (double)seg / (double)S->smin;
-        double C[3] = {0, 0, 0};
-        for (int j = 0; j < J->nimp; j++) {
-            float t = fmaf((float)j + 0.5f, seg, ta);
-            sample s;
-            eval_sample(S, &R, (double)t, ratio, &s);
-            for (int c = 0; c < 3; c++) C[c] += T * s.a * s.col[c];
-            T *= (1.0 - s.a);
-            ns = j + 1;
-            if (1.0 - T >= (double)S->P.term) break;
-        }
-        out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
+        float *t = J->fbuf[tid], *len = J->fbuf[tid] + J->nimp;
+        importance_positions(S, &R, J->pdf ? J->pdf + (size_t)PROF_BINS * idx : NULL, J->occ, J->nimp, J->sampling,
+                             J->lambda, t, len);
+        importance_composite(S, &R, t, len, J->nimp, -1, out, &T, &ns, &tie_k);
+        if (tie_k >= 0) importance_composite(S, &R, t, len, J->nimp, tie_k, alt, &T2, &ns2, NULL);
+        else memcpy(alt, out, sizeof out);
     }
-    for (int c = 0; c < 4; c++) J->rgba[4 * idx + c] = out[c];
+    for (int c = 0; c < 4; c++) {
+        J->rgba[4 * idx + c] = out[c];
+        if (J->rgba_alt) J->rgba_alt[4 * idx + c] = alt[c];
+    }
+    if (J->tie) J->tie[idx] = (uint8_t)(tie_k >= 0);
     J->aux2[idx] = T;
     if (J->nsamp) J->nsamp[idx] = ns;
 }
 
+/* pdf: npix x 32 (may be NULL for INVCDF with lambda = 1); occ: cell-brick
+ * occupancy (RANGE). Returns 0, or 1 for invalid arguments. */
 int orc_importance(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
                    const orc_params *prm, const int32_t *pix, int64_t npix, const float *pdf,
-                   const uint8_t *occ, int nimp, double *rgba, double *tfinal, int32_t *nsamp,
-                   int nthreads) {
+                   const uint8_t *occ, int nimp, int sampling, float lambda, double *rgba, double *rgba_alt,
+                   uint8_t *tie, double *tfinal, int32_t *nsamp, int nthreads) {
+    if (nimp < 1 || (sampling != ORC_SAMPLING_RANGE && sampling != ORC_SAMPLING_INVCDF)) return 1;
+    if (sampling == ORC_SAMPLING_RANGE && (!pdf || !occ)) return 1;
+    if (sampling == ORC_SAMPLING_INVCDF && (!(lambda >= 0.0f && lambda <= 1.0f) || (!pdf && lambda != 1.0f)))
+        return 1;
     scene S;
     int rc = scene_init(&S, vol, tf, cam, prm);
     if (rc) { scene_free(&S); return rc; }
@@ -1063,12 +1173,42 @@ int orc_importance(const orc_volume *vol, const orc_tf *tf, const orc_camera *ca
     J.pdf = pdf;
     J.occ = occ;
     J.nimp = nimp;
+    J.sampling = sampling;
+    J.lambda = lambda;
     J.rgba = rgba;
+    J.rgba_alt = rgba_alt;
+    J.tie = tie;
     J.aux2 = tfinal;
     J.nsamp = nsamp;
-    run_job(&J, nthreads, 0);
+    int nt = nthreads < 1 ? 1 : (nthreads > 256 ? 256 : nthreads);
+    J.fbuf = (float **)calloc((size_t)nt, sizeof(float *));
+    int ok = J.fbuf != NULL;
+    for (int i = 0; ok && i < nt; i++) ok = (J.fbuf[i] = (float *)malloc(2 * (size_t)nimp * sizeof(float))) != NULL;
+    if (ok) run_job(&J, nt, 0);
+    for (int i = 0; J.fbuf && i < nt; i++) free(J.fbuf[i]);
+    free(J.fbuf);
     scene_free(&S);
-    return 0;
+    return ok ? 0 : 2;
+}
+
+/* The positions and segment lengths of one pixel's importance samples (the
+ * sampling step alone, for the tests of the sampling rules). Returns the
+ * number of samples written (nimp; 0 for a ray that misses), or -1. */
+int orc_importance_positions(const orc_volume *vol, const orc_tf *tf, const orc_camera *cam,
+                             const orc_params *prm, int x, int y, const float *pdf, const uint8_t *occ, int nimp,
+                             int sampling, float lambda, float *t, float *len) {
+    if (nimp < 1) return -1;
+    scene S;
+    if (scene_init(&S, vol, tf, cam, prm)) { scene_free(&S); return -1; }
+    ray R;
+    ray_setup_f32(&S, S.P.step_vox, x, y, &R);
+    int n = 0;
+    if (R.hit) {
+        importance_positions(&S, &R, pdf, occ, nimp, sampling, lambda, t, len);
+        n = nimp;
+    }
+    scene_free(&S);
+    return n;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1177,24 +1317,26 @@ void orc_brick_minmax(const orc_volume *vol, uint16_t *mn, uint16_t *mx) {
 /* A brick is occupied unless every table entry a sample inside it can touch
  * has zero opacity. For values in [mn, mx] the lerp touches entries
  * lo = floor(u(mn)) .. hi = min(floor(u(mx)) + 1, K - 1), with the table
- * coordinate of the written FP32 specification u(v) = fl(v * c),
- * c = fl((K - 1) / full scale): raw codes v with full scale vmax; FP16-
- * normalised values v = h(code), the FP16 rounding of the FP32 quotient
- * code / vmax, with full scale 1. u is monotone in v, so every sample inside
- * the brick has its coordinate in [u(mn), u(mx)]. With a 2-D table the
+ * coordinate of the written FP32 specification: raw codes v give
+ * u(v) = fl(v * c) with c = fl((K - 1) / vmax); FP16 storage (value_mode 1)
+ * holds h = fp16((code - o) / o) and gives u(h) = fl((h + 1) * c) with
+ * c = fl((K - 1) / fl(vmax / o)) (h + 1 is exact in FP32). u is monotone in
+ * the stored value, so every sample inside the brick has its coordinate in
+ * [u(mn), u(mx)]. With a 2-D table the
  * gradient coordinate of a sample is not bounded by the grid, so every row of
  * those entries must have zero opacity. */
 void orc_occupancy(const orc_volume *vol, const orc_tf *tf, const uint16_t *mn,
                    const uint16_t *mx, uint8_t *occ) {
     int nb = ((vol->nx - 1 + 15) / 16) * ((vol->ny - 1 + 15) / 16) * ((vol->nz - 1 + 15) / 16);
     int K = tf->K;
-    float c = (float)(K - 1) / (vol->value_mode ? 1.0f : (float)vol->vmax);
+    float full = vol->value_mode ? (float)vol->vmax / (float)f16_offset(vol->vmax) : (float)vol->vmax;
+    float c = (float)(K - 1) / full;
     for (int b = 0; b < nb; b++) {
         long lo, hi;
         float vmn = (float)mn[b], vmx = (float)mx[b];
         if (vol->value_mode) {
-            vmn = (float)half_round(vmn / (float)vol->vmax);
-            vmx = (float)half_round(vmx / (float)vol->vmax);
+            vmn = f16_value(mn[b], vol->vmax) + 1.0f;
+            vmx = f16_value(mx[b], vol->vmax) + 1.0f;
         }
         lo = (long)floorf(vmn * c);
         hi = (long)floorf(vmx * c) + 1;

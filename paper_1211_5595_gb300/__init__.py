@@ -21,6 +21,7 @@ RC_OK, RC_ERR_INVALID_ARG, RC_ERR_OOM, RC_ERR_CUDA, RC_ERR_STATE, RC_ERR_TIMEOUT
 RC_STORE_F32, RC_STORE_F16, RC_STORE_U16 = range(3)
 RC_FUNC_COMPOSITE, RC_FUNC_MIP, RC_FUNC_AVERAGE, RC_FUNC_XRAY, RC_FUNC_ISO, RC_FUNC_THRESHOLD = range(6)
 RC_FILTER_TRILINEAR, RC_FILTER_BSPLINE = range(2)
+RC_SAMPLING_RANGE, RC_SAMPLING_INVCDF = range(2)
 
 
 class RCError(RuntimeError):
@@ -60,7 +61,6 @@ SIGNATURES = {
     "rc_context_create": (_I, [_I, _P, C.POINTER(_P)]),
     "rc_context_set_stream": (_I, [_P, _P]),
     "rc_context_sync": (_I, [_P]),
-    "rc_probe_read_bandwidth": (_I, [_P, _P, C.c_size_t, _I]),
     "rc_context_destroy": (_I, [_P]),
     "rc_volume_create": (_I, [_P, _I, _I, _I, C.c_float, C.c_float, C.c_float, C.c_uint16, _I,
                               C.POINTER(_P)]),
@@ -98,6 +98,10 @@ SIGNATURES = {
     "rc_render_proposal": (_I, [_P, _P, C.POINTER(rc_render_params), _I, C.c_float, _P, _P, C.POINTER(rc_stats)]),
     "rc_render_proposal_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _I, C.c_float,
                                       _P, _P, C.POINTER(rc_stats)]),
+    "rc_render_importance_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _I,
+                                        C.c_float, _P, _P, _I, C.c_float, _P, _P, C.POINTER(rc_stats)]),
+    "rc_render_proposal_sampled": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _I,
+                                        C.c_float, _I, C.c_float, _P, _P, C.POINTER(rc_stats)]),
 }
 
 _lib = None
@@ -166,12 +170,6 @@ def rc_context_create(device: int = 0, stream=None):
 
 def rc_context_sync(ctx):
     _check(lib().rc_context_sync(ctx), ctx, "rc_context_sync")
-
-
-def rc_probe_read_bandwidth(ctx, buf, reps):
-    """One launch reading the CUDA tensor buf reps times through L2 (L1 bypassed)."""
-    _check(lib().rc_probe_read_bandwidth(ctx, _ptr(buf), buf.numel() * buf.element_size(), int(reps)), ctx,
-           "rc_probe_read_bandwidth")
 
 
 def rc_context_set_stream(ctx, stream):
@@ -459,4 +457,34 @@ def rc_render_proposal_views(ctx, vol, params, cams, nimp, eps, out, fallback=No
     _check(lib().rc_render_proposal_views(ctx, vol, C.byref(p), arr, len(cams), int(nimp), float(eps), _ptr(out),
                                           _ptr(fallback), C.byref(st) if st is not None else None), ctx,
            "rc_render_proposal_views")
+    return _stats_dict(st)
+
+
+def _camera_array(cams):
+    return (rc_camera * len(cams))(*[c if isinstance(c, rc_camera) else make_camera(c) for c in cams])
+
+
+def rc_render_importance_views(ctx, vol, params, cams, sampling, lam, pdf, that, nimp, eps, out, fallback=None,
+                               stats=False):
+    """Importance-sampled render of every camera from given PDFs (pdf: CUDA
+    float32 n x H x W x 32 or None for the uniform density, that: n x H x W or
+    None for no fallback; out: n x H x W x 4); sampling RC_SAMPLING_*."""
+    p = _params(params)
+    st = rc_stats() if stats else None
+    _check(lib().rc_render_importance_views(ctx, vol, C.byref(p), _camera_array(cams), len(cams), int(sampling),
+                                            float(lam), _ptr(pdf), _ptr(that), int(nimp), float(eps), _ptr(out),
+                                            _ptr(fallback), C.byref(st) if st is not None else None), ctx,
+           "rc_render_importance_views")
+    return _stats_dict(st)
+
+
+def rc_render_proposal_sampled(ctx, vol, params, cams, sampling, lam, nimp, eps, out, fallback=None, stats=False):
+    """Learned-proposal render of every camera with the chosen placement of
+    the importance samples (RC_SAMPLING_*)."""
+    p = _params(params)
+    st = rc_stats() if stats else None
+    _check(lib().rc_render_proposal_sampled(ctx, vol, C.byref(p), _camera_array(cams), len(cams), int(sampling),
+                                            float(lam), int(nimp), float(eps), _ptr(out), _ptr(fallback),
+                                            C.byref(st) if st is not None else None), ctx,
+           "rc_render_proposal_sampled")
     return _stats_dict(st)

@@ -1,6 +1,8 @@
-"""Builds librc.so (the C-ABI CUDA library) in-tree with nvcc for sm_103a.
+"""Builds librc.so (the C-ABI CUDA library, csrc/*.cu) and librc_probe.so
+(the bandwidth probes of include/rc_probe.h, csrc/probe/*.cu) in-tree with nvcc
+for sm_103a.
 
-Each .cu file compiles to an object in parallel, then nvcc links the shared
+Each .cu file compiles to an object in parallel, then nvcc links each shared
 library (static CUDA runtime). Host code is compiled without floating-point
 contraction so the FP64 camera record rounds exactly as specified.
 """
@@ -18,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librc.so")
+PROBE_DIR = os.path.join(CSRC, "probe")
+PROBE_LIB = os.path.join(PKG, "librc_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math",
@@ -32,26 +36,25 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+def sources(d=CSRC):
+    return sorted(os.path.join(d, f) for f in os.listdir(d) if f.endswith(".cu"))
 
 
-def _deps_mtime():
-    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    files.append(os.path.join(INCLUDE, "rc.h"))
+def _deps_mtime(d, headers):
+    files = sources(d) + [os.path.join(d, f) for f in os.listdir(d) if f.endswith((".h", ".cuh"))]
+    files += [os.path.join(INCLUDE, h) for h in headers]
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
+def _build_lib(lib, src_dir, headers, tag, force, verbose, extra_flags):
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime(src_dir, headers):
+        return lib
     os.makedirs(BUILD, exist_ok=True)
     nv = nvcc()
-    objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nv, *ARCH, *FLAGS, *extra_flags, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+        obj = os.path.join(BUILD, tag + os.path.basename(src)[:-3] + ".o")
+        cmd = [nv, *ARCH, *FLAGS, *extra_flags, "-I", INCLUDE, "-I", src_dir, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -60,14 +63,28 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(compile_one, sources(src_dir)))
+    tmp = lib + ".tmp"
     cmd = [nv, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_probe(force: bool = False, verbose: bool = False) -> str:
+    """librc_probe.so: the bandwidth probes the bench's rooflines use."""
+    return _build_lib(PROBE_LIB, PROBE_DIR, ["rc_probe.h"], "probe_", force, verbose, ())
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """librc.so (and librc_probe.so beside it); returns librc.so's path."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        probe = ex.submit(build_probe, force, verbose)
+        lib = _build_lib(LIB, CSRC, ["rc.h"], "", force, verbose, extra_flags)
+        probe.result()
+    return lib
 
 
 if __name__ == "__main__":

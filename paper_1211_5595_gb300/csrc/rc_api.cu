@@ -55,6 +55,8 @@ struct rc_context {
     uint8_t *d_umma = nullptr;               // BF16 B operands of the tcgen05 network
     uint2 *d_range = nullptr;                // range records of the proposal render
     long long range_cap = 0;
+    float *d_netpdf = nullptr;               // inverse-CDF proposal render: per ray 32 PDF bins, then T^ per ray
+    long long netpdf_cap = 0;
     float *d_partial = nullptr, *d_loss_partial = nullptr;
     int partial_blocks = 0;
     long long adam_step = 0;
@@ -251,6 +253,7 @@ rc_status rc_context_destroy(rc_context *ctx) {
     cudaFree(ctx->d_grad);
     cudaFree(ctx->d_umma);
     cudaFree(ctx->d_range);
+    cudaFree(ctx->d_netpdf);
     cudaFree(ctx->d_partial);
     cudaFree(ctx->d_loss_partial);
     if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
@@ -346,6 +349,20 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
     return RC_OK;
 }
 
+// FP16 storage holds h = (code - o) / o with o the smallest power of two
+// (>= 1) for which 2o >= vmax: every code 0 .. min(vmax, 4096) then has
+// |code - o| <= 2048, an integer FP16 represents exactly, so h is exact.
+static int f16_offset(int vmax) {
+    int o = 1;
+    while (2 * o < vmax) o *= 2;
+    return o;
+}
+
+// Full scale of the stored values: vmax for raw codes, vmax / o for FP16.
+static float full_scale(const rc_volume *v) {
+    return v->storage == RC_STORE_F16 ? (float)v->vmax / (float)f16_offset(v->vmax) : (float)v->vmax;
+}
+
 static VolDev vol_dev(const rc_volume *v) {
     VolDev d;
     d.data = v->d_data;
@@ -361,7 +378,8 @@ static VolDev vol_dev(const rc_volume *v) {
     }
     d.smin = smin;
     d.vmax = v->vmax;
-    d.vscale = v->storage == RC_STORE_F16 ? 1.0f : (float)v->vmax;
+    d.vscale = full_scale(v);
+    d.f16o = v->storage == RC_STORE_F16 ? (float)f16_offset(v->vmax) : 0.0f;
     d.gmin = 1e-6f * d.vscale;
     return d;
 }
@@ -723,10 +741,12 @@ static rc_status check_plain_form(rc_context *ctx, const rc_render_params *p, co
     return RC_OK;
 }
 
-// The table with its coordinate coefficients for volume v: u = fl(v * fl((K-1) / vscale)),
-// and for a 2-D table w = fl(|g| * fl((M-1) * vmax / (vscale * gmax))).
+// The table with its coordinate coefficients for volume v: ucoef = fl((K-1) / vscale)
+// (u = fl(v ucoef) for raw codes, fl((h + 1) ucoef) for FP16 values), and for
+// a 2-D table w = fl(|g| * fl((M-1) * vmax / (vscale * gmax))), vscale the
+// full scale in stored units.
 static TFDev tf_dev(const rc_context *ctx, const rc_volume *v) {
-    const float vscale = v->storage == RC_STORE_F16 ? 1.0f : (float)v->vmax;
+    const float vscale = full_scale(v);
     TFDev t{};
     t.K = ctx->K;
     t.fp16 = ctx->tf_fp16;
@@ -778,10 +798,10 @@ static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v, int f) {
     rc_status st = ensure_grid(ctx, v, f);
     if (st != RC_OK) return st;
     TFDev tf = tf_dev(ctx, v);
-    RC_CUDA(ctx, launch_occupancy(v->d_mn[f], v->d_mx[f], v->nbricks, v->vmax, v->storage == RC_STORE_F16, tf,
-                                  v->d_occ[f], ctx->stream));
-    RC_CUDA(ctx, launch_finemask(v->d_mn4[f], v->d_mx4[f], v->n, v->cb, v->vmax, v->storage == RC_STORE_F16, tf,
-                                 v->d_fine[f], ctx->stream));
+    const int f16o = v->storage == RC_STORE_F16 ? f16_offset(v->vmax) : 0;
+    RC_CUDA(ctx, launch_occupancy(v->d_mn[f], v->d_mx[f], v->nbricks, v->vmax, f16o, tf, v->d_occ[f], ctx->stream));
+    RC_CUDA(ctx, launch_finemask(v->d_mn4[f], v->d_mx4[f], v->n, v->cb, v->vmax, f16o, tf, v->d_fine[f],
+                                 ctx->stream));
     v->occ_tf_version[f] = ctx->tf_version;
     v->occ_data_version[f] = v->data_version;
     return RC_OK;
@@ -814,8 +834,10 @@ static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render
     a.p.kd = p->kd;
     a.p.ks = p->ks;
     a.p.func = p->func;
+    // the iso-value in stored units: (iso - o) / o for FP16 values
+    const float o = (float)f16_offset(v->vmax);
     a.p.iso = p->func == RC_FUNC_ISO || p->func == RC_FUNC_THRESHOLD
-                  ? (v->storage == RC_STORE_F16 ? p->iso / (float)v->vmax : p->iso)
+                  ? (v->storage == RC_STORE_F16 ? (p->iso - o) / o : p->iso)
                   : p->iso;
     a.p.skip = p->skip;
     // ds / ds_ref, with ds = step * smin rounded in FP32 as on the device
@@ -1157,7 +1179,12 @@ rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, cons
     long long *scratch = nullptr;
     st = noalloc_scratch(ctx, &scratch);
     if (st != RC_OK) return st;
-    st = ensure_occupancy(ctx, const_cast<rc_volume *>(vol), p->filter);   // no allocation: grids exist
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    st = ensure_occupancy(ctx, v, p->filter);   // no allocation: the grids and masks exist from creation
+    // pair bricks that an earlier render allocated are rebuilt in place when
+    // stale (a copy kernel, no allocation); a volume that never had them reads
+    // the apron bricks (the same stored values)
+    if (st == RC_OK && v->d_pairs) st = prepare_filter(ctx, v, p);
     if (st != RC_OK) return st;
     AdjointArgs a;
     a.m = march_args(ctx, vol, p, nullptr);
@@ -1434,6 +1461,8 @@ static ImportanceArgs importance_args(rc_context *ctx, rc_volume *v, const rc_re
     a.pdf = nullptr;
     a.that = nullptr;
     a.range = nullptr;
+    a.sampling = RC_SAMPLING_RANGE;
+    a.lambda = 0.0f;
     a.nimp = nimp;
     a.eps = eps;
     a.fallback = fallback;
@@ -1463,16 +1492,20 @@ rc_status rc_render_importance(rc_context *ctx, const rc_volume *vol, const rc_r
     return RC_OK;
 }
 
-// The network kernel writes each ray's sample range and T^ (8 bytes per ray),
-// then the importance march renders every view from those records.
-static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const rc_camera *cams,
-                                int nviews, int nimp, float eps, float *out, uint8_t *fallback, rc_stats *stats,
-                                const char *who) {
+}  // extern "C"
+
+// The importance checks for views cams[0..nviews) (cams[0] standing in for
+// the context's camera).
+static rc_status check_importance_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, float *out,
+                                        const rc_camera *cams, int nviews, int nimp, float eps, int sampling,
+                                        float lambda, const char *who) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
-    if (!ctx->net_loaded) return fail(ctx, RC_ERR_STATE, "%s: no network loaded", who);
     rc_status st = check_views(ctx, cams, nviews, who);
     if (st != RC_OK) return st;
-    const long long nrays = (long long)nviews * cams[0].width * cams[0].height;
+    if (sampling != RC_SAMPLING_RANGE && sampling != RC_SAMPLING_INVCDF)
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: sampling %d", who, sampling);
+    if (sampling == RC_SAMPLING_INVCDF && !(lambda >= 0.0f && lambda <= 1.0f))
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: lambda %g (must be in [0, 1])", who, (double)lambda);
     const bool had = ctx->cam_set;
     const rc_camera keep = ctx->cam;
     ctx->cam = cams[0];
@@ -1480,38 +1513,50 @@ static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_
     st = check_importance(ctx, vol, p, out, nimp, eps, who);
     ctx->cam = keep;
     ctx->cam_set = had;
+    return st;
+}
+
+// Grows a context-owned device buffer (after the stream drains: queued
+// kernels may still use the old one).
+template <typename T>
+static rc_status grow_buffer(rc_context *ctx, T **buf, long long *cap, long long need) {
+    if (*cap >= need) return RC_OK;
+    T *nb = nullptr;
+    RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    RC_CUDA(ctx, dev_alloc(&nb, (size_t)need * sizeof(T)));
+    cudaFree(*buf);
+    *buf = nb;
+    *cap = need;
+    return RC_OK;
+}
+
+extern "C" {
+
+rc_status rc_render_importance_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                                const rc_camera *cams, int nviews, int sampling, float lambda,
+                                                const float *pdf, const float *that, int nimp, float eps,
+                                                float *out_rgba, uint8_t *fallback, rc_stats *stats) {
+    const char *who = "rc_render_importance_views";
+    rc_status st = check_importance_views(ctx, vol, p, out_rgba, cams, nviews, nimp, eps, sampling, lambda, who);
     if (st != RC_OK) return st;
+    if (sampling == RC_SAMPLING_RANGE && (!pdf || !that))
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: pdf / that is NULL (the range reading needs both)", who);
+    if (sampling == RC_SAMPLING_INVCDF && !pdf && lambda != 1.0f)
+        return fail(ctx, RC_ERR_INVALID_ARG, "%s: pdf is NULL (allowed only for lambda = 1)", who);
     DeviceScope ds(ctx->device);
     rc_volume *v = const_cast<rc_volume *>(vol);
     st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
     if (st != RC_OK) return st;
-    if (ctx->range_cap < nrays) {
-        uint2 *buf = nullptr;
-        RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // queued kernels may still use the old records
-        RC_CUDA(ctx, dev_alloc(&buf, (size_t)nrays * sizeof(uint2)));
-        cudaFree(ctx->d_range);
-        ctx->d_range = buf;
-        ctx->range_cap = nrays;
-    }
     CamRec first;
     st = upload_views(ctx, v, cams, nviews, &first, who);
     if (st != RC_OK) return st;
-    TcNetArgs n{};
-    n.m = march_args(ctx, v, p, nullptr);
-    n.m.cam = first;
-    n.m.cams = ctx->d_cams;
-    n.net = NetDev{ctx->d_umma, ctx->d_param};
-    n.range = ctx->d_range;
-    n.tiles_x = (first.W + 15) / 16;
-    n.tiles_y = (first.H + 7) / 8;
-    n.ntiles = (long long)n.tiles_x * n.tiles_y * nviews;
-    n.budget = wait_budget(&n.issue_mma);
-    n.err = error_word(ctx);
-    RC_CUDA(ctx, launch_tc_net(n, ctx->stream));
-    ImportanceArgs a = importance_args(ctx, v, p, nimp, eps, out, fallback);
+    ImportanceArgs a = importance_args(ctx, v, p, nimp, eps, out_rgba, fallback);
     a.m.cam = first;
     a.m.cams = ctx->d_cams;
-    a.range = ctx->d_range;
+    a.pdf = pdf;
+    a.that = that;
+    a.sampling = sampling;
+    a.lambda = lambda;
     if (stats) {
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
         a.m.stats = ctx->d_stats;
@@ -1521,29 +1566,93 @@ static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_
     return RC_OK;
 }
 
+}  // extern "C"
+
+// RANGE: the network kernel writes each ray's sample range and T^ (8 bytes
+// per ray), then the importance march renders every view from those records.
+// INVCDF: the network kernel writes each ray's PDF and T^, then the
+// inverse-CDF march.
+static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, const rc_camera *cams,
+                                int nviews, int sampling, float lambda, int nimp, float eps, float *out,
+                                uint8_t *fallback, rc_stats *stats, const char *who) {
+    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
+    if (!ctx->net_loaded) return fail(ctx, RC_ERR_STATE, "%s: no network loaded", who);
+    rc_status st = check_importance_views(ctx, vol, p, out, cams, nviews, nimp, eps, sampling, lambda, who);
+    if (st != RC_OK) return st;
+    const long long nrays = (long long)nviews * cams[0].width * cams[0].height;
+    DeviceScope ds(ctx->device);
+    rc_volume *v = const_cast<rc_volume *>(vol);
+    st = ensure_occupancy(ctx, v, RC_FILTER_TRILINEAR);
+    if (st != RC_OK) return st;
+    const bool invcdf = sampling == RC_SAMPLING_INVCDF;
+    st = invcdf ? grow_buffer(ctx, &ctx->d_netpdf, &ctx->netpdf_cap, nrays * (kBins + 1))
+                : grow_buffer(ctx, &ctx->d_range, &ctx->range_cap, nrays);
+    if (st != RC_OK) return st;
+    CamRec first;
+    st = upload_views(ctx, v, cams, nviews, &first, who);
+    if (st != RC_OK) return st;
+    TcNetArgs n{};
+    n.m = march_args(ctx, v, p, nullptr);
+    n.m.cam = first;
+    n.m.cams = ctx->d_cams;
+    n.net = NetDev{ctx->d_umma, ctx->d_param};
+    if (invcdf) {
+        n.pdf_out = ctx->d_netpdf;
+        n.that_out = ctx->d_netpdf + nrays * kBins;
+    } else {
+        n.range = ctx->d_range;
+    }
+    n.tiles_x = (first.W + 15) / 16;
+    n.tiles_y = (first.H + 7) / 8;
+    n.ntiles = (long long)n.tiles_x * n.tiles_y * nviews;
+    n.budget = wait_budget(&n.issue_mma);
+    n.err = error_word(ctx);
+    RC_CUDA(ctx, launch_tc_net(n, ctx->stream));
+    ImportanceArgs a = importance_args(ctx, v, p, nimp, eps, out, fallback);
+    a.m.cam = first;
+    a.m.cams = ctx->d_cams;
+    if (invcdf) {
+        a.pdf = ctx->d_netpdf;
+        a.that = ctx->d_netpdf + nrays * kBins;
+        a.sampling = RC_SAMPLING_INVCDF;
+        a.lambda = lambda;
+    } else {
+        a.range = ctx->d_range;
+    }
+    if (stats) {
+        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        a.m.stats = ctx->d_stats;
+    }
+    RC_CUDA(ctx, launch_importance(a, nviews, ctx->stream));
+    if (stats) return read_stats(ctx, stats, true);
+    return RC_OK;
+}
+
+extern "C" {
+
 rc_status rc_render_proposal(rc_context *ctx, const rc_volume *vol, const rc_render_params *p, int nimp, float eps,
                              float *out_rgba, uint8_t *fallback, rc_stats *stats) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_render_proposal: ctx is NULL");
     if (!ctx->cam_set) return fail(ctx, RC_ERR_STATE, "rc_render_proposal: no camera (call rc_camera_set)");
     const rc_camera cam = ctx->cam;
-    return proposal_views(ctx, vol, p, &cam, 1, nimp, eps, out_rgba, fallback, stats, "rc_render_proposal");
+    return proposal_views(ctx, vol, p, &cam, 1, RC_SAMPLING_RANGE, 0.0f, nimp, eps, out_rgba, fallback, stats,
+                          "rc_render_proposal");
 }
 
 rc_status rc_render_proposal_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
                                    const rc_camera *cams, int nviews, int nimp, float eps, float *out_rgba,
                                    uint8_t *fallback, rc_stats *stats) {
-    return proposal_views(ctx, vol, p, cams, nviews, nimp, eps, out_rgba, fallback, stats,
+    return proposal_views(ctx, vol, p, cams, nviews, RC_SAMPLING_RANGE, 0.0f, nimp, eps, out_rgba, fallback, stats,
                           "rc_render_proposal_views");
 }
 
-rc_status rc_probe_read_bandwidth(rc_context *ctx, const void *buf, size_t bytes, int reps) {
-    if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_probe_read_bandwidth: ctx is NULL");
-    if (!buf || bytes < 16 || bytes % 16 != 0 || (reinterpret_cast<uintptr_t>(buf) & 15) != 0 || reps < 1)
-        return fail(ctx, RC_ERR_INVALID_ARG, "rc_probe_read_bandwidth: 16-byte aligned buffer, size a multiple of 16, reps >= 1");
-    DeviceScope ds(ctx->device);
-    RC_CUDA(ctx, launch_read_probe(buf, bytes, reps, reinterpret_cast<float *>(ctx->d_stats + 4), ctx->stream));
-    return RC_OK;
+rc_status rc_render_proposal_sampled(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                     const rc_camera *cams, int nviews, int sampling, float lambda, int nimp,
+                                     float eps, float *out_rgba, uint8_t *fallback, rc_stats *stats) {
+    return proposal_views(ctx, vol, p, cams, nviews, sampling, lambda, nimp, eps, out_rgba, fallback, stats,
+                          "rc_render_proposal_sampled");
 }
+
 
 rc_status rc_context_sync(rc_context *ctx) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_context_sync: ctx is NULL");

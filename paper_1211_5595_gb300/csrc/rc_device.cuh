@@ -500,10 +500,16 @@ __device__ __forceinline__ float bspline_grad(const VolDev &v, const Cell &c, fl
     return bspline_grad_x<ST, false>(v, c, g);
 }
 
-// Table coordinate u = fl(v * fl((K-1) / vscale)): one rounded FP32 multiply,
-// monotone in v. The occupancy mask floors the same function at a brick's
-// integer min and max, which makes skipping exact.
-__device__ __forceinline__ float tf_coord(float val, float ucoef) { return __fmul_rn(val, ucoef); }
+// Table coordinate of a stored value, one rounding, monotone in the value:
+// raw codes v give u = fl(v * ucoef); FP16 values h = (code - o) / o give
+// u = fl((h + 1) * ucoef) as one fused multiply-add (ucoef = fl(o (K-1) / vmax)).
+// The occupancy mask floors the same function at a brick's min and max, which
+// makes skipping exact.
+template <int ST>
+__device__ __forceinline__ float tf_coord(float val, float ucoef) {
+    if (ST == RC_STORE_F16) return __fmaf_rn(val, ucoef, ucoef);
+    return __fmul_rn(val, ucoef);
+}
 
 // Sec. 2.6: linear interpolation of the two neighbouring table entries.
 __device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, int *i0 = nullptr,
@@ -622,9 +628,9 @@ __device__ __forceinline__ float4 eval_sample_x(const VolDev &vol, const MarchPa
     }
     float4 e;
     if (TF2) {
-        e = classify2(tf, tf_coord(val, tf.ucoef), tf2_row_coord(tf, g));
+        e = classify2(tf, tf_coord<ST>(val, tf.ucoef), tf2_row_coord(tf, g));
     } else {
-        e = classify(s_tf, tf.K, tf_coord(val, tf.ucoef));
+        e = classify(s_tf, tf.K, tf_coord<ST>(val, tf.ucoef));
     }
     float ap = correct_alpha<RM>(e.w, rmode, ratio);
     if (SHADE) {

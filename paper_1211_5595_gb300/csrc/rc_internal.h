@@ -43,7 +43,9 @@ struct VolDev {
     float s[3];            // spacing (mm)
     float inv2s[3];        // 0.5 / spacing
     float smin;            // reference step: finest spacing
-    float vscale;          // full scale of the stored values: vmax (raw codes) or 1 (FP16)
+    float vscale;          // full scale in stored units: vmax (raw codes) or vmax / o (FP16, see f16o)
+    float f16o;            // FP16 storage: the offset o, a power of two; a stored value h is
+                           // (code - o) / o, so code = (h + 1) o (exact for codes 0 .. 2o <= 4096). 0 for raw codes
     float gmin;            // shading falls back to ambient+diffuse below this |gradient|
     int vmax;
 };
@@ -55,7 +57,8 @@ struct TFDev {
     const uint2 *f16;      // 4 halves per entry
     int K;
     int fp16;
-    float ucoef;           // table coordinate per stored value: fl((K-1) / vscale)
+    float ucoef;           // table coordinate per stored unit: fl((K-1) / vscale); u = fl(v ucoef) for
+                           // raw codes, fl((h + 1) ucoef) for FP16 values h
     // 2-D table (M >= 2; M = 0 for a 1-D table)
     const float4 *tab2;    // [M][K] FP32 (entries already FP16-rounded for an FP16 table)
     const float *amax;     // K: largest opacity of each value entry over the M rows
@@ -161,6 +164,8 @@ struct TcNetArgs {
     const float *feat;        // feature-matrix form: n x 112 FP32 (else null)
     float *net_out;           // feature-matrix form: n x 33
     uint2 *range;             // camera form: per ray (b_start | b_end << 8, T^ bits), view-major
+    float *pdf_out;           // camera form writing PDFs instead (else null): per ray 32 floats, view-major
+    float *that_out;          // with pdf_out: per ray T^
     long long n;              // feature-matrix form: rays
     long long ntiles;         // tiles of 128 rays
     int tiles_x, tiles_y;     // camera form: 16 x 8 pixel tiles per view
@@ -171,9 +176,11 @@ struct TcNetArgs {
 
 struct ImportanceArgs {
     MarchArgs m;
-    const float *pdf;         // given-PDF form: H*W*32
-    const float *that;        // given-PDF form: H*W
+    const float *pdf;         // given-PDF form: H*W*32 per view, view-major (null: uniform, INVCDF with lambda 1)
+    const float *that;        // given-PDF form: H*W per view (null: no fallback)
     const uint2 *range;       // range form: records of the network kernel (view-major)
+    int sampling;             // given-PDF form: RC_SAMPLING_RANGE or RC_SAMPLING_INVCDF
+    float lambda;             // INVCDF: weight of the uniform density in the mixture
     int nimp;                 // importance samples per ray
     float eps;                // fallback when |T_nimp - T^| > eps
     uint8_t *fallback;        // per pixel flag (or null), view-major
@@ -199,17 +206,17 @@ cudaError_t launch_prep(const uint16_t *stage, VolDev v, void *apron, void *vg, 
                         uint16_t *mn4, uint16_t *mx4, cudaStream_t s);
 cudaError_t launch_minmax(const uint16_t *stage, const int n[3], const int cb[3], int vmax, int filter,
                           uint16_t *mn, uint16_t *mx, cudaStream_t s);
+// f16o: 0 for raw codes; for FP16 storage the offset o of its values.
 cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax,
-                             int f16_values, TFDev tf, uint8_t *occ, cudaStream_t s);
+                             int f16o, TFDev tf, uint8_t *occ, cudaStream_t s);
 // 4^3 sub-block min/max grid of a filter (cells 4j..4j+3; footprint voxels
 // 4j..4j+4, or 4j-1..4j+5 for the B-spline, clamped) and the fine mask built
 // from it: per cell-brick one bit per sub-block.
 cudaError_t launch_minmax4(const uint16_t *stage, const int n[3], int vmax, int filter, uint16_t *mn, uint16_t *mx,
                            cudaStream_t s);
 cudaError_t launch_finemask(const uint16_t *mn4, const uint16_t *mx4, const int n[3], const int cb[3], int vmax,
-                            int f16_values, TFDev tf, unsigned long long *fine, cudaStream_t s);
+                            int f16o, TFDev tf, unsigned long long *fine, cudaStream_t s);
 cudaError_t launch_march(const MarchArgs &a, int nviews, cudaStream_t s);
-cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, float *sink, cudaStream_t s);
 cudaError_t launch_march_cubic(const MarchArgs &a, int nviews, cudaStream_t s);   // filter = B-spline
 cudaError_t launch_march_tf2(const MarchArgs &a, int nviews, cudaStream_t s);     // trilinear, 2-D table
 cudaError_t launch_adjoint(const AdjointArgs &a, int nviews, float *dL_dtf, cudaStream_t s);

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kMarchThreads) function_kernel(const MarchArgs
         } else if (v >= a.p.iso) {
             found = true;
             if (func == RC_FUNC_THRESHOLD) {
-                float4 e = classify(s_tf, a.tf.K, tf_coord(v, a.tf.ucoef));
+                float4 e = classify(s_tf, a.tf.K, tf_coord<ST>(v, a.tf.ucoef));
                 out = make_float4(e.x, e.y, e.z, 1.0f);
             } else {
                 float ts = k > 0 ? prev_t + (t - prev_t) * ((a.p.iso - prev_v) / (v - prev_v)) : t;
@@ -154,12 +154,21 @@ __global__ void __launch_bounds__(kMarchThreads) function_kernel(const MarchArgs
         prev_t = t;
     }
     if (!found && nsamp > 0) {
+        // over full scale; FP16 values h = (code - o) / o are shifted by 1 first
+        // (code / vmax = (h + 1) / vscale)
         float m = 0.0f;
         bool have = true;
-        if (func == RC_FUNC_MIP) m = acc / a.vol.vscale;
-        else if (func == RC_FUNC_AVERAGE) m = acc / (float)nsamp / a.vol.vscale;
-        else if (func == RC_FUNC_XRAY) m = acc * R.ds / a.vol.vscale;
-        else have = false;
+        if (ST == RC_STORE_F16) {
+            if (func == RC_FUNC_MIP) m = (acc + 1.0f) / a.vol.vscale;
+            else if (func == RC_FUNC_AVERAGE) m = (acc / (float)nsamp + 1.0f) / a.vol.vscale;
+            else if (func == RC_FUNC_XRAY) m = (acc + (float)nsamp) * R.ds / a.vol.vscale;
+            else have = false;
+        } else {
+            if (func == RC_FUNC_MIP) m = acc / a.vol.vscale;
+            else if (func == RC_FUNC_AVERAGE) m = acc / (float)nsamp / a.vol.vscale;
+            else if (func == RC_FUNC_XRAY) m = acc * R.ds / a.vol.vscale;
+            else have = false;
+        }
         if (have) out = make_float4(m, m, m, 1.0f);
     }
     if (inimg) outp[(size_t)y * cam.W + x] = out;

@@ -407,9 +407,17 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads) tc_net_kernel(const T
             for (int e = t; e < valid * kOutUsed; e += kGroupThreads) o[e] = stage[e];
             group_sync(g);                  // before the next tile's features overwrite the stage
         } else if (out_idx >= 0) {
-            int b0 = 0, b1 = kBins - 1;
-            if (hit) range_of(A.m, R, pdf, centre, true, b0, b1);
-            A.range[out_idx] = make_uint2((unsigned)b0 | ((unsigned)b1 << 8), __float_as_uint(that));
+            if (A.pdf_out) {
+                // the ray's PDF and T^ for the inverse-CDF march (32 + 1 floats)
+                float4 *o = reinterpret_cast<float4 *>(A.pdf_out + out_idx * kBins);
+#pragma unroll
+                for (int b = 0; b < kBins; b += 4) o[b / 4] = make_float4(pdf[b], pdf[b + 1], pdf[b + 2], pdf[b + 3]);
+                A.that_out[out_idx] = that;
+            } else {
+                int b0 = 0, b1 = kBins - 1;
+                if (hit) range_of(A.m, R, pdf, centre, true, b0, b1);
+                A.range[out_idx] = make_uint2((unsigned)b0 | ((unsigned)b1 << 8), __float_as_uint(that));
+            }
         }
     }
     if (!ok) {
@@ -530,6 +538,68 @@ __device__ __forceinline__ void march_range(const ImportanceArgs &A, const float
     }
 }
 
+// Stratified inverse-CDF samples of the mixture q_b = (1 - lambda) pdf_b +
+// lambda / 32 over the bins of the chord: sample j where the mixture's CDF
+// reaches (j + 0.5) / nimp of its total, standing for the stretch between the
+// midpoints to its neighbours (t_near and t_far at the ends), with its
+// opacity corrected to that length. FP32 operations as written (the bin
+// search continues from the previous sample's bin: the targets increase).
+// pdf: the ray's 32 bins, or null for the uniform density (lambda = 1).
+template <int ST, bool SHADE>
+__device__ __forceinline__ void march_invcdf(const ImportanceArgs &A, const float4 *s_tf, const Ray &R,
+                                             const float *pdf, float &C0, float &C1, float &C2, float &T,
+                                             unsigned &evald) {
+    const MarchArgs &a = A.m;
+    const float bw = __fdiv_rn(__fsub_rn(R.tf, R.tn), (float)kBins);
+    const float wp = __fsub_rn(1.0f, A.lambda), wu = __fdiv_rn(A.lambda, (float)kBins);
+    auto qb = [&](int b) { return __fmaf_rn(wp, pdf ? __ldg(pdf + b) : 0.0f, wu); };
+    float total = 0.0f;
+#pragma unroll 8
+    for (int b = 0; b < kBins; b++) total = __fadd_rn(total, qb(b));
+    int b = 0;
+    float Qb = 0.0f, q = qb(0);
+    float Qn = __fadd_rn(Qb, q);
+    auto position = [&](int j) {
+        const float y = __fmul_rn(__fdiv_rn((float)j + 0.5f, (float)A.nimp), total);
+        while (b < kBins - 1 && !(Qn > y)) {
+            b++;
+            Qb = Qn;
+            q = qb(b);
+            Qn = __fadd_rn(Qb, q);
+        }
+        float f = 0.0f;
+        if (q > 0.0f) f = fminf(fmaxf(__fdiv_rn(__fsub_rn(y, Qb), q), 0.0f), 1.0f);
+        return __fmaf_rn(__fadd_rn((float)b, f), bw, R.tn);
+    };
+    C0 = C1 = C2 = 0.0f;
+    T = 1.0f;
+    float tj = position(0), m = R.tn;
+    for (int j = 0; j < A.nimp; j++) {
+        const bool last = j + 1 == A.nimp;
+        const float tn1 = last ? R.tf : position(j + 1);
+        const float mn = last ? R.tf : __fmul_rn(__fadd_rn(tj, tn1), 0.5f);
+        const float len = __fsub_rn(mn, m);
+        float p[3];
+        position_at(R, tj, p);
+        Cell c;
+        cell_of(a.vol, p, c);
+        bool empty = false;
+        if (a.p.skip) {                                                   // opacity exactly 0
+            const int bb = brick_of(a.vol, c);
+            empty = a.fine ? empty_block(__ldg(a.fine + bb), c) >= 0 : !__ldg(a.occ + bb);
+        }
+        if (!empty) {
+            const float ratio = __fdiv_rn(len, a.vol.smin);
+            float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, 3, ratio);
+            composite_add(e, C0, C1, C2, T);
+            evald++;
+            if ((1.0f - T) >= a.p.term) break;
+        }
+        m = mn;
+        tj = tn1;
+    }
+}
+
 __device__ __forceinline__ void importance_stats(const MarchArgs &a, unsigned evald, unsigned fb, bool hit,
                                                  bool inimg) {
     unsigned e = __reduce_add_sync(0xffffffffu, evald), f = __reduce_add_sync(0xffffffffu, fb);
@@ -542,11 +612,15 @@ __device__ __forceinline__ void importance_stats(const MarchArgs &a, unsigned ev
     }
 }
 
-// RANGE: the sample range and T^ of each ray come from the network kernel's
-// records (several views, grid.z = view); otherwise from the given per-pixel
-// PDF and T^ (one view). Rays with |T_nimp - T^| > eps are re-marched by the
-// plain march.
-template <int ST, bool SHADE, bool RANGE>
+// SRC = kSrcRecords: the sample range and T^ of each ray come from the
+// network kernel's range records; kSrcRange: the range from the given per-ray
+// PDF; kSrcInvCdf: inverse-CDF samples of the given PDF (or of the uniform
+// density when A.pdf is null). Several views, grid.z = view, inputs
+// view-major. Rays with |T_nimp - T^| > eps are re-marched by the plain march
+// (never without a T^).
+enum { kSrcRecords = 0, kSrcRange = 1, kSrcInvCdf = 2 };
+
+template <int ST, bool SHADE, int SRC>
 __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A) {
     const MarchArgs &a = A.m;
     extern __shared__ float4 s_tf[];
@@ -563,22 +637,29 @@ __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A)
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
     unsigned evald = 0, fb = 0;
     if (hit) {
-        int b0, b1;
         float that;
-        if (RANGE) {
-            const uint2 rec = A.range[pix];
-            b0 = min((int)(rec.x & 255u), kBins - 1);
-            b1 = min(max((int)((rec.x >> 8) & 255u), b0), kBins - 1);
-            that = __uint_as_float(rec.y);
+        bool check = true;
+        if (SRC == kSrcInvCdf) {
+            march_invcdf<ST, SHADE>(A, s_tf, R, A.pdf ? A.pdf + pix * kBins : nullptr, C0, C1, C2, T, evald);
+            check = A.that != nullptr;
+            that = check ? A.that[pix] : 0.0f;
         } else {
-            float pdf[kBins];
+            int b0, b1;
+            if (SRC == kSrcRecords) {
+                const uint2 rec = A.range[pix];
+                b0 = min((int)(rec.x & 255u), kBins - 1);
+                b1 = min(max((int)((rec.x >> 8) & 255u), b0), kBins - 1);
+                that = __uint_as_float(rec.y);
+            } else {
+                float pdf[kBins];
 #pragma unroll
-            for (int b = 0; b < kBins; b++) pdf[b] = A.pdf[pix * kBins + b];
-            that = A.that[pix];
-            range_of(a, R, pdf, 0u, false, b0, b1);
+                for (int b = 0; b < kBins; b++) pdf[b] = A.pdf[pix * kBins + b];
+                that = A.that[pix];
+                range_of(a, R, pdf, 0u, false, b0, b1);
+            }
+            march_range<ST, SHADE>(A, s_tf, R, b0, b1, C0, C1, C2, T, evald);
         }
-        march_range<ST, SHADE>(A, s_tf, R, b0, b1, C0, C1, C2, T, evald);
-        if (fabsf(T - that) > A.eps) {
+        if (check && fabsf(T - that) > A.eps) {
             fb = 1;
             plain_ray<ST, SHADE>(a, s_tf, R, C0, C1, C2, T, evald);
         }
@@ -1031,7 +1112,9 @@ static cudaError_t launch_imp_st(const ImportanceArgs &a, int nviews, cudaStream
         kern<<<grid, 128, smem, s>>>(a);
         return cudaGetLastError();
     };
-    return a.range ? go(importance_kernel<ST, SHADE, true>) : go(importance_kernel<ST, SHADE, false>);
+    if (a.range) return go(importance_kernel<ST, SHADE, kSrcRecords>);
+    if (a.sampling == RC_SAMPLING_INVCDF) return go(importance_kernel<ST, SHADE, kSrcInvCdf>);
+    return go(importance_kernel<ST, SHADE, kSrcRange>);
 }
 
 cudaError_t launch_importance(const ImportanceArgs &a, int nviews, cudaStream_t s) {

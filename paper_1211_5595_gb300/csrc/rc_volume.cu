@@ -36,7 +36,9 @@ cudaError_t launch_pairs(VolDev v, void *dst, cudaStream_t s) {
 // volume so border voxels are replicated; codes clamped to vmax) are read once
 // into shared memory and written out as
 //   - the apron brick in the storage type: F32 keeps the code, F16 stores
-//     fp16(code / vmax) (FP32 quotient, round-to-nearest-even), U16 the code;
+//     h = fp16((code - o) / o) with the volume's offset o (a power of two with
+//     2o >= vmax, so |code - o| <= 2048 is an FP16 integer for 12-bit data and
+//     h is exact), U16 the code;
 //   - FP32 and uint16 storage: the 17^3 value+gradient entries of voxels
 //     16b .. 16b+16 (clamped) as (V, V(x+1) - V(x-1), V(y+1) - V(y-1),
 //     V(z+1) - V(z-1)), neighbour indices clamped to the volume: exact in FP32
@@ -51,6 +53,7 @@ struct PrepArgs {
     const uint16_t *stage;
     int n[3], cb[3], c4[3];
     int vmax;
+    int f16o;                    // FP16 storage: the offset o
     void *apron;
     void *vg;                    // float4 (FP32 storage), uint2 (uint16 storage), null (FP16)
     uint16_t *mn, *mx, *mn4, *mx4;
@@ -73,7 +76,8 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs A) {
         s_code[e] = (uint16_t)code;
         const size_t o = (size_t)b * kApronVox + e;
         if (ST == RC_STORE_F32) ((float *)A.apron)[o] = (float)code;
-        else if (ST == RC_STORE_F16) ((__half *)A.apron)[o] = __float2half_rn(__fdiv_rn((float)code, (float)A.vmax));
+        else if (ST == RC_STORE_F16)
+            ((__half *)A.apron)[o] = __float2half_rn(__fdiv_rn((float)(code - A.f16o), (float)A.f16o));
         else ((uint16_t *)A.apron)[o] = (uint16_t)code;
     }
     __syncthreads();
@@ -176,6 +180,7 @@ cudaError_t launch_prep(const uint16_t *stage, VolDev v, void *apron, void *vg, 
         a.c4[i] = (v.n[i] - 1 + 3) / 4;
     }
     a.vmax = v.vmax;
+    a.f16o = (int)v.f16o;
     a.apron = apron;
     a.vg = vg;
     a.mn = mn;
@@ -268,16 +273,23 @@ cudaError_t launch_minmax4(const uint16_t *stage, const int n[3], int vmax, int 
     return cudaGetLastError();
 }
 
-// Whether any table entry a value in [vmn, vmx] can touch has non-zero
-// opacity, with the march's coordinate u(v) = fl(v * ucoef).
-__device__ __forceinline__ bool range_visible(float vmn, float vmx, int vmax, int f16_values, const TFDev &tf) {
-    const int K = tf.K;
-    if (f16_values) {
-        vmn = __half2float(__float2half_rn(__fdiv_rn(vmn, (float)vmax)));
-        vmx = __half2float(__float2half_rn(__fdiv_rn(vmx, (float)vmax)));
+// The march's table coordinate of a code as the volume stores it: raw codes
+// u = fl(v * ucoef); FP16 storage (f16o = o > 0) h = fp16((v - o) / o) and
+// u = fl((h + 1) * ucoef), as tf_coord computes them.
+__device__ __forceinline__ float code_coord(float v, int f16o, float ucoef) {
+    if (f16o) {
+        const float h = __half2float(__float2half_rn(__fdiv_rn(v - (float)f16o, (float)f16o)));
+        return __fmaf_rn(h, ucoef, ucoef);
     }
-    const int lo = min((int)floorf(__fmul_rn(vmn, tf.ucoef)), K - 1);
-    const int hi = min((int)floorf(__fmul_rn(vmx, tf.ucoef)) + 1, K - 1);
+    return __fmul_rn(v, ucoef);
+}
+
+// Whether any table entry a value in [vmn, vmx] can touch has non-zero
+// opacity, with the march's coordinate u.
+__device__ __forceinline__ bool range_visible(float vmn, float vmx, int f16o, const TFDev &tf) {
+    const int K = tf.K;
+    const int lo = min((int)floorf(code_coord(vmn, f16o, tf.ucoef)), K - 1);
+    const int hi = min((int)floorf(code_coord(vmx, f16o, tf.ucoef)) + 1, K - 1);
     for (int i = lo; i <= hi; i++) {
         const float a = tf.M >= 2 ? tf.amax[i] : (tf.fp16 ? half4_to_float4(tf.f16[i]).w : tf.f32[i].w);
         if (a != 0.0f) return true;
@@ -289,8 +301,8 @@ __device__ __forceinline__ bool range_visible(float vmn, float vmx, int vmax, in
 // the brick's mask is set when sub-block (4*bx + sx, 4*by + sy, 4*bz + sz)
 // exists and may hold non-zero opacity; each warp's ballot is one 32-bit half.
 __global__ void __launch_bounds__(128) finemask_kernel(const uint16_t *mn4, const uint16_t *mx4, int c0, int c1,
-                                                       int c2, int cb0, int cb1, int nbricks, int vmax,
-                                                       int f16_values, TFDev tf, uint32_t *fine) {
+                                                       int c2, int cb0, int cb1, int nbricks, int f16o,
+                                                       TFDev tf, uint32_t *fine) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int b = (int)(e >> 6), t = (int)(e & 63);
     bool vis = false;
@@ -299,7 +311,7 @@ __global__ void __launch_bounds__(128) finemask_kernel(const uint16_t *mn4, cons
         const int jx = 4 * bx + (t & 3), jy = 4 * by + ((t >> 2) & 3), jz = 4 * bz + (t >> 4);
         if (jx < c0 && jy < c1 && jz < c2) {
             const int j = (jz * c1 + jy) * c0 + jx;
-            vis = range_visible((float)mn4[j], (float)mx4[j], vmax, f16_values, tf);
+            vis = range_visible((float)mn4[j], (float)mx4[j], f16o, tf);
         }
     }
     const unsigned bits = __ballot_sync(0xffffffffu, vis);
@@ -307,33 +319,28 @@ __global__ void __launch_bounds__(128) finemask_kernel(const uint16_t *mn4, cons
 }
 
 cudaError_t launch_finemask(const uint16_t *mn4, const uint16_t *mx4, const int n[3], const int cb[3], int vmax,
-                            int f16_values, TFDev tf, unsigned long long *fine, cudaStream_t s) {
+                            int f16o, TFDev tf, unsigned long long *fine, cudaStream_t s) {
     const int c0 = (n[0] - 1 + 3) / 4, c1 = (n[1] - 1 + 3) / 4, c2 = (n[2] - 1 + 3) / 4;
     const int nb = cb[0] * cb[1] * cb[2];
     const long long threads = (long long)nb * 64;
-    finemask_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(mn4, mx4, c0, c1, c2, cb[0], cb[1], nb, vmax,
-                                                                      f16_values, tf,
-                                                                      reinterpret_cast<uint32_t *>(fine));
+    (void)vmax;
+    finemask_kernel<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(mn4, mx4, c0, c1, c2, cb[0], cb[1], nb, f16o,
+                                                                      tf, reinterpret_cast<uint32_t *>(fine));
     return cudaGetLastError();
 }
 
 // A cell-brick is occupied unless every entry lo..hi its samples can touch has
-// zero opacity, with the march's own coordinate u(v) = fl(v * ucoef): raw codes
-// v = min, max; FP16 storage v = fp16(min / vmax), fp16(max / vmax). With a
-// 2-D table an entry's opacity is its largest over the gradient rows.
-__global__ void occupancy_kernel(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax, int f16_values,
-                                 TFDev tf, uint8_t *occ) {
+// zero opacity, with the march's own coordinate u of the brick's min and max
+// as stored (code_coord). With a 2-D table an entry's opacity is its largest
+// over the gradient rows.
+__global__ void occupancy_kernel(const uint16_t *mn, const uint16_t *mx, int nbricks, int f16o, TFDev tf,
+                                 uint8_t *occ) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbricks) return;
     const int K = tf.K;
     int lo, hi;
-    float vmn = (float)mn[b], vmx = (float)mx[b];
-    if (f16_values) {
-        vmn = __half2float(__float2half_rn(__fdiv_rn(vmn, (float)vmax)));
-        vmx = __half2float(__float2half_rn(__fdiv_rn(vmx, (float)vmax)));
-    }
-    lo = (int)floorf(__fmul_rn(vmn, tf.ucoef));
-    hi = (int)floorf(__fmul_rn(vmx, tf.ucoef)) + 1;
+    lo = (int)floorf(code_coord((float)mn[b], f16o, tf.ucoef));
+    hi = (int)floorf(code_coord((float)mx[b], f16o, tf.ucoef)) + 1;
     hi = min(hi, K - 1);
     lo = min(lo, K - 1);
     uint8_t any = 0;
@@ -344,9 +351,10 @@ __global__ void occupancy_kernel(const uint16_t *mn, const uint16_t *mx, int nbr
     occ[b] = any;
 }
 
-cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax, int f16_values,
+cudaError_t launch_occupancy(const uint16_t *mn, const uint16_t *mx, int nbricks, int vmax, int f16o,
                              TFDev tf, uint8_t *occ, cudaStream_t s) {
-    occupancy_kernel<<<(nbricks + 127) / 128, 128, 0, s>>>(mn, mx, nbricks, vmax, f16_values, tf, occ);
+    (void)vmax;
+    occupancy_kernel<<<(nbricks + 127) / 128, 128, 0, s>>>(mn, mx, nbricks, f16o, tf, occ);
     return cudaGetLastError();
 }
 

@@ -18,19 +18,19 @@ def rc():
     return rc
 
 
-def declared_symbols():
-    names = set()
-    inc = os.path.join(ROOT, "include")
-    for f in os.listdir(inc):
-        if f.endswith(".h"):
-            text = open(os.path.join(inc, f)).read()
-            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names.update(re.findall(r"\b(rc_[a-z0-9_]+)\s*\(", text))
-    return names
+def declared_symbols(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"\b(rc_[a-z0-9_]+)\s*\(", text))
+
+
+def test_headers_are_known():
+    # every header of include/ is checked against its library below
+    assert sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")) == ["rc.h", "rc_probe.h"]
 
 
 def test_every_declared_symbol_is_exported(rc):
-    names = declared_symbols()
+    names = declared_symbols("rc.h")
     assert len(names) >= 16
     lib = C.CDLL(rc.LIB_PATH)
     missing = [n for n in sorted(names) if not hasattr(lib, n)]
@@ -39,6 +39,21 @@ def test_every_declared_symbol_is_exported(rc):
     assert names <= set(rc.SIGNATURES), sorted(names - set(rc.SIGNATURES))
     for n in names:
         assert callable(getattr(rc, n)), n
+
+
+def test_probe_library_exports_its_header(rc):
+    """The measurement probes live in their own library, outside the
+    raycasting interface."""
+    from paper_1211_5595_gb300 import build
+    names = declared_symbols("rc_probe.h")
+    assert names == {"rc_probe_read_l1", "rc_probe_read_l2", "rc_probe_l1_bytes"}
+    lib = C.CDLL(build.PROBE_LIB)
+    assert all(hasattr(lib, n) for n in names)
+    assert not (names & declared_symbols("rc.h"))
+    lib.rc_probe_read_l1.argtypes = [C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]
+    # invalid arguments are refused before any launch (cudaErrorInvalidValue = 1)
+    assert lib.rc_probe_read_l1(None, 16, 1, None) == 1
+    assert lib.rc_probe_read_l1(C.c_void_p(16), 1 << 20, 1, None) == 1
 
 
 def test_status_strings(rc):

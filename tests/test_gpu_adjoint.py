@@ -69,7 +69,9 @@ def seeded_upstream(seed, pixels, shape):
 def test_gradient_matches_oracle(rc, orc, c4, shade, term, bspline):
     """Against the FP64 oracle's reverse mode, with trilinear or cubic
     B-spline reconstruction (the B-spline also through the entry point that
-    allocates nothing, which reads the apron bricks instead of the pairs)."""
+    allocates nothing; here the pair bricks exist, so both entry points read
+    them; the apron path of a volume without pairs is covered in
+    test_zz_no_alloc.py)."""
     ph, ctx, vol, cams = c4
     tf = init_tf()
     filt = rc.RC_FILTER_BSPLINE if bspline else rc.RC_FILTER_TRILINEAR

@@ -1,10 +1,11 @@
-"""Precision form: the 512x512x256 phantom stored as FP16 (normalised) and as
-raw uint16, a 1024-entry FP16 table, FP32 compositing, step 0.25, shaded,
-2048^2 image. Checked against the FP64 oracle on the original uint16 codes and
-the FP32 table (total error, tolerance 4e-3) on 4096 seeded rays of the 2048^2
-frame and on the full frame rendered at 512^2, and against the diagnostic
-oracle that uses the same FP16-rounded volume and table (arithmetic error
-only, tolerance 2e-4)."""
+"""Precision form: the 512x512x256 phantom stored as FP16 (offset-normalised,
+(code - 2048) / 2048, exact for 12-bit codes) and as raw uint16, a 1024-entry
+FP16 table, FP32 compositing, step 0.25, shaded, 2048^2 image. Checked against
+the FP64 oracle on the original uint16 codes and the FP32 table (total error,
+tolerance 4e-3) on 4096 seeded rays of the 2048^2 frame and on every pixel of
+the full frame rendered at 512^2, and against the diagnostic oracle that uses
+the same FP16-rounded volume and table (arithmetic error only, tolerance
+2e-4)."""
 import numpy as np
 import pytest
 
@@ -60,16 +61,9 @@ def test_precision_form(rc, orc, c3, storage):
                                       tf_fp16=True, **kw))
         compare(small, diag_s, TOL_FP32)
         tot_s = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cs, **kw))
-        if storage == "U16":
-            err_s, _ = compare(small, tot_s, TOL_REDUCED)
-        else:
-            # FP16 holds 12-bit codes above 2048 only to +-1 code (11-bit
-            # significand): on the steepest table ramp (3.7e-3 opacity per code)
-            # a few boundary pixels of the frame exceed 4e-3 of total error while
-            # the arithmetic (diagnostic comparison above) stays within 2e-4
-            d = np.abs(small.reshape(-1, 4) - tot_s["rgba"].reshape(-1, 4)).max(axis=1)
-            err_s = float(d.max())
-            assert (d > TOL_REDUCED).mean() < 1e-4 and err_s < 1e-2, (err_s, int((d > TOL_REDUCED).sum()))
+        # every pixel of the frame within the reduced-precision tolerance of the
+        # FP64 oracle on the original codes and the FP32 table
+        err_s, _ = compare(small, tot_s, TOL_REDUCED)
         print(f"{storage}: 4096 rays max-abs {err_total:.2e} (diagnostic {err_diag:.2e}); 512^2 max-abs "
               f"{err_s:.2e}, PSNR {psnr(small, tot_s['rgba']):.1f} dB")
     finally:

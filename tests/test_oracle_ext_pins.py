@@ -219,20 +219,46 @@ def test_tf2d_equal_rows_equals_1d(orc):
 
 
 def test_tf2d_normalised_values_use_code_units(orc):
-    """FP16-normalised storage (values code / vmax) classifies with the
-    gradient in code units: with vmax = 4096 and even codes the normalised
-    values are exact, and every sample matches the raw-code scene."""
+    """FP16 storage (values (code - o) / o, o = 2048 for vmax 4096) classifies
+    with the gradient in code units: every code up to 4096 is exact in that
+    form, so every sample (odd codes included) matches the raw-code scene."""
     dims = (30, 26, 22)
-    vol = ramp_volume(dims, (40, -16, 28), 16 * 25 + 100) & 0xFFFE
+    vol = ramp_volume(dims, (40, -16, 28), 16 * 25 + 101)
+    assert (vol & 1).any()
     tab = affine_table(64, 8, COEF)
     cam = synth.orbit_camera(dims, (1, 1, 1), 15.0, width=32, height=32)
     raw = orc.Scene(vol, (1, 1, 1), tab, cam, term=1.0, gmax=60.0, vmax=4096)
     nrm = orc.Scene(vol, (1, 1, 1), tab, cam, term=1.0, gmax=60.0, vmax=4096, value_mode=1)
     sr = samples_of(orc, raw, PIXELS)
     sn = samples_of(orc, nrm, PIXELS)
-    np.testing.assert_allclose(sn["v"] * 4096.0, sr["v"], rtol=1e-15, atol=1e-9)
-    np.testing.assert_allclose(sn["gw"], sr["gw"], rtol=1e-12, atol=1e-12)
-    np.testing.assert_allclose(sn["a"], sr["a"], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(sn["v"], sr["v"])
+    np.testing.assert_array_equal(sn["gw"], sr["gw"])
+    np.testing.assert_array_equal(sn["a"], sr["a"])
+
+
+def test_fp16_offset_form_is_exact_for_12_bit_codes(orc):
+    """The FP16 storage form holds every 12-bit code exactly: (c - 2048) / 2048
+    is an integer of magnitude <= 2048 over a power of two, and numpy's own
+    FP16 rounding round-trips it for all 4096 codes (an FP16 of c / 4095 does
+    not: codes above 2048 keep only 11 significant bits). So the oracle's
+    diagnostic FP16 scene renders the raw-code image exactly, on a shaded
+    phantom with a 12-bit table, and the occupancy mask of the stored form
+    equals the raw one."""
+    c = np.arange(4096, dtype=np.float64)
+    h = ((c - 2048.0) / 2048.0).astype(np.float16)
+    np.testing.assert_array_equal((h.astype(np.float64) + 1.0) * 2048.0, c)
+    old = (c / 4095.0).astype(np.float16).astype(np.float64) * 4095.0
+    assert np.abs(old - c).max() > 0.4
+    ph = synth.head_phantom((40, 36, 30), (1.0, 1.1, 1.3), seed=17, tumor_radius_vox=4)
+    tf = synth.tf_table(1024)
+    cam = synth.orbit_camera(ph.dims, ph.spacing, 35.0, width=40, height=36)
+    a = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cam, step=0.25, shade=True))
+    b = orc.render(orc.Scene(ph.vol, ph.spacing, tf, cam, step=0.25, shade=True, value_mode=1))
+    assert a["rgba"][..., 3].max() > 0.3
+    np.testing.assert_array_equal(a["rgba"], b["rgba"])
+    mn, mx = orc.brick_minmax(ph.vol)
+    np.testing.assert_array_equal(orc.occupancy(ph.dims, tf, mn, mx, value_mode=1),
+                                  orc.occupancy(ph.dims, tf, mn, mx))
 
 
 def test_tf2d_occupancy_is_sound(orc):

@@ -531,7 +531,8 @@ def test_importance_constant_volume_closed_form(orc, pdf_kind, nimp):
         pdf[7], cover = 1.0, 9 * L / 32
     else:
         pdf[3], pdf[20], cover = 0.3, 0.7, 22 * L / 32
-    rgba, tfin, ns = orc.importance(sc, pdf[None, :], nimp=nimp)
+    r = orc.importance(sc, pdf[None, :], nimp=nimp)
+    rgba, ns = r["rgba"], r["nsamp"]
     expect = 1.0 - (1.0 - float(np.float32(a))) ** cover
     assert ns[0] == nimp
     assert rgba[0, 3] == pytest.approx(expect, abs=2e-6)
@@ -552,9 +553,9 @@ def test_importance_range_starts_at_first_occupied_bin(orc):
     cam = axis_camera(64, 3.0, 3.0)
     early = np.zeros(32); early[11] = 1.0                   # range ends after bin 12 (x about 38)
     late = np.full(32, 1 / 32)
-    a, _, _ = orc.importance(orc.Scene(vol, (1, 1, 1), tf, cam, term=1.0), early[None, :])
-    b, _, _ = orc.importance(orc.Scene(near_only, (1, 1, 1), tf, cam, term=1.0), early[None, :])
-    c, _, _ = orc.importance(orc.Scene(vol, (1, 1, 1), tf, cam, term=1.0), late[None, :])
+    a = orc.importance(orc.Scene(vol, (1, 1, 1), tf, cam, term=1.0), early[None, :])["rgba"]
+    b = orc.importance(orc.Scene(near_only, (1, 1, 1), tf, cam, term=1.0), early[None, :])["rgba"]
+    c = orc.importance(orc.Scene(vol, (1, 1, 1), tf, cam, term=1.0), late[None, :])["rgba"]
     assert a[0, 3] > 0.3 and a[0, 3] == b[0, 3]
     assert c[0, 3] > a[0, 3] + 0.1
     # 8 voxels of opacity 0.1 per voxel: the composite approaches 1 - 0.9^8
@@ -571,9 +572,113 @@ def test_importance_uniform_pdf_is_midpoint_march(orc):
     cam = synth.orbit_camera((40, 40, 30), (1, 1, 1), 0.0, width=8, height=8)
     sc = orc.Scene(vol, (1, 1, 1), tf, cam, term=1.0)
     pdf = np.full((64, 32), 1 / 32)
-    rgba, tfin, ns = orc.importance(sc, pdf, nimp=512)
+    r = orc.importance(sc, pdf, nimp=512)
+    rgba, tfin, ns = r["rgba"], r["tfinal"], r["nsamp"]
     bins, tprof = orc.profiles(sc)
     hit = ns > 0
     assert hit.sum() > 10
     np.testing.assert_allclose(tfin, tprof, atol=1e-12)
     np.testing.assert_allclose(rgba[:, 3], bins.sum(axis=1), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# the inverse-CDF reading of the importance samples
+# --------------------------------------------------------------------------
+def mixture_cdf(pdf, lam, s):
+    """CDF at s in [0, 32] (bin units) of the piecewise-constant density
+    (1 - lam) pdf + lam / 32, normalised to 1 (FP64)."""
+    q = (1 - lam) * np.asarray(pdf, np.float64) + lam / 32
+    Q = np.concatenate([[0.0], np.cumsum(q)])
+    b = np.minimum(np.floor(s).astype(int), 31)
+    return (Q[b] + (s - b) * q[b]) / Q[-1]
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.05, 0.5])
+def test_invcdf_samples_are_stratified(orc, lam):
+    """Sample j sits where the mixture's CDF reaches (j + 0.5) / nimp (one
+    sample per stratum), and the segments between the midpoints of
+    neighbouring samples tile the chord [t_near, t_far]."""
+    vol = np.full((8, 8, 60), 2000, dtype=np.uint16)
+    tf = identity_tf({2000: (1.0, 1.0, 1.0, 0.05)})
+    sc = orc.Scene(vol, (1, 1, 1), tf, axis_camera(60, 3.0, 3.0), term=1.0)
+    g = orc.ray_geometry(sc, 0, 0)
+    L = g["tf"] - g["tn"]
+    rng = np.random.default_rng(4)
+    pdf = rng.random(32) ** 4
+    pdf[[2, 9, 10, 30]] = 0.0
+    pdf /= pdf.sum()
+    for nimp in (1, 7, 64):
+        t, ln = orc.importance_positions(sc, 0, 0, pdf, nimp=nimp, sampling="invcdf", lam=lam)
+        s = (t - g["tn"]) / (L / 32)
+        np.testing.assert_allclose(mixture_cdf(pdf, lam, s), (np.arange(nimp) + 0.5) / nimp, atol=2e-6)
+        assert np.all(np.diff(t) >= 0)
+        mid = np.concatenate([[g["tn"]], (t[1:] + t[:-1]) / 2, [g["tf"]]])
+        np.testing.assert_allclose(ln, np.diff(mid), atol=2e-5)     # FP32 rounding at t ~ 60 mm
+        assert ln.sum() == pytest.approx(L, abs=1e-4)
+
+
+def test_invcdf_hand_worked_positions(orc):
+    """lambda = 0, mass 0.3 in bin 3 and 0.7 in bin 20, 10 samples: u = 0.05,
+    0.15, 0.25 fall in bin 3 at fractions 1/6, 1/2, 5/6; u = 0.35 .. 0.95 in
+    bin 20 at fractions (u - 0.3) / 0.7. lambda = 1 puts sample j at the centre
+    of the j-th of nimp equal segments of the chord."""
+    vol = np.full((8, 8, 60), 2000, dtype=np.uint16)
+    tf = identity_tf({2000: (1.0, 1.0, 1.0, 0.05)})
+    sc = orc.Scene(vol, (1, 1, 1), tf, axis_camera(60, 3.0, 3.0), term=1.0)
+    g = orc.ray_geometry(sc, 0, 0)
+    bw = (g["tf"] - g["tn"]) / 32
+    pdf = np.zeros(32)
+    pdf[3], pdf[20] = 0.3, 0.7
+    t, _ = orc.importance_positions(sc, 0, 0, pdf, nimp=10, sampling="invcdf", lam=0.0)
+    u = (np.arange(10) + 0.5) / 10
+    pos = np.where(u < 0.3, 3 + u / 0.3, 20 + (u - 0.3) / 0.7)
+    np.testing.assert_allclose(t, g["tn"] + pos * bw, atol=2e-5)
+    t1, ln1 = orc.importance_positions(sc, 0, 0, None, nimp=5, sampling="invcdf", lam=1.0)
+    L = g["tf"] - g["tn"]
+    np.testing.assert_allclose(t1, g["tn"] + (np.arange(5) + 0.5) * L / 5, atol=2e-5)
+    np.testing.assert_allclose(ln1, L / 5, atol=2e-5)
+
+
+@pytest.mark.parametrize("lam", [0.05, 1.0])
+@pytest.mark.parametrize("nimp", [64, 9])
+def test_invcdf_constant_volume_closed_form(orc, lam, nimp):
+    """In a constant medium the midpoint segments tile the whole chord, so for
+    any PDF the composite is 1 - (1 - a)^(L / ds_ref) with L = t_far - t_near
+    (Eq. 3 per segment, the segment lengths summing to L)."""
+    V0, a = 2000, 0.03
+    vol = np.full((8, 8, 60), V0, dtype=np.uint16)
+    tf = identity_tf({V0: (0.2, 0.4, 0.8, a)})
+    sc = orc.Scene(vol, (1, 1, 1), tf, axis_camera(60, 3.0, 3.0), term=1.0)
+    g = orc.ray_geometry(sc, 0, 0)
+    pdf = np.zeros(32)
+    pdf[3], pdf[20] = 0.3, 0.7
+    r = orc.importance(sc, pdf[None, :], nimp=nimp, sampling="invcdf", lam=lam)
+    expect = 1.0 - (1.0 - float(np.float32(a))) ** (g["tf"] - g["tn"])
+    assert r["nsamp"][0] == nimp
+    assert r["rgba"][0, 3] == pytest.approx(expect, abs=2e-5)
+    np.testing.assert_allclose(r["rgba"][0, :3], np.float32([0.2, 0.4, 0.8]) * r["rgba"][0, 3], atol=1e-12)
+
+
+@pytest.mark.parametrize("sampling", ["range", "invcdf"])
+def test_importance_termination_tie_gives_both_branches(orc, sampling):
+    """With term set to the opacity the march reaches at its m-th sample, the
+    stop decision there is a tie: the oracle flags it and returns both
+    branches, the composites of m and m + 1 samples of the constant medium
+    (Eq. 4 stopped either side of the threshold)."""
+    V0, a = 2000, 0.03
+    vol = np.full((8, 8, 60), V0, dtype=np.uint16)
+    tf = identity_tf({V0: (0.2, 0.4, 0.8, a)})
+    pdf = np.full((1, 32), 1 / 32)
+    base = orc.Scene(vol, (1, 1, 1), tf, axis_camera(60, 3.0, 3.0), term=1.0)
+    nimp, m = 64, 23
+    t, ln = orc.importance_positions(base, 0, 0, pdf, nimp=nimp, sampling=sampling, lam=1.0)
+    ap = 1.0 - (1.0 - float(np.float32(a))) ** (ln / 1.0)
+    T = np.cumprod(1.0 - ap)
+    term = float(np.float32(1.0 - T[m - 1]))
+    sc = orc.Scene(vol, (1, 1, 1), tf, axis_camera(60, 3.0, 3.0), term=term)
+    r = orc.importance(sc, pdf, nimp=nimp, sampling=sampling, lam=1.0)
+    assert r["tie"][0]
+    got = sorted([r["rgba"][0, 3], r["alt"][0, 3]])
+    np.testing.assert_allclose(got, [1.0 - T[m - 1], 1.0 - T[m]], atol=1e-9)
+    far = orc.Scene(vol, (1, 1, 1), tf, axis_camera(60, 3.0, 3.0), term=0.5 * term)
+    assert not orc.importance(far, pdf, nimp=nimp, sampling=sampling, lam=1.0)["tie"][0]
