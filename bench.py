@@ -379,6 +379,36 @@ def precision_form(rc, ctx, flush, stream, hbm_peak):
     return out, capture
 
 
+def precision_frames(rc, ctx, stream):
+    """One 2048^2 frame of the precision workload per storage form (FP32 with
+    the FP32 table, FP16 and uint16 with the FP16 table), each rendered twice
+    (the second launch timed): exactly two march launches per form, in that
+    order, for a profiler to capture."""
+    import torch
+    wp = synth.WORKLOADS["precision_512x512x256"]
+    ph = synth.workload_phantom("precision_512x512x256")
+    tf = synth.tf_table(wp["K"])
+    cam = synth.orbit_camera(ph.dims, ph.spacing, wp["azimuths"][0], width=wp["width"], height=wp["height"])
+    P = rc.RenderParams(step_vox=wp["step"], term=wp["term"], shade=wp["shade"], skip=True)
+    img = torch.empty((wp["height"], wp["width"], 4), device="cuda")
+    out = {}
+    for name, storage, fp16 in (("f32", rc.RC_STORE_F32, False), ("f16", rc.RC_STORE_F16, True),
+                                ("u16", rc.RC_STORE_U16, True)):
+        vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, storage)
+        rc.rc_volume_upload(ctx, vol, ph.vol)
+        rc.rc_tf_set(ctx, tf, fp16)
+        rc.rc_camera_set(ctx, cam)
+        rc.rc_render(ctx, vol, P, img)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        rc.rc_render(ctx, vol, P, img)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_frame": ev[0].elapsed_time(ev[1])}
+        rc.rc_volume_destroy(ctx, vol)
+    return out
+
+
 def oracle_errors(gpu, o):
     """Max-abs per channel of GPU colours against the oracle's (a ray whose
     stop decision is a termination tie takes the nearer branch) and the PSNR
@@ -719,9 +749,11 @@ def main():
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal form")
     ap.add_argument("--no-precision", action="store_true", help="skip the 512x512x256 precision form")
     ap.add_argument("--proposal-phantoms", type=int, default=8, help="training phantoms of the proposal form")
-    ap.add_argument("--case", choices=["adjoint", "network"], default=None,
-                    help="run only the table-gradient form or the network throughput (forward and training "
-                         "gradient, seeded initial network) and print its JSON (profiling)")
+    ap.add_argument("--case", choices=["adjoint", "network", "precision"], default=None,
+                    help="run only the table-gradient form, the network throughput (forward and training "
+                         "gradient, seeded initial network) or one 2048^2 frame of each precision form (FP32, "
+                         "FP16, uint16 storage: two launches each, the first untimed) and print its JSON "
+                         "(profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -756,6 +788,8 @@ def main():
         flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda", dtype=torch.float32)
         if args.case == "adjoint":
             out = adjoint_form(rc, ctx, flush, stream)
+        elif args.case == "precision":
+            out = precision_frames(rc, ctx, stream)
         else:
             rc.rc_proposal_load(ctx, rc.pack_proposal_blob(synth.proposal_init_params(61)))
             out = network_throughput(rc, ctx, stream)

@@ -14,7 +14,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librc.so")
+# RC_DEBUG=1 in the environment loads the debug build (device index checks
+# reported as RC_ERR_CUDA at the next synchronising call) instead
+LIB_PATH = os.path.join(_HERE, "librc_debug.so" if os.environ.get("RC_DEBUG") == "1" else "librc.so")
 
 RC_OK, RC_ERR_INVALID_ARG, RC_ERR_OOM, RC_ERR_CUDA, RC_ERR_STATE, RC_ERR_TIMEOUT, \
     RC_ERR_UNSUPPORTED, RC_ERR_FORMAT = range(8)

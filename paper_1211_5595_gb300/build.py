@@ -73,17 +73,29 @@ def _build_lib(lib, src_dir, headers, tag, force, verbose, extra_flags):
     return lib
 
 
+DEBUG_LIB = os.path.join(PKG, "librc_debug.so")
+
+
+def build_debug(force: bool = False, verbose: bool = False) -> str:
+    """librc_debug.so: the same library compiled with -DRC_DEBUG (every brick
+    and table index checked on the device, failures reported as a status)."""
+    return _build_lib(DEBUG_LIB, CSRC, ["rc.h"], "debug_", force, verbose, ("-DRC_DEBUG",))
+
+
 def build_probe(force: bool = False, verbose: bool = False) -> str:
     """librc_probe.so: the bandwidth probes the bench's rooflines use."""
     return _build_lib(PROBE_LIB, PROBE_DIR, ["rc_probe.h"], "probe_", force, verbose, ())
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """librc.so (and librc_probe.so beside it); returns librc.so's path."""
-    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+    """librc.so, with librc_debug.so and librc_probe.so beside it; returns
+    librc.so's path."""
+    with cf.ThreadPoolExecutor(max_workers=3) as ex:
         probe = ex.submit(build_probe, force, verbose)
+        debug = ex.submit(build_debug, force, verbose)
         lib = _build_lib(LIB, CSRC, ["rc.h"], "", force, verbose, extra_flags)
         probe.result()
+        debug.result()
     return lib
 
 

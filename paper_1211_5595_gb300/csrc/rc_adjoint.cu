@@ -204,10 +204,11 @@ __global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 128) adjoint_kernel(cons
             float4 e;
             if (TF2) {
                 int j;
-                e = classify2_at(a.tf, tf_coord<ST>(val, a.tf.ucoef), tf2_row_coord(a.tf, gr), i, j, w, wb);
+                e = classify2_at(a.tf, tf_coord<ST>(val, a.tf.ucoef), tf2_row_coord(a.tf, gr), i, j, w, wb,
+                                 RC_DBG_ERR(a.vol));
                 i += j * K;                           // entry (i, j) of the M x K table
             } else {
-                e = classify(s_tf, K, tf_coord<ST>(val, a.tf.ucoef), &i, &w);
+                e = classify(s_tf, K, tf_coord<ST>(val, a.tf.ucoef), &i, &w, RC_DBG_ERR(a.vol));
             }
             float ap = correct_alpha<RM>(e.w, a.p.rmode, a.p.ratio);
             float r = e.x, gg = e.y, b = e.z;

@@ -170,14 +170,23 @@ static long long wait_budget(int *issue_mma) {
     return fault ? 2000000ll : 2000000000ll;
 }
 
-// Reads and clears the device error word (synchronises the stream).
+// Reads and clears the device error word (synchronises the stream): bit 0,
+// a bounded wait of a tensor-core kernel gave up (RC_ERR_TIMEOUT); bit 1, an
+// index check of a debug build failed, with the sites in bits 8 and up
+// (RC_ERR_CUDA).
 static rc_status check_device_errors(rc_context *ctx, const char *who) {
     RC_CUDA(ctx, cudaMemcpyAsync(ctx->h_stats + 5, ctx->d_stats + 5, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->h_stats[5] != 0) {
+    const unsigned long long word = ctx->h_stats[5];
+    if (word != 0) {
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats + 5, 0, sizeof(unsigned long long), ctx->stream));
         RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (word & 2)
+            return fail(ctx, RC_ERR_CUDA,
+                        "%s: a device index check failed (debug build; sites 0x%llx: 1 brick, 2 table, 4 2-D table); "
+                        "the outputs of the launches since the last check are invalid",
+                        who, (word >> 8) & 0xffull);
         return fail(ctx, RC_ERR_TIMEOUT, "%s: a tensor-core wait gave up (outputs of that launch are invalid)", who);
     }
     return RC_OK;
@@ -381,6 +390,14 @@ static VolDev vol_dev(const rc_volume *v) {
     d.vscale = full_scale(v);
     d.f16o = v->storage == RC_STORE_F16 ? (float)f16_offset(v->vmax) : 0.0f;
     d.gmin = 1e-6f * d.vscale;
+#ifdef RC_DEBUG
+    // debug builds: the kernels' index checks report to the context's error
+    // word; RC_DEBUG_POISON (tests) moves every brick index out of range, so
+    // that every check fires and replaces the index by 0
+    d.dbg_err = error_word(v->ctx);
+    const char *poison = getenv("RC_DEBUG_POISON");
+    d.dbg_poison = poison && *poison ? v->nbricks : 0;
+#endif
     return d;
 }
 

@@ -7,6 +7,26 @@
 
 namespace rc {
 
+// Debug builds (-DRC_DEBUG, librc_debug.so) check every brick index and every
+// table entry index against its extent before it is used: one out of range
+// sets bit 1 of the context's error word, and bit 8 + site, and is replaced
+// by 0 (an element inside the buffer), so that no access leaves its buffer
+// and nothing traps; the next rc_context_sync (or statistics read) returns
+// RC_ERR_CUDA. Release builds compile none of it. The brick index feeds every
+// voxel, value+gradient and pair gather and every mask lookup; the table
+// index feeds the classification and the adjoint's accumulators.
+#ifdef RC_DEBUG
+enum { kSiteBrick = 0, kSiteTable = 1, kSiteTable2 = 2 };
+__device__ __forceinline__ int dbg_index(int idx, int bound, int *err, int site) {
+    if ((unsigned)idx < (unsigned)bound) return idx;
+    if (err) atomicOr(err, 2 | (256 << site));
+    return 0;
+}
+#define RC_DBG_ERR(v) ((v).dbg_err)
+#else
+#define RC_DBG_ERR(v) nullptr
+#endif
+
 struct Ray {
     float o[3], d[3], dir[3];
     float tn, tf, ds;
@@ -92,7 +112,12 @@ __device__ __forceinline__ void cell_of(const VolDev &v, const float p[3], Cell 
 }
 
 __device__ __forceinline__ int brick_of(const VolDev &v, const Cell &c) {
-    return ((c.i[2] >> 4) * v.cb[1] + (c.i[1] >> 4)) * v.cb[0] + (c.i[0] >> 4);
+    const int b = ((c.i[2] >> 4) * v.cb[1] + (c.i[1] >> 4)) * v.cb[0] + (c.i[0] >> 4);
+#ifdef RC_DEBUG
+    return dbg_index(b + v.dbg_poison, v.cb[0] * v.cb[1] * v.cb[2], v.dbg_err, kSiteBrick);
+#else
+    return b;
+#endif
 }
 
 // Apron bricks: cell-brick b stores the voxels 16b-1 .. 16b+17 of each axis
@@ -513,10 +538,15 @@ __device__ __forceinline__ float tf_coord(float val, float ucoef) {
 
 // Sec. 2.6: linear interpolation of the two neighbouring table entries.
 __device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, int *i0 = nullptr,
-                                           float *w0 = nullptr) {
+                                           float *w0 = nullptr, int *err = nullptr) {
     float q = fminf(fmaxf(u, 0.0f), (float)(K - 1));
     int i = min((int)q, K - 2);
     float w = q - (float)i;
+#ifdef RC_DEBUG
+    i = dbg_index(i, K - 1, err, kSiteTable);
+#else
+    (void)err;
+#endif
     const ulonglong2 *t2 = reinterpret_cast<const ulonglong2 *>(tab);
     if (i0) *i0 = i;
     if (w0) *w0 = w;
@@ -530,7 +560,7 @@ __device__ __forceinline__ float4 classify(const float4 *tab, int K, float u, in
 // table stays in global memory (read-only path; at most a few MB).
 // The bilinear cell (i, j) and weights (a, b) are returned for the gradient.
 __device__ __forceinline__ float4 classify2_at(const TFDev &tf, float u, float w, int &i, int &j, float &a,
-                                               float &b) {
+                                               float &b, int *err = nullptr) {
     const int K = tf.K, M = tf.M;
     const float qu = fminf(fmaxf(u, 0.0f), (float)(K - 1));
     const float qw = fminf(fmaxf(w, 0.0f), (float)(M - 1));
@@ -538,6 +568,12 @@ __device__ __forceinline__ float4 classify2_at(const TFDev &tf, float u, float w
     j = min((int)qw, M - 2);
     a = qu - (float)i;
     b = qw - (float)j;
+#ifdef RC_DEBUG
+    i = dbg_index(i, K - 1, err, kSiteTable2);
+    j = dbg_index(j, M - 1, err, kSiteTable2);
+#else
+    (void)err;
+#endif
     const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(tf.tab2) + (size_t)j * K + i;
     const unsigned long long A = pack2(a, a);
     const ulonglong2 r0 = lerp4p(__ldg(p), __ldg(p + 1), A);
@@ -545,10 +581,10 @@ __device__ __forceinline__ float4 classify2_at(const TFDev &tf, float u, float w
     return unpack4(lerp4p(r0, r1, pack2(b, b)));
 }
 
-__device__ __forceinline__ float4 classify2(const TFDev &tf, float u, float w) {
+__device__ __forceinline__ float4 classify2(const TFDev &tf, float u, float w, int *err = nullptr) {
     int i, j;
     float a, b;
-    return classify2_at(tf, u, w, i, j, a, b);
+    return classify2_at(tf, u, w, i, j, a, b, err);
 }
 
 // The gradient-magnitude coordinate of a 2-D table: fl(|g| * wcoef).
@@ -628,9 +664,9 @@ __device__ __forceinline__ float4 eval_sample_x(const VolDev &vol, const MarchPa
     }
     float4 e;
     if (TF2) {
-        e = classify2(tf, tf_coord<ST>(val, tf.ucoef), tf2_row_coord(tf, g));
+        e = classify2(tf, tf_coord<ST>(val, tf.ucoef), tf2_row_coord(tf, g), RC_DBG_ERR(vol));
     } else {
-        e = classify(s_tf, tf.K, tf_coord<ST>(val, tf.ucoef));
+        e = classify(s_tf, tf.K, tf_coord<ST>(val, tf.ucoef), nullptr, nullptr, RC_DBG_ERR(vol));
     }
     float ap = correct_alpha<RM>(e.w, rmode, ratio);
     if (SHADE) {

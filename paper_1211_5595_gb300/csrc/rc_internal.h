@@ -48,6 +48,10 @@ struct VolDev {
                            // (code - o) / o, so code = (h + 1) o (exact for codes 0 .. 2o <= 4096). 0 for raw codes
     float gmin;            // shading falls back to ambient+diffuse below this |gradient|
     int vmax;
+#ifdef RC_DEBUG
+    int *dbg_err;          // debug builds: the context's error word (bit 1: an index check failed)
+    int dbg_poison;        // debug builds, test hook: added to every brick index (0 unless set)
+#endif
 };
 
 // Transfer function: K entries of straight RGBA, FP32 or FP16 in device memory

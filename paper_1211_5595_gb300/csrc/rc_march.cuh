@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kMarchThreads) function_kernel(const MarchArgs
         } else if (v >= a.p.iso) {
             found = true;
             if (func == RC_FUNC_THRESHOLD) {
-                float4 e = classify(s_tf, a.tf.K, tf_coord<ST>(v, a.tf.ucoef));
+                float4 e = classify(s_tf, a.tf.K, tf_coord<ST>(v, a.tf.ucoef), nullptr, nullptr, RC_DBG_ERR(a.vol));
                 out = make_float4(e.x, e.y, e.z, 1.0f);
             } else {
                 float ts = k > 0 ? prev_t + (t - prev_t) * ((a.p.iso - prev_v) / (v - prev_v)) : t;

@@ -41,6 +41,14 @@ def test_every_declared_symbol_is_exported(rc):
         assert callable(getattr(rc, n)), n
 
 
+def test_debug_library_exports_the_same_calls(rc):
+    """The debug build (device index checks) is the same interface."""
+    from paper_1211_5595_gb300 import build
+    lib = C.CDLL(build.DEBUG_LIB)
+    missing = [n for n in sorted(declared_symbols("rc.h")) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
 def test_probe_library_exports_its_header(rc):
     """The measurement probes live in their own library, outside the
     raycasting interface."""
