@@ -409,6 +409,44 @@ def precision_frames(rc, ctx, stream):
     return out
 
 
+def staged_form(rc, ctx, stream, flush, cams, reps=3):
+    """The bench march (FP32, shaded, every view of `cams` in one launch)
+    against its brick-staged variant (RC_MARCH_STAGED=1: each CTA stages the
+    value+gradient brick its rays need next in shared memory): median launch
+    time of each and whether the images are identical. With two views and
+    one repetition it is the small case a profiler captures (two launches of
+    each kernel, the first untimed)."""
+    import torch
+    w = synth.WORKLOADS[WORKLOAD]
+    ph = synth.workload_phantom(WORKLOAD)
+    vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, rc.RC_STORE_F32)
+    rc.rc_volume_upload(ctx, vol, ph.vol)
+    rc.rc_tf_set(ctx, synth.tf_table(w["K"]))
+    cam_structs = [rc.make_camera(c) for c in cams]
+    P = params(w)
+    imgs = {}
+    out = {"views": len(cams)}
+    for name in ("cached", "staged"):
+        if name == "staged":
+            os.environ["RC_MARCH_STAGED"] = "1"
+        img = torch.empty((len(cams), w["height"], w["width"], 4), device="cuda")
+        rc.rc_render_views(ctx, vol, P, cam_structs, img)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            rc.rc_render_views(ctx, vol, P, cam_structs, img)
+            b.record(stream)
+            flush.zero_()
+        rc.rc_context_sync(ctx)
+        os.environ.pop("RC_MARCH_STAGED", None)
+        out[name + "_ms_per_frame"] = statistics.median(x.elapsed_time(y) for x, y in ev) / len(cams)
+        imgs[name] = img
+    out["identical"] = bool(torch.equal(imgs["cached"], imgs["staged"]))
+    out["staged_over_cached"] = out["staged_ms_per_frame"] / out["cached_ms_per_frame"]
+    rc.rc_volume_destroy(ctx, vol)
+    return out
+
+
 def oracle_errors(gpu, o):
     """Max-abs per channel of GPU colours against the oracle's (a ray whose
     stop decision is a termination tie takes the nearer branch) and the PSNR
@@ -749,7 +787,7 @@ def main():
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal form")
     ap.add_argument("--no-precision", action="store_true", help="skip the 512x512x256 precision form")
     ap.add_argument("--proposal-phantoms", type=int, default=8, help="training phantoms of the proposal form")
-    ap.add_argument("--case", choices=["adjoint", "network", "precision"], default=None,
+    ap.add_argument("--case", choices=["adjoint", "network", "precision", "staged"], default=None,
                     help="run only the table-gradient form, the network throughput (forward and training "
                          "gradient, seeded initial network) or one 2048^2 frame of each precision form (FP32, "
                          "FP16, uint16 storage: two launches each, the first untimed) and print its JSON "
@@ -790,6 +828,8 @@ def main():
             out = adjoint_form(rc, ctx, flush, stream)
         elif args.case == "precision":
             out = precision_frames(rc, ctx, stream)
+        elif args.case == "staged":
+            out = staged_form(rc, ctx, stream, flush, cams)
         else:
             rc.rc_proposal_load(ctx, rc.pack_proposal_blob(synth.proposal_init_params(61)))
             out = network_throughput(rc, ctx, stream)

@@ -12,6 +12,12 @@
 
 #include "rc_internal.h"
 
+namespace rc {
+// the brick-staged march variant (rc_march_staged.cu)
+bool staged_eligible(const MarchArgs &a);
+cudaError_t launch_march_staged(const MarchArgs &a, int nviews, int *err, long long budget, cudaStream_t s);
+}  // namespace rc
+
 using namespace rc;
 
 struct rc_context {
@@ -839,6 +845,19 @@ static rc_status read_stats(rc_context *ctx, rc_stats *stats, bool importance) {
     return RC_OK;
 }
 
+// The march of rc_render and rc_render_views. RC_MARCH_STAGED=1 in the
+// environment selects, for the forms it covers (FP32 storage, shaded,
+// trilinear, 1-D table, skipping on), the brick-staged variant
+// (rc_march_staged.cu): the same images, kept to measure shared-memory
+// staging against the cached gathers. A bulk copy that does not complete
+// within its bounded wait is reported as RC_ERR_TIMEOUT at the next sync.
+static cudaError_t launch_march_any(rc_context *ctx, const MarchArgs &a, int nviews) {
+    const char *e = getenv("RC_MARCH_STAGED");
+    if (e && e[0] == '1' && e[1] == 0 && staged_eligible(a))
+        return launch_march_staged(a, nviews, error_word(ctx), 2000000000ll, ctx->stream);
+    return launch_march(a, nviews, ctx->stream);
+}
+
 static MarchArgs march_args(rc_context *ctx, const rc_volume *v, const rc_render_params *p, float *out) {
     MarchArgs a;
     a.vol = vol_dev(v);
@@ -889,7 +908,7 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
         a.stats = ctx->d_stats;
     }
-    RC_CUDA(ctx, launch_march(a, 1, ctx->stream));
+    RC_CUDA(ctx, launch_march_any(ctx, a, 1));
     if (stats) return read_stats(ctx, stats, false);
     return RC_OK;
 }
@@ -919,7 +938,7 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
         RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
         a.stats = ctx->d_stats;
     }
-    RC_CUDA(ctx, launch_march(a, nviews, ctx->stream));
+    RC_CUDA(ctx, launch_march_any(ctx, a, nviews));
     if (stats) return read_stats(ctx, stats, false);
     return RC_OK;
 }

@@ -76,11 +76,25 @@ __device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// One potentially blocking test: the thread may be suspended in hardware
+// until the phase completes or about `suspend_ns` nanoseconds pass (it then
+// issues nothing, leaving the issue slots to the other warps).
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity, uint32_t suspend_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(suspend_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for the phase with the given parity to complete, for at most
-// `budget` clock cycles. Returns false on timeout.
+// `budget` clock cycles (checked between suspended tests of at most 20 us).
+// Returns false on timeout.
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, long long budget) {
     const long long t0 = clock64();
-    while (!bar_test(bar, parity))
+    while (!bar_try(bar, parity, 20000u))
         if (clock64() - t0 > budget) return false;
     return true;
 }

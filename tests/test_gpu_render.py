@@ -299,6 +299,41 @@ def test_render_views_equals_single_renders(rc, c1):
     assert ei.value.status == rc.RC_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("step", [0.5, 1.0, 0.37])
+def test_brick_staged_march_equals_cached_march(rc, c2, monkeypatch, step):
+    """The brick-staged variant of the shaded FP32 march (RC_MARCH_STAGED=1:
+    each CTA copies the value+gradient brick its rays need next into shared
+    memory with one bulk copy) renders the cached-gather march's images bit for
+    bit, with the same sample counts, on ragged tiles of the full-size phantom
+    and a small ragged volume, for each opacity-correction instance."""
+    import torch
+    ph, tf, w, r = c2
+    cams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=203, height=141) for az in (10.0, 130.0, 250.0)]
+    P = dict(step_vox=step, term=0.99, shade=True, skip=True)
+    a = torch.empty((3, 141, 203, 4), device="cuda")
+    b = torch.empty_like(a)
+    sa = rc.rc_render_views(r.ctx, r.vol, P, cams, a, stats=True)
+    monkeypatch.setenv("RC_MARCH_STAGED", "1")
+    sb = rc.rc_render_views(r.ctx, r.vol, P, cams, b, stats=True)
+    rc.rc_context_sync(r.ctx)
+    monkeypatch.delenv("RC_MARCH_STAGED")
+    assert torch.equal(a, b)
+    assert sa == sb and sa["evaluated_samples"] > 0
+    small = synth.head_phantom((37, 29, 21), (1.0, 1.2, 0.9), seed=8, tumor_radius_vox=3)
+    g = GPURenderer(rc, small.vol, small.spacing)
+    try:
+        g.set_tf(tf)
+        cam = synth.orbit_camera(small.dims, small.spacing, 75.0, width=45, height=39)
+        ref = g.render(cam, **P)
+        monkeypatch.setenv("RC_MARCH_STAGED", "1")
+        got = g.render(cam, **P)
+        rc.rc_context_sync(g.ctx)
+        monkeypatch.delenv("RC_MARCH_STAGED")
+        assert np.array_equal(ref, got)
+    finally:
+        g.close()
+
+
 def test_render_views_host_equals_device_render(rc, c1):
     """Host delivery: groups rendered into two device buffers in turn and
     copied on a second stream give the device render's images bit for bit,
