@@ -229,20 +229,37 @@ __device__ __forceinline__ uint32_t bias_relu_bf16x2(float lo, float hi, float2 
     return r;
 }
 
+// Bias, ReLU and BF16 rounding of 16 hidden values (columns c .. c + 15),
+// stored as two 16-byte chunks of row `row` of the next A operand.
+__device__ __forceinline__ void store_hidden16(uint8_t *A, const float *v, const float2 *b2, int c, int row) {
+#pragma unroll
+    for (int j = 0; j < 16; j += 8) {
+        uint4 q;
+        uint32_t *w = reinterpret_cast<uint32_t *>(&q);
+#pragma unroll
+        for (int h = 0; h < 4; h++) w[h] = bias_relu_bf16x2(v[j + 2 * h], v[j + 2 * h + 1], b2[(c + j) / 2 + h]);
+        *reinterpret_cast<uint4 *>(A + tc::core_offset(row, c + j, 128)) = q;
+    }
+}
+
+// WIDE: the whole row in one TMEM load and wait (faster where the 64 live
+// registers fit: the feature-matrix network and the training kernel); else
+// four 16-column loads, each consumed before the next (the camera-ray
+// network, at its register limit).
+template <bool WIDE>
 __device__ __forceinline__ void store_hidden(uint8_t *A, uint32_t taddr, const float *bias, int row) {
     const float2 *b2 = reinterpret_cast<const float2 *>(bias);
+    if (WIDE) {
+        float v[kHid];
+        tc::tmem_ld64(taddr, v);
 #pragma unroll
-    for (int c = 0; c < kHid; c += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + c, v);
+        for (int c = 0; c < kHid; c += 16) store_hidden16(A, v + c, b2, c, row);
+    } else {
 #pragma unroll
-        for (int j = 0; j < 16; j += 8) {
-            uint4 q;
-            uint32_t *w = reinterpret_cast<uint32_t *>(&q);
-#pragma unroll
-            for (int h = 0; h < 4; h++)
-                w[h] = bias_relu_bf16x2(v[j + 2 * h], v[j + 2 * h + 1], b2[(c + j) / 2 + h]);
-            *reinterpret_cast<uint4 *>(A + tc::core_offset(row, c + j, 128)) = q;
+        for (int c = 0; c < kHid; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+            store_hidden16(A, v, b2, c, row);
         }
     }
 }
@@ -261,14 +278,23 @@ __device__ __forceinline__ void store_chunk(uint8_t *A, int row, int chunk, cons
 }
 
 // Network head: 32 logits -> PDF (softmax), logit 32 -> T^ (sigmoid).
+template <bool WIDE>
 __device__ __forceinline__ void net_head(uint32_t taddr, const float *bias, float (&pdf)[kBins], float &that) {
+    // the head uses 33 of its 48 accumulator columns
     float z[kN4];
+    if (WIDE) {
+        float v[kHid];
+        tc::tmem_ld64(taddr, v);
 #pragma unroll
-    for (int c = 0; c < kN4; c += 16) {
-        float v[16];
-        tc::tmem_ld16(taddr + c, v);
+        for (int j = 0; j < kN4; j++) z[j] = v[j] + bias[j];
+    } else {
 #pragma unroll
-        for (int j = 0; j < 16; j++) z[c + j] = v[j] + bias[c + j];
+        for (int c = 0; c < kN4; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int j = 0; j < 16; j++) z[c + j] = v[j] + bias[c + j];
+        }
     }
     float mx = z[0];
 #pragma unroll
@@ -290,6 +316,7 @@ __device__ __forceinline__ void net_head(uint32_t taddr, const float *bias, floa
 // Runs the four layers of group g on its A operand (the group's 128 threads
 // call; thread t of the group is TMEM lane t). Returns false when a wait gave
 // up; the caller then stops.
+template <bool WIDE>
 __device__ __forceinline__ bool run_network(const TcNetArgs &A, NetSmem &S, int g, uint32_t tmem, uint32_t bar,
                                             uint32_t &phase, float (&pdf)[kBins], float &that) {
     const int t = threadIdx.x - g * kGroupThreads;
@@ -306,8 +333,8 @@ __device__ __forceinline__ bool run_network(const TcNetArgs &A, NetSmem &S, int 
         if (!ok) return false;
         phase ^= 1u;
         tc::fence_after();
-        if (l < 3) store_hidden(S.a[g], taddr, S.bias + l * kHid, t);
-        else net_head(taddr, S.bias + 3 * kHid, pdf, that);
+        if (l < 3) store_hidden<WIDE>(S.a[g], taddr, S.bias + l * kHid, t);
+        else net_head<WIDE>(taddr, S.bias + 3 * kHid, pdf, that);
     }
     return true;
 }
@@ -387,7 +414,7 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads) tc_net_kernel(const T
                                   [&](int chunk, const float (&v)[8]) { store_chunk(Ag, t, chunk, v); });
         }
         float pdf[kBins], that;
-        ok = run_network(A, S, g, tmem, bar_m, phase, pdf, that);
+        ok = run_network<FEAT>(A, S, g, tmem, bar_m, phase, pdf, that);
         if (!ok) {
             mma_waited_out = true;
             break;
@@ -827,15 +854,12 @@ __global__ void __launch_bounds__(128) tc_train_kernel(const TrainArgs A) {
                 break;
             }
             if (l < 3) {
-                store_hidden(S.h[l], taddr + kColD, S.bias + l * kHid, t);
+                store_hidden<true>(S.h[l], taddr + kColD, S.bias + l * kHid, t);
             } else {
+                float v[64];
+                tc::tmem_ld64(taddr + kColD, v);       // the 48 used of the 64 D columns, one round trip
 #pragma unroll
-                for (int c = 0; c < kN4; c += 16) {
-                    float v[16];
-                    tc::tmem_ld16(taddr + kColD + c, v);
-#pragma unroll
-                    for (int j = 0; j < 16; j++) z[c + j] = v[j] + S.bias[3 * kHid + c + j];
-                }
+                for (int j = 0; j < kN4; j++) z[j] = v[j] + S.bias[3 * kHid + j];
             }
         }
         if (!ok) break;
@@ -897,13 +921,10 @@ __global__ void __launch_bounds__(128) tc_train_kernel(const TrainArgs A) {
             }
             if (l > 0) {
                 // dZ_{l-1} = dH * [H_{l-1} > 0]
+                float v[kHid];
+                tc::tmem_ld64(taddr + kColD, v);
 #pragma unroll
-                for (int c = 0; c < kHid; c += 16) {
-                    float v[16];
-                    tc::tmem_ld16(taddr + kColD + c, v);
-#pragma unroll
-                    for (int j = 0; j < 16; j++) dz[c + j] = get_bf16(S.h[l - 1], t, c + j, 128) > 0.0f ? v[j] : 0.0f;
-                }
+                for (int j = 0; j < kHid; j++) dz[j] = get_bf16(S.h[l - 1], t, j, 128) > 0.0f ? v[j] : 0.0f;
             }
         }
         first = false;

@@ -149,21 +149,39 @@ def test_argument_and_state_errors(rc):
         rc.rc_context_destroy(ctx)
 
 
-def test_read_probe(rc):
-    """The read-bandwidth probe runs on the context's stream and checks its
-    arguments."""
+def test_read_probes(rc):
+    """The read-bandwidth probes of librc_probe.so (include/rc_probe.h) run on
+    the given stream, report launch errors as cudaError_t values and check
+    their arguments before any launch; the L1 probe's byte count is CTAs x
+    reps x buffer bytes and its rate is far above the L2 probe's."""
+    import ctypes as C
+
     import torch
-    ctx = rc.rc_context_create(0)
-    try:
-        buf = torch.ones(1 << 20, device="cuda")
+    from paper_1211_5595_gb300 import build
+    L = C.CDLL(build.build_probe())
+    for f in ("rc_probe_read_l1", "rc_probe_read_l2"):
+        getattr(L, f).argtypes = [C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]
+        getattr(L, f).restype = C.c_int
+    L.rc_probe_l1_bytes.argtypes = [C.c_size_t, C.c_int]
+    L.rc_probe_l1_bytes.restype = C.c_size_t
+    s = torch.cuda.current_stream()
+    small = torch.ones(8 << 10, device="cuda")                 # 32 KB
+    big = torch.ones(24 << 20, device="cuda")                  # 96 MB
+    rates = {}
+    for name, buf, reps in (("l1", small, 200), ("l2", big, 4)):
+        fn = getattr(L, "rc_probe_read_" + name)
+        nbytes = buf.numel() * 4
+        assert fn(buf.data_ptr(), nbytes, reps, s.cuda_stream) == 0
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev[0].record()
-        rc.rc_probe_read_bandwidth(ctx, buf, 4)
-        ev[1].record()
-        rc.rc_context_sync(ctx)
-        assert ev[0].elapsed_time(ev[1]) > 0
-        with pytest.raises(rc.RCError) as ei:
-            rc.rc_probe_read_bandwidth(ctx, buf[1:], 4)          # not 16-byte aligned
-        assert ei.value.status == rc.RC_ERR_INVALID_ARG
-    finally:
-        rc.rc_context_destroy(ctx)
+        ev[0].record(s)
+        assert fn(buf.data_ptr(), nbytes, reps, s.cuda_stream) == 0
+        ev[1].record(s)
+        torch.cuda.synchronize()
+        moved = L.rc_probe_l1_bytes(nbytes, reps) if name == "l1" else nbytes * reps
+        rates[name] = moved / (ev[0].elapsed_time(ev[1]) / 1e3)
+        assert fn(buf.data_ptr() + 4, nbytes - 16, reps, s.cuda_stream) == 1      # not 16-byte aligned
+        assert fn(buf.data_ptr(), nbytes, 0, s.cuda_stream) == 1
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert L.rc_probe_l1_bytes(32 << 10, 3) == sms * 4 * 3 * (32 << 10)
+    assert L.rc_probe_read_l1(big.data_ptr(), 1 << 20, 1, s.cuda_stream) == 1    # above the 64 KB limit
+    assert rates["l1"] > 2 * rates["l2"] > 0

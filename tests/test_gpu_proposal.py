@@ -204,18 +204,28 @@ def test_importance_parity(rc, orc, small, term, nimp):
     print(f"importance range nimp {nimp} term {term}: max-abs {err:.2e}, {int(o['tie'].sum())} tie rays")
 
 
-@pytest.mark.parametrize("lam,nimp,term", [(0.05, 64, 1.0), (0.05, 17, 0.99), (0.0, 64, 0.99), (1.0, 64, 0.99),
-                                           (1.0, 128, 1.0)])
-def test_importance_invcdf_parity(rc, orc, small, lam, nimp, term):
+@pytest.mark.parametrize("lam,nimp,term,sparse", [(0.05, 64, 1.0, False), (0.05, 17, 0.99, False),
+                                                  (0.0, 64, 0.99, False), (1.0, 64, 0.99, False),
+                                                  (1.0, 128, 1.0, False), (0.05, 1, 0.99, False),
+                                                  (0.0, 33, 0.99, True), (0.0, 1, 1.0, True)])
+def test_importance_invcdf_parity(rc, orc, small, lam, nimp, term, sparse):
     """The inverse-CDF reading (stratified samples of the lambda-mixture,
     midpoint segments) over two views in one launch against the oracle, every
     pixel within 2e-4 (either branch of a termination tie); lambda = 1 without
-    a PDF (the uniform march over the chord) and without T^ (no fallback)."""
+    a PDF (the uniform march over the chord) and without T^ (no fallback); a
+    single sample per ray (it stands for the whole chord); lambda = 0 with
+    PDFs whose bins are mostly empty (the bin search steps over zero-width
+    bins)."""
     import torch
     ph, tf, r = small
     cams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=72, height=64) for az in (40.0, 230.0)]
     n = 72 * 64
     pdf = np.stack([seeded_pdfs(n, 81), seeded_pdfs(n, 82)])
+    if sparse:
+        keep = synth.uniform01(83, np.arange(2 * n * 32)).reshape(2, n, 32) < 0.15
+        keep[..., 5] = True                                  # at least one bin per ray
+        pdf = np.where(keep, pdf, 0.0)
+        pdf = (pdf / pdf.sum(axis=-1, keepdims=True)).astype(np.float32)
     out = torch.empty((2, 64, 72, 4), device="cuda")
     fb = torch.empty((2, n), dtype=torch.uint8, device="cuda")
     uniform = lam == 1.0
