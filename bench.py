@@ -447,6 +447,31 @@ def staged_form(rc, ctx, stream, flush, cams, reps=3):
     return out
 
 
+def proposal_frames(rc, ctx, stream, cams, reps=2):
+    """The learned-proposal render of the bench workload with a seeded
+    (untrained) network: every view of `cams` in one launch pair (the camera-ray
+    network kernel, then the importance march, 64 samples per ray, no
+    fallback), reps times; median ms per frame. The small case a profiler
+    captures."""
+    import torch
+    w = synth.WORKLOADS[WORKLOAD]
+    ph = synth.workload_phantom(WORKLOAD)
+    vol = rc.rc_volume_create(ctx, ph.dims, ph.spacing, synth.VMAX, rc.RC_STORE_F32)
+    rc.rc_volume_upload(ctx, vol, ph.vol)
+    rc.rc_tf_set(ctx, synth.tf_table(w["K"]))
+    rc.rc_proposal_load(ctx, rc.pack_proposal_blob(synth.proposal_init_params(61)))
+    cam_structs = [rc.make_camera(c) for c in cams]
+    img = torch.empty((len(cams), w["height"], w["width"], 4), device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        rc.rc_render_proposal_views(ctx, vol, params(w), cam_structs, 64, 2.0, img)
+        b.record(stream)
+    rc.rc_context_sync(ctx)
+    rc.rc_volume_destroy(ctx, vol)
+    return {"views": len(cams), "ms_per_frame": statistics.median(x.elapsed_time(y) for x, y in ev) / len(cams)}
+
+
 def oracle_errors(gpu, o):
     """Max-abs per channel of GPU colours against the oracle's (a ray whose
     stop decision is a termination tie takes the nearer branch) and the PSNR
@@ -787,7 +812,7 @@ def main():
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal form")
     ap.add_argument("--no-precision", action="store_true", help="skip the 512x512x256 precision form")
     ap.add_argument("--proposal-phantoms", type=int, default=8, help="training phantoms of the proposal form")
-    ap.add_argument("--case", choices=["adjoint", "network", "precision", "staged"], default=None,
+    ap.add_argument("--case", choices=["adjoint", "network", "precision", "staged", "proposal"], default=None,
                     help="run only the table-gradient form, the network throughput (forward and training "
                          "gradient, seeded initial network) or one 2048^2 frame of each precision form (FP32, "
                          "FP16, uint16 storage: two launches each, the first untimed) and print its JSON "
@@ -830,6 +855,8 @@ def main():
             out = precision_frames(rc, ctx, stream)
         elif args.case == "staged":
             out = staged_form(rc, ctx, stream, flush, cams)
+        elif args.case == "proposal":
+            out = proposal_frames(rc, ctx, stream, cams)
         else:
             rc.rc_proposal_load(ctx, rc.pack_proposal_blob(synth.proposal_init_params(61)))
             out = network_throughput(rc, ctx, stream)

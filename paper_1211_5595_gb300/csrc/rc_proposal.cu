@@ -152,21 +152,29 @@ __global__ void __launch_bounds__(128) features_kernel(const MarchArgs a, float 
 // ---------------------------------------------------------------------------
 // the network on the tensor cores: one M = 128 tile of rays per MMA
 // ---------------------------------------------------------------------------
-// A network CTA runs two independent groups of 128 threads, each on its own
+// A network CTA runs G independent groups of 128 threads, each on its own
 // tiles of 128 rays with its own A operand, MMA barrier and 64 TMEM columns
 // (TMEM lane = ray); the weights and biases are shared. The A operand holds a
 // tile's features (128 x 112 BF16) and then, layer by layer, its hidden
 // activations (128 x 64): every layer's MMA has completed before its output
-// overwrites the operand it read.
-constexpr int kGroups = 2;
+// overwrites the operand it read. The camera-ray kernel runs one CTA of
+// kCamGroups groups per SM (one copy of the weights, 209 KB of shared memory,
+// 80 registers per thread; measured per 1024^2 view: 2 x 2 groups 0.146 ms,
+// one CTA of 4 groups 0.149, of 5 groups 0.129, of 6 groups 0.121); the
+// feature-matrix kernel two CTAs of kFeatGroups groups (its wide TMEM loads
+// need more registers).
+constexpr int kCamGroups = 6;
+constexpr int kFeatGroups = 2;
 constexpr int kGroupThreads = 128;
-constexpr int kTmemCols = 64 * kGroups;    // FP32 accumulators: 128 lanes x 64 columns per group
+// TMEM columns of a CTA: 64 per group, allocated as a power of two
+constexpr int tmem_cols(int groups) { return groups * 64 <= 128 ? 128 : groups * 64 <= 256 ? 256 : 512; }
 
+template <int G>
 struct NetSmem {
     uint8_t w[kUmmaBytes];                 // B operands of the four layers
-    uint8_t a[kGroups][128 * kFeat * 2];   // A operands
+    uint8_t a[G][128 * kFeat * 2];         // A operands
     float bias[3 * kHid + kN4];
-    unsigned long long bar_w, bar_mma[kGroups];
+    unsigned long long bar_w, bar_mma[G];
     uint32_t tmem;
 };
 
@@ -201,7 +209,8 @@ __device__ __forceinline__ void group_sync(int g) {
 
 // One layer, issued by one thread: D[128 x N] = A[128 x K] * W^T, K / 16 MMAs,
 // then a commit that arrives on the group's MMA barrier when they are done.
-__device__ __forceinline__ void issue_layer(const NetSmem &S, int g, int l, uint32_t tmem_d, uint32_t bar) {
+template <int G>
+__device__ __forceinline__ void issue_layer(const NetSmem<G> &S, int g, int l, uint32_t tmem_d, uint32_t bar) {
     const NetLayer L = net_layer(l);
     const uint32_t a0 = tc::smem_addr(S.a[g]), b0 = tc::smem_addr(S.w) + L.b_off;
     const uint32_t lbo_a = (128 / 8) * 128, lbo_b = (uint32_t)(L.N / 8) * 128;
@@ -316,8 +325,8 @@ __device__ __forceinline__ void net_head(uint32_t taddr, const float *bias, floa
 // Runs the four layers of group g on its A operand (the group's 128 threads
 // call; thread t of the group is TMEM lane t). Returns false when a wait gave
 // up; the caller then stops.
-template <bool WIDE>
-__device__ __forceinline__ bool run_network(const TcNetArgs &A, NetSmem &S, int g, uint32_t tmem, uint32_t bar,
+template <bool WIDE, int G>
+__device__ __forceinline__ bool run_network(const TcNetArgs &A, NetSmem<G> &S, int g, uint32_t tmem, uint32_t bar,
                                             uint32_t &phase, float (&pdf)[kBins], float &that) {
     const int t = threadIdx.x - g * kGroupThreads;
     const uint32_t tmem_d = tmem + 64u * (uint32_t)g;
@@ -345,17 +354,18 @@ __device__ __forceinline__ void range_of(const MarchArgs &a, const Ray &R, const
 // FEAT: rays are rows of a feature matrix (outputs: the 33 network outputs);
 // otherwise rays are the pixels of the cameras' views (outputs: the range
 // record of each ray for the importance march).
-template <bool FEAT>
-__global__ void __launch_bounds__(kGroups * kGroupThreads) tc_net_kernel(const TcNetArgs A) {
+template <bool FEAT, int G>
+__global__ void __launch_bounds__(G * kGroupThreads) tc_net_kernel(const TcNetArgs A) {
+    constexpr int kTmemCols = tmem_cols(G);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    NetSmem &S = *reinterpret_cast<NetSmem *>(smem_raw);
+    NetSmem<G> &S = *reinterpret_cast<NetSmem<G> *>(smem_raw);
     const int tid = threadIdx.x, g = tid / kGroupThreads, t = tid % kGroupThreads;
     const int warp = t >> 5, lane = t & 31;
     const uint32_t bar_w = tc::smem_addr(&S.bar_w), bar_m = tc::smem_addr(&S.bar_mma[g]);
     if (tid < 32) tc::tmem_alloc<kTmemCols>(tc::smem_addr(&S.tmem));
     if (tid == 0) {
         tc::bar_init(bar_w, 1);
-        for (int i = 0; i < kGroups; i++) tc::bar_init(tc::smem_addr(&S.bar_mma[i]), 1);
+        for (int i = 0; i < G; i++) tc::bar_init(tc::smem_addr(&S.bar_mma[i]), 1);
     }
     for (int i = tid; i < 3 * kHid + kN4; i += blockDim.x) {
         const int l = i / kHid, j = i % kHid;
@@ -374,9 +384,9 @@ __global__ void __launch_bounds__(kGroups * kGroupThreads) tc_net_kernel(const T
     uint32_t phase = 0;
     bool mma_waited_out = false;
     uint8_t *Ag = S.a[g];
-    const long long stride = (long long)gridDim.x * kGroups;
+    const long long stride = (long long)gridDim.x * G;
 #pragma unroll 1
-    for (long long tile = (long long)blockIdx.x * kGroups + g; ok && tile < A.ntiles; tile += stride) {
+    for (long long tile = (long long)blockIdx.x * G + g; ok && tile < A.ntiles; tile += stride) {
         Ray R;
         bool hit = false;
         long long out_idx = -1;
@@ -759,23 +769,40 @@ __device__ __forceinline__ float get_bf16(const uint8_t *M, int row, int k, int 
 }
 
 // Column t of the weight-gradient A operand: the thread's n inputs (BF16,
-// already rounded) in rows 0..n-1, 1 in row n; rows n+1 .. zero_to-1 zeroed.
+// already rounded; n a multiple of 8, read 8 at a time from the thread's own
+// row of src) in rows 0..n-1, 1 in row n; rows n+1 .. zero_to-1 zeroed.
 __device__ __forceinline__ void put_inputs_t(uint8_t *at, const uint8_t *src, int n, int t, int zero_to) {
-    for (int r = 0; r < n; r++)
-        *reinterpret_cast<__nv_bfloat16 *>(at + tc::core_offset(r, t, 128)) =
-            *reinterpret_cast<const __nv_bfloat16 *>(src + tc::core_offset(t, r, 128));
+    for (int r0 = 0; r0 < n; r0 += 8) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(src + tc::core_offset(t, r0, 128));
+        const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&q);
+#pragma unroll
+        for (int i = 0; i < 8; i++) *reinterpret_cast<__nv_bfloat16 *>(at + tc::core_offset(r0 + i, t, 128)) = h[i];
+    }
     put_bf16(at, n, t, 128, 1.0f);
     for (int r = n + 1; r < zero_to; r++) put_bf16(at, r, t, 128, 0.0f);
 }
 
-// dZ of this thread's ray (n values) as row t of A (K = k_pad) and column t of B^T.
+// dZ of this thread's ray (n values) as row t of A (K = k_pad, 8 values per
+// 16-byte store) and column t of B^T.
 __device__ __forceinline__ void put_dz(TrainSmem &S, const float (&dz)[kHid], int n, int k_pad, int t, bool as_a) {
 #pragma unroll
-    for (int j = 0; j < kHid; j++) {
-        if (j >= k_pad) break;
-        const float v = j < n ? dz[j] : 0.0f;
-        if (as_a) put_bf16(S.adz, t, j, 128, v);
-        put_bf16(S.bdz, j, t, k_pad, v);
+    for (int j0 = 0; j0 < kHid; j0 += 8) {
+        if (j0 >= k_pad) break;
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) v[i] = j0 + i < n ? dz[j0 + i] : 0.0f;
+        if (as_a) {
+            uint4 q;
+            uint32_t *w = reinterpret_cast<uint32_t *>(&q);
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+                w[h] = *reinterpret_cast<uint32_t *>(&b2);
+            }
+            *reinterpret_cast<uint4 *>(S.adz + tc::core_offset(t, j0, 128)) = q;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) put_bf16(S.bdz, j0 + i, t, k_pad, v[i]);
     }
 }
 
@@ -1086,12 +1113,13 @@ cudaError_t launch_features(const MarchArgs &a, float *out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Persistent network CTAs: as many as fit on the device at once (each holds
-// 64 TMEM columns and about 65 KB of shared memory), at most one per tile.
-template <bool FEAT>
+// Persistent network CTAs: as many as fit on the device at once (shared
+// memory, registers and the SM's 512 TMEM columns), at most one per G tiles.
+template <bool FEAT, int G>
 static cudaError_t launch_tc(const TcNetArgs &a, cudaStream_t s) {
-    auto kern = tc_net_kernel<FEAT>;
-    const int smem = (int)sizeof(NetSmem);
+    constexpr int kTmemCols = tmem_cols(G);
+    auto kern = tc_net_kernel<FEAT, G>;
+    const int smem = (int)sizeof(NetSmem<G>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
@@ -1106,18 +1134,18 @@ static cudaError_t launch_tc(const TcNetArgs &a, cudaStream_t s) {
     if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess) return e;
     cudaFuncAttributes fa;
     if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
-    const int threads = kGroups * kGroupThreads;
+    const int threads = G * kGroupThreads;
     const int by_smem = smem_sm / (smem + smem_rsv);
     const int by_regs = regs_sm / max(1, fa.numRegs * threads);
     const int per_sm = max(1, min(min(by_smem, by_regs), 512 / kTmemCols));
-    const long long grid = min((long long)sms * per_sm, (a.ntiles + kGroups - 1) / kGroups);
+    const long long grid = min((long long)sms * per_sm, (a.ntiles + G - 1) / G);
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_net(const TcNetArgs &a, cudaStream_t s) {
-    return a.feat ? launch_tc<true>(a, s) : launch_tc<false>(a, s);
+    return a.feat ? launch_tc<true, kFeatGroups>(a, s) : launch_tc<false, kCamGroups>(a, s);
 }
 
 template <int ST, bool SHADE>
