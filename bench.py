@@ -580,26 +580,30 @@ def adjoint_form(rc, ctx, flush, stream):
     G = torch.randn(imgs.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
 
     def pair_ms(Pf, dt, reps):
-        """Median forward and backward time per view over reps runs."""
+        """Median forward, backward and backward-given-the-forward times per
+        view over reps runs."""
         rc.rc_render_backward_views(ctx, vol, Pf, cam_structs, G, dt)    # builds what the form needs
         ev = []
         for rep in range(reps):
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             e[0].record(stream)
             rc.rc_render_views(ctx, vol, Pf, cam_structs, imgs)
             e[1].record(stream)
             rc.rc_render_backward_views(ctx, vol, Pf, cam_structs, G, dt)
             e[2].record(stream)
+            rc.rc_render_backward_views_with_forward(ctx, vol, Pf, cam_structs, imgs, G, dt)
+            e[3].record(stream)
             ev.append(e)
             flush.zero_()
         torch.cuda.synchronize()
-        return (statistics.median(a.elapsed_time(b) for a, b, c in ev) / n,
-                statistics.median(b.elapsed_time(c) for a, b, c in ev) / n)
+        return (statistics.median(a.elapsed_time(b) for a, b, c, d in ev) / n,
+                statistics.median(b.elapsed_time(c) for a, b, c, d in ev) / n,
+                statistics.median(c.elapsed_time(d) for a, b, c, d in ev) / n)
 
-    f_ms, b_ms = pair_ms(P, dtf, 3)
+    f_ms, b_ms, bf_ms = pair_ms(P, dtf, 3)
     # the same with cubic B-spline reconstruction
     Pb = rc.RenderParams(step_vox=wd["step"], term=wd["term"], shade=False, skip=False, filter=rc.RC_FILTER_BSPLINE)
-    fb_ms, bb_ms = pair_ms(Pb, dtf, 3)
+    fb_ms, bb_ms, bbf_ms = pair_ms(Pb, dtf, 3)
     # a 2-D table (the same rows, opacity rising with gradient magnitude):
     # the gradient scatters into four entries per sample in global memory
     M2 = 32
@@ -607,17 +611,20 @@ def adjoint_form(rc, ctx, flush, stream):
     tab2[..., 3] *= np.linspace(0.4, 1.0, M2, dtype=np.float32)[:, None]
     rc.rc_tf2d_set(ctx, tab2, 1200.0)
     dtf2 = torch.empty((M2, wd["K"], 4), device="cuda")
-    f2_ms, b2_ms = pair_ms(P, dtf2, 3)
+    f2_ms, b2_ms, b2f_ms = pair_ms(P, dtf2, 3)
     rc.rc_volume_destroy(ctx, vol)
     per_view = dense / len(cams)
     return {"workload": "diff_128x128x96", "views": len(cams), "image": "512x512",
             "forward_ms_per_view": f_ms, "backward_ms_per_view": b_ms, "backward_over_forward": b_ms / f_ms,
+            "backward_with_forward_ms_per_view": bf_ms, "backward_with_forward_over_forward": bf_ms / f_ms,
             "dense_samples_per_view": per_view,
             "backward_gsamples_s": 2 * per_view / (b_ms / 1e3) / 1e9,
             "bspline": {"forward_ms_per_view": fb_ms, "backward_ms_per_view": bb_ms,
-                        "backward_over_forward": bb_ms / fb_ms},
+                        "backward_over_forward": bb_ms / fb_ms, "backward_with_forward_ms_per_view": bbf_ms,
+                        "backward_with_forward_over_forward": bbf_ms / fb_ms},
             "tf2d": {"table": f"{M2}x{wd['K']}", "forward_ms_per_view": f2_ms, "backward_ms_per_view": b2_ms,
-                     "backward_over_forward": b2_ms / f2_ms},
+                     "backward_over_forward": b2_ms / f2_ms, "backward_with_forward_ms_per_view": b2f_ms,
+                     "backward_with_forward_over_forward": b2f_ms / f2_ms},
             "note": "exact skipping in the forward recompute, none in the gradient pass (an empty brick still has a gradient)"}
 
 

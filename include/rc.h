@@ -272,6 +272,21 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol,
 rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *params,
                                    const rc_camera *cams, int nviews, const float *dL_dimages, float *dL_dtf);
 
+/* rc_render_backward_views for a caller that still holds the forward images:
+ * images (device, nviews*H*W*4 floats, view-major) are the images
+ * rc_render_views wrote for the same volume, table, parameters and cameras.
+ * Each ray's final colour C and transmittance T = 1 - alpha are read from them
+ * instead of being recomputed by a first forward march, and the gradient
+ * march stops at the forward's termination sample by itself (it rebuilds the
+ * transmittance sample by sample): one march per ray instead of two. The
+ * result equals rc_render_backward_views' up to the rounding of T = 1 - alpha
+ * (and the few ulps by which compiled instances may differ); images of other
+ * inputs give a wrong gradient, not an error. */
+rc_status rc_render_backward_views_with_forward(rc_context *ctx, const rc_volume *vol,
+                                                const rc_render_params *params, const rc_camera *cams,
+                                                int nviews, const float *images, const float *dL_dimages,
+                                                float *dL_dtf);
+
 /* The gradient of rc_render_backward for callers that cannot allocate device
  * memory once they are running: for example a host application whose device
  * memory is all handed out up front by its own allocator, or a frame loop in

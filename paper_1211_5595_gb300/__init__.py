@@ -97,6 +97,8 @@ SIGNATURES = {
     "rc_render_batch": (_I, [_P, _P, _I, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P,
                              C.POINTER(rc_stats)]),
     "rc_render_backward_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _P, _P]),
+    "rc_render_backward_views_with_forward": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I,
+                                                   _P, _P, _P]),
     "rc_render_proposal": (_I, [_P, _P, C.POINTER(rc_render_params), _I, C.c_float, _P, _P, C.POINTER(rc_stats)]),
     "rc_render_proposal_views": (_I, [_P, _P, C.POINTER(rc_render_params), C.POINTER(rc_camera), _I, _I, C.c_float,
                                       _P, _P, C.POINTER(rc_stats)]),
@@ -490,3 +492,13 @@ def rc_render_proposal_sampled(ctx, vol, params, cams, sampling, lam, nimp, eps,
                                             C.byref(st) if st is not None else None), ctx,
            "rc_render_proposal_sampled")
     return _stats_dict(st)
+
+
+def rc_render_backward_views_with_forward(ctx, vol, params, cams, images, dimages, dtf):
+    """rc_render_backward_views given the forward images of the same views
+    (images: CUDA float32 n x H x W x 4, as rc_render_views wrote them): one
+    march per ray instead of two."""
+    p = _params(params)
+    _check(lib().rc_render_backward_views_with_forward(ctx, vol, C.byref(p), _camera_array(cams), len(cams),
+                                                       _ptr(images), _ptr(dimages), _ptr(dtf)), ctx,
+           "rc_render_backward_views_with_forward")

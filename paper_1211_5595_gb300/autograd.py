@@ -1,13 +1,14 @@
 """torch.autograd.Function over the library's render and its hand-written
 adjoint: gradients of an image loss with respect to the transfer-function table
 (Eq. 4-5 are differentiable in the table entries). Marshalling only: the
-forward calls rc_render, the backward calls rc_render_backward.
+forward calls rc_render, the backward calls rc_render_backward_views_with_forward
+with the forward's image (one march per ray instead of two).
 """
 from __future__ import annotations
 
 import torch
 
-from . import rc_camera_set, rc_render, rc_render_backward, rc_tf2d_set_device, rc_tf_set_device
+from . import rc_camera_set, rc_render, rc_render_backward_views_with_forward, rc_tf2d_set_device, rc_tf_set_device
 
 
 def _set_table(handle, tf, gmax):
@@ -36,16 +37,16 @@ class RenderTF(torch.autograd.Function):
         out = torch.empty((camera["height"], camera["width"], 4), device=tf.device, dtype=torch.float32)
         rc_render(handle, vol, params, out)
         fctx.handle, fctx.vol, fctx.params, fctx.camera, fctx.gmax = handle, vol, params, camera, gmax
-        fctx.save_for_backward(tf)
+        fctx.save_for_backward(tf, out)
         return out
 
     @staticmethod
     def backward(fctx, gout):
-        (tf,) = fctx.saved_tensors
+        tf, out = fctx.saved_tensors
         _set_table(fctx.handle, tf, fctx.gmax)
-        rc_camera_set(fctx.handle, fctx.camera)
         dtf = torch.empty_like(tf)
-        rc_render_backward(fctx.handle, fctx.vol, fctx.params, gout.contiguous(), dtf)
+        rc_render_backward_views_with_forward(fctx.handle, fctx.vol, fctx.params, [fctx.camera], out,
+                                              gout.contiguous(), dtf)
         return dtf, None, None, None, None, None
 
 

@@ -1,8 +1,12 @@
 // Adjoint of the compositing ray function with respect to the transfer-function
 // table (Eq. 4-5 are differentiable in the table entries).
 //
-// Per ray, pass 1 recomputes the forward march (no empty-space skipping) to get
-// C_final, T_final and the number n of samples up to termination. Pass 2
+// Per ray, pass 1 recomputes the forward march (with exact empty-space
+// skipping) to get C_final, T_final and the number n of samples up to
+// termination; when the caller gives the forward images, C_final and T_final
+// are read from them instead and pass 2 stops at the termination sample by
+// itself (it rebuilds T sample by sample, and the skipped samples of the
+// forward have zero opacity, so its stop decisions are the forward's). Pass 2
 // marches again front to back, rebuilding T_k and the prefix C_{<=k}, so that
 // the suffix S_k = C_final - C_{<=k} is known without storing samples or
 // dividing transmittance backwards:
@@ -159,7 +163,17 @@ __global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 128) adjoint_kernel(cons
     // T_final and the sample count n up to termination
     float Cf0 = 0.0f, Cf1 = 0.0f, Cf2 = 0.0f, Tf = 1.0f;
     int n = 0;
-    if (has_g) {
+    const bool given = A.fimg != nullptr;
+    if (given) {
+        if (has_g) {
+            const float4 f = A.fimg[((size_t)blockIdx.z * cam.H + y) * cam.W + x];
+            Cf0 = f.x;
+            Cf1 = f.y;
+            Cf2 = f.z;
+            Tf = 1.0f - f.w;
+            n = R.nsamp;
+        }
+    } else if (has_g) {
         int k = 0;
         while (k < R.nsamp) {
             float p[3];
@@ -230,6 +244,7 @@ __global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 128) adjoint_kernel(cons
             C1 = __fmaf_rn(ta, gg, C1);
             C2 = __fmaf_rn(ta, b, C2);
             T = T * (1.0f - ap);
+            if (given && (1.0f - T) >= a.p.term) n = k + 1;        // the forward stopped after this sample
             const float om = 1.0f - ap;
             const float inv = om > 0.0f ? 1.0f / om : 0.0f;
             float dap = g.x * (Tk * r - (Cf0 - C0) * inv) + g.y * (Tk * gg - (Cf1 - C1) * inv) +

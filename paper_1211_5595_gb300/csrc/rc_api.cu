@@ -1128,13 +1128,33 @@ rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol, const rc_ren
     a.dimg = reinterpret_cast<const float4 *>(dL_dimage);
     a.acc = reinterpret_cast<long long *>(ctx->d_scratch);
     a.acc_scale = 0.0f;
+    a.fimg = nullptr;
     RC_CUDA(ctx, launch_adjoint(a, 1, dL_dtf, ctx->stream));
     return RC_OK;
 }
 
+static rc_status backward_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                const rc_camera *cams, int nviews, const float *images, const float *dL_dimages,
+                                float *dL_dtf, const char *who);
+
 rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
                                    const rc_camera *cams, int nviews, const float *dL_dimages, float *dL_dtf) {
-    const char *who = "rc_render_backward_views";
+    return backward_views(ctx, vol, p, cams, nviews, nullptr, dL_dimages, dL_dtf, "rc_render_backward_views");
+}
+
+rc_status rc_render_backward_views_with_forward(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                                const rc_camera *cams, int nviews, const float *images,
+                                                const float *dL_dimages, float *dL_dtf) {
+    const char *who = "rc_render_backward_views_with_forward";
+    if (ctx && !images) return fail(ctx, RC_ERR_INVALID_ARG, "%s: images is NULL", who);
+    return backward_views(ctx, vol, p, cams, nviews, images, dL_dimages, dL_dtf, who);
+}
+
+}  // extern "C"
+
+static rc_status backward_views(rc_context *ctx, const rc_volume *vol, const rc_render_params *p,
+                                const rc_camera *cams, int nviews, const float *images, const float *dL_dimages,
+                                float *dL_dtf, const char *who) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "%s: ctx is NULL", who);
     rc_status st = check_views(ctx, cams, nviews, who);
     if (st == RC_OK) st = check_render_views(ctx, vol, p, cams, dL_dtf, who);
@@ -1159,9 +1179,12 @@ rc_status rc_render_backward_views(rc_context *ctx, const rc_volume *vol, const 
     a.dimg = reinterpret_cast<const float4 *>(dL_dimages);
     a.acc = reinterpret_cast<long long *>(ctx->d_scratch);
     a.acc_scale = 0.0f;
+    a.fimg = reinterpret_cast<const float4 *>(images);
     RC_CUDA(ctx, launch_adjoint(a, nviews, dL_dtf, ctx->stream));
     return RC_OK;
 }
+
+extern "C" {
 
 }  // extern "C"
 
@@ -1228,6 +1251,7 @@ rc_status rc_render_backward_noalloc(rc_context *ctx, const rc_volume *vol, cons
     a.dimg = reinterpret_cast<const float4 *>(dL_dimage);
     a.acc = scratch;            // cleared on the stream before the kernel runs
     a.acc_scale = 0.0f;
+    a.fimg = nullptr;
     RC_CUDA(ctx, launch_adjoint(a, 1, dL_dtf, ctx->stream));
     return RC_OK;
 }

@@ -117,6 +117,7 @@ struct MarchArgs {
 struct AdjointArgs {
     MarchArgs m;
     const float4 *dimg;            // H x W dL/dI
+    const float4 *fimg;            // the forward images (C, 1 - T) of the same views, or null: recomputed
     long long *acc;                // K x 4 fixed-point accumulators (scratch)
     float acc_scale;               // fixed-point units per unit of gradient
 };

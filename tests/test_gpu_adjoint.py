@@ -127,6 +127,64 @@ def test_views_gradient_matches_oracle_and_single_views(rc, orc, c4):
     assert np.array_equal(dtf.cpu().numpy().astype(np.float64), got)
 
 
+@pytest.mark.parametrize("form", ["plain", "plain_term1", "shaded", "bspline", "tf2d"])
+def test_gradient_with_forward_images(rc, orc, c4, form):
+    """The gradient given the forward images (one march per ray, the final
+    colour and transmittance read from the images, termination found by the
+    gradient march itself) equals the gradient that recomputes the forward,
+    for every form the gradient takes, over four views in one launch; the
+    plain form also against the oracle."""
+    import torch
+    ph, ctx, vol, cams = c4
+    cams = cams[:4]
+    term = 1.0 if form == "plain_term1" else 0.99
+    shade = form in ("shaded", "bspline")
+    filt = rc.RC_FILTER_BSPLINE if form == "bspline" else rc.RC_FILTER_TRILINEAR
+    if form == "tf2d":
+        tab = init_tf2d(8)
+        rc.rc_tf2d_set(ctx, tab, GMAX)
+        shape = tab.shape
+    else:
+        rc.rc_tf_set(ctx, init_tf())
+        shape = (W["K"], 4)
+    p = rc.RenderParams(step_vox=W["step"], term=term, shade=shade, skip=True, filter=filt)
+    H, Wd = W["height"], W["width"]
+    imgs = torch.empty((len(cams), H, Wd, 4), device="cuda")
+    rc.rc_render_views(ctx, vol, p, cams, imgs)
+    G = torch.randn(imgs.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(77))
+    a = torch.empty(shape, device="cuda")
+    b = torch.empty(shape, device="cuda")
+    rc.rc_render_backward_views(ctx, vol, p, cams, G, a)
+    rc.rc_render_backward_views_with_forward(ctx, vol, p, cams, imgs, G, b)
+    torch.cuda.synchronize()
+    A, B = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+    scale = np.abs(A).max()
+    assert scale > 0 and np.abs(A - B).max() <= 2e-5 * scale, np.abs(A - B).max() / scale
+    rc.rc_render_backward_views_with_forward(ctx, vol, p, cams, imgs, G, a)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy().astype(np.float64), B)            # deterministic
+    if form == "plain":
+        tf = init_tf()
+        total_o = np.zeros((W["K"], 4))
+        gs = []
+        for v, cam in enumerate(cams):
+            pix = synth.sample_pixels(W["width"], W["height"], 2048, seed=960 + v)
+            sc = orc.Scene(ph.vol, ph.spacing, tf, cam, step=W["step"], term=term)
+            keep = pix[~orc.render(sc, pixels=pix)["tie"]]
+            g = seeded_upstream(970 + v, keep, (H, Wd))
+            gs.append(g)
+            total_o += orc.render_grad(sc, g[keep], pixels=keep)[0]
+        G2 = torch.from_numpy(np.stack(gs).astype(np.float32).reshape(len(cams), H, Wd, 4)).cuda()
+        rc.rc_render_backward_views_with_forward(ctx, vol, p, cams, imgs, G2, b)
+        torch.cuda.synchronize()
+        got = b.cpu().numpy().astype(np.float64)
+        assert np.abs(got - total_o).max() / np.abs(total_o).max() < 2e-4
+    with pytest.raises(rc.RCError) as ei:
+        rc.rc_render_backward_views_with_forward(ctx, vol, p, cams, None, G, b)
+    assert ei.value.status == rc.RC_ERR_INVALID_ARG
+    rc.rc_tf_set(ctx, init_tf())
+
+
 GMAX = 1200.0
 
 
