@@ -1048,9 +1048,11 @@ def main():
                      "dram": dram, "l2": l2, "issue": issue},
         "e2e": e2e,
         "forms": forms,
-        # per step: re-layout, value+gradient bricks, 16^3 and 4^3 min/max grids,
-        # table, brick and sub-block occupancy masks, march
-        "gpu_launches": args.steps * 8,
+        # per step, this library's kernels (the ncu launch list): the volume
+        # preparation (apron and value+gradient bricks, both trilinear grids),
+        # the table's FP16 copy, the brick and the 4^3 sub-block occupancy
+        # masks, the march of every view
+        "gpu_launches": args.steps * 5,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
