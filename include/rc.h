@@ -258,7 +258,8 @@ rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvo
  * does not skip empty space (an
  * empty brick still has a gradient). The forward march is recomputed per ray;
  * nothing is stored per sample. The result does not depend on thread
- * scheduling (fixed-point accumulation). */
+ * scheduling: each warp sums in its own program order, and the sums across
+ * warps and blocks are 64-bit fixed point (scale 2^32 / max|dL/dI|). */
 rc_status rc_render_backward(rc_context *ctx, const rc_volume *vol,
                              const rc_render_params *params, const float *dL_dimage,
                              float *dL_dtf);

@@ -13,9 +13,15 @@
 //   dI_c/da'_k = T_k col_kc - S_kc / (1 - a'_k),  dI_a/da'_k = T_k - (T_{k+1} - T_n) / (1 - a'_k)
 //   dI_c/dcol_kc = T_k a'_k,  da'/da = r (1 - min(a, 1 - 1e-6))^(r - 1)
 // and the two table entries of the sample's lerp receive weights (1 - w, w).
-// Contributions are summed as 64-bit fixed point (scale 2^32 / max|dL/dI|) in
-// shared memory, then in global memory: integer sums do not depend on the order
-// of the atomics, so the result is deterministic.
+// Lanes of a warp that hit the same entries are summed first (a fixed tree
+// order). A 1-D table of at most kWarpAccK entries then keeps one FP32 copy
+// per warp in shared memory, which only that warp's group leaders update, in
+// its own program order; at the end each CTA adds its warps' copies in warp
+// order and converts the sums to 64-bit fixed point (scale 2^32 / max|dL/dI|)
+// for the global sums. Larger tables add each group's sums as 64-bit fixed
+// point to the CTA's shared accumulators directly. Integer sums do not depend
+// on the order of the atomics, and no other sum depends on thread scheduling,
+// so the result is deterministic.
 #include "rc_device.cuh"
 
 namespace rc {
@@ -44,6 +50,14 @@ __device__ __forceinline__ void acc_add(unsigned long long *acc, int idx, float 
     long long q = __float2ll_rn(v * scale);
     if (q != 0) atomicAdd(acc + idx, (unsigned long long)q);
 }
+
+// 1-D tables of up to this many entries take the per-warp FP32 accumulators
+// (16 B per entry and warp; with the FP32 table 80 B per entry and CTA: 40 KB
+// at 512 entries). Measured on the 128x128x96 workload (256 entries, 8 views
+// at 512^2, ms per view given the forward images): 0.231 with the CTA's 64-bit
+// fixed-point atomics, 0.161 per warp: no conversion and no atomic per group.
+constexpr int kWarpAccK = 512;
+constexpr int kAdjWarps = 4;                     // warps of a 1-D table's CTA
 
 // 2-D table accumulators: the table's M x K x 4 fixed-point sums live in
 // global memory (they do not fit in shared memory), fronted per CTA by a
@@ -130,18 +144,24 @@ __device__ __forceinline__ float dalpha_factor(float x, float ratio, int rmode) 
 // leaders add through the CTA's slot cache to the global fixed-point
 // accumulators (the M x K table's accumulators do not fit in shared memory).
 template <int ST, bool SHADE, int RM, bool CUBIC, bool TF2>
-__global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 128) adjoint_kernel(const AdjointArgs A, const float *absmax) {
+__global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 32 * kAdjWarps) adjoint_kernel(const AdjointArgs A, const float *absmax) {
     const MarchArgs &a = A.m;
     const int K = a.tf.K;
     constexpr bool GRAD = SHADE || TF2;
     constexpr int NV = TF2 ? 16 : 8;                  // contributions per sample
+    const bool wacc = !TF2 && K <= kWarpAccK;         // per-warp FP32 accumulators
     extern __shared__ float4 smem[];
     float4 *s_tf = smem;
     unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(smem + (TF2 ? 0 : K));
+    float4 *s_wacc = smem + K;                        // [warp][entry], 1-D tables of <= kWarpAccK entries
     int *s_tag = reinterpret_cast<int *>(s_acc + 4 * kSlots);          // 2-D table only
     if (!TF2) {
         load_tf(a.tf, s_tf);
-        for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) s_acc[e] = 0ull;
+        if (wacc) {
+            for (int e = threadIdx.x; e < kAdjWarps * K; e += blockDim.x) s_wacc[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else {
+            for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) s_acc[e] = 0ull;
+        }
     } else {
         for (int e = threadIdx.x; e < 4 * kSlots; e += blockDim.x) s_acc[e] = 0ull;
         for (int e = threadIdx.x; e < kSlots; e += blockDim.x) s_tag[e] = -1;
@@ -198,8 +218,9 @@ __global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 128) adjoint_kernel(cons
     }
     // pass 2: every sample again (an empty brick still has a gradient), the
     // prefix C_{<=k} rebuilt, one gradient contribution per sample; lanes that
-    // hit the same table entries are summed first, then one 64-bit fixed-point
-    // atomic per entry and channel
+    // hit the same table entries are summed first, then the group's leader
+    // adds the sums to its warp's FP32 copy (or, for a large table, one 64-bit
+    // fixed-point atomic per entry and channel)
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, T = 1.0f;
     for (int k = 0; __any_sync(0xffffffffu, k < n); k++) {
         const bool active = k < n;
@@ -268,7 +289,26 @@ __global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 128) adjoint_kernel(cons
         const unsigned peers = __match_any_sync(0xffffffffu, active ? i : -1 - lane);
         group_sum<NV>(peers, v);
         const bool leader = active && (peers & ((1u << lane) - 1u)) == 0u;
-        if (leader) {
+        if (wacc) {
+            // the leaders hold distinct entries i, but the i + 1 of one group
+            // may be the i of another: entry i first, then (after the warp
+            // barrier) entry i + 1, each a plain read-modify-write of a slot
+            // no other leader touches in that phase. The barrier before the
+            // first phase orders it after the previous sample's second phase.
+            float4 *wa = s_wacc + warp * K;
+            __syncwarp();
+            if (leader) {
+                float4 q = wa[i];
+                q.x += v[0]; q.y += v[1]; q.z += v[2]; q.w += v[3];
+                wa[i] = q;
+            }
+            __syncwarp();
+            if (leader) {
+                float4 q = wa[i + 1];
+                q.x += v[4]; q.y += v[5]; q.z += v[6]; q.w += v[7];
+                wa[i + 1] = q;
+            }
+        } else if (leader) {
             if constexpr (TF2) {
                 unsigned long long *g_acc = reinterpret_cast<unsigned long long *>(A.acc);
                 cache_add4(s_acc, s_tag, g_acc, i, v, scale);
@@ -283,7 +323,17 @@ __global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 128) adjoint_kernel(cons
     }
     __syncthreads();
     unsigned long long *g_acc = reinterpret_cast<unsigned long long *>(A.acc);
-    if (!TF2) {
+    if (wacc) {
+        // the warps' copies summed in warp order, then one fixed-point add
+        const float *w = reinterpret_cast<const float *>(s_wacc);
+        for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) {
+            float sum = w[e];
+#pragma unroll
+            for (int wi = 1; wi < kAdjWarps; wi++) sum += w[wi * 4 * K + e];
+            const long long q = __float2ll_rn(sum * scale);
+            if (q != 0) atomicAdd(g_acc + e, (unsigned long long)q);
+        }
+    } else if (!TF2) {
         for (int e = threadIdx.x; e < 4 * K; e += blockDim.x) {
             unsigned long long v = s_acc[e];
             if (v != 0ull) atomicAdd(g_acc + e, v);
@@ -306,17 +356,20 @@ __global__ void finalize_kernel(const long long *acc, int n, const float *absmax
 
 template <typename Kern>
 static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
-    // the 1-D table and its accumulators in shared memory; for a 2-D table
-    // the slot cache (values and tags)
-    size_t smem = a.m.tf.M >= 2 ? (size_t)kSlots * (4 * sizeof(long long) + sizeof(int))
-                                : (size_t)a.m.tf.K * (sizeof(float4) + 4 * sizeof(long long));
+    // the 1-D table and its accumulators in shared memory (per warp in FP32
+    // up to kWarpAccK entries, else per CTA in 64-bit fixed point); for a 2-D
+    // table the slot cache (values and tags)
+    const int K = a.m.tf.K;
+    size_t smem = a.m.tf.M >= 2   ? (size_t)kSlots * (4 * sizeof(long long) + sizeof(int))
+                  : K <= kWarpAccK ? (size_t)K * (1 + kAdjWarps) * sizeof(float4)
+                                   : (size_t)K * (sizeof(float4) + 4 * sizeof(long long));
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const int rows = a.m.tf.M >= 2 ? 2 * kWarps2D : 8;         // pixel rows per CTA
     dim3 grid((a.m.cam.W + 15) / 16, (a.m.cam.H + rows - 1) / rows, nviews);
-    kern<<<grid, a.m.tf.M >= 2 ? 32 * kWarps2D : 128, smem, s>>>(a, absmax);
+    kern<<<grid, a.m.tf.M >= 2 ? 32 * kWarps2D : 32 * kAdjWarps, smem, s>>>(a, absmax);
     return cudaGetLastError();
 }
 

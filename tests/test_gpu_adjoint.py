@@ -93,6 +93,43 @@ def test_gradient_matches_oracle(rc, orc, c4, shade, term, bspline):
     assert np.abs(total_o).sum() > 0
 
 
+@pytest.mark.parametrize("K", [2, 512, 513, 4096])
+def test_gradient_table_sizes(rc, orc, c4, K):
+    """Both accumulator forms of a 1-D table against the FP64 oracle at their
+    edges: per-warp FP32 copies up to 512 entries (2: every sample lerps
+    entries 0 and 1; 512: the largest), the CTA's 64-bit fixed-point sums
+    above (513: the smallest; 4096: the largest table), one 4-view launch and
+    repeated bit for bit."""
+    import torch
+    ph, ctx, vol, cams = c4
+    cams = cams[:4]
+    tf = synth.noise_tf(K, 300 + K, alpha_max=0.1)
+    term = 0.99
+    total_o = np.zeros((K, 4))
+    gs = []
+    for v, cam in enumerate(cams):
+        pix = synth.sample_pixels(W["width"], W["height"], 1024, seed=1300 + v)
+        sc = orc.Scene(ph.vol, ph.spacing, tf, cam, step=W["step"], term=term)
+        keep = pix[~orc.render(sc, pixels=pix)["tie"]]
+        g = seeded_upstream(1350 + v, keep, (W["height"], W["width"]))
+        gs.append(g)
+        og, _ = orc.render_grad(sc, g[keep], pixels=keep)
+        total_o += og
+    rc.rc_tf_set(ctx, tf)
+    G = torch.from_numpy(np.stack(gs).astype(np.float32).reshape(len(cams), W["height"], W["width"], 4)).cuda()
+    dtf = torch.empty((K, 4), device="cuda", dtype=torch.float32)
+    p = rc.RenderParams(step_vox=W["step"], term=term, shade=False, skip=False)
+    rc.rc_render_backward_views(ctx, vol, p, cams, G, dtf)
+    torch.cuda.synchronize()
+    got = dtf.cpu().numpy().astype(np.float64)
+    scale = np.abs(total_o).max()
+    assert scale > 0
+    assert np.abs(got - total_o).max() / scale < 2e-4, np.abs(got - total_o).max() / scale
+    rc.rc_render_backward_views(ctx, vol, p, cams, G, dtf)
+    torch.cuda.synchronize()
+    assert np.array_equal(dtf.cpu().numpy().astype(np.float64), got)
+
+
 def test_views_gradient_matches_oracle_and_single_views(rc, orc, c4):
     """One launch over all 8 views: the summed gradient equals the oracle's
     sum over the views, and the sum of the per-view gradients (to the
