@@ -130,6 +130,56 @@ def test_gradient_table_sizes(rc, orc, c4, K):
     assert np.array_equal(dtf.cpu().numpy().astype(np.float64), got)
 
 
+@pytest.mark.parametrize("K,tf2d", [(256, False), (1024, False), (256, True)])
+def test_gradient_ragged_image_every_pixel(rc, orc, c4, K, tf2d):
+    """An image of 45 x 27 pixels, neither side a multiple of the block's
+    16 x 8 (or, 2-D table, 16 x 16) pixels: the lanes outside the image take
+    part in every warp barrier of the scatter and add nothing. Every pixel's
+    upstream gradient is non-zero (except termination ties); two views in one
+    launch, recomputing the forward and given the forward images, against the
+    FP64 oracle; 256 entries take the per-warp accumulators, 1024 the block's
+    fixed-point ones."""
+    import torch
+    ph, ctx, vol, _ = c4
+    H, Wd = 27, 45
+    cams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=Wd, height=H) for az in (20.0, 200.0)]
+    if tf2d:
+        M = 8
+        tab = np.repeat(synth.noise_tf(K, 1400, alpha_max=0.1)[None], M, axis=0)
+        tab[..., 3] *= np.linspace(0.4, 1.0, M, dtype=np.float32)[:, None]
+        rc.rc_tf2d_set(ctx, tab, GMAX)
+        shape = tab.shape
+    else:
+        tab = synth.noise_tf(K, 1400 + K, alpha_max=0.1)
+        rc.rc_tf_set(ctx, tab)
+        shape = (K, 4)
+    term = 0.99
+    total_o = np.zeros(shape)
+    gs = []
+    for v, cam in enumerate(cams):
+        sc = orc.Scene(ph.vol, ph.spacing, tab, cam, step=W["step"], term=term, gmax=GMAX if tf2d else None)
+        fwd = orc.render(sc)
+        keep = np.flatnonzero(~fwd["tie"].reshape(-1))
+        assert len(keep) > 0.9 * H * Wd
+        g = seeded_upstream(1450 + v, keep, (H, Wd))
+        gs.append(g)
+        total_o += orc.render_grad(sc, g[keep], pixels=keep)[0]
+    G = torch.from_numpy(np.stack(gs).astype(np.float32).reshape(len(cams), H, Wd, 4)).cuda()
+    p = rc.RenderParams(step_vox=W["step"], term=term, shade=False, skip=False)
+    imgs = torch.empty((len(cams), H, Wd, 4), device="cuda")
+    rc.rc_render_views(ctx, vol, p, cams, imgs)
+    a = torch.empty(shape, device="cuda")
+    b = torch.empty(shape, device="cuda")
+    rc.rc_render_backward_views(ctx, vol, p, cams, G, a)
+    rc.rc_render_backward_views_with_forward(ctx, vol, p, cams, imgs, G, b)
+    torch.cuda.synchronize()
+    scale = np.abs(total_o).max()
+    assert scale > 0
+    for got in (a, b):
+        err = np.abs(got.cpu().numpy().astype(np.float64) - total_o).max() / scale
+        assert err < 2e-4, err
+
+
 def test_views_gradient_matches_oracle_and_single_views(rc, orc, c4):
     """One launch over all 8 views: the summed gradient equals the oracle's
     sum over the views, and the sum of the per-view gradients (to the
