@@ -267,20 +267,34 @@ __device__ __forceinline__ float value_grad_vg(const VolDev &v, const Cell &c, f
     return r.x;
 }
 
-// A uint16 value+gradient entry as the FP32 pairs (V, D_x) and (D_y, D_z),
-// exactly: a byte permute places each 16-bit field in the mantissa of 2^23,
-// and one packed subtraction per pair removes 2^23 (the value) or
-// 2^23 + 32768 (the offset differences).
-__device__ __forceinline__ ulonglong2 vg16_decode(uint2 q) {
-    unsigned long long a, b, r0, r1;
+// A uint16 value+gradient entry as biased FP32 pairs (V + m0, D_x + m1) and
+// (D_y + m1, D_z + m1), exactly: a byte permute places each 16-bit field in
+// the mantissa of 2^23, so m0 = 2^23 for the value and m1 = 2^23 + 32768 for
+// the offset differences.
+__device__ __forceinline__ ulonglong2 vg16_biased(uint2 q) {
+    unsigned long long a, b;
     asm("mov.b64 %0, {%1, %2};"
         : "=l"(a)
         : "r"(__byte_perm(q.x, 0x4B000000u, 0x7610)), "r"(__byte_perm(q.x, 0x4B000000u, 0x7632)));
     asm("mov.b64 %0, {%1, %2};"
         : "=l"(b)
         : "r"(__byte_perm(q.y, 0x4B000000u, 0x7610)), "r"(__byte_perm(q.y, 0x4B000000u, 0x7632)));
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r0) : "l"(a), "l"(pack2(8388608.0f, 8421376.0f)));
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r1) : "l"(b), "l"(pack2(8421376.0f, 8421376.0f)));
+    return make_ulonglong2(a, b);
+}
+
+// lerp4p of two uint16 entries a and b along x. With a' = a + m and
+// b' = b + m (biased, exact integers below 2^24), b' - a' = b - a exactly,
+// so fma(w, b' - a', a' - m) is lerp4p of the decoded entries bit for bit,
+// with the bias removed from the first entry only.
+__device__ __forceinline__ ulonglong2 vg16_lerp(uint2 qa, uint2 qb, unsigned long long w) {
+    const ulonglong2 a = vg16_biased(qa), b = vg16_biased(qb);
+    unsigned long long d0, d1, s0, s1, r0, r1;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(b.x), "l"(a.x));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(b.y), "l"(a.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(s0) : "l"(a.x), "l"(pack2(8388608.0f, 8421376.0f)));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(s1) : "l"(a.y), "l"(pack2(8421376.0f, 8421376.0f)));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r0) : "l"(w), "l"(d0), "l"(s0));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r1) : "l"(w), "l"(d1), "l"(s1));
     return make_ulonglong2(r0, r1);
 }
 
@@ -293,11 +307,10 @@ __device__ __forceinline__ float value_grad_vg16(const VolDev &v, const Cell &c,
     const uint2 *p = reinterpret_cast<const uint2 *>(v.vg) + idx;
     constexpr int DY = kGradEdge, DZ = kGradEdge * kGradEdge;
     const unsigned long long wx = pack2(c.w[0], c.w[0]), wy = pack2(c.w[1], c.w[1]), wz = pack2(c.w[2], c.w[2]);
-    auto ld = [&](int o) { return vg16_decode(__ldg(p + o)); };
-    const ulonglong2 c00 = lerp4p(ld(0), ld(1), wx);
-    const ulonglong2 c10 = lerp4p(ld(DY), ld(DY + 1), wx);
-    const ulonglong2 c01 = lerp4p(ld(DZ), ld(DZ + 1), wx);
-    const ulonglong2 c11 = lerp4p(ld(DZ + DY), ld(DZ + DY + 1), wx);
+    const ulonglong2 c00 = vg16_lerp(__ldg(p), __ldg(p + 1), wx);
+    const ulonglong2 c10 = vg16_lerp(__ldg(p + DY), __ldg(p + DY + 1), wx);
+    const ulonglong2 c01 = vg16_lerp(__ldg(p + DZ), __ldg(p + DZ + 1), wx);
+    const ulonglong2 c11 = vg16_lerp(__ldg(p + DZ + DY), __ldg(p + DZ + DY + 1), wx);
     const float4 r = unpack4(lerp4p(lerp4p(c00, c10, wy), lerp4p(c01, c11, wy), wz));
     g[0] = r.y * v.inv2s[0];
     g[1] = r.z * v.inv2s[1];
