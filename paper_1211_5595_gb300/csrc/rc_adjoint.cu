@@ -55,7 +55,7 @@ __device__ __forceinline__ void acc_add(unsigned long long *acc, int idx, float 
 // (16 B per entry and warp; with the FP32 table 80 B per entry and CTA: 40 KB
 // at 512 entries). Measured on the 128x128x96 workload (256 entries, 8 views
 // at 512^2, ms per view given the forward images): 0.231 with the CTA's 64-bit
-// fixed-point atomics, 0.161 per warp: no conversion and no atomic per group.
+// fixed-point atomics, 0.151 per warp: no conversion and no atomic per group.
 constexpr int kWarpAccK = 512;
 constexpr int kAdjWarps = 4;                     // warps of a 1-D table's CTA
 
