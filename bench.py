@@ -183,15 +183,18 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        if not self.samples:
+    def summary(self, first=0, last=None):
+        """Median SM clock, the largest maximum clock and the throttle reasons
+        seen in samples[first:last]."""
+        samples = self.samples[first:last]
+        if not samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        sm = [float(s[0]) for s in samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in samples if s[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[2 + i].lower() == "active"})
+        reasons = sorted({names[i] for s in samples for i in range(4) if s[2 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(samples)}
 
 
 def max_over_ranks(value, world, device):
@@ -949,19 +952,29 @@ def main():
         # host-timed: three timed loops of the K steps, the median reported
         # (one loop alone moves by several percent with the host's load)
         # (the slowest rank's time of each loop, the ranks started together)
-        runs = []
-        for _ in range(3):
-            if world > 1:
-                dist.barrier()
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                e2e_step()
-            el = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-            runs.append(world * dense * args.steps / el / 1e9)
+        runs, spans, loop_steps = [], [], []
+        with ClockSampler(local) as ck:
+            time.sleep(0.5)                              # the sampler's first lines
+            for _ in range(3):
+                if world > 1:
+                    dist.barrier()
+                i0 = len(ck.samples)
+                t0 = time.perf_counter()
+                ts = [t0]
+                for _ in range(args.steps):
+                    e2e_step()                           # returns once the images are in host memory
+                    ts.append(time.perf_counter())
+                el = max_over_ranks(ts[-1] - t0, world, "cuda")
+                runs.append(world * dense * args.steps / el / 1e9)
+                spans.append((i0, len(ck.samples)))
+                st_ms = [1e3 * (b - a) for a, b in zip(ts, ts[1:])]
+                loop_steps.append({"median": statistics.median(st_ms), "min": min(st_ms), "max": max(st_ms)})
+        run_clocks = [ck.summary(a, b) for a, b in spans]
         e2e = {"value": statistics.median(runs), "unit": "Gsamples/s",
                "h2d_bytes_per_step": codes_host.numel() * 2 + tf.nbytes,
                "d2h_bytes_per_step": img_host.numel() * 4,
-               "runs": runs, "timing": f"host clock over {args.steps} steps, median of 3 loops"}
+               "runs": runs, "run_clocks": run_clocks, "run_step_ms": loop_steps,
+               "timing": f"host clock over {args.steps} steps, median of 3 loops"}
 
     hbm_peak, peak_kind = peaks()
     # reduced-precision storage forms on the same workload: FP16 (normalised)

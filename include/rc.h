@@ -169,7 +169,11 @@ rc_status rc_volume_brick_dims(const rc_volume *vol, int dims[3]);
  * entries in [0, 1], host memory, entry i at code i*vmax/(n_entries-1); a value
  * between entries is the linear interpolation of its two neighbours (table
  * coordinate u = fl(v * fl((n_entries-1) / vmax)), see rc_skip_mask_get). fp16 = 1
- * stores the table as FP16 (the precision form). */
+ * stores the table as FP16 (the precision form). The table is copied into a
+ * page-locked buffer of the context during the call (rgba may be reused at
+ * once) and reaches the device in stream order, without waiting for the work
+ * queued before it; the copy before it must have run (in a frame loop it ran
+ * before the previous frame's render). */
 rc_status rc_tf_set(rc_context *ctx, const float *rgba, int n_entries, int fp16);
 /* Same from device memory (asynchronous device-to-device copy). Values are not
  * range-checked on this path. */
@@ -188,7 +192,8 @@ rc_status rc_tf_set_device(rc_context *ctx, const float *rgba_dev, int n_entries
  * four entries around (u, w) blend
  * bilinearly. n_values 2..4096, n_grad 2..4096, n_values * n_grad <= 2^20,
  * gmax finite and > 0. fp16 = 1 rounds the entries to FP16. Replaces the
- * current table (1-D or 2-D). Compositing, the table gradient and the ray
+ * current table (1-D or 2-D). Copied as rc_tf_set copies (rgba may be reused
+ * at once; no wait for the queued work). Compositing, the table gradient and the ray
  * functions that do not classify use it; thresholding and the learned
  * proposal need a 1-D table (RC_ERR_UNSUPPORTED). Shading off still computes
  * the gradient. Empty-space skipping stays exact: a brick is empty only when

@@ -44,6 +44,10 @@ struct rc_context {
     // bit 0 = a bounded wait of a kernel gave up)
     unsigned long long *d_stats = nullptr;
     unsigned long long *h_stats = nullptr;   // pinned
+    void *h_tfstage = nullptr;               // pinned staging of host tables (rc_tf_set, rc_tf2d_set)
+    size_t tfstage_cap = 0;
+    cudaEvent_t ev_tfstage = nullptr;        // after the last copy out of the staging buffer
+    bool tfstage_pending = false;
     // camera records of a multi-view render
     CamRec *d_cams = nullptr;
     int cams_cap = 0;
@@ -261,6 +265,8 @@ rc_status rc_context_destroy(rc_context *ctx) {
     cudaFree(ctx->d_cams);
     cudaFree(ctx->d_batch);
     cudaFreeHost(ctx->h_stats);
+    cudaFreeHost(ctx->h_tfstage);
+    if (ctx->ev_tfstage) cudaEventDestroy(ctx->ev_tfstage);
     cudaFree(ctx->d_scratch);
     cudaFree(ctx->d_param);
     cudaFree(ctx->d_m);
@@ -478,6 +484,31 @@ __global__ void tf_to_half_kernel(const float4 *src, uint2 *dst, int K) {
     dst[i] = o;
 }
 
+// Copies a host table to device memory on the context's stream without
+// waiting for the work queued before it: through a page-locked staging
+// buffer owned by the context (the caller's memory may be reused as soon as
+// the call returns). The buffer is reused once its previous copy has run,
+// which in a frame loop happened before the previous frame's render.
+static rc_status stage_table(rc_context *ctx, void *dst, const void *src, size_t bytes) {
+    if (ctx->tfstage_pending) {
+        RC_CUDA(ctx, cudaEventSynchronize(ctx->ev_tfstage));
+        ctx->tfstage_pending = false;
+    }
+    if (!ctx->ev_tfstage) RC_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_tfstage, cudaEventDisableTiming));
+    if (bytes > ctx->tfstage_cap) {
+        void *nb = nullptr;
+        RC_CUDA(ctx, cudaMallocHost(&nb, bytes));
+        cudaFreeHost(ctx->h_tfstage);
+        ctx->h_tfstage = nb;
+        ctx->tfstage_cap = bytes;
+    }
+    memcpy(ctx->h_tfstage, src, bytes);
+    RC_CUDA(ctx, cudaMemcpyAsync(dst, ctx->h_tfstage, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    RC_CUDA(ctx, cudaEventRecord(ctx->ev_tfstage, ctx->stream));
+    ctx->tfstage_pending = true;
+    return RC_OK;
+}
+
 static rc_status tf_common(rc_context *ctx, const float *rgba, int K, int fp16, bool dev) {
     if (!ctx) return fail(nullptr, RC_ERR_INVALID_ARG, "rc_tf_set: ctx is NULL");
     if (!rgba) return fail(ctx, RC_ERR_INVALID_ARG, "rc_tf_set: rgba is NULL");
@@ -491,11 +522,15 @@ static rc_status tf_common(rc_context *ctx, const float *rgba, int K, int fp16, 
     DeviceScope ds(ctx->device);
     rc_status st = tf_reserve(ctx, K);
     if (st != RC_OK) return st;
-    RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_tf32, rgba, (size_t)K * sizeof(float4),
-                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    if (dev) {
+        RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_tf32, rgba, (size_t)K * sizeof(float4), cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+    } else {
+        st = stage_table(ctx, ctx->d_tf32, rgba, (size_t)K * sizeof(float4));
+        if (st != RC_OK) return st;
+    }
     tf_to_half_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_tf32, ctx->d_tf16, K);
     RC_CUDA(ctx, cudaGetLastError());
-    if (!dev) RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host source may be reused at once
     ctx->K = K;
     ctx->M = 0;
     ctx->tf_fp16 = fp16 ? 1 : 0;
@@ -563,15 +598,19 @@ static rc_status tf2_common(rc_context *ctx, const float *rgba, int K, int M, fl
         ctx->d_amax = am;
         ctx->tf2_cap = cap;
     }
-    RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_tf2, rgba, (size_t)n * sizeof(float4),
-                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    if (dev) {
+        RC_CUDA(ctx, cudaMemcpyAsync(ctx->d_tf2, rgba, (size_t)n * sizeof(float4), cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+    } else {
+        rc_status st = stage_table(ctx, ctx->d_tf2, rgba, (size_t)n * sizeof(float4));
+        if (st != RC_OK) return st;
+    }
     if (fp16) {
         tf2_round_half_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_tf2, n);
         RC_CUDA(ctx, cudaGetLastError());
     }
     tf2_amax_kernel<<<(K + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_tf2, K, M, ctx->d_amax);
     RC_CUDA(ctx, cudaGetLastError());
-    if (!dev) RC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host source may be reused at once
     ctx->K = K;
     ctx->M = M;
     ctx->gmax = gmax;

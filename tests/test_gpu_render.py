@@ -205,6 +205,47 @@ def test_table_size_limits(rc, orc, K):
         r.close()
 
 
+def test_tf_set_copies_the_host_table_and_keeps_order(rc, c1):
+    """rc_tf_set from host memory copies the table during the call (the
+    caller's array is overwritten right after each call here) without waiting
+    for the queued renders, and stays ordered with them: renders queued with
+    tables A, B, A (1-D) and then a 2-D table, without synchronising between
+    them, each equal the same render done alone."""
+    import torch
+    ph, tf, w, r = c1
+    cam = synth.orbit_camera(ph.dims, ph.spacing, 30.0, width=80, height=72)
+    tab_b = synth.noise_tf(256, 77, alpha_max=0.3)
+    tab2 = np.repeat(tab_b[None], 4, axis=0)
+    tab2[..., 3] *= np.linspace(0.3, 1.0, 4, dtype=np.float32)[:, None]
+    P = dict(step_vox=0.5, term=0.99, shade=True, skip=True)
+    try:
+        refs = []
+        for t in (tf, tab_b, tf):
+            r.set_tf(t)
+            refs.append(r.render(cam, **P))
+        rc.rc_tf2d_set(r.ctx, tab2, 900.0)
+        refs.append(r.render(cam, **P))
+        rc.rc_camera_set(r.ctx, cam)
+        outs = [torch.empty((72, 80, 4), device="cuda") for _ in range(4)]
+        buf = np.empty((256, 4), np.float32)
+        buf2 = np.empty_like(tab2)
+        for o, src in zip(outs[:3], (tf, tab_b, tf)):
+            buf[:] = src
+            rc.rc_tf_set(r.ctx, buf)
+            buf[:] = 0.5                                 # the call has taken its copy
+            rc.rc_render(r.ctx, r.vol, P, o)
+        buf2[:] = tab2
+        rc.rc_tf2d_set(r.ctx, buf2, 900.0)
+        buf2[:] = 0.5
+        rc.rc_render(r.ctx, r.vol, P, outs[3])
+        torch.cuda.synchronize()
+        for o, ref in zip(outs, refs):
+            assert np.array_equal(o.cpu().numpy(), ref)
+        assert not np.array_equal(refs[0], refs[1]) and not np.array_equal(refs[1], refs[3])
+    finally:
+        r.set_tf(tf)
+
+
 def test_empty_transfer_function_renders_black(c1):
     ph, tf, w, r = c1
     try:
