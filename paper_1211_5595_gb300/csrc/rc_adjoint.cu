@@ -59,6 +59,16 @@ __device__ __forceinline__ void acc_add(unsigned long long *acc, int idx, float 
 constexpr int kWarpAccK = 512;
 constexpr int kAdjWarps = 4;                     // warps of a 1-D table's CTA
 
+// Whether a 1-D table's gradient takes the per-warp accumulators: up to
+// kWarpAccK entries, except with the cubic B-spline when the forward is
+// recomputed: that march's 64-voxel gathers need the L1 capacity the larger
+// shared-memory footprint takes (same workload, B-spline, ms per view:
+// recomputing 0.529 with the CTA's accumulators, 0.575 per warp; given the
+// forward images 0.340 and 0.315).
+__host__ __device__ constexpr bool warp_acc(int K, bool tf2, bool cubic, bool given) {
+    return !tf2 && K <= kWarpAccK && (!cubic || given);
+}
+
 // 2-D table accumulators: the table's M x K x 4 fixed-point sums live in
 // global memory (they do not fit in shared memory), fronted per CTA by a
 // direct-mapped cache of kSlots entries in shared memory (72 KB). A slot is
@@ -149,7 +159,7 @@ __global__ void __launch_bounds__(TF2 ? 32 * kWarps2D : 32 * kAdjWarps) adjoint_
     const int K = a.tf.K;
     constexpr bool GRAD = SHADE || TF2;
     constexpr int NV = TF2 ? 16 : 8;                  // contributions per sample
-    const bool wacc = !TF2 && K <= kWarpAccK;         // per-warp FP32 accumulators
+    const bool wacc = warp_acc(K, TF2, CUBIC, A.fimg != nullptr);   // per-warp FP32 accumulators
     extern __shared__ float4 smem[];
     float4 *s_tf = smem;
     unsigned long long *s_acc = reinterpret_cast<unsigned long long *>(smem + (TF2 ? 0 : K));
@@ -354,15 +364,16 @@ __global__ void finalize_kernel(const long long *acc, int n, const float *absmax
     out[i] = (float)((double)acc[i] / scale);
 }
 
-template <typename Kern>
+template <bool CUBIC, typename Kern>
 static cudaError_t launch_adj(Kern kern, const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
     // the 1-D table and its accumulators in shared memory (per warp in FP32
-    // up to kWarpAccK entries, else per CTA in 64-bit fixed point); for a 2-D
+    // where warp_acc says so, else per CTA in 64-bit fixed point); for a 2-D
     // table the slot cache (values and tags)
     const int K = a.m.tf.K;
-    size_t smem = a.m.tf.M >= 2   ? (size_t)kSlots * (4 * sizeof(long long) + sizeof(int))
-                  : K <= kWarpAccK ? (size_t)K * (1 + kAdjWarps) * sizeof(float4)
-                                   : (size_t)K * (sizeof(float4) + 4 * sizeof(long long));
+    const bool wacc = warp_acc(K, a.m.tf.M >= 2, CUBIC, a.fimg != nullptr);
+    size_t smem = a.m.tf.M >= 2 ? (size_t)kSlots * (4 * sizeof(long long) + sizeof(int))
+                  : wacc         ? (size_t)K * (1 + kAdjWarps) * sizeof(float4)
+                                 : (size_t)K * (sizeof(float4) + 4 * sizeof(long long));
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -379,16 +390,16 @@ template <int RM, bool CUBIC, bool TF2>
 static cudaError_t launch_adj_rm(const AdjointArgs &a, int nviews, const float *absmax, cudaStream_t s) {
     switch (a.m.vol.storage * 2 + (a.m.p.shade ? 1 : 0)) {
         case RC_STORE_F32 * 2:
-            return launch_adj(adjoint_kernel<RC_STORE_F32, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
+            return launch_adj<CUBIC>(adjoint_kernel<RC_STORE_F32, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
         case RC_STORE_F32 * 2 + 1:
-            return launch_adj(adjoint_kernel<RC_STORE_F32, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
+            return launch_adj<CUBIC>(adjoint_kernel<RC_STORE_F32, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
         case RC_STORE_F16 * 2:
-            return launch_adj(adjoint_kernel<RC_STORE_F16, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
+            return launch_adj<CUBIC>(adjoint_kernel<RC_STORE_F16, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
         case RC_STORE_F16 * 2 + 1:
-            return launch_adj(adjoint_kernel<RC_STORE_F16, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
+            return launch_adj<CUBIC>(adjoint_kernel<RC_STORE_F16, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
         case RC_STORE_U16 * 2:
-            return launch_adj(adjoint_kernel<RC_STORE_U16, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
-        default: return launch_adj(adjoint_kernel<RC_STORE_U16, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
+            return launch_adj<CUBIC>(adjoint_kernel<RC_STORE_U16, false, RM, CUBIC, TF2>, a, nviews, absmax, s);
+        default: return launch_adj<CUBIC>(adjoint_kernel<RC_STORE_U16, true, RM, CUBIC, TF2>, a, nviews, absmax, s);
     }
 }
 
