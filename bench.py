@@ -17,6 +17,7 @@ no data-path collective); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -952,28 +953,29 @@ def main():
         # host-timed: three timed loops of the K steps, the median reported
         # (one loop alone moves by several percent with the host's load)
         # (the slowest rank's time of each loop, the ranks started together)
-        runs, spans, loop_steps = [], [], []
-        with ClockSampler(local) as ck:
-            time.sleep(0.5)                              # the sampler's first lines
-            for _ in range(3):
-                if world > 1:
-                    dist.barrier()
-                i0 = len(ck.samples)
-                t0 = time.perf_counter()
-                ts = [t0]
-                for _ in range(args.steps):
-                    e2e_step()                           # returns once the images are in host memory
-                    ts.append(time.perf_counter())
-                el = max_over_ranks(ts[-1] - t0, world, "cuda")
-                runs.append(world * dense * args.steps / el / 1e9)
-                spans.append((i0, len(ck.samples)))
-                st_ms = [1e3 * (b - a) for a, b in zip(ts, ts[1:])]
-                loop_steps.append({"median": statistics.median(st_ms), "min": min(st_ms), "max": max(st_ms)})
-        run_clocks = [ck.summary(a, b) for a, b in spans]
+        runs, loop_steps = [], []
+        # the garbage collector paused in the timed loops, as timeit does (a
+        # collection pass stalled a single step by 12-14 ms now and then); no
+        # clock sampler here: its queries go through the same driver
+        gc.collect()
+        gc.disable()
+        for _ in range(3):
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            ts = [t0]
+            for _ in range(args.steps):
+                e2e_step()                               # returns once the images are in host memory
+                ts.append(time.perf_counter())
+            el = max_over_ranks(ts[-1] - t0, world, "cuda")
+            runs.append(world * dense * args.steps / el / 1e9)
+            st_ms = [1e3 * (b - a) for a, b in zip(ts, ts[1:])]
+            loop_steps.append({"median": statistics.median(st_ms), "min": min(st_ms), "max": max(st_ms)})
+        gc.enable()
         e2e = {"value": statistics.median(runs), "unit": "Gsamples/s",
                "h2d_bytes_per_step": codes_host.numel() * 2 + tf.nbytes,
                "d2h_bytes_per_step": img_host.numel() * 4,
-               "runs": runs, "run_clocks": run_clocks, "run_step_ms": loop_steps,
+               "runs": runs, "run_step_ms": loop_steps,
                "timing": f"host clock over {args.steps} steps, median of 3 loops"}
 
     hbm_peak, peak_kind = peaks()

@@ -168,7 +168,8 @@ struct TcNetArgs {
     NetDev net;
     const float *feat;        // feature-matrix form: n x 112 FP32 (else null)
     float *net_out;           // feature-matrix form: n x 33
-    uint2 *range;             // camera form: per ray (b_start | b_end << 8, T^ bits), view-major
+    uint2 *range;             // camera form: per ray (b_start | b_end << 8, T^ bits), view-major; this and
+                              // pdf_out are not written for tiles none of whose rays meets the volume
     float *pdf_out;           // camera form writing PDFs instead (else null): per ray 32 floats, view-major
     float *that_out;          // with pdf_out: per ray T^
     long long n;              // feature-matrix form: rays
