@@ -119,6 +119,9 @@ typedef struct {
     uint64_t rays_hit;           /* rays that intersect the volume box */
     uint64_t rays_total;
     uint64_t fallback_rays;      /* importance-sampled renders: rays re-marched */
+    float device_ms;             /* device time of the call's work: CUDA events on the
+                                    context's stream before its first launch and after
+                                    its last one (copies of rc_render_views_host included) */
 } rc_stats;
 
 /* Text of a status code (static storage). */

@@ -45,7 +45,8 @@ class rc_render_params(C.Structure):
 
 class rc_stats(C.Structure):
     _fields_ = [("dense_samples", C.c_uint64), ("evaluated_samples", C.c_uint64),
-                ("rays_hit", C.c_uint64), ("rays_total", C.c_uint64), ("fallback_rays", C.c_uint64)]
+                ("rays_hit", C.c_uint64), ("rays_total", C.c_uint64), ("fallback_rays", C.c_uint64),
+                ("device_ms", C.c_float)]
 
 
 RC_PROPOSAL_BINS = 32
@@ -289,7 +290,8 @@ def _stats_dict(st):
     if st is None:
         return None
     return dict(dense_samples=st.dense_samples, evaluated_samples=st.evaluated_samples,
-                rays_hit=st.rays_hit, rays_total=st.rays_total, fallback_rays=st.fallback_rays)
+                rays_hit=st.rays_hit, rays_total=st.rays_total, fallback_rays=st.fallback_rays,
+                device_ms=st.device_ms)
 
 
 def rc_render_views(ctx, vol, params, cams, out, stats=False):

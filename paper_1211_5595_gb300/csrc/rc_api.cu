@@ -78,6 +78,7 @@ struct rc_context {
     size_t img_cap = 0;
     cudaEvent_t ev_rendered[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
     cudaEvent_t ev_start = nullptr;
+    cudaEvent_t ev_stats[2] = {nullptr, nullptr};   // around a call that returns statistics
 };
 
 struct rc_volume {
@@ -285,6 +286,8 @@ rc_status rc_context_destroy(rc_context *ctx) {
         if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);
     }
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    for (int i = 0; i < 2; i++)
+        if (ctx->ev_stats[i]) cudaEventDestroy(ctx->ev_stats[i]);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
     delete ctx;
@@ -871,11 +874,25 @@ static rc_status ensure_occupancy(rc_context *ctx, rc_volume *v, int f) {
 
 // Copies the device counters into *stats (synchronises the stream). The
 // importance kernels count fallback rays in the first slot.
+// Zeroes the statistics counters and marks the start of a call's device work
+// on the context's stream (read_stats marks its end).
+static cudaError_t stats_begin(rc_context *ctx) {
+    cudaError_t e = cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++)
+        if (!ctx->ev_stats[i]) e = cudaEventCreate(&ctx->ev_stats[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_stats[0], ctx->stream);
+    return e;
+}
+
 static rc_status read_stats(rc_context *ctx, rc_stats *stats, bool importance) {
+    RC_CUDA(ctx, cudaEventRecord(ctx->ev_stats[1], ctx->stream));
     RC_CUDA(ctx, cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                  ctx->stream));
     rc_status st = check_device_errors(ctx, "statistics");
     if (st != RC_OK) return st;
+    float ms = 0.0f;
+    RC_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_stats[0], ctx->ev_stats[1]));
+    stats->device_ms = ms;
     stats->dense_samples = importance ? 0 : ctx->h_stats[0];
     stats->evaluated_samples = ctx->h_stats[1];
     stats->rays_hit = ctx->h_stats[2];
@@ -944,7 +961,7 @@ rc_status rc_render(rc_context *ctx, const rc_volume *vol, const rc_render_param
     if (st != RC_OK) return st;
     MarchArgs a = march_args(ctx, v, p, out_rgba);
     if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        RC_CUDA(ctx, stats_begin(ctx));
         a.stats = ctx->d_stats;
     }
     RC_CUDA(ctx, launch_march_any(ctx, a, 1));
@@ -974,7 +991,7 @@ rc_status rc_render_views(rc_context *ctx, const rc_volume *vol, const rc_render
     a.cam = first;
     a.cams = ctx->d_cams;
     if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        RC_CUDA(ctx, stats_begin(ctx));
         a.stats = ctx->d_stats;
     }
     RC_CUDA(ctx, launch_march_any(ctx, a, nviews));
@@ -1072,7 +1089,7 @@ rc_status rc_render_views_host(rc_context *ctx, const rc_volume *vol, const rc_r
     MarchArgs a = march_args(ctx, v, p, nullptr);
     a.cam = first;
     if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        RC_CUDA(ctx, stats_begin(ctx));
         a.stats = ctx->d_stats;
     }
     st = render_groups_to_host(ctx, a, nviews, g, px, host_rgba);
@@ -1140,7 +1157,7 @@ rc_status rc_render_batch(rc_context *ctx, const rc_volume *const *vols, int nvo
     a.batch = ctx->d_batch;
     a.views = nviews;
     if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        RC_CUDA(ctx, stats_begin(ctx));
         a.stats = ctx->d_stats;
     }
     RC_CUDA(ctx, launch_march(a, nvols * nviews, ctx->stream));
@@ -1583,7 +1600,7 @@ rc_status rc_render_importance(rc_context *ctx, const rc_volume *vol, const rc_r
     a.pdf = pdf;
     a.that = that;
     if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        RC_CUDA(ctx, stats_begin(ctx));
         a.m.stats = ctx->d_stats;
     }
     RC_CUDA(ctx, launch_importance(a, 1, ctx->stream));
@@ -1657,7 +1674,7 @@ rc_status rc_render_importance_views(rc_context *ctx, const rc_volume *vol, cons
     a.sampling = sampling;
     a.lambda = lambda;
     if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
+        RC_CUDA(ctx, stats_begin(ctx));
         a.m.stats = ctx->d_stats;
     }
     RC_CUDA(ctx, launch_importance(a, nviews, ctx->stream));
@@ -1706,6 +1723,7 @@ static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_
     n.ntiles = (long long)n.tiles_x * n.tiles_y * nviews;
     n.budget = wait_budget(&n.issue_mma);
     n.err = error_word(ctx);
+    if (stats) RC_CUDA(ctx, stats_begin(ctx));       // the network kernel is part of the call's time
     RC_CUDA(ctx, launch_tc_net(n, ctx->stream));
     ImportanceArgs a = importance_args(ctx, v, p, nimp, eps, out, fallback);
     a.m.cam = first;
@@ -1718,10 +1736,7 @@ static rc_status proposal_views(rc_context *ctx, const rc_volume *vol, const rc_
     } else {
         a.range = ctx->d_range;
     }
-    if (stats) {
-        RC_CUDA(ctx, cudaMemsetAsync(ctx->d_stats, 0, 5 * sizeof(unsigned long long), ctx->stream));
-        a.m.stats = ctx->d_stats;
-    }
+    if (stats) a.m.stats = ctx->d_stats;
     RC_CUDA(ctx, launch_importance(a, nviews, ctx->stream));
     if (stats) return read_stats(ctx, stats, true);
     return RC_OK;

@@ -112,6 +112,24 @@ def test_dense_sample_counts_exact(c1, orc):
     compare(img, o, TOL_FP32)
 
 
+def test_stats_report_device_time(c1):
+    """rc_stats.device_ms: the device time of the call's work from CUDA events
+    on the context's stream: positive, within the call's wall time, and
+    longer for a 1024^2 image than for a 64^2 one."""
+    import time
+    ph, tf, w, r = c1
+    times = []
+    for size in (64, 1024):
+        cam = synth.orbit_camera(ph.dims, ph.spacing, 30.0, width=size, height=size)
+        r.render(cam, stats=True, step_vox=0.25, term=0.99, shade=True, skip=True)      # warm
+        t0 = time.perf_counter()
+        _, st = r.render(cam, stats=True, step_vox=0.25, term=0.99, shade=True, skip=True)
+        wall_ms = 1e3 * (time.perf_counter() - t0)
+        assert 0.0 < st["device_ms"] <= wall_ms
+        times.append(st["device_ms"])
+    assert times[1] > times[0]
+
+
 @pytest.mark.parametrize("shade", [False, True])
 def test_skip_on_off_bit_identical(c1, shade):
     ph, tf, w, r = c1
@@ -359,7 +377,9 @@ def test_brick_staged_march_equals_cached_march(rc, c2, monkeypatch, step):
     rc.rc_context_sync(r.ctx)
     monkeypatch.delenv("RC_MARCH_STAGED")
     assert torch.equal(a, b)
+    ta, tb = sa.pop("device_ms"), sb.pop("device_ms")
     assert sa == sb and sa["evaluated_samples"] > 0
+    assert tb > ta > 0.0                                 # the staged march is the slower one
     small = synth.head_phantom((37, 29, 21), (1.0, 1.2, 0.9), seed=8, tumor_radius_vox=3)
     g = GPURenderer(rc, small.vol, small.spacing)
     try:
@@ -396,7 +416,9 @@ def test_render_views_host_equals_device_render(rc, c1):
             sh = rc.rc_render_views_host(r.ctx, r.vol, P, cams, host, group=group, stats=group == 3)
             assert torch.equal(host, ref), (pinned, group)
             if group == 3:
-                assert sh == st
+                ms = sh.pop("device_ms")
+                assert sh == {k: v for k, v in st.items() if k != "device_ms"}
+                assert 0.0 < ms < 1e4
     # the device render is unchanged after the host path used the context
     rc.rc_render_views(r.ctx, r.vol, P, cams, dev)
     assert torch.equal(dev.cpu(), ref)
