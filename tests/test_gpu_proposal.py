@@ -353,6 +353,47 @@ def test_fused_render_matches_network_pdfs(rc, small):
     assert torch.equal(a.view(-1, 4)[hit], b.view(-1, 4)[hit])
 
 
+@pytest.mark.parametrize("sampling", ["range", "invcdf"])
+def test_proposal_render_with_empty_tiles(rc, small, sampling):
+    """A distant camera: the volume covers a small part of a ragged image, so
+    most 128-ray tiles have no ray that meets it and the network kernel skips
+    them. The proposal render still equals the importance march fed with the
+    network's outputs on every pixel (rays that miss are black), in both
+    readings, over three views in one launch pair."""
+    import torch
+    ph, tf, r = small
+    rc.rc_proposal_load(r.ctx, rc.pack_proposal_blob(synth.proposal_init_params(57)))
+    W, H = 150, 131
+    cams = [synth.orbit_camera(ph.dims, ph.spacing, az, width=W, height=H, distance_scale=4.0)
+            for az in (20.0, 140.0, 260.0)]
+    n = W * H
+    net = torch.empty((3, n, 33), device="cuda")
+    hits = []
+    for v, cam in enumerate(cams):
+        rc.rc_camera_set(r.ctx, cam)
+        F = torch.empty((n, 112), device="cuda")
+        rc.rc_proposal_features(r.ctx, r.vol, params_for(), F)
+        rc.rc_proposal_forward(r.ctx, F, n, net[v])
+        hits.append(F[:, 3:6].abs().sum(dim=1) > 0)
+    hit = torch.stack(hits).view(3, H, W)
+    # most 16 x 8 tiles see no hit ray
+    tiles = torch.zeros((3, (H + 7) // 8 * 8, (W + 15) // 16 * 16), dtype=torch.bool, device="cuda")
+    tiles[:, :H, :W] = hit
+    any_hit = tiles.view(3, (H + 7) // 8, 8, (W + 15) // 16, 16).any(dim=4).any(dim=2)
+    assert 0 < int(any_hit.sum()) < 0.5 * any_hit.numel()
+    mode = rc.RC_SAMPLING_RANGE if sampling == "range" else rc.RC_SAMPLING_INVCDF
+    a = torch.full((3, H, W, 4), -1.0, device="cuda")
+    b = torch.full((3, H, W, 4), -1.0, device="cuda")
+    fa = torch.empty((3, n), dtype=torch.uint8, device="cuda")
+    fbb = torch.empty_like(fa)
+    rc.rc_render_importance_views(r.ctx, r.vol, params_for(), cams, mode, 0.05, net[:, :, :32].contiguous(),
+                                  net[:, :, 32].contiguous(), 64, 0.02, a, fa)
+    rc.rc_render_proposal_sampled(r.ctx, r.vol, params_for(), cams, mode, 0.05, 64, 0.02, b, fbb)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(fa, fbb)
+    assert float(b[hit].abs().max()) > 0 and float(b[~hit].abs().max()) == 0.0
+
+
 # --------------------------------------------------------------------------
 # trained on 32 phantoms, evaluated on 8 held out
 # --------------------------------------------------------------------------
