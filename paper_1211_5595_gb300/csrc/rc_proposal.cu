@@ -719,18 +719,20 @@ __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A)
 // the input gradient (rays as M)
 // ---------------------------------------------------------------------------
 // Weight gradient of layer l: dW_l = H_{l-1}^T dZ_l over the tile's 128 rays,
-// an M = 128 MMA whose A rows are the layer's inputs (H^T, written here with
-// the rays contiguous), a row of ones (its D row is the bias gradient
-// sum_rays dZ) and zero rows; B is dZ^T (outputs x rays). Input gradient:
-// dH_{l-1} = dZ_l W_l^T, A = dZ (rays x outputs), B = W_l (inputs x outputs).
-// All operands BF16 (dZ rounded once), FP32 accumulation.
+// an M = 128, K = 128 MMA that reads both operands MN-major: A = H^T from H
+// itself (rays x inputs, the forward's K-major operand, whose ones column
+// gives the D row of the bias gradient sum_rays dZ, zero columns after it)
+// and B = dZ^T from dZ (rays x outputs): no transposed copies. Input gradient:
+// dH_{l-1} = dZ_l W_l^T, A = dZ (rays x outputs, K-major), B = W_l (inputs x
+// outputs). All operands BF16 (dZ rounded once), FP32 accumulation. (Writing
+// H^T and dZ^T as separate transposed operands took 1.062 ms per 1 M rays
+// against 0.764 with the MN-major reads; the gradients are identical bit for
+// bit.)
 struct TrainSmem {
     uint8_t w[kUmmaAllBytes];              // forward and backward B operands
-    uint8_t x[128 * kFeat * 2];            // A: features (rays x 112)
-    uint8_t h[3][128 * kHid * 2];          // A: H1, H2, H3 (rays x 64)
-    uint8_t adz[128 * kHid * 2];           // A: dZ (rays x outputs)
-    uint8_t bdz[kHid * 128 * 2];           // B: dZ^T (outputs x rays)
-    uint8_t at[128 * 128 * 2];             // A: inputs^T + ones row (128 rows x rays)
+    uint8_t x[128 * 128 * 2];              // features (rays x 112), ones column 112, zero columns after it
+    uint8_t h[3][128 * 128 * 2];           // H1..H3 (rays x 64), ones column 64, zero columns after it
+    uint8_t adz[128 * kHid * 2];           // dZ (rays x outputs)
     float bias[3 * kHid + kN4];
     float wloss[4];
     unsigned long long bar_w, bar_m;
@@ -747,6 +749,17 @@ __device__ __forceinline__ void issue_mma(uint32_t a0, int rows_a, uint32_t b0, 
     for (int ks = 0; ks < K / 16; ks++)
         tc::mma_bf16(tmem_d, tc::smem_desc(a0 + ks * 2 * lbo_a, lbo_a, 128), tc::smem_desc(b0 + ks * 2 * lbo_b, lbo_b, 128),
                      idesc, accumulate || ks > 0);
+}
+
+// D (+)= A B^T over K = 128 rays with A and B read MN-major from operands
+// stored rays x M and rays x N (core matrices of 8 rays x 8 elements; the
+// K-adjacent cores 128 bytes apart, the M- or N-adjacent ones 2048): the
+// weight gradient straight from the forward's operands.
+__device__ __forceinline__ void issue_mma_mn(uint32_t a0, uint32_t b0, int n, uint32_t tmem_d, bool accumulate) {
+    const uint32_t idesc = tc::idesc_bf16_f32(128, n) | tc::kIdescMnMajorA | tc::kIdescMnMajorB;
+    for (int ks = 0; ks < 8; ks++)
+        tc::mma_bf16(tmem_d, tc::smem_desc(a0 + ks * 256, 128, 2048), tc::smem_desc(b0 + ks * 256, 128, 2048), idesc,
+                     accumulate || ks > 0);
 }
 
 // A bounded wait for the CTA's committed MMAs (all 128 threads).
@@ -773,41 +786,21 @@ __device__ __forceinline__ float get_bf16(const uint8_t *M, int row, int k, int 
     return __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(M + tc::core_offset(row, k, rows)));
 }
 
-// Column t of the weight-gradient A operand: the thread's n inputs (BF16,
-// already rounded; n a multiple of 8, read 8 at a time from the thread's own
-// row of src) in rows 0..n-1, 1 in row n; rows n+1 .. zero_to-1 zeroed.
-__device__ __forceinline__ void put_inputs_t(uint8_t *at, const uint8_t *src, int n, int t, int zero_to) {
-    for (int r0 = 0; r0 < n; r0 += 8) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(src + tc::core_offset(t, r0, 128));
-        const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&q);
-#pragma unroll
-        for (int i = 0; i < 8; i++) *reinterpret_cast<__nv_bfloat16 *>(at + tc::core_offset(r0 + i, t, 128)) = h[i];
-    }
-    put_bf16(at, n, t, 128, 1.0f);
-    for (int r = n + 1; r < zero_to; r++) put_bf16(at, r, t, 128, 0.0f);
-}
-
-// dZ of this thread's ray (n values) as row t of A (K = k_pad, 8 values per
-// 16-byte store) and column t of B^T.
-__device__ __forceinline__ void put_dz(TrainSmem &S, const float (&dz)[kHid], int n, int k_pad, int t, bool as_a) {
+// dZ of this thread's ray (n values, zeros up to k_pad) as row t of the dZ
+// operand, 8 values per 16-byte store.
+__device__ __forceinline__ void put_dz(TrainSmem &S, const float (&dz)[kHid], int n, int k_pad, int t) {
 #pragma unroll
     for (int j0 = 0; j0 < kHid; j0 += 8) {
         if (j0 >= k_pad) break;
-        float v[8];
+        uint4 q;
+        uint32_t *w = reinterpret_cast<uint32_t *>(&q);
 #pragma unroll
-        for (int i = 0; i < 8; i++) v[i] = j0 + i < n ? dz[j0 + i] : 0.0f;
-        if (as_a) {
-            uint4 q;
-            uint32_t *w = reinterpret_cast<uint32_t *>(&q);
-#pragma unroll
-            for (int h = 0; h < 4; h++) {
-                __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
-                w[h] = *reinterpret_cast<uint32_t *>(&b2);
-            }
-            *reinterpret_cast<uint4 *>(S.adz + tc::core_offset(t, j0, 128)) = q;
+        for (int h = 0; h < 4; h++) {
+            const float lo = j0 + 2 * h < n ? dz[j0 + 2 * h] : 0.0f, hi = j0 + 2 * h + 1 < n ? dz[j0 + 2 * h + 1] : 0.0f;
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+            w[h] = *reinterpret_cast<uint32_t *>(&b2);
         }
-#pragma unroll
-        for (int i = 0; i < 8; i++) put_bf16(S.bdz, j0 + i, t, k_pad, v[i]);
+        *reinterpret_cast<uint4 *>(S.adz + tc::core_offset(t, j0, 128)) = q;
     }
 }
 
@@ -828,8 +821,12 @@ __global__ void __launch_bounds__(128) tc_train_kernel(const TrainArgs A) {
         else if (j < kOut) b = A.params[kOffB4 + j];
         S.bias[i] = b;
     }
-    // the weight-gradient A operand starts all zero (rows beyond the ones row)
-    for (int i = t; i < 128 * 128 * 2 / 16; i += blockDim.x) reinterpret_cast<uint4 *>(S.at)[i] = make_uint4(0, 0, 0, 0);
+    // features and hidden layers all zero, then their ones columns (constant:
+    // the tiles rewrite the value columns only)
+    for (int i = t; i < 4 * 128 * 128 * 2 / 16; i += blockDim.x) reinterpret_cast<uint4 *>(S.x)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    put_bf16(S.x, t, kFeat, 128, 1.0f);
+    for (int l = 0; l < 3; l++) put_bf16(S.h[l], t, kHid, 128, 1.0f);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -931,15 +928,12 @@ __global__ void __launch_bounds__(128) tc_train_kernel(const TrainArgs A) {
         // backward, layer 4 .. 1
 #pragma unroll 1
         for (int l = 3; l >= 0 && ok; l--) {
-            const int n_out = l == 3 ? kN4 : kHid, n_in = l == 0 ? kFeat : kHid;
-            put_dz(S, dz, l == 3 ? kOut : kHid, n_out, t, l > 0);
-            // inputs^T with the ones row; rows up to 113 are cleared when the
-            // previous layer (layer 1 of the previous tile) used more rows
-            put_inputs_t(S.at, l == 0 ? S.x : S.h[l - 1], n_in, t, l == 3 ? kFeat + 1 : n_in + 1);
+            const int n_out = l == 3 ? kN4 : kHid;
+            put_dz(S, dz, l == 3 ? kOut : kHid, n_out, t);
             operands_ready();
             const uint32_t wcol = l == 3 ? kColW4 : l == 2 ? kColW3 : l == 1 ? kColW2 : kColW1;
             if (t == 0 && A.issue_mma) {
-                issue_mma(tc::smem_addr(S.at), 128, tc::smem_addr(S.bdz), n_out, 128, tmem + wcol, !first);
+                issue_mma_mn(tc::smem_addr(l == 0 ? S.x : S.h[l - 1]), tc::smem_addr(S.adz), n_out, tmem + wcol, !first);
                 if (l > 0) {
                     const uint32_t bb = l == 3 ? kUmmaB4 : l == 2 ? kUmmaB3 : kUmmaB2;
                     issue_mma(tc::smem_addr(S.adz), 128, tc::smem_addr(S.w) + bb, kHid, n_out, tmem + kColD, false);

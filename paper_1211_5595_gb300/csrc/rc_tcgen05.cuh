@@ -4,12 +4,18 @@
 // global-to-shared copy. Every wait is bounded by a clock budget and reports
 // failure instead of spinning forever.
 //
-// Operand layout (both A and B, K-major, no swizzle): 8 x 8 BF16 core
-// matrices of 128 contiguous bytes (8 rows of 16 bytes). For a matrix of R
-// rows and K columns, core (row8, kc) sits at byte ((kc * R/8) + row8) * 128;
-// the descriptor's leading byte offset is the distance between K-adjacent
-// cores (R/8 * 128) and its stride byte offset the distance between
-// row-adjacent cores (128). One MMA consumes K = 16 (two cores along K).
+// Operand layout (no swizzle): 8 x 8 BF16 core matrices of 128 contiguous
+// bytes (8 rows of 16 bytes). K-major: for a matrix of R rows and K columns,
+// core (row8, kc) sits at byte ((kc * R/8) + row8) * 128 and holds 8 rows of
+// 8 consecutive K; the descriptor's leading byte offset is the distance
+// between K-adjacent cores (R/8 * 128) and its stride byte offset the
+// distance between row-adjacent cores (128). MN-major (the instruction
+// descriptor's transpose bits): a core holds 8 consecutive K of 8 consecutive
+// M (or N) elements, and again the leading byte offset is the distance
+// between K-adjacent cores and the stride byte offset the distance between
+// M- (N-) adjacent ones; a K-major operand stored rays x C is so read as the
+// MN-major C x rays operand with offsets 128 and R/8 * 128. One MMA consumes
+// K = 16 (two cores along K).
 #pragma once
 
 #include <stdint.h>
@@ -39,6 +45,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+// Instruction-descriptor bits that read A (bit 15) or B (bit 16) MN-major.
+constexpr uint32_t kIdescMnMajorA = 1u << 15, kIdescMnMajorB = 1u << 16;
 
 // D[tmem] (+)= A * B^T for one K = 16 slice; issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
