@@ -1045,6 +1045,15 @@ def main():
         a = counters["warp_instructions_per_launch"] / launch_avg_s
         issue = {"achieved_warp_inst_s": a, "peak_warp_inst_s": issue_peak, "frac": a / issue_peak,
                  "peak_kind": "4 issue slots per SM per clock x SMs x median SM clock under load"}
+    # the bytes a frame cannot avoid: the volume's FP32 values read once and
+    # the image written once (the brick grid and table are negligible), at
+    # the measured HBM rate, against the measured frame time
+    vol_bytes = 4 * int(np.prod(ph.dims))
+    img_bytes = 16 * H * W
+    floor_us = (vol_bytes + img_bytes) / (hbm_peak * 1e9) * 1e6
+    floor = {"bytes_per_frame": vol_bytes + img_bytes, "volume_bytes": vol_bytes, "image_bytes": img_bytes,
+             "us_per_frame_at_hbm_peak": floor_us,
+             "frac_of_frame_time": floor_us / (1e3 * statistics.median(frame_ms))}
     line = {
         "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -1069,7 +1078,8 @@ def main():
                      "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
                      "l1_data_pipe_frac": (counters["l1_data_pipe_pct"] / 100.0) if "l1_data_pipe_pct" in counters
                      else None,
-                     "dram": dram, "l2": l2, "issue": issue},
+                     "dram": dram, "l2": l2, "issue": issue,
+                     "compulsory_floor": floor},
         "e2e": e2e,
         "forms": forms,
         # per step, this library's kernels (the ncu launch list): the volume
