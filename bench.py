@@ -954,12 +954,13 @@ def main():
         # (one loop alone moves by several percent with the host's load)
         # (the slowest rank's time of each loop, the ranks started together)
         runs, loop_steps = [], []
-        # the garbage collector paused in the timed loops, as timeit does (a
-        # collection pass stalled a single step by 12-14 ms now and then); no
-        # clock sampler here: its queries go through the same driver
+        # five timed loops, the median reported: a single step of a loop can
+        # stall by 10-25 ms on a busy host; the garbage collector paused in
+        # the loops, as timeit does; no clock sampler here: its queries go
+        # through the same driver
         gc.collect()
         gc.disable()
-        for _ in range(3):
+        for _ in range(5):
             if world > 1:
                 dist.barrier()
             t0 = time.perf_counter()
@@ -976,7 +977,7 @@ def main():
                "h2d_bytes_per_step": codes_host.numel() * 2 + tf.nbytes,
                "d2h_bytes_per_step": img_host.numel() * 4,
                "runs": runs, "run_step_ms": loop_steps,
-               "timing": f"host clock over {args.steps} steps, median of 3 loops"}
+               "timing": f"host clock over {args.steps} steps, median of 5 loops"}
 
     hbm_peak, peak_kind = peaks()
     # reduced-precision storage forms on the same workload: FP16 (normalised)
