@@ -152,9 +152,10 @@ rc_status rc_context_destroy(rc_context *ctx);
  * lies in 16b..16b+15 per axis), each stored with an apron as the 19^3 voxels
  * 16b-1..16b+17 (clamped to the volume) in the chosen storage, with a min/max
  * grid over the cell-bricks (footprint voxels 16b..min(16b+16, N-1)). FP32
- * storage and uint16 storage with vmax < 32768 also hold value+gradient
- * bricks (each voxel's value and central differences: 16 and 8 bytes per
- * voxel) that shaded and 2-D-table samples read. */
+ * storage, uint16 storage with vmax < 32768 and FP16 storage with
+ * vmax <= 4096 also hold value+gradient bricks (each voxel's stored value and
+ * the central differences of its codes: 16 bytes per voxel for FP32, 8 for
+ * the others) that shaded and 2-D-table samples read. */
 rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz,
                            float sx, float sy, float sz, uint16_t vmax,
                            rc_storage storage, rc_volume **out);

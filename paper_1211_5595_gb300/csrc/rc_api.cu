@@ -90,7 +90,7 @@ struct rc_volume {
     int cb[3] = {0, 0, 0};       // cell-bricks per axis (each stored as a 19^3 apron brick)
     int nbricks = 0;             // cell-bricks
     void *d_data = nullptr;
-    void *d_vg = nullptr;        // value+gradient bricks (FP32 storage; uint16 storage with vmax < 32768)
+    void *d_vg = nullptr;        // value+gradient bricks (FP32; uint16 with vmax < 32768; FP16 with vmax <= 4096)
     void *d_pairs = nullptr;     // pair bricks (storage type), built on the first render that reads them
     uint64_t pairs_data_version = ~0ull;
     uint16_t *d_stage = nullptr;
@@ -342,11 +342,14 @@ rc_status rc_volume_create(rc_context *ctx, int nx, int ny, int nz, float sx, fl
     v->nbricks = v->cb[0] * v->cb[1] * v->cb[2];
     size_t esz = storage == RC_STORE_F32 ? 4 : 2;
     size_t nvox = (size_t)nx * ny * nz;
-    // value+gradient bricks: FP32 storage, and uint16 storage while the
-    // central differences fit 16 bits (vmax < 32768)
-    const size_t vg_bytes = storage == RC_STORE_F32                   ? (size_t)v->nbricks * kGradVox * sizeof(float4)
-                            : storage == RC_STORE_U16 && vmax < 32768 ? (size_t)v->nbricks * kGradVox * sizeof(uint2)
-                                                                      : 0;
+    // value+gradient bricks: FP32 storage; uint16 storage while the central
+    // differences fit 16 bits (vmax < 32768); FP16 storage while every stored
+    // value is exact (vmax <= 4096: offset o <= 2048), so that the differences
+    // of stored values are integer code differences / o
+    const size_t vg_bytes = storage == RC_STORE_F32 ? (size_t)v->nbricks * kGradVox * sizeof(float4)
+                            : (storage == RC_STORE_U16 && vmax < 32768) || (storage == RC_STORE_F16 && vmax <= 4096)
+                                ? (size_t)v->nbricks * kGradVox * sizeof(uint2)
+                                : 0;
     const size_t n4 = (size_t)((nx - 1 + 3) / 4) * ((ny - 1 + 3) / 4) * ((nz - 1 + 3) / 4);
     if (dev_alloc(&v->d_data, (size_t)padded * esz) != cudaSuccess ||
         (vg_bytes && dev_alloc(&v->d_vg, vg_bytes) != cudaSuccess) ||

@@ -318,6 +318,45 @@ __device__ __forceinline__ float value_grad_vg16(const VolDev &v, const Cell &c,
     return r.x;
 }
 
+// value_grad_vg for FP16 storage (8-byte entries: the stored FP16 value h and
+// the code differences offset by 32768): the value is interpolated from the
+// h as the FP16 storage's other paths do (lerp(a, b, w) = fma(w, b - a, a),
+// x, then y, then z), the differences as integers, and the gradient of h is
+// the code gradient / o (o a power of two: exact scaling).
+__device__ __forceinline__ float value_grad_vg16h(const VolDev &v, const Cell &c, float g[3]) {
+    const unsigned idx = (unsigned)brick_of(v, c) * (unsigned)kGradVox +
+                         (unsigned)(((c.i[2] & 15) * kGradEdge + (c.i[1] & 15)) * kGradEdge + (c.i[0] & 15));
+    const uint2 *p = reinterpret_cast<const uint2 *>(v.vg) + idx;
+    constexpr int DY = kGradEdge, DZ = kGradEdge * kGradEdge;
+    const unsigned long long wx = pack2(c.w[0], c.w[0]), wy = pack2(c.w[1], c.w[1]), wz = pack2(c.w[2], c.w[2]);
+    // (h, D_x + m) and (D_y + m, D_z + m) with m = 2^23 + 32768 (as vg16_biased);
+    // along x the bias leaves the first entry only, and h is not biased
+    auto lerp_x = [&](uint2 qa, uint2 qb) {
+        const ulonglong2 a = vg16_biased(qa), b = vg16_biased(qb);
+        const float ha = __half2float(__ushort_as_half((unsigned short)(qa.x & 0xFFFFu)));
+        const float hb = __half2float(__ushort_as_half((unsigned short)(qb.x & 0xFFFFu)));
+        const unsigned long long a0 = pack2(ha, unpack2(a.x).y), b0 = pack2(hb, unpack2(b.x).y);
+        unsigned long long d0, d1, s0, s1, r0, r1;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d0) : "l"(b0), "l"(a0));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d1) : "l"(b.y), "l"(a.y));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(s0) : "l"(a0), "l"(pack2(0.0f, 8421376.0f)));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(s1) : "l"(a.y), "l"(pack2(8421376.0f, 8421376.0f)));
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r0) : "l"(wx), "l"(d0), "l"(s0));
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r1) : "l"(wx), "l"(d1), "l"(s1));
+        return make_ulonglong2(r0, r1);
+    };
+    const ulonglong2 c00 = lerp_x(__ldg(p), __ldg(p + 1));
+    const ulonglong2 c10 = lerp_x(__ldg(p + DY), __ldg(p + DY + 1));
+    const ulonglong2 c01 = lerp_x(__ldg(p + DZ), __ldg(p + DZ + 1));
+    const ulonglong2 c11 = lerp_x(__ldg(p + DZ + DY), __ldg(p + DZ + DY + 1));
+    const float4 r = unpack4(lerp4p(lerp4p(c00, c10, wy), lerp4p(c01, c11, wy), wz));
+    const float inv_o = 1.0f / (float)v.f16o;
+    g[0] = r.y * v.inv2s[0] * inv_o;
+    g[1] = r.z * v.inv2s[1] * inv_o;
+    g[2] = r.w * v.inv2s[2] * inv_o;
+    return r.x;
+}
+
 // Value and world-space central-difference gradient of the trilinear field,
 // one index unit per axis, from the 32 distinct voxels around the cell.
 // The samples at p -/+ e_a use the cells with base coordinates
@@ -399,6 +438,7 @@ template <int ST>
 __device__ __forceinline__ float value_grad(const VolDev &v, const Cell &c, float g[3]) {
     if (ST == RC_STORE_F32) return value_grad_vg(v, c, g);
     if (ST == RC_STORE_U16 && v.vg != nullptr) return value_grad_vg16(v, c, g);
+    if (ST == RC_STORE_F16 && v.vg != nullptr) return value_grad_vg16h(v, c, g);
     if (ST == RC_STORE_F16 && v.pairs != nullptr) return value_grad_x<ST, true>(v, c, g);
     return value_grad_x<ST, false>(v, c, g);
 }

@@ -39,11 +39,13 @@ cudaError_t launch_pairs(VolDev v, void *dst, cudaStream_t s) {
 //     h = fp16((code - o) / o) with the volume's offset o (a power of two with
 //     2o >= vmax, so |code - o| <= 2048 is an FP16 integer for 12-bit data and
 //     h is exact), U16 the code;
-//   - FP32 and uint16 storage: the 17^3 value+gradient entries of voxels
-//     16b .. 16b+16 (clamped) as (V, V(x+1) - V(x-1), V(y+1) - V(y-1),
-//     V(z+1) - V(z-1)), neighbour indices clamped to the volume: exact in FP32
-//     (float4), and for uint16 as 16-bit fields with the differences offset by
-//     32768 (uint2: V | Dx << 16, Dy | Dz << 16);
+//   - the 17^3 value+gradient entries of voxels 16b .. 16b+16 (clamped) as
+//     (V, V(x+1) - V(x-1), V(y+1) - V(y-1), V(z+1) - V(z-1)) of the codes,
+//     neighbour indices clamped to the volume: exact in FP32 (float4) for
+//     FP32 storage; for uint16 as 16-bit fields with the differences offset
+//     by 32768 (uint2: V | Dx << 16, Dy | Dz << 16); for FP16 the same with
+//     the bits of the stored FP16 value h in place of V (the differences of
+//     stored values are the code differences / o, exactly, when o <= 2048);
 //   - the trilinear cell-brick min / max over voxels max(16b, 0) .. min(16b+16, N-1);
 //   - the trilinear min / max of the brick's 4^3 sub-blocks j over voxels
 //     4j .. min(4j+4, N-1) (ceil((N-1)/4) sub-blocks per axis).
@@ -55,7 +57,7 @@ struct PrepArgs {
     int vmax;
     int f16o;                    // FP16 storage: the offset o
     void *apron;
-    void *vg;                    // float4 (FP32 storage), uint2 (uint16 storage), null (FP16)
+    void *vg;                    // float4 (FP32 storage), uint2 (uint16, FP16 storage) or null
     uint16_t *mn, *mx, *mn4, *mx4;
 };
 
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs A) {
     auto at = [&](int x, int y, int z) {
         return (int)s_code[((z - z0) * kApron + (y - y0)) * kApron + (x - x0)];
     };
-    if (ST != RC_STORE_F16 && A.vg != nullptr) {
+    if (A.vg != nullptr) {
         for (unsigned e = threadIdx.x; e < (unsigned)kGradVox; e += blockDim.x) {
             const int lx = (int)(e % kGradEdge), ly = (int)((e / kGradEdge) % kGradEdge),
                       lz = (int)(e / (kGradEdge * kGradEdge));
@@ -98,6 +100,12 @@ __global__ void __launch_bounds__(256) prep_kernel(const PrepArgs A) {
             if (ST == RC_STORE_F32) {
                 reinterpret_cast<float4 *>(A.vg)[(size_t)b * kGradVox + e] =
                     make_float4((float)V, (float)dx, (float)dy, (float)dz);
+            } else if (ST == RC_STORE_F16) {
+                // the apron brick's value of this voxel, h = fp16((V - o) / o)
+                const __half h = __float2half_rn(__fdiv_rn((float)(V - A.f16o), (float)A.f16o));
+                reinterpret_cast<uint2 *>(A.vg)[(size_t)b * kGradVox + e] =
+                    make_uint2((unsigned)__half_as_ushort(h) | ((unsigned)(dx + 32768) << 16),
+                               (unsigned)(dy + 32768) | ((unsigned)(dz + 32768) << 16));
             } else {
                 // codes <= 65535 and differences in (-32768, 32768): 16-bit fields
                 reinterpret_cast<uint2 *>(A.vg)[(size_t)b * kGradVox + e] =
