@@ -553,7 +553,46 @@ __device__ __forceinline__ void range_of(const MarchArgs &a, const Ray &R, const
 
 // nimp samples at the centres of nimp equal segments of [t_a, t_b] (start of
 // bin b0 to end of bin b1), each with its opacity corrected to the segment.
-template <int ST, bool SHADE>
+// jump_block on the evenly spaced grid t_j = ta + (j + 0.5) seg, j < n, of a
+// range march: the first sample index that may lie outside the empty block
+// of 2^s cells around cell c (sample j is in it). The sample m just before
+// the computed exit is verified to be in the same block, with its position
+// computed exactly as the march computes it; positions are monotone in j
+// along each axis, so every sample between j and m is in the block too.
+// Falls back to j + 1 when the check fails.
+__device__ __forceinline__ int jump_block_grid(const Ray &R, const VolDev &v, const Cell &c, int j, int s, float ta,
+                                               float seg, int n) {
+    const float INF = __int_as_float(0x7f800000);
+    float texit = INF;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int lo = (c.i[a] >> s) << s, hi = lo + (1 << s);
+        if (R.d[a] > 0.0f && hi <= v.n[a] - 2)
+            texit = fminf(texit, __fdiv_rn((float)hi - R.o[a], R.d[a]));
+        else if (R.d[a] < 0.0f && lo > 0)
+            texit = fminf(texit, __fdiv_rn((float)lo - R.o[a], R.d[a]));
+    }
+    if (texit == INF) return n;
+    const float fm = floorf(__fsub_rn(__fdiv_rn(texit - ta, seg), 0.5f));
+    int m = fm >= (float)n ? n - 1 : (int)fm;
+    if (m <= j) return j + 1;
+#pragma unroll 1
+    for (int tries = 0; tries < 2 && m > j; tries++, m--) {
+        float p[3];
+        position_at(R, __fmaf_rn((float)m + 0.5f, seg, ta), p);
+        Cell cm;
+        cell_of(v, p, cm);
+        if (((cm.i[0] ^ c.i[0]) >> s) == 0 && ((cm.i[1] ^ c.i[1]) >> s) == 0 && ((cm.i[2] ^ c.i[2]) >> s) == 0)
+            return m + 1;
+    }
+    return j + 1;
+}
+
+// JUMP: past an empty block in one step (jump_block_grid) instead of sample by
+// sample; pays where a block spans several samples (measured on the bench
+// orbit, ms per frame: 64 samples per ray 0.1735 -> 0.169, 128 samples
+// 0.254 -> 0.228; 16 and 32 samples 3-4% slower, so chosen from 48 samples up)
+template <int ST, bool SHADE, bool JUMP>
 __device__ __forceinline__ void march_range(const ImportanceArgs &A, const float4 *s_tf, const Ray &R, int b0, int b1,
                                             float &C0, float &C1, float &C2, float &T, unsigned &evald) {
     const MarchArgs &a = A.m;
@@ -564,18 +603,23 @@ __device__ __forceinline__ void march_range(const ImportanceArgs &A, const float
     const float ratio = __fdiv_rn(seg, a.vol.smin);
     C0 = C1 = C2 = 0.0f;
     T = 1.0f;
-    for (int j = 0; j < A.nimp; j++) {
+    for (int j = 0; j < A.nimp;) {
         float p[3];
         position_at(R, __fmaf_rn((float)j + 0.5f, seg, ta), p);
         Cell c;
         cell_of(a.vol, p, c);
-        if (a.p.skip) {                                                   // opacity exactly 0
+        if (a.p.skip) {          // opacity exactly 0: past the largest empty block around the sample
             const int b = brick_of(a.vol, c);
-            if (a.fine ? empty_block(__ldg(a.fine + b), c) >= 0 : !__ldg(a.occ + b)) continue;
+            const int s = a.fine ? empty_block(__ldg(a.fine + b), c) : (__ldg(a.occ + b) ? -1 : 4);
+            if (s >= 0) {
+                j = JUMP ? jump_block_grid(R, a.vol, c, j, s, ta, seg, A.nimp) : j + 1;
+                continue;
+            }
         }
         float4 e = eval_sample<ST, SHADE>(a.vol, a.p, s_tf, a.tf.K, a.tf.ucoef, R.dir, c, 3, ratio);
         composite_add(e, C0, C1, C2, T);
         evald++;
+        j++;
         if ((1.0f - T) >= a.p.term) break;
     }
 }
@@ -662,7 +706,7 @@ __device__ __forceinline__ void importance_stats(const MarchArgs &a, unsigned ev
 // (never without a T^).
 enum { kSrcRecords = 0, kSrcRange = 1, kSrcInvCdf = 2 };
 
-template <int ST, bool SHADE, int SRC>
+template <int ST, bool SHADE, int SRC, bool JUMP = false>
 __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A) {
     const MarchArgs &a = A.m;
     extern __shared__ float4 s_tf[];
@@ -699,7 +743,7 @@ __global__ void __launch_bounds__(128) importance_kernel(const ImportanceArgs A)
                 that = A.that[pix];
                 range_of(a, R, pdf, 0u, false, b0, b1);
             }
-            march_range<ST, SHADE>(A, s_tf, R, b0, b1, C0, C1, C2, T, evald);
+            march_range<ST, SHADE, JUMP>(A, s_tf, R, b0, b1, C0, C1, C2, T, evald);
         }
         if (check && fabsf(T - that) > A.eps) {
             fb = 1;
@@ -1160,9 +1204,12 @@ static cudaError_t launch_imp_st(const ImportanceArgs &a, int nviews, cudaStream
         kern<<<grid, 128, smem, s>>>(a);
         return cudaGetLastError();
     };
-    if (a.range) return go(importance_kernel<ST, SHADE, kSrcRecords>);
+    // the range marches jump empty blocks from 48 samples per ray up
+    const bool jump = a.nimp >= 48;
+    if (a.range)
+        return jump ? go(importance_kernel<ST, SHADE, kSrcRecords, true>) : go(importance_kernel<ST, SHADE, kSrcRecords>);
     if (a.sampling == RC_SAMPLING_INVCDF) return go(importance_kernel<ST, SHADE, kSrcInvCdf>);
-    return go(importance_kernel<ST, SHADE, kSrcRange>);
+    return jump ? go(importance_kernel<ST, SHADE, kSrcRange, true>) : go(importance_kernel<ST, SHADE, kSrcRange>);
 }
 
 cudaError_t launch_importance(const ImportanceArgs &a, int nviews, cudaStream_t s) {
