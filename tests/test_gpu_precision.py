@@ -85,6 +85,50 @@ def test_fp32_storage_with_fp16_table_matches_diagnostic(rc, orc):
         r.close()
 
 
+@pytest.mark.parametrize("vmax,scale", [(4096, 1), (12000, 3)])
+def test_f16_value_gradient_bricks_and_pairs(rc, orc, vmax, scale):
+    """FP16 storage with vmax <= 4096 (offset o <= 2048, every stored value
+    exact) reads shaded samples from its 8-byte value+gradient bricks (the
+    stored FP16 value and the code differences); above, from pair bricks of
+    the stored values (o = 8192 for vmax 12000: values rounded to FP16). Both
+    match the FP64 oracle on the same stored values (diagnostic oracle, FP16
+    table), shaded with a 1-D and a 2-D table and as isosurface, within 2e-4."""
+    ph = synth.head_phantom((70, 58, 41), (1.0, 0.9, 1.3), seed=36, tumor_radius_vox=4)
+    data = np.minimum(ph.vol.astype(np.int64) * scale, vmax).astype(np.uint16)
+    # a table over the code range of this vmax: the default table's shape
+    tf = synth.tf_table(256)
+    cam = synth.orbit_camera(ph.dims, ph.spacing, 140.0, width=75, height=53)
+    r = GPURenderer(rc, data, ph.spacing, storage=rc.RC_STORE_F16, vmax=vmax)
+    try:
+        r.set_tf(tf, fp16=True)
+        P = dict(step_vox=0.5, term=0.99, shade=True, skip=True)
+        img = r.render(cam, **P)
+        o = orc.render(orc.Scene(data, ph.spacing, tf, cam, step=0.5, term=0.99, shade=True, vmax=vmax,
+                                 value_mode=1, tf_fp16=True))
+        compare(img, o, TOL_FP32)
+        assert o["rgba"][..., 3].max() > 0.3
+        # isosurface: the hit sample (FP32 and FP64 may disagree on one within
+        # rounding of the iso-value), its distance and its shading
+        iso = float(0.4 * vmax)
+        img = r.render(cam, step_vox=0.5, term=0.99, shade=True, skip=True, func=rc.RC_FUNC_ISO, iso=iso)
+        o = orc.render(orc.Scene(data, ph.spacing, tf, cam, step=0.5, term=0.99, shade=True, vmax=vmax,
+                                 value_mode=1, tf_fp16=True, func=orc.ISO, iso=iso))
+        g, a = img.reshape(-1, 4).astype(np.float64), o["rgba"].reshape(-1, 4)
+        same = (g[:, 3] == a[:, 3]) & (g[:, 2] == a[:, 2])
+        assert same.mean() > 0.99 and a[:, 3].sum() > 100
+        np.testing.assert_allclose(g[same][:, 0], a[same][:, 0], rtol=1e-5, atol=1e-4)
+        np.testing.assert_allclose(g[same][:, 1], a[same][:, 1], atol=2e-4)
+        gmax = 1200.0 * scale
+        tab = synth.tf2d_table(256, 16, gmax)
+        rc.rc_tf2d_set(r.ctx, tab, gmax, True)
+        img = r.render(cam, **P)
+        o = orc.render(orc.Scene(data, ph.spacing, tab, cam, step=0.5, term=0.99, shade=True, vmax=vmax,
+                                 value_mode=1, tf_fp16=True, gmax=gmax))
+        compare(img, o, TOL_FP32)
+    finally:
+        r.close()
+
+
 def test_u16_value_gradient_bricks_equal_fp32_storage(rc, orc):
     """uint16 storage with vmax < 32768 reads the gradient from 8-byte
     value+gradient bricks holding the same integers as the FP32 storage's
